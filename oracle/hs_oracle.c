@@ -1,0 +1,475 @@
+/*
+ * hs_oracle.c -- plain, slow, obviously-correct FP64 CPU oracle for the
+ * single-spin Metropolis sweep of the classical anisotropic Heisenberg model.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing on the product path may link, load or
+ * call this file: only the test suite, the smoke check and the CPU-baseline
+ * leg of the benchmark use it.  It shares no code, header, table or helper
+ * with the CUDA library; the two are written separately and compared.
+ *
+ * What it follows (arXiv 2106.11286):
+ *   - Eq. 1:  H = -J sum_<ij> S_i.S_j - K sum_i (S_i.e)^2, |S_i| = 1
+ *             (each nearest-neighbour bond counted once).
+ *   - Metropolis steps (i)-(iii): pick a site, propose a new orientation at
+ *             random, accept if dH <= 0, else accept iff P <= exp(-beta dH)
+ *             with P uniform in [0,1).
+ *   - Eq. 2:  M = (1 / (N |S|)) sum_i S_i.
+ * Readings where the paper is silent (all listed in the design notes):
+ *   - sites are visited colour class by colour class (independent sets of
+ *     the neighbour graph), ascending natural index inside a class;
+ *   - the trial orientation is uniform on the sphere: z = 2u-1,
+ *     phi = pi (2u'-1), r = sqrt((1-z)(1+z)), S' = (r cos phi, r sin phi, z);
+ *   - random numbers come from Philox4x32-10 (Salmon, Moraes, Dror, Shaw,
+ *     "Parallel random numbers: as easy as 1, 2, 3", SC'11), counter
+ *     (site, sweep, tag<<24 | colour<<8 | call, replica), key (seed lo, hi).
+ *
+ * Build: gcc -O2 -ffp-contract=off -fPIC -shared (no FMA contraction, so
+ * every product and sum is the one written here).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------------ */
+/* Philox4x32-10, from its published definition (SC'11, Sec. 4 / Table 2):  */
+/* a round multiplies words 0 and 2 by two fixed odd constants, swaps the   */
+/* high/low halves across lanes and xors in the round key; the key is       */
+/* bumped by the two Weyl constants between rounds.                          */
+/* ------------------------------------------------------------------------ */
+#define PHILOX_M0 0xD2511F53u
+#define PHILOX_M1 0xCD9E8D57u
+#define PHILOX_W0 0x9E3779B9u
+#define PHILOX_W1 0xBB67AE85u
+
+void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    uint32_t x0 = ctr[0], x1 = ctr[1], x2 = ctr[2], x3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) {
+            k0 += PHILOX_W0;
+            k1 += PHILOX_W1;
+        }
+        uint64_t p0 = (uint64_t)PHILOX_M0 * (uint64_t)x0;
+        uint64_t p1 = (uint64_t)PHILOX_M1 * (uint64_t)x2;
+        uint32_t y0 = (uint32_t)(p1 >> 32) ^ x1 ^ k0;
+        uint32_t y1 = (uint32_t)p1;
+        uint32_t y2 = (uint32_t)(p0 >> 32) ^ x3 ^ k1;
+        uint32_t y3 = (uint32_t)p0;
+        x0 = y0; x1 = y1; x2 = y2; x3 = y3;
+    }
+    out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
+}
+
+/* Uniform in [0,1) on the 2^-53 grid from two words (27 + 26 top bits).   */
+double or_u53(uint32_t a, uint32_t b)
+{
+    double hi = (double)(a >> 5);
+    double lo = (double)(b >> 6);
+    return (hi * 67108864.0 + lo) / 9007199254740992.0; /* 2^26, 2^53 */
+}
+
+/* Uniform in [0,1) on the 2^-24 grid from the top 24 bits of one word.     */
+double or_u24(uint32_t a)
+{
+    return (double)(a >> 8) / 16777216.0; /* 2^24 */
+}
+
+enum { OR_TAG_TRIAL = 0, OR_TAG_INIT = 1 };
+
+/* Counter/key schedule of one Philox call. */
+static void or_draw(uint64_t seed, uint32_t replica, uint64_t site, uint64_t sweep,
+                    uint32_t tag, uint32_t colour, uint32_t call, uint32_t out[4])
+{
+    uint32_t ctr[4], key[2];
+    ctr[0] = (uint32_t)site;
+    ctr[1] = (uint32_t)sweep;
+    ctr[2] = (tag << 24) | (colour << 8) | call;
+    ctr[3] = replica;
+    key[0] = (uint32_t)seed;
+    key[1] = (uint32_t)(seed >> 32);
+    or_philox4x32_10(ctr, key, out);
+}
+
+/* Uniform point on the unit sphere from two uniforms (Archimedes: z is
+ * uniform on [-1,1), the azimuth uniform on [-pi,pi)). */
+static void or_sphere_point(double uz, double uphi, double s[3])
+{
+    double z = 2.0 * uz - 1.0;
+    double v = 2.0 * uphi - 1.0;
+    double phi = M_PI * v;
+    double r = sqrt((1.0 - z) * (1.0 + z));
+    s[0] = r * cos(phi);
+    s[1] = r * sin(phi);
+    s[2] = z;
+}
+
+/* Draw the two uniforms (u_z, u_phi) and the acceptance uniform P of one
+ * trial move.  mode 0: FP64 schedule (two Philox calls, three 53-bit
+ * uniforms).  mode 1 and 2: FP32 schedule (one call, three 24-bit uniforms). */
+static void or_trial_uniforms(int mode, uint64_t seed, uint32_t replica, uint64_t site,
+                              uint64_t sweep, uint32_t colour, double u[3])
+{
+    uint32_t r[4];
+    if (mode == 0) {
+        or_draw(seed, replica, site, sweep, OR_TAG_TRIAL, colour, 0, r);
+        u[0] = or_u53(r[0], r[1]);
+        u[1] = or_u53(r[2], r[3]);
+        or_draw(seed, replica, site, sweep, OR_TAG_TRIAL, colour, 1, r);
+        u[2] = or_u53(r[0], r[1]);
+    } else {
+        or_draw(seed, replica, site, sweep, OR_TAG_TRIAL, colour, 0, r);
+        u[0] = or_u24(r[0]);
+        u[1] = or_u24(r[1]);
+        u[2] = or_u24(r[2]);
+    }
+}
+
+/* Round a double to the nearest binary16 value (round half to even),
+ * returned as a double.  Written from the IEEE 754 binary16 definition:
+ * 11 significant bits for |x| >= 2^-14, a fixed 2^-24 spacing below. */
+double or_round_half(double x)
+{
+    if (x == 0.0 || !isfinite(x))
+        return x;
+    double a = fabs(x);
+    int e;
+    frexp(a, &e); /* a = f * 2^e, f in [0.5,1) */
+    int exp_unbiased = e - 1; /* a in [2^(e-1), 2^e) */
+    double quantum;
+    if (exp_unbiased < -14)
+        quantum = ldexp(1.0, -24);
+    else
+        quantum = ldexp(1.0, exp_unbiased - 10);
+    double q = a / quantum;            /* exact: power-of-two scaling */
+    double n = nearbyint(q);           /* default rounding: half to even */
+    double rounded = n * quantum;
+    if (rounded > 65504.0)
+        rounded = INFINITY;
+    return x < 0 ? -rounded : rounded;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Lattices.  Natural index:                                                 */
+/*   sc : i = (z*Ly + y)*Lx + x                                              */
+/*   bcc: i = ((cz*Ly + cy)*Lx + cx)*2 + b, b=0 cube corner, b=1 centre      */
+/*   fcc: i = ((cz*Ly + cy)*Lx + cx)*4 + b, basis (0,0,0),(0,h,h),(h,0,h),   */
+/*        (h,h,0) with h = 1/2                                               */
+/* Neighbour order of each site is fixed:                                    */
+/*   sc : -x, +x, -y, +y, -z, +z                                             */
+/*   bcc: the 8 diagonal offsets with dz, then dy, then dx ascending         */
+/*   fcc: the 12 offsets (two half-integer components) with dz, dy, dx       */
+/*        ascending                                                          */
+/* Open boundaries drop the missing neighbours; periodic ones wrap.          */
+/* Each builder fills row_ptr[n+1]; col may be NULL to count only.           */
+/* ------------------------------------------------------------------------ */
+static int wrap(int v, int L, int periodic, int *ok)
+{
+    if (v >= 0 && v < L)
+        return v;
+    if (!periodic) {
+        *ok = 0;
+        return 0;
+    }
+    return ((v % L) + L) % L;
+}
+
+int64_t or_sc_neighbours(int Lx, int Ly, int Lz, int periodic, int64_t *row_ptr, int32_t *col)
+{
+    static const int off[6][3] = {{-1, 0, 0}, {1, 0, 0}, {0, -1, 0}, {0, 1, 0}, {0, 0, -1}, {0, 0, 1}};
+    int64_t nnz = 0;
+    int64_t i = 0;
+    row_ptr[0] = 0;
+    for (int z = 0; z < Lz; ++z)
+        for (int y = 0; y < Ly; ++y)
+            for (int x = 0; x < Lx; ++x, ++i) {
+                for (int k = 0; k < 6; ++k) {
+                    int ok = 1;
+                    int nx = wrap(x + off[k][0], Lx, periodic, &ok);
+                    int ny = wrap(y + off[k][1], Ly, periodic, &ok);
+                    int nz = wrap(z + off[k][2], Lz, periodic, &ok);
+                    if (!ok)
+                        continue;
+                    if (col)
+                        col[nnz] = (int32_t)(((int64_t)nz * Ly + ny) * Lx + nx);
+                    ++nnz;
+                }
+                row_ptr[i + 1] = nnz;
+            }
+    return nnz;
+}
+
+int64_t or_bcc_neighbours(int Lx, int Ly, int Lz, int periodic, int64_t *row_ptr, int32_t *col)
+{
+    int64_t nnz = 0;
+    int64_t i = 0;
+    row_ptr[0] = 0;
+    for (int cz = 0; cz < Lz; ++cz)
+        for (int cy = 0; cy < Ly; ++cy)
+            for (int cx = 0; cx < Lx; ++cx)
+                for (int b = 0; b < 2; ++b, ++i) {
+                    /* corner (b=0) sees the centres of the 8 cells around it,
+                     * i.e. cell offsets in {-1,0}; a centre (b=1) sees the 8
+                     * corners of its own cell, i.e. offsets in {0,1}. */
+                    int lo = (b == 0) ? -1 : 0;
+                    for (int dz = lo; dz <= lo + 1; ++dz)
+                        for (int dy = lo; dy <= lo + 1; ++dy)
+                            for (int dx = lo; dx <= lo + 1; ++dx) {
+                                int ok = 1;
+                                int nx = wrap(cx + dx, Lx, periodic, &ok);
+                                int ny = wrap(cy + dy, Ly, periodic, &ok);
+                                int nz = wrap(cz + dz, Lz, periodic, &ok);
+                                if (!ok)
+                                    continue;
+                                if (col)
+                                    col[nnz] = (int32_t)((((int64_t)nz * Ly + ny) * Lx + nx) * 2 + (1 - b));
+                                ++nnz;
+                            }
+                    row_ptr[i + 1] = nnz;
+                }
+    return nnz;
+}
+
+/* fcc basis in half-lattice-constant units. */
+static const int fcc_basis[4][3] = {{0, 0, 0}, {0, 1, 1}, {1, 0, 1}, {1, 1, 0}};
+
+static int fcc_basis_index(int px, int py, int pz)
+{
+    for (int b = 0; b < 4; ++b)
+        if (fcc_basis[b][0] == px && fcc_basis[b][1] == py && fcc_basis[b][2] == pz)
+            return b;
+    return -1;
+}
+
+static int floor_div2(int v) { return (v >= 0) ? v / 2 : -((-v + 1) / 2); }
+
+int64_t or_fcc_neighbours(int Lx, int Ly, int Lz, int periodic, int64_t *row_ptr, int32_t *col)
+{
+    int64_t nnz = 0;
+    int64_t i = 0;
+    row_ptr[0] = 0;
+    for (int cz = 0; cz < Lz; ++cz)
+        for (int cy = 0; cy < Ly; ++cy)
+            for (int cx = 0; cx < Lx; ++cx)
+                for (int b = 0; b < 4; ++b, ++i) {
+                    /* position in half units */
+                    int px = 2 * cx + fcc_basis[b][0];
+                    int py = 2 * cy + fcc_basis[b][1];
+                    int pz = 2 * cz + fcc_basis[b][2];
+                    for (int dz = -1; dz <= 1; ++dz)
+                        for (int dy = -1; dy <= 1; ++dy)
+                            for (int dx = -1; dx <= 1; ++dx) {
+                                int nonzero = (dx != 0) + (dy != 0) + (dz != 0);
+                                if (nonzero != 2)
+                                    continue;
+                                int qx = px + dx, qy = py + dy, qz = pz + dz;
+                                int ncx = floor_div2(qx), ncy = floor_div2(qy), ncz = floor_div2(qz);
+                                int nb = fcc_basis_index(qx - 2 * ncx, qy - 2 * ncy, qz - 2 * ncz);
+                                int ok = (nb >= 0);
+                                ncx = wrap(ncx, Lx, periodic, &ok);
+                                ncy = wrap(ncy, Ly, periodic, &ok);
+                                ncz = wrap(ncz, Lz, periodic, &ok);
+                                if (!ok)
+                                    continue;
+                                if (col)
+                                    col[nnz] = (int32_t)((((int64_t)ncz * Ly + ncy) * Lx + ncx) * 4 + nb);
+                                ++nnz;
+                            }
+                    row_ptr[i + 1] = nnz;
+                }
+    return nnz;
+}
+
+/* Structured colouring: sc (x+y+z) mod 2, bcc and fcc the basis index.
+ * kind: 0 sc, 1 bcc, 2 fcc. */
+void or_colour_structured(int kind, int Lx, int Ly, int Lz, int32_t *colour)
+{
+    int64_t i = 0;
+    int nb = (kind == 0) ? 1 : (kind == 1 ? 2 : 4);
+    for (int z = 0; z < Lz; ++z)
+        for (int y = 0; y < Ly; ++y)
+            for (int x = 0; x < Lx; ++x)
+                for (int b = 0; b < nb; ++b, ++i)
+                    colour[i] = (kind == 0) ? ((x + y + z) & 1) : b;
+}
+
+/* Greedy colouring: present vertices in ascending natural index each take
+ * the smallest colour not held by an already-coloured present neighbour.
+ * Absent vertices get colour -1.  Returns the number of colours. */
+int or_colour_greedy(int64_t n, const int64_t *row_ptr, const int32_t *col, const uint8_t *mask,
+                     int32_t *colour)
+{
+    int n_colours = 0;
+    int cap = 64;
+    char *used = (char *)malloc((size_t)cap);
+    for (int64_t i = 0; i < n; ++i)
+        colour[i] = -1;
+    for (int64_t i = 0; i < n; ++i) {
+        if (mask && !mask[i])
+            continue;
+        int64_t deg = row_ptr[i + 1] - row_ptr[i];
+        if (deg + 1 > cap) {
+            cap = (int)(deg + 1);
+            used = (char *)realloc(used, (size_t)cap);
+        }
+        memset(used, 0, (size_t)cap);
+        for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
+            int32_t c = colour[col[k]];
+            if (c >= 0 && c < cap)
+                used[c] = 1;
+        }
+        int c = 0;
+        while (used[c])
+            ++c;
+        colour[i] = c;
+        if (c + 1 > n_colours)
+            n_colours = c + 1;
+    }
+    free(used);
+    return n_colours;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Initial state: each present site gets an independent uniform point on   */
+/* the sphere from one Philox call with tag INIT at sweep 0, colour 0.     */
+/* Absent sites are zero.  S is n x 3, natural order.                       */
+/* ------------------------------------------------------------------------ */
+void or_init_spins(int64_t n, const uint8_t *mask, uint64_t seed, uint32_t replica, double *S)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        if (mask && !mask[i]) {
+            S[3 * i] = S[3 * i + 1] = S[3 * i + 2] = 0.0;
+            continue;
+        }
+        uint32_t r[4];
+        or_draw(seed, replica, (uint64_t)i, 0, OR_TAG_INIT, 0, 0, r);
+        or_sphere_point(or_u53(r[0], r[1]), or_u53(r[2], r[3]), &S[3 * i]);
+    }
+}
+
+/* Single-site energy -J S.h - K (S.e)^2 for a given local field h. */
+static double site_energy(const double s[3], const double h[3], double J, double K, const double e[3])
+{
+    double sh = s[0] * h[0] + s[1] * h[1] + s[2] * h[2];
+    double se = s[0] * e[0] + s[1] * e[1] + s[2] * e[2];
+    return -J * sh - K * se * se;
+}
+
+/* ------------------------------------------------------------------------ */
+/* One Metropolis sweep: colour classes 0..n_colours-1 in order, present    */
+/* sites of the class in ascending natural index.                           */
+/*   mode 0: FP64 random-number schedule, spins kept in FP64               */
+/*   mode 1: FP32 random-number schedule, spins kept in FP64               */
+/*   mode 2: FP32 schedule, the trial spin rounded to binary16 per          */
+/*           component before dH (the stored state is the rounded one)     */
+/* Outputs: returns accepted moves; *sum_dH gets the sum of accepted dH;    */
+/* *n_band counts dH > 0 decisions with |beta dH + ln P| < band; band_site  */
+/* (optional, n bytes) is set to 1 at those sites.                          */
+/* ------------------------------------------------------------------------ */
+int64_t or_sweep(int64_t n, const int64_t *row_ptr, const int32_t *col, const int32_t *colour,
+                 int n_colours, const uint8_t *mask, double J, double K, const double e[3],
+                 double beta, uint64_t seed, uint32_t replica, uint64_t sweep, int mode, double band,
+                 double *S, double *sum_dH, int64_t *n_band, uint8_t *band_site)
+{
+    int64_t accepted = 0;
+    double dH_total = 0.0;
+    int64_t bands = 0;
+    for (int c = 0; c < n_colours; ++c) {
+        for (int64_t i = 0; i < n; ++i) {
+            if (colour[i] != c)
+                continue;
+            if (mask && !mask[i])
+                continue;
+            /* step (i): site i; local field from present neighbours */
+            double h[3] = {0.0, 0.0, 0.0};
+            for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
+                int32_t j = col[k];
+                if (mask && !mask[j])
+                    continue;
+                h[0] += S[3 * (int64_t)j];
+                h[1] += S[3 * (int64_t)j + 1];
+                h[2] += S[3 * (int64_t)j + 2];
+            }
+            /* step (ii): random new orientation */
+            double u[3];
+            or_trial_uniforms(mode, seed, replica, (uint64_t)i, sweep, (uint32_t)c, u);
+            double trial[3];
+            or_sphere_point(u[0], u[1], trial);
+            if (mode == 2) {
+                trial[0] = or_round_half(trial[0]);
+                trial[1] = or_round_half(trial[1]);
+                trial[2] = or_round_half(trial[2]);
+            }
+            /* step (iii): energy change from Eq. 1 and the acceptance test */
+            double *s = &S[3 * i];
+            double dH = site_energy(trial, h, J, K, e) - site_energy(s, h, J, K, e);
+            double P = u[2];
+            int accept;
+            if (dH <= 0.0) {
+                accept = 1;
+            } else {
+                accept = (P <= exp(-beta * dH));
+                if (band > 0.0 && P > 0.0 && fabs(beta * dH + log(P)) < band) {
+                    ++bands;
+                    if (band_site)
+                        band_site[i] = 1;
+                }
+            }
+            if (accept) {
+                s[0] = trial[0];
+                s[1] = trial[1];
+                s[2] = trial[2];
+                dH_total += dH;
+                ++accepted;
+            }
+        }
+    }
+    if (sum_dH)
+        *sum_dH = dH_total;
+    if (n_band)
+        *n_band = bands;
+    return accepted;
+}
+
+/* Total energy, Eq. 1, full recompute: every undirected bond once (pairs
+ * listed as j > i in a symmetric neighbour list), plus the anisotropy of
+ * every present site. */
+double or_energy(int64_t n, const int64_t *row_ptr, const int32_t *col, const uint8_t *mask, double J,
+                 double K, const double e[3], const double *S)
+{
+    double exch = 0.0, anis = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        if (mask && !mask[i])
+            continue;
+        const double *si = &S[3 * i];
+        for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
+            int64_t j = col[k];
+            if (j <= i)
+                continue;
+            if (mask && !mask[j])
+                continue;
+            const double *sj = &S[3 * j];
+            exch += si[0] * sj[0] + si[1] * sj[1] + si[2] * sj[2];
+        }
+        double se = si[0] * e[0] + si[1] * e[1] + si[2] * e[2];
+        anis += se * se;
+    }
+    return -J * exch - K * anis;
+}
+
+/* Sum of the present spins (numerator of Eq. 2); returns the count N. */
+int64_t or_spin_sum(int64_t n, const uint8_t *mask, const double *S, double out[3])
+{
+    int64_t count = 0;
+    out[0] = out[1] = out[2] = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        if (mask && !mask[i])
+            continue;
+        out[0] += S[3 * i];
+        out[1] += S[3 * i + 1];
+        out[2] += S[3 * i + 2];
+        ++count;
+    }
+    return count;
+}
