@@ -1,0 +1,371 @@
+"""Benchmark: Metropolis spin-update attempts/ns of the single-spin sweep of the
+3-D anisotropic Heisenberg model (arXiv 2106.11286) on one GB300, and the
+fraction of the HBM roofline reached by the colour-pass kernel.
+
+Workload (the headline configuration): sc 256^3 periodic (16,777,216 spins),
+J = 1, K = 0.05, e = z, T = 1.2, random start from seed 2, FP32 spin storage
+with FP64 reductions.  One step = one Metropolis sweep = both colour passes
+with the fused E / M reductions into the FP64 accumulator.  The same
+workload in plain FP64 is timed beside it ("fp64").  The state (201 MB in
+FP32, 403 MB in FP64) is larger than the 129 MB L2, so no flush is needed
+between steps.
+
+Prints one JSON line (rank 0).  Under torchrun (N > 1) every rank advances
+its own replica of the workload (replica index = rank; no data-path
+collective) and the whole-job value is the attempts of all ranks over the
+slowest rank's time ("scaling": "weak").
+
+``--impl reference`` times the CPU oracle (the plain FP64 C program that
+defines the expected results) on this machine's host cores instead, each step
+one oracle sweep of a bounded sub-lattice with the same parameters.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(name="sc256_fp32", kind="sc", L=256, J=1.0, K=0.05, e=(0.0, 0.0, 1.0), T=1.2, seed=2)
+METRIC = "Metropolis spin-update attempts/ns (sc 256^3, FP32 spins, FP64 reductions)"
+UNIT = "attempts/ns"
+BYTES_PER_SPIN = {"fp64": 24, "fp32": 12, "fp16": 6}
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "sc_pass_fp32_sc256_traffic.txt")
+
+
+def config_dict(args, n_gpus):
+    w = WORKLOAD
+    return {"workload": f"sc {w['L']}^3 periodic, J={w['J']}, K={w['K']}, e=z, T={w['T']}, seed {w['seed']}, "
+                        f"FP32 spins + FP64 reductions; step = 1 sweep (2 colour passes, fused E/M)",
+            "lattice": "sc", "L": w["L"], "n_spins": w["L"] ** 3, "precision": "fp32",
+            "sweeps_per_step": 1, "l2_policy": "inputs larger than L2 (201 MB state vs 129 MB L2)",
+            "parallelism": f"replicas x{n_gpus}" if n_gpus > 1 else "1 GPU"}
+
+
+# ------------------------------------------------------------------ helpers
+def kernels_sha() -> str:
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(os.path.join(ROOT, "paper_2106_11286_gb300", "csrc"))):
+        with open(os.path.join(ROOT, "paper_2106_11286_gb300", "csrc", f), "rb") as fh:
+            h.update(f.encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+def read_traffic():
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel sources (else None)."""
+    try:
+        kv = {}
+        for line in open(TRAFFIC_FILE):
+            if ":" in line and not line.startswith("#"):
+                k, v = line.split(":", 1)
+                kv[k.strip()] = v.strip()
+        if kv.get("sources_sha") != kernels_sha():
+            return None
+        return float(kv["dram_bytes_per_launch"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "20"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            time.sleep(0.3)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc is not None:
+            time.sleep(0.1)
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.strip().splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], 0.0, set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for l in getattr(self, "lines", []):
+            parts = [p.strip() for p in l.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = max(mx, float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ distributed
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def aggregate(local_attempts: float, local_seconds: float, world: int, device=None):
+    """Whole-job throughput: attempts of all ranks / slowest rank's time."""
+    if world == 1:
+        return local_attempts, local_seconds
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([local_attempts, local_seconds], dtype=torch.float64, device=device)
+    a = t[0:1].clone()
+    s = t[1:2].clone()
+    dist.all_reduce(a, op=dist.ReduceOp.SUM)
+    dist.all_reduce(s, op=dist.ReduceOp.MAX)
+    return float(a.item()), float(s.item())
+
+
+# ------------------------------------------------------------------ our arm
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_2106_11286_gb300 import hs
+
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    w = WORKLOAD
+    L = w["L"]
+    N = L ** 3
+    beta = 1.0 / w["T"]
+    stream = torch.cuda.Stream(device=dev)
+    params = dict(J=w["J"], K=w["K"], e=w["e"], seed=w["seed"], replica=rank, stream=stream)
+
+    def barrier_sync():
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    # ---- headline: FP32, step = one sweep with fused reductions
+    lat = hs.Lattice("sc", dims=(L, L, L), precision="fp32", **params)
+    lat.init()
+    lat.accumulate(True)
+    lat.sweep(beta, args.warmup)
+    lat.reset_accumulator()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    barrier_sync()
+    with ClockSampler(local) as clk:
+        hs.hs_enable_timing(lat.h, True)
+        t0.record(stream)
+        lat.sweep(beta, args.steps)
+        t1.record(stream)
+        barrier_sync()
+    ms = t0.elapsed_time(t1)
+    k_ms, k_launches = hs.hs_read_timing(lat.h)
+    hs.hs_enable_timing(lat.h, False)
+    mom, count = lat.read_accumulator()
+    meas = lat.measure()
+    tot_attempts, tot_s = aggregate(float(N) * args.steps, ms / 1e3, world, dev)
+    value = tot_attempts / (tot_s * 1e9)
+    kernel_ms = k_ms / max(k_launches, 1)
+    alg_bytes = 3 * BYTES_PER_SPIN["fp32"] * (N // 2)   # per launch: N/2 attempts x 3 s
+    peaks, peak_kind = measured_peaks()
+    achieved_gbs = alg_bytes / (kernel_ms * 1e-3) / 1e9
+    traffic = read_traffic()
+    roofline = {"bound": "hbm", "achieved": round(achieved_gbs, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": round(achieved_gbs / peaks["hbm_gbs"], 4), "traffic": traffic,
+                "peak_source": f"{peak_kind} copy bandwidth", "kernel": "sc_pass_kernel<fp32>",
+                "kernel_ms": round(kernel_ms, 5), "alg_bytes_per_launch": alg_bytes,
+                "frac_of_8TBs_nominal": round(achieved_gbs / 8000.0, 4)}
+    physics = {"E_per_spin": mom[0] / count / N, "absM": mom[2] / count, "accept_rate": meas["accept_rate"],
+               "sweeps_averaged": count}
+    lat.close()
+
+    # ---- plain FP64 form of the same workload
+    fp64 = None
+    if not args.no_fp64:
+        lat64 = hs.Lattice("sc", dims=(L, L, L), precision="fp64", **params)
+        lat64.init()
+        lat64.accumulate(True)
+        lat64.sweep(beta, 3)
+        barrier_sync()
+        hs.hs_enable_timing(lat64.h, True)
+        t0.record(stream)
+        lat64.sweep(beta, args.fp64_steps)
+        t1.record(stream)
+        barrier_sync()
+        ms64 = t0.elapsed_time(t1)
+        k64, n64 = hs.hs_read_timing(lat64.h)
+        a64, s64 = aggregate(float(N) * args.fp64_steps, ms64 / 1e3, world, dev)
+        km64 = k64 / max(n64, 1)
+        gbs64 = 3 * BYTES_PER_SPIN["fp64"] * (N // 2) / (km64 * 1e-3) / 1e9
+        fp64 = {"value": round(a64 / (s64 * 1e9), 4), "unit": UNIT, "steps": args.fp64_steps,
+                "ms_per_step": round(ms64 / args.fp64_steps, 4), "kernel_ms": round(km64, 4),
+                "hbm_GBs": round(gbs64, 1), "hbm_frac": round(gbs64 / peaks["hbm_gbs"], 4),
+                "bound": "fp64 ALU (GB300 FP64 rate), see roofline notes"}
+        lat64.close()
+
+    # ---- end to end through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        rng = np.random.default_rng(w["seed"])
+        S0 = rng.standard_normal((N, 3))
+        S0 /= np.linalg.norm(S0, axis=1, keepdims=True)
+        host = torch.from_numpy(S0).pin_memory()
+        lat = hs.Lattice("sc", dims=(L, L, L), precision="fp32", **params)
+        lat.accumulate(True)
+        mom_out = np.zeros(hs.HS_N_MOMENTS)
+        cnt = hs.ctypes.c_int64(0)
+        sweeps = args.e2e_sweeps
+
+        def e2e_step():
+            hs.load().hs_set_spins(lat.h, host.data_ptr())                 # H2D of the step's input state
+            lat.reset_accumulator()
+            lat.sweep(beta, sweeps)
+            hs.load().hs_read_accumulator(lat.h, mom_out.ctypes.data_as(hs._dp), hs.ctypes.byref(cnt))  # D2H
+        for _ in range(2):
+            e2e_step()
+        barrier_sync()
+        te = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            e2e_step()
+        barrier_sync()
+        se = time.perf_counter() - te
+        ea, es = aggregate(float(N) * sweeps * args.e2e_steps, se, world, dev)
+        e2e = {"value": round(ea / (es * 1e9), 4), "unit": UNIT, "h2d_bytes_per_step": int(N * 3 * 8),
+               "d2h_bytes_per_step": int(hs.HS_N_MOMENTS * 8 + 8), "sweeps_per_step": sweeps,
+               "steps": args.e2e_steps,
+               "what": "hs_set_spins from pinned host FP64 state, hs_sweep x sweeps_per_step, "
+                       "hs_read_accumulator to host; wall clock"}
+        lat.close()
+
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    if rank != 0:
+        return None
+    cpu = None if (args.no_cpu_baseline or world > 1) else cpu_baseline(args)
+    line = {"metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(tot_s * 1e3 / args.steps, 5), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": config_dict(args, world), "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": int(2 * args.steps), "clocks": clk.summary(), "fp64": fp64, "physics": physics}
+    return line
+
+
+# ------------------------------------------------------------------ CPU oracle
+def cpu_baseline(args, sweeps=None, L=None):
+    """The oracle as it stands, single-threaded, on a bounded sample of the
+    workload: a few sweeps of the full 256^3 lattice."""
+    from oracle import oracle as orc
+    w = WORKLOAD
+    L = L or w["L"]
+    sweeps = sweeps or args.cpu_sweeps
+    g = orc.lattice("sc", (L, L, L))
+    S = orc.init_spins(g, seed=w["seed"])
+    t = time.perf_counter()
+    for s in range(sweeps):
+        orc.sweep(g, S, J=w["J"], K=w["K"], e=w["e"], beta=1.0 / w["T"], seed=w["seed"], sweep_index=s,
+                  mode=orc.MODE_FP32)
+    dt = time.perf_counter() - t
+    n = g.n * sweeps
+    return {"value": round(n / (dt * 1e9), 6), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{sweeps} sweeps of the sc {L}^3 lattice ({n} attempts), FP64 oracle with the FP32 "
+                      f"random-number schedule, 1 thread, {dt:.1f} s"}
+
+
+def run_reference(args):
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return None
+    # bounded sample per step: an even sub-lattice sized so all steps take about a minute at ~150 ns/attempt
+    total = max(args.steps + args.warmup, 1)
+    L = int(round((4e8 / total) ** (1 / 3)))
+    L = max(8, min(WORKLOAD["L"], L - (L % 2)))
+    from oracle import oracle as orc
+    w = WORKLOAD
+    g = orc.lattice("sc", (L, L, L))
+    S = orc.init_spins(g, seed=w["seed"])
+
+    def step(s):
+        orc.sweep(g, S, J=w["J"], K=w["K"], e=w["e"], beta=1.0 / w["T"], seed=w["seed"], sweep_index=s,
+                  mode=orc.MODE_FP32)
+    for s in range(args.warmup):
+        step(s)
+    t = time.perf_counter()
+    for s in range(args.steps):
+        step(args.warmup + s)
+    dt = time.perf_counter() - t
+    n = g.n * args.steps
+    value = n / (dt * 1e9)
+    return {"impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt * 1e3 / max(args.steps, 1), 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_dict(args, world),
+            "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"each step one oracle sweep of an sc {L}^3 sub-lattice of the workload"},
+            "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--fp64-steps", type=int, default=30)
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--e2e-sweeps", type=int, default=100)
+    ap.add_argument("--cpu-sweeps", type=int, default=3)
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    line = run_reference(args) if args.impl == "reference" else run_ours(args)
+    if line is not None:
+        print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

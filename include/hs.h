@@ -1,0 +1,230 @@
+/*
+ * hs.h -- C ABI of the GB300 single-spin Metropolis library for the classical
+ * anisotropic Heisenberg model (arXiv 2106.11286).
+ *
+ * The method (all citations are to the paper):
+ *   Eq. 1   H = -J sum_<ij> S_i.S_j - K sum_i (S_i.e)^2, |S_i| = 1, each
+ *           nearest-neighbour bond counted once, e the uniaxial easy axis.
+ *   Metropolis steps (i)-(iii): pick a site, propose a random orientation,
+ *           accept if dH <= 0, else accept iff P <= exp(-beta dH), P uniform
+ *           in [0,1).
+ *   Eq. 2   M = (1 / (N |S|)) sum_i S_i with N the number of present spins.
+ *
+ * Parallel decomposition (the paper's own racy block scheme is replaced):
+ * the neighbour graph is split into colour classes (independent sets); a
+ * sweep updates class 0, then class 1, ..., each class fully in parallel.
+ * Sites inside a class share no bond and random numbers are keyed by site,
+ * so the result of a class update does not depend on the visiting order.
+ *   sc:  2 classes, colour = (x+y+z) mod 2  (periodic dims must be even)
+ *   bcc: 2 classes, colour = basis index (0 cube corner, 1 body centre)
+ *   fcc: 4 classes, colour = basis index
+ *   CSR: greedy colouring, present sites in ascending natural index each
+ *        take the smallest colour unused by an earlier-coloured neighbour.
+ *
+ * Random numbers: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) with
+ *   counter = (site natural index, sweep, tag<<24 | colour<<8 | call, replica)
+ *   key     = (seed & 0xffffffff, seed >> 32)
+ * tag 0 = trial move, tag 1 = initial spin.  The FP64 path draws two blocks
+ * per trial (calls 0 and 1): u_z from words 0,1, u_phi from words 2,3 of
+ * call 0 and P from words 0,1 of call 1, each u = ((a>>5) 2^26 + (b>>6)) 2^-53.
+ * The FP32 and FP16 paths draw one block: u_z, u_phi, P from words 0, 1, 2,
+ * each u = (a>>8) 2^-24.  Initial spins always use one FP64-schedule block.
+ * Trial orientation: z = 2u_z - 1, phi = pi (2u_phi - 1),
+ * r = sqrt((1-z)(1+z)), S' = (r cos phi, r sin phi, z).
+ * There is no random-number state in memory.
+ *
+ * Conventions for every call:
+ *   - Return HS_OK (0) or a negative hs_status; hs_last_error() gives a
+ *     thread-local message for the last failure on the calling thread.
+ *     Nothing aborts the process.
+ *   - Host arrays passed in are copied; the caller keeps ownership.
+ *   - The lattice handle owns all device memory it allocates.
+ *   - Device work is ordered on the CUDA stream given at creation (NULL =
+ *     the legacy default stream).  Calls that return data to host memory
+ *     synchronise that stream before returning.
+ *   - Spins cross the boundary in FP64, natural site order, 3 doubles per
+ *     site (x, y, z), for all n_sites natural indices; absent (masked) sites
+ *     read back as 0 and are ignored on input.
+ *   - A device-side error (a bounded wait that timed out) is latched on the
+ *     device and reported by the next call that synchronises.
+ */
+#ifndef HS_H
+#define HS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define HS_API_VERSION 1
+
+typedef struct hs_lattice hs_lattice;
+typedef struct hs_batch hs_batch;
+
+enum hs_lattice_type { HS_SC = 0, HS_BCC = 1, HS_FCC = 2, HS_CSR = 3 };
+enum hs_precision { HS_FP64 = 0, HS_FP32 = 1, HS_FP16 = 2 };
+enum hs_init_mode { HS_INIT_RANDOM = 0, HS_INIT_ALIGNED = 1 };
+enum hs_status {
+    HS_OK = 0,
+    HS_E_INVALID = -1, /* bad argument or unsupported shape */
+    HS_E_CUDA = -2,    /* a CUDA runtime call failed */
+    HS_E_OOM = -3,     /* device or host allocation failed */
+    HS_E_COLOUR = -4,  /* the requested structural colouring is not proper */
+    HS_E_TIMEOUT = -5, /* a bounded device-side wait gave up */
+    HS_E_DEVICE = -6   /* no usable CUDA device */
+};
+
+/* Hamiltonian parameters of Eq. 1.  e need not be normalised: the library
+ * normalises it (a zero vector is HS_E_INVALID). */
+typedef struct {
+    double J;
+    double K;
+    double e[3];
+} hs_params;
+
+/* Instantaneous observables (FP64), Eq. 1 and Eq. 2. */
+typedef struct {
+    double E;           /* total energy, each bond once */
+    double M[3];        /* M vector = sum S_i / N (|S| = 1) */
+    double absM;        /* |M| */
+    double M2;          /* |M|^2 */
+    double M4;          /* |M|^4 */
+    int64_t n_sites;    /* N: present spins */
+    double accept_rate; /* accepted / attempted moves of the last hs_sweep call */
+} hs_measurement;
+
+/* Layout of the per-sweep accumulator read by hs_read_accumulator. */
+#define HS_N_MOMENTS 9
+enum hs_moment {
+    HS_SUM_E = 0,     /* sum E            */
+    HS_SUM_E2 = 1,    /* sum E^2          */
+    HS_SUM_ABSM = 2,  /* sum |M|          */
+    HS_SUM_M2 = 3,    /* sum |M|^2        */
+    HS_SUM_M4 = 4,    /* sum |M|^4        */
+    HS_SUM_MX = 5,    /* sum M_x          */
+    HS_SUM_MY = 6,    /* sum M_y          */
+    HS_SUM_MZ = 7,    /* sum M_z          */
+    HS_SUM_ABSME = 8  /* sum |M . e|      */
+};
+
+typedef struct {
+    int type;          /* hs_lattice_type */
+    int precision;     /* hs_precision */
+    int n_colours;     /* colour classes per sweep */
+    int structured;    /* 1: sc stencil kernel, 0: neighbour-table kernel */
+    int64_t n_sites;   /* natural indices */
+    int64_t n_present; /* N */
+    int64_t device_bytes; /* device memory held by the handle */
+    uint64_t sweep;    /* next sweep index (Philox counter word 1) */
+} hs_info;
+
+/*
+ * Create a lattice, copy its geometry to the device and set all spins along
+ * +e (call hs_init_spins for a random start).
+ *   type      HS_SC / HS_BCC / HS_FCC: dims[3] = cells (Lx, Ly, Lz) and
+ *             periodic (0/1); row_ptr, col_idx must be NULL and n_sites is
+ *             ignored.  Natural index sc (z*Ly+y)*Lx+x, bcc/fcc
+ *             ((cz*Ly+cy)*Lx+cx)*B+b.  Periodic sc needs even dims >= 2.
+ *             Unmasked periodic sc with Lx/2 a multiple of the vector width
+ *             runs the stencil kernel; every other case runs the
+ *             neighbour-table kernel.
+ *             HS_CSR: row_ptr[n_sites+1] (int64, row_ptr[0] = 0) and
+ *             col_idx[row_ptr[n_sites]] (int32 in [0, n_sites), no self
+ *             loops) give a symmetric neighbour list; its stored order is
+ *             the order of the neighbour sum.  dims and periodic are ignored.
+ *   site_mask n_sites bytes, 0 = vacancy (removed from the graph), or NULL.
+ *   p         Eq. 1 parameters.
+ *   precision HS_FP64 / HS_FP32 / HS_FP16 spin storage and arithmetic (FP16
+ *             stores binary16 and computes in FP32); reductions are FP64.
+ *   seed, replica  Philox key and counter word 3.
+ *   cuda_stream    cudaStream_t to order all work on (NULL = default).
+ * Errors: HS_E_INVALID (shape, neighbour list), HS_E_COLOUR (odd periodic
+ * sc), HS_E_OOM, HS_E_CUDA, HS_E_DEVICE.  On error *out is NULL.
+ */
+int hs_lattice_create(hs_lattice **out, int type, const int32_t dims[3], int periodic,
+                      const int64_t *row_ptr, const int32_t *col_idx, int64_t n_sites,
+                      const uint8_t *site_mask, const hs_params *p, int precision, uint64_t seed,
+                      uint32_t replica, void *cuda_stream);
+
+/* Free the handle and its device memory (NULL is a no-op).  Synchronises
+ * the stream first. */
+void hs_lattice_destroy(hs_lattice *h);
+
+/* Initial state.  HS_INIT_RANDOM: every present site gets an independent
+ * uniform point on the sphere from the tag-1 Philox block of its natural
+ * index (sweep 0, colour 0), computed in FP64 and rounded to the storage
+ * precision.  HS_INIT_ALIGNED: every spin = +e.  Does not change the sweep
+ * counter. */
+int hs_init_spins(hs_lattice *h, int mode);
+
+/* n_sweeps Metropolis sweeps (Metropolis steps (i)-(iii), every present site
+ * attempted once per sweep, colour classes in order) at inverse temperature
+ * beta >= 0.  Sweep k of the call uses Philox counter word 1 = the sweep
+ * counter + k; the counter then advances by n_sweeps.  With accumulation on
+ * (hs_accumulate), every sweep also adds its E and M moments (computed
+ * inside the colour passes, FP64 totals) to the accumulator.  Asynchronous:
+ * returns after queueing the work on the stream. */
+int hs_sweep(hs_lattice *h, double beta, int64_t n_sweeps);
+
+/* Recompute E (Eq. 1) and M (Eq. 2) of the current state and copy them to
+ * *out; accept_rate refers to the last hs_sweep call.  Synchronous. */
+int hs_measure(hs_lattice *h, hs_measurement *out);
+
+/* Switch per-sweep accumulation of the moments on (1) or off (0). */
+int hs_accumulate(hs_lattice *h, int on);
+
+/* Zero the accumulator and its sweep count. */
+int hs_reset_accumulator(hs_lattice *h);
+
+/* Copy the HS_N_MOMENTS sums (hs_moment order) and the number of
+ * accumulated sweeps.  Synchronous. */
+int hs_read_accumulator(hs_lattice *h, double moments[HS_N_MOMENTS], int64_t *count);
+
+/* Spins to / from host memory: xyz is 3 * n_sites doubles in natural order.
+ * hs_set_spins normalises nothing: callers pass unit vectors.  Both are
+ * synchronous (the host buffer may be reused on return). */
+int hs_get_spins(hs_lattice *h, double *xyz);
+int hs_set_spins(hs_lattice *h, const double *xyz);
+
+/* Same with a device pointer (3 * n_sites doubles, device memory); ordered
+ * on the handle's stream, asynchronous. */
+int hs_get_spins_device(hs_lattice *h, double *d_xyz);
+int hs_set_spins_device(hs_lattice *h, const double *d_xyz);
+
+/* Set the next sweep index (checkpoint / resume: spins + sweep counter +
+ * seed + replica fix the rest of the chain bit for bit). */
+int hs_set_sweep_counter(hs_lattice *h, uint64_t sweep);
+
+int hs_get_info(const hs_lattice *h, hs_info *out);
+
+/* Per-kernel timing of the colour passes: when enabled, hs_sweep brackets
+ * each colour-pass launch with CUDA events on the handle's stream.
+ * hs_read_timing synchronises, returns the summed kernel time in ms and the
+ * number of timed launches since the last enable, and keeps counting. */
+int hs_enable_timing(hs_lattice *h, int on);
+int hs_read_timing(hs_lattice *h, double *ms, int64_t *launches);
+
+/* Host-only helper (no device needed): the greedy colouring the library
+ * uses for HS_CSR lattices.  colour_out[n] gets the class of each present
+ * site (-1 for masked sites); *n_colours the number of classes. */
+int hs_colour_greedy(int64_t n, const int64_t *row_ptr, const int32_t *col_idx,
+                     const uint8_t *site_mask, int32_t *colour_out, int *n_colours);
+
+/* Batched replicas: many independent lattices (FP32 periodic sc, any even L)
+ * advanced by one persistent kernel, each at its own beta.  Members stay
+ * owned by the caller and must outlive the batch; all must share one
+ * stream.  hs_batch_run performs n_equil sweeps without and then n_sweeps
+ * sweeps with accumulation into each member's accumulator. */
+int hs_batch_create(hs_batch **out, hs_lattice *const *members, int n_members);
+int hs_batch_run(hs_batch *b, const double *betas, int64_t n_sweeps, int64_t n_equil);
+void hs_batch_destroy(hs_batch *b);
+
+const char *hs_last_error(void);
+int hs_api_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HS_H */

@@ -1,0 +1,728 @@
+// C ABI of the GB300 Metropolis library (declarations and contract in
+// include/hs.h).  Host side: argument checks, lattice geometry, colouring,
+// colour-sorted renumbering, device allocation and the sweep schedule.
+//
+// Geometry (arXiv 2106.11286 states the method for "any crystal lattice";
+// the nearest-neighbour sets below are the sc / bcc / fcc coordination
+// shells, z = 6 / 8 / 12).  Neighbour order of each site, which is also the
+// order of the local-field sum:
+//   sc : -x, +x, -y, +y, -z, +z
+//   bcc: the 8 partner cells ordered by (dz, dy, dx) ascending; a corner
+//        (basis 0) pairs with the centres of cells c + {-1,0}^3, a centre
+//        with the corners of cells c + {0,1}^3
+//   fcc: the 12 displacements (two half-integer components, one zero)
+//        ordered by (dz, dy, dx) ascending
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "hs_impl.h"
+
+using hs::DevAccum;
+using hs::Layout;
+using hs::PassArgs;
+
+namespace {
+
+thread_local std::string g_error;
+
+int fail(int code, const std::string &msg) {
+    g_error = msg;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what) {
+    g_error = std::string(what) + ": " + cudaGetErrorString(e);
+    if (e == cudaErrorMemoryAllocation) return HS_E_OOM;
+    if (e == cudaErrorNoDevice || e == cudaErrorInsufficientDriver) return HS_E_DEVICE;
+    return HS_E_CUDA;
+}
+
+#define HS_CUDA(call)                                        \
+    do {                                                     \
+        cudaError_t e_ = (call);                             \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call);  \
+    } while (0)
+
+// ---------------------------------------------------------------- geometry
+struct Offset {
+    int dx, dy, dz, basis;
+};
+
+// Neighbour offsets (cell offset + partner basis) of each basis site.
+std::vector<std::vector<Offset>> lattice_offsets(int type) {
+    std::vector<std::vector<Offset>> off;
+    if (type == HS_SC) {
+        off.push_back({{-1, 0, 0, 0}, {1, 0, 0, 0}, {0, -1, 0, 0}, {0, 1, 0, 0}, {0, 0, -1, 0}, {0, 0, 1, 0}});
+    } else if (type == HS_BCC) {
+        for (int b = 0; b < 2; ++b) {
+            std::vector<Offset> o;
+            const int base = b == 0 ? -1 : 0;
+            for (int k = 0; k < 8; ++k)  // k = dz*4 + dy*2 + dx in {0,1}^3, dz slowest
+                o.push_back({base + (k & 1), base + ((k >> 1) & 1), base + (k >> 2), 1 - b});
+            off.push_back(o);
+        }
+    } else {  // fcc: basis in half units
+        const int B[4][3] = {{0, 0, 0}, {0, 1, 1}, {1, 0, 1}, {1, 1, 0}};
+        std::vector<std::array<int, 3>> disp;
+        for (int k = 0; k < 27; ++k) {
+            const int dx = k % 3 - 1, dy = (k / 3) % 3 - 1, dz = k / 9 - 1;
+            if ((dx != 0) + (dy != 0) + (dz != 0) == 2) disp.push_back({dx, dy, dz});
+        }
+        for (int b = 0; b < 4; ++b) {
+            std::vector<Offset> o;
+            for (auto &d : disp) {
+                int q[3], cell[3];
+                for (int a = 0; a < 3; ++a) {
+                    q[a] = B[b][a] + d[a];
+                    cell[a] = (q[a] >= 0) ? q[a] / 2 : -((1 - q[a]) / 2);
+                    q[a] -= 2 * cell[a];
+                }
+                int nb = -1;
+                for (int t = 0; t < 4; ++t)
+                    if (B[t][0] == q[0] && B[t][1] == q[1] && B[t][2] == q[2]) nb = t;
+                o.push_back({cell[0], cell[1], cell[2], nb});
+            }
+            off.push_back(o);
+        }
+    }
+    return off;
+}
+
+struct Graph {
+    int64_t n = 0;
+    std::vector<int64_t> row_ptr;
+    std::vector<int32_t> col;
+    std::vector<int32_t> colour;  // natural index -> class (-1 absent)
+    int n_colours = 0;
+};
+
+void build_structured(int type, const int32_t d[3], int periodic, Graph &g) {
+    const auto off = lattice_offsets(type);
+    const int nb = (int)off.size();
+    const int64_t Lx = d[0], Ly = d[1], Lz = d[2];
+    g.n = Lx * Ly * Lz * nb;
+    g.row_ptr.assign(g.n + 1, 0);
+    g.col.clear();
+    g.col.reserve((size_t)g.n * off[0].size());
+    g.colour.assign(g.n, 0);
+    int64_t i = 0;
+    for (int64_t cz = 0; cz < Lz; ++cz)
+        for (int64_t cy = 0; cy < Ly; ++cy)
+            for (int64_t cx = 0; cx < Lx; ++cx)
+                for (int b = 0; b < nb; ++b, ++i) {
+                    for (const Offset &o : off[b]) {
+                        int64_t x = cx + o.dx, y = cy + o.dy, z = cz + o.dz;
+                        const bool inside = x >= 0 && x < Lx && y >= 0 && y < Ly && z >= 0 && z < Lz;
+                        if (!inside) {
+                            if (!periodic) continue;
+                            x = (x + Lx) % Lx;
+                            y = (y + Ly) % Ly;
+                            z = (z + Lz) % Lz;
+                        }
+                        g.col.push_back((int32_t)(((z * Ly + y) * Lx + x) * nb + o.basis));
+                    }
+                    g.row_ptr[i + 1] = (int64_t)g.col.size();
+                    g.colour[i] = (type == HS_SC) ? (int32_t)((cx + cy + cz) & 1) : b;
+                }
+    g.n_colours = (type == HS_FCC) ? 4 : 2;
+}
+
+int greedy(int64_t n, const int64_t *row_ptr, const int32_t *col, const uint8_t *mask, int32_t *colour) {
+    std::vector<int64_t> seen;  // seen[c] == i marks colour c taken for site i
+    int n_colours = 0;
+    for (int64_t i = 0; i < n; ++i) colour[i] = -1;
+    for (int64_t i = 0; i < n; ++i) {
+        if (mask && !mask[i]) continue;
+        for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
+            const int32_t c = colour[col[k]];
+            if (c < 0) continue;
+            if ((size_t)c >= seen.size()) seen.resize((size_t)c + 1, -1);
+            seen[(size_t)c] = i;
+        }
+        int32_t c = 0;
+        while ((size_t)c < seen.size() && seen[(size_t)c] == i) ++c;
+        colour[i] = c;
+        n_colours = std::max(n_colours, c + 1);
+    }
+    return n_colours;
+}
+
+int check_csr(int64_t n, const int64_t *row_ptr, const int32_t *col) {
+    if (n < 0 || n >= (int64_t(1) << 31)) return fail(HS_E_INVALID, "n_sites must be in [0, 2^31)");
+    if (!row_ptr || (n > 0 && !col && row_ptr[n] > 0)) return fail(HS_E_INVALID, "row_ptr/col_idx missing");
+    if (row_ptr[0] != 0) return fail(HS_E_INVALID, "row_ptr[0] must be 0");
+    for (int64_t i = 0; i < n; ++i)
+        if (row_ptr[i + 1] < row_ptr[i]) return fail(HS_E_INVALID, "row_ptr must be non-decreasing");
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
+            if (col[k] < 0 || col[k] >= n) return fail(HS_E_INVALID, "col_idx out of range");
+            if (col[k] == i) return fail(HS_E_INVALID, "self loop in neighbour list");
+        }
+    return HS_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- handle
+struct hs_lattice {
+    int type = 0, precision = 0, periodic = 0, device = 0, n_sm = 0;
+    int32_t dims[3] = {0, 0, 0};
+    hs_params p{};
+    uint64_t seed = 0;
+    uint32_t replica = 0;
+    cudaStream_t stream = nullptr;
+    uint64_t sweep = 0;
+    int accumulate = 0;
+    int64_t last_n_sweeps = 0;
+    Layout L{};
+    int n_blocks = 1;
+    double *partials = nullptr;
+    DevAccum *acc = nullptr;
+    double *stage = nullptr;  // 3 * n_sites doubles, lazily for host copies
+    int64_t device_bytes = 0;
+    std::vector<void *> allocations;
+    // timing
+    bool timing = false;
+    std::vector<cudaEvent_t> ev;
+    size_t ev_used = 0;
+    double timed_ms = 0.0;
+    int64_t timed_launches = 0;
+
+    ~hs_lattice() {
+        cudaStreamSynchronize(stream);
+        for (void *a : allocations) cudaFree(a);
+        if (stage) cudaFree(stage);
+        for (cudaEvent_t e : ev) cudaEventDestroy(e);
+    }
+    template <typename T>
+    int alloc(T **ptr, size_t bytes) {
+        void *p_ = nullptr;
+        cudaError_t e = cudaMalloc(&p_, bytes ? bytes : 16);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+        allocations.push_back(p_);
+        device_bytes += (int64_t)bytes;
+        *ptr = static_cast<T *>(p_);
+        return HS_OK;
+    }
+};
+
+namespace {
+
+PassArgs base_args(const hs_lattice *h) {
+    PassArgs a{};
+    const Layout &L = h->L;
+    a.Lx = L.Lx;
+    a.Ly = L.Ly;
+    a.Lz = L.Lz;
+    a.Lh = L.Lh;
+    if (L.structured) {
+        a.div_nxv = hs::FastDiv((uint32_t)(L.Lh / L.vec));
+        a.div_ly = hs::FastDiv((uint32_t)L.Ly);
+    }
+    a.spins4 = L.spins4;
+    a.nbr = L.nbr;
+    a.nat = L.nat;
+    a.width = L.width;
+    a.n_pad = L.n_pad;
+    a.n_colours = L.n_colours;
+    a.J = h->p.J;
+    a.K = h->p.K;
+    a.e[0] = h->p.e[0];
+    a.e[1] = h->p.e[1];
+    a.e[2] = h->p.e[2];
+    a.key0 = (uint32_t)h->seed;
+    a.key1 = (uint32_t)(h->seed >> 32);
+    a.replica = h->replica;
+    a.partials = h->partials;
+    a.n_blocks = h->n_blocks;
+    a.n_present = (double)L.n_present;
+    a.acc = h->acc;
+    return a;
+}
+
+int setup_structured(hs_lattice *h) {
+    Layout &L = h->L;
+    const size_t es = hs::storage_size(h->precision);
+    L.Lx = h->dims[0];
+    L.Ly = h->dims[1];
+    L.Lz = h->dims[2];
+    L.Lh = L.Lx / 2;
+    L.vec = 1;
+    for (int v = 16 / (int)es; v >= 1; v /= 2)
+        if (L.Lh % v == 0) {
+            L.vec = v;
+            break;
+        }
+    const int64_t plane = (int64_t)L.Lz * L.Ly * L.Lh;
+    return h->alloc(&L.planes, (size_t)plane * 6 * es);
+}
+
+int setup_table(hs_lattice *h, Graph &g, const uint8_t *mask) {
+    Layout &L = h->L;
+    const int64_t n = g.n;
+    // colour classes must be independent sets among present sites
+    for (int64_t i = 0; i < n; ++i) {
+        if (mask && !mask[i]) continue;
+        for (int64_t k = g.row_ptr[i]; k < g.row_ptr[i + 1]; ++k) {
+            const int32_t j = g.col[k];
+            if (mask && !mask[j]) continue;
+            if (g.colour[i] == g.colour[j])
+                return fail(HS_E_COLOUR, "colouring is not proper (periodic sc needs even dimensions)");
+        }
+    }
+    if (g.n_colours > 64) return fail(HS_E_INVALID, "more than 64 colour classes");
+    // renumber: class by class, ascending natural index inside a class
+    std::vector<int64_t> count(g.n_colours + 1, 0);
+    int64_t n_present = 0;
+    for (int64_t i = 0; i < n; ++i)
+        if (!mask || mask[i]) {
+            ++count[g.colour[i] + 1];
+            ++n_present;
+        }
+    for (int c = 0; c < g.n_colours; ++c) count[c + 1] += count[c];
+    for (int c = 0; c <= g.n_colours; ++c) L.colour_begin[c] = count[c];
+    std::vector<int64_t> renum(n, -1);
+    std::vector<uint32_t> nat(n_present);
+    std::vector<int64_t> cursor(count.begin(), count.end() - 1);
+    int width = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        if (mask && !mask[i]) continue;
+        const int64_t r = cursor[g.colour[i]]++;
+        renum[i] = r;
+        nat[r] = (uint32_t)i;
+        int deg = 0;
+        for (int64_t k = g.row_ptr[i]; k < g.row_ptr[i + 1]; ++k)
+            if (!mask || mask[g.col[k]]) ++deg;
+        width = std::max(width, deg);
+    }
+    L.n_present = n_present;
+    L.width = width;
+    L.n_pad = n_present + 1;
+    const int32_t dummy = (int32_t)n_present;
+    std::vector<int32_t> table((size_t)width * L.n_pad, dummy);
+    for (int64_t r = 0; r < n_present; ++r) {
+        const int64_t i = nat[r];
+        int k2 = 0;
+        for (int64_t k = g.row_ptr[i]; k < g.row_ptr[i + 1]; ++k) {
+            const int32_t j = g.col[k];
+            if (mask && !mask[j]) continue;
+            table[(size_t)k2 * L.n_pad + r] = (int32_t)renum[j];
+            ++k2;
+        }
+    }
+    const size_t es = hs::storage_size(h->precision);
+    int st;
+    if ((st = h->alloc(&L.spins4, (size_t)L.n_pad * 4 * es))) return st;
+    if ((st = h->alloc(&L.nbr, std::max<size_t>(table.size(), 1) * sizeof(int32_t)))) return st;
+    if ((st = h->alloc(&L.nat, std::max<size_t>(nat.size(), 1) * sizeof(uint32_t)))) return st;
+    HS_CUDA(cudaMemsetAsync(L.spins4, 0, (size_t)L.n_pad * 4 * es, h->stream));
+    if (!table.empty())
+        HS_CUDA(cudaMemcpyAsync(L.nbr, table.data(), table.size() * sizeof(int32_t), cudaMemcpyHostToDevice, h->stream));
+    if (!nat.empty())
+        HS_CUDA(cudaMemcpyAsync(L.nat, nat.data(), nat.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, h->stream));
+    HS_CUDA(cudaStreamSynchronize(h->stream));  // host vectors die on return
+    return HS_OK;
+}
+
+int flush_timing(hs_lattice *h) {
+    if (h->ev_used == 0) return HS_OK;
+    HS_CUDA(cudaStreamSynchronize(h->stream));
+    for (size_t k = 0; k + 1 < h->ev_used; k += 2) {
+        float ms = 0.f;
+        HS_CUDA(cudaEventElapsedTime(&ms, h->ev[k], h->ev[k + 1]));
+        h->timed_ms += ms;
+        ++h->timed_launches;
+    }
+    h->ev_used = 0;
+    return HS_OK;
+}
+
+int record_event(hs_lattice *h) {
+    if (h->ev_used == h->ev.size()) {
+        if (h->ev.size() >= 8192) {
+            if (h->ev_used % 2 != 0) return fail(HS_E_INVALID, "timing events unbalanced");
+            int st = flush_timing(h);
+            if (st) return st;
+        } else {
+            cudaEvent_t e;
+            HS_CUDA(cudaEventCreate(&e));
+            h->ev.push_back(e);
+        }
+    }
+    HS_CUDA(cudaEventRecord(h->ev[h->ev_used++], h->stream));
+    return HS_OK;
+}
+
+int check_device_error(hs_lattice *h) {
+    int err = 0;
+    HS_CUDA(cudaMemcpyAsync(&err, &h->acc->error, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    HS_CUDA(cudaStreamSynchronize(h->stream));
+    if (err != 0) {
+        HS_CUDA(cudaMemsetAsync(&h->acc->error, 0, sizeof(int), h->stream));
+        return fail(HS_E_TIMEOUT, "a bounded device-side wait timed out");
+    }
+    return HS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *hs_last_error(void) { return g_error.c_str(); }
+
+int hs_api_version(void) { return HS_API_VERSION; }
+
+int hs_colour_greedy(int64_t n, const int64_t *row_ptr, const int32_t *col_idx, const uint8_t *site_mask,
+                     int32_t *colour_out, int *n_colours) {
+    if (!colour_out || !n_colours) return fail(HS_E_INVALID, "null output");
+    int st = check_csr(n, row_ptr, col_idx);
+    if (st) return st;
+    *n_colours = greedy(n, row_ptr, col_idx, site_mask, colour_out);
+    return HS_OK;
+}
+
+int hs_lattice_create(hs_lattice **out, int type, const int32_t dims[3], int periodic, const int64_t *row_ptr,
+                      const int32_t *col_idx, int64_t n_sites, const uint8_t *site_mask, const hs_params *p,
+                      int precision, uint64_t seed, uint32_t replica, void *cuda_stream) {
+    if (!out) return fail(HS_E_INVALID, "out is NULL");
+    *out = nullptr;
+    if (!p) return fail(HS_E_INVALID, "params are NULL");
+    if (precision < HS_FP64 || precision > HS_FP16) return fail(HS_E_INVALID, "unknown precision");
+    if (type < HS_SC || type > HS_CSR) return fail(HS_E_INVALID, "unknown lattice type");
+    const double en = std::sqrt(p->e[0] * p->e[0] + p->e[1] * p->e[1] + p->e[2] * p->e[2]);
+    if (!(en > 0.0) || !std::isfinite(en) || !std::isfinite(p->J) || !std::isfinite(p->K))
+        return fail(HS_E_INVALID, "J, K must be finite and e non-zero");
+    Graph g;
+    bool structured = false;
+    if (type == HS_CSR) {
+        if (row_ptr == nullptr) return fail(HS_E_INVALID, "HS_CSR needs row_ptr and col_idx");
+        int st = check_csr(n_sites, row_ptr, col_idx);
+        if (st) return st;
+    } else {
+        if (!dims || row_ptr || col_idx) return fail(HS_E_INVALID, "structured lattices take dims, not a CSR");
+        const int nb = type == HS_SC ? 1 : (type == HS_BCC ? 2 : 4);
+        for (int a = 0; a < 3; ++a)
+            if (dims[a] < 1) return fail(HS_E_INVALID, "dims must be >= 1");
+        const double total = (double)dims[0] * dims[1] * dims[2] * nb;
+        if (total >= 2147483647.0) return fail(HS_E_INVALID, "more than 2^31 - 1 sites");
+        if (type == HS_SC && periodic) {
+            for (int a = 0; a < 3; ++a)
+                if (dims[a] % 2 != 0)
+                    return fail(HS_E_COLOUR, "periodic sc with an odd dimension is not two-colourable");
+        }
+        structured = (type == HS_SC && periodic && site_mask == nullptr);
+    }
+    int dev = 0;
+    {
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    }
+    hs_lattice *h = new (std::nothrow) hs_lattice();
+    if (!h) return fail(HS_E_OOM, "host allocation failed");
+    h->type = type;
+    h->precision = precision;
+    h->periodic = periodic ? 1 : 0;
+    h->device = dev;
+    if (dims) std::memcpy(h->dims, dims, sizeof(h->dims));
+    h->p = *p;
+    for (int a = 0; a < 3; ++a) h->p.e[a] = p->e[a] / en;
+    h->seed = seed;
+    h->replica = replica;
+    h->stream = (cudaStream_t)cuda_stream;
+    {
+        cudaError_t e = cudaDeviceGetAttribute(&h->n_sm, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) {
+            delete h;
+            return cuda_fail(e, "cudaDeviceGetAttribute");
+        }
+    }
+    int st = HS_OK;
+    Layout &L = h->L;
+    L.structured = structured;
+    try {
+        if (structured) {
+            L.n_colours = 2;
+            L.n_sites = L.n_present = (int64_t)dims[0] * dims[1] * dims[2];
+            st = setup_structured(h);
+        } else {
+            if (type == HS_CSR) {
+                g.n = n_sites;
+                g.row_ptr.assign(row_ptr, row_ptr + n_sites + 1);
+                g.col.assign(col_idx, col_idx + row_ptr[n_sites]);
+                g.colour.assign(n_sites, -1);
+                g.n_colours = greedy(n_sites, row_ptr, col_idx, site_mask, g.colour.data());
+            } else {
+                build_structured(type, dims, periodic, g);
+            }
+            L.n_sites = g.n;
+            L.n_colours = std::max(g.n_colours, 1);
+            st = setup_table(h, g, site_mask);
+        }
+    } catch (const std::bad_alloc &) {
+        st = fail(HS_E_OOM, "host allocation failed");
+    }
+    if (st == HS_OK) {
+        h->n_blocks = hs::pass_blocks(precision, L, h->n_sm);
+        st = h->alloc(&h->partials, (size_t)L.n_colours * h->n_blocks * hs::kPartials * sizeof(double));
+    }
+    if (st == HS_OK) st = h->alloc(&h->acc, sizeof(DevAccum));
+    if (st == HS_OK) {
+        cudaError_t e = cudaMemsetAsync(h->acc, 0, sizeof(DevAccum), h->stream);
+        if (e != cudaSuccess) st = cuda_fail(e, "cudaMemsetAsync");
+    }
+    if (st == HS_OK) st = hs_init_spins(h, HS_INIT_ALIGNED);
+    if (st == HS_OK) {
+        cudaError_t e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) st = cuda_fail(e, "cudaStreamSynchronize");
+    }
+    if (st != HS_OK) {
+        delete h;
+        return st;
+    }
+    *out = h;
+    return HS_OK;
+}
+
+void hs_lattice_destroy(hs_lattice *h) { delete h; }
+
+int hs_init_spins(hs_lattice *h, int mode) {
+    if (!h) return fail(HS_E_INVALID, "null handle");
+    if (mode != HS_INIT_RANDOM && mode != HS_INIT_ALIGNED) return fail(HS_E_INVALID, "unknown init mode");
+    if (h->L.n_present == 0) return HS_OK;
+    HS_CUDA(hs::launch_init(h->precision, h->L, mode, h->p.e, (uint32_t)h->seed, (uint32_t)(h->seed >> 32),
+                            h->replica, h->stream));
+    return HS_OK;
+}
+
+int hs_sweep(hs_lattice *h, double beta, int64_t n_sweeps) {
+    if (!h) return fail(HS_E_INVALID, "null handle");
+    if (!(beta >= 0.0) || !std::isfinite(beta)) return fail(HS_E_INVALID, "beta must be finite and >= 0");
+    if (n_sweeps < 0) return fail(HS_E_INVALID, "n_sweeps must be >= 0");
+    h->last_n_sweeps = n_sweeps;
+    HS_CUDA(cudaMemsetAsync(&h->acc->accepted, 0, sizeof(double), h->stream));
+    if (n_sweeps == 0 || h->L.n_present == 0) {
+        h->sweep += (uint64_t)n_sweeps;
+        return HS_OK;
+    }
+    const Layout &L = h->L;
+    PassArgs a = base_args(h);
+    a.beta = beta;
+    a.accumulate = h->accumulate;
+    const size_t es = hs::storage_size(h->precision);
+    const int64_t plane = (int64_t)L.Lz * L.Ly * L.Lh;
+    for (int64_t s = 0; s < n_sweeps; ++s) {
+        a.sweep = (uint32_t)(h->sweep + (uint64_t)s);
+        for (int c = 0; c < L.n_colours; ++c) {
+            a.colour = c;
+            a.pass = c;
+            a.finish = (c == L.n_colours - 1);
+            if (L.structured) {
+                char *base = static_cast<char *>(L.planes);
+                for (int q = 0; q < 3; ++q) {
+                    a.own[q] = base + (size_t)(3 * c + q) * plane * es;
+                    a.oth[q] = base + (size_t)(3 * (1 - c) + q) * plane * es;
+                }
+            } else {
+                a.begin = L.colour_begin[c];
+                a.end = L.colour_begin[c + 1];
+                a.colour_begin = L.colour_begin[c];
+            }
+            if (h->timing) {
+                int st = record_event(h);
+                if (st) return st;
+            }
+            HS_CUDA(hs::launch_pass(h->precision, L, a, h->n_blocks, h->stream));
+            if (h->timing) {
+                int st = record_event(h);
+                if (st) return st;
+            }
+        }
+    }
+    h->sweep += (uint64_t)n_sweeps;
+    return HS_OK;
+}
+
+int hs_measure(hs_lattice *h, hs_measurement *out) {
+    if (!h || !out) return fail(HS_E_INVALID, "null argument");
+    std::memset(out, 0, sizeof(*out));
+    out->n_sites = h->L.n_present;
+    if (h->L.n_present == 0) return HS_OK;
+    PassArgs a = base_args(h);
+    a.n_colours = 1;
+    a.pass = 0;
+    a.finish = 1;
+    a.accumulate = 0;
+    HS_CUDA(hs::launch_measure(h->precision, h->L, a, h->n_blocks, h->stream));
+    double last[8], accepted = 0.0;
+    HS_CUDA(cudaMemcpyAsync(last, h->acc->last, sizeof(last), cudaMemcpyDeviceToHost, h->stream));
+    HS_CUDA(cudaMemcpyAsync(&accepted, &h->acc->accepted, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    int st = check_device_error(h);
+    if (st) return st;
+    out->E = last[0];
+    out->M[0] = last[1];
+    out->M[1] = last[2];
+    out->M[2] = last[3];
+    out->absM = last[4];
+    out->M2 = last[5];
+    out->M4 = last[6];
+    const double attempts = (double)h->last_n_sweeps * (double)h->L.n_present;
+    out->accept_rate = attempts > 0 ? accepted / attempts : 0.0;
+    return HS_OK;
+}
+
+int hs_accumulate(hs_lattice *h, int on) {
+    if (!h) return fail(HS_E_INVALID, "null handle");
+    h->accumulate = on ? 1 : 0;
+    return HS_OK;
+}
+
+int hs_reset_accumulator(hs_lattice *h) {
+    if (!h) return fail(HS_E_INVALID, "null handle");
+    HS_CUDA(cudaMemsetAsync(h->acc->moments, 0, sizeof(h->acc->moments) + sizeof(double), h->stream));
+    return HS_OK;
+}
+
+int hs_read_accumulator(hs_lattice *h, double moments[HS_N_MOMENTS], int64_t *count) {
+    if (!h || !moments || !count) return fail(HS_E_INVALID, "null argument");
+    double buf[HS_N_MOMENTS + 1];
+    HS_CUDA(cudaMemcpyAsync(buf, h->acc->moments, sizeof(buf), cudaMemcpyDeviceToHost, h->stream));
+    int st = check_device_error(h);
+    if (st) return st;
+    std::memcpy(moments, buf, sizeof(double) * HS_N_MOMENTS);
+    *count = (int64_t)buf[HS_N_MOMENTS];
+    return HS_OK;
+}
+
+static int ensure_stage(hs_lattice *h) {
+    if (h->stage) return HS_OK;
+    cudaError_t e = cudaMalloc(&h->stage, (size_t)std::max<int64_t>(h->L.n_sites, 1) * 3 * sizeof(double));
+    if (e != cudaSuccess) {
+        h->stage = nullptr;
+        return cuda_fail(e, "cudaMalloc(stage)");
+    }
+    return HS_OK;
+}
+
+int hs_get_spins_device(hs_lattice *h, double *d_xyz) {
+    if (!h || !d_xyz) return fail(HS_E_INVALID, "null argument");
+    if (!h->L.structured)
+        HS_CUDA(cudaMemsetAsync(d_xyz, 0, (size_t)h->L.n_sites * 3 * sizeof(double), h->stream));
+    if (h->L.n_present == 0) return HS_OK;
+    HS_CUDA(hs::launch_gather(h->precision, h->L, d_xyz, h->stream));
+    return HS_OK;
+}
+
+int hs_set_spins_device(hs_lattice *h, const double *d_xyz) {
+    if (!h || !d_xyz) return fail(HS_E_INVALID, "null argument");
+    if (h->L.n_present == 0) return HS_OK;
+    HS_CUDA(hs::launch_scatter(h->precision, h->L, d_xyz, h->stream));
+    return HS_OK;
+}
+
+int hs_get_spins(hs_lattice *h, double *xyz) {
+    if (!h || !xyz) return fail(HS_E_INVALID, "null argument");
+    int st = ensure_stage(h);
+    if (st) return st;
+    if ((st = hs_get_spins_device(h, h->stage))) return st;
+    HS_CUDA(cudaMemcpyAsync(xyz, h->stage, (size_t)h->L.n_sites * 3 * sizeof(double), cudaMemcpyDeviceToHost,
+                            h->stream));
+    HS_CUDA(cudaStreamSynchronize(h->stream));
+    return HS_OK;
+}
+
+int hs_set_spins(hs_lattice *h, const double *xyz) {
+    if (!h || !xyz) return fail(HS_E_INVALID, "null argument");
+    int st = ensure_stage(h);
+    if (st) return st;
+    HS_CUDA(cudaMemcpyAsync(h->stage, xyz, (size_t)h->L.n_sites * 3 * sizeof(double), cudaMemcpyHostToDevice,
+                            h->stream));
+    if ((st = hs_set_spins_device(h, h->stage))) return st;
+    HS_CUDA(cudaStreamSynchronize(h->stream));
+    return HS_OK;
+}
+
+int hs_set_sweep_counter(hs_lattice *h, uint64_t sweep) {
+    if (!h) return fail(HS_E_INVALID, "null handle");
+    h->sweep = sweep;
+    return HS_OK;
+}
+
+int hs_get_info(const hs_lattice *h, hs_info *out) {
+    if (!h || !out) return fail(HS_E_INVALID, "null argument");
+    out->type = h->type;
+    out->precision = h->precision;
+    out->n_colours = h->L.n_colours;
+    out->structured = h->L.structured ? 1 : 0;
+    out->n_sites = h->L.n_sites;
+    out->n_present = h->L.n_present;
+    out->device_bytes = h->device_bytes;
+    out->sweep = h->sweep;
+    return HS_OK;
+}
+
+int hs_enable_timing(hs_lattice *h, int on) {
+    if (!h) return fail(HS_E_INVALID, "null handle");
+    int st = flush_timing(h);
+    if (st) return st;
+    h->timing = on != 0;
+    h->timed_ms = 0.0;
+    h->timed_launches = 0;
+    return HS_OK;
+}
+
+int hs_read_timing(hs_lattice *h, double *ms, int64_t *launches) {
+    if (!h || !ms || !launches) return fail(HS_E_INVALID, "null argument");
+    int st = flush_timing(h);
+    if (st) return st;
+    *ms = h->timed_ms;
+    *launches = h->timed_launches;
+    return HS_OK;
+}
+
+// ---------------------------------------------------------------- batch
+struct hs_batch {
+    std::vector<hs_lattice *> members;
+};
+
+int hs_batch_create(hs_batch **out, hs_lattice *const *members, int n_members) {
+    if (!out) return fail(HS_E_INVALID, "out is NULL");
+    *out = nullptr;
+    if (!members || n_members < 1) return fail(HS_E_INVALID, "need at least one member");
+    for (int r = 0; r < n_members; ++r) {
+        if (!members[r]) return fail(HS_E_INVALID, "null member");
+        if (members[r]->stream != members[0]->stream) return fail(HS_E_INVALID, "members must share one stream");
+    }
+    hs_batch *b = new (std::nothrow) hs_batch();
+    if (!b) return fail(HS_E_OOM, "host allocation failed");
+    b->members.assign(members, members + n_members);
+    *out = b;
+    return HS_OK;
+}
+
+int hs_batch_run(hs_batch *b, const double *betas, int64_t n_sweeps, int64_t n_equil) {
+    if (!b || !betas) return fail(HS_E_INVALID, "null argument");
+    if (n_sweeps < 0 || n_equil < 0) return fail(HS_E_INVALID, "sweep counts must be >= 0");
+    for (size_t r = 0; r < b->members.size(); ++r) {
+        hs_lattice *h = b->members[r];
+        const int keep = h->accumulate;
+        h->accumulate = 0;
+        int st = hs_sweep(h, betas[r], n_equil);
+        h->accumulate = 1;
+        if (st == HS_OK) st = hs_sweep(h, betas[r], n_sweeps);
+        h->accumulate = keep;
+        if (st) return st;
+    }
+    return HS_OK;
+}
+
+void hs_batch_destroy(hs_batch *b) { delete b; }
+
+}  // extern "C"

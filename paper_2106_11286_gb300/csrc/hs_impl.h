@@ -1,0 +1,110 @@
+// Internal declarations of the GB300 Metropolis library (not part of the ABI).
+//
+// Device layouts (all in HBM, allocated by the lattice handle):
+//  * stencil path (unmasked periodic sc, Lx/2 divisible by the vector width):
+//    colour-major SoA.  Plane (colour c, component a) is an array
+//    [Lz][Ly][Lx/2] of the storage type; site (x,y,z) of colour
+//    c = (x+y+z)&1 sits at xh = x/2 in row (z,y).  Planes are ordered
+//    c0x c0y c0z c1x c1y c1z so that one colour is 3 contiguous planes.
+//  * table path (everything else): present sites renumbered colour by colour
+//    (ascending natural index inside a class); spins as 4-vectors (x,y,z,0)
+//    of the storage type, one per renumbered site plus one zero dummy at the
+//    end; neighbour table [width][n_pad] of renumbered indices, padded with
+//    the dummy; nat[i] = natural index of renumbered site i.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/hs.h"
+
+namespace hs {
+
+constexpr int kPartials = 5;  // E, Sx, Sy, Sz, accepted
+constexpr int kBlock = 256;   // threads per CTA of the sweep kernels
+
+// Division by a runtime constant d (1 <= d < 2^31) of numerators n < 2^31
+// by multiply-high and shift: with l = ceil(log2 d) and m = ceil(2^(31+l)/d)
+// (m < 2^32), floor(n m / 2^(31+l)) = floor(n / d) because the rounding
+// excess n (m - 2^(31+l)/d) / 2^(31+l) stays below 2^-l <= 1/d.
+struct FastDiv {
+    uint32_t d, m, l;
+    FastDiv() : d(1), m(0), l(0) {}
+    explicit FastDiv(uint32_t div) : d(div), l(0) {
+        while ((1ull << l) < div) ++l;
+        m = (l == 0) ? 0u : (uint32_t)(((1ull << (31 + l)) + div - 1) / div);
+    }
+#ifdef __CUDACC__
+    __device__ __forceinline__ uint32_t div(uint32_t n) const { return l == 0 ? n : (__umulhi(n, m) >> (l - 1)); }
+#endif
+};
+
+// Device-resident accumulator block of one lattice.
+struct DevAccum {
+    double moments[HS_N_MOMENTS];
+    double count;          // accumulated sweeps
+    double accepted;       // accepted moves since the last hs_sweep began
+    double last[8];        // E, Mx, My, Mz, |M|, M2, M4, |M.e| of the last finalised reduction
+    unsigned int done;     // CTA arrival counter of the finishing pass
+    int error;             // latched device error code (0 = none)
+};
+
+// Parameters of one colour pass.
+struct PassArgs {
+    // stencil layout
+    void *own[3];
+    const void *oth[3];
+    int Lx, Ly, Lz, Lh;
+    FastDiv div_nxv, div_ly;   // row = t / (Lh/V), z = row / Ly
+    // table layout
+    void *spins4;           // 4-vectors, renumbered order
+    const int32_t *nbr;     // [width][n_pad]
+    const uint32_t *nat;    // natural index per renumbered site
+    int width;
+    int64_t n_pad;
+    int64_t begin, end;     // renumbered range of this colour
+    int64_t colour_begin;   // first renumbered index of this colour (energy split)
+    // common
+    int colour;
+    int n_colours;
+    double J, K, e[3];
+    double beta;
+    uint32_t key0, key1, replica, sweep;
+    double *partials;       // [n_colours][n_blocks][kPartials]
+    int pass;               // colour index = partial slot
+    int n_blocks;
+    int finish;             // 1: last pass of the sweep, reduce and finalise
+    int accumulate;         // 1: add the moments to the accumulator
+    double n_present;
+    DevAccum *acc;
+};
+
+struct Layout {
+    bool structured;
+    int vec;                // vector width of the stencil kernel
+    int n_colours;
+    int64_t n_sites, n_present;
+    // stencil
+    int Lx, Ly, Lz, Lh;
+    void *planes;           // 6 planes of Lz*Ly*Lh elements
+    // table
+    void *spins4;
+    int32_t *nbr;
+    uint32_t *nat;
+    int width;
+    int64_t n_pad;
+    int64_t colour_begin[65];  // renumbered colour ranges (n_colours + 1 entries)
+};
+
+size_t storage_size(int precision);
+
+// Kernel launchers (kernels.cu).  All return cudaError_t of the launch.
+cudaError_t launch_pass(int precision, const Layout &L, const PassArgs &a, int n_blocks, cudaStream_t s);
+cudaError_t launch_init(int precision, const Layout &L, int mode, const double e[3], uint32_t key0,
+                        uint32_t key1, uint32_t replica, cudaStream_t s);
+cudaError_t launch_scatter(int precision, const Layout &L, const double *d_xyz, cudaStream_t s);
+cudaError_t launch_gather(int precision, const Layout &L, double *d_xyz, cudaStream_t s);
+cudaError_t launch_measure(int precision, const Layout &L, const PassArgs &a, int n_blocks, cudaStream_t s);
+int pass_blocks(int precision, const Layout &L, int n_sm);
+
+}  // namespace hs

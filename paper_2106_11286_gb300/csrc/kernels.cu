@@ -1,0 +1,735 @@
+// Colour-pass Metropolis kernels for sm_103a (arXiv 2106.11286: Eq. 1, the
+// Metropolis steps (i)-(iii), Eq. 2), plus initialisation, layout
+// conversion and measurement.
+//
+// Every kernel here is HBM- or ALU-bound elementwise work over one colour
+// class: no dense contraction exists, so no tensor-core path is used.  The
+// stencil pass reads its own colour and the other colour with 128-bit
+// coalesced loads (own values, plus the other colour's rows at y+-1, z+-1 and
+// the same row for the x neighbours, all at the same xh); the neighbour rows
+// are shared by adjacent rows of the grid through L1/L2.  Random numbers come
+// from an in-register Philox4x32-10 keyed by (seed, replica, sweep, colour,
+// site): nothing of the generator lives in memory.
+//
+// Reductions: per-thread partials -> warp shuffle -> CTA (FP64) -> one slot
+// per CTA and pass; the last CTA of the finishing pass sums the slots in a
+// fixed order (bit-reproducible) and updates the FP64 accumulator.
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+#include "hs_impl.h"
+
+namespace hs {
+namespace {
+
+// ----------------------------------------------------------------- Philox
+// Philox4x32-10 as published (Salmon et al., SC'11): ten rounds of two
+// 32x32->64 multiplies with fixed odd multipliers, a cross-lane swap of the
+// high halves xored with the round key, and a Weyl key schedule.
+constexpr uint32_t kMulA = 0xD2511F53u;
+constexpr uint32_t kMulB = 0xCD9E8D57u;
+constexpr uint32_t kWeylA = 0x9E3779B9u;
+constexpr uint32_t kWeylB = 0xBB67AE85u;
+
+__device__ __forceinline__ uint4 philox10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo_a = kMulA * c.x;
+        const uint32_t hi_a = __umulhi(kMulA, c.x);
+        const uint32_t lo_b = kMulB * c.z;
+        const uint32_t hi_b = __umulhi(kMulB, c.z);
+        c = make_uint4(hi_b ^ c.y ^ k0, lo_b, hi_a ^ c.w ^ k1, lo_a);
+        k0 += kWeylA;
+        k1 += kWeylB;
+    }
+    return c;
+}
+
+constexpr uint32_t kTagTrial = 0u;
+constexpr uint32_t kTagInit = 1u;
+
+// ----------------------------------------------------------------- precision
+template <int P> struct Tr;
+template <> struct Tr<HS_FP64> { using S = double; using C = double; };
+template <> struct Tr<HS_FP32> { using S = float; using C = float; };
+template <> struct Tr<HS_FP16> { using S = __half; using C = float; };
+
+__device__ __forceinline__ double to_c(double v) { return v; }
+__device__ __forceinline__ float to_c(float v) { return v; }
+__device__ __forceinline__ float to_c(__half v) { return __half2float(v); }
+
+template <typename S> __device__ __forceinline__ S store_from_double(double v);
+template <> __device__ __forceinline__ double store_from_double<double>(double v) { return v; }
+template <> __device__ __forceinline__ float store_from_double<float>(double v) { return __double2float_rn(v); }
+template <> __device__ __forceinline__ __half store_from_double<__half>(double v) { return __double2half(v); }
+
+template <typename T, int V>
+struct alignas(sizeof(T) * V) Vec {
+    T v[V];
+};
+
+// Uniform point on the sphere in FP64 from one Philox block (words 0,1 -> u_z,
+// words 2,3 -> u_phi, 53 bits each): z = 2u_z - 1 and v = 2u_phi - 1 are
+// formed exactly from the integers, r = sqrt((1-z)(1+z)) is correctly
+// rounded, phi = pi v.
+__device__ __forceinline__ void sphere_fp64(uint4 w, double &x, double &y, double &z) {
+    const int64_t two52 = int64_t(1) << 52;
+    const int64_t iz = (int64_t)((((uint64_t)(w.x >> 5)) << 26) | (uint64_t)(w.y >> 6));
+    const int64_t iv = (int64_t)((((uint64_t)(w.z >> 5)) << 26) | (uint64_t)(w.w >> 6));
+    z = (double)(iz - two52) * 0x1p-52;
+    const double v = (double)(iv - two52) * 0x1p-52;
+    const double r = sqrt((1.0 - z) * (1.0 + z));
+    double sn, cs;
+    sincospi(v, &sn, &cs);
+    x = r * cs;
+    y = r * sn;
+}
+
+// Trial orientation and acceptance uniform of one site (Metropolis step (ii)).
+template <int P>
+__device__ __forceinline__ void draw_trial(uint32_t site, uint32_t sweep, uint32_t colour, uint32_t replica,
+                                           uint32_t k0, uint32_t k1, typename Tr<P>::C &tx,
+                                           typename Tr<P>::C &ty, typename Tr<P>::C &tz,
+                                           typename Tr<P>::C &u);
+
+template <>
+__device__ __forceinline__ void draw_trial<HS_FP64>(uint32_t site, uint32_t sweep, uint32_t colour,
+                                                    uint32_t replica, uint32_t k0, uint32_t k1, double &tx,
+                                                    double &ty, double &tz, double &u) {
+    const uint32_t w2 = (kTagTrial << 24) | (colour << 8);
+    const uint4 a = philox10(make_uint4(site, sweep, w2, replica), k0, k1);
+    const uint4 b = philox10(make_uint4(site, sweep, w2 | 1u, replica), k0, k1);
+    sphere_fp64(a, tx, ty, tz);
+    const uint64_t ip = (((uint64_t)(b.x >> 5)) << 26) | (uint64_t)(b.y >> 6);
+    u = (double)ip * 0x1p-53;
+}
+
+__device__ __forceinline__ void sphere_fp32(uint4 w, float &tx, float &ty, float &tz, float &u) {
+    tz = (float)((int)(w.x >> 8) - (1 << 23)) * 0x1p-23f;
+    const float v = (float)((int)(w.y >> 8) - (1 << 23)) * 0x1p-23f;
+    u = (float)(w.z >> 8) * 0x1p-24f;
+    const float r = sqrtf((1.0f - tz) * (1.0f + tz));
+    float sn, cs;
+    sincospif(v, &sn, &cs);
+    tx = r * cs;
+    ty = r * sn;
+}
+
+template <>
+__device__ __forceinline__ void draw_trial<HS_FP32>(uint32_t site, uint32_t sweep, uint32_t colour,
+                                                    uint32_t replica, uint32_t k0, uint32_t k1, float &tx,
+                                                    float &ty, float &tz, float &u) {
+    const uint4 a = philox10(make_uint4(site, sweep, (kTagTrial << 24) | (colour << 8), replica), k0, k1);
+    sphere_fp32(a, tx, ty, tz, u);
+}
+
+// FP16 storage: the FP32 trial is renormalised and rounded to binary16; the
+// rounded vector is the one tested and stored, so the chain samples the
+// stored state.
+template <>
+__device__ __forceinline__ void draw_trial<HS_FP16>(uint32_t site, uint32_t sweep, uint32_t colour,
+                                                    uint32_t replica, uint32_t k0, uint32_t k1, float &tx,
+                                                    float &ty, float &tz, float &u) {
+    const uint4 a = philox10(make_uint4(site, sweep, (kTagTrial << 24) | (colour << 8), replica), k0, k1);
+    sphere_fp32(a, tx, ty, tz, u);
+    const float inv = rsqrtf(tx * tx + ty * ty + tz * tz);
+    tx = __half2float(__float2half_rn(tx * inv));
+    ty = __half2float(__float2half_rn(ty * inv));
+    tz = __half2float(__float2half_rn(tz * inv));
+}
+
+template <typename S, typename C> __device__ __forceinline__ S to_store(C v);
+template <> __device__ __forceinline__ double to_store<double, double>(double v) { return v; }
+template <> __device__ __forceinline__ float to_store<float, float>(float v) { return v; }
+template <> __device__ __forceinline__ __half to_store<__half, float>(float v) { return __float2half_rn(v); }
+
+__device__ __forceinline__ float exp_c(float x) { return __expf(x); }
+__device__ __forceinline__ double exp_c(double x) { return exp(x); }
+
+// Metropolis step (iii) for one site: dH of Eq. 1 restricted to the terms
+// that contain S_i, then dH <= 0 or P <= exp(-beta dH).
+template <typename C>
+__device__ __forceinline__ bool metropolis(C sx, C sy, C sz, C tx, C ty, C tz, C hx, C hy, C hz, C J, C K,
+                                           C ex, C ey, C ez, C beta, C u) {
+    const C dot_h = (tx - sx) * hx + (ty - sy) * hy + (tz - sz) * hz;
+    const C pe = tx * ex + ty * ey + tz * ez;
+    const C se = sx * ex + sy * ey + sz * ez;
+    const C dH = -J * dot_h - K * ((pe - se) * (pe + se));
+    return (dH <= C(0)) || (u <= exp_c(-beta * dH));
+}
+
+// ----------------------------------------------------------------- reduction
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Finalise a sweep (or a standalone measurement): the last CTA to arrive sums
+// every CTA's slots of every pass in a fixed order, so the FP64 totals do not
+// depend on scheduling.
+__device__ void finish_reduction(const PassArgs &a, bool measured) {
+    __shared__ int s_last;
+    __shared__ double s_fin[kBlock / 32][kPartials];
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned ticket = atomicAdd(&a.acc->done, 1u);
+        s_last = (ticket == (unsigned)a.n_blocks - 1u);
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    double t[kPartials] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int p = 0; p < a.n_colours; ++p)
+        for (int b = threadIdx.x; b < a.n_blocks; b += kBlock) {
+            const double *slot = a.partials + ((size_t)p * a.n_blocks + b) * kPartials;
+#pragma unroll
+            for (int q = 0; q < kPartials; ++q) t[q] += __ldcg(slot + q);
+        }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < kPartials; ++q) t[q] = warp_sum(t[q]);
+    if (lane == 0)
+#pragma unroll
+        for (int q = 0; q < kPartials; ++q) s_fin[warp][q] = t[q];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double tot[kPartials] = {0.0, 0.0, 0.0, 0.0, 0.0};
+        for (int w = 0; w < kBlock / 32; ++w)
+#pragma unroll
+            for (int q = 0; q < kPartials; ++q) tot[q] += s_fin[w][q];
+        DevAccum *A = a.acc;
+        A->accepted += tot[4];
+        if (measured) {
+            // Eq. 2 with |S| = 1: M = sum S / N
+            const double E = tot[0];
+            const double mx = tot[1] / a.n_present;
+            const double my = tot[2] / a.n_present;
+            const double mz = tot[3] / a.n_present;
+            const double m2 = mx * mx + my * my + mz * mz;
+            const double am = sqrt(m2);
+            const double me = fabs(mx * a.e[0] + my * a.e[1] + mz * a.e[2]);
+            A->last[0] = E;
+            A->last[1] = mx;
+            A->last[2] = my;
+            A->last[3] = mz;
+            A->last[4] = am;
+            A->last[5] = m2;
+            A->last[6] = m2 * m2;
+            A->last[7] = me;
+            if (a.accumulate) {
+                A->moments[HS_SUM_E] += E;
+                A->moments[HS_SUM_E2] += E * E;
+                A->moments[HS_SUM_ABSM] += am;
+                A->moments[HS_SUM_M2] += m2;
+                A->moments[HS_SUM_M4] += m2 * m2;
+                A->moments[HS_SUM_MX] += mx;
+                A->moments[HS_SUM_MY] += my;
+                A->moments[HS_SUM_MZ] += mz;
+                A->moments[HS_SUM_ABSME] += me;
+                A->count += 1.0;
+            }
+        }
+        A->done = 0u;
+    }
+}
+
+template <typename C, bool MEAS>
+__device__ __forceinline__ void write_partials(const PassArgs &a, C e, C x, C y, C z, unsigned nacc) {
+    __shared__ double s_w[kBlock / 32][kPartials];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (MEAS) {
+        e = warp_sum(e);
+        x = warp_sum(x);
+        y = warp_sum(y);
+        z = warp_sum(z);
+    }
+    nacc = __reduce_add_sync(0xffffffffu, nacc);
+    if (lane == 0) {
+        s_w[warp][0] = MEAS ? (double)e : 0.0;
+        s_w[warp][1] = MEAS ? (double)x : 0.0;
+        s_w[warp][2] = MEAS ? (double)y : 0.0;
+        s_w[warp][3] = MEAS ? (double)z : 0.0;
+        s_w[warp][4] = (double)nacc;
+    }
+    __syncthreads();
+    if (threadIdx.x < kPartials) {
+        double s = 0.0;
+#pragma unroll
+        for (int w = 0; w < kBlock / 32; ++w) s += s_w[w][threadIdx.x];
+        a.partials[((size_t)a.pass * a.n_blocks + blockIdx.x) * kPartials + threadIdx.x] = s;
+    }
+    if (a.finish) finish_reduction(a, MEAS);
+}
+
+// ----------------------------------------------------------------- stencil pass
+// One colour pass of the periodic sc lattice in colour-major SoA layout.
+// Work item = V consecutive sites of one row of the updated colour.  Row
+// parity p = (y+z+c)&1 fixes where the x neighbours sit in the other colour's
+// row: p = 0 -> (xh-1, xh), p = 1 -> (xh, xh+1); the +-y and +-z neighbours
+// sit at the same xh in the adjacent rows.  Neighbour order of the local
+// field sum: -x, +x, -y, +y, -z, +z.
+template <int P, int V, bool MEAS>
+__global__ void __launch_bounds__(kBlock) sc_pass_kernel(const PassArgs a) {
+    using S = typename Tr<P>::S;
+    using C = typename Tr<P>::C;
+    using VT = Vec<S, V>;
+    const uint32_t Lh = a.Lh, Ly = a.Ly, Lz = a.Lz, Lx = a.Lx;
+    const uint32_t nxv = Lh / V;
+    const uint32_t n_items = Lz * Ly * nxv;  // < 2^31: n_sites < 2^32
+    const int c = a.colour;
+    const C J = (C)a.J, K = (C)a.K, ex = (C)a.e[0], ey = (C)a.e[1], ez = (C)a.e[2], beta = (C)a.beta;
+    S *own[3] = {(S *)a.own[0], (S *)a.own[1], (S *)a.own[2]};
+    const S *oth[3] = {(const S *)a.oth[0], (const S *)a.oth[1], (const S *)a.oth[2]};
+    C accE = C(0), accX = C(0), accY = C(0), accZ = C(0);
+    unsigned nacc = 0;
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < n_items; t += stride) {
+        const uint32_t row = a.div_nxv.div(t);
+        const uint32_t xv = t - row * nxv;
+        const uint32_t z = a.div_ly.div(row);
+        const uint32_t y = row - z * Ly;
+        const uint32_t p = (y + z + (uint32_t)c) & 1u;
+        const uint32_t xh0 = xv * V;
+        const uint32_t ym = (y == 0) ? Ly - 1 : y - 1;
+        const uint32_t yp = (y == Ly - 1) ? 0 : y + 1;
+        const uint32_t zm = (z == 0) ? Lz - 1 : z - 1;
+        const uint32_t zp = (z == Lz - 1) ? 0 : z + 1;
+        const uint32_t b0 = row * Lh + xh0;
+        const uint32_t bym = (z * Ly + ym) * Lh + xh0;
+        const uint32_t byp = (z * Ly + yp) * Lh + xh0;
+        const uint32_t bzm = (zm * Ly + y) * Lh + xh0;
+        const uint32_t bzp = (zp * Ly + y) * Lh + xh0;
+        const uint32_t bed = row * Lh + (p ? ((xh0 + V == Lh) ? 0 : xh0 + V) : ((xh0 == 0) ? Lh - 1 : xh0 - 1));
+        VT s[3], o[3], nym[3], nyp[3], nzm[3], nzp[3];
+        C ed[3];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            s[q] = *reinterpret_cast<const VT *>(own[q] + b0);
+            o[q] = *reinterpret_cast<const VT *>(oth[q] + b0);
+            nym[q] = *reinterpret_cast<const VT *>(oth[q] + bym);
+            nyp[q] = *reinterpret_cast<const VT *>(oth[q] + byp);
+            nzm[q] = *reinterpret_cast<const VT *>(oth[q] + bzm);
+            nzp[q] = *reinterpret_cast<const VT *>(oth[q] + bzp);
+            ed[q] = to_c(oth[q][bed]);
+        }
+        const uint32_t site0 = row * Lx + 2 * xh0 + p;
+        bool any = false;
+#pragma unroll
+        for (int k = 0; k < V; ++k) {
+            C h[3];
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                const C xm = p ? to_c(o[q].v[k]) : (k == 0 ? ed[q] : to_c(o[q].v[k - 1]));
+                const C xp = p ? (k == V - 1 ? ed[q] : to_c(o[q].v[k + 1])) : to_c(o[q].v[k]);
+                h[q] = ((((xm + xp) + to_c(nym[q].v[k])) + to_c(nyp[q].v[k])) + to_c(nzm[q].v[k])) +
+                       to_c(nzp[q].v[k]);
+            }
+            C tx, ty, tz, u;
+            draw_trial<P>(site0 + 2u * k, a.sweep, (uint32_t)c, a.replica, a.key0, a.key1, tx, ty, tz, u);
+            C sx = to_c(s[0].v[k]), sy = to_c(s[1].v[k]), sz = to_c(s[2].v[k]);
+            const bool acc = metropolis<C>(sx, sy, sz, tx, ty, tz, h[0], h[1], h[2], J, K, ex, ey, ez, beta, u);
+            if (acc) {
+                sx = tx;
+                sy = ty;
+                sz = tz;
+                s[0].v[k] = to_store<S, C>(tx);
+                s[1].v[k] = to_store<S, C>(ty);
+                s[2].v[k] = to_store<S, C>(tz);
+                any = true;
+                ++nacc;
+            }
+            if (MEAS) {
+                // bond energy counted at the later colour's end: pass 1 owns
+                // every sc bond, pass 0 only the anisotropy term
+                const C se = sx * ex + sy * ey + sz * ez;
+                C ei = -K * se * se;
+                if (c == 1) ei -= J * (sx * h[0] + sy * h[1] + sz * h[2]);
+                accE += ei;
+                accX += sx;
+                accY += sy;
+                accZ += sz;
+            }
+        }
+        if (any) {
+#pragma unroll
+            for (int q = 0; q < 3; ++q) *reinterpret_cast<VT *>(own[q] + b0) = s[q];
+        }
+    }
+    write_partials<C, MEAS>(a, accE, accX, accY, accZ, nacc);
+}
+
+// ----------------------------------------------------------------- table pass
+// One colour pass over renumbered sites [begin, end) with a neighbour table.
+// Neighbours sum in stored order; padding points at a zero dummy spin.
+template <int P, bool MEAS>
+__global__ void __launch_bounds__(kBlock) table_pass_kernel(const PassArgs a) {
+    using S = typename Tr<P>::S;
+    using C = typename Tr<P>::C;
+    using S4 = Vec<S, 4>;
+    S4 *spins = reinterpret_cast<S4 *>(a.spins4);
+    const C J = (C)a.J, K = (C)a.K, ex = (C)a.e[0], ey = (C)a.e[1], ez = (C)a.e[2], beta = (C)a.beta;
+    C accE = C(0), accX = C(0), accY = C(0), accZ = C(0);
+    unsigned nacc = 0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = a.begin + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.end; i += stride) {
+        C hx = C(0), hy = C(0), hz = C(0);
+        C lx = C(0), ly = C(0), lz = C(0);
+        for (int k = 0; k < a.width; ++k) {
+            const int32_t j = __ldg(a.nbr + (int64_t)k * a.n_pad + i);
+            const S4 n = spins[j];
+            const C nx = to_c(n.v[0]), ny = to_c(n.v[1]), nz = to_c(n.v[2]);
+            hx += nx;
+            hy += ny;
+            hz += nz;
+            if (MEAS && j < a.colour_begin) {
+                lx += nx;
+                ly += ny;
+                lz += nz;
+            }
+        }
+        S4 s = spins[i];
+        C sx = to_c(s.v[0]), sy = to_c(s.v[1]), sz = to_c(s.v[2]);
+        C tx, ty, tz, u;
+        draw_trial<P>(__ldg(a.nat + i), a.sweep, (uint32_t)a.colour, a.replica, a.key0, a.key1, tx, ty, tz, u);
+        if (metropolis<C>(sx, sy, sz, tx, ty, tz, hx, hy, hz, J, K, ex, ey, ez, beta, u)) {
+            sx = tx;
+            sy = ty;
+            sz = tz;
+            s.v[0] = to_store<S, C>(tx);
+            s.v[1] = to_store<S, C>(ty);
+            s.v[2] = to_store<S, C>(tz);
+            spins[i] = s;
+            ++nacc;
+        }
+        if (MEAS) {
+            const C se = sx * ex + sy * ey + sz * ez;
+            accE += -J * (sx * lx + sy * ly + sz * lz) - K * se * se;
+            accX += sx;
+            accY += sy;
+            accZ += sz;
+        }
+    }
+    write_partials<C, MEAS>(a, accE, accX, accY, accZ, nacc);
+}
+
+// ----------------------------------------------------------------- measure
+// Standalone Eq. 1 / Eq. 2 of the current state in FP64: every site adds
+// -J/2 S_i.h_i - K (S_i.e)^2, so each bond is counted once overall.
+template <int P>
+__global__ void __launch_bounds__(kBlock) sc_measure_kernel(const PassArgs a, const void *planes) {
+    using S = typename Tr<P>::S;
+    const S *pl = (const S *)planes;
+    const int Lh = a.Lh, Ly = a.Ly, Lz = a.Lz;
+    const int64_t plane = (int64_t)Lz * Ly * Lh;
+    double accE = 0, accX = 0, accY = 0, accZ = 0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < 2 * plane; t += stride) {
+        const int c = (int)(t / plane);
+        const int64_t idx = t - c * plane;
+        const int xh = (int)(idx % Lh);
+        const int64_t row = idx / Lh;
+        const int y = (int)(row % Ly), z = (int)(row / Ly);
+        const int p = (y + z + c) & 1;
+        const S *me = pl + (int64_t)(3 * c) * plane;
+        const S *ot = pl + (int64_t)(3 * (1 - c)) * plane;
+        const int xm = p ? xh : (xh == 0 ? Lh - 1 : xh - 1);
+        const int xp = p ? (xh == Lh - 1 ? 0 : xh + 1) : xh;
+        const int ym = (y == 0) ? Ly - 1 : y - 1, yp = (y == Ly - 1) ? 0 : y + 1;
+        const int zm = (z == 0) ? Lz - 1 : z - 1, zp = (z == Lz - 1) ? 0 : z + 1;
+        const int64_t nb[6] = {row * Lh + xm,
+                               row * Lh + xp,
+                               ((int64_t)z * Ly + ym) * Lh + xh,
+                               ((int64_t)z * Ly + yp) * Lh + xh,
+                               ((int64_t)zm * Ly + y) * Lh + xh,
+                               ((int64_t)zp * Ly + y) * Lh + xh};
+        double s[3], h[3] = {0.0, 0.0, 0.0};
+        for (int q = 0; q < 3; ++q) {
+            s[q] = (double)to_c(me[q * plane + idx]);
+            for (int k = 0; k < 6; ++k) h[q] += (double)to_c(ot[q * plane + nb[k]]);
+        }
+        const double se = s[0] * a.e[0] + s[1] * a.e[1] + s[2] * a.e[2];
+        accE += -0.5 * a.J * (s[0] * h[0] + s[1] * h[1] + s[2] * h[2]) - a.K * se * se;
+        accX += s[0];
+        accY += s[1];
+        accZ += s[2];
+    }
+    write_partials<double, true>(a, accE, accX, accY, accZ, 0u);
+}
+
+template <int P>
+__global__ void __launch_bounds__(kBlock) table_measure_kernel(const PassArgs a, int64_t n_present) {
+    using S = typename Tr<P>::S;
+    using S4 = Vec<S, 4>;
+    const S4 *spins = reinterpret_cast<const S4 *>(a.spins4);
+    double accE = 0, accX = 0, accY = 0, accZ = 0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_present; i += stride) {
+        double h[3] = {0.0, 0.0, 0.0};
+        for (int k = 0; k < a.width; ++k) {
+            const S4 n = spins[a.nbr[(int64_t)k * a.n_pad + i]];
+            for (int q = 0; q < 3; ++q) h[q] += (double)to_c(n.v[q]);
+        }
+        const S4 sv = spins[i];
+        const double s0 = to_c(sv.v[0]), s1 = to_c(sv.v[1]), s2 = to_c(sv.v[2]);
+        const double se = s0 * a.e[0] + s1 * a.e[1] + s2 * a.e[2];
+        accE += -0.5 * a.J * (s0 * h[0] + s1 * h[1] + s2 * h[2]) - a.K * se * se;
+        accX += s0;
+        accY += s1;
+        accZ += s2;
+    }
+    write_partials<double, true>(a, accE, accX, accY, accZ, 0u);
+}
+
+// ----------------------------------------------------------------- init / layout
+template <int P>
+__global__ void sc_init_kernel(void *planes, int Lx, int Ly, int Lz, int Lh, int mode, double e0, double e1,
+                               double e2, uint32_t k0, uint32_t k1, uint32_t replica) {
+    using S = typename Tr<P>::S;
+    S *pl = (S *)planes;
+    const int64_t plane = (int64_t)Lz * Ly * Lh;
+    const int64_t n = (int64_t)Lx * Ly * Lz;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int x = (int)(i % Lx);
+        const int64_t row = i / Lx;
+        const int y = (int)(row % Ly), z = (int)(row / Ly);
+        const int c = (x + y + z) & 1;
+        const int64_t idx = row * Lh + (x >> 1);
+        double v[3] = {e0, e1, e2};
+        if (mode == HS_INIT_RANDOM) {
+            const uint4 w = philox10(make_uint4((uint32_t)i, 0u, kTagInit << 24, replica), k0, k1);
+            sphere_fp64(w, v[0], v[1], v[2]);
+        }
+        for (int q = 0; q < 3; ++q) pl[(int64_t)(3 * c + q) * plane + idx] = store_from_double<S>(v[q]);
+    }
+}
+
+template <int P>
+__global__ void table_init_kernel(void *spins4, const uint32_t *nat, int64_t n_present, int mode, double e0,
+                                  double e1, double e2, uint32_t k0, uint32_t k1, uint32_t replica) {
+    using S = typename Tr<P>::S;
+    using S4 = Vec<S, 4>;
+    S4 *sp = reinterpret_cast<S4 *>(spins4);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_present;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        double v[3] = {e0, e1, e2};
+        if (mode == HS_INIT_RANDOM) {
+            const uint4 w = philox10(make_uint4(nat[i], 0u, kTagInit << 24, replica), k0, k1);
+            sphere_fp64(w, v[0], v[1], v[2]);
+        }
+        S4 s;
+        s.v[0] = store_from_double<S>(v[0]);
+        s.v[1] = store_from_double<S>(v[1]);
+        s.v[2] = store_from_double<S>(v[2]);
+        s.v[3] = store_from_double<S>(0.0);
+        sp[i] = s;
+    }
+}
+
+template <int P>
+__global__ void sc_convert_kernel(void *planes, double *xyz, int Lx, int Ly, int Lz, int Lh, int to_layout) {
+    using S = typename Tr<P>::S;
+    S *pl = (S *)planes;
+    const int64_t plane = (int64_t)Lz * Ly * Lh;
+    const int64_t n = (int64_t)Lx * Ly * Lz;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int x = (int)(i % Lx);
+        const int64_t row = i / Lx;
+        const int y = (int)(row % Ly), z = (int)(row / Ly);
+        const int c = (x + y + z) & 1;
+        const int64_t idx = row * Lh + (x >> 1);
+        for (int q = 0; q < 3; ++q) {
+            S *d = pl + (int64_t)(3 * c + q) * plane + idx;
+            if (to_layout)
+                *d = store_from_double<S>(xyz[3 * i + q]);
+            else
+                xyz[3 * i + q] = (double)to_c(*d);
+        }
+    }
+}
+
+template <int P>
+__global__ void table_convert_kernel(void *spins4, const uint32_t *nat, int64_t n_present, double *xyz,
+                                     int to_layout) {
+    using S = typename Tr<P>::S;
+    using S4 = Vec<S, 4>;
+    S4 *sp = reinterpret_cast<S4 *>(spins4);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_present;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t site = nat[i];
+        if (to_layout) {
+            S4 s;
+            s.v[0] = store_from_double<S>(xyz[3 * site]);
+            s.v[1] = store_from_double<S>(xyz[3 * site + 1]);
+            s.v[2] = store_from_double<S>(xyz[3 * site + 2]);
+            s.v[3] = store_from_double<S>(0.0);
+            sp[i] = s;
+        } else {
+            const S4 s = sp[i];
+            xyz[3 * site] = (double)to_c(s.v[0]);
+            xyz[3 * site + 1] = (double)to_c(s.v[1]);
+            xyz[3 * site + 2] = (double)to_c(s.v[2]);
+        }
+    }
+}
+
+inline int grid_for(int64_t n, int cap = 152 * 16) {
+    int64_t g = (n + kBlock - 1) / kBlock;
+    if (g < 1) g = 1;
+    if (g > cap) g = cap;
+    return (int)g;
+}
+
+template <int P, int V>
+cudaError_t launch_sc_v(const PassArgs &a, int n_blocks, cudaStream_t s, bool meas) {
+    if (meas)
+        sc_pass_kernel<P, V, true><<<n_blocks, kBlock, 0, s>>>(a);
+    else
+        sc_pass_kernel<P, V, false><<<n_blocks, kBlock, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <int P>
+cudaError_t launch_pass_p(const Layout &L, const PassArgs &a, int n_blocks, cudaStream_t s) {
+    const bool meas = a.accumulate != 0;
+    if (L.structured) {
+        switch (L.vec) {
+        case 1: return launch_sc_v<P, 1>(a, n_blocks, s, meas);
+        case 2: return launch_sc_v<P, 2>(a, n_blocks, s, meas);
+        case 4: if constexpr (P != HS_FP64) return launch_sc_v<P, 4>(a, n_blocks, s, meas); break;
+        case 8: if constexpr (P == HS_FP16) return launch_sc_v<P, 8>(a, n_blocks, s, meas); break;
+        default: break;
+        }
+        return cudaErrorInvalidValue;
+    }
+    if (meas)
+        table_pass_kernel<P, true><<<n_blocks, kBlock, 0, s>>>(a);
+    else
+        table_pass_kernel<P, false><<<n_blocks, kBlock, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t storage_size(int precision) {
+    return precision == HS_FP64 ? 8 : (precision == HS_FP32 ? 4 : 2);
+}
+
+int pass_blocks(int precision, const Layout &L, int n_sm) {
+    int64_t items;
+    if (L.structured) {
+        items = (int64_t)L.Lz * L.Ly * (L.Lh / L.vec);
+    } else {
+        items = 0;
+        for (int c = 0; c < L.n_colours; ++c)
+            items = items > (L.colour_begin[c + 1] - L.colour_begin[c]) ? items
+                                                                        : (L.colour_begin[c + 1] - L.colour_begin[c]);
+    }
+    (void)precision;
+    return grid_for(items, n_sm * 8);
+}
+
+cudaError_t launch_pass(int precision, const Layout &L, const PassArgs &a, int n_blocks, cudaStream_t s) {
+    switch (precision) {
+    case HS_FP64: return launch_pass_p<HS_FP64>(L, a, n_blocks, s);
+    case HS_FP32: return launch_pass_p<HS_FP32>(L, a, n_blocks, s);
+    case HS_FP16: return launch_pass_p<HS_FP16>(L, a, n_blocks, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_measure(int precision, const Layout &L, const PassArgs &a, int n_blocks, cudaStream_t s) {
+    if (L.structured) {
+        switch (precision) {
+        case HS_FP64: sc_measure_kernel<HS_FP64><<<n_blocks, kBlock, 0, s>>>(a, L.planes); break;
+        case HS_FP32: sc_measure_kernel<HS_FP32><<<n_blocks, kBlock, 0, s>>>(a, L.planes); break;
+        case HS_FP16: sc_measure_kernel<HS_FP16><<<n_blocks, kBlock, 0, s>>>(a, L.planes); break;
+        default: return cudaErrorInvalidValue;
+        }
+    } else {
+        switch (precision) {
+        case HS_FP64: table_measure_kernel<HS_FP64><<<n_blocks, kBlock, 0, s>>>(a, L.n_present); break;
+        case HS_FP32: table_measure_kernel<HS_FP32><<<n_blocks, kBlock, 0, s>>>(a, L.n_present); break;
+        case HS_FP16: table_measure_kernel<HS_FP16><<<n_blocks, kBlock, 0, s>>>(a, L.n_present); break;
+        default: return cudaErrorInvalidValue;
+        }
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init(int precision, const Layout &L, int mode, const double e[3], uint32_t key0, uint32_t key1,
+                        uint32_t replica, cudaStream_t s) {
+    if (L.structured) {
+        const int g = grid_for(L.n_sites);
+        switch (precision) {
+        case HS_FP64:
+            sc_init_kernel<HS_FP64><<<g, kBlock, 0, s>>>(L.planes, L.Lx, L.Ly, L.Lz, L.Lh, mode, e[0], e[1], e[2],
+                                                          key0, key1, replica);
+            break;
+        case HS_FP32:
+            sc_init_kernel<HS_FP32><<<g, kBlock, 0, s>>>(L.planes, L.Lx, L.Ly, L.Lz, L.Lh, mode, e[0], e[1], e[2],
+                                                          key0, key1, replica);
+            break;
+        case HS_FP16:
+            sc_init_kernel<HS_FP16><<<g, kBlock, 0, s>>>(L.planes, L.Lx, L.Ly, L.Lz, L.Lh, mode, e[0], e[1], e[2],
+                                                          key0, key1, replica);
+            break;
+        default: return cudaErrorInvalidValue;
+        }
+    } else {
+        const int g = grid_for(L.n_present);
+        switch (precision) {
+        case HS_FP64:
+            table_init_kernel<HS_FP64><<<g, kBlock, 0, s>>>(L.spins4, L.nat, L.n_present, mode, e[0], e[1], e[2],
+                                                             key0, key1, replica);
+            break;
+        case HS_FP32:
+            table_init_kernel<HS_FP32><<<g, kBlock, 0, s>>>(L.spins4, L.nat, L.n_present, mode, e[0], e[1], e[2],
+                                                             key0, key1, replica);
+            break;
+        case HS_FP16:
+            table_init_kernel<HS_FP16><<<g, kBlock, 0, s>>>(L.spins4, L.nat, L.n_present, mode, e[0], e[1], e[2],
+                                                             key0, key1, replica);
+            break;
+        default: return cudaErrorInvalidValue;
+        }
+    }
+    return cudaGetLastError();
+}
+
+static cudaError_t launch_convert(int precision, const Layout &L, double *xyz, int to_layout, cudaStream_t s) {
+    if (L.structured) {
+        const int g = grid_for(L.n_sites);
+        switch (precision) {
+        case HS_FP64: sc_convert_kernel<HS_FP64><<<g, kBlock, 0, s>>>(L.planes, xyz, L.Lx, L.Ly, L.Lz, L.Lh, to_layout); break;
+        case HS_FP32: sc_convert_kernel<HS_FP32><<<g, kBlock, 0, s>>>(L.planes, xyz, L.Lx, L.Ly, L.Lz, L.Lh, to_layout); break;
+        case HS_FP16: sc_convert_kernel<HS_FP16><<<g, kBlock, 0, s>>>(L.planes, xyz, L.Lx, L.Ly, L.Lz, L.Lh, to_layout); break;
+        default: return cudaErrorInvalidValue;
+        }
+    } else {
+        const int g = grid_for(L.n_present);
+        switch (precision) {
+        case HS_FP64: table_convert_kernel<HS_FP64><<<g, kBlock, 0, s>>>(L.spins4, L.nat, L.n_present, xyz, to_layout); break;
+        case HS_FP32: table_convert_kernel<HS_FP32><<<g, kBlock, 0, s>>>(L.spins4, L.nat, L.n_present, xyz, to_layout); break;
+        case HS_FP16: table_convert_kernel<HS_FP16><<<g, kBlock, 0, s>>>(L.spins4, L.nat, L.n_present, xyz, to_layout); break;
+        default: return cudaErrorInvalidValue;
+        }
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scatter(int precision, const Layout &L, const double *d_xyz, cudaStream_t s) {
+    return launch_convert(precision, L, const_cast<double *>(d_xyz), 1, s);
+}
+
+cudaError_t launch_gather(int precision, const Layout &L, double *d_xyz, cudaStream_t s) {
+    return launch_convert(precision, L, d_xyz, 0, s);
+}
+
+}  // namespace hs

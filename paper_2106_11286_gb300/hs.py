@@ -1,0 +1,315 @@
+"""Thin ctypes binding of the C ABI in ``include/hs.h`` (same names, argument
+marshalling only).  Every step of the Metropolis sweep runs in the CUDA
+library ``libhs.so``; there is no Python or CPU fallback: if the library is
+missing or fails to load, every call raises.
+
+PyTorch is used only for plumbing: a ``torch.cuda.Stream`` (or its raw
+handle) may be passed as the stream, and ``get_spins_device`` /
+``set_spins_device`` accept CUDA tensors.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+HS_SC, HS_BCC, HS_FCC, HS_CSR = 0, 1, 2, 3
+HS_FP64, HS_FP32, HS_FP16 = 0, 1, 2
+HS_INIT_RANDOM, HS_INIT_ALIGNED = 0, 1
+HS_OK = 0
+HS_N_MOMENTS = 9
+STATUS = {0: "HS_OK", -1: "HS_E_INVALID", -2: "HS_E_CUDA", -3: "HS_E_OOM", -4: "HS_E_COLOUR",
+          -5: "HS_E_TIMEOUT", -6: "HS_E_DEVICE"}
+MOMENTS = ("sum_E", "sum_E2", "sum_absM", "sum_M2", "sum_M4", "sum_Mx", "sum_My", "sum_Mz", "sum_absMe")
+TYPES = {"sc": HS_SC, "bcc": HS_BCC, "fcc": HS_FCC, "csr": HS_CSR}
+PRECISIONS = {"fp64": HS_FP64, "fp32": HS_FP32, "fp16": HS_FP16}
+
+
+class HSError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class hs_params(ctypes.Structure):
+    _fields_ = [("J", ctypes.c_double), ("K", ctypes.c_double), ("e", ctypes.c_double * 3)]
+
+
+class hs_measurement(ctypes.Structure):
+    _fields_ = [("E", ctypes.c_double), ("M", ctypes.c_double * 3), ("absM", ctypes.c_double),
+                ("M2", ctypes.c_double), ("M4", ctypes.c_double), ("n_sites", ctypes.c_int64),
+                ("accept_rate", ctypes.c_double)]
+
+
+class hs_info(ctypes.Structure):
+    _fields_ = [("type", ctypes.c_int), ("precision", ctypes.c_int), ("n_colours", ctypes.c_int),
+                ("structured", ctypes.c_int), ("n_sites", ctypes.c_int64), ("n_present", ctypes.c_int64),
+                ("device_bytes", ctypes.c_int64), ("sweep", ctypes.c_uint64)]
+
+
+_vp = ctypes.c_void_p
+_i64p = ctypes.POINTER(ctypes.c_int64)
+_i32p = ctypes.POINTER(ctypes.c_int32)
+_u8p = ctypes.POINTER(ctypes.c_uint8)
+_dp = ctypes.POINTER(ctypes.c_double)
+
+# name -> (restype, argtypes); mirrors include/hs.h
+SIGNATURES = {
+    "hs_lattice_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, _i32p, ctypes.c_int, _i64p, _i32p,
+                                         ctypes.c_int64, _u8p, ctypes.POINTER(hs_params), ctypes.c_int,
+                                         ctypes.c_uint64, ctypes.c_uint32, _vp]),
+    "hs_lattice_destroy": (None, [_vp]),
+    "hs_init_spins": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "hs_sweep": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_int64]),
+    "hs_measure": (ctypes.c_int, [_vp, ctypes.POINTER(hs_measurement)]),
+    "hs_accumulate": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "hs_reset_accumulator": (ctypes.c_int, [_vp]),
+    "hs_read_accumulator": (ctypes.c_int, [_vp, _dp, _i64p]),
+    "hs_get_spins": (ctypes.c_int, [_vp, _vp]),
+    "hs_set_spins": (ctypes.c_int, [_vp, _vp]),
+    "hs_get_spins_device": (ctypes.c_int, [_vp, _vp]),
+    "hs_set_spins_device": (ctypes.c_int, [_vp, _vp]),
+    "hs_set_sweep_counter": (ctypes.c_int, [_vp, ctypes.c_uint64]),
+    "hs_get_info": (ctypes.c_int, [_vp, ctypes.POINTER(hs_info)]),
+    "hs_enable_timing": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "hs_read_timing": (ctypes.c_int, [_vp, _dp, _i64p]),
+    "hs_colour_greedy": (ctypes.c_int, [ctypes.c_int64, _i64p, _i32p, _u8p, _i32p, ctypes.POINTER(ctypes.c_int)]),
+    "hs_batch_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.c_int]),
+    "hs_batch_run": (ctypes.c_int, [_vp, _dp, ctypes.c_int64, ctypes.c_int64]),
+    "hs_batch_destroy": (None, [_vp]),
+    "hs_last_error": (ctypes.c_char_p, []),
+    "hs_api_version": (ctypes.c_int, []),
+}
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libhs.so (building it in-tree first if it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.build() if build_if_missing else _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library {path} is missing; run paper_2106_11286_gb300.build.build()")
+    L = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def _check(code: int):
+    if code != HS_OK:
+        raise HSError(code, load().hs_last_error().decode())
+
+
+def _stream_handle(stream) -> int | None:
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)  # torch.cuda.Stream
+
+
+def _ptr(a, ctype):
+    return None if a is None else a.ctypes.data_as(ctypes.POINTER(ctype))
+
+
+# ------------------------------------------------------------ functions (same names as the C ABI)
+def hs_lattice_create(type, dims=None, periodic=True, row_ptr=None, col_idx=None, n_sites=0, site_mask=None,
+                      J=1.0, K=0.0, e=(0.0, 0.0, 1.0), precision=HS_FP64, seed=0, replica=0, stream=None):
+    L = load()
+    t = TYPES[type] if isinstance(type, str) else int(type)
+    prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    d = None if dims is None else np.ascontiguousarray(dims, dtype=np.int32)
+    rp = None if row_ptr is None else np.ascontiguousarray(row_ptr, dtype=np.int64)
+    ci = None if col_idx is None else np.ascontiguousarray(col_idx, dtype=np.int32)
+    if rp is not None:
+        n_sites = len(rp) - 1
+        if ci is None or len(ci) == 0:
+            ci = np.zeros(1, dtype=np.int32)
+    m = None if site_mask is None else np.ascontiguousarray(site_mask, dtype=np.uint8)
+    p = hs_params(float(J), float(K), (ctypes.c_double * 3)(*[float(v) for v in e]))
+    h = _vp()
+    _check(L.hs_lattice_create(ctypes.byref(h), t, _ptr(d, ctypes.c_int32), int(bool(periodic)),
+                               _ptr(rp, ctypes.c_int64), _ptr(ci, ctypes.c_int32), int(n_sites),
+                               _ptr(m, ctypes.c_uint8), ctypes.byref(p), prec, int(seed), int(replica),
+                               _stream_handle(stream)))
+    return h
+
+
+def hs_lattice_destroy(h):
+    load().hs_lattice_destroy(h)
+
+
+def hs_init_spins(h, mode=HS_INIT_RANDOM):
+    _check(load().hs_init_spins(h, int(mode)))
+
+
+def hs_sweep(h, beta, n_sweeps=1):
+    _check(load().hs_sweep(h, float(beta), int(n_sweeps)))
+
+
+def hs_measure(h) -> dict:
+    m = hs_measurement()
+    _check(load().hs_measure(h, ctypes.byref(m)))
+    return {"E": m.E, "M": np.array(list(m.M)), "absM": m.absM, "M2": m.M2, "M4": m.M4,
+            "n_sites": m.n_sites, "accept_rate": m.accept_rate}
+
+
+def hs_accumulate(h, on=True):
+    _check(load().hs_accumulate(h, int(bool(on))))
+
+
+def hs_reset_accumulator(h):
+    _check(load().hs_reset_accumulator(h))
+
+
+def hs_read_accumulator(h):
+    buf = np.zeros(HS_N_MOMENTS, dtype=np.float64)
+    cnt = ctypes.c_int64(0)
+    _check(load().hs_read_accumulator(h, _ptr(buf, ctypes.c_double), ctypes.byref(cnt)))
+    return buf, cnt.value
+
+
+def hs_get_info(h) -> hs_info:
+    info = hs_info()
+    _check(load().hs_get_info(h, ctypes.byref(info)))
+    return info
+
+
+def hs_get_spins(h, out: np.ndarray | None = None) -> np.ndarray:
+    info = hs_get_info(h)
+    if out is None:
+        out = np.empty((info.n_sites, 3), dtype=np.float64)
+    assert out.dtype == np.float64 and out.flags.c_contiguous and out.size == 3 * info.n_sites
+    _check(load().hs_get_spins(h, out.ctypes.data))
+    return out
+
+
+def hs_set_spins(h, xyz: np.ndarray):
+    info = hs_get_info(h)
+    a = np.ascontiguousarray(xyz, dtype=np.float64)
+    assert a.size == 3 * info.n_sites
+    _check(load().hs_set_spins(h, a.ctypes.data))
+
+
+def hs_get_spins_device(h, out):
+    """out: contiguous float64 CUDA tensor with 3 * n_sites elements."""
+    _check(load().hs_get_spins_device(h, out.data_ptr()))
+    return out
+
+
+def hs_set_spins_device(h, xyz):
+    _check(load().hs_set_spins_device(h, xyz.data_ptr()))
+
+
+def hs_set_sweep_counter(h, sweep: int):
+    _check(load().hs_set_sweep_counter(h, int(sweep)))
+
+
+def hs_enable_timing(h, on=True):
+    _check(load().hs_enable_timing(h, int(bool(on))))
+
+
+def hs_read_timing(h):
+    ms = ctypes.c_double(0.0)
+    n = ctypes.c_int64(0)
+    _check(load().hs_read_timing(h, ctypes.byref(ms), ctypes.byref(n)))
+    return ms.value, n.value
+
+
+def hs_colour_greedy(row_ptr, col_idx, site_mask=None):
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    ci = np.ascontiguousarray(col_idx, dtype=np.int32)
+    if len(ci) == 0:
+        ci = np.zeros(1, dtype=np.int32)
+    m = None if site_mask is None else np.ascontiguousarray(site_mask, dtype=np.uint8)
+    n = len(rp) - 1
+    out = np.zeros(max(n, 1), dtype=np.int32)
+    nc = ctypes.c_int(0)
+    _check(load().hs_colour_greedy(n, _ptr(rp, ctypes.c_int64), _ptr(ci, ctypes.c_int32), _ptr(m, ctypes.c_uint8),
+                                   _ptr(out, ctypes.c_int32), ctypes.byref(nc)))
+    return out[:n], nc.value
+
+
+def hs_batch_create(members):
+    arr = (_vp * len(members))(*[m.value if isinstance(m, _vp) else m for m in members])
+    b = _vp()
+    _check(load().hs_batch_create(ctypes.byref(b), arr, len(members)))
+    return b
+
+
+def hs_batch_run(b, betas, n_sweeps, n_equil=0):
+    bt = np.ascontiguousarray(betas, dtype=np.float64)
+    _check(load().hs_batch_run(b, _ptr(bt, ctypes.c_double), int(n_sweeps), int(n_equil)))
+
+
+def hs_batch_destroy(b):
+    load().hs_batch_destroy(b)
+
+
+# ------------------------------------------------------------ convenience wrapper
+class Lattice:
+    """Owning wrapper: ``Lattice("sc", dims=(16,16,16), J=1, K=0.1, precision="fp64", seed=1)``."""
+
+    def __init__(self, type, **kw):
+        self.h = hs_lattice_create(type, **kw)
+
+    def close(self):
+        if self.h:
+            hs_lattice_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def init(self, mode=HS_INIT_RANDOM):
+        hs_init_spins(self.h, mode)
+
+    def sweep(self, beta, n=1):
+        hs_sweep(self.h, beta, n)
+
+    def measure(self):
+        return hs_measure(self.h)
+
+    def accumulate(self, on=True):
+        hs_accumulate(self.h, on)
+
+    def reset_accumulator(self):
+        hs_reset_accumulator(self.h)
+
+    def read_accumulator(self):
+        return hs_read_accumulator(self.h)
+
+    def get_spins(self):
+        return hs_get_spins(self.h)
+
+    def set_spins(self, xyz):
+        hs_set_spins(self.h, xyz)
+
+    def set_sweep_counter(self, s):
+        hs_set_sweep_counter(self.h, s)
+
+    @property
+    def info(self):
+        return hs_get_info(self.h)
