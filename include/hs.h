@@ -205,6 +205,23 @@ int hs_get_info(const hs_lattice *h, hs_info *out);
 int hs_enable_timing(hs_lattice *h, int on);
 int hs_read_timing(hs_lattice *h, double *ms, int64_t *launches);
 
+/* Launch configuration of the colour-pass kernels (the autotuner's knobs).
+ * vec_width: sites per thread of the sc stencil kernel, one 128-bit (or
+ * narrower) load per component: 1, 2, 4 or 8, dividing Lx/2, at most 16
+ * bytes of storage (0 = keep); the neighbour-table kernel uses 1.
+ * blocks_per_sm: resident CTAs per SM of the persistent-style grid (0 = as
+ * many as fit).  Results do not depend on either: a site's random numbers
+ * and arithmetic are fixed by its natural index. */
+int hs_set_launch(hs_lattice *h, int vec_width, int blocks_per_sm);
+int hs_get_launch(const hs_lattice *h, int *vec_width, int *blocks_per_sm);
+
+/* Autotuner: time every valid (vec_width, blocks_per_sm) for n_trial_sweeps
+ * sweeps at beta and keep the fastest.  The spins, the accumulator and the
+ * sweep counter are restored afterwards, so the chain is exactly as if the
+ * call had not happened.  Choices are cached per (precision, shape, SM
+ * count) for the life of the process.  Synchronous. */
+int hs_autotune(hs_lattice *h, double beta, int n_trial_sweeps);
+
 /* Host-only helper (no device needed): the greedy colouring the library
  * uses for HS_CSR lattices.  colour_out[n] gets the class of each present
  * site (-1 for masked sites); *n_colours the number of classes. */

@@ -19,6 +19,9 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <new>
 #include <string>
 #include <vector>
@@ -184,6 +187,8 @@ struct hs_lattice {
     int64_t last_n_sweeps = 0;
     Layout L{};
     int n_blocks = 1;
+    int blocks_per_sm = 0;  // 0 = as many as fit
+    int max_blocks = 1;     // capacity of the partials buffer
     double *partials = nullptr;
     DevAccum *acc = nullptr;
     double *stage = nullptr;  // 3 * n_sites doubles, lazily for host copies
@@ -238,6 +243,9 @@ PassArgs base_args(const hs_lattice *h) {
     a.e[0] = h->p.e[0];
     a.e[1] = h->p.e[1];
     a.e[2] = h->p.e[2];
+    a.fJ = (float)h->p.J;
+    a.fK = (float)h->p.K;
+    for (int q = 0; q < 3; ++q) a.fe[q] = (float)h->p.e[q];
     a.key0 = (uint32_t)h->seed;
     a.key1 = (uint32_t)(h->seed >> 32);
     a.replica = h->replica;
@@ -329,6 +337,16 @@ int setup_table(hs_lattice *h, Graph &g, const uint8_t *mask) {
     if (!nat.empty())
         HS_CUDA(cudaMemcpyAsync(L.nat, nat.data(), nat.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, h->stream));
     HS_CUDA(cudaStreamSynchronize(h->stream));  // host vectors die on return
+    return HS_OK;
+}
+
+// Grid of the colour passes: blocks_per_sm resident CTAs (0 = the occupancy
+// limit of the slower of the two pass variants) on every SM.
+int configure_launch(hs_lattice *h) {
+    int bps = h->blocks_per_sm;
+    const int occ = std::min(hs::pass_occupancy(h->precision, h->L, 0), hs::pass_occupancy(h->precision, h->L, 1));
+    if (bps <= 0 || bps > occ) bps = occ;
+    h->n_blocks = std::min(hs::pass_blocks(h->precision, h->L, h->n_sm, bps), h->max_blocks);
     return HS_OK;
 }
 
@@ -470,8 +488,9 @@ int hs_lattice_create(hs_lattice **out, int type, const int32_t dims[3], int per
         st = fail(HS_E_OOM, "host allocation failed");
     }
     if (st == HS_OK) {
-        h->n_blocks = hs::pass_blocks(precision, L, h->n_sm);
-        st = h->alloc(&h->partials, (size_t)L.n_colours * h->n_blocks * hs::kPartials * sizeof(double));
+        h->max_blocks = h->n_sm * (2048 / hs::kBlock);
+        st = h->alloc(&h->partials, (size_t)L.n_colours * h->max_blocks * hs::kPartials * sizeof(double));
+        if (st == HS_OK) st = configure_launch(h);
     }
     if (st == HS_OK) st = h->alloc(&h->acc, sizeof(DevAccum));
     if (st == HS_OK) {
@@ -515,6 +534,7 @@ int hs_sweep(hs_lattice *h, double beta, int64_t n_sweeps) {
     const Layout &L = h->L;
     PassArgs a = base_args(h);
     a.beta = beta;
+    a.fbeta = (float)beta;
     a.accumulate = h->accumulate;
     const size_t es = hs::storage_size(h->precision);
     const int64_t plane = (int64_t)L.Lz * L.Ly * L.Lh;
@@ -685,6 +705,123 @@ int hs_read_timing(hs_lattice *h, double *ms, int64_t *launches) {
     *ms = h->timed_ms;
     *launches = h->timed_launches;
     return HS_OK;
+}
+
+// ---------------------------------------------------------------- launch configuration
+static bool valid_vec(const hs_lattice *h, int v) {
+    if (!h->L.structured) return v == 1;
+    const int es = (int)hs::storage_size(h->precision);
+    const int vmax = 16 / es;
+    return (v == 1 || v == 2 || v == 4 || v == 8) && v <= vmax && h->L.Lh % v == 0;
+}
+
+int hs_set_launch(hs_lattice *h, int vec_width, int blocks_per_sm) {
+    if (!h) return fail(HS_E_INVALID, "null handle");
+    if (vec_width != 0) {
+        if (!valid_vec(h, vec_width)) return fail(HS_E_INVALID, "vector width must divide Lx/2, 16 bytes at most");
+        h->L.vec = vec_width;
+    }
+    if (blocks_per_sm < 0 || blocks_per_sm > 2048 / hs::kBlock) return fail(HS_E_INVALID, "blocks_per_sm out of range");
+    h->blocks_per_sm = blocks_per_sm;
+    return configure_launch(h);
+}
+
+int hs_get_launch(const hs_lattice *h, int *vec_width, int *blocks_per_sm) {
+    if (!h || !vec_width || !blocks_per_sm) return fail(HS_E_INVALID, "null argument");
+    *vec_width = h->L.structured ? h->L.vec : 1;
+    *blocks_per_sm = h->n_blocks / std::max(h->n_sm, 1);
+    return HS_OK;
+}
+
+namespace {
+struct TuneKey {
+    int precision, structured, accumulate;
+    int64_t a, b, c, d;
+    bool operator<(const TuneKey &o) const {
+        return std::tie(precision, structured, accumulate, a, b, c, d) <
+               std::tie(o.precision, o.structured, o.accumulate, o.a, o.b, o.c, o.d);
+    }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, std::pair<int, int>> g_tune_cache;
+}  // namespace
+
+int hs_autotune(hs_lattice *h, double beta, int n_trial_sweeps) {
+    if (!h) return fail(HS_E_INVALID, "null handle");
+    if (n_trial_sweeps < 1) return fail(HS_E_INVALID, "n_trial_sweeps must be >= 1");
+    if (h->L.n_present == 0) return HS_OK;
+    const Layout &L = h->L;
+    const TuneKey key{h->precision, L.structured ? 1 : 0, h->accumulate, L.structured ? L.Lx : L.n_present,
+                      L.structured ? L.Ly : L.width, L.structured ? L.Lz : L.n_colours, h->n_sm};
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) return hs_set_launch(h, it->second.first, it->second.second);
+    }
+    // save state: spins, accumulator, sweep counter
+    const size_t es = hs::storage_size(h->precision);
+    void *state = L.structured ? L.planes : L.spins4;
+    const size_t bytes = L.structured ? (size_t)L.Lz * L.Ly * L.Lh * 6 * es : (size_t)L.n_pad * 4 * es;
+    void *saved = nullptr;
+    HS_CUDA(cudaMalloc(&saved, bytes));
+    DevAccum acc_saved;
+    const uint64_t sweep_saved = h->sweep;
+    const int64_t last_saved = h->last_n_sweeps;
+    const bool timing_saved = h->timing;
+    h->timing = false;
+    int st = HS_OK;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    std::vector<int> vecs;
+    for (int v : {1, 2, 4, 8})
+        if (valid_vec(h, v)) vecs.push_back(v);
+    float best_ms = 1e30f;
+    int best_v = L.structured ? L.vec : 1, best_b = 0;
+    auto run = [&]() -> int {
+        HS_CUDA(cudaMemcpyAsync(saved, state, bytes, cudaMemcpyDeviceToDevice, h->stream));
+        HS_CUDA(cudaMemcpyAsync(&acc_saved, h->acc, sizeof(DevAccum), cudaMemcpyDeviceToHost, h->stream));
+        HS_CUDA(cudaStreamSynchronize(h->stream));
+        HS_CUDA(cudaEventCreate(&e0));
+        HS_CUDA(cudaEventCreate(&e1));
+        for (int v : vecs) {
+            int r = hs_set_launch(h, v, 0);
+            if (r) return r;
+            const int occ = std::min(hs::pass_occupancy(h->precision, h->L, 0),
+                                     hs::pass_occupancy(h->precision, h->L, 1));
+            for (int b = 1; b <= occ; ++b) {
+                if ((r = hs_set_launch(h, v, b))) return r;
+                if ((r = hs_sweep(h, beta, 1))) return r;  // warm-up
+                HS_CUDA(cudaEventRecord(e0, h->stream));
+                if ((r = hs_sweep(h, beta, n_trial_sweeps))) return r;
+                HS_CUDA(cudaEventRecord(e1, h->stream));
+                HS_CUDA(cudaEventSynchronize(e1));
+                float ms = 0.f;
+                HS_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+                if (ms < best_ms) {
+                    best_ms = ms;
+                    best_v = v;
+                    best_b = b;
+                }
+            }
+        }
+        return HS_OK;
+    };
+    st = run();
+    // restore the chain exactly
+    cudaMemcpyAsync(state, saved, bytes, cudaMemcpyDeviceToDevice, h->stream);
+    cudaMemcpyAsync(h->acc, &acc_saved, sizeof(DevAccum), cudaMemcpyHostToDevice, h->stream);
+    cudaStreamSynchronize(h->stream);
+    cudaFree(saved);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    h->sweep = sweep_saved;
+    h->last_n_sweeps = last_saved;
+    h->timing = timing_saved;
+    if (st) return st;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune_cache[key] = {best_v, best_b};
+    }
+    return hs_set_launch(h, best_v, best_b);
 }
 
 // ---------------------------------------------------------------- batch

@@ -69,6 +69,7 @@ struct PassArgs {
     int n_colours;
     double J, K, e[3];
     double beta;
+    float fJ, fK, fe[3], fbeta;  // the same in FP32 for the FP32 / FP16 kernels
     uint32_t key0, key1, replica, sweep;
     double *partials;       // [n_colours][n_blocks][kPartials]
     int pass;               // colour index = partial slot
@@ -105,6 +106,7 @@ cudaError_t launch_init(int precision, const Layout &L, int mode, const double e
 cudaError_t launch_scatter(int precision, const Layout &L, const double *d_xyz, cudaStream_t s);
 cudaError_t launch_gather(int precision, const Layout &L, double *d_xyz, cudaStream_t s);
 cudaError_t launch_measure(int precision, const Layout &L, const PassArgs &a, int n_blocks, cudaStream_t s);
-int pass_blocks(int precision, const Layout &L, int n_sm);
+int pass_blocks(int precision, const Layout &L, int n_sm, int blocks_per_sm);
+int pass_occupancy(int precision, const Layout &L, int accumulate);
 
 }  // namespace hs

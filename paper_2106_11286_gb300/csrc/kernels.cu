@@ -17,6 +17,8 @@
 #include <cuda_fp16.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 #include "hs_impl.h"
 
 namespace hs {
@@ -34,11 +36,9 @@ constexpr uint32_t kWeylB = 0xBB67AE85u;
 __device__ __forceinline__ uint4 philox10(uint4 c, uint32_t k0, uint32_t k1) {
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
-        const uint32_t lo_a = kMulA * c.x;
-        const uint32_t hi_a = __umulhi(kMulA, c.x);
-        const uint32_t lo_b = kMulB * c.z;
-        const uint32_t hi_b = __umulhi(kMulB, c.z);
-        c = make_uint4(hi_b ^ c.y ^ k0, lo_b, hi_a ^ c.w ^ k1, lo_a);
+        const uint64_t pa = (uint64_t)kMulA * c.x;  // one 32x32->64 multiply per lane pair
+        const uint64_t pb = (uint64_t)kMulB * c.z;
+        c = make_uint4((uint32_t)(pb >> 32) ^ c.y ^ k0, (uint32_t)pb, (uint32_t)(pa >> 32) ^ c.w ^ k1, (uint32_t)pa);
         k0 += kWeylA;
         k1 += kWeylB;
     }
@@ -104,13 +104,18 @@ __device__ __forceinline__ void draw_trial<HS_FP64>(uint32_t site, uint32_t swee
     u = (double)ip * 0x1p-53;
 }
 
+// FP32 trial: z and v = 2u - 1 exact from the 24-bit integers, r from the
+// hardware reciprocal square root (r = w / sqrt(w), w = (1-z)(1+z) >= 0), the
+// azimuth from the hardware sine / cosine on [-pi, pi) (absolute error about
+// 4e-7, far below what a 24-bit proposal resolves statistically).
 __device__ __forceinline__ void sphere_fp32(uint4 w, float &tx, float &ty, float &tz, float &u) {
     tz = (float)((int)(w.x >> 8) - (1 << 23)) * 0x1p-23f;
     const float v = (float)((int)(w.y >> 8) - (1 << 23)) * 0x1p-23f;
     u = (float)(w.z >> 8) * 0x1p-24f;
-    const float r = sqrtf((1.0f - tz) * (1.0f + tz));
+    const float w2 = (1.0f - tz) * (1.0f + tz);
+    const float r = (w2 > 0.0f) ? w2 * rsqrtf(w2) : 0.0f;
     float sn, cs;
-    sincospif(v, &sn, &cs);
+    __sincosf(3.14159265358979f * v, &sn, &cs);
     tx = r * cs;
     ty = r * sn;
 }
@@ -156,6 +161,25 @@ __device__ __forceinline__ bool metropolis(C sx, C sy, C sz, C tx, C ty, C tz, C
     const C se = sx * ex + sy * ey + sz * ez;
     const C dH = -J * dot_h - K * ((pe - se) * (pe + se));
     return (dH <= C(0)) || (u <= exp_c(-beta * dH));
+}
+
+__device__ __forceinline__ void load_params(const PassArgs &a, double &J, double &K, double &ex, double &ey,
+                                            double &ez, double &beta) {
+    J = a.J;
+    K = a.K;
+    ex = a.e[0];
+    ey = a.e[1];
+    ez = a.e[2];
+    beta = a.beta;
+}
+__device__ __forceinline__ void load_params(const PassArgs &a, float &J, float &K, float &ex, float &ey, float &ez,
+                                            float &beta) {
+    J = a.fJ;
+    K = a.fK;
+    ex = a.fe[0];
+    ey = a.fe[1];
+    ez = a.fe[2];
+    beta = a.fbeta;
 }
 
 // ----------------------------------------------------------------- reduction
@@ -284,7 +308,8 @@ __global__ void __launch_bounds__(kBlock) sc_pass_kernel(const PassArgs a) {
     const uint32_t nxv = Lh / V;
     const uint32_t n_items = Lz * Ly * nxv;  // < 2^31: n_sites < 2^32
     const int c = a.colour;
-    const C J = (C)a.J, K = (C)a.K, ex = (C)a.e[0], ey = (C)a.e[1], ez = (C)a.e[2], beta = (C)a.beta;
+    C J, K, ex, ey, ez, beta;
+    load_params(a, J, K, ex, ey, ez, beta);
     S *own[3] = {(S *)a.own[0], (S *)a.own[1], (S *)a.own[2]};
     const S *oth[3] = {(const S *)a.oth[0], (const S *)a.oth[1], (const S *)a.oth[2]};
     C accE = C(0), accX = C(0), accY = C(0), accZ = C(0);
@@ -374,7 +399,8 @@ __global__ void __launch_bounds__(kBlock) table_pass_kernel(const PassArgs a) {
     using C = typename Tr<P>::C;
     using S4 = Vec<S, 4>;
     S4 *spins = reinterpret_cast<S4 *>(a.spins4);
-    const C J = (C)a.J, K = (C)a.K, ex = (C)a.e[0], ey = (C)a.e[1], ez = (C)a.e[2], beta = (C)a.beta;
+    C J, K, ex, ey, ez, beta;
+    load_params(a, J, K, ex, ey, ez, beta);
     C accE = C(0), accX = C(0), accY = C(0), accZ = C(0);
     unsigned nacc = 0;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -621,18 +647,53 @@ size_t storage_size(int precision) {
     return precision == HS_FP64 ? 8 : (precision == HS_FP32 ? 4 : 2);
 }
 
-int pass_blocks(int precision, const Layout &L, int n_sm) {
-    int64_t items;
+static int64_t pass_items(const Layout &L) {
+    if (L.structured) return (int64_t)L.Lz * L.Ly * (L.Lh / L.vec);
+    int64_t items = 0;
+    for (int c = 0; c < L.n_colours; ++c)
+        items = std::max<int64_t>(items, L.colour_begin[c + 1] - L.colour_begin[c]);
+    return items;
+}
+
+template <int P>
+static const void *pass_kernel_ptr(const Layout &L, bool meas) {
     if (L.structured) {
-        items = (int64_t)L.Lz * L.Ly * (L.Lh / L.vec);
-    } else {
-        items = 0;
-        for (int c = 0; c < L.n_colours; ++c)
-            items = items > (L.colour_begin[c + 1] - L.colour_begin[c]) ? items
-                                                                        : (L.colour_begin[c + 1] - L.colour_begin[c]);
+        switch (L.vec) {
+        case 1: return meas ? (const void *)sc_pass_kernel<P, 1, true> : (const void *)sc_pass_kernel<P, 1, false>;
+        case 2: return meas ? (const void *)sc_pass_kernel<P, 2, true> : (const void *)sc_pass_kernel<P, 2, false>;
+        case 4:
+            if constexpr (P != HS_FP64)
+                return meas ? (const void *)sc_pass_kernel<P, 4, true> : (const void *)sc_pass_kernel<P, 4, false>;
+            break;
+        case 8:
+            if constexpr (P == HS_FP16)
+                return meas ? (const void *)sc_pass_kernel<P, 8, true> : (const void *)sc_pass_kernel<P, 8, false>;
+            break;
+        default: break;
+        }
+        return nullptr;
     }
+    return meas ? (const void *)table_pass_kernel<P, true> : (const void *)table_pass_kernel<P, false>;
+}
+
+int pass_occupancy(int precision, const Layout &L, int accumulate) {
+    const void *k = nullptr;
+    switch (precision) {
+    case HS_FP64: k = pass_kernel_ptr<HS_FP64>(L, accumulate != 0); break;
+    case HS_FP32: k = pass_kernel_ptr<HS_FP32>(L, accumulate != 0); break;
+    case HS_FP16: k = pass_kernel_ptr<HS_FP16>(L, accumulate != 0); break;
+    default: break;
+    }
+    int blocks = 0;
+    if (!k || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k, kBlock, 0) != cudaSuccess) return 1;
+    return blocks > 0 ? blocks : 1;
+}
+
+// Persistent-style grid: resident CTAs per SM x SMs, never more CTAs than
+// work items need.
+int pass_blocks(int precision, const Layout &L, int n_sm, int blocks_per_sm) {
     (void)precision;
-    return grid_for(items, n_sm * 8);
+    return grid_for(pass_items(L), n_sm * std::max(blocks_per_sm, 1));
 }
 
 cudaError_t launch_pass(int precision, const Layout &L, const PassArgs &a, int n_blocks, cudaStream_t s) {

@@ -76,6 +76,9 @@ SIGNATURES = {
     "hs_get_info": (ctypes.c_int, [_vp, ctypes.POINTER(hs_info)]),
     "hs_enable_timing": (ctypes.c_int, [_vp, ctypes.c_int]),
     "hs_read_timing": (ctypes.c_int, [_vp, _dp, _i64p]),
+    "hs_set_launch": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int]),
+    "hs_get_launch": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+    "hs_autotune": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_int]),
     "hs_colour_greedy": (ctypes.c_int, [ctypes.c_int64, _i64p, _i32p, _u8p, _i32p, ctypes.POINTER(ctypes.c_int)]),
     "hs_batch_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.c_int]),
     "hs_batch_run": (ctypes.c_int, [_vp, _dp, ctypes.c_int64, ctypes.c_int64]),
@@ -229,6 +232,21 @@ def hs_read_timing(h):
     return ms.value, n.value
 
 
+def hs_set_launch(h, vec_width=0, blocks_per_sm=0):
+    _check(load().hs_set_launch(h, int(vec_width), int(blocks_per_sm)))
+
+
+def hs_get_launch(h):
+    v = ctypes.c_int(0)
+    b = ctypes.c_int(0)
+    _check(load().hs_get_launch(h, ctypes.byref(v), ctypes.byref(b)))
+    return v.value, b.value
+
+
+def hs_autotune(h, beta, n_trial_sweeps=3):
+    _check(load().hs_autotune(h, float(beta), int(n_trial_sweeps)))
+
+
 def hs_colour_greedy(row_ptr, col_idx, site_mask=None):
     rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
     ci = np.ascontiguousarray(col_idx, dtype=np.int32)
@@ -309,6 +327,17 @@ class Lattice:
 
     def set_sweep_counter(self, s):
         hs_set_sweep_counter(self.h, s)
+
+    def autotune(self, beta, n_trial_sweeps=3):
+        hs_autotune(self.h, beta, n_trial_sweeps)
+        return hs_get_launch(self.h)
+
+    def set_launch(self, vec_width=0, blocks_per_sm=0):
+        hs_set_launch(self.h, vec_width, blocks_per_sm)
+
+    @property
+    def launch(self):
+        return hs_get_launch(self.h)
 
     @property
     def info(self):

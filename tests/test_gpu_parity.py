@@ -220,3 +220,34 @@ def test_beta_zero_accepts_everything_and_infinite_beta_nothing():
         lat.sweep(1e12, 3)
         m = lat.measure()
         assert m["accept_rate"] == 0.0 and m["E"] == E0
+
+
+@pytest.mark.parametrize("precision,dims", [("fp32", (16, 8, 8)), ("fp16", (32, 8, 4)), ("fp64", (8, 8, 8))])
+def test_launch_configuration_does_not_change_results(precision, dims):
+    """A site's random numbers and arithmetic depend only on its natural index,
+    so every vector width and grid size gives bit-identical chains; the
+    autotuner restores the state it perturbs."""
+    outs = []
+    widths = {"fp64": (1, 2), "fp32": (1, 2, 4), "fp16": (1, 2, 4, 8)}[precision]
+    for v in widths:
+        for bps in (1, 0):
+            with hs.Lattice("sc", dims=dims, K=0.1, precision=precision, seed=6) as lat:
+                lat.set_launch(v, bps)
+                assert lat.launch[0] == v
+                lat.init()
+                lat.accumulate(True)
+                lat.sweep(0.9, 6)
+                outs.append((lat.get_spins(), lat.read_accumulator()[0]))
+    for S, mom in outs[1:]:
+        assert np.array_equal(S, outs[0][0])
+        # spins are bit-identical; FP32 per-thread partial sums group differently
+        np.testing.assert_allclose(mom, outs[0][1], rtol=1e-12 if precision == "fp64" else 2e-6)
+    with hs.Lattice("sc", dims=dims, K=0.1, precision=precision, seed=6) as lat:
+        lat.init()
+        lat.accumulate(True)
+        lat.sweep(0.9, 2)
+        lat.autotune(0.9, 2)
+        assert lat.info.sweep == 2
+        lat.sweep(0.9, 4)
+        assert np.array_equal(lat.get_spins(), outs[0][0])
+        assert lat.read_accumulator()[1] == 6
