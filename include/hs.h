@@ -206,17 +206,34 @@ int hs_enable_timing(hs_lattice *h, int on);
 int hs_read_timing(hs_lattice *h, double *ms, int64_t *launches);
 
 /* Launch configuration of the colour-pass kernels (the autotuner's knobs).
- * vec_width: sites per thread of the sc stencil kernel, one 128-bit (or
- * narrower) load per component: 1, 2, 4 or 8, dividing Lx/2, at most 16
- * bytes of storage (0 = keep); the neighbour-table kernel uses 1.
- * blocks_per_sm: resident CTAs per SM of the persistent-style grid (0 = as
- * many as fit).  Results do not depend on either: a site's random numbers
- * and arithmetic are fixed by its natural index. */
-int hs_set_launch(hs_lattice *h, int vec_width, int blocks_per_sm);
-int hs_get_launch(const hs_lattice *h, int *vec_width, int *blocks_per_sm);
+ * Results never depend on it: a site's random numbers and arithmetic are
+ * fixed by its natural index, so every configuration gives bit-identical
+ * spins.  Zero fields mean "choose automatically". */
+enum hs_kernel {
+    HS_KERNEL_AUTO = 0,
+    HS_KERNEL_STENCIL = 1, /* sc: operands loaded through L1/L2 into registers */
+    HS_KERNEL_STAGED = 2,  /* sc: other-colour planes staged in shared memory by
+                              bulk async copies, CTAs march along z */
+    HS_KERNEL_TABLE = 3    /* neighbour-table kernel (bcc, fcc, CSR, masked) */
+};
+typedef struct {
+    int kernel;        /* hs_kernel; the table kernel is the only one for non-sc */
+    int vec_width;     /* sc kernels: sites per thread, 1/2/4/8, dividing Lx/2,
+                          at most 16 bytes of storage per load */
+    int blocks_per_sm; /* stencil / table: resident CTAs per SM (0 = max) */
+    int tile_y;        /* staged: rows per CTA slab (divides Ly) */
+    int chunk_z;       /* staged: planes per CTA work unit */
+} hs_launch;
 
-/* Autotuner: time every valid (vec_width, blocks_per_sm) for n_trial_sweeps
- * sweeps at beta and keep the fastest.  The spins, the accumulator and the
+/* Set (fields 0 = automatic) or read the launch configuration.  The staged
+ * kernel needs Lx/2 * storage bytes to be a multiple of 16 and its slabs to
+ * fit in shared memory; HS_E_INVALID otherwise. */
+int hs_set_launch(hs_lattice *h, const hs_launch *cfg);
+int hs_get_launch(const hs_lattice *h, hs_launch *out);
+
+/* Autotuner: time every valid launch configuration (kernel, vector width,
+ * CTAs per SM or slab rows and z chunk) for n_trial_sweeps sweeps at beta
+ * and keep the fastest.  The spins, the accumulator and the
  * sweep counter are restored afterwards, so the chain is exactly as if the
  * call had not happened.  Choices are cached per (precision, shape, SM
  * count) for the life of the process.  Synchronous. */

@@ -187,7 +187,7 @@ struct hs_lattice {
     int64_t last_n_sweeps = 0;
     Layout L{};
     int n_blocks = 1;
-    int blocks_per_sm = 0;  // 0 = as many as fit
+    hs_launch req{};        // requested launch configuration (0 = automatic)
     int max_blocks = 1;     // capacity of the partials buffer
     double *partials = nullptr;
     DevAccum *acc = nullptr;
@@ -231,6 +231,9 @@ PassArgs base_args(const hs_lattice *h) {
     if (L.structured) {
         a.div_nxv = hs::FastDiv((uint32_t)(L.Lh / L.vec));
         a.div_ly = hs::FastDiv((uint32_t)L.Ly);
+        a.ty = L.ty;
+        a.zchunk = L.zchunk;
+        a.n_units = L.n_units;
     }
     a.spins4 = L.spins4;
     a.nbr = L.nbr;
@@ -264,11 +267,6 @@ int setup_structured(hs_lattice *h) {
     L.Lz = h->dims[2];
     L.Lh = L.Lx / 2;
     L.vec = 1;
-    for (int v = 16 / (int)es; v >= 1; v /= 2)
-        if (L.Lh % v == 0) {
-            L.vec = v;
-            break;
-        }
     const int64_t plane = (int64_t)L.Lz * L.Ly * L.Lh;
     return h->alloc(&L.planes, (size_t)plane * 6 * es);
 }
@@ -340,13 +338,80 @@ int setup_table(hs_lattice *h, Graph &g, const uint8_t *mask) {
     return HS_OK;
 }
 
-// Grid of the colour passes: blocks_per_sm resident CTAs (0 = the occupancy
-// limit of the slower of the two pass variants) on every SM.
+bool vec_ok(const hs_lattice *h, int v) {
+    const int es = (int)hs::storage_size(h->precision);
+    return (v == 1 || v == 2 || v == 4 || v == 8) && v * es <= 16 && h->L.Lh % v == 0;
+}
+
+int default_vec(const hs_lattice *h) {
+    const int es = (int)hs::storage_size(h->precision);
+    for (int v = 16 / es; v > 1; v /= 2)
+        if (h->L.Lh % v == 0) return v;
+    return 1;
+}
+
+bool staged_ok(const hs_lattice *h) {
+    const Layout &L = h->L;
+    return L.structured && ((size_t)L.Lh * hs::storage_size(h->precision)) % 16 == 0;
+}
+
+// Resolve the requested configuration into kernel, vector width and grid.
+// Stencil / table: blocks_per_sm resident CTAs (0 = occupancy limit of the
+// slower pass variant) on every SM.  Staged: slabs of tile_y rows (default:
+// the largest of 8, 4, 2, 1 dividing Ly whose slabs fit two CTAs per SM),
+// z chunks sized so that all units fit in one wave.
 int configure_launch(hs_lattice *h) {
-    int bps = h->blocks_per_sm;
-    const int occ = std::min(hs::pass_occupancy(h->precision, h->L, 0), hs::pass_occupancy(h->precision, h->L, 1));
+    Layout &L = h->L;
+    const hs_launch &r = h->req;
+    if (!L.structured) {
+        L.kernel = hs::kTable;
+        int bps = r.blocks_per_sm;
+        const int occ = std::min(hs::pass_occupancy(h->precision, L, 0), hs::pass_occupancy(h->precision, L, 1));
+        if (bps <= 0 || bps > occ) bps = occ;
+        h->n_blocks = std::min(hs::pass_blocks(h->precision, L, h->n_sm, bps), h->max_blocks);
+        return HS_OK;
+    }
+    L.vec = r.vec_width ? r.vec_width : default_vec(h);
+    int kind = r.kernel;
+    // automatic choice: the register stencil (measured faster than the staged
+    // kernel on GB300 at 256^3 and 464^3; hs_autotune compares both)
+    if (kind == HS_KERNEL_AUTO) kind = HS_KERNEL_STENCIL;
+    if (kind == HS_KERNEL_STAGED) {
+        if (!staged_ok(h)) return fail(HS_E_INVALID, "staged kernel needs Lx/2 * storage bytes divisible by 16");
+        int ty = r.tile_y;
+        if (ty == 0) {
+            for (int c : {8, 4, 2, 1})
+                if (L.Ly % c == 0 && hs::staged_smem_bytes(h->precision, c, L.Lh) <= 110 * 1024) {
+                    ty = c;
+                    break;
+                }
+            if (ty == 0) ty = 1;
+        }
+        if (ty < 1 || L.Ly % ty != 0) return fail(HS_E_INVALID, "tile_y must divide Ly");
+        const size_t smem = hs::staged_smem_bytes(h->precision, ty, L.Lh);
+        const int occ = hs::staged_occupancy(h->precision, L.vec, smem);
+        if (occ < 1) return fail(HS_E_INVALID, "staged slabs do not fit in shared memory");
+        const int slots = h->n_sm * occ;
+        const int n_yslab = L.Ly / ty;
+        int zc = r.chunk_z;
+        if (zc <= 0) {
+            const int n_chunks = std::max(1, slots / n_yslab);
+            zc = (L.Lz + n_chunks - 1) / n_chunks;
+        }
+        zc = std::min(std::max(zc, 1), L.Lz);
+        L.kernel = hs::kStaged;
+        L.ty = ty;
+        L.zchunk = zc;
+        L.n_units = n_yslab * ((L.Lz + zc - 1) / zc);
+        L.grid = std::min(L.n_units, slots);
+        h->n_blocks = L.grid;
+        return HS_OK;
+    }
+    L.kernel = hs::kStencil;  // before the occupancy query, which looks at the kind
+    int bps = r.blocks_per_sm;
+    const int occ = std::min(hs::pass_occupancy(h->precision, L, 0), hs::pass_occupancy(h->precision, L, 1));
     if (bps <= 0 || bps > occ) bps = occ;
-    h->n_blocks = std::min(hs::pass_blocks(h->precision, h->L, h->n_sm, bps), h->max_blocks);
+    h->n_blocks = std::min(hs::pass_blocks(h->precision, L, h->n_sm, bps), h->max_blocks);
     return HS_OK;
 }
 
@@ -708,28 +773,41 @@ int hs_read_timing(hs_lattice *h, double *ms, int64_t *launches) {
 }
 
 // ---------------------------------------------------------------- launch configuration
-static bool valid_vec(const hs_lattice *h, int v) {
-    if (!h->L.structured) return v == 1;
-    const int es = (int)hs::storage_size(h->precision);
-    const int vmax = 16 / es;
-    return (v == 1 || v == 2 || v == 4 || v == 8) && v <= vmax && h->L.Lh % v == 0;
-}
-
-int hs_set_launch(hs_lattice *h, int vec_width, int blocks_per_sm) {
-    if (!h) return fail(HS_E_INVALID, "null handle");
-    if (vec_width != 0) {
-        if (!valid_vec(h, vec_width)) return fail(HS_E_INVALID, "vector width must divide Lx/2, 16 bytes at most");
-        h->L.vec = vec_width;
+int hs_set_launch(hs_lattice *h, const hs_launch *cfg) {
+    if (!h || !cfg) return fail(HS_E_INVALID, "null argument");
+    if (cfg->kernel < HS_KERNEL_AUTO || cfg->kernel > HS_KERNEL_TABLE)
+        return fail(HS_E_INVALID, "unknown kernel kind");
+    if (h->L.structured) {
+        if (cfg->kernel == HS_KERNEL_TABLE) return fail(HS_E_INVALID, "sc stencil lattices have no table kernel");
+        if (cfg->vec_width != 0 && !vec_ok(h, cfg->vec_width))
+            return fail(HS_E_INVALID, "vector width must divide Lx/2, 16 bytes at most");
+    } else if (cfg->kernel == HS_KERNEL_STENCIL || cfg->kernel == HS_KERNEL_STAGED) {
+        return fail(HS_E_INVALID, "stencil kernels need an unmasked periodic sc lattice");
     }
-    if (blocks_per_sm < 0 || blocks_per_sm > 2048 / hs::kBlock) return fail(HS_E_INVALID, "blocks_per_sm out of range");
-    h->blocks_per_sm = blocks_per_sm;
-    return configure_launch(h);
+    if (cfg->blocks_per_sm < 0 || cfg->blocks_per_sm > 2048 / hs::kBlock)
+        return fail(HS_E_INVALID, "blocks_per_sm out of range");
+    if (cfg->tile_y < 0 || cfg->chunk_z < 0) return fail(HS_E_INVALID, "negative tile");
+    const hs_launch keep = h->req;
+    const Layout keep_l = h->L;
+    const int keep_b = h->n_blocks;
+    h->req = *cfg;
+    int st = configure_launch(h);
+    if (st) {
+        h->req = keep;
+        h->L = keep_l;
+        h->n_blocks = keep_b;
+    }
+    return st;
 }
 
-int hs_get_launch(const hs_lattice *h, int *vec_width, int *blocks_per_sm) {
-    if (!h || !vec_width || !blocks_per_sm) return fail(HS_E_INVALID, "null argument");
-    *vec_width = h->L.structured ? h->L.vec : 1;
-    *blocks_per_sm = h->n_blocks / std::max(h->n_sm, 1);
+int hs_get_launch(const hs_lattice *h, hs_launch *out) {
+    if (!h || !out) return fail(HS_E_INVALID, "null argument");
+    const Layout &L = h->L;
+    out->kernel = L.kernel;
+    out->vec_width = L.structured ? L.vec : 1;
+    out->blocks_per_sm = (h->n_blocks + h->n_sm - 1) / std::max(h->n_sm, 1);
+    out->tile_y = L.kernel == hs::kStaged ? L.ty : 0;
+    out->chunk_z = L.kernel == hs::kStaged ? L.zchunk : 0;
     return HS_OK;
 }
 
@@ -743,7 +821,38 @@ struct TuneKey {
     }
 };
 std::mutex g_tune_mu;
-std::map<TuneKey, std::pair<int, int>> g_tune_cache;
+std::map<TuneKey, hs_launch> g_tune_cache;
+
+// Candidate configurations of one lattice.
+std::vector<hs_launch> tune_candidates(hs_lattice *h) {
+    std::vector<hs_launch> out;
+    const Layout &L = h->L;
+    if (!L.structured) {
+        for (int b = 1; b <= 8; ++b) out.push_back({HS_KERNEL_TABLE, 1, b, 0, 0});
+        return out;
+    }
+    for (int v : {1, 2, 4, 8}) {
+        if (!vec_ok(h, v)) continue;
+        for (int b = 1; b <= 8; ++b) out.push_back({HS_KERNEL_STENCIL, v, b, 0, 0});
+        if (!staged_ok(h)) continue;
+        for (int ty : {1, 2, 4, 8, 16}) {
+            if (L.Ly % ty != 0) continue;
+            const size_t smem = hs::staged_smem_bytes(h->precision, ty, L.Lh);
+            const int occ = hs::staged_occupancy(h->precision, v, smem);
+            if (occ < 1) continue;
+            const int slots = h->n_sm * occ;
+            const int n_yslab = L.Ly / ty;
+            const int n_chunks = std::max(1, slots / n_yslab);
+            const int zc = (L.Lz + n_chunks - 1) / n_chunks;
+            for (int f : {1, 2, 4}) {
+                const int z = std::max(1, zc / f);
+                if (f > 1 && z == zc) continue;
+                out.push_back({HS_KERNEL_STAGED, v, 0, ty, z});
+            }
+        }
+    }
+    return out;
+}
 }  // namespace
 
 int hs_autotune(hs_lattice *h, double beta, int n_trial_sweeps) {
@@ -756,7 +865,7 @@ int hs_autotune(hs_lattice *h, double beta, int n_trial_sweeps) {
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_tune_cache.find(key);
-        if (it != g_tune_cache.end()) return hs_set_launch(h, it->second.first, it->second.second);
+        if (it != g_tune_cache.end()) return hs_set_launch(h, &it->second);
     }
     // save state: spins, accumulator, sweep counter
     const size_t es = hs::storage_size(h->precision);
@@ -768,44 +877,35 @@ int hs_autotune(hs_lattice *h, double beta, int n_trial_sweeps) {
     const uint64_t sweep_saved = h->sweep;
     const int64_t last_saved = h->last_n_sweeps;
     const bool timing_saved = h->timing;
+    const hs_launch req_saved = h->req;
     h->timing = false;
-    int st = HS_OK;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
-    std::vector<int> vecs;
-    for (int v : {1, 2, 4, 8})
-        if (valid_vec(h, v)) vecs.push_back(v);
     float best_ms = 1e30f;
-    int best_v = L.structured ? L.vec : 1, best_b = 0;
+    hs_launch best = h->req;
     auto run = [&]() -> int {
         HS_CUDA(cudaMemcpyAsync(saved, state, bytes, cudaMemcpyDeviceToDevice, h->stream));
         HS_CUDA(cudaMemcpyAsync(&acc_saved, h->acc, sizeof(DevAccum), cudaMemcpyDeviceToHost, h->stream));
         HS_CUDA(cudaStreamSynchronize(h->stream));
         HS_CUDA(cudaEventCreate(&e0));
         HS_CUDA(cudaEventCreate(&e1));
-        for (int v : vecs) {
-            int r = hs_set_launch(h, v, 0);
-            if (r) return r;
-            const int occ = std::min(hs::pass_occupancy(h->precision, h->L, 0),
-                                     hs::pass_occupancy(h->precision, h->L, 1));
-            for (int b = 1; b <= occ; ++b) {
-                if ((r = hs_set_launch(h, v, b))) return r;
-                if ((r = hs_sweep(h, beta, 1))) return r;  // warm-up
-                HS_CUDA(cudaEventRecord(e0, h->stream));
-                if ((r = hs_sweep(h, beta, n_trial_sweeps))) return r;
-                HS_CUDA(cudaEventRecord(e1, h->stream));
-                HS_CUDA(cudaEventSynchronize(e1));
-                float ms = 0.f;
-                HS_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-                if (ms < best_ms) {
-                    best_ms = ms;
-                    best_v = v;
-                    best_b = b;
-                }
+        for (const hs_launch &cand : tune_candidates(h)) {
+            if (hs_set_launch(h, &cand) != HS_OK) continue;  // e.g. more CTAs per SM than fit
+            int r;
+            if ((r = hs_sweep(h, beta, 1))) return r;  // warm-up
+            HS_CUDA(cudaEventRecord(e0, h->stream));
+            if ((r = hs_sweep(h, beta, n_trial_sweeps))) return r;
+            HS_CUDA(cudaEventRecord(e1, h->stream));
+            HS_CUDA(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            HS_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = cand;
             }
         }
         return HS_OK;
     };
-    st = run();
+    int st = run();
     // restore the chain exactly
     cudaMemcpyAsync(state, saved, bytes, cudaMemcpyDeviceToDevice, h->stream);
     cudaMemcpyAsync(h->acc, &acc_saved, sizeof(DevAccum), cudaMemcpyHostToDevice, h->stream);
@@ -816,12 +916,15 @@ int hs_autotune(hs_lattice *h, double beta, int n_trial_sweeps) {
     h->sweep = sweep_saved;
     h->last_n_sweeps = last_saved;
     h->timing = timing_saved;
-    if (st) return st;
+    if (st) {
+        hs_set_launch(h, &req_saved);
+        return st;
+    }
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
-        g_tune_cache[key] = {best_v, best_b};
+        g_tune_cache[key] = best;
     }
-    return hs_set_launch(h, best_v, best_b);
+    return hs_set_launch(h, &best);
 }
 
 // ---------------------------------------------------------------- batch

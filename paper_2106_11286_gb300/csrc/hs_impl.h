@@ -56,6 +56,7 @@ struct PassArgs {
     const void *oth[3];
     int Lx, Ly, Lz, Lh;
     FastDiv div_nxv, div_ly;   // row = t / (Lh/V), z = row / Ly
+    int ty, zchunk, n_units;   // staged stencil: slab rows, planes per unit, units
     // table layout
     void *spins4;           // 4-vectors, renumbered order
     const int32_t *nbr;     // [width][n_pad]
@@ -80,9 +81,13 @@ struct PassArgs {
     DevAccum *acc;
 };
 
+enum KernelKind { kStencil = 1, kStaged = 2, kTable = 3 };
+
 struct Layout {
     bool structured;
-    int vec;                // vector width of the stencil kernel
+    int kernel;             // KernelKind
+    int vec;                // vector width of the stencil kernels
+    int ty, zchunk, n_units, grid;  // staged stencil tiling and grid
     int n_colours;
     int64_t n_sites, n_present;
     // stencil
@@ -108,5 +113,7 @@ cudaError_t launch_gather(int precision, const Layout &L, double *d_xyz, cudaStr
 cudaError_t launch_measure(int precision, const Layout &L, const PassArgs &a, int n_blocks, cudaStream_t s);
 int pass_blocks(int precision, const Layout &L, int n_sm, int blocks_per_sm);
 int pass_occupancy(int precision, const Layout &L, int accumulate);
+size_t staged_smem_bytes(int precision, int ty, int Lh);
+int staged_occupancy(int precision, int vec, size_t smem_bytes);  // 0 = does not fit
 
 }  // namespace hs

@@ -299,6 +299,65 @@ __device__ __forceinline__ void write_partials(const PassArgs &a, C e, C x, C y,
 // row: p = 0 -> (xh-1, xh), p = 1 -> (xh, xh+1); the +-y and +-z neighbours
 // sit at the same xh in the adjacent rows.  Neighbour order of the local
 // field sum: -x, +x, -y, +y, -z, +z.
+
+// Metropolis steps (ii)-(iii) for the V sites of one work item, given the
+// item's own spins s, the other colour's same row o (+ the edge element ed
+// beyond it), and the other colour's rows at y-1, y+1, z-1, z+1.  Updates s
+// in place; returns whether any site was accepted.
+template <int P, int V, bool MEAS>
+__device__ __forceinline__ bool update_item(Vec<typename Tr<P>::S, V> (&s)[3], const Vec<typename Tr<P>::S, V> (&o)[3],
+                                            const Vec<typename Tr<P>::S, V> (&nym)[3],
+                                            const Vec<typename Tr<P>::S, V> (&nyp)[3],
+                                            const Vec<typename Tr<P>::S, V> (&nzm)[3],
+                                            const Vec<typename Tr<P>::S, V> (&nzp)[3], const typename Tr<P>::C (&ed)[3],
+                                            uint32_t p, uint32_t site0, int c, const PassArgs &a,
+                                            typename Tr<P>::C J, typename Tr<P>::C K, typename Tr<P>::C ex,
+                                            typename Tr<P>::C ey, typename Tr<P>::C ez, typename Tr<P>::C beta,
+                                            typename Tr<P>::C &accE, typename Tr<P>::C &accX,
+                                            typename Tr<P>::C &accY, typename Tr<P>::C &accZ, unsigned &nacc) {
+    using S = typename Tr<P>::S;
+    using C = typename Tr<P>::C;
+    bool any = false;
+#pragma unroll
+    for (int k = 0; k < V; ++k) {
+        C h[3];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            const C xm = p ? to_c(o[q].v[k]) : (k == 0 ? ed[q] : to_c(o[q].v[k - 1]));
+            const C xp = p ? (k == V - 1 ? ed[q] : to_c(o[q].v[k + 1])) : to_c(o[q].v[k]);
+            h[q] = ((((xm + xp) + to_c(nym[q].v[k])) + to_c(nyp[q].v[k])) + to_c(nzm[q].v[k])) + to_c(nzp[q].v[k]);
+        }
+        C tx, ty, tz, u;
+        draw_trial<P>(site0 + 2u * k, a.sweep, (uint32_t)c, a.replica, a.key0, a.key1, tx, ty, tz, u);
+        C sx = to_c(s[0].v[k]), sy = to_c(s[1].v[k]), sz = to_c(s[2].v[k]);
+        const bool acc = metropolis<C>(sx, sy, sz, tx, ty, tz, h[0], h[1], h[2], J, K, ex, ey, ez, beta, u);
+        if (acc) {
+            sx = tx;
+            sy = ty;
+            sz = tz;
+            s[0].v[k] = to_store<S, C>(tx);
+            s[1].v[k] = to_store<S, C>(ty);
+            s[2].v[k] = to_store<S, C>(tz);
+            any = true;
+            ++nacc;
+        }
+        if (MEAS) {
+            // bond energy counted at the later colour's end: pass 1 owns
+            // every sc bond, pass 0 only the anisotropy term
+            const C se = sx * ex + sy * ey + sz * ez;
+            C ei = -K * se * se;
+            if (c == 1) ei -= J * (sx * h[0] + sy * h[1] + sz * h[2]);
+            accE += ei;
+            accX += sx;
+            accY += sy;
+            accZ += sz;
+        }
+    }
+    return any;
+}
+
+// Register stencil: every operand is loaded from global memory (L1/L2 serve
+// the neighbour rows shared by adjacent work items).
 template <int P, int V, bool MEAS>
 __global__ void __launch_bounds__(kBlock) sc_pass_kernel(const PassArgs a) {
     using S = typename Tr<P>::S;
@@ -345,47 +404,200 @@ __global__ void __launch_bounds__(kBlock) sc_pass_kernel(const PassArgs a) {
             ed[q] = to_c(oth[q][bed]);
         }
         const uint32_t site0 = row * Lx + 2 * xh0 + p;
-        bool any = false;
-#pragma unroll
-        for (int k = 0; k < V; ++k) {
-            C h[3];
-#pragma unroll
-            for (int q = 0; q < 3; ++q) {
-                const C xm = p ? to_c(o[q].v[k]) : (k == 0 ? ed[q] : to_c(o[q].v[k - 1]));
-                const C xp = p ? (k == V - 1 ? ed[q] : to_c(o[q].v[k + 1])) : to_c(o[q].v[k]);
-                h[q] = ((((xm + xp) + to_c(nym[q].v[k])) + to_c(nyp[q].v[k])) + to_c(nzm[q].v[k])) +
-                       to_c(nzp[q].v[k]);
-            }
-            C tx, ty, tz, u;
-            draw_trial<P>(site0 + 2u * k, a.sweep, (uint32_t)c, a.replica, a.key0, a.key1, tx, ty, tz, u);
-            C sx = to_c(s[0].v[k]), sy = to_c(s[1].v[k]), sz = to_c(s[2].v[k]);
-            const bool acc = metropolis<C>(sx, sy, sz, tx, ty, tz, h[0], h[1], h[2], J, K, ex, ey, ez, beta, u);
-            if (acc) {
-                sx = tx;
-                sy = ty;
-                sz = tz;
-                s[0].v[k] = to_store<S, C>(tx);
-                s[1].v[k] = to_store<S, C>(ty);
-                s[2].v[k] = to_store<S, C>(tz);
-                any = true;
-                ++nacc;
-            }
-            if (MEAS) {
-                // bond energy counted at the later colour's end: pass 1 owns
-                // every sc bond, pass 0 only the anisotropy term
-                const C se = sx * ex + sy * ey + sz * ez;
-                C ei = -K * se * se;
-                if (c == 1) ei -= J * (sx * h[0] + sy * h[1] + sz * h[2]);
-                accE += ei;
-                accX += sx;
-                accY += sy;
-                accZ += sz;
-            }
-        }
-        if (any) {
+        if (update_item<P, V, MEAS>(s, o, nym, nyp, nzm, nzp, ed, p, site0, c, a, J, K, ex, ey, ez, beta, accE, accX,
+                                    accY, accZ, nacc)) {
 #pragma unroll
             for (int q = 0; q < 3; ++q) *reinterpret_cast<VT *>(own[q] + b0) = s[q];
         }
+    }
+    write_partials<C, MEAS>(a, accE, accX, accY, accZ, nacc);
+}
+
+// ----------------------------------------------------------------- staged stencil pass
+// The other colour's planes are staged in shared memory by the bulk-copy
+// (TMA) engine.  A CTA owns a slab of ty rows (full x) and marches through a
+// chunk of z planes.  Shared memory holds a ring of 4 other-colour plane
+// slabs (z-1, z, z+1 and z+2 arriving), each ty+2 rows (halo rows y0-1 and
+// y0+ty wrap periodically), and 2 own-colour slabs (z, z+1 arriving).  Every
+// copy group completes on an mbarrier with an expected byte count; waits are
+// bounded (timeout -> device error word, uniform abort of the CTA).
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint64_t *bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
+// Bounded wait on one phase of an mbarrier: about one second of clock, or
+// 2^26 polls, whichever comes first.
+constexpr long long kWaitCycles = 2000000000LL;
+
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
+    if (mbar_try(bar, parity)) return true;
+    const long long t0 = clock64();
+    for (uint32_t it = 0; it < (1u << 26); ++it) {
+        if (mbar_try(bar, parity)) return true;
+        if (clock64() - t0 > kWaitCycles) return false;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+// Issue one copy group from warp 0: n_oth other-colour planes starting at
+// plane zo (ring slots so..so+n_oth-1) and optionally the own plane zw into
+// own slot sw.  Lane l issues copy l: other copies are (plane, component,
+// {main rows, low halo row, high halo row}), own copies one per component.
+template <typename S>
+__device__ __forceinline__ void issue_group(uint64_t *bar, S *oth_s, S *own_s, const PassArgs &a, int ty, int y0,
+                                            int zo, int n_oth, int so, int zw, int sw) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t row_bytes = (uint32_t)a.Lh * sizeof(S);
+    const int n_own = (zw >= 0) ? 3 : 0;
+    if (lane == 0) {
+        const uint32_t bytes = (uint32_t)(n_oth * 3 * (ty + 2) + n_own * ty) * row_bytes;
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_expect_tx(bar, bytes);
+    }
+    __syncwarp();
+    const int n_copies = n_oth * 9 + n_own;
+    const int Ly = a.Ly, Lz = a.Lz, Lh = a.Lh;
+    for (int l = lane; l < n_copies; l += 32) {
+        if (l < n_oth * 9) {
+            const int pl = l / 9, q = (l % 9) / 3, part = l % 3;
+            int z = zo + pl;
+            z = (z % Lz + Lz) % Lz;
+            const int slot = (so + pl) & 3;
+            const S *plane = static_cast<const S *>(a.oth[q]);
+            S *dst = oth_s + ((size_t)(slot * 3 + q) * (ty + 2)) * Lh;
+            if (part == 0) {
+                bulk_g2s(dst + Lh, plane + ((size_t)z * Ly + y0) * Lh, (uint32_t)ty * row_bytes, bar);
+            } else if (part == 1) {
+                const int y = (y0 == 0) ? Ly - 1 : y0 - 1;
+                bulk_g2s(dst, plane + ((size_t)z * Ly + y) * Lh, row_bytes, bar);
+            } else {
+                const int y = (y0 + ty == Ly) ? 0 : y0 + ty;
+                bulk_g2s(dst + (size_t)(ty + 1) * Lh, plane + ((size_t)z * Ly + y) * Lh, row_bytes, bar);
+            }
+        } else {
+            const int q = l - n_oth * 9;
+            const S *plane = static_cast<const S *>(a.own[q]);
+            S *dst = own_s + ((size_t)(sw * 3 + q) * ty) * Lh;
+            bulk_g2s(dst, plane + ((size_t)zw * Ly + y0) * Lh, (uint32_t)ty * row_bytes, bar);
+        }
+    }
+}
+
+template <int P, int V, bool MEAS>
+__global__ void __launch_bounds__(kBlock) sc_staged_kernel(const PassArgs a) {
+    using S = typename Tr<P>::S;
+    using C = typename Tr<P>::C;
+    using VT = Vec<S, V>;
+    extern __shared__ __align__(128) unsigned char hs_dyn_smem[];
+    __shared__ __align__(8) uint64_t bars[2];
+    const int Lh = a.Lh, Ly = a.Ly, Lx = a.Lx;
+    const int ty = a.ty;
+    const int nxv = Lh / V;
+    const int items = ty * nxv;
+    const int n_yslab = Ly / ty;
+    const int c = a.colour;
+    S *oth_s = reinterpret_cast<S *>(hs_dyn_smem);               // [4][3][ty+2][Lh]
+    S *own_s = oth_s + (size_t)4 * 3 * (ty + 2) * Lh;            // [2][3][ty][Lh]
+    S *own_g[3] = {(S *)a.own[0], (S *)a.own[1], (S *)a.own[2]};
+    C J, K, ex, ey, ez, beta;
+    load_params(a, J, K, ex, ey, ez, beta);
+    C accE = C(0), accX = C(0), accY = C(0), accZ = C(0);
+    unsigned nacc = 0;
+    if (threadIdx.x == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    uint32_t G = 0;  // copy groups issued so far by this CTA (barrier G&1, phase G>>1)
+    bool abort = false;
+    for (int unit = blockIdx.x; unit < a.n_units && !abort; unit += gridDim.x) {
+        const int ys = unit % n_yslab;
+        const int y0 = ys * ty;
+        const int z0 = (unit / n_yslab) * a.zchunk;
+        const int z1 = min(a.Lz, z0 + a.zchunk);
+        // prologue: other planes z0-1, z0, z0+1 into slots 0..2, own plane z0 into slot 0
+        if (threadIdx.x < 32) issue_group<S>(&bars[G & 1], oth_s, own_s, a, ty, y0, z0 - 1, 3, 0, z0, 0);
+        for (int z = z0; z < z1; ++z) {
+            const int j = z - z0;
+            const bool ok = mbar_wait_bounded(&bars[G & 1], (G >> 1) & 1);
+            if (__syncthreads_or(!ok)) {
+                abort = true;
+                break;
+            }
+            ++G;
+            if (z + 1 < z1 && threadIdx.x < 32)
+                issue_group<S>(&bars[G & 1], oth_s, own_s, a, ty, y0, z + 2, 1, (j + 3) & 3, z + 1, (j + 1) & 1);
+            const S *Om = oth_s + (size_t)((j & 3) * 3) * (ty + 2) * Lh;        // plane z-1
+            const S *O0 = oth_s + (size_t)(((j + 1) & 3) * 3) * (ty + 2) * Lh;  // plane z
+            const S *Op = oth_s + (size_t)(((j + 2) & 3) * 3) * (ty + 2) * Lh;  // plane z+1
+            const S *W = own_s + (size_t)((j & 1) * 3) * ty * Lh;               // own plane z
+            const size_t cs = (size_t)(ty + 2) * Lh;                            // component stride (other)
+            const size_t ws = (size_t)ty * Lh;                                  // component stride (own)
+            for (int it = threadIdx.x; it < items; it += kBlock) {
+                const int yl = (int)a.div_nxv.div((uint32_t)it);
+                const int xh0 = (it - yl * nxv) * V;
+                const int y = y0 + yl;
+                const uint32_t p = (uint32_t)(y + z + c) & 1u;
+                const int xe = p ? ((xh0 + V == Lh) ? 0 : xh0 + V) : ((xh0 == 0) ? Lh - 1 : xh0 - 1);
+                VT s[3], o[3], nym[3], nyp[3], nzm[3], nzp[3];
+                C ed[3];
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    const S *r0 = O0 + q * cs + (size_t)(yl + 1) * Lh;
+                    s[q] = *reinterpret_cast<const VT *>(W + q * ws + (size_t)yl * Lh + xh0);
+                    o[q] = *reinterpret_cast<const VT *>(r0 + xh0);
+                    nym[q] = *reinterpret_cast<const VT *>(r0 - Lh + xh0);
+                    nyp[q] = *reinterpret_cast<const VT *>(r0 + Lh + xh0);
+                    nzm[q] = *reinterpret_cast<const VT *>(Om + q * cs + (size_t)(yl + 1) * Lh + xh0);
+                    nzp[q] = *reinterpret_cast<const VT *>(Op + q * cs + (size_t)(yl + 1) * Lh + xh0);
+                    ed[q] = to_c(r0[xe]);
+                }
+                const uint32_t site0 = (uint32_t)((z * Ly + y) * Lx + 2 * xh0) + p;
+                if (update_item<P, V, MEAS>(s, o, nym, nyp, nzm, nzp, ed, p, site0, c, a, J, K, ex, ey, ez, beta,
+                                            accE, accX, accY, accZ, nacc)) {
+                    const size_t gi = ((size_t)z * Ly + y) * Lh + xh0;
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) *reinterpret_cast<VT *>(own_g[q] + gi) = s[q];
+                }
+            }
+            __syncthreads();  // every thread is done with the slots the next group overwrites
+        }
+    }
+    if (abort) {
+        if (threadIdx.x == 0) atomicExch(&a.acc->error, 1);
+        // the group that timed out may still land: give it one more bounded wait
+        mbar_wait_bounded(&bars[G & 1], (G >> 1) & 1);
+        __syncthreads();
     }
     write_partials<C, MEAS>(a, accE, accX, accY, accZ, nacc);
 }
@@ -621,10 +833,30 @@ cudaError_t launch_sc_v(const PassArgs &a, int n_blocks, cudaStream_t s, bool me
     return cudaGetLastError();
 }
 
+template <int P, int V>
+cudaError_t launch_staged_v(const Layout &L, const PassArgs &a, cudaStream_t s, bool meas) {
+    const size_t smem = staged_smem_bytes(P, L.ty, L.Lh);
+    if (meas)
+        sc_staged_kernel<P, V, true><<<L.grid, kBlock, smem, s>>>(a);
+    else
+        sc_staged_kernel<P, V, false><<<L.grid, kBlock, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
 template <int P>
 cudaError_t launch_pass_p(const Layout &L, const PassArgs &a, int n_blocks, cudaStream_t s) {
     const bool meas = a.accumulate != 0;
-    if (L.structured) {
+    if (L.kernel == kStaged) {
+        switch (L.vec) {
+        case 1: return launch_staged_v<P, 1>(L, a, s, meas);
+        case 2: return launch_staged_v<P, 2>(L, a, s, meas);
+        case 4: if constexpr (P != HS_FP64) return launch_staged_v<P, 4>(L, a, s, meas); break;
+        case 8: if constexpr (P == HS_FP16) return launch_staged_v<P, 8>(L, a, s, meas); break;
+        default: break;
+        }
+        return cudaErrorInvalidValue;
+    }
+    if (L.kernel == kStencil) {
         switch (L.vec) {
         case 1: return launch_sc_v<P, 1>(a, n_blocks, s, meas);
         case 2: return launch_sc_v<P, 2>(a, n_blocks, s, meas);
@@ -641,10 +873,58 @@ cudaError_t launch_pass_p(const Layout &L, const PassArgs &a, int n_blocks, cuda
     return cudaGetLastError();
 }
 
+template <int P>
+const void *staged_ptr(int vec, bool meas) {
+    switch (vec) {
+    case 1: return meas ? (const void *)sc_staged_kernel<P, 1, true> : (const void *)sc_staged_kernel<P, 1, false>;
+    case 2: return meas ? (const void *)sc_staged_kernel<P, 2, true> : (const void *)sc_staged_kernel<P, 2, false>;
+    case 4:
+        if constexpr (P != HS_FP64)
+            return meas ? (const void *)sc_staged_kernel<P, 4, true> : (const void *)sc_staged_kernel<P, 4, false>;
+        break;
+    case 8:
+        if constexpr (P == HS_FP16)
+            return meas ? (const void *)sc_staged_kernel<P, 8, true> : (const void *)sc_staged_kernel<P, 8, false>;
+        break;
+    default: break;
+    }
+    return nullptr;
+}
+
 }  // namespace
 
 size_t storage_size(int precision) {
     return precision == HS_FP64 ? 8 : (precision == HS_FP32 ? 4 : 2);
+}
+
+// 4 other-colour slabs of ty+2 rows and 2 own-colour slabs of ty rows, 3
+// components each, rows of Lh elements.
+size_t staged_smem_bytes(int precision, int ty, int Lh) {
+    return (size_t)(4 * 3 * (ty + 2) + 2 * 3 * ty) * (size_t)Lh * storage_size(precision);
+}
+
+int staged_occupancy(int precision, int vec, size_t smem_bytes) {
+    int dev = 0, optin = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return 0;
+    if (smem_bytes + 2048 > (size_t)optin) return 0;
+    int occ = 8;
+    for (int m = 0; m < 2; ++m) {
+        const void *k = nullptr;
+        switch (precision) {
+        case HS_FP64: k = staged_ptr<HS_FP64>(vec, m != 0); break;
+        case HS_FP32: k = staged_ptr<HS_FP32>(vec, m != 0); break;
+        case HS_FP16: k = staged_ptr<HS_FP16>(vec, m != 0); break;
+        default: break;
+        }
+        if (!k) return 0;
+        if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes) != cudaSuccess)
+            return 0;
+        int b = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k, kBlock, smem_bytes) != cudaSuccess) return 0;
+        occ = std::min(occ, b);
+    }
+    return occ;
 }
 
 static int64_t pass_items(const Layout &L) {
@@ -657,7 +937,7 @@ static int64_t pass_items(const Layout &L) {
 
 template <int P>
 static const void *pass_kernel_ptr(const Layout &L, bool meas) {
-    if (L.structured) {
+    if (L.kernel == kStencil) {
         switch (L.vec) {
         case 1: return meas ? (const void *)sc_pass_kernel<P, 1, true> : (const void *)sc_pass_kernel<P, 1, false>;
         case 2: return meas ? (const void *)sc_pass_kernel<P, 2, true> : (const void *)sc_pass_kernel<P, 2, false>;

@@ -44,6 +44,18 @@ class hs_measurement(ctypes.Structure):
                 ("accept_rate", ctypes.c_double)]
 
 
+class hs_launch(ctypes.Structure):
+    _fields_ = [("kernel", ctypes.c_int), ("vec_width", ctypes.c_int), ("blocks_per_sm", ctypes.c_int),
+                ("tile_y", ctypes.c_int), ("chunk_z", ctypes.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+HS_KERNEL_AUTO, HS_KERNEL_STENCIL, HS_KERNEL_STAGED, HS_KERNEL_TABLE = 0, 1, 2, 3
+KERNELS = {"auto": 0, "stencil": 1, "staged": 2, "table": 3}
+
+
 class hs_info(ctypes.Structure):
     _fields_ = [("type", ctypes.c_int), ("precision", ctypes.c_int), ("n_colours", ctypes.c_int),
                 ("structured", ctypes.c_int), ("n_sites", ctypes.c_int64), ("n_present", ctypes.c_int64),
@@ -76,8 +88,8 @@ SIGNATURES = {
     "hs_get_info": (ctypes.c_int, [_vp, ctypes.POINTER(hs_info)]),
     "hs_enable_timing": (ctypes.c_int, [_vp, ctypes.c_int]),
     "hs_read_timing": (ctypes.c_int, [_vp, _dp, _i64p]),
-    "hs_set_launch": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int]),
-    "hs_get_launch": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+    "hs_set_launch": (ctypes.c_int, [_vp, ctypes.POINTER(hs_launch)]),
+    "hs_get_launch": (ctypes.c_int, [_vp, ctypes.POINTER(hs_launch)]),
     "hs_autotune": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_int]),
     "hs_colour_greedy": (ctypes.c_int, [ctypes.c_int64, _i64p, _i32p, _u8p, _i32p, ctypes.POINTER(ctypes.c_int)]),
     "hs_batch_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.c_int]),
@@ -232,15 +244,16 @@ def hs_read_timing(h):
     return ms.value, n.value
 
 
-def hs_set_launch(h, vec_width=0, blocks_per_sm=0):
-    _check(load().hs_set_launch(h, int(vec_width), int(blocks_per_sm)))
+def hs_set_launch(h, kernel=0, vec_width=0, blocks_per_sm=0, tile_y=0, chunk_z=0):
+    k = KERNELS[kernel] if isinstance(kernel, str) else int(kernel)
+    cfg = hs_launch(k, int(vec_width), int(blocks_per_sm), int(tile_y), int(chunk_z))
+    _check(load().hs_set_launch(h, ctypes.byref(cfg)))
 
 
-def hs_get_launch(h):
-    v = ctypes.c_int(0)
-    b = ctypes.c_int(0)
-    _check(load().hs_get_launch(h, ctypes.byref(v), ctypes.byref(b)))
-    return v.value, b.value
+def hs_get_launch(h) -> dict:
+    cfg = hs_launch()
+    _check(load().hs_get_launch(h, ctypes.byref(cfg)))
+    return cfg.as_dict()
 
 
 def hs_autotune(h, beta, n_trial_sweeps=3):
@@ -332,8 +345,8 @@ class Lattice:
         hs_autotune(self.h, beta, n_trial_sweeps)
         return hs_get_launch(self.h)
 
-    def set_launch(self, vec_width=0, blocks_per_sm=0):
-        hs_set_launch(self.h, vec_width, blocks_per_sm)
+    def set_launch(self, kernel=0, vec_width=0, blocks_per_sm=0, tile_y=0, chunk_z=0):
+        hs_set_launch(self.h, kernel, vec_width, blocks_per_sm, tile_y, chunk_z)
 
     @property
     def launch(self):

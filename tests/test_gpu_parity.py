@@ -222,24 +222,44 @@ def test_beta_zero_accepts_everything_and_infinite_beta_nothing():
         assert m["accept_rate"] == 0.0 and m["E"] == E0
 
 
-@pytest.mark.parametrize("precision,dims", [("fp32", (16, 8, 8)), ("fp16", (32, 8, 4)), ("fp64", (8, 8, 8))])
+def _launch_configs(precision, dims):
+    widths = {"fp64": (1, 2), "fp32": (1, 2, 4), "fp16": (1, 2, 4, 8)}[precision]
+    es = {"fp64": 8, "fp32": 4, "fp16": 2}[precision]
+    lh = dims[0] // 2
+    out = []
+    for v in widths:
+        if lh % v:
+            continue
+        out += [dict(kernel="stencil", vec_width=v, blocks_per_sm=1), dict(kernel="stencil", vec_width=v)]
+        if (lh * es) % 16 == 0:
+            for ty in (1, 2, 4):
+                if dims[1] % ty == 0:
+                    out += [dict(kernel="staged", vec_width=v, tile_y=ty),
+                            dict(kernel="staged", vec_width=v, tile_y=ty, chunk_z=1),
+                            dict(kernel="staged", vec_width=v, tile_y=ty, chunk_z=3)]
+    return out
+
+
+@pytest.mark.parametrize("precision,dims", [("fp32", (16, 8, 6)), ("fp16", (32, 8, 4)), ("fp64", (8, 12, 8)),
+                                            ("fp32", (8, 4, 2))])
 def test_launch_configuration_does_not_change_results(precision, dims):
     """A site's random numbers and arithmetic depend only on its natural index,
-    so every vector width and grid size gives bit-identical chains; the
-    autotuner restores the state it perturbs."""
+    so every kernel, vector width, slab and chunk gives bit-identical chains;
+    the autotuner restores the state it perturbs."""
     outs = []
-    widths = {"fp64": (1, 2), "fp32": (1, 2, 4), "fp16": (1, 2, 4, 8)}[precision]
-    for v in widths:
-        for bps in (1, 0):
-            with hs.Lattice("sc", dims=dims, K=0.1, precision=precision, seed=6) as lat:
-                lat.set_launch(v, bps)
-                assert lat.launch[0] == v
-                lat.init()
-                lat.accumulate(True)
-                lat.sweep(0.9, 6)
-                outs.append((lat.get_spins(), lat.read_accumulator()[0]))
-    for S, mom in outs[1:]:
-        assert np.array_equal(S, outs[0][0])
+    cfgs = _launch_configs(precision, dims)
+    assert any(c["kernel"] == "staged" for c in cfgs)
+    for cfg in cfgs:
+        with hs.Lattice("sc", dims=dims, K=0.1, precision=precision, seed=6) as lat:
+            lat.set_launch(**cfg)
+            got = lat.launch
+            assert got["vec_width"] == cfg["vec_width"] and got["kernel"] == hs.KERNELS[cfg["kernel"]]
+            lat.init()
+            lat.accumulate(True)
+            lat.sweep(0.9, 6)
+            outs.append((lat.get_spins(), lat.read_accumulator()[0]))
+    for (S, mom), cfg in zip(outs[1:], cfgs[1:]):
+        assert np.array_equal(S, outs[0][0]), cfg
         # spins are bit-identical; FP32 per-thread partial sums group differently
         np.testing.assert_allclose(mom, outs[0][1], rtol=1e-12 if precision == "fp64" else 2e-6)
     with hs.Lattice("sc", dims=dims, K=0.1, precision=precision, seed=6) as lat:
@@ -251,3 +271,20 @@ def test_launch_configuration_does_not_change_results(precision, dims):
         lat.sweep(0.9, 4)
         assert np.array_equal(lat.get_spins(), outs[0][0])
         assert lat.read_accumulator()[1] == 6
+
+
+def test_staged_kernel_parity_large(orc):
+    """Staged kernel on a lattice with several slabs and chunks, one FP64 sweep
+    against the oracle."""
+    dims = (16, 24, 20)
+    g = orc.lattice("sc", dims)
+    S0 = inputs.random_unit_spins(g.n, 12)
+    with hs.Lattice("sc", dims=dims, precision="fp64", seed=3, **PARAMS) as lat:
+        lat.set_launch(kernel="staged", tile_y=4, chunk_z=3)
+        lat.set_spins(S0)
+        lat.sweep(0.7, 1)
+        got = lat.get_spins()
+    want = S0.copy()
+    band = np.zeros(g.n, dtype=np.uint8)
+    orc.sweep(g, want, beta=0.7, seed=3, sweep_index=0, band=1e-9, band_site=band, **PARAMS)
+    check_sweep_parity(g, S0, got, want, band, 1e-12)
