@@ -254,6 +254,39 @@ int hs_batch_create(hs_batch **out, hs_lattice *const *members, int n_members);
 int hs_batch_run(hs_batch *b, const double *betas, int64_t n_sweeps, int64_t n_equil);
 void hs_batch_destroy(hs_batch *b);
 
+/* Allocation-free sweep (the paper has no counterpart; it is a service to
+ * callers that cannot allocate device memory themselves: a host framework
+ * whose caching allocator or fixed budget owns all device memory, or a
+ * latency-critical loop that cannot afford cudaMalloc's implicit device-wide
+ * synchronisation).
+ * Runs n_sweeps sweeps (sweep indices first_sweep, first_sweep+1, ...) of the
+ * FP32 sc stencil kernel, with the same random numbers and arithmetic as a
+ * handle created with HS_SC, periodic, HS_FP32, seed and replica, on spins
+ * the caller holds in device memory:
+ *   planes  device, 6 planes of Lz*Ly*(Lx/2) floats in the order colour 0
+ *           x, y, z, colour 1 x, y, z; site (x,y,z) of colour (x+y+z)&1 at
+ *           index (z*Ly + y)*(Lx/2) + x/2 of its colour's planes.  Updated
+ *           in place.  dims all even and >= 2, fewer than 2^31 sites.
+ *   d_out   device, HS_N_MOMENTS + 2 doubles, overwritten with the moment
+ *           sums of this call's sweeps (hs_moment order), the number of
+ *           sweeps and the number of accepted moves.
+ * It calls no cudaMalloc, cudaFree or allocating library routine.  Its
+ * reduction scratch (per-CTA slots for at most HS_NOALLOC_MAX_CTAS CTAs, the
+ * accumulator and an arrival counter, about 80 KB) is one static device
+ * array that every GPU loading the library holds until the process exits.
+ * Each call zeroes what must start at zero; every call shares the array, so
+ * calls whose work overlaps on the GPU (on different streams, or from
+ * several threads) race and must be serialised by the caller.  The first
+ * call on a device looks up the array's device address (cudaGetSymbolAddress,
+ * once per device, with that device current); make that first call before
+ * any stream capture.  A device that would need more CTAs than the scratch
+ * holds is rejected with HS_E_INVALID.  Asynchronous on cuda_stream;
+ * errors are reported through hs_last_error. */
+#define HS_NOALLOC_MAX_CTAS 1024
+int hs_sweep_sc_fp32_noalloc(float *planes, const int32_t dims[3], const hs_params *p, double beta,
+                             uint64_t seed, uint32_t replica, uint64_t first_sweep, int64_t n_sweeps,
+                             double *d_out, void *cuda_stream);
+
 const char *hs_last_error(void);
 int hs_api_version(void);
 

@@ -28,6 +28,15 @@
 
 #include "hs_impl.h"
 
+namespace {
+std::string &g_error_ref();
+}
+
+int hs::set_last_error(int code, const std::string &msg) {
+    g_error_ref() = msg;
+    return code;
+}
+
 using hs::DevAccum;
 using hs::Layout;
 using hs::PassArgs;
@@ -35,6 +44,8 @@ using hs::PassArgs;
 namespace {
 
 thread_local std::string g_error;
+
+std::string &g_error_ref() { return g_error; }
 
 int fail(int code, const std::string &msg) {
     g_error = msg;

@@ -16,6 +16,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+
 #include "../../include/hs.h"
 
 namespace hs {
@@ -103,6 +105,9 @@ struct Layout {
 };
 
 size_t storage_size(int precision);
+
+// Record the thread-local message returned by hs_last_error; returns code.
+int set_last_error(int code, const std::string &msg);
 
 // Kernel launchers (kernels.cu).  All return cudaError_t of the launch.
 cudaError_t launch_pass(int precision, const Layout &L, const PassArgs &a, int n_blocks, cudaStream_t s);

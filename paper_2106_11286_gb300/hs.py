@@ -95,6 +95,9 @@ SIGNATURES = {
     "hs_batch_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.c_int]),
     "hs_batch_run": (ctypes.c_int, [_vp, _dp, ctypes.c_int64, ctypes.c_int64]),
     "hs_batch_destroy": (None, [_vp]),
+    "hs_sweep_sc_fp32_noalloc": (ctypes.c_int, [_vp, _i32p, ctypes.POINTER(hs_params), ctypes.c_double,
+                                                 ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int64,
+                                                 _vp, _vp]),
     "hs_last_error": (ctypes.c_char_p, []),
     "hs_api_version": (ctypes.c_int, []),
 }
@@ -272,6 +275,17 @@ def hs_colour_greedy(row_ptr, col_idx, site_mask=None):
     _check(load().hs_colour_greedy(n, _ptr(rp, ctypes.c_int64), _ptr(ci, ctypes.c_int32), _ptr(m, ctypes.c_uint8),
                                    _ptr(out, ctypes.c_int32), ctypes.byref(nc)))
     return out[:n], nc.value
+
+
+def hs_sweep_sc_fp32_noalloc(planes, dims, beta, n_sweeps, d_out, *, J=1.0, K=0.0, e=(0.0, 0.0, 1.0), seed=0,
+                             replica=0, first_sweep=0, stream=None):
+    """planes: CUDA float32 tensor (6 * Lz * Ly * Lx/2, stencil layout); d_out:
+    CUDA float64 tensor with HS_N_MOMENTS + 2 elements.  Allocates nothing."""
+    d = np.ascontiguousarray(dims, dtype=np.int32)
+    p = hs_params(float(J), float(K), (ctypes.c_double * 3)(*[float(v) for v in e]))
+    _check(load().hs_sweep_sc_fp32_noalloc(planes.data_ptr(), _ptr(d, ctypes.c_int32), ctypes.byref(p),
+                                           float(beta), int(seed), int(replica), int(first_sweep), int(n_sweeps),
+                                           d_out.data_ptr(), _stream_handle(stream)))
 
 
 def hs_batch_create(members):
