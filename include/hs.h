@@ -22,13 +22,19 @@
  *        take the smallest colour unused by an earlier-coloured neighbour.
  *
  * Random numbers: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) with
- *   counter = (site natural index, sweep, tag<<24 | colour<<8 | call, replica)
+ *   counter = (index, sweep, tag<<24 | colour<<8 | call, replica)
  *   key     = (seed & 0xffffffff, seed >> 32)
  * tag 0 = trial move, tag 1 = initial spin.  The FP64 path draws two blocks
- * per trial (calls 0 and 1): u_z from words 0,1, u_phi from words 2,3 of
- * call 0 and P from words 0,1 of call 1, each u = ((a>>5) 2^26 + (b>>6)) 2^-53.
- * The FP32 and FP16 paths draw one block: u_z, u_phi, P from words 0, 1, 2,
- * each u = (a>>8) 2^-24.  Initial spins always use one FP64-schedule block.
+ * per trial keyed by the natural site index (calls 0 and 1): u_z from words
+ * 0,1, u_phi from words 2,3 of call 0 and P from words 0,1 of call 1, each
+ * u = ((a>>5) 2^26 + (b>>6)) 2^-53.  The FP32 and FP16 paths share one block
+ * between two sites of the same colour: the site whose rank among the
+ * present sites of its colour (ascending natural index) is r uses block
+ * index r >> 1 and its half r & 1, words (a, b) = 2(r&1), 2(r&1)+1;
+ * u_z = (a>>11) 2^-21, u_phi = (b>>11) 2^-21,
+ * P = (((a & 0x7ff) << 11) | (b & 0x7ff)) 2^-22.  On a periodic sc lattice
+ * r = natural index >> 1.  Initial spins always use one FP64-schedule block
+ * keyed by the natural index.
  * Trial orientation: z = 2u_z - 1, phi = pi (2u_phi - 1),
  * r = sqrt((1-z)(1+z)), S' = (r cos phi, r sin phi, z).
  * There is no random-number state in memory.
@@ -223,6 +229,8 @@ typedef struct {
     int blocks_per_sm; /* stencil / table: resident CTAs per SM (0 = max) */
     int tile_y;        /* staged: rows per CTA slab (divides Ly) */
     int chunk_z;       /* staged: planes per CTA work unit */
+    int prefetch;      /* stencil: 1 = issue the next work item's loads before
+                          computing the current one, 2 = off, 0 = automatic */
 } hs_launch;
 
 /* Set (fields 0 = automatic) or read the launch configuration.  The staged

@@ -21,7 +21,9 @@
  *     phi = pi (2u'-1), r = sqrt((1-z)(1+z)), S' = (r cos phi, r sin phi, z);
  *   - random numbers come from Philox4x32-10 (Salmon, Moraes, Dror, Shaw,
  *     "Parallel random numbers: as easy as 1, 2, 3", SC'11), counter
- *     (site, sweep, tag<<24 | colour<<8 | call, replica), key (seed lo, hi).
+ *     (index, sweep, tag<<24 | colour<<8 | call, replica), key (seed lo, hi);
+ *     index = natural site index (FP64 schedule, initial spins) or the
+ *     site's rank within its colour class halved (FP32 schedule).
  *
  * Build: gcc -O2 -ffp-contract=off -fPIC -shared (no FMA contraction, so
  * every product and sum is the one written here).
@@ -106,9 +108,17 @@ static void or_sphere_point(double uz, double uphi, double s[3])
 }
 
 /* Draw the two uniforms (u_z, u_phi) and the acceptance uniform P of one
- * trial move.  mode 0: FP64 schedule (two Philox calls, three 53-bit
- * uniforms).  mode 1 and 2: FP32 schedule (one call, three 24-bit uniforms). */
-static void or_trial_uniforms(int mode, uint64_t seed, uint32_t replica, uint64_t site,
+ * trial move.
+ * mode 0 (FP64 schedule): two Philox blocks keyed by the natural site index
+ *   (calls 0 and 1), three 53-bit uniforms: u_z from words 0,1 and u_phi
+ *   from words 2,3 of call 0, P from words 0,1 of call 1.
+ * mode 1 and 2 (FP32 schedule): one Philox block serves two sites of the
+ *   same colour: the site whose rank among the present sites of its colour
+ *   (ascending natural index) is r uses block r >> 1 (counter word 0) and
+ *   its half r & 1, i.e. words a = 2(r&1) and b = a+1.  u_z and u_phi are
+ *   the top 21 bits of a and b, P the two low 11-bit fields (a's above b's),
+ *   22 bits: u = k 2^-21, P = k 2^-22. */
+static void or_trial_uniforms(int mode, uint64_t seed, uint32_t replica, uint64_t site, uint64_t rank,
                               uint64_t sweep, uint32_t colour, double u[3])
 {
     uint32_t r[4];
@@ -119,10 +129,12 @@ static void or_trial_uniforms(int mode, uint64_t seed, uint32_t replica, uint64_
         or_draw(seed, replica, site, sweep, OR_TAG_TRIAL, colour, 1, r);
         u[2] = or_u53(r[0], r[1]);
     } else {
-        or_draw(seed, replica, site, sweep, OR_TAG_TRIAL, colour, 0, r);
-        u[0] = or_u24(r[0]);
-        u[1] = or_u24(r[1]);
-        u[2] = or_u24(r[2]);
+        or_draw(seed, replica, rank >> 1, sweep, OR_TAG_TRIAL, colour, 0, r);
+        uint32_t a = r[2 * (rank & 1)];
+        uint32_t b = r[2 * (rank & 1) + 1];
+        u[0] = (double)(a >> 11) / 2097152.0;                               /* 2^21 */
+        u[1] = (double)(b >> 11) / 2097152.0;
+        u[2] = (double)(((a & 0x7FFu) << 11) | (b & 0x7FFu)) / 4194304.0;  /* 2^22 */
     }
 }
 
@@ -360,7 +372,8 @@ static double site_energy(const double s[3], const double h[3], double J, double
 /* One Metropolis sweep: colour classes 0..n_colours-1 in order, present    */
 /* sites of the class in ascending natural index.                           */
 /*   mode 0: FP64 random-number schedule, spins kept in FP64               */
-/*   mode 1: FP32 random-number schedule, spins kept in FP64               */
+/*   mode 1: FP32 random-number schedule (a block per two same-colour      */
+/*           sites), spins kept in FP64                                     */
 /*   mode 2: FP32 schedule, the trial spin rounded to binary16 per          */
 /*           component before dH (the stored state is the rounded one)     */
 /* Outputs: returns accepted moves; *sum_dH gets the sum of accepted dH;    */
@@ -376,11 +389,13 @@ int64_t or_sweep(int64_t n, const int64_t *row_ptr, const int32_t *col, const in
     double dH_total = 0.0;
     int64_t bands = 0;
     for (int c = 0; c < n_colours; ++c) {
+        uint64_t rank = 0; /* rank of site i among the present sites of colour c */
         for (int64_t i = 0; i < n; ++i) {
             if (colour[i] != c)
                 continue;
             if (mask && !mask[i])
                 continue;
+            uint64_t my_rank = rank++;
             /* step (i): site i; local field from present neighbours */
             double h[3] = {0.0, 0.0, 0.0};
             for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
@@ -393,7 +408,7 @@ int64_t or_sweep(int64_t n, const int64_t *row_ptr, const int32_t *col, const in
             }
             /* step (ii): random new orientation */
             double u[3];
-            or_trial_uniforms(mode, seed, replica, (uint64_t)i, sweep, (uint32_t)c, u);
+            or_trial_uniforms(mode, seed, replica, (uint64_t)i, my_rank, sweep, (uint32_t)c, u);
             double trial[3];
             or_sphere_point(u[0], u[1], trial);
             if (mode == 2) {

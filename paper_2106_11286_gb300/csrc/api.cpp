@@ -354,9 +354,12 @@ bool vec_ok(const hs_lattice *h, int v) {
     return (v == 1 || v == 2 || v == 4 || v == 8) && v * es <= 16 && h->L.Lh % v == 0;
 }
 
+// Widest vector of at most 16 bytes dividing Lx/2; FP16 stops at 4 sites
+// (8 bytes), which measured faster than 8 on GB300 (fewer registers).
 int default_vec(const hs_lattice *h) {
     const int es = (int)hs::storage_size(h->precision);
-    for (int v = 16 / es; v > 1; v /= 2)
+    const int vmax = std::min(16 / es, 4);
+    for (int v = vmax; v > 1; v /= 2)
         if (h->L.Lh % v == 0) return v;
     return 1;
 }
@@ -419,6 +422,7 @@ int configure_launch(hs_lattice *h) {
         return HS_OK;
     }
     L.kernel = hs::kStencil;  // before the occupancy query, which looks at the kind
+    L.prefetch = (r.prefetch == 1);
     int bps = r.blocks_per_sm;
     const int occ = std::min(hs::pass_occupancy(h->precision, L, 0), hs::pass_occupancy(h->precision, L, 1));
     if (bps <= 0 || bps > occ) bps = occ;
@@ -798,6 +802,7 @@ int hs_set_launch(hs_lattice *h, const hs_launch *cfg) {
     if (cfg->blocks_per_sm < 0 || cfg->blocks_per_sm > 2048 / hs::kBlock)
         return fail(HS_E_INVALID, "blocks_per_sm out of range");
     if (cfg->tile_y < 0 || cfg->chunk_z < 0) return fail(HS_E_INVALID, "negative tile");
+    if (cfg->prefetch < 0 || cfg->prefetch > 2) return fail(HS_E_INVALID, "prefetch must be 0, 1 or 2");
     const hs_launch keep = h->req;
     const Layout keep_l = h->L;
     const int keep_b = h->n_blocks;
@@ -819,6 +824,7 @@ int hs_get_launch(const hs_lattice *h, hs_launch *out) {
     out->blocks_per_sm = (h->n_blocks + h->n_sm - 1) / std::max(h->n_sm, 1);
     out->tile_y = L.kernel == hs::kStaged ? L.ty : 0;
     out->chunk_z = L.kernel == hs::kStaged ? L.zchunk : 0;
+    out->prefetch = (L.kernel == hs::kStencil) ? (L.prefetch ? 1 : 2) : 0;
     return HS_OK;
 }
 
@@ -839,12 +845,13 @@ std::vector<hs_launch> tune_candidates(hs_lattice *h) {
     std::vector<hs_launch> out;
     const Layout &L = h->L;
     if (!L.structured) {
-        for (int b = 1; b <= 8; ++b) out.push_back({HS_KERNEL_TABLE, 1, b, 0, 0});
+        for (int b = 1; b <= 8; ++b) out.push_back({HS_KERNEL_TABLE, 1, b, 0, 0, 0});
         return out;
     }
     for (int v : {1, 2, 4, 8}) {
         if (!vec_ok(h, v)) continue;
-        for (int b = 1; b <= 8; ++b) out.push_back({HS_KERNEL_STENCIL, v, b, 0, 0});
+        for (int b = 1; b <= 8; ++b)
+            for (int pf : {1, 2}) out.push_back({HS_KERNEL_STENCIL, v, b, 0, 0, pf});
         if (!staged_ok(h)) continue;
         for (int ty : {1, 2, 4, 8, 16}) {
             if (L.Ly % ty != 0) continue;
@@ -858,7 +865,7 @@ std::vector<hs_launch> tune_candidates(hs_lattice *h) {
             for (int f : {1, 2, 4}) {
                 const int z = std::max(1, zc / f);
                 if (f > 1 && z == zc) continue;
-                out.push_back({HS_KERNEL_STAGED, v, 0, ty, z});
+                out.push_back({HS_KERNEL_STAGED, v, 0, ty, z, 0});
             }
         }
     }

@@ -89,6 +89,7 @@ struct Layout {
     bool structured;
     int kernel;             // KernelKind
     int vec;                // vector width of the stencil kernels
+    bool prefetch;          // register stencil: next work item's loads in flight
     int ty, zchunk, n_units, grid;  // staged stencil tiling and grid
     int n_colours;
     int64_t n_sites, n_present;

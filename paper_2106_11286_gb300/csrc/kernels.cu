@@ -108,10 +108,23 @@ __device__ __forceinline__ void draw_trial<HS_FP64>(uint32_t site, uint32_t swee
 // hardware reciprocal square root (r = w / sqrt(w), w = (1-z)(1+z) >= 0), the
 // azimuth from the hardware sine / cosine on [-pi, pi) (absolute error about
 // 4e-7, far below what a 24-bit proposal resolves statistically).
-__device__ __forceinline__ void sphere_fp32(uint4 w, float &tx, float &ty, float &tz, float &u) {
-    tz = (float)((int)(w.x >> 8) - (1 << 23)) * 0x1p-23f;
-    const float v = (float)((int)(w.y >> 8) - (1 << 23)) * 0x1p-23f;
-    u = (float)(w.z >> 8) * 0x1p-24f;
+// FP32 schedule: one Philox block serves two sites of the same colour.  The
+// site of rank r within its colour class (ascending natural index) uses
+// block r >> 1 and the half r & 1: words (a, b) = (x, y) or (z, w).
+// u_z and u_phi are the top 21 bits of a and b, P the two low 11-bit fields
+// (22 bits).  z and v = 2u - 1 are exact from the integers; r from the
+// hardware reciprocal square root (r = w / sqrt(w), w = (1-z)(1+z) >= 0);
+// the azimuth from the hardware sine / cosine on [-pi, pi) (absolute error
+// about 4e-7, far below what a 21-bit proposal resolves statistically).
+__device__ __forceinline__ uint4 trial_block(uint32_t rank_pair, uint32_t sweep, uint32_t colour, uint32_t replica,
+                                             uint32_t k0, uint32_t k1) {
+    return philox10(make_uint4(rank_pair, sweep, (kTagTrial << 24) | (colour << 8), replica), k0, k1);
+}
+
+__device__ __forceinline__ void sphere_fp32(uint32_t wa, uint32_t wb, float &tx, float &ty, float &tz, float &u) {
+    tz = (float)((int)(wa >> 11) - (1 << 20)) * 0x1p-20f;
+    const float v = (float)((int)(wb >> 11) - (1 << 20)) * 0x1p-20f;
+    u = (float)(((wa & 0x7FFu) << 11) | (wb & 0x7FFu)) * 0x1p-22f;
     const float w2 = (1.0f - tz) * (1.0f + tz);
     const float r = (w2 > 0.0f) ? w2 * rsqrtf(w2) : 0.0f;
     float sn, cs;
@@ -120,27 +133,30 @@ __device__ __forceinline__ void sphere_fp32(uint4 w, float &tx, float &ty, float
     ty = r * sn;
 }
 
-template <>
-__device__ __forceinline__ void draw_trial<HS_FP32>(uint32_t site, uint32_t sweep, uint32_t colour,
-                                                    uint32_t replica, uint32_t k0, uint32_t k1, float &tx,
-                                                    float &ty, float &tz, float &u) {
-    const uint4 a = philox10(make_uint4(site, sweep, (kTagTrial << 24) | (colour << 8), replica), k0, k1);
-    sphere_fp32(a, tx, ty, tz, u);
+// Trial orientation and acceptance uniform from one half (wa, wb) of a block
+// (FP32 schedule).  FP16 storage additionally renormalises and rounds the
+// trial to binary16, and the rounded vector is the one tested and stored, so
+// the chain samples the stored state.
+template <int P>
+__device__ __forceinline__ void trial_from_half(uint32_t wa, uint32_t wb, float &tx, float &ty, float &tz, float &u) {
+    sphere_fp32(wa, wb, tx, ty, tz, u);
+    if constexpr (P == HS_FP16) {
+        const float inv = rsqrtf(tx * tx + ty * ty + tz * tz);
+        tx = __half2float(__float2half_rn(tx * inv));
+        ty = __half2float(__float2half_rn(ty * inv));
+        tz = __half2float(__float2half_rn(tz * inv));
+    }
 }
 
-// FP16 storage: the FP32 trial is renormalised and rounded to binary16; the
-// rounded vector is the one tested and stored, so the chain samples the
-// stored state.
-template <>
-__device__ __forceinline__ void draw_trial<HS_FP16>(uint32_t site, uint32_t sweep, uint32_t colour,
-                                                    uint32_t replica, uint32_t k0, uint32_t k1, float &tx,
-                                                    float &ty, float &tz, float &u) {
-    const uint4 a = philox10(make_uint4(site, sweep, (kTagTrial << 24) | (colour << 8), replica), k0, k1);
-    sphere_fp32(a, tx, ty, tz, u);
-    const float inv = rsqrtf(tx * tx + ty * ty + tz * tz);
-    tx = __half2float(__float2half_rn(tx * inv));
-    ty = __half2float(__float2half_rn(ty * inv));
-    tz = __half2float(__float2half_rn(tz * inv));
+// One site's trial, FP32 / FP16 schedule, from its rank in the colour class.
+template <int P>
+__device__ __forceinline__ void draw_trial_rank(uint32_t rank, uint32_t sweep, uint32_t colour, uint32_t replica,
+                                                uint32_t k0, uint32_t k1, float &tx, float &ty, float &tz, float &u) {
+    const uint4 w = trial_block(rank >> 1, sweep, colour, replica, k0, k1);
+    if (rank & 1u)
+        trial_from_half<P>(w.z, w.w, tx, ty, tz, u);
+    else
+        trial_from_half<P>(w.x, w.y, tx, ty, tz, u);
 }
 
 template <typename S, typename C> __device__ __forceinline__ S to_store(C v);
@@ -152,15 +168,26 @@ __device__ __forceinline__ float exp_c(float x) { return __expf(x); }
 __device__ __forceinline__ double exp_c(double x) { return exp(x); }
 
 // Metropolis step (iii) for one site: dH of Eq. 1 restricted to the terms
-// that contain S_i, then dH <= 0 or P <= exp(-beta dH).
+// that contain S_i, dH = J (S.h - S'.h) + K ((S.e)^2 - (S'.e)^2), then
+// dH <= 0 or P <= exp(-beta dH).  The dot products are returned for the
+// fused energy measurement.
 template <typename C>
-__device__ __forceinline__ bool metropolis(C sx, C sy, C sz, C tx, C ty, C tz, C hx, C hy, C hz, C J, C K,
-                                           C ex, C ey, C ez, C beta, C u) {
-    const C dot_h = (tx - sx) * hx + (ty - sy) * hy + (tz - sz) * hz;
-    const C pe = tx * ex + ty * ey + tz * ez;
-    const C se = sx * ex + sy * ey + sz * ez;
-    const C dH = -J * dot_h - K * ((pe - se) * (pe + se));
-    return (dH <= C(0)) || (u <= exp_c(-beta * dH));
+struct SiteDots {
+    C sh, th, se, pe;
+    bool acc;
+};
+
+template <typename C>
+__device__ __forceinline__ SiteDots<C> metropolis(C sx, C sy, C sz, C tx, C ty, C tz, C hx, C hy, C hz, C J, C K,
+                                                  C ex, C ey, C ez, C beta, C u) {
+    SiteDots<C> d;
+    d.sh = sx * hx + sy * hy + sz * hz;
+    d.th = tx * hx + ty * hy + tz * hz;
+    d.se = sx * ex + sy * ey + sz * ez;
+    d.pe = tx * ex + ty * ey + tz * ez;
+    const C dH = J * (d.sh - d.th) + K * ((d.se - d.pe) * (d.se + d.pe));
+    d.acc = (dH <= C(0)) || (u <= exp_c(-beta * dH));
+    return d;
 }
 
 __device__ __forceinline__ void load_params(const PassArgs &a, double &J, double &K, double &ex, double &ey,
@@ -318,8 +345,8 @@ __device__ __forceinline__ bool update_item(Vec<typename Tr<P>::S, V> (&s)[3], c
     using S = typename Tr<P>::S;
     using C = typename Tr<P>::C;
     bool any = false;
-#pragma unroll
-    for (int k = 0; k < V; ++k) {
+    // Metropolis steps (ii)-(iii) for site k with trial (tx, ty, tz), uniform u
+    auto site = [&](int k, C tx, C ty, C tz, C u) {
         C h[3];
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
@@ -327,11 +354,9 @@ __device__ __forceinline__ bool update_item(Vec<typename Tr<P>::S, V> (&s)[3], c
             const C xp = p ? (k == V - 1 ? ed[q] : to_c(o[q].v[k + 1])) : to_c(o[q].v[k]);
             h[q] = ((((xm + xp) + to_c(nym[q].v[k])) + to_c(nyp[q].v[k])) + to_c(nzm[q].v[k])) + to_c(nzp[q].v[k]);
         }
-        C tx, ty, tz, u;
-        draw_trial<P>(site0 + 2u * k, a.sweep, (uint32_t)c, a.replica, a.key0, a.key1, tx, ty, tz, u);
         C sx = to_c(s[0].v[k]), sy = to_c(s[1].v[k]), sz = to_c(s[2].v[k]);
-        const bool acc = metropolis<C>(sx, sy, sz, tx, ty, tz, h[0], h[1], h[2], J, K, ex, ey, ez, beta, u);
-        if (acc) {
+        const SiteDots<C> d = metropolis<C>(sx, sy, sz, tx, ty, tz, h[0], h[1], h[2], J, K, ex, ey, ez, beta, u);
+        if (d.acc) {
             sx = tx;
             sy = ty;
             sz = tz;
@@ -344,70 +369,137 @@ __device__ __forceinline__ bool update_item(Vec<typename Tr<P>::S, V> (&s)[3], c
         if (MEAS) {
             // bond energy counted at the later colour's end: pass 1 owns
             // every sc bond, pass 0 only the anisotropy term
-            const C se = sx * ex + sy * ey + sz * ez;
-            C ei = -K * se * se;
-            if (c == 1) ei -= J * (sx * h[0] + sy * h[1] + sz * h[2]);
+            const C e_new = d.acc ? d.pe : d.se;
+            C ei = -K * e_new * e_new;
+            if (c == 1) ei -= J * (d.acc ? d.th : d.sh);
             accE += ei;
             accX += sx;
             accY += sy;
             accZ += sz;
         }
+    };
+    if constexpr (P == HS_FP64) {
+#pragma unroll
+        for (int k = 0; k < V; ++k) {
+            C tx, ty, tz, u;
+            draw_trial<P>(site0 + 2u * k, a.sweep, (uint32_t)c, a.replica, a.key0, a.key1, tx, ty, tz, u);
+            site(k, tx, ty, tz, u);
+        }
+    } else {
+        // ranks of the item's sites in their colour class: rank0 + k
+        const uint32_t rank0 = site0 >> 1;
+        if (V >= 2 && (rank0 & 1u) == 0u) {
+#pragma unroll
+            for (int j = 0; j < V / 2; ++j) {  // one Philox block per pair of sites
+                const uint4 w = trial_block((rank0 >> 1) + j, a.sweep, (uint32_t)c, a.replica, a.key0, a.key1);
+                float tx, ty, tz, u;
+                trial_from_half<P>(w.x, w.y, tx, ty, tz, u);
+                site(2 * j, tx, ty, tz, u);
+                trial_from_half<P>(w.z, w.w, tx, ty, tz, u);
+                site(2 * j + 1, tx, ty, tz, u);
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < V; ++k) {
+                float tx, ty, tz, u;
+                draw_trial_rank<P>(rank0 + k, a.sweep, (uint32_t)c, a.replica, a.key0, a.key1, tx, ty, tz, u);
+                site(k, tx, ty, tz, u);
+            }
+        }
     }
     return any;
 }
 
+// Operands of one work item of the register stencil.
+template <int P, int V>
+struct StencilItem {
+    Vec<typename Tr<P>::S, V> s[3], o[3], nym[3], nyp[3], nzm[3], nzp[3];
+    typename Tr<P>::C ed[3];
+    uint32_t b0, p, site0;
+};
+
+template <int P, int V>
+__device__ __forceinline__ void load_item(const PassArgs &a, uint32_t t, const typename Tr<P>::S *const (&own)[3],
+                                          const typename Tr<P>::S *const (&oth)[3], StencilItem<P, V> &it) {
+    using VT = Vec<typename Tr<P>::S, V>;
+    const uint32_t Lh = a.Lh, Ly = a.Ly, Lz = a.Lz, Lx = a.Lx;
+    const uint32_t nxv = Lh / V;
+    const uint32_t row = a.div_nxv.div(t);
+    const uint32_t xv = t - row * nxv;
+    const uint32_t z = a.div_ly.div(row);
+    const uint32_t y = row - z * Ly;
+    const uint32_t p = (y + z + (uint32_t)a.colour) & 1u;
+    const uint32_t xh0 = xv * V;
+    const uint32_t ym = (y == 0) ? Ly - 1 : y - 1;
+    const uint32_t yp = (y == Ly - 1) ? 0 : y + 1;
+    const uint32_t zm = (z == 0) ? Lz - 1 : z - 1;
+    const uint32_t zp = (z == Lz - 1) ? 0 : z + 1;
+    const uint32_t b0 = row * Lh + xh0;
+    const uint32_t bym = (z * Ly + ym) * Lh + xh0;
+    const uint32_t byp = (z * Ly + yp) * Lh + xh0;
+    const uint32_t bzm = (zm * Ly + y) * Lh + xh0;
+    const uint32_t bzp = (zp * Ly + y) * Lh + xh0;
+    const uint32_t bed = row * Lh + (p ? ((xh0 + V == Lh) ? 0 : xh0 + V) : ((xh0 == 0) ? Lh - 1 : xh0 - 1));
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        it.s[q] = *reinterpret_cast<const VT *>(own[q] + b0);
+        it.o[q] = *reinterpret_cast<const VT *>(oth[q] + b0);
+        it.nym[q] = *reinterpret_cast<const VT *>(oth[q] + bym);
+        it.nyp[q] = *reinterpret_cast<const VT *>(oth[q] + byp);
+        it.nzm[q] = *reinterpret_cast<const VT *>(oth[q] + bzm);
+        it.nzp[q] = *reinterpret_cast<const VT *>(oth[q] + bzp);
+        it.ed[q] = to_c(oth[q][bed]);
+    }
+    it.b0 = b0;
+    it.p = p;
+    it.site0 = row * Lx + 2 * xh0 + p;
+}
+
 // Register stencil: every operand is loaded from global memory (L1/L2 serve
-// the neighbour rows shared by adjacent work items).
-template <int P, int V, bool MEAS>
+// the neighbour rows shared by adjacent work items).  With PF the loads of
+// the thread's next work item are issued before the current one is
+// computed (two items in flight, unrolled by hand so no operand is copied).
+template <int P, int V, bool MEAS, bool PF>
 __global__ void __launch_bounds__(kBlock) sc_pass_kernel(const PassArgs a) {
     using S = typename Tr<P>::S;
     using C = typename Tr<P>::C;
     using VT = Vec<S, V>;
-    const uint32_t Lh = a.Lh, Ly = a.Ly, Lz = a.Lz, Lx = a.Lx;
-    const uint32_t nxv = Lh / V;
-    const uint32_t n_items = Lz * Ly * nxv;  // < 2^31: n_sites < 2^32
+    const uint32_t n_items = (uint32_t)a.Lz * a.Ly * (a.Lh / V);  // < 2^31: n_sites < 2^32
     const int c = a.colour;
     C J, K, ex, ey, ez, beta;
     load_params(a, J, K, ex, ey, ez, beta);
-    S *own[3] = {(S *)a.own[0], (S *)a.own[1], (S *)a.own[2]};
-    const S *oth[3] = {(const S *)a.oth[0], (const S *)a.oth[1], (const S *)a.oth[2]};
+    S *own_w[3] = {(S *)a.own[0], (S *)a.own[1], (S *)a.own[2]};
+    const S *const own[3] = {(const S *)a.own[0], (const S *)a.own[1], (const S *)a.own[2]};
+    const S *const oth[3] = {(const S *)a.oth[0], (const S *)a.oth[1], (const S *)a.oth[2]};
     C accE = C(0), accX = C(0), accY = C(0), accZ = C(0);
     unsigned nacc = 0;
     const uint32_t stride = gridDim.x * blockDim.x;
-    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < n_items; t += stride) {
-        const uint32_t row = a.div_nxv.div(t);
-        const uint32_t xv = t - row * nxv;
-        const uint32_t z = a.div_ly.div(row);
-        const uint32_t y = row - z * Ly;
-        const uint32_t p = (y + z + (uint32_t)c) & 1u;
-        const uint32_t xh0 = xv * V;
-        const uint32_t ym = (y == 0) ? Ly - 1 : y - 1;
-        const uint32_t yp = (y == Ly - 1) ? 0 : y + 1;
-        const uint32_t zm = (z == 0) ? Lz - 1 : z - 1;
-        const uint32_t zp = (z == Lz - 1) ? 0 : z + 1;
-        const uint32_t b0 = row * Lh + xh0;
-        const uint32_t bym = (z * Ly + ym) * Lh + xh0;
-        const uint32_t byp = (z * Ly + yp) * Lh + xh0;
-        const uint32_t bzm = (zm * Ly + y) * Lh + xh0;
-        const uint32_t bzp = (zp * Ly + y) * Lh + xh0;
-        const uint32_t bed = row * Lh + (p ? ((xh0 + V == Lh) ? 0 : xh0 + V) : ((xh0 == 0) ? Lh - 1 : xh0 - 1));
-        VT s[3], o[3], nym[3], nyp[3], nzm[3], nzp[3];
-        C ed[3];
+    auto compute = [&](StencilItem<P, V> &it) {
+        if (update_item<P, V, MEAS>(it.s, it.o, it.nym, it.nyp, it.nzm, it.nzp, it.ed, it.p, it.site0, c, a, J, K,
+                                    ex, ey, ez, beta, accE, accX, accY, accZ, nacc)) {
 #pragma unroll
-        for (int q = 0; q < 3; ++q) {
-            s[q] = *reinterpret_cast<const VT *>(own[q] + b0);
-            o[q] = *reinterpret_cast<const VT *>(oth[q] + b0);
-            nym[q] = *reinterpret_cast<const VT *>(oth[q] + bym);
-            nyp[q] = *reinterpret_cast<const VT *>(oth[q] + byp);
-            nzm[q] = *reinterpret_cast<const VT *>(oth[q] + bzm);
-            nzp[q] = *reinterpret_cast<const VT *>(oth[q] + bzp);
-            ed[q] = to_c(oth[q][bed]);
+            for (int q = 0; q < 3; ++q) *reinterpret_cast<VT *>(own_w[q] + it.b0) = it.s[q];
         }
-        const uint32_t site0 = row * Lx + 2 * xh0 + p;
-        if (update_item<P, V, MEAS>(s, o, nym, nyp, nzm, nzp, ed, p, site0, c, a, J, K, ex, ey, ez, beta, accE, accX,
-                                    accY, accZ, nacc)) {
-#pragma unroll
-            for (int q = 0; q < 3; ++q) *reinterpret_cast<VT *>(own[q] + b0) = s[q];
+    };
+    uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (!PF) {
+        for (; t < n_items; t += stride) {
+            StencilItem<P, V> it;
+            load_item<P, V>(a, t, own, oth, it);
+            compute(it);
+        }
+    } else if (t < n_items) {
+        StencilItem<P, V> A, B;
+        load_item<P, V>(a, t, own, oth, A);
+        while (true) {
+            if (t + stride < n_items) load_item<P, V>(a, t + stride, own, oth, B);
+            compute(A);
+            t += stride;
+            if (t >= n_items) break;
+            if (t + stride < n_items) load_item<P, V>(a, t + stride, own, oth, A);
+            compute(B);
+            t += stride;
+            if (t >= n_items) break;
         }
     }
     write_partials<C, MEAS>(a, accE, accX, accY, accZ, nacc);
@@ -635,8 +727,12 @@ __global__ void __launch_bounds__(kBlock) table_pass_kernel(const PassArgs a) {
         S4 s = spins[i];
         C sx = to_c(s.v[0]), sy = to_c(s.v[1]), sz = to_c(s.v[2]);
         C tx, ty, tz, u;
-        draw_trial<P>(__ldg(a.nat + i), a.sweep, (uint32_t)a.colour, a.replica, a.key0, a.key1, tx, ty, tz, u);
-        if (metropolis<C>(sx, sy, sz, tx, ty, tz, hx, hy, hz, J, K, ex, ey, ez, beta, u)) {
+        if constexpr (P == HS_FP64)
+            draw_trial<P>(__ldg(a.nat + i), a.sweep, (uint32_t)a.colour, a.replica, a.key0, a.key1, tx, ty, tz, u);
+        else
+            draw_trial_rank<P>((uint32_t)(i - a.colour_begin), a.sweep, (uint32_t)a.colour, a.replica, a.key0,
+                               a.key1, tx, ty, tz, u);
+        if (metropolis<C>(sx, sy, sz, tx, ty, tz, hx, hy, hz, J, K, ex, ey, ez, beta, u).acc) {
             sx = tx;
             sy = ty;
             sz = tz;
@@ -825,11 +921,18 @@ inline int grid_for(int64_t n, int cap = 152 * 16) {
 }
 
 template <int P, int V>
-cudaError_t launch_sc_v(const PassArgs &a, int n_blocks, cudaStream_t s, bool meas) {
-    if (meas)
-        sc_pass_kernel<P, V, true><<<n_blocks, kBlock, 0, s>>>(a);
-    else
-        sc_pass_kernel<P, V, false><<<n_blocks, kBlock, 0, s>>>(a);
+cudaError_t launch_sc_v(const PassArgs &a, int n_blocks, cudaStream_t s, bool meas, bool pf) {
+    if (pf) {
+        if (meas)
+            sc_pass_kernel<P, V, true, true><<<n_blocks, kBlock, 0, s>>>(a);
+        else
+            sc_pass_kernel<P, V, false, true><<<n_blocks, kBlock, 0, s>>>(a);
+    } else {
+        if (meas)
+            sc_pass_kernel<P, V, true, false><<<n_blocks, kBlock, 0, s>>>(a);
+        else
+            sc_pass_kernel<P, V, false, false><<<n_blocks, kBlock, 0, s>>>(a);
+    }
     return cudaGetLastError();
 }
 
@@ -858,10 +961,10 @@ cudaError_t launch_pass_p(const Layout &L, const PassArgs &a, int n_blocks, cuda
     }
     if (L.kernel == kStencil) {
         switch (L.vec) {
-        case 1: return launch_sc_v<P, 1>(a, n_blocks, s, meas);
-        case 2: return launch_sc_v<P, 2>(a, n_blocks, s, meas);
-        case 4: if constexpr (P != HS_FP64) return launch_sc_v<P, 4>(a, n_blocks, s, meas); break;
-        case 8: if constexpr (P == HS_FP16) return launch_sc_v<P, 8>(a, n_blocks, s, meas); break;
+        case 1: return launch_sc_v<P, 1>(a, n_blocks, s, meas, L.prefetch);
+        case 2: return launch_sc_v<P, 2>(a, n_blocks, s, meas, L.prefetch);
+        case 4: if constexpr (P != HS_FP64) return launch_sc_v<P, 4>(a, n_blocks, s, meas, L.prefetch); break;
+        case 8: if constexpr (P == HS_FP16) return launch_sc_v<P, 8>(a, n_blocks, s, meas, L.prefetch); break;
         default: break;
         }
         return cudaErrorInvalidValue;
@@ -935,19 +1038,23 @@ static int64_t pass_items(const Layout &L) {
     return items;
 }
 
+template <int P, int V>
+static const void *sc_ptr(bool meas, bool pf) {
+    if (pf) return meas ? (const void *)sc_pass_kernel<P, V, true, true> : (const void *)sc_pass_kernel<P, V, false, true>;
+    return meas ? (const void *)sc_pass_kernel<P, V, true, false> : (const void *)sc_pass_kernel<P, V, false, false>;
+}
+
 template <int P>
 static const void *pass_kernel_ptr(const Layout &L, bool meas) {
     if (L.kernel == kStencil) {
         switch (L.vec) {
-        case 1: return meas ? (const void *)sc_pass_kernel<P, 1, true> : (const void *)sc_pass_kernel<P, 1, false>;
-        case 2: return meas ? (const void *)sc_pass_kernel<P, 2, true> : (const void *)sc_pass_kernel<P, 2, false>;
+        case 1: return sc_ptr<P, 1>(meas, L.prefetch);
+        case 2: return sc_ptr<P, 2>(meas, L.prefetch);
         case 4:
-            if constexpr (P != HS_FP64)
-                return meas ? (const void *)sc_pass_kernel<P, 4, true> : (const void *)sc_pass_kernel<P, 4, false>;
+            if constexpr (P != HS_FP64) return sc_ptr<P, 4>(meas, L.prefetch);
             break;
         case 8:
-            if constexpr (P == HS_FP16)
-                return meas ? (const void *)sc_pass_kernel<P, 8, true> : (const void *)sc_pass_kernel<P, 8, false>;
+            if constexpr (P == HS_FP16) return sc_ptr<P, 8>(meas, L.prefetch);
             break;
         default: break;
         }

@@ -230,7 +230,9 @@ def _launch_configs(precision, dims):
     for v in widths:
         if lh % v:
             continue
-        out += [dict(kernel="stencil", vec_width=v, blocks_per_sm=1), dict(kernel="stencil", vec_width=v)]
+        out += [dict(kernel="stencil", vec_width=v, blocks_per_sm=1), dict(kernel="stencil", vec_width=v),
+                dict(kernel="stencil", vec_width=v, prefetch=1), dict(kernel="stencil", vec_width=v, prefetch=1,
+                                                                       blocks_per_sm=1)]
         if (lh * es) % 16 == 0:
             for ty in (1, 2, 4):
                 if dims[1] % ty == 0:

@@ -313,3 +313,18 @@ def test_low_and_high_temperature_limits(orc):
                     observe=lambda S: orc.measure(g, S, J=1.0, K=0.1, e=e)["M2"])
     # high T: M^2 of order 1/N (weakly enhanced by the residual coupling)
     assert np.mean(obs[50:]) < 2.0 / g.n
+
+
+@pytest.mark.parametrize("kind,dims", [("sc", (8, 6, 4)), ("fcc", (3, 3, 2))])
+def test_fp32_schedule_gives_every_site_its_own_numbers(orc, kind, dims):
+    """The FP32 schedule shares a Philox block between two sites of a colour
+    (rank >> 1, halves rank & 1): no two sites may receive the same trial."""
+    g = orc.lattice(kind, dims)
+    S = orc.init_spins(g, seed=4)
+    acc, _, _ = orc.sweep(g, S, J=1.0, K=0.0, e=(0, 0, 1), beta=0.0, seed=4, sweep_index=2, mode=1)
+    assert acc == g.n
+    assert len(np.unique(S, axis=0)) == g.n
+    # and a second sweep draws fresh numbers
+    S2 = S.copy()
+    orc.sweep(g, S2, J=1.0, K=0.0, e=(0, 0, 1), beta=0.0, seed=4, sweep_index=3, mode=1)
+    assert not np.any(np.all(S2 == S, axis=1))
