@@ -253,11 +253,19 @@ int hs_autotune(hs_lattice *h, double beta, int n_trial_sweeps);
 int hs_colour_greedy(int64_t n, const int64_t *row_ptr, const int32_t *col_idx,
                      const uint8_t *site_mask, int32_t *colour_out, int *n_colours);
 
-/* Batched replicas: many independent lattices (FP32 periodic sc, any even L)
- * advanced by one persistent kernel, each at its own beta.  Members stay
- * owned by the caller and must outlive the batch; all must share one
- * stream.  hs_batch_run performs n_equil sweeps without and then n_sweeps
- * sweeps with accumulation into each member's accumulator. */
+/* Batched replicas: many independent lattices advanced together by one
+ * persistent kernel (cooperative launch, captured once in a CUDA graph per
+ * (n_sweeps, n_equil) pair), each member at its own beta, with its own seed,
+ * replica, sweep counter and accumulator.  Members must be FP32 unmasked
+ * periodic sc lattices with Lx divisible by 8 (any sizes, mixed), created on
+ * one stream and device; they stay owned by the caller and must outlive the
+ * batch.  hs_batch_run performs n_equil sweeps, then n_sweeps sweeps whose
+ * moments are added to each member's accumulator (as hs_sweep with
+ * accumulation on would), with the same random numbers and arithmetic as
+ * hs_sweep on each member alone.  Colour passes are separated by a grid-wide
+ * barrier whose waits are bounded: a timeout is latched in every member and
+ * reported (HS_E_TIMEOUT) by the next synchronising call on a member.
+ * Asynchronous. */
 int hs_batch_create(hs_batch **out, hs_lattice *const *members, int n_members);
 int hs_batch_run(hs_batch *b, const double *betas, int64_t n_sweeps, int64_t n_equil);
 void hs_batch_destroy(hs_batch *b);

@@ -948,36 +948,193 @@ int hs_autotune(hs_lattice *h, double beta, int n_trial_sweeps) {
 // ---------------------------------------------------------------- batch
 struct hs_batch {
     std::vector<hs_lattice *> members;
+    cudaStream_t stream = nullptr;
+    int grid = 0, n_segs = 0;
+    std::vector<hs::BatchMember> host_members;
+    hs::BatchMember *d_members = nullptr;
+    hs::BatchSeg *d_segs = nullptr;
+    int *d_cta_seg = nullptr;
+    double *d_slots = nullptr;
+    unsigned int *d_bar = nullptr;
+    int *d_error = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int graph_total = -1, graph_equil = -1;
+    bool graph_failed = false;
+    ~hs_batch() {
+        cudaStreamSynchronize(stream);
+        if (exec) cudaGraphExecDestroy(exec);
+        if (cap_stream) cudaStreamDestroy(cap_stream);
+        cudaFree(d_members);
+        cudaFree(d_segs);
+        cudaFree(d_cta_seg);
+        cudaFree(d_slots);
+        cudaFree(d_bar);
+        cudaFree(d_error);
+    }
 };
+
+namespace {
+hs::BatchArgs batch_args(const hs_batch *b, int n_total, int n_equil) {
+    hs::BatchArgs a{};
+    a.members = b->d_members;
+    a.n_members = (int)b->members.size();
+    a.segs = b->d_segs;
+    a.cta_seg = b->d_cta_seg;
+    a.n_segs = b->n_segs;
+    a.slots = b->d_slots;
+    a.bar = b->d_bar;
+    a.error = b->d_error;
+    a.n_total = n_total;
+    a.n_equil = n_equil;
+    return a;
+}
+}  // namespace
 
 int hs_batch_create(hs_batch **out, hs_lattice *const *members, int n_members) {
     if (!out) return fail(HS_E_INVALID, "out is NULL");
     *out = nullptr;
     if (!members || n_members < 1) return fail(HS_E_INVALID, "need at least one member");
     for (int r = 0; r < n_members; ++r) {
-        if (!members[r]) return fail(HS_E_INVALID, "null member");
-        if (members[r]->stream != members[0]->stream) return fail(HS_E_INVALID, "members must share one stream");
+        const hs_lattice *h = members[r];
+        if (!h) return fail(HS_E_INVALID, "null member");
+        if (h->stream != members[0]->stream || h->device != members[0]->device)
+            return fail(HS_E_INVALID, "members must share one stream and device");
+        if (!h->L.structured || h->precision != HS_FP32 || h->L.Lh % 4 != 0)
+            return fail(HS_E_INVALID, "batch members must be FP32 unmasked periodic sc with Lx divisible by 8");
+        for (int q = 0; q < r; ++q)
+            if (members[q] == h) return fail(HS_E_INVALID, "a lattice appears twice in the batch");
     }
+    const int occ = hs::batch_occupancy();
+    if (occ < 1) return fail(HS_E_CUDA, "batch kernel does not fit on an SM");
     hs_batch *b = new (std::nothrow) hs_batch();
     if (!b) return fail(HS_E_OOM, "host allocation failed");
     b->members.assign(members, members + n_members);
+    b->stream = members[0]->stream;
+    b->grid = members[0]->n_sm * occ;
+    // items of all members, concatenated, cut into one equal chunk per CTA
+    std::vector<int64_t> items(n_members), offset(n_members + 1, 0);
+    for (int r = 0; r < n_members; ++r) {
+        const Layout &L = members[r]->L;
+        items[r] = (int64_t)L.Lz * L.Ly * (L.Lh / 4);
+        offset[r + 1] = offset[r] + items[r];
+    }
+    const int64_t total = offset[n_members];
+    const int64_t chunk = (total + b->grid - 1) / b->grid;
+    std::vector<hs::BatchSeg> segs;
+    std::vector<int> seg_cta;
+    b->host_members.resize(n_members);
+    for (int r = 0; r < n_members; ++r) {
+        hs::BatchMember &m = b->host_members[r];
+        const hs_lattice *h = members[r];
+        const Layout &L = h->L;
+        m.planes = static_cast<float *>(L.planes);
+        m.Lx = L.Lx;
+        m.Ly = L.Ly;
+        m.Lz = L.Lz;
+        m.Lh = L.Lh;
+        m.div_nxv = hs::FastDiv((uint32_t)(L.Lh / 4));
+        m.div_ly = hs::FastDiv((uint32_t)L.Ly);
+        m.fJ = (float)h->p.J;
+        m.fK = (float)h->p.K;
+        for (int q = 0; q < 3; ++q) {
+            m.fe[q] = (float)h->p.e[q];
+            m.e[q] = h->p.e[q];
+        }
+        m.key0 = (uint32_t)h->seed;
+        m.key1 = (uint32_t)(h->seed >> 32);
+        m.replica = h->replica;
+        m.n_present = (double)L.n_present;
+        m.acc = h->acc;
+        m.seg_begin = (int)segs.size();
+        for (int64_t g = offset[r]; g < offset[r + 1];) {
+            const int64_t cta = g / chunk;
+            const int64_t g_end = std::min(offset[r + 1], (cta + 1) * chunk);
+            segs.push_back({r, (uint32_t)(g - offset[r]), (uint32_t)(g_end - offset[r])});
+            seg_cta.push_back((int)cta);
+            g = g_end;
+        }
+        m.seg_end = (int)segs.size();
+    }
+    b->n_segs = (int)segs.size();
+    std::vector<int> cta_seg(b->grid + 1, 0);
+    for (int c : seg_cta) ++cta_seg[c + 1];
+    for (int c = 0; c < b->grid; ++c) cta_seg[c + 1] += cta_seg[c];
+    auto cleanup = [&](int code) {
+        delete b;
+        return code;
+    };
+    cudaError_t e;
+    if ((e = cudaMalloc(&b->d_members, sizeof(hs::BatchMember) * n_members)) != cudaSuccess ||
+        (e = cudaMalloc(&b->d_segs, sizeof(hs::BatchSeg) * segs.size())) != cudaSuccess ||
+        (e = cudaMalloc(&b->d_cta_seg, sizeof(int) * cta_seg.size())) != cudaSuccess ||
+        (e = cudaMalloc(&b->d_slots, sizeof(double) * 4 * segs.size() * hs::kPartials)) != cudaSuccess ||
+        (e = cudaMalloc(&b->d_bar, 2 * sizeof(unsigned int))) != cudaSuccess ||
+        (e = cudaMalloc(&b->d_error, sizeof(int))) != cudaSuccess)
+        return cleanup(cuda_fail(e, "cudaMalloc(batch)"));
+    if ((e = cudaMemcpyAsync(b->d_segs, segs.data(), sizeof(hs::BatchSeg) * segs.size(), cudaMemcpyHostToDevice,
+                             b->stream)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(b->d_cta_seg, cta_seg.data(), sizeof(int) * cta_seg.size(), cudaMemcpyHostToDevice,
+                             b->stream)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(b->stream)) != cudaSuccess)
+        return cleanup(cuda_fail(e, "batch upload"));
+    if ((e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
+        return cleanup(cuda_fail(e, "cudaStreamCreate"));
     *out = b;
     return HS_OK;
 }
 
 int hs_batch_run(hs_batch *b, const double *betas, int64_t n_sweeps, int64_t n_equil) {
     if (!b || !betas) return fail(HS_E_INVALID, "null argument");
-    if (n_sweeps < 0 || n_equil < 0) return fail(HS_E_INVALID, "sweep counts must be >= 0");
-    for (size_t r = 0; r < b->members.size(); ++r) {
+    if (n_sweeps < 0 || n_equil < 0 || n_sweeps + n_equil > (int64_t)1 << 30)
+        return fail(HS_E_INVALID, "sweep counts must be >= 0 and below 2^30");
+    const int n = (int)b->members.size();
+    for (int r = 0; r < n; ++r)
+        if (!(betas[r] >= 0.0) || !std::isfinite(betas[r])) return fail(HS_E_INVALID, "betas must be finite, >= 0");
+    const int n_total = (int)(n_sweeps + n_equil), n_eq = (int)n_equil;
+    for (int r = 0; r < n; ++r) {
         hs_lattice *h = b->members[r];
-        const int keep = h->accumulate;
-        h->accumulate = 0;
-        int st = hs_sweep(h, betas[r], n_equil);
-        h->accumulate = 1;
-        if (st == HS_OK) st = hs_sweep(h, betas[r], n_sweeps);
-        h->accumulate = keep;
-        if (st) return st;
+        b->host_members[r].fbeta = (float)betas[r];
+        b->host_members[r].sweep0 = (uint32_t)h->sweep;
+        h->last_n_sweeps = n_total;
+        HS_CUDA(cudaMemsetAsync(&h->acc->accepted, 0, sizeof(double), b->stream));
     }
+    if (n_total == 0) return HS_OK;
+    HS_CUDA(cudaMemcpyAsync(b->d_members, b->host_members.data(), sizeof(hs::BatchMember) * n,
+                            cudaMemcpyHostToDevice, b->stream));
+    HS_CUDA(cudaMemsetAsync(b->d_bar, 0, 2 * sizeof(unsigned int), b->stream));
+    HS_CUDA(cudaMemsetAsync(b->d_error, 0, sizeof(int), b->stream));
+    const hs::BatchArgs args = batch_args(b, n_total, n_eq);
+    // the persistent kernel runs as one node of a CUDA graph, captured once per
+    // (sweeps, equilibration) pair; without graph support it is launched directly
+    if (!b->graph_failed && (b->graph_total != n_total || b->graph_equil != n_eq || !b->exec)) {
+        if (b->exec) {
+            cudaGraphExecDestroy(b->exec);
+            b->exec = nullptr;
+        }
+        cudaGraph_t graph = nullptr;
+        bool ok = cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+        if (ok) {
+            const cudaError_t le = hs::launch_batch(args, b->grid, b->cap_stream);
+            ok = (cudaStreamEndCapture(b->cap_stream, &graph) == cudaSuccess) && le == cudaSuccess;
+        }
+        if (ok) ok = cudaGraphInstantiate(&b->exec, graph, 0) == cudaSuccess;
+        if (graph) cudaGraphDestroy(graph);
+        if (!ok) {
+            cudaGetLastError();
+            b->exec = nullptr;
+            b->graph_failed = true;
+        } else {
+            b->graph_total = n_total;
+            b->graph_equil = n_eq;
+        }
+    }
+    if (b->exec) {
+        HS_CUDA(cudaGraphLaunch(b->exec, b->stream));
+    } else {
+        HS_CUDA(hs::launch_batch(args, b->grid, b->stream));
+    }
+    for (int r = 0; r < n; ++r) b->members[r]->sweep += (uint64_t)n_total;
     return HS_OK;
 }
 

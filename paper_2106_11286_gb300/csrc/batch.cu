@@ -1,0 +1,203 @@
+// Batched replicas in one persistent kernel: many FP32 periodic sc lattices of
+// uneven size, each at its own beta, advanced sweep by sweep (Metropolis
+// steps (i)-(iii) of arXiv 2106.11286, colour class by colour class) with the
+// E / M moments of Eq. 1 / Eq. 2 accumulated per member in FP64.
+//
+// Work split: the members' items (4 sites of a row of one colour) are
+// concatenated and cut into equal contiguous chunks, one per CTA; a chunk may
+// cover several members, and each (CTA, member) piece is a segment with its
+// own FP64 reduction slot, so the per-member sums are taken in a fixed order
+// (bit-reproducible).  Colour passes are separated by a grid barrier (the
+// launch is cooperative, so every CTA is resident); every wait on it is
+// bounded and a timeout latches an error word that the host reports.  Data
+// written by other CTAs in the same launch is read L2-only.
+#include <cuda_runtime.h>
+
+#include "device.cuh"
+
+namespace hs {
+namespace {
+
+constexpr long long kBarrierCycles = 2000000000LL;  // about one second
+
+// Grid-wide barrier: generation read before arriving; the last arriver resets
+// the count and bumps the generation.  Bounded spin; returns false (and
+// latches the error word) if the generation does not change in time.
+__device__ bool grid_barrier(unsigned int *bar, unsigned int n_ctas, int *error) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        volatile unsigned int *gen = bar + 1;
+        const unsigned int g = *gen;
+        __threadfence();
+        if (atomicAdd(bar, 1u) == n_ctas - 1u) {
+            atomicExch(bar, 0u);
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            const long long t0 = clock64();
+            for (uint32_t it = 0; *gen == g; ++it) {
+                if (it > (1u << 30) || clock64() - t0 > kBarrierCycles) {
+                    ok = 0;
+                    atomicExch(error, 1);
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+__device__ __forceinline__ PassArgs member_args(const BatchMember &m, int colour, uint32_t sweep) {
+    PassArgs a{};
+    a.Lx = m.Lx;
+    a.Ly = m.Ly;
+    a.Lz = m.Lz;
+    a.Lh = m.Lh;
+    a.div_nxv = m.div_nxv;
+    a.div_ly = m.div_ly;
+    a.colour = colour;
+    a.fJ = m.fJ;
+    a.fK = m.fK;
+    a.fe[0] = m.fe[0];
+    a.fe[1] = m.fe[1];
+    a.fe[2] = m.fe[2];
+    a.fbeta = m.fbeta;
+    a.key0 = m.key0;
+    a.key1 = m.key1;
+    a.replica = m.replica;
+    a.sweep = sweep;
+    return a;
+}
+
+__global__ void __launch_bounds__(kBlock, 2) batch_kernel(const BatchArgs b) {
+    constexpr int P = HS_FP32;
+    constexpr int V = 4;
+    using VT = Vec<float, V>;
+    __shared__ double s_red[kBlock / 32][kPartials];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int s = 0; s < b.n_total; ++s) {
+        const int par = s & 1;
+        for (int c = 0; c < 2; ++c) {
+            for (int si = b.cta_seg[blockIdx.x]; si < b.cta_seg[blockIdx.x + 1]; ++si) {
+                const BatchSeg sg = b.segs[si];
+                const BatchMember &m = b.members[sg.member];
+                const PassArgs a = member_args(m, c, m.sweep0 + (uint32_t)s);
+                const size_t plane = (size_t)m.Lz * m.Ly * m.Lh;
+                float *own_w[3];
+                const float *own[3], *oth[3];
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    own_w[q] = m.planes + (size_t)(3 * c + q) * plane;
+                    own[q] = own_w[q];
+                    oth[q] = m.planes + (size_t)(3 * (1 - c) + q) * plane;
+                }
+                float J, K, ex, ey, ez, beta;
+                load_params(a, J, K, ex, ey, ez, beta);
+                float accE = 0.f, accX = 0.f, accY = 0.f, accZ = 0.f;
+                unsigned nacc = 0;
+                for (uint32_t t = sg.begin + threadIdx.x; t < sg.end; t += kBlock) {
+                    StencilItem<P, V> it;
+                    load_item<P, V, true>(a, t, own, oth, it);
+                    if (update_item<P, V, true>(it.s, it.o, it.nym, it.nyp, it.nzm, it.nzp, it.ed, it.p, it.site0, c,
+                                                a, J, K, ex, ey, ez, beta, accE, accX, accY, accZ, nacc)) {
+#pragma unroll
+                        for (int q = 0; q < 3; ++q) *reinterpret_cast<VT *>(own_w[q] + it.b0) = it.s[q];
+                    }
+                }
+                // segment partials: warp shuffle -> CTA (FP64) -> slot
+                accE = warp_sum(accE);
+                accX = warp_sum(accX);
+                accY = warp_sum(accY);
+                accZ = warp_sum(accZ);
+                nacc = __reduce_add_sync(0xffffffffu, nacc);
+                if (lane == 0) {
+                    s_red[warp][0] = accE;
+                    s_red[warp][1] = accX;
+                    s_red[warp][2] = accY;
+                    s_red[warp][3] = accZ;
+                    s_red[warp][4] = (double)nacc;
+                }
+                __syncthreads();
+                if (threadIdx.x < kPartials) {
+                    double t = 0.0;
+                    for (int w = 0; w < kBlock / 32; ++w) t += s_red[w][threadIdx.x];
+                    b.slots[(((size_t)par * 2 + c) * b.n_segs + si) * kPartials + threadIdx.x] = t;
+                }
+                __syncthreads();
+            }
+            if (!grid_barrier(b.bar, gridDim.x, b.error)) {  // uniform per CTA
+                if (threadIdx.x == 0)
+                    for (int r = 0; r < b.n_members; ++r) atomicExch(&b.members[r].acc->error, 1);
+                return;
+            }
+        }
+        // finalise this sweep for the members this CTA owns (reads parity par;
+        // the next sweep writes the other parity)
+        if (threadIdx.x == 0) {
+            for (int r = blockIdx.x; r < b.n_members; r += gridDim.x) {
+                const BatchMember &m = b.members[r];
+                double tot[kPartials] = {0.0, 0.0, 0.0, 0.0, 0.0};
+                for (int c = 0; c < 2; ++c)
+                    for (int si = m.seg_begin; si < m.seg_end; ++si)
+                        for (int q = 0; q < kPartials; ++q)
+                            tot[q] += __ldcg(b.slots + (((size_t)par * 2 + c) * b.n_segs + si) * kPartials + q);
+                DevAccum *A = m.acc;
+                A->accepted += tot[4];
+                const double mx = tot[1] / m.n_present, my = tot[2] / m.n_present, mz = tot[3] / m.n_present;
+                const double m2 = mx * mx + my * my + mz * mz;
+                const double am = sqrt(m2);
+                const double me = fabs(mx * m.e[0] + my * m.e[1] + mz * m.e[2]);
+                A->last[0] = tot[0];
+                A->last[1] = mx;
+                A->last[2] = my;
+                A->last[3] = mz;
+                A->last[4] = am;
+                A->last[5] = m2;
+                A->last[6] = m2 * m2;
+                A->last[7] = me;
+                if (s >= b.n_equil) {
+                    A->moments[HS_SUM_E] += tot[0];
+                    A->moments[HS_SUM_E2] += tot[0] * tot[0];
+                    A->moments[HS_SUM_ABSM] += am;
+                    A->moments[HS_SUM_M2] += m2;
+                    A->moments[HS_SUM_M4] += m2 * m2;
+                    A->moments[HS_SUM_MX] += mx;
+                    A->moments[HS_SUM_MY] += my;
+                    A->moments[HS_SUM_MZ] += mz;
+                    A->moments[HS_SUM_ABSME] += me;
+                    A->count += 1.0;
+                }
+            }
+        }
+    }
+}
+
+}  // namespace
+
+int batch_occupancy() {
+    int blocks = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, batch_kernel, kBlock, 0) != cudaSuccess) return 0;
+    return blocks;
+}
+
+cudaError_t launch_batch(const BatchArgs &b, int grid, cudaStream_t s) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(kBlock);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, batch_kernel, b);
+}
+
+}  // namespace hs

@@ -1,0 +1,476 @@
+// Device building blocks shared by the colour-pass kernels (kernels.cu) and
+// the batched persistent kernel (batch.cu): Philox4x32-10, the trial
+// orientation, the Metropolis test of Eq. 1, the fused reductions and the
+// stencil work item.  Internal to the library.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <stdint.h>
+#include <string.h>
+
+#include "hs_impl.h"
+
+namespace hs {
+namespace {
+
+
+// ----------------------------------------------------------------- Philox
+// Philox4x32-10 as published (Salmon et al., SC'11): ten rounds of two
+// 32x32->64 multiplies with fixed odd multipliers, a cross-lane swap of the
+// high halves xored with the round key, and a Weyl key schedule.
+constexpr uint32_t kMulA = 0xD2511F53u;
+constexpr uint32_t kMulB = 0xCD9E8D57u;
+constexpr uint32_t kWeylA = 0x9E3779B9u;
+constexpr uint32_t kWeylB = 0xBB67AE85u;
+
+__device__ __forceinline__ uint4 philox10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint64_t pa = (uint64_t)kMulA * c.x;  // one 32x32->64 multiply per lane pair
+        const uint64_t pb = (uint64_t)kMulB * c.z;
+        c = make_uint4((uint32_t)(pb >> 32) ^ c.y ^ k0, (uint32_t)pb, (uint32_t)(pa >> 32) ^ c.w ^ k1, (uint32_t)pa);
+        k0 += kWeylA;
+        k1 += kWeylB;
+    }
+    return c;
+}
+
+constexpr uint32_t kTagTrial = 0u;
+constexpr uint32_t kTagInit = 1u;
+
+// ----------------------------------------------------------------- precision
+template <int P> struct Tr;
+template <> struct Tr<HS_FP64> { using S = double; using C = double; };
+template <> struct Tr<HS_FP32> { using S = float; using C = float; };
+template <> struct Tr<HS_FP16> { using S = __half; using C = float; };
+
+__device__ __forceinline__ double to_c(double v) { return v; }
+__device__ __forceinline__ float to_c(float v) { return v; }
+__device__ __forceinline__ float to_c(__half v) { return __half2float(v); }
+
+template <typename S> __device__ __forceinline__ S store_from_double(double v);
+template <> __device__ __forceinline__ double store_from_double<double>(double v) { return v; }
+template <> __device__ __forceinline__ float store_from_double<float>(double v) { return __double2float_rn(v); }
+template <> __device__ __forceinline__ __half store_from_double<__half>(double v) { return __double2half(v); }
+
+template <typename T, int V>
+struct alignas(sizeof(T) * V) Vec {
+    T v[V];
+};
+
+// Uniform point on the sphere in FP64 from one Philox block (words 0,1 -> u_z,
+// words 2,3 -> u_phi, 53 bits each): z = 2u_z - 1 and v = 2u_phi - 1 are
+// formed exactly from the integers, r = sqrt((1-z)(1+z)) is correctly
+// rounded, phi = pi v.
+__device__ __forceinline__ void sphere_fp64(uint4 w, double &x, double &y, double &z) {
+    const int64_t two52 = int64_t(1) << 52;
+    const int64_t iz = (int64_t)((((uint64_t)(w.x >> 5)) << 26) | (uint64_t)(w.y >> 6));
+    const int64_t iv = (int64_t)((((uint64_t)(w.z >> 5)) << 26) | (uint64_t)(w.w >> 6));
+    z = (double)(iz - two52) * 0x1p-52;
+    const double v = (double)(iv - two52) * 0x1p-52;
+    const double r = sqrt((1.0 - z) * (1.0 + z));
+    double sn, cs;
+    sincospi(v, &sn, &cs);
+    x = r * cs;
+    y = r * sn;
+}
+
+// Trial orientation and acceptance uniform of one site (Metropolis step (ii)).
+template <int P>
+__device__ __forceinline__ void draw_trial(uint32_t site, uint32_t sweep, uint32_t colour, uint32_t replica,
+                                           uint32_t k0, uint32_t k1, typename Tr<P>::C &tx,
+                                           typename Tr<P>::C &ty, typename Tr<P>::C &tz,
+                                           typename Tr<P>::C &u);
+
+template <>
+__device__ __forceinline__ void draw_trial<HS_FP64>(uint32_t site, uint32_t sweep, uint32_t colour,
+                                                    uint32_t replica, uint32_t k0, uint32_t k1, double &tx,
+                                                    double &ty, double &tz, double &u) {
+    const uint32_t w2 = (kTagTrial << 24) | (colour << 8);
+    const uint4 a = philox10(make_uint4(site, sweep, w2, replica), k0, k1);
+    const uint4 b = philox10(make_uint4(site, sweep, w2 | 1u, replica), k0, k1);
+    sphere_fp64(a, tx, ty, tz);
+    const uint64_t ip = (((uint64_t)(b.x >> 5)) << 26) | (uint64_t)(b.y >> 6);
+    u = (double)ip * 0x1p-53;
+}
+
+// FP32 trial: z and v = 2u - 1 exact from the 24-bit integers, r from the
+// hardware reciprocal square root (r = w / sqrt(w), w = (1-z)(1+z) >= 0), the
+// azimuth from the hardware sine / cosine on [-pi, pi) (absolute error about
+// 4e-7, far below what a 24-bit proposal resolves statistically).
+// FP32 schedule: one Philox block serves two sites of the same colour.  The
+// site of rank r within its colour class (ascending natural index) uses
+// block r >> 1 and the half r & 1: words (a, b) = (x, y) or (z, w).
+// u_z and u_phi are the top 21 bits of a and b, P the two low 11-bit fields
+// (22 bits).  z and v = 2u - 1 are exact from the integers; r from the
+// hardware reciprocal square root (r = w / sqrt(w), w = (1-z)(1+z) >= 0);
+// the azimuth from the hardware sine / cosine on [-pi, pi) (absolute error
+// about 4e-7, far below what a 21-bit proposal resolves statistically).
+__device__ __forceinline__ uint4 trial_block(uint32_t rank_pair, uint32_t sweep, uint32_t colour, uint32_t replica,
+                                             uint32_t k0, uint32_t k1) {
+    return philox10(make_uint4(rank_pair, sweep, (kTagTrial << 24) | (colour << 8), replica), k0, k1);
+}
+
+__device__ __forceinline__ void sphere_fp32(uint32_t wa, uint32_t wb, float &tx, float &ty, float &tz, float &u) {
+    tz = (float)((int)(wa >> 11) - (1 << 20)) * 0x1p-20f;
+    const float v = (float)((int)(wb >> 11) - (1 << 20)) * 0x1p-20f;
+    u = (float)(((wa & 0x7FFu) << 11) | (wb & 0x7FFu)) * 0x1p-22f;
+    const float w2 = (1.0f - tz) * (1.0f + tz);
+    const float r = (w2 > 0.0f) ? w2 * rsqrtf(w2) : 0.0f;
+    float sn, cs;
+    __sincosf(3.14159265358979f * v, &sn, &cs);
+    tx = r * cs;
+    ty = r * sn;
+}
+
+// Trial orientation and acceptance uniform from one half (wa, wb) of a block
+// (FP32 schedule).  FP16 storage additionally renormalises and rounds the
+// trial to binary16, and the rounded vector is the one tested and stored, so
+// the chain samples the stored state.
+template <int P>
+__device__ __forceinline__ void trial_from_half(uint32_t wa, uint32_t wb, float &tx, float &ty, float &tz, float &u) {
+    sphere_fp32(wa, wb, tx, ty, tz, u);
+    if constexpr (P == HS_FP16) {
+        const float inv = rsqrtf(tx * tx + ty * ty + tz * tz);
+        tx = __half2float(__float2half_rn(tx * inv));
+        ty = __half2float(__float2half_rn(ty * inv));
+        tz = __half2float(__float2half_rn(tz * inv));
+    }
+}
+
+// One site's trial, FP32 / FP16 schedule, from its rank in the colour class.
+template <int P>
+__device__ __forceinline__ void draw_trial_rank(uint32_t rank, uint32_t sweep, uint32_t colour, uint32_t replica,
+                                                uint32_t k0, uint32_t k1, float &tx, float &ty, float &tz, float &u) {
+    const uint4 w = trial_block(rank >> 1, sweep, colour, replica, k0, k1);
+    if (rank & 1u)
+        trial_from_half<P>(w.z, w.w, tx, ty, tz, u);
+    else
+        trial_from_half<P>(w.x, w.y, tx, ty, tz, u);
+}
+
+template <typename S, typename C> __device__ __forceinline__ S to_store(C v);
+template <> __device__ __forceinline__ double to_store<double, double>(double v) { return v; }
+template <> __device__ __forceinline__ float to_store<float, float>(float v) { return v; }
+template <> __device__ __forceinline__ __half to_store<__half, float>(float v) { return __float2half_rn(v); }
+
+__device__ __forceinline__ float exp_c(float x) { return __expf(x); }
+__device__ __forceinline__ double exp_c(double x) { return exp(x); }
+
+// Metropolis step (iii) for one site: dH of Eq. 1 restricted to the terms
+// that contain S_i, dH = J (S.h - S'.h) + K ((S.e)^2 - (S'.e)^2), then
+// dH <= 0 or P <= exp(-beta dH).  The dot products are returned for the
+// fused energy measurement.
+template <typename C>
+struct SiteDots {
+    C sh, th, se, pe;
+    bool acc;
+};
+
+template <typename C>
+__device__ __forceinline__ SiteDots<C> metropolis(C sx, C sy, C sz, C tx, C ty, C tz, C hx, C hy, C hz, C J, C K,
+                                                  C ex, C ey, C ez, C beta, C u) {
+    SiteDots<C> d;
+    d.sh = sx * hx + sy * hy + sz * hz;
+    d.th = tx * hx + ty * hy + tz * hz;
+    d.se = sx * ex + sy * ey + sz * ez;
+    d.pe = tx * ex + ty * ey + tz * ez;
+    const C dH = J * (d.sh - d.th) + K * ((d.se - d.pe) * (d.se + d.pe));
+    d.acc = (dH <= C(0)) || (u <= exp_c(-beta * dH));
+    return d;
+}
+
+__device__ __forceinline__ void load_params(const PassArgs &a, double &J, double &K, double &ex, double &ey,
+                                            double &ez, double &beta) {
+    J = a.J;
+    K = a.K;
+    ex = a.e[0];
+    ey = a.e[1];
+    ez = a.e[2];
+    beta = a.beta;
+}
+__device__ __forceinline__ void load_params(const PassArgs &a, float &J, float &K, float &ex, float &ey, float &ez,
+                                            float &beta) {
+    J = a.fJ;
+    K = a.fK;
+    ex = a.fe[0];
+    ey = a.fe[1];
+    ez = a.fe[2];
+    beta = a.fbeta;
+}
+
+// ----------------------------------------------------------------- reduction
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Finalise a sweep (or a standalone measurement): the last CTA to arrive sums
+// every CTA's slots of every pass in a fixed order, so the FP64 totals do not
+// depend on scheduling.
+__device__ void finish_reduction(const PassArgs &a, bool measured) {
+    __shared__ int s_last;
+    __shared__ double s_fin[kBlock / 32][kPartials];
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned ticket = atomicAdd(&a.acc->done, 1u);
+        s_last = (ticket == (unsigned)a.n_blocks - 1u);
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    double t[kPartials] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int p = 0; p < a.n_colours; ++p)
+        for (int b = threadIdx.x; b < a.n_blocks; b += kBlock) {
+            const double *slot = a.partials + ((size_t)p * a.n_blocks + b) * kPartials;
+#pragma unroll
+            for (int q = 0; q < kPartials; ++q) t[q] += __ldcg(slot + q);
+        }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < kPartials; ++q) t[q] = warp_sum(t[q]);
+    if (lane == 0)
+#pragma unroll
+        for (int q = 0; q < kPartials; ++q) s_fin[warp][q] = t[q];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double tot[kPartials] = {0.0, 0.0, 0.0, 0.0, 0.0};
+        for (int w = 0; w < kBlock / 32; ++w)
+#pragma unroll
+            for (int q = 0; q < kPartials; ++q) tot[q] += s_fin[w][q];
+        DevAccum *A = a.acc;
+        A->accepted += tot[4];
+        if (measured) {
+            // Eq. 2 with |S| = 1: M = sum S / N
+            const double E = tot[0];
+            const double mx = tot[1] / a.n_present;
+            const double my = tot[2] / a.n_present;
+            const double mz = tot[3] / a.n_present;
+            const double m2 = mx * mx + my * my + mz * mz;
+            const double am = sqrt(m2);
+            const double me = fabs(mx * a.e[0] + my * a.e[1] + mz * a.e[2]);
+            A->last[0] = E;
+            A->last[1] = mx;
+            A->last[2] = my;
+            A->last[3] = mz;
+            A->last[4] = am;
+            A->last[5] = m2;
+            A->last[6] = m2 * m2;
+            A->last[7] = me;
+            if (a.accumulate) {
+                A->moments[HS_SUM_E] += E;
+                A->moments[HS_SUM_E2] += E * E;
+                A->moments[HS_SUM_ABSM] += am;
+                A->moments[HS_SUM_M2] += m2;
+                A->moments[HS_SUM_M4] += m2 * m2;
+                A->moments[HS_SUM_MX] += mx;
+                A->moments[HS_SUM_MY] += my;
+                A->moments[HS_SUM_MZ] += mz;
+                A->moments[HS_SUM_ABSME] += me;
+                A->count += 1.0;
+            }
+        }
+        A->done = 0u;
+    }
+}
+
+template <typename C, bool MEAS>
+__device__ __forceinline__ void write_partials(const PassArgs &a, C e, C x, C y, C z, unsigned nacc) {
+    __shared__ double s_w[kBlock / 32][kPartials];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (MEAS) {
+        e = warp_sum(e);
+        x = warp_sum(x);
+        y = warp_sum(y);
+        z = warp_sum(z);
+    }
+    nacc = __reduce_add_sync(0xffffffffu, nacc);
+    if (lane == 0) {
+        s_w[warp][0] = MEAS ? (double)e : 0.0;
+        s_w[warp][1] = MEAS ? (double)x : 0.0;
+        s_w[warp][2] = MEAS ? (double)y : 0.0;
+        s_w[warp][3] = MEAS ? (double)z : 0.0;
+        s_w[warp][4] = (double)nacc;
+    }
+    __syncthreads();
+    if (threadIdx.x < kPartials) {
+        double s = 0.0;
+#pragma unroll
+        for (int w = 0; w < kBlock / 32; ++w) s += s_w[w][threadIdx.x];
+        a.partials[((size_t)a.pass * a.n_blocks + blockIdx.x) * kPartials + threadIdx.x] = s;
+    }
+    if (a.finish) finish_reduction(a, MEAS);
+}
+
+// ----------------------------------------------------------------- stencil pass
+// One colour pass of the periodic sc lattice in colour-major SoA layout.
+// Work item = V consecutive sites of one row of the updated colour.  Row
+// parity p = (y+z+c)&1 fixes where the x neighbours sit in the other colour's
+// row: p = 0 -> (xh-1, xh), p = 1 -> (xh, xh+1); the +-y and +-z neighbours
+// sit at the same xh in the adjacent rows.  Neighbour order of the local
+// field sum: -x, +x, -y, +y, -z, +z.
+
+// Metropolis steps (ii)-(iii) for the V sites of one work item, given the
+// item's own spins s, the other colour's same row o (+ the edge element ed
+// beyond it), and the other colour's rows at y-1, y+1, z-1, z+1.  Updates s
+// in place; returns whether any site was accepted.
+template <int P, int V, bool MEAS>
+__device__ __forceinline__ bool update_item(Vec<typename Tr<P>::S, V> (&s)[3], const Vec<typename Tr<P>::S, V> (&o)[3],
+                                            const Vec<typename Tr<P>::S, V> (&nym)[3],
+                                            const Vec<typename Tr<P>::S, V> (&nyp)[3],
+                                            const Vec<typename Tr<P>::S, V> (&nzm)[3],
+                                            const Vec<typename Tr<P>::S, V> (&nzp)[3], const typename Tr<P>::C (&ed)[3],
+                                            uint32_t p, uint32_t site0, int c, const PassArgs &a,
+                                            typename Tr<P>::C J, typename Tr<P>::C K, typename Tr<P>::C ex,
+                                            typename Tr<P>::C ey, typename Tr<P>::C ez, typename Tr<P>::C beta,
+                                            typename Tr<P>::C &accE, typename Tr<P>::C &accX,
+                                            typename Tr<P>::C &accY, typename Tr<P>::C &accZ, unsigned &nacc) {
+    using S = typename Tr<P>::S;
+    using C = typename Tr<P>::C;
+    bool any = false;
+    // Metropolis steps (ii)-(iii) for site k with trial (tx, ty, tz), uniform u
+    auto site = [&](int k, C tx, C ty, C tz, C u) {
+        C h[3];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            const C xm = p ? to_c(o[q].v[k]) : (k == 0 ? ed[q] : to_c(o[q].v[k - 1]));
+            const C xp = p ? (k == V - 1 ? ed[q] : to_c(o[q].v[k + 1])) : to_c(o[q].v[k]);
+            h[q] = ((((xm + xp) + to_c(nym[q].v[k])) + to_c(nyp[q].v[k])) + to_c(nzm[q].v[k])) + to_c(nzp[q].v[k]);
+        }
+        C sx = to_c(s[0].v[k]), sy = to_c(s[1].v[k]), sz = to_c(s[2].v[k]);
+        const SiteDots<C> d = metropolis<C>(sx, sy, sz, tx, ty, tz, h[0], h[1], h[2], J, K, ex, ey, ez, beta, u);
+        if (d.acc) {
+            sx = tx;
+            sy = ty;
+            sz = tz;
+            s[0].v[k] = to_store<S, C>(tx);
+            s[1].v[k] = to_store<S, C>(ty);
+            s[2].v[k] = to_store<S, C>(tz);
+            any = true;
+            ++nacc;
+        }
+        if (MEAS) {
+            // bond energy counted at the later colour's end: pass 1 owns
+            // every sc bond, pass 0 only the anisotropy term
+            const C e_new = d.acc ? d.pe : d.se;
+            C ei = -K * e_new * e_new;
+            if (c == 1) ei -= J * (d.acc ? d.th : d.sh);
+            accE += ei;
+            accX += sx;
+            accY += sy;
+            accZ += sz;
+        }
+    };
+    if constexpr (P == HS_FP64) {
+#pragma unroll
+        for (int k = 0; k < V; ++k) {
+            C tx, ty, tz, u;
+            draw_trial<P>(site0 + 2u * k, a.sweep, (uint32_t)c, a.replica, a.key0, a.key1, tx, ty, tz, u);
+            site(k, tx, ty, tz, u);
+        }
+    } else {
+        // ranks of the item's sites in their colour class: rank0 + k
+        const uint32_t rank0 = site0 >> 1;
+        if (V >= 2 && (rank0 & 1u) == 0u) {
+#pragma unroll
+            for (int j = 0; j < V / 2; ++j) {  // one Philox block per pair of sites
+                const uint4 w = trial_block((rank0 >> 1) + j, a.sweep, (uint32_t)c, a.replica, a.key0, a.key1);
+                float tx, ty, tz, u;
+                trial_from_half<P>(w.x, w.y, tx, ty, tz, u);
+                site(2 * j, tx, ty, tz, u);
+                trial_from_half<P>(w.z, w.w, tx, ty, tz, u);
+                site(2 * j + 1, tx, ty, tz, u);
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < V; ++k) {
+                float tx, ty, tz, u;
+                draw_trial_rank<P>(rank0 + k, a.sweep, (uint32_t)c, a.replica, a.key0, a.key1, tx, ty, tz, u);
+                site(k, tx, ty, tz, u);
+            }
+        }
+    }
+    return any;
+}
+
+// Vector load, optionally L2-only (ld.global.cg).  A kernel that reads data
+// other CTAs wrote earlier in the same launch must not be served from a
+// stale line of its SM's L1 (L1 is not coherent across SMs).
+template <typename T, bool CG>
+__device__ __forceinline__ T ld_val(const T *p) {
+    if constexpr (!CG) {
+        return *p;
+    } else {
+        T out;
+        if constexpr (sizeof(T) == 16) {
+            const uint4 v = __ldcg(reinterpret_cast<const uint4 *>(p));
+            memcpy(&out, &v, 16);
+        } else if constexpr (sizeof(T) == 8) {
+            const uint2 v = __ldcg(reinterpret_cast<const uint2 *>(p));
+            memcpy(&out, &v, 8);
+        } else if constexpr (sizeof(T) == 4) {
+            const unsigned int v = __ldcg(reinterpret_cast<const unsigned int *>(p));
+            memcpy(&out, &v, 4);
+        } else {
+            const unsigned short v = __ldcg(reinterpret_cast<const unsigned short *>(p));
+            memcpy(&out, &v, 2);
+        }
+        return out;
+    }
+}
+
+// Operands of one work item of the register stencil.
+template <int P, int V>
+struct StencilItem {
+    Vec<typename Tr<P>::S, V> s[3], o[3], nym[3], nyp[3], nzm[3], nzp[3];
+    typename Tr<P>::C ed[3];
+    uint32_t b0, p, site0;
+};
+
+template <int P, int V, bool CG = false>
+__device__ __forceinline__ void load_item(const PassArgs &a, uint32_t t, const typename Tr<P>::S *const (&own)[3],
+                                          const typename Tr<P>::S *const (&oth)[3], StencilItem<P, V> &it) {
+    using S = typename Tr<P>::S;
+    using VT = Vec<S, V>;
+    const uint32_t Lh = a.Lh, Ly = a.Ly, Lz = a.Lz, Lx = a.Lx;
+    const uint32_t nxv = Lh / V;
+    const uint32_t row = a.div_nxv.div(t);
+    const uint32_t xv = t - row * nxv;
+    const uint32_t z = a.div_ly.div(row);
+    const uint32_t y = row - z * Ly;
+    const uint32_t p = (y + z + (uint32_t)a.colour) & 1u;
+    const uint32_t xh0 = xv * V;
+    const uint32_t ym = (y == 0) ? Ly - 1 : y - 1;
+    const uint32_t yp = (y == Ly - 1) ? 0 : y + 1;
+    const uint32_t zm = (z == 0) ? Lz - 1 : z - 1;
+    const uint32_t zp = (z == Lz - 1) ? 0 : z + 1;
+    const uint32_t b0 = row * Lh + xh0;
+    const uint32_t bym = (z * Ly + ym) * Lh + xh0;
+    const uint32_t byp = (z * Ly + yp) * Lh + xh0;
+    const uint32_t bzm = (zm * Ly + y) * Lh + xh0;
+    const uint32_t bzp = (zp * Ly + y) * Lh + xh0;
+    const uint32_t bed = row * Lh + (p ? ((xh0 + V == Lh) ? 0 : xh0 + V) : ((xh0 == 0) ? Lh - 1 : xh0 - 1));
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        it.s[q] = ld_val<VT, CG>(reinterpret_cast<const VT *>(own[q] + b0));
+        it.o[q] = ld_val<VT, CG>(reinterpret_cast<const VT *>(oth[q] + b0));
+        it.nym[q] = ld_val<VT, CG>(reinterpret_cast<const VT *>(oth[q] + bym));
+        it.nyp[q] = ld_val<VT, CG>(reinterpret_cast<const VT *>(oth[q] + byp));
+        it.nzm[q] = ld_val<VT, CG>(reinterpret_cast<const VT *>(oth[q] + bzm));
+        it.nzp[q] = ld_val<VT, CG>(reinterpret_cast<const VT *>(oth[q] + bzp));
+        it.ed[q] = to_c(ld_val<S, CG>(oth[q] + bed));
+    }
+    it.b0 = b0;
+    it.p = p;
+    it.site0 = row * Lx + 2 * xh0 + p;
+}
+
+}  // namespace
+}  // namespace hs

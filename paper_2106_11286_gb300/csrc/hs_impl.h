@@ -29,9 +29,15 @@ constexpr int kBlock = 256;   // threads per CTA of the sweep kernels
 // by multiply-high and shift: with l = ceil(log2 d) and m = ceil(2^(31+l)/d)
 // (m < 2^32), floor(n m / 2^(31+l)) = floor(n / d) because the rounding
 // excess n (m - 2^(31+l)/d) / 2^(31+l) stays below 2^-l <= 1/d.
+#ifdef __CUDACC__
+#define HS_HOST_DEVICE __host__ __device__
+#else
+#define HS_HOST_DEVICE
+#endif
+
 struct FastDiv {
     uint32_t d, m, l;
-    FastDiv() : d(1), m(0), l(0) {}
+    HS_HOST_DEVICE FastDiv() : d(1), m(0), l(0) {}
     explicit FastDiv(uint32_t div) : d(div), l(0) {
         while ((1ull << l) < div) ++l;
         m = (l == 0) ? 0u : (uint32_t)(((1ull << (31 + l)) + div - 1) / div);
@@ -104,6 +110,42 @@ struct Layout {
     int64_t n_pad;
     int64_t colour_begin[65];  // renumbered colour ranges (n_colours + 1 entries)
 };
+
+// ---- batched persistent kernel (batch.cu)
+// One member lattice (FP32 periodic sc, stencil layout, vector width 4).
+struct BatchMember {
+    float *planes;
+    int Lx, Ly, Lz, Lh;
+    FastDiv div_nxv, div_ly;
+    float fJ, fK, fe[3], fbeta;
+    double e[3];
+    uint32_t key0, key1, replica;
+    uint32_t sweep0;        // the member's sweep index at batch sweep 0
+    double n_present;
+    DevAccum *acc;
+    int seg_begin, seg_end;  // the member's segments (contiguous)
+};
+
+// Item range [begin, end) of one member's colour pass processed by one CTA.
+struct BatchSeg {
+    int member;
+    uint32_t begin, end;
+};
+
+struct BatchArgs {
+    const BatchMember *members;
+    int n_members;
+    const BatchSeg *segs;
+    const int *cta_seg;      // CTA c owns segments [cta_seg[c], cta_seg[c+1])
+    int n_segs;
+    double *slots;           // [sweep parity][colour][segment][kPartials]
+    unsigned int *bar;       // grid barrier: [0] arrivals, [1] generation
+    int *error;              // latched device error (barrier timeout)
+    int n_total, n_equil;    // sweeps, of which the first n_equil unmeasured
+};
+
+cudaError_t launch_batch(const BatchArgs &b, int grid, cudaStream_t s);
+int batch_occupancy();
 
 size_t storage_size(int precision);
 

@@ -1,0 +1,123 @@
+"""Batched replicas (one persistent kernel for many lattices of uneven size).
+
+* The batch reproduces, member by member, what hs_sweep does on each lattice
+  alone: identical spins, moments within the FP32 partial-sum tolerance.
+* Physics: for K = 0 the Binder cumulant U4 = 1 - <M^4> / (3 <M^2>^2) of
+  Eq. 2's magnetisation crosses between sizes at T_c; the sc Heisenberg value
+  is T_c / J = 1.443 (the paper quotes 1.445).  The crossing of L = 32 and
+  L = 48 must lie within max(3 sigma, 0.01) of 1.443, sigma from a jackknife
+  over measurement blocks.
+"""
+import numpy as np
+import pytest
+
+from paper_2106_11286_gb300 import hs
+
+pytestmark = pytest.mark.gpu
+
+
+def _members(dims_list, betas, K=0.1, seed=11):
+    return [hs.Lattice("sc", dims=d, J=1.0, K=K, e=(0, 0, 1), precision="fp32", seed=seed, replica=r)
+            for r, d in enumerate(dims_list)]
+
+
+def test_batch_matches_individual_sweeps():
+    dims = [(16, 16, 16), (24, 24, 24), (8, 8, 8), (32, 16, 8), (40, 8, 12)]
+    betas = [0.6, 0.8, 1.0, 1.2, 0.9]
+    a = _members(dims, betas)
+    b = _members(dims, betas)
+    for x, y in zip(a, b):
+        x.init()
+        y.init()
+        x.accumulate(True)
+    batch = hs.hs_batch_create([m.h for m in a])
+    try:
+        for n_equil, n_sweeps in ((3, 5), (3, 5), (0, 4)):   # second call reuses the captured graph
+            for m in a:
+                m.reset_accumulator()
+            hs.hs_batch_run(batch, betas, n_sweeps, n_equil)
+            rates = []
+            for m, beta in zip(b, betas):
+                m.accumulate(False)
+                m.sweep(beta, n_equil)
+                r_eq = m.measure()["accept_rate"] if n_equil else 0.0
+                m.accumulate(True)
+                m.reset_accumulator()
+                m.sweep(beta, n_sweeps)
+                r_sw = m.measure()["accept_rate"]
+                rates.append((r_eq * n_equil + r_sw * n_sweeps) / (n_equil + n_sweeps))
+            for x, y, rate in zip(a, b, rates):
+                assert np.array_equal(x.get_spins(), y.get_spins())
+                mx, cx = x.read_accumulator()
+                my, cy = y.read_accumulator()
+                assert cx == cy == n_sweeps
+                np.testing.assert_allclose(mx, my, rtol=2e-6, atol=1e-9)
+                assert x.info.sweep == y.info.sweep
+                # a batch run's acceptance rate covers all of its sweeps
+                assert x.measure()["accept_rate"] == pytest.approx(rate, abs=1e-12)
+    finally:
+        hs.hs_batch_destroy(batch)
+        for m in a + b:
+            m.close()
+
+
+def test_batch_rejects_unsupported_members():
+    with hs.Lattice("sc", dims=(8, 8, 8), precision="fp64") as x:
+        with pytest.raises(hs.HSError):
+            hs.hs_batch_create([x.h])
+    with hs.Lattice("sc", dims=(12, 8, 8), precision="fp32") as x:   # Lx/2 = 6 not divisible by 4
+        with pytest.raises(hs.HSError):
+            hs.hs_batch_create([x.h])
+
+
+def _crossing(Ts, u_small, u_large):
+    d = u_large - u_small
+    idx = np.nonzero((d[:-1] > 0) & (d[1:] <= 0))[0]
+    if len(idx) == 0:
+        return np.nan
+    k = idx[0]
+    return Ts[k] + (Ts[k + 1] - Ts[k]) * d[k] / (d[k] - d[k + 1])
+
+
+def test_binder_crossing_locates_tc():
+    sizes = (32, 48)
+    Ts = np.linspace(1.41, 1.47, 7)
+    lats = []
+    for L in sizes:
+        for i, T in enumerate(Ts):
+            lats.append(hs.Lattice("sc", dims=(L, L, L), J=1.0, K=0.0, precision="fp32", seed=2024,
+                                   replica=1000 * L + i))
+    betas = [1.0 / T for L in sizes for T in Ts]
+    for m in lats:
+        m.init()
+    batch = hs.hs_batch_create([m.h for m in lats])
+    n_blocks, block = 24, 2500
+    m2 = np.zeros((n_blocks, len(lats)))
+    m4 = np.zeros((n_blocks, len(lats)))
+    try:
+        hs.hs_batch_run(batch, betas, 0, 5000)       # equilibrate
+        for k in range(n_blocks):
+            for m in lats:
+                m.reset_accumulator()
+            hs.hs_batch_run(batch, betas, block, 0)
+            for j, m in enumerate(lats):
+                mom, cnt = m.read_accumulator()
+                assert cnt == block
+                m2[k, j] = mom[3] / cnt
+                m4[k, j] = mom[4] / cnt
+    finally:
+        hs.hs_batch_destroy(batch)
+        for m in lats:
+            m.close()
+    nT = len(Ts)
+
+    def estimate(rows):
+        a2 = m2[rows].mean(0)
+        a4 = m4[rows].mean(0)
+        u = 1.0 - a4 / (3.0 * a2 ** 2)
+        return _crossing(Ts, u[:nT], u[nT:])
+    t_all = estimate(np.arange(n_blocks))
+    jack = np.array([estimate(np.delete(np.arange(n_blocks), k)) for k in range(n_blocks)])
+    assert np.isfinite(t_all) and np.isfinite(jack).all()
+    sigma = np.sqrt((n_blocks - 1) / n_blocks * ((jack - jack.mean()) ** 2).sum())
+    assert abs(t_all - 1.443) < max(3 * sigma, 0.01), (t_all, sigma)
