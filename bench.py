@@ -188,6 +188,9 @@ def run_ours(args):
     lat = hs.Lattice("sc", dims=(L, L, L), precision="fp32", **params)
     lat.init()
     lat.accumulate(True)
+    # project autotuner (restores the chain); off for profiling runs, which
+    # want a fixed launch sequence
+    launch = lat.launch if args.no_autotune else lat.autotune(beta, 3)
     lat.sweep(beta, args.warmup)
     lat.reset_accumulator()
     t0 = torch.cuda.Event(enable_timing=True)
@@ -215,7 +218,7 @@ def run_ours(args):
                 "frac": round(achieved_gbs / peaks["hbm_gbs"], 4), "traffic": traffic,
                 "peak_source": f"{peak_kind} copy bandwidth", "kernel": "sc_pass_kernel<fp32>",
                 "kernel_ms": round(kernel_ms, 5), "alg_bytes_per_launch": alg_bytes,
-                "frac_of_8TBs_nominal": round(achieved_gbs / 8000.0, 4)}
+                "frac_of_8TBs_nominal": round(achieved_gbs / 8000.0, 4), "launch": launch}
     physics = {"E_per_spin": mom[0] / count / N, "absM": mom[2] / count, "accept_rate": meas["accept_rate"],
                "sweeps_averaged": count}
     lat.close()
@@ -278,6 +281,8 @@ def run_ours(args):
                        "hs_read_accumulator to host; wall clock"}
         lat.close()
 
+    variants = None if args.no_variants else run_variants(args, rank, stream, barrier_sync, world, dev)
+
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
@@ -288,8 +293,107 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": round(tot_s * 1e3 / args.steps, 5), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": config_dict(args, world), "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-            "gpu_launches": int(2 * args.steps), "clocks": clk.summary(), "fp64": fp64, "physics": physics}
+            "gpu_launches": int(2 * args.steps), "clocks": clk.summary(), "fp64": fp64, "physics": physics,
+            "variants": variants}
     return line
+
+
+# ------------------------------------------------------------------ other forms of the metric
+BATCH_SIZES = (16, 24, 32, 48, 64, 96)
+
+
+def _timed(stream, fn):
+    import torch
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / 1e3
+
+
+def run_variants(args, rank, stream, barrier_sync, world, dev):
+    """The batched form, the 464^3 precision ladder and the bcc nanoparticle,
+    each timed on the device (attempts/ns), with its physics beside it."""
+    from paper_2106_11286_gb300 import hs, inputs
+    out = {}
+    peaks, _ = measured_peaks()
+    # (1) batched: 64 sc replicas, L = sizes[r mod 6], T_r = 1.30 + 0.30 r / 63, K = 0,
+    #     2000 sweeps (1000 equilibration + 1000 measured) in one persistent launch
+    lats = [hs.Lattice("sc", dims=(BATCH_SIZES[r % 6],) * 3, J=1.0, K=0.0, precision="fp32", seed=4,
+                       replica=64 * rank + r, stream=stream) for r in range(64)]
+    betas = [1.0 / (1.30 + 0.30 * r / 63) for r in range(64)]
+    for m in lats:
+        m.init()
+    batch = hs.hs_batch_create([m.h for m in lats])
+    hs.hs_batch_run(batch, betas, 5, 5)  # warm-up (captures a graph for these counts)
+    for m in lats:
+        m.reset_accumulator()
+    n_spins = sum(BATCH_SIZES[r % 6] ** 3 for r in range(64))
+    sec = _timed(stream, lambda: hs.hs_batch_run(batch, betas, args.batch_sweeps // 2, args.batch_sweeps // 2))
+    u4 = {}
+    for r, m in enumerate(lats):
+        mom, cnt = m.read_accumulator()
+        L = BATCH_SIZES[r % 6]
+        u4.setdefault(L, []).append((round(1.0 / betas[r], 4), round(1 - (mom[4] / cnt) / (3 * (mom[3] / cnt) ** 2), 4)))
+    hs.hs_batch_destroy(batch)
+    for m in lats:
+        m.close()
+    out["batched"] = {"value": round(n_spins * args.batch_sweeps / (sec * 1e9), 3), "unit": UNIT,
+                      "replicas": 64, "n_spins_total": n_spins, "sweeps": args.batch_sweeps,
+                      "hbm_frac": round(n_spins * args.batch_sweeps * 36 / sec / 1e9 / peaks["hbm_gbs"], 4),
+                      "what": "one persistent cooperative kernel (CUDA graph), FP32 spins, FP64 moments",
+                      "binder_u4": {str(L): v for L, v in u4.items()}}
+    # (2) sc 464^3, K = 0.1, T = 1.0, 200 sweeps: FP16 vs FP32 vs FP64 (bias against FP64)
+    L5 = 464
+    N5 = L5 ** 3
+    ladder = {}
+    for prec, sweeps in (("fp16", args.big_sweeps), ("fp32", args.big_sweeps), ("fp64", args.big_sweeps)):
+        lat = hs.Lattice("sc", dims=(L5,) * 3, J=1.0, K=0.1, e=(0, 0, 1), precision=prec, seed=5, replica=rank,
+                         stream=stream)
+        lat.init()
+        lat.accumulate(True)
+        lat.sweep(1.0, 3)
+        lat.reset_accumulator()
+        hs.hs_enable_timing(lat.h, True)
+        sec = _timed(stream, lambda: lat.sweep(1.0, sweeps))
+        kms, nl = hs.hs_read_timing(lat.h)
+        mom, cnt = lat.read_accumulator()
+        ladder[prec] = {"value": round(N5 * sweeps / (sec * 1e9), 3), "unit": UNIT, "sweeps": sweeps,
+                        "hbm_frac": round(3 * BYTES_PER_SPIN[prec] * (N5 // 2) / (kms / nl * 1e-3) / 1e9 /
+                                          peaks["hbm_gbs"], 4),
+                        "E_per_spin": mom[0] / cnt / N5, "absM": mom[2] / cnt}
+        lat.close()
+    for prec in ("fp16", "fp32"):
+        ladder[prec]["bias_E_per_spin_vs_fp64"] = ladder[prec]["E_per_spin"] - ladder["fp64"]["E_per_spin"]
+        ladder[prec]["bias_absM_vs_fp64"] = ladder[prec]["absM"] - ladder["fp64"]["absM"]
+    out["sc464"] = ladder
+    # (3) bcc nanoparticle: radius 110 in a 232^3-cell box, open surface, 1 % vacancies (seed 3),
+    #     CSR neighbour list, K = 0.2 along (1,1,1), T = 0.9, FP32
+    if not args.no_csr:
+        rp, col, mask = inputs.bcc_nanoparticle(radius=110, box=232, vacancy_fraction=0.01, seed=3)
+        lat = hs.Lattice("csr", row_ptr=rp, col_idx=col, site_mask=mask, J=1.0, K=0.2, e=(1, 1, 1),
+                         precision="fp32", seed=3, replica=rank, stream=stream)
+        n_present = lat.info.n_present
+        del rp, col
+        lat.init()
+        lat.accumulate(True)
+        lat.sweep(1 / 0.9, 3)
+        lat.reset_accumulator()
+        hs.hs_enable_timing(lat.h, True)
+        sec = _timed(stream, lambda: lat.sweep(1 / 0.9, args.csr_sweeps))
+        kms, nl = hs.hs_read_timing(lat.h)
+        mom, cnt = lat.read_accumulator()
+        per_attempt = 3 * 16 + 4 * 8 + 4   # 4-vector spins, 8 int32 neighbours, natural index
+        out["bcc_nanoparticle"] = {"value": round(n_present * args.csr_sweeps / (sec * 1e9), 3), "unit": UNIT,
+                                   "n_spins": n_present, "colours": lat.info.n_colours, "sweeps": args.csr_sweeps,
+                                   "hbm_frac": round(per_attempt * n_present / lat.info.n_colours / (kms / nl * 1e-3)
+                                                     / 1e9 / peaks["hbm_gbs"], 4),
+                                   "E_per_spin": mom[0] / cnt / n_present, "absM": mom[2] / cnt}
+        lat.close()
+    return out
 
 
 # ------------------------------------------------------------------ CPU oracle
@@ -359,6 +463,12 @@ def main(argv=None):
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--no-csr", action="store_true")
+    ap.add_argument("--batch-sweeps", type=int, default=2000)
+    ap.add_argument("--big-sweeps", type=int, default=200)
+    ap.add_argument("--csr-sweeps", type=int, default=500)
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
