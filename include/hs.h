@@ -231,6 +231,10 @@ typedef struct {
     int chunk_z;       /* staged: planes per CTA work unit */
     int prefetch;      /* stencil: 1 = issue the next work item's loads before
                           computing the current one, 2 = off, 0 = automatic */
+    int ring;          /* staged: shared-memory slots of the other colour's
+                          planes (4..8; the own colour gets ring - 2) */
+    int consumers;     /* staged: consumer warps per CTA, 4 or 8 (plus one
+                          producer warp) */
 } hs_launch;
 
 /* Set (fields 0 = automatic) or read the launch configuration.  The staged

@@ -245,6 +245,8 @@ PassArgs base_args(const hs_lattice *h) {
         a.ty = L.ty;
         a.zchunk = L.zchunk;
         a.n_units = L.n_units;
+        a.ring_o = L.ring_o;
+        a.ring_w = L.ring_w;
     }
     a.spins4 = L.spins4;
     a.nbr = L.nbr;
@@ -392,18 +394,23 @@ int configure_launch(hs_lattice *h) {
     if (kind == HS_KERNEL_AUTO) kind = HS_KERNEL_STENCIL;
     if (kind == HS_KERNEL_STAGED) {
         if (!staged_ok(h)) return fail(HS_E_INVALID, "staged kernel needs Lx/2 * storage bytes divisible by 16");
+        const int ring = r.ring ? r.ring : 5;
+        if (ring < 4 || ring > 8) return fail(HS_E_INVALID, "ring must be in [4, 8]");
+        const int consumers = r.consumers ? 32 * r.consumers : 128;
+        if (consumers != 128 && consumers != 256) return fail(HS_E_INVALID, "consumer warps must be 4 or 8");
         int ty = r.tile_y;
-        if (ty == 0) {
-            for (int c : {8, 4, 2, 1})
-                if (L.Ly % c == 0 && hs::staged_smem_bytes(h->precision, c, L.Lh) <= 110 * 1024) {
+        if (ty == 0) {  // smallest slab whose items fill the consumer warps
+            const int nxv = L.Lh / L.vec;
+            for (int c : {1, 2, 4, 8, 16})
+                if (L.Ly % c == 0 && c * nxv >= consumers) {
                     ty = c;
                     break;
                 }
-            if (ty == 0) ty = 1;
+            if (ty == 0) ty = L.Ly;
         }
         if (ty < 1 || L.Ly % ty != 0) return fail(HS_E_INVALID, "tile_y must divide Ly");
-        const size_t smem = hs::staged_smem_bytes(h->precision, ty, L.Lh);
-        const int occ = hs::staged_occupancy(h->precision, L.vec, smem);
+        const size_t smem = hs::staged_smem_bytes(h->precision, ty, L.Lh, ring, ring - 2);
+        const int occ = hs::staged_occupancy(h->precision, L.vec, smem, consumers);
         if (occ < 1) return fail(HS_E_INVALID, "staged slabs do not fit in shared memory");
         const int slots = h->n_sm * occ;
         const int n_yslab = L.Ly / ty;
@@ -416,6 +423,9 @@ int configure_launch(hs_lattice *h) {
         L.kernel = hs::kStaged;
         L.ty = ty;
         L.zchunk = zc;
+        L.ring_o = ring;
+        L.ring_w = ring - 2;
+        L.consumers = consumers;
         L.n_units = n_yslab * ((L.Lz + zc - 1) / zc);
         L.grid = std::min(L.n_units, slots);
         h->n_blocks = L.grid;
@@ -803,6 +813,9 @@ int hs_set_launch(hs_lattice *h, const hs_launch *cfg) {
         return fail(HS_E_INVALID, "blocks_per_sm out of range");
     if (cfg->tile_y < 0 || cfg->chunk_z < 0) return fail(HS_E_INVALID, "negative tile");
     if (cfg->prefetch < 0 || cfg->prefetch > 2) return fail(HS_E_INVALID, "prefetch must be 0, 1 or 2");
+    if (cfg->ring != 0 && (cfg->ring < 4 || cfg->ring > 8)) return fail(HS_E_INVALID, "ring must be 0 or in [4, 8]");
+    if (cfg->consumers != 0 && cfg->consumers != 4 && cfg->consumers != 8)
+        return fail(HS_E_INVALID, "consumer warps must be 0, 4 or 8");
     const hs_launch keep = h->req;
     const Layout keep_l = h->L;
     const int keep_b = h->n_blocks;
@@ -825,6 +838,8 @@ int hs_get_launch(const hs_lattice *h, hs_launch *out) {
     out->tile_y = L.kernel == hs::kStaged ? L.ty : 0;
     out->chunk_z = L.kernel == hs::kStaged ? L.zchunk : 0;
     out->prefetch = (L.kernel == hs::kStencil) ? (L.prefetch ? 1 : 2) : 0;
+    out->ring = L.kernel == hs::kStaged ? L.ring_o : 0;
+    out->consumers = L.kernel == hs::kStaged ? L.consumers / 32 : 0;
     return HS_OK;
 }
 
@@ -845,27 +860,31 @@ std::vector<hs_launch> tune_candidates(hs_lattice *h) {
     std::vector<hs_launch> out;
     const Layout &L = h->L;
     if (!L.structured) {
-        for (int b = 1; b <= 8; ++b) out.push_back({HS_KERNEL_TABLE, 1, b, 0, 0, 0});
+        for (int b = 1; b <= 8; ++b) out.push_back({HS_KERNEL_TABLE, 1, b, 0, 0, 0, 0, 0});
         return out;
     }
     for (int v : {1, 2, 4, 8}) {
         if (!vec_ok(h, v)) continue;
         for (int b = 1; b <= 8; ++b)
-            for (int pf : {1, 2}) out.push_back({HS_KERNEL_STENCIL, v, b, 0, 0, pf});
+            for (int pf : {1, 2}) out.push_back({HS_KERNEL_STENCIL, v, b, 0, 0, pf, 0, 0});
         if (!staged_ok(h)) continue;
-        for (int ty : {1, 2, 4, 8, 16}) {
-            if (L.Ly % ty != 0) continue;
-            const size_t smem = hs::staged_smem_bytes(h->precision, ty, L.Lh);
-            const int occ = hs::staged_occupancy(h->precision, v, smem);
-            if (occ < 1) continue;
-            const int slots = h->n_sm * occ;
-            const int n_yslab = L.Ly / ty;
-            const int n_chunks = std::max(1, slots / n_yslab);
-            const int zc = (L.Lz + n_chunks - 1) / n_chunks;
-            for (int f : {1, 2, 4}) {
-                const int z = std::max(1, zc / f);
-                if (f > 1 && z == zc) continue;
-                out.push_back({HS_KERNEL_STAGED, v, 0, ty, z, 0});
+        for (int cw : {4, 8}) {
+            for (int ty : {1, 2, 4, 8, 16}) {
+                if (L.Ly % ty != 0 || ty * (L.Lh / v) < 32 * cw) continue;
+                for (int ring : {4, 5, 6}) {
+                    const size_t smem = hs::staged_smem_bytes(h->precision, ty, L.Lh, ring, ring - 2);
+                    const int occ = hs::staged_occupancy(h->precision, v, smem, 32 * cw);
+                    if (occ < 1) continue;
+                    const int slots = h->n_sm * occ;
+                    const int n_yslab = L.Ly / ty;
+                    const int n_chunks = std::max(1, slots / n_yslab);
+                    const int zc = (L.Lz + n_chunks - 1) / n_chunks;
+                    for (int f : {1, 2}) {
+                        const int z = std::max(1, zc / f);
+                        if (f > 1 && z == zc) continue;
+                        out.push_back({HS_KERNEL_STAGED, v, 0, ty, z, 0, ring, cw});
+                    }
+                }
             }
         }
     }

@@ -99,23 +99,22 @@ __global__ void __launch_bounds__(kBlock, 2) batch_kernel(const BatchArgs b) {
                 }
                 float J, K, ex, ey, ez, beta;
                 load_params(a, J, K, ex, ey, ez, beta);
-                float accE = 0.f, accX = 0.f, accY = 0.f, accZ = 0.f;
-                unsigned nacc = 0;
+                SiteAcc<P> acc;
                 for (uint32_t t = sg.begin + threadIdx.x; t < sg.end; t += kBlock) {
                     StencilItem<P, V> it;
                     load_item<P, V, true>(a, t, own, oth, it);
                     if (update_item<P, V, true>(it.s, it.o, it.nym, it.nyp, it.nzm, it.nzp, it.ed, it.p, it.site0, c,
-                                                a, J, K, ex, ey, ez, beta, accE, accX, accY, accZ, nacc)) {
+                                                a, J, K, ex, ey, ez, beta, acc)) {
 #pragma unroll
                         for (int q = 0; q < 3; ++q) *reinterpret_cast<VT *>(own_w[q] + it.b0) = it.s[q];
                     }
                 }
                 // segment partials: warp shuffle -> CTA (FP64) -> slot
-                accE = warp_sum(accE);
-                accX = warp_sum(accX);
-                accY = warp_sum(accY);
-                accZ = warp_sum(accZ);
-                nacc = __reduce_add_sync(0xffffffffu, nacc);
+                const float accE = warp_sum(acc.E());
+                const float accX = warp_sum(acc.X());
+                const float accY = warp_sum(acc.Y());
+                const float accZ = warp_sum(acc.Z());
+                const unsigned nacc = __reduce_add_sync(0xffffffffu, acc.n);
                 if (lane == 0) {
                     s_red[warp][0] = accE;
                     s_red[warp][1] = accX;

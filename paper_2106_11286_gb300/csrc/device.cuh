@@ -94,47 +94,87 @@ __device__ __forceinline__ void draw_trial<HS_FP64>(uint32_t site, uint32_t swee
     u = (double)ip * 0x1p-53;
 }
 
-// FP32 trial: z and v = 2u - 1 exact from the 24-bit integers, r from the
-// hardware reciprocal square root (r = w / sqrt(w), w = (1-z)(1+z) >= 0), the
-// azimuth from the hardware sine / cosine on [-pi, pi) (absolute error about
-// 4e-7, far below what a 24-bit proposal resolves statistically).
+
+// ---- FP32 arithmetic of one site (float) or of the two sites of a Philox
+// pair (float2, packed sm_100+ instructions).  Every operation is rounded
+// explicitly and identically in both forms, so a site's result never depends
+// on whether it was processed alone or as a lane of a pair.
+__device__ __forceinline__ float f_add(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float f_sub(float a, float b) { return __fadd_rn(a, -b); }
+__device__ __forceinline__ float f_mul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float f_fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ float2 f_add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 f_sub(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+__device__ __forceinline__ float2 f_mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 f_fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+template <typename T> __device__ __forceinline__ T splat(float v);
+template <> __device__ __forceinline__ float splat<float>(float v) { return v; }
+template <> __device__ __forceinline__ float2 splat<float2>(float v) { return make_float2(v, v); }
+
+// 2^x from the hardware base-2 exponential (relative error about 2^-22).
+__device__ __forceinline__ float ex2_hw(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float ex2_l(float x) { return ex2_hw(x); }
+__device__ __forceinline__ float2 ex2_l(float2 x) { return make_float2(ex2_hw(x.x), ex2_hw(x.y)); }
+__device__ __forceinline__ float rsqrt_l(float x) { return rsqrtf(x); }
+__device__ __forceinline__ float2 rsqrt_l(float2 x) { return make_float2(rsqrtf(x.x), rsqrtf(x.y)); }
+__device__ __forceinline__ float pos_or_zero(float w, float r) { return w > 0.0f ? r : 0.0f; }
+__device__ __forceinline__ float2 pos_or_zero(float2 w, float2 r) {
+    return make_float2(w.x > 0.0f ? r.x : 0.0f, w.y > 0.0f ? r.y : 0.0f);
+}
+__device__ __forceinline__ void sincos_l(float a, float &s, float &c) { __sincosf(a, &s, &c); }
+__device__ __forceinline__ void sincos_l(float2 a, float2 &s, float2 &c) {
+    __sincosf(a.x, &s.x, &c.x);
+    __sincosf(a.y, &s.y, &c.y);
+}
+__device__ __forceinline__ float half_round(float x) { return __half2float(__float2half_rn(x)); }
+__device__ __forceinline__ float half_round_l(float x) { return half_round(x); }
+__device__ __forceinline__ float2 half_round_l(float2 x) { return make_float2(half_round(x.x), half_round(x.y)); }
+
 // FP32 schedule: one Philox block serves two sites of the same colour.  The
 // site of rank r within its colour class (ascending natural index) uses
 // block r >> 1 and the half r & 1: words (a, b) = (x, y) or (z, w).
 // u_z and u_phi are the top 21 bits of a and b, P the two low 11-bit fields
-// (22 bits).  z and v = 2u - 1 are exact from the integers; r from the
-// hardware reciprocal square root (r = w / sqrt(w), w = (1-z)(1+z) >= 0);
-// the azimuth from the hardware sine / cosine on [-pi, pi) (absolute error
-// about 4e-7, far below what a 21-bit proposal resolves statistically).
+// (22 bits).
 __device__ __forceinline__ uint4 trial_block(uint32_t rank_pair, uint32_t sweep, uint32_t colour, uint32_t replica,
                                              uint32_t k0, uint32_t k1) {
     return philox10(make_uint4(rank_pair, sweep, (kTagTrial << 24) | (colour << 8), replica), k0, k1);
 }
 
-__device__ __forceinline__ void sphere_fp32(uint32_t wa, uint32_t wb, float &tx, float &ty, float &tz, float &u) {
-    tz = (float)((int)(wa >> 11) - (1 << 20)) * 0x1p-20f;
-    const float v = (float)((int)(wb >> 11) - (1 << 20)) * 0x1p-20f;
-    u = (float)(((wa & 0x7FFu) << 11) | (wb & 0x7FFu)) * 0x1p-22f;
-    const float w2 = (1.0f - tz) * (1.0f + tz);
-    const float r = (w2 > 0.0f) ? w2 * rsqrtf(w2) : 0.0f;
-    float sn, cs;
-    __sincosf(3.14159265358979f * v, &sn, &cs);
-    tx = r * cs;
-    ty = r * sn;
+// The three integers of one half (a, b): z index, azimuth index, P index.
+__device__ __forceinline__ void half_ints(uint32_t a, uint32_t b, float &zi, float &vi, float &ui) {
+    zi = (float)((int)(a >> 11) - (1 << 20));
+    vi = (float)((int)(b >> 11) - (1 << 20));
+    ui = (float)(((a & 0x7FFu) << 11) | (b & 0x7FFu));
 }
 
-// Trial orientation and acceptance uniform from one half (wa, wb) of a block
-// (FP32 schedule).  FP16 storage additionally renormalises and rounds the
-// trial to binary16, and the rounded vector is the one tested and stored, so
-// the chain samples the stored state.
-template <int P>
-__device__ __forceinline__ void trial_from_half(uint32_t wa, uint32_t wb, float &tx, float &ty, float &tz, float &u) {
-    sphere_fp32(wa, wb, tx, ty, tz, u);
+// Trial orientation and acceptance uniform (Metropolis step (ii)) from the
+// integers: z and v = 2u - 1 are exact, r = w / sqrt(w) with w = (1-z)(1+z)
+// >= 0 from the hardware reciprocal square root, the azimuth pi v from the
+// hardware sine / cosine on [-pi, pi) (absolute error about 4e-7, below what
+// a 21-bit proposal resolves).  FP16 storage renormalises and rounds the trial
+// to binary16; the rounded vector is the one tested and stored, so the chain
+// samples the stored state.
+template <int P, typename T>
+__device__ __forceinline__ void trial32(T zi, T vi, T ui, T &tx, T &ty, T &tz, T &u) {
+    tz = f_mul(zi, splat<T>(0x1p-20f));
+    const T v = f_mul(vi, splat<T>(0x1p-20f));
+    u = f_mul(ui, splat<T>(0x1p-22f));
+    const T w2 = f_mul(f_sub(splat<T>(1.0f), tz), f_add(splat<T>(1.0f), tz));
+    const T r = pos_or_zero(w2, f_mul(w2, rsqrt_l(w2)));
+    T sn, cs;
+    sincos_l(f_mul(splat<T>(3.14159265358979f), v), sn, cs);
+    tx = f_mul(r, cs);
+    ty = f_mul(r, sn);
     if constexpr (P == HS_FP16) {
-        const float inv = rsqrtf(tx * tx + ty * ty + tz * tz);
-        tx = __half2float(__float2half_rn(tx * inv));
-        ty = __half2float(__float2half_rn(ty * inv));
-        tz = __half2float(__float2half_rn(tz * inv));
+        const T inv = rsqrt_l(f_fma(tz, tz, f_fma(ty, ty, f_mul(tx, tx))));
+        tx = half_round_l(f_mul(tx, inv));
+        ty = half_round_l(f_mul(ty, inv));
+        tz = half_round_l(f_mul(tz, inv));
     }
 }
 
@@ -143,10 +183,37 @@ template <int P>
 __device__ __forceinline__ void draw_trial_rank(uint32_t rank, uint32_t sweep, uint32_t colour, uint32_t replica,
                                                 uint32_t k0, uint32_t k1, float &tx, float &ty, float &tz, float &u) {
     const uint4 w = trial_block(rank >> 1, sweep, colour, replica, k0, k1);
+    float zi, vi, ui;
     if (rank & 1u)
-        trial_from_half<P>(w.z, w.w, tx, ty, tz, u);
+        half_ints(w.z, w.w, zi, vi, ui);
     else
-        trial_from_half<P>(w.x, w.y, tx, ty, tz, u);
+        half_ints(w.x, w.y, zi, vi, ui);
+    trial32<P, float>(zi, vi, ui, tx, ty, tz, u);
+}
+
+// Metropolis step (iii), FP32 (one site or a pair of lanes): dH of Eq. 1
+// restricted to the terms containing S_i, dH = J (S.h - S'.h) +
+// K ((S.e)^2 - (S'.e)^2); the dot products are kept for the fused energy.
+// Acceptance: dH <= 0 or P <= exp(-beta dH) = 2^(-beta log2(e) dH).
+template <typename T>
+struct Dots32 {
+    T sh, th, se, pe, dH;
+};
+
+template <typename T>
+__device__ __forceinline__ Dots32<T> site_math32(T sx, T sy, T sz, T tx, T ty, T tz, T hx, T hy, T hz, float J,
+                                                 float K, float ex, float ey, float ez) {
+    Dots32<T> d;
+    d.sh = f_fma(sz, hz, f_fma(sy, hy, f_mul(sx, hx)));
+    d.th = f_fma(tz, hz, f_fma(ty, hy, f_mul(tx, hx)));
+    d.se = f_fma(sz, splat<T>(ez), f_fma(sy, splat<T>(ey), f_mul(sx, splat<T>(ex))));
+    d.pe = f_fma(tz, splat<T>(ez), f_fma(ty, splat<T>(ey), f_mul(tx, splat<T>(ex))));
+    d.dH = f_fma(splat<T>(K), f_mul(f_sub(d.se, d.pe), f_add(d.se, d.pe)), f_mul(splat<T>(J), f_sub(d.sh, d.th)));
+    return d;
+}
+
+__device__ __forceinline__ bool accept32(float dH, float u, float neg_beta_log2e) {
+    return (dH <= 0.0f) || (u <= ex2_hw(f_mul(neg_beta_log2e, dH)));
 }
 
 template <typename S, typename C> __device__ __forceinline__ S to_store(C v);
@@ -154,11 +221,10 @@ template <> __device__ __forceinline__ double to_store<double, double>(double v)
 template <> __device__ __forceinline__ float to_store<float, float>(float v) { return v; }
 template <> __device__ __forceinline__ __half to_store<__half, float>(float v) { return __float2half_rn(v); }
 
-__device__ __forceinline__ float exp_c(float x) { return __expf(x); }
 __device__ __forceinline__ double exp_c(double x) { return exp(x); }
 
-// Metropolis step (iii) for one site: dH of Eq. 1 restricted to the terms
-// that contain S_i, dH = J (S.h - S'.h) + K ((S.e)^2 - (S'.e)^2), then
+// Metropolis step (iii) for one site in FP64: dH of Eq. 1 restricted to the
+// terms that contain S_i, dH = J (S.h - S'.h) + K ((S.e)^2 - (S'.e)^2), then
 // dH <= 0 or P <= exp(-beta dH).  The dot products are returned for the
 // fused energy measurement.
 template <typename C>
@@ -214,9 +280,10 @@ __device__ __forceinline__ double warp_sum(double v) {
 // Finalise a sweep (or a standalone measurement): the last CTA to arrive sums
 // every CTA's slots of every pass in a fixed order, so the FP64 totals do not
 // depend on scheduling.
+template <int NT = kBlock>
 __device__ void finish_reduction(const PassArgs &a, bool measured) {
     __shared__ int s_last;
-    __shared__ double s_fin[kBlock / 32][kPartials];
+    __shared__ double s_fin[NT / 32][kPartials];
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -228,7 +295,7 @@ __device__ void finish_reduction(const PassArgs &a, bool measured) {
     __threadfence();
     double t[kPartials] = {0.0, 0.0, 0.0, 0.0, 0.0};
     for (int p = 0; p < a.n_colours; ++p)
-        for (int b = threadIdx.x; b < a.n_blocks; b += kBlock) {
+        for (int b = threadIdx.x; b < a.n_blocks; b += NT) {
             const double *slot = a.partials + ((size_t)p * a.n_blocks + b) * kPartials;
 #pragma unroll
             for (int q = 0; q < kPartials; ++q) t[q] += __ldcg(slot + q);
@@ -242,7 +309,7 @@ __device__ void finish_reduction(const PassArgs &a, bool measured) {
     __syncthreads();
     if (threadIdx.x == 0) {
         double tot[kPartials] = {0.0, 0.0, 0.0, 0.0, 0.0};
-        for (int w = 0; w < kBlock / 32; ++w)
+        for (int w = 0; w < NT / 32; ++w)
 #pragma unroll
             for (int q = 0; q < kPartials; ++q) tot[q] += s_fin[w][q];
         DevAccum *A = a.acc;
@@ -281,9 +348,10 @@ __device__ void finish_reduction(const PassArgs &a, bool measured) {
     }
 }
 
-template <typename C, bool MEAS>
+// NT = threads of the CTA (a multiple of 32).
+template <typename C, bool MEAS, int NT = kBlock>
 __device__ __forceinline__ void write_partials(const PassArgs &a, C e, C x, C y, C z, unsigned nacc) {
-    __shared__ double s_w[kBlock / 32][kPartials];
+    __shared__ double s_w[NT / 32][kPartials];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (MEAS) {
         e = warp_sum(e);
@@ -303,10 +371,10 @@ __device__ __forceinline__ void write_partials(const PassArgs &a, C e, C x, C y,
     if (threadIdx.x < kPartials) {
         double s = 0.0;
 #pragma unroll
-        for (int w = 0; w < kBlock / 32; ++w) s += s_w[w][threadIdx.x];
+        for (int w = 0; w < NT / 32; ++w) s += s_w[w][threadIdx.x];
         a.partials[((size_t)a.pass * a.n_blocks + blockIdx.x) * kPartials + threadIdx.x] = s;
     }
-    if (a.finish) finish_reduction(a, MEAS);
+    if (a.finish) finish_reduction<NT>(a, MEAS);
 }
 
 // ----------------------------------------------------------------- stencil pass
@@ -316,6 +384,31 @@ __device__ __forceinline__ void write_partials(const PassArgs &a, C e, C x, C y,
 // row: p = 0 -> (xh-1, xh), p = 1 -> (xh, xh+1); the +-y and +-z neighbours
 // sit at the same xh in the adjacent rows.  Neighbour order of the local
 // field sum: -x, +x, -y, +y, -z, +z.
+
+// Per-thread partial sums of the fused measurement (E, S) and accepted moves.
+// FP32 / FP16 accumulate in float2 lanes (even / odd site of a pair).
+template <int P>
+struct SiteAcc {
+    float2 e = make_float2(0.f, 0.f), x = make_float2(0.f, 0.f), y = make_float2(0.f, 0.f),
+           z = make_float2(0.f, 0.f);
+    unsigned n = 0;
+    __device__ __forceinline__ float E() const { return e.x + e.y; }
+    __device__ __forceinline__ float X() const { return x.x + x.y; }
+    __device__ __forceinline__ float Y() const { return y.x + y.y; }
+    __device__ __forceinline__ float Z() const { return z.x + z.y; }
+};
+template <>
+struct SiteAcc<HS_FP64> {
+    double e = 0.0, x = 0.0, y = 0.0, z = 0.0;
+    unsigned n = 0;
+    __device__ __forceinline__ double E() const { return e; }
+    __device__ __forceinline__ double X() const { return x; }
+    __device__ __forceinline__ double Y() const { return y; }
+    __device__ __forceinline__ double Z() const { return z; }
+};
+
+// -beta log2(e), rounded once; every FP32 path uses this same value.
+__device__ __forceinline__ float neg_beta_log2e(float beta) { return f_mul(-beta, 1.44269504088896341f); }
 
 // Metropolis steps (ii)-(iii) for the V sites of one work item, given the
 // item's own spins s, the other colour's same row o (+ the edge element ed
@@ -330,70 +423,137 @@ __device__ __forceinline__ bool update_item(Vec<typename Tr<P>::S, V> (&s)[3], c
                                             uint32_t p, uint32_t site0, int c, const PassArgs &a,
                                             typename Tr<P>::C J, typename Tr<P>::C K, typename Tr<P>::C ex,
                                             typename Tr<P>::C ey, typename Tr<P>::C ez, typename Tr<P>::C beta,
-                                            typename Tr<P>::C &accE, typename Tr<P>::C &accX,
-                                            typename Tr<P>::C &accY, typename Tr<P>::C &accZ, unsigned &nacc) {
+                                            SiteAcc<P> &acc) {
     using S = typename Tr<P>::S;
     using C = typename Tr<P>::C;
     bool any = false;
-    // Metropolis steps (ii)-(iii) for site k with trial (tx, ty, tz), uniform u
-    auto site = [&](int k, C tx, C ty, C tz, C u) {
-        C h[3];
-#pragma unroll
-        for (int q = 0; q < 3; ++q) {
-            const C xm = p ? to_c(o[q].v[k]) : (k == 0 ? ed[q] : to_c(o[q].v[k - 1]));
-            const C xp = p ? (k == V - 1 ? ed[q] : to_c(o[q].v[k + 1])) : to_c(o[q].v[k]);
-            h[q] = ((((xm + xp) + to_c(nym[q].v[k])) + to_c(nyp[q].v[k])) + to_c(nzm[q].v[k])) + to_c(nzp[q].v[k]);
-        }
-        C sx = to_c(s[0].v[k]), sy = to_c(s[1].v[k]), sz = to_c(s[2].v[k]);
-        const SiteDots<C> d = metropolis<C>(sx, sy, sz, tx, ty, tz, h[0], h[1], h[2], J, K, ex, ey, ez, beta, u);
-        if (d.acc) {
-            sx = tx;
-            sy = ty;
-            sz = tz;
-            s[0].v[k] = to_store<S, C>(tx);
-            s[1].v[k] = to_store<S, C>(ty);
-            s[2].v[k] = to_store<S, C>(tz);
-            any = true;
-            ++nacc;
-        }
-        if (MEAS) {
-            // bond energy counted at the later colour's end: pass 1 owns
-            // every sc bond, pass 0 only the anisotropy term
-            const C e_new = d.acc ? d.pe : d.se;
-            C ei = -K * e_new * e_new;
-            if (c == 1) ei -= J * (d.acc ? d.th : d.sh);
-            accE += ei;
-            accX += sx;
-            accY += sy;
-            accZ += sz;
-        }
-    };
+    // the x neighbours of site k: row parity p picks (xh-1, xh) or (xh, xh+1)
+    auto xm_of = [&](int k, int q) -> C { return p ? to_c(o[q].v[k]) : (k == 0 ? ed[q] : to_c(o[q].v[k - 1])); };
+    auto xp_of = [&](int k, int q) -> C { return p ? (k == V - 1 ? ed[q] : to_c(o[q].v[k + 1])) : to_c(o[q].v[k]); };
     if constexpr (P == HS_FP64) {
 #pragma unroll
         for (int k = 0; k < V; ++k) {
             C tx, ty, tz, u;
             draw_trial<P>(site0 + 2u * k, a.sweep, (uint32_t)c, a.replica, a.key0, a.key1, tx, ty, tz, u);
-            site(k, tx, ty, tz, u);
+            C h[3];
+#pragma unroll
+            for (int q = 0; q < 3; ++q)
+                h[q] = ((((xm_of(k, q) + xp_of(k, q)) + to_c(nym[q].v[k])) + to_c(nyp[q].v[k])) +
+                        to_c(nzm[q].v[k])) +
+                       to_c(nzp[q].v[k]);
+            C sx = to_c(s[0].v[k]), sy = to_c(s[1].v[k]), sz = to_c(s[2].v[k]);
+            const SiteDots<C> d = metropolis<C>(sx, sy, sz, tx, ty, tz, h[0], h[1], h[2], J, K, ex, ey, ez, beta, u);
+            if (d.acc) {
+                sx = tx;
+                sy = ty;
+                sz = tz;
+                s[0].v[k] = tx;
+                s[1].v[k] = ty;
+                s[2].v[k] = tz;
+                any = true;
+                ++acc.n;
+            }
+            if (MEAS) {
+                // bond energy counted at the later colour's end: pass 1 owns
+                // every sc bond, pass 0 only the anisotropy term
+                const C e_new = d.acc ? d.pe : d.se;
+                C ei = -K * e_new * e_new;
+                if (c == 1) ei -= J * (d.acc ? d.th : d.sh);
+                acc.e += ei;
+                acc.x += sx;
+                acc.y += sy;
+                acc.z += sz;
+            }
         }
     } else {
+        const float nb = neg_beta_log2e(beta);
+        // one site in lane x of the accumulators
+        auto single = [&](int k, float tx, float ty, float tz, float u) {
+            float h[3];
+#pragma unroll
+            for (int q = 0; q < 3; ++q)
+                h[q] = f_add(f_add(f_add(f_add(f_add(xm_of(k, q), xp_of(k, q)), to_c(nym[q].v[k])), to_c(nyp[q].v[k])),
+                                     to_c(nzm[q].v[k])),
+                             to_c(nzp[q].v[k]));
+            const float sx = to_c(s[0].v[k]), sy = to_c(s[1].v[k]), sz = to_c(s[2].v[k]);
+            const Dots32<float> d = site_math32<float>(sx, sy, sz, tx, ty, tz, h[0], h[1], h[2], J, K, ex, ey, ez);
+            const bool ac = accept32(d.dH, u, nb);
+            if (ac) {
+                s[0].v[k] = to_store<S, C>(tx);
+                s[1].v[k] = to_store<S, C>(ty);
+                s[2].v[k] = to_store<S, C>(tz);
+                any = true;
+                ++acc.n;
+            }
+            if (MEAS) {
+                const float en = ac ? d.pe : d.se;
+                float ei = f_mul(-K, f_mul(en, en));
+                if (c == 1) ei = f_fma(-J, ac ? d.th : d.sh, ei);
+                acc.e.x = f_add(acc.e.x, ei);
+                acc.x.x = f_add(acc.x.x, ac ? tx : sx);
+                acc.y.x = f_add(acc.y.x, ac ? ty : sy);
+                acc.z.x = f_add(acc.z.x, ac ? tz : sz);
+            }
+        };
         // ranks of the item's sites in their colour class: rank0 + k
         const uint32_t rank0 = site0 >> 1;
         if (V >= 2 && (rank0 & 1u) == 0u) {
 #pragma unroll
-            for (int j = 0; j < V / 2; ++j) {  // one Philox block per pair of sites
+            for (int j = 0; j < V / 2; ++j) {  // one Philox block and packed arithmetic per pair
+                const int k0 = 2 * j, k1 = 2 * j + 1;
                 const uint4 w = trial_block((rank0 >> 1) + j, a.sweep, (uint32_t)c, a.replica, a.key0, a.key1);
-                float tx, ty, tz, u;
-                trial_from_half<P>(w.x, w.y, tx, ty, tz, u);
-                site(2 * j, tx, ty, tz, u);
-                trial_from_half<P>(w.z, w.w, tx, ty, tz, u);
-                site(2 * j + 1, tx, ty, tz, u);
+                float2 zi, vi, ui;
+                half_ints(w.x, w.y, zi.x, vi.x, ui.x);
+                half_ints(w.z, w.w, zi.y, vi.y, ui.y);
+                float2 tx, ty, tz, u;
+                trial32<P, float2>(zi, vi, ui, tx, ty, tz, u);
+                float2 h[3];
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    const float2 xm = make_float2(xm_of(k0, q), xm_of(k1, q));
+                    const float2 xp = make_float2(xp_of(k0, q), xp_of(k1, q));
+                    const float2 ym = make_float2(to_c(nym[q].v[k0]), to_c(nym[q].v[k1]));
+                    const float2 yp = make_float2(to_c(nyp[q].v[k0]), to_c(nyp[q].v[k1]));
+                    const float2 zm = make_float2(to_c(nzm[q].v[k0]), to_c(nzm[q].v[k1]));
+                    const float2 zp = make_float2(to_c(nzp[q].v[k0]), to_c(nzp[q].v[k1]));
+                    h[q] = f_add(f_add(f_add(f_add(f_add(xm, xp), ym), yp), zm), zp);
+                }
+                const float2 sx = make_float2(to_c(s[0].v[k0]), to_c(s[0].v[k1]));
+                const float2 sy = make_float2(to_c(s[1].v[k0]), to_c(s[1].v[k1]));
+                const float2 sz = make_float2(to_c(s[2].v[k0]), to_c(s[2].v[k1]));
+                const Dots32<float2> d = site_math32<float2>(sx, sy, sz, tx, ty, tz, h[0], h[1], h[2], J, K, ex, ey, ez);
+                const bool a0 = accept32(d.dH.x, u.x, nb);
+                const bool a1 = accept32(d.dH.y, u.y, nb);
+                if (a0) {
+                    s[0].v[k0] = to_store<S, C>(tx.x);
+                    s[1].v[k0] = to_store<S, C>(ty.x);
+                    s[2].v[k0] = to_store<S, C>(tz.x);
+                    ++acc.n;
+                }
+                if (a1) {
+                    s[0].v[k1] = to_store<S, C>(tx.y);
+                    s[1].v[k1] = to_store<S, C>(ty.y);
+                    s[2].v[k1] = to_store<S, C>(tz.y);
+                    ++acc.n;
+                }
+                any = any || a0 || a1;
+                if (MEAS) {
+                    const float2 en = make_float2(a0 ? d.pe.x : d.se.x, a1 ? d.pe.y : d.se.y);
+                    float2 ei = f_mul(splat<float2>(-K), f_mul(en, en));
+                    if (c == 1)
+                        ei = f_fma(splat<float2>(-J), make_float2(a0 ? d.th.x : d.sh.x, a1 ? d.th.y : d.sh.y), ei);
+                    acc.e = f_add(acc.e, ei);
+                    acc.x = f_add(acc.x, make_float2(a0 ? tx.x : sx.x, a1 ? tx.y : sx.y));
+                    acc.y = f_add(acc.y, make_float2(a0 ? ty.x : sy.x, a1 ? ty.y : sy.y));
+                    acc.z = f_add(acc.z, make_float2(a0 ? tz.x : sz.x, a1 ? tz.y : sz.y));
+                }
             }
         } else {
 #pragma unroll
             for (int k = 0; k < V; ++k) {
                 float tx, ty, tz, u;
                 draw_trial_rank<P>(rank0 + k, a.sweep, (uint32_t)c, a.replica, a.key0, a.key1, tx, ty, tz, u);
-                site(k, tx, ty, tz, u);
+                single(k, tx, ty, tz, u);
             }
         }
     }

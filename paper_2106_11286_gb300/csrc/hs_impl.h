@@ -65,6 +65,7 @@ struct PassArgs {
     int Lx, Ly, Lz, Lh;
     FastDiv div_nxv, div_ly;   // row = t / (Lh/V), z = row / Ly
     int ty, zchunk, n_units;   // staged stencil: slab rows, planes per unit, units
+    int ring_o, ring_w;        // staged stencil: other / own ring slots
     // table layout
     void *spins4;           // 4-vectors, renumbered order
     const int32_t *nbr;     // [width][n_pad]
@@ -97,6 +98,8 @@ struct Layout {
     int vec;                // vector width of the stencil kernels
     bool prefetch;          // register stencil: next work item's loads in flight
     int ty, zchunk, n_units, grid;  // staged stencil tiling and grid
+    int ring_o, ring_w;             // staged stencil ring depths
+    int consumers;                  // staged stencil consumer threads (128 or 256)
     int n_colours;
     int64_t n_sites, n_present;
     // stencil
@@ -161,7 +164,7 @@ cudaError_t launch_gather(int precision, const Layout &L, double *d_xyz, cudaStr
 cudaError_t launch_measure(int precision, const Layout &L, const PassArgs &a, int n_blocks, cudaStream_t s);
 int pass_blocks(int precision, const Layout &L, int n_sm, int blocks_per_sm);
 int pass_occupancy(int precision, const Layout &L, int accumulate);
-size_t staged_smem_bytes(int precision, int ty, int Lh);
-int staged_occupancy(int precision, int vec, size_t smem_bytes);  // 0 = does not fit
+size_t staged_smem_bytes(int precision, int ty, int Lh, int ring_o, int ring_w);
+int staged_occupancy(int precision, int vec, size_t smem_bytes, int consumers);  // 0 = does not fit
 
 }  // namespace hs

@@ -46,7 +46,8 @@ class hs_measurement(ctypes.Structure):
 
 class hs_launch(ctypes.Structure):
     _fields_ = [("kernel", ctypes.c_int), ("vec_width", ctypes.c_int), ("blocks_per_sm", ctypes.c_int),
-                ("tile_y", ctypes.c_int), ("chunk_z", ctypes.c_int), ("prefetch", ctypes.c_int)]
+                ("tile_y", ctypes.c_int), ("chunk_z", ctypes.c_int), ("prefetch", ctypes.c_int),
+                ("ring", ctypes.c_int), ("consumers", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -247,9 +248,11 @@ def hs_read_timing(h):
     return ms.value, n.value
 
 
-def hs_set_launch(h, kernel=0, vec_width=0, blocks_per_sm=0, tile_y=0, chunk_z=0, prefetch=0):
+def hs_set_launch(h, kernel=0, vec_width=0, blocks_per_sm=0, tile_y=0, chunk_z=0, prefetch=0, ring=0,
+                  consumers=0):
     k = KERNELS[kernel] if isinstance(kernel, str) else int(kernel)
-    cfg = hs_launch(k, int(vec_width), int(blocks_per_sm), int(tile_y), int(chunk_z), int(prefetch))
+    cfg = hs_launch(k, int(vec_width), int(blocks_per_sm), int(tile_y), int(chunk_z), int(prefetch), int(ring),
+                    int(consumers))
     _check(load().hs_set_launch(h, ctypes.byref(cfg)))
 
 
@@ -359,8 +362,8 @@ class Lattice:
         hs_autotune(self.h, beta, n_trial_sweeps)
         return hs_get_launch(self.h)
 
-    def set_launch(self, kernel=0, vec_width=0, blocks_per_sm=0, tile_y=0, chunk_z=0, prefetch=0):
-        hs_set_launch(self.h, kernel, vec_width, blocks_per_sm, tile_y, chunk_z, prefetch)
+    def set_launch(self, **cfg):
+        hs_set_launch(self.h, **cfg)
 
     @property
     def launch(self):

@@ -237,8 +237,8 @@ def _launch_configs(precision, dims):
             for ty in (1, 2, 4):
                 if dims[1] % ty == 0:
                     out += [dict(kernel="staged", vec_width=v, tile_y=ty),
-                            dict(kernel="staged", vec_width=v, tile_y=ty, chunk_z=1),
-                            dict(kernel="staged", vec_width=v, tile_y=ty, chunk_z=3)]
+                            dict(kernel="staged", vec_width=v, tile_y=ty, chunk_z=1, ring=4),
+                            dict(kernel="staged", vec_width=v, tile_y=ty, chunk_z=3, ring=6, consumers=8)]
     return out
 
 
@@ -282,7 +282,7 @@ def test_staged_kernel_parity_large(orc):
     g = orc.lattice("sc", dims)
     S0 = inputs.random_unit_spins(g.n, 12)
     with hs.Lattice("sc", dims=dims, precision="fp64", seed=3, **PARAMS) as lat:
-        lat.set_launch(kernel="staged", tile_y=4, chunk_z=3)
+        lat.set_launch(kernel="staged", tile_y=4, chunk_z=3, ring=4)
         lat.set_spins(S0)
         lat.sweep(0.7, 1)
         got = lat.get_spins()
