@@ -221,7 +221,6 @@ template <> __device__ __forceinline__ double to_store<double, double>(double v)
 template <> __device__ __forceinline__ float to_store<float, float>(float v) { return v; }
 template <> __device__ __forceinline__ __half to_store<__half, float>(float v) { return __float2half_rn(v); }
 
-__device__ __forceinline__ double exp_c(double x) { return exp(x); }
 
 // Metropolis step (iii) for one site in FP64: dH of Eq. 1 restricted to the
 // terms that contain S_i, dH = J (S.h - S'.h) + K ((S.e)^2 - (S'.e)^2), then
@@ -233,6 +232,24 @@ struct SiteDots {
     bool acc;
 };
 
+// The FP64 acceptance P <= exp(x), x = -beta dH < 0, decided first with the
+// hardware base-2 exponential in FP32: for |x| <= 80 its relative error is at
+// most 2^-22 (ex2) + 3 |x| 2^-24 (rounding x, x log2(e) and log2(e) to FP32)
+// < 1.5e-5, so outside a band of relative width 3e-5 around it the FP64
+// comparison has a known outcome.  Inside the band (or for |x| > 80) the FP64
+// exponential decides, so the decision always equals the plain FP64 rule.
+__device__ __forceinline__ bool accept64(double x, double u) {
+    if (x >= -80.0) {
+        const float y = __fmul_rn((float)x, 1.44269504088896341f);
+        float e;
+        asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(y));
+        const double ed = (double)e;
+        if (u < ed * (1.0 - 3e-5)) return true;
+        if (u > ed * (1.0 + 3e-5)) return false;
+    }
+    return u <= exp(x);
+}
+
 template <typename C>
 __device__ __forceinline__ SiteDots<C> metropolis(C sx, C sy, C sz, C tx, C ty, C tz, C hx, C hy, C hz, C J, C K,
                                                   C ex, C ey, C ez, C beta, C u) {
@@ -242,7 +259,7 @@ __device__ __forceinline__ SiteDots<C> metropolis(C sx, C sy, C sz, C tx, C ty, 
     d.se = sx * ex + sy * ey + sz * ez;
     d.pe = tx * ex + ty * ey + tz * ez;
     const C dH = J * (d.sh - d.th) + K * ((d.se - d.pe) * (d.se + d.pe));
-    d.acc = (dH <= C(0)) || (u <= exp_c(-beta * dH));
+    d.acc = (dH <= C(0)) || accept64(-beta * dH, u);
     return d;
 }
 
