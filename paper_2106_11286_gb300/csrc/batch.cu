@@ -44,7 +44,7 @@ __device__ bool grid_barrier(unsigned int *bar, unsigned int n_ctas, int *error)
                     atomicExch(error, 1);
                     break;
                 }
-                __nanosleep(64);
+                __nanosleep(20);
             }
         }
         __threadfence();
@@ -137,16 +137,19 @@ __global__ void __launch_bounds__(kBlock, 2) batch_kernel(const BatchArgs b) {
                 return;
             }
         }
-        // finalise this sweep for the members this CTA owns (reads parity par;
-        // the next sweep writes the other parity)
-        if (threadIdx.x == 0) {
-            for (int r = blockIdx.x; r < b.n_members; r += gridDim.x) {
-                const BatchMember &m = b.members[r];
-                double tot[kPartials] = {0.0, 0.0, 0.0, 0.0, 0.0};
-                for (int c = 0; c < 2; ++c)
-                    for (int si = m.seg_begin; si < m.seg_end; ++si)
-                        for (int q = 0; q < kPartials; ++q)
-                            tot[q] += __ldcg(b.slots + (((size_t)par * 2 + c) * b.n_segs + si) * kPartials + q);
+        // finalise this sweep for the members this CTA owns, one warp per
+        // member (reads parity par; the next sweep writes the other parity)
+        for (int r = blockIdx.x * (kBlock / 32) + warp; r < b.n_members; r += gridDim.x * (kBlock / 32)) {
+            const BatchMember &m = b.members[r];
+            double tot[kPartials] = {0.0, 0.0, 0.0, 0.0, 0.0};
+            for (int c = 0; c < 2; ++c)
+                for (int si = m.seg_begin + lane; si < m.seg_end; si += 32)
+#pragma unroll
+                    for (int q = 0; q < kPartials; ++q)
+                        tot[q] += __ldcg(b.slots + (((size_t)par * 2 + c) * b.n_segs + si) * kPartials + q);
+#pragma unroll
+            for (int q = 0; q < kPartials; ++q) tot[q] = warp_sum(tot[q]);
+            if (lane == 0) {
                 DevAccum *A = m.acc;
                 A->accepted += tot[4];
                 const double mx = tot[1] / m.n_present, my = tot[2] / m.n_present, mz = tot[3] / m.n_present;

@@ -611,17 +611,15 @@ struct StencilItem {
     uint32_t b0, p, site0;
 };
 
+// Load the operands of the work item at row (y, z), vector xv.
 template <int P, int V, bool CG = false>
-__device__ __forceinline__ void load_item(const PassArgs &a, uint32_t t, const typename Tr<P>::S *const (&own)[3],
-                                          const typename Tr<P>::S *const (&oth)[3], StencilItem<P, V> &it) {
+__device__ __forceinline__ void load_item_at(const PassArgs &a, uint32_t y, uint32_t z, uint32_t xv,
+                                             const typename Tr<P>::S *const (&own)[3],
+                                             const typename Tr<P>::S *const (&oth)[3], StencilItem<P, V> &it) {
     using S = typename Tr<P>::S;
     using VT = Vec<S, V>;
     const uint32_t Lh = a.Lh, Ly = a.Ly, Lz = a.Lz, Lx = a.Lx;
-    const uint32_t nxv = Lh / V;
-    const uint32_t row = a.div_nxv.div(t);
-    const uint32_t xv = t - row * nxv;
-    const uint32_t z = a.div_ly.div(row);
-    const uint32_t y = row - z * Ly;
+    const uint32_t row = z * Ly + y;
     const uint32_t p = (y + z + (uint32_t)a.colour) & 1u;
     const uint32_t xh0 = xv * V;
     const uint32_t ym = (y == 0) ? Ly - 1 : y - 1;
@@ -647,6 +645,18 @@ __device__ __forceinline__ void load_item(const PassArgs &a, uint32_t t, const t
     it.b0 = b0;
     it.p = p;
     it.site0 = row * Lx + 2 * xh0 + p;
+}
+
+// The work item with linear index t = (z Ly + y) (Lh/V) + xv.
+template <int P, int V, bool CG = false>
+__device__ __forceinline__ void load_item(const PassArgs &a, uint32_t t, const typename Tr<P>::S *const (&own)[3],
+                                          const typename Tr<P>::S *const (&oth)[3], StencilItem<P, V> &it) {
+    const uint32_t nxv = a.Lh / V;
+    const uint32_t row = a.div_nxv.div(t);
+    const uint32_t xv = t - row * nxv;
+    const uint32_t z = a.div_ly.div(row);
+    const uint32_t y = row - z * a.Ly;
+    load_item_at<P, V, CG>(a, y, z, xv, own, oth, it);
 }
 
 }  // namespace

@@ -90,7 +90,7 @@ struct PassArgs {
     DevAccum *acc;
 };
 
-enum KernelKind { kStencil = 1, kStaged = 2, kTable = 3 };
+enum KernelKind { kStencil = 1, kStaged = 2, kTable = 3, kMarch = 4 };
 
 struct Layout {
     bool structured;

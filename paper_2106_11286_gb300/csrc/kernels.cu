@@ -74,6 +74,67 @@ __global__ void __launch_bounds__(kBlock, 2) sc_pass_kernel(const PassArgs a) {
     write_partials<C, MEAS>(a, acc.E(), acc.X(), acc.Y(), acc.Z(), acc.n);
 }
 
+// ----------------------------------------------------------------- z-marching stencil pass
+// Register stencil in slab order: the plane-slabs (ty rows of one z plane)
+// of every y slab, z fastest, are split into equal contiguous ranges, one per
+// CTA, so a CTA walks along z.  The other colour's rows at z and z+1, loaded
+// as the z+-1 neighbours of plane z, come back from L1 for plane z+1; only
+// the own plane z+1 and the other colour's plane z+2 are new, and thread 0
+// asks the bulk-copy engine to prefetch those into L2 one plane ahead.
+__device__ __forceinline__ void prefetch_l2(const void *p, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
+template <int P, int V, bool MEAS>
+__global__ void __launch_bounds__(kBlock, 2) sc_march_kernel(const PassArgs a) {
+    using S = typename Tr<P>::S;
+    using C = typename Tr<P>::C;
+    using VT = Vec<S, V>;
+    const int c = a.colour;
+    const uint32_t Lh = a.Lh, Ly = a.Ly, Lz = a.Lz;
+    const uint32_t ty = (uint32_t)a.ty;
+    const uint32_t nxv = Lh / V;
+    const uint32_t items = ty * nxv;
+    const uint32_t n_slabs = Ly / ty;
+    const uint64_t total = (uint64_t)n_slabs * Lz;  // plane-slabs
+    const uint32_t q0 = (uint32_t)(total * blockIdx.x / gridDim.x);
+    const uint32_t q1 = (uint32_t)(total * (blockIdx.x + 1) / gridDim.x);
+    C J, K, ex, ey, ez, beta;
+    load_params(a, J, K, ex, ey, ez, beta);
+    S *own_w[3] = {(S *)a.own[0], (S *)a.own[1], (S *)a.own[2]};
+    const S *const own[3] = {(const S *)a.own[0], (const S *)a.own[1], (const S *)a.own[2]};
+    const S *const oth[3] = {(const S *)a.oth[0], (const S *)a.oth[1], (const S *)a.oth[2]};
+    const uint32_t slab_bytes = ty * Lh * (uint32_t)sizeof(S);
+    const bool pf = (slab_bytes % 16u) == 0u;
+    SiteAcc<P> acc;
+    for (uint32_t q = q0; q < q1; ++q) {
+        const uint32_t slab = q / Lz;  // once per plane-slab: plain division is fine
+        const uint32_t z = q - slab * Lz;
+        const uint32_t y0 = slab * ty;
+        if (pf && threadIdx.x == 0 && q + 1 < q1) {
+            const uint32_t z1 = (z + 1 == Lz) ? 0 : z + 1;
+            const uint32_t z2 = (z1 + 1 == Lz) ? 0 : z1 + 1;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                prefetch_l2(own[k] + ((size_t)z1 * Ly + y0) * Lh, slab_bytes);
+                prefetch_l2(oth[k] + ((size_t)z2 * Ly + y0) * Lh, slab_bytes);
+            }
+        }
+        for (uint32_t it = threadIdx.x; it < items; it += kBlock) {
+            const uint32_t yl = a.div_nxv.div(it);
+            const uint32_t xv = it - yl * nxv;
+            StencilItem<P, V> item;
+            load_item_at<P, V>(a, y0 + yl, z, xv, own, oth, item);
+            if (update_item<P, V, MEAS>(item.s, item.o, item.nym, item.nyp, item.nzm, item.nzp, item.ed, item.p,
+                                        item.site0, c, a, J, K, ex, ey, ez, beta, acc)) {
+#pragma unroll
+                for (int k = 0; k < 3; ++k) *reinterpret_cast<VT *>(own_w[k] + item.b0) = item.s[k];
+            }
+        }
+    }
+    write_partials<C, MEAS>(a, acc.E(), acc.X(), acc.Y(), acc.Z(), acc.n);
+}
+
 // ----------------------------------------------------------------- staged stencil pass
 // The other colour's planes (and the updated colour's own planes) are staged
 // in shared memory by the bulk-copy (TMA) engine.  A CTA owns a slab of ty
@@ -595,9 +656,28 @@ cudaError_t launch_staged_v(const Layout &L, const PassArgs &a, cudaStream_t s, 
     return L.consumers == 128 ? launch_staged_nc<P, V, 128>(L, a, s, meas) : launch_staged_nc<P, V, 256>(L, a, s, meas);
 }
 
+template <int P, int V>
+cudaError_t launch_march_v(const PassArgs &a, int n_blocks, cudaStream_t s, bool meas) {
+    if (meas)
+        sc_march_kernel<P, V, true><<<n_blocks, kBlock, 0, s>>>(a);
+    else
+        sc_march_kernel<P, V, false><<<n_blocks, kBlock, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
 template <int P>
 cudaError_t launch_pass_p(const Layout &L, const PassArgs &a, int n_blocks, cudaStream_t s) {
     const bool meas = a.accumulate != 0;
+    if (L.kernel == kMarch) {
+        switch (L.vec) {
+        case 1: return launch_march_v<P, 1>(a, n_blocks, s, meas);
+        case 2: return launch_march_v<P, 2>(a, n_blocks, s, meas);
+        case 4: if constexpr (P != HS_FP64) return launch_march_v<P, 4>(a, n_blocks, s, meas); break;
+        case 8: if constexpr (P == HS_FP16) return launch_march_v<P, 8>(a, n_blocks, s, meas); break;
+        default: break;
+        }
+        return cudaErrorInvalidValue;
+    }
     if (L.kernel == kStaged) {
         switch (L.vec) {
         case 1: return launch_staged_v<P, 1>(L, a, s, meas);
@@ -699,8 +779,27 @@ static const void *sc_ptr(bool meas, bool pf) {
     return meas ? (const void *)sc_pass_kernel<P, V, true, false> : (const void *)sc_pass_kernel<P, V, false, false>;
 }
 
+template <int P, int V>
+static const void *march_ptr(bool meas) {
+    return meas ? (const void *)sc_march_kernel<P, V, true> : (const void *)sc_march_kernel<P, V, false>;
+}
+
 template <int P>
 static const void *pass_kernel_ptr(const Layout &L, bool meas) {
+    if (L.kernel == kMarch) {
+        switch (L.vec) {
+        case 1: return march_ptr<P, 1>(meas);
+        case 2: return march_ptr<P, 2>(meas);
+        case 4:
+            if constexpr (P != HS_FP64) return march_ptr<P, 4>(meas);
+            break;
+        case 8:
+            if constexpr (P == HS_FP16) return march_ptr<P, 8>(meas);
+            break;
+        default: break;
+        }
+        return nullptr;
+    }
     if (L.kernel == kStencil) {
         switch (L.vec) {
         case 1: return sc_ptr<P, 1>(meas, L.prefetch);

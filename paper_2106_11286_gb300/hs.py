@@ -53,8 +53,8 @@ class hs_launch(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
-HS_KERNEL_AUTO, HS_KERNEL_STENCIL, HS_KERNEL_STAGED, HS_KERNEL_TABLE = 0, 1, 2, 3
-KERNELS = {"auto": 0, "stencil": 1, "staged": 2, "table": 3}
+HS_KERNEL_AUTO, HS_KERNEL_STENCIL, HS_KERNEL_STAGED, HS_KERNEL_TABLE, HS_KERNEL_MARCH = 0, 1, 2, 3, 4
+KERNELS = {"auto": 0, "stencil": 1, "staged": 2, "table": 3, "march": 4}
 
 
 class hs_info(ctypes.Structure):

@@ -233,6 +233,10 @@ def _launch_configs(precision, dims):
         out += [dict(kernel="stencil", vec_width=v, blocks_per_sm=1), dict(kernel="stencil", vec_width=v),
                 dict(kernel="stencil", vec_width=v, prefetch=1), dict(kernel="stencil", vec_width=v, prefetch=1,
                                                                        blocks_per_sm=1)]
+        for ty in (1, 2, 4):
+            if dims[1] % ty == 0:
+                out += [dict(kernel="march", vec_width=v, tile_y=ty), dict(kernel="march", vec_width=v, tile_y=ty,
+                                                                           blocks_per_sm=1)]
         if (lh * es) % 16 == 0:
             for ty in (1, 2, 4):
                 if dims[1] % ty == 0:
