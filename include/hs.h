@@ -310,6 +310,19 @@ int hs_sweep_sc_fp32_noalloc(float *planes, const int32_t dims[3], const hs_para
                              uint64_t seed, uint32_t replica, uint64_t first_sweep, int64_t n_sweeps,
                              double *d_out, void *cuda_stream);
 
+/* Test hooks for the bounded device-side waits (failure detection without a
+ * GPU fault).  hs_lattice_inject_timeout: the next colour pass of a lattice
+ * running the staged kernel expects 16 bytes more than it copies, so the
+ * consumers' bounded mbarrier wait runs out (about one second).
+ * hs_batch_inject_timeout: in the next hs_batch_run one CTA skips its first
+ * grid-barrier arrival, so every other CTA's bounded wait runs out.  Either
+ * way the kernel latches its error word and returns; the next synchronising
+ * call on the lattice (each member) reports HS_E_TIMEOUT and clears it, the
+ * CUDA context stays usable, and the spins of the interrupted sweep are left
+ * part-updated. */
+int hs_lattice_inject_timeout(hs_lattice *h, int on);
+int hs_batch_inject_timeout(hs_batch *b, int on);
+
 const char *hs_last_error(void);
 int hs_api_version(void);
 

@@ -198,6 +198,7 @@ struct hs_lattice {
     int64_t last_n_sweeps = 0;
     Layout L{};
     int n_blocks = 1;
+    int inject_timeout = 0;  // test hook, consumed by the next staged pass
     hs_launch req{};        // requested launch configuration (0 = automatic)
     int max_blocks = 1;     // capacity of the partials buffer
     double *partials = nullptr;
@@ -670,6 +671,11 @@ int hs_sweep(hs_lattice *h, double beta, int64_t n_sweeps) {
                 int st = record_event(h);
                 if (st) return st;
             }
+            a.inject_extra_tx = 0;
+            if (h->inject_timeout && L.kernel == hs::kStaged) {
+                a.inject_extra_tx = 16;
+                h->inject_timeout = 0;
+            }
             HS_CUDA(hs::launch_pass(h->precision, L, a, h->n_blocks, h->stream));
             if (h->timing) {
                 int st = record_event(h);
@@ -1005,6 +1011,7 @@ struct hs_batch {
     cudaGraphExec_t exec = nullptr;
     int graph_total = -1, graph_equil = -1;
     bool graph_failed = false;
+    int inject_timeout = 0;  // test hook, consumed by the next run
     ~hs_batch() {
         cudaStreamSynchronize(stream);
         if (exec) cudaGraphExecDestroy(exec);
@@ -1148,7 +1155,14 @@ int hs_batch_run(hs_batch *b, const double *betas, int64_t n_sweeps, int64_t n_e
                             cudaMemcpyHostToDevice, b->stream));
     HS_CUDA(cudaMemsetAsync(b->d_bar, 0, 2 * sizeof(unsigned int), b->stream));
     HS_CUDA(cudaMemsetAsync(b->d_error, 0, sizeof(int), b->stream));
-    const hs::BatchArgs args = batch_args(b, n_total, n_eq);
+    hs::BatchArgs args = batch_args(b, n_total, n_eq);
+    if (b->inject_timeout) {  // test hook: launched directly, never captured
+        args.inject_skip = 1;
+        b->inject_timeout = 0;
+        HS_CUDA(hs::launch_batch(args, b->grid, b->stream));
+        for (int r = 0; r < n; ++r) b->members[r]->sweep += (uint64_t)n_total;
+        return HS_OK;
+    }
     // the persistent kernel runs as one node of a CUDA graph, captured once per
     // (sweeps, equilibration) pair; without graph support it is launched directly
     if (!b->graph_failed && (b->graph_total != n_total || b->graph_equil != n_eq || !b->exec)) {
@@ -1183,5 +1197,18 @@ int hs_batch_run(hs_batch *b, const double *betas, int64_t n_sweeps, int64_t n_e
 }
 
 void hs_batch_destroy(hs_batch *b) { delete b; }
+
+int hs_batch_inject_timeout(hs_batch *b, int on) {
+    if (!b) return fail(HS_E_INVALID, "null handle");
+    b->inject_timeout = on ? 1 : 0;
+    return HS_OK;
+}
+
+int hs_lattice_inject_timeout(hs_lattice *h, int on) {
+    if (!h) return fail(HS_E_INVALID, "null handle");
+    if (on && h->L.kernel != hs::kStaged) return fail(HS_E_INVALID, "the hook needs the staged kernel");
+    h->inject_timeout = on ? 1 : 0;
+    return HS_OK;
+}
 
 }  // extern "C"

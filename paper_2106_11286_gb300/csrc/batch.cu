@@ -24,7 +24,7 @@ constexpr long long kBarrierCycles = 2000000000LL;  // about one second
 // Grid-wide barrier: generation read before arriving; the last arriver resets
 // the count and bumps the generation.  Bounded spin; returns false (and
 // latches the error word) if the generation does not change in time.
-__device__ bool grid_barrier(unsigned int *bar, unsigned int n_ctas, int *error) {
+__device__ bool grid_barrier(unsigned int *bar, unsigned int n_ctas, int *error, bool skip_arrival) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -32,7 +32,8 @@ __device__ bool grid_barrier(unsigned int *bar, unsigned int n_ctas, int *error)
         volatile unsigned int *gen = bar + 1;
         const unsigned int g = *gen;
         __threadfence();
-        if (atomicAdd(bar, 1u) == n_ctas - 1u) {
+        // (test hook: a skipped arrival leaves every other CTA's wait to run out)
+        if (!skip_arrival && atomicAdd(bar, 1u) == n_ctas - 1u) {
             atomicExch(bar, 0u);
             __threadfence();
             atomicAdd(bar + 1, 1u);
@@ -131,7 +132,8 @@ __global__ void __launch_bounds__(kBlock, 2) batch_kernel(const BatchArgs b) {
                 }
                 __syncthreads();
             }
-            if (!grid_barrier(b.bar, gridDim.x, b.error)) {  // uniform per CTA
+            const bool skip = b.inject_skip && blockIdx.x == 0 && s == 0 && c == 0;
+            if (!grid_barrier(b.bar, gridDim.x, b.error, skip)) {  // uniform per CTA
                 if (threadIdx.x == 0)
                     for (int r = 0; r < b.n_members; ++r) atomicExch(&b.members[r].acc->error, 1);
                 return;

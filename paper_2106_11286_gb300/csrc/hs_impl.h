@@ -88,6 +88,7 @@ struct PassArgs {
     int accumulate;         // 1: add the moments to the accumulator
     double n_present;
     DevAccum *acc;
+    int inject_extra_tx;    // test hook: extra bytes the first staged fill expects
 };
 
 enum KernelKind { kStencil = 1, kStaged = 2, kTable = 3, kMarch = 4 };
@@ -145,6 +146,7 @@ struct BatchArgs {
     unsigned int *bar;       // grid barrier: [0] arrivals, [1] generation
     int *error;              // latched device error (barrier timeout)
     int n_total, n_equil;    // sweeps, of which the first n_equil unmeasured
+    int inject_skip;         // test hook: 1 = CTA 0 skips its first barrier arrival
 };
 
 cudaError_t launch_batch(const BatchArgs &b, int grid, cudaStream_t s);

@@ -218,12 +218,12 @@ template <> struct StagedShape<256> { static constexpr int threads = 288, min_ct
 // then lanes issue one row-block copy each.
 template <typename S>
 __device__ __forceinline__ void stage_plane(uint64_t *full, S *dst, const PassArgs &a, int ty, int y0, int z,
-                                            bool other) {
+                                            bool other, uint32_t extra_tx = 0) {
     const int lane = threadIdx.x & 31;
     const int Ly = a.Ly, Lz = a.Lz, Lh = a.Lh;
     z = (z % Lz + Lz) % Lz;
     const uint32_t row_bytes = (uint32_t)Lh * sizeof(S);
-    if (lane == 0) mbar_expect_tx(full, (uint32_t)(3 * (other ? ty + 2 : ty)) * row_bytes);
+    if (lane == 0) mbar_expect_tx(full, (uint32_t)(3 * (other ? ty + 2 : ty)) * row_bytes + extra_tx);
     __syncwarp();
     if (other) {
         if (lane < 9) {
@@ -309,7 +309,9 @@ __global__ void __launch_bounds__(StagedShape<NC>::threads, StagedShape<NC>::min
                 } else {
                     const uint32_t g = go + io, slot = g % NO, fill = g / NO;
                     if (fill > 0 && !mbar_wait(&empty_o[slot], (fill - 1) & 1, abort_flag)) break;
-                    stage_plane<S>(&full_o[slot], oth_s + slot * oslab, a, ty, y0, z0 - 1 + io, true);
+                    // test hook: CTA 0's first fill expects bytes that never come
+                    const uint32_t extra = (g == 0 && blockIdx.x == 0) ? (uint32_t)a.inject_extra_tx : 0u;
+                    stage_plane<S>(&full_o[slot], oth_s + slot * oslab, a, ty, y0, z0 - 1 + io, true, extra);
                     ++io;
                     issued_o = g + 1;
                 }

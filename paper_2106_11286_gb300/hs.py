@@ -99,6 +99,8 @@ SIGNATURES = {
     "hs_sweep_sc_fp32_noalloc": (ctypes.c_int, [_vp, _i32p, ctypes.POINTER(hs_params), ctypes.c_double,
                                                  ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int64,
                                                  _vp, _vp]),
+    "hs_lattice_inject_timeout": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "hs_batch_inject_timeout": (ctypes.c_int, [_vp, ctypes.c_int]),
     "hs_last_error": (ctypes.c_char_p, []),
     "hs_api_version": (ctypes.c_int, []),
 }
@@ -305,6 +307,14 @@ def hs_batch_run(b, betas, n_sweeps, n_equil=0):
 
 def hs_batch_destroy(b):
     load().hs_batch_destroy(b)
+
+
+def hs_lattice_inject_timeout(h, on=True):
+    _check(load().hs_lattice_inject_timeout(h, int(bool(on))))
+
+
+def hs_batch_inject_timeout(b, on=True):
+    _check(load().hs_batch_inject_timeout(b, int(bool(on))))
 
 
 # ------------------------------------------------------------ convenience wrapper
