@@ -35,6 +35,15 @@ __device__ __forceinline__ uint4 philox10(uint4 c, uint32_t k0, uint32_t k1) {
     return c;
 }
 
+// Programmatic dependent launch: a pass kernel lets the next kernel in the
+// stream be scheduled as its own CTAs retire, then waits until the previous
+// kernel has completed and its writes are visible before touching memory.
+// Without a programmatic dependency both instructions are no-ops.
+__device__ __forceinline__ void pdl_enter() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
 constexpr uint32_t kTagTrial = 0u;
 constexpr uint32_t kTagInit = 1u;
 

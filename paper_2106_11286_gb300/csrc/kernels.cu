@@ -31,6 +31,7 @@ namespace {
 // computed (two items in flight, unrolled by hand so no operand is copied).
 template <int P, int V, bool MEAS, bool PF>
 __global__ void __launch_bounds__(kBlock, 2) sc_pass_kernel(const PassArgs a) {
+    pdl_enter();
     using S = typename Tr<P>::S;
     using C = typename Tr<P>::C;
     using VT = Vec<S, V>;
@@ -87,6 +88,7 @@ __device__ __forceinline__ void prefetch_l2(const void *p, uint32_t bytes) {
 
 template <int P, int V, bool MEAS>
 __global__ void __launch_bounds__(kBlock, 2) sc_march_kernel(const PassArgs a) {
+    pdl_enter();
     using S = typename Tr<P>::S;
     using C = typename Tr<P>::C;
     using VT = Vec<S, V>;
@@ -249,6 +251,7 @@ __device__ __forceinline__ void stage_plane(uint64_t *full, S *dst, const PassAr
 template <int P, int V, bool MEAS, int NC>
 __global__ void __launch_bounds__(StagedShape<NC>::threads, StagedShape<NC>::min_ctas)
     sc_staged_kernel(const PassArgs a) {
+    pdl_enter();
     constexpr int kStagedConsumers = NC;
     constexpr int kStagedThreads = StagedShape<NC>::threads;
     using S = typename Tr<P>::S;
@@ -401,6 +404,7 @@ __global__ void __launch_bounds__(StagedShape<NC>::threads, StagedShape<NC>::min
 // Neighbours sum in stored order; padding points at a zero dummy spin.
 template <int P, bool MEAS>
 __global__ void __launch_bounds__(kBlock) table_pass_kernel(const PassArgs a) {
+    pdl_enter();
     using S = typename Tr<P>::S;
     using C = typename Tr<P>::C;
     using S4 = Vec<S, 4>;
@@ -465,6 +469,7 @@ __global__ void __launch_bounds__(kBlock) table_pass_kernel(const PassArgs a) {
 // -J/2 S_i.h_i - K (S_i.e)^2, so each bond is counted once overall.
 template <int P>
 __global__ void __launch_bounds__(kBlock) sc_measure_kernel(const PassArgs a, const void *planes) {
+    pdl_enter();
     using S = typename Tr<P>::S;
     const S *pl = (const S *)planes;
     const int Lh = a.Lh, Ly = a.Ly, Lz = a.Lz;
@@ -506,6 +511,7 @@ __global__ void __launch_bounds__(kBlock) sc_measure_kernel(const PassArgs a, co
 
 template <int P>
 __global__ void __launch_bounds__(kBlock) table_measure_kernel(const PassArgs a, int64_t n_present) {
+    pdl_enter();
     using S = typename Tr<P>::S;
     using S4 = Vec<S, 4>;
     const S4 *spins = reinterpret_cast<const S4 *>(a.spins4);
@@ -627,30 +633,36 @@ inline int grid_for(int64_t n, int cap = 152 * 16) {
     return (int)g;
 }
 
+// Launch with programmatic stream serialisation (see pdl_enter).
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), int grid, int block, size_t smem, cudaStream_t s, Args... args) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 template <int P, int V>
 cudaError_t launch_sc_v(const PassArgs &a, int n_blocks, cudaStream_t s, bool meas, bool pf) {
-    if (pf) {
-        if (meas)
-            sc_pass_kernel<P, V, true, true><<<n_blocks, kBlock, 0, s>>>(a);
-        else
-            sc_pass_kernel<P, V, false, true><<<n_blocks, kBlock, 0, s>>>(a);
-    } else {
-        if (meas)
-            sc_pass_kernel<P, V, true, false><<<n_blocks, kBlock, 0, s>>>(a);
-        else
-            sc_pass_kernel<P, V, false, false><<<n_blocks, kBlock, 0, s>>>(a);
-    }
-    return cudaGetLastError();
+    if (pf)
+        return meas ? launch_pdl(sc_pass_kernel<P, V, true, true>, n_blocks, kBlock, 0, s, a)
+                    : launch_pdl(sc_pass_kernel<P, V, false, true>, n_blocks, kBlock, 0, s, a);
+    return meas ? launch_pdl(sc_pass_kernel<P, V, true, false>, n_blocks, kBlock, 0, s, a)
+                : launch_pdl(sc_pass_kernel<P, V, false, false>, n_blocks, kBlock, 0, s, a);
 }
 
 template <int P, int V, int NC>
 cudaError_t launch_staged_nc(const Layout &L, const PassArgs &a, cudaStream_t s, bool meas) {
     const size_t smem = staged_smem_bytes(P, L.ty, L.Lh, L.ring_o, L.ring_w);
-    if (meas)
-        sc_staged_kernel<P, V, true, NC><<<L.grid, StagedShape<NC>::threads, smem, s>>>(a);
-    else
-        sc_staged_kernel<P, V, false, NC><<<L.grid, StagedShape<NC>::threads, smem, s>>>(a);
-    return cudaGetLastError();
+    return meas ? launch_pdl(sc_staged_kernel<P, V, true, NC>, L.grid, StagedShape<NC>::threads, smem, s, a)
+                : launch_pdl(sc_staged_kernel<P, V, false, NC>, L.grid, StagedShape<NC>::threads, smem, s, a);
 }
 
 template <int P, int V>
@@ -660,11 +672,8 @@ cudaError_t launch_staged_v(const Layout &L, const PassArgs &a, cudaStream_t s, 
 
 template <int P, int V>
 cudaError_t launch_march_v(const PassArgs &a, int n_blocks, cudaStream_t s, bool meas) {
-    if (meas)
-        sc_march_kernel<P, V, true><<<n_blocks, kBlock, 0, s>>>(a);
-    else
-        sc_march_kernel<P, V, false><<<n_blocks, kBlock, 0, s>>>(a);
-    return cudaGetLastError();
+    return meas ? launch_pdl(sc_march_kernel<P, V, true>, n_blocks, kBlock, 0, s, a)
+                : launch_pdl(sc_march_kernel<P, V, false>, n_blocks, kBlock, 0, s, a);
 }
 
 template <int P>
@@ -700,11 +709,8 @@ cudaError_t launch_pass_p(const Layout &L, const PassArgs &a, int n_blocks, cuda
         }
         return cudaErrorInvalidValue;
     }
-    if (meas)
-        table_pass_kernel<P, true><<<n_blocks, kBlock, 0, s>>>(a);
-    else
-        table_pass_kernel<P, false><<<n_blocks, kBlock, 0, s>>>(a);
-    return cudaGetLastError();
+    return meas ? launch_pdl(table_pass_kernel<P, true>, n_blocks, kBlock, 0, s, a)
+                : launch_pdl(table_pass_kernel<P, false>, n_blocks, kBlock, 0, s, a);
 }
 
 template <int P, int NC>
