@@ -62,9 +62,14 @@ def kernels_sha() -> str:
     return h.hexdigest()[:16]
 
 
-def read_traffic():
+# colour-pass kernel of each hs_kernel kind (hs_get_launch's "kernel")
+KERNEL_NAMES = {1: "sc_pass_kernel", 2: "sc_staged_kernel", 3: "table_pass_kernel", 4: "sc_march_kernel",
+                5: "sc_pipe_kernel"}
+
+
+def read_traffic(kernel=None):
     """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel sources (else None)."""
+    on the current kernel sources and on this kernel (else None)."""
     try:
         kv = {}
         for line in open(TRAFFIC_FILE):
@@ -72,6 +77,8 @@ def read_traffic():
                 k, v = line.split(":", 1)
                 kv[k.strip()] = v.strip()
         if kv.get("sources_sha") != kernels_sha():
+            return None
+        if kernel is not None and not kv.get("kernel", "").startswith(kernel + "<"):
             return None
         return float(kv["dram_bytes_per_launch"])
     except (OSError, KeyError, ValueError):
@@ -224,10 +231,11 @@ def run_ours(args):
     alg_bytes = 3 * BYTES_PER_SPIN["fp32"] * (N // 2)   # per launch: N/2 attempts x 3 s
     peaks, peak_kind = measured_peaks()
     achieved_gbs = alg_bytes / (kernel_ms * 1e-3) / 1e9
-    traffic = read_traffic()
+    kname = KERNEL_NAMES.get(launch["kernel"], "sc_pass_kernel") if launch else "sc_pass_kernel"
+    traffic = read_traffic(kname)
     roofline = {"bound": "hbm", "achieved": round(achieved_gbs, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": round(achieved_gbs / peaks["hbm_gbs"], 4), "traffic": traffic,
-                "peak_source": f"{peak_kind} copy bandwidth", "kernel": "sc_pass_kernel<fp32>",
+                "peak_source": f"{peak_kind} copy bandwidth", "kernel": f"{kname}<fp32>",
                 "kernel_ms": round(kernel_ms, 5), "alg_bytes_per_launch": alg_bytes,
                 "kernel_timing": "timed-region CUDA events / colour-pass launches (the region holds only them)",
                 "kernel_ms_bracketed": round(kernel_ms_bracketed, 5),
@@ -368,6 +376,7 @@ def run_variants(args, rank, stream, barrier_sync, world, dev):
                          stream=stream)
         lat.init()
         lat.accumulate(True)
+        launch = lat.launch if args.no_autotune else lat.autotune(1.0, 2)
         lat.sweep(1.0, 3)
         lat.reset_accumulator()
         hs.hs_enable_timing(lat.h, True)
@@ -377,7 +386,8 @@ def run_variants(args, rank, stream, barrier_sync, world, dev):
         ladder[prec] = {"value": round(N5 * sweeps / (sec * 1e9), 3), "unit": UNIT, "sweeps": sweeps,
                         "hbm_frac": round(3 * BYTES_PER_SPIN[prec] * (N5 // 2) / (kms / nl * 1e-3) / 1e9 /
                                           peaks["hbm_gbs"], 4),
-                        "E_per_spin": mom[0] / cnt / N5, "absM": mom[2] / cnt}
+                        "E_per_spin": mom[0] / cnt / N5, "absM": mom[2] / cnt,
+                        "kernel": KERNEL_NAMES.get(launch["kernel"], "?"), "launch": launch}
         lat.close()
     for prec in ("fp16", "fp32"):
         ladder[prec]["bias_E_per_spin_vs_fp64"] = ladder[prec]["E_per_spin"] - ladder["fp64"]["E_per_spin"]
@@ -393,6 +403,7 @@ def run_variants(args, rank, stream, barrier_sync, world, dev):
         del rp, col
         lat.init()
         lat.accumulate(True)
+        launch = lat.launch if args.no_autotune else lat.autotune(1 / 0.9, 2)
         lat.sweep(1 / 0.9, 3)
         lat.reset_accumulator()
         hs.hs_enable_timing(lat.h, True)
@@ -404,7 +415,8 @@ def run_variants(args, rank, stream, barrier_sync, world, dev):
                                    "n_spins": n_present, "colours": lat.info.n_colours, "sweeps": args.csr_sweeps,
                                    "hbm_frac": round(per_attempt * n_present / lat.info.n_colours / (kms / nl * 1e-3)
                                                      / 1e9 / peaks["hbm_gbs"], 4),
-                                   "E_per_spin": mom[0] / cnt / n_present, "absM": mom[2] / cnt}
+                                   "E_per_spin": mom[0] / cnt / n_present, "absM": mom[2] / cnt,
+                                   "launch": launch}
         lat.close()
     return out
 

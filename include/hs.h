@@ -221,15 +221,19 @@ enum hs_kernel {
     HS_KERNEL_STAGED = 2,  /* sc: other-colour planes staged in shared memory by
                               bulk async copies, CTAs march along z */
     HS_KERNEL_TABLE = 3,   /* neighbour-table kernel (bcc, fcc, CSR, masked) */
-    HS_KERNEL_MARCH = 4    /* sc: register stencil walking each CTA's slab along z
+    HS_KERNEL_MARCH = 4,   /* sc: register stencil walking each CTA's slab along z
                               (neighbour rows reused from L1, next plane
                               prefetched into L2) */
+    HS_KERNEL_PIPE = 5     /* sc: register stencil whose next work item is copied
+                              global -> shared (cp.async, one slot per thread)
+                              while the current one is computed; needs 4..16
+                              bytes of storage per vector */
 };
 typedef struct {
     int kernel;        /* hs_kernel; the table kernel is the only one for non-sc */
     int vec_width;     /* sc kernels: sites per thread, 1/2/4/8, dividing Lx/2,
                           at most 16 bytes of storage per load */
-    int blocks_per_sm; /* stencil / table: resident CTAs per SM (0 = max) */
+    int blocks_per_sm; /* stencil / pipe / table: resident CTAs per SM (0 = max) */
     int tile_y;        /* staged / march: rows per CTA slab (divides Ly) */
     int chunk_z;       /* staged: planes per CTA work unit */
     int prefetch;      /* stencil: 1 = issue the next work item's loads before

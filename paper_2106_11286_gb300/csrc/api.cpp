@@ -453,8 +453,19 @@ int configure_launch(hs_lattice *h) {
         h->n_blocks = (int)std::min<int64_t>(std::min<int64_t>(slabs, (int64_t)h->n_sm * bps), h->max_blocks);
         return HS_OK;
     }
+    if (kind == HS_KERNEL_PIPE) {
+        if (hs::pipe_smem_bytes(h->precision, L.vec) == 0)
+            return fail(HS_E_INVALID, "pipelined stencil needs 4 to 16 bytes of storage per vector");
+        L.kernel = hs::kPipe;
+        const int occ = std::min(hs::pass_occupancy(h->precision, L, 0), hs::pass_occupancy(h->precision, L, 1));
+        if (occ < 1) return fail(HS_E_INVALID, "pipelined stencil slots do not fit in shared memory");
+        int bps = r.blocks_per_sm;
+        if (bps <= 0 || bps > occ) bps = occ;
+        h->n_blocks = std::min(hs::pass_blocks(h->precision, L, h->n_sm, bps), h->max_blocks);
+        return HS_OK;
+    }
     L.kernel = hs::kStencil;  // before the occupancy query, which looks at the kind
-    L.prefetch = (r.prefetch == 1);
+    L.prefetch = (r.prefetch == 1) ? 1 : 0;
     int bps = r.blocks_per_sm;
     const int occ = std::min(hs::pass_occupancy(h->precision, L, 0), hs::pass_occupancy(h->precision, L, 1));
     if (bps <= 0 || bps > occ) bps = occ;
@@ -827,14 +838,14 @@ int hs_read_timing(hs_lattice *h, double *ms, int64_t *launches) {
 // ---------------------------------------------------------------- launch configuration
 int hs_set_launch(hs_lattice *h, const hs_launch *cfg) {
     if (!h || !cfg) return fail(HS_E_INVALID, "null argument");
-    if (cfg->kernel < HS_KERNEL_AUTO || cfg->kernel > HS_KERNEL_MARCH)
+    if (cfg->kernel < HS_KERNEL_AUTO || cfg->kernel > HS_KERNEL_PIPE)
         return fail(HS_E_INVALID, "unknown kernel kind");
     if (h->L.structured) {
         if (cfg->kernel == HS_KERNEL_TABLE) return fail(HS_E_INVALID, "sc stencil lattices have no table kernel");
         if (cfg->vec_width != 0 && !vec_ok(h, cfg->vec_width))
             return fail(HS_E_INVALID, "vector width must divide Lx/2, 16 bytes at most");
     } else if (cfg->kernel == HS_KERNEL_STENCIL || cfg->kernel == HS_KERNEL_STAGED ||
-               cfg->kernel == HS_KERNEL_MARCH) {
+               cfg->kernel == HS_KERNEL_MARCH || cfg->kernel == HS_KERNEL_PIPE) {
         return fail(HS_E_INVALID, "stencil kernels need an unmasked periodic sc lattice");
     }
     if (cfg->blocks_per_sm < 0 || cfg->blocks_per_sm > 2048 / hs::kBlock)
@@ -865,7 +876,7 @@ int hs_get_launch(const hs_lattice *h, hs_launch *out) {
     out->blocks_per_sm = (h->n_blocks + h->n_sm - 1) / std::max(h->n_sm, 1);
     out->tile_y = (L.kernel == hs::kStaged || L.kernel == hs::kMarch) ? L.ty : 0;
     out->chunk_z = L.kernel == hs::kStaged ? L.zchunk : 0;
-    out->prefetch = (L.kernel == hs::kStencil) ? (L.prefetch ? 1 : 2) : 0;
+    out->prefetch = (L.kernel == hs::kStencil) ? (L.prefetch == 1 ? 1 : 2) : 0;
     out->ring = L.kernel == hs::kStaged ? L.ring_o : 0;
     out->consumers = L.kernel == hs::kStaged ? L.consumers / 32 : 0;
     return HS_OK;
@@ -895,6 +906,8 @@ std::vector<hs_launch> tune_candidates(hs_lattice *h) {
         if (!vec_ok(h, v)) continue;
         for (int b = 1; b <= 8; ++b)
             for (int pf : {1, 2}) out.push_back({HS_KERNEL_STENCIL, v, b, 0, 0, pf, 0, 0});
+        if (hs::pipe_smem_bytes(h->precision, v) != 0)
+            for (int b = 1; b <= 2; ++b) out.push_back({HS_KERNEL_PIPE, v, b, 0, 0, 0, 0, 0});
         for (int ty : {2, 4, 8, 16})
             if (L.Ly % ty == 0 && ty * (L.Lh / v) >= 64)
                 for (int b : {1, 2}) out.push_back({HS_KERNEL_MARCH, v, b, ty, 0, 0, 0, 0});

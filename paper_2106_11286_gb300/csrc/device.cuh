@@ -620,6 +620,35 @@ struct StencilItem {
     uint32_t b0, p, site0;
 };
 
+// Element offsets (within a colour plane) of the operands of the work item at
+// row (y, z), vector xv: the own vector b0 (and the other colour's same-row
+// vector at the same offset), the other colour's rows at y-1, y+1, z-1, z+1,
+// and the edge element beyond the row vector on the side parity p picks.
+struct ItemOffsets {
+    uint32_t b0, bym, byp, bzm, bzp, bed, p, site0;
+};
+
+template <int V>
+__device__ __forceinline__ ItemOffsets item_offsets(const PassArgs &a, uint32_t y, uint32_t z, uint32_t xv) {
+    const uint32_t Lh = a.Lh, Ly = a.Ly, Lz = a.Lz, Lx = a.Lx;
+    const uint32_t row = z * Ly + y;
+    const uint32_t xh0 = xv * V;
+    const uint32_t ym = (y == 0) ? Ly - 1 : y - 1;
+    const uint32_t yp = (y == Ly - 1) ? 0 : y + 1;
+    const uint32_t zm = (z == 0) ? Lz - 1 : z - 1;
+    const uint32_t zp = (z == Lz - 1) ? 0 : z + 1;
+    ItemOffsets o;
+    o.p = (y + z + (uint32_t)a.colour) & 1u;
+    o.b0 = row * Lh + xh0;
+    o.bym = (z * Ly + ym) * Lh + xh0;
+    o.byp = (z * Ly + yp) * Lh + xh0;
+    o.bzm = (zm * Ly + y) * Lh + xh0;
+    o.bzp = (zp * Ly + y) * Lh + xh0;
+    o.bed = row * Lh + (o.p ? ((xh0 + V == Lh) ? 0 : xh0 + V) : ((xh0 == 0) ? Lh - 1 : xh0 - 1));
+    o.site0 = row * Lx + 2 * xh0 + o.p;
+    return o;
+}
+
 // Load the operands of the work item at row (y, z), vector xv.
 template <int P, int V, bool CG = false>
 __device__ __forceinline__ void load_item_at(const PassArgs &a, uint32_t y, uint32_t z, uint32_t xv,
@@ -627,33 +656,20 @@ __device__ __forceinline__ void load_item_at(const PassArgs &a, uint32_t y, uint
                                              const typename Tr<P>::S *const (&oth)[3], StencilItem<P, V> &it) {
     using S = typename Tr<P>::S;
     using VT = Vec<S, V>;
-    const uint32_t Lh = a.Lh, Ly = a.Ly, Lz = a.Lz, Lx = a.Lx;
-    const uint32_t row = z * Ly + y;
-    const uint32_t p = (y + z + (uint32_t)a.colour) & 1u;
-    const uint32_t xh0 = xv * V;
-    const uint32_t ym = (y == 0) ? Ly - 1 : y - 1;
-    const uint32_t yp = (y == Ly - 1) ? 0 : y + 1;
-    const uint32_t zm = (z == 0) ? Lz - 1 : z - 1;
-    const uint32_t zp = (z == Lz - 1) ? 0 : z + 1;
-    const uint32_t b0 = row * Lh + xh0;
-    const uint32_t bym = (z * Ly + ym) * Lh + xh0;
-    const uint32_t byp = (z * Ly + yp) * Lh + xh0;
-    const uint32_t bzm = (zm * Ly + y) * Lh + xh0;
-    const uint32_t bzp = (zp * Ly + y) * Lh + xh0;
-    const uint32_t bed = row * Lh + (p ? ((xh0 + V == Lh) ? 0 : xh0 + V) : ((xh0 == 0) ? Lh - 1 : xh0 - 1));
+    const ItemOffsets f = item_offsets<V>(a, y, z, xv);
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
-        it.s[q] = ld_val<VT, CG>(reinterpret_cast<const VT *>(own[q] + b0));
-        it.o[q] = ld_val<VT, CG>(reinterpret_cast<const VT *>(oth[q] + b0));
-        it.nym[q] = ld_val<VT, CG>(reinterpret_cast<const VT *>(oth[q] + bym));
-        it.nyp[q] = ld_val<VT, CG>(reinterpret_cast<const VT *>(oth[q] + byp));
-        it.nzm[q] = ld_val<VT, CG>(reinterpret_cast<const VT *>(oth[q] + bzm));
-        it.nzp[q] = ld_val<VT, CG>(reinterpret_cast<const VT *>(oth[q] + bzp));
-        it.ed[q] = to_c(ld_val<S, CG>(oth[q] + bed));
+        it.s[q] = ld_val<VT, CG>(reinterpret_cast<const VT *>(own[q] + f.b0));
+        it.o[q] = ld_val<VT, CG>(reinterpret_cast<const VT *>(oth[q] + f.b0));
+        it.nym[q] = ld_val<VT, CG>(reinterpret_cast<const VT *>(oth[q] + f.bym));
+        it.nyp[q] = ld_val<VT, CG>(reinterpret_cast<const VT *>(oth[q] + f.byp));
+        it.nzm[q] = ld_val<VT, CG>(reinterpret_cast<const VT *>(oth[q] + f.bzm));
+        it.nzp[q] = ld_val<VT, CG>(reinterpret_cast<const VT *>(oth[q] + f.bzp));
+        it.ed[q] = to_c(ld_val<S, CG>(oth[q] + f.bed));
     }
-    it.b0 = b0;
-    it.p = p;
-    it.site0 = row * Lx + 2 * xh0 + p;
+    it.b0 = f.b0;
+    it.p = f.p;
+    it.site0 = f.site0;
 }
 
 // The work item with linear index t = (z Ly + y) (Lh/V) + xv.

@@ -91,13 +91,13 @@ struct PassArgs {
     int inject_extra_tx;    // test hook: extra bytes the first staged fill expects
 };
 
-enum KernelKind { kStencil = 1, kStaged = 2, kTable = 3, kMarch = 4 };
+enum KernelKind { kStencil = 1, kStaged = 2, kTable = 3, kMarch = 4, kPipe = 5 };
 
 struct Layout {
     bool structured;
     int kernel;             // KernelKind
     int vec;                // vector width of the stencil kernels
-    bool prefetch;          // register stencil: next work item's loads in flight
+    int prefetch;           // register stencil: 0 none, 1 next work item's loads in flight
     int ty, zchunk, n_units, grid;  // staged stencil tiling and grid
     int ring_o, ring_w;             // staged stencil ring depths
     int consumers;                  // staged stencil consumer threads (128 or 256)
@@ -168,5 +168,6 @@ int pass_blocks(int precision, const Layout &L, int n_sm, int blocks_per_sm);
 int pass_occupancy(int precision, const Layout &L, int accumulate);
 size_t staged_smem_bytes(int precision, int ty, int Lh, int ring_o, int ring_w);
 int staged_occupancy(int precision, int vec, size_t smem_bytes, int consumers);  // 0 = does not fit
+size_t pipe_smem_bytes(int precision, int vec);  // dynamic shared memory of the pipelined stencil
 
 }  // namespace hs

@@ -18,6 +18,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "device.cuh"
 
@@ -26,10 +27,13 @@ namespace {
 
 // Register stencil: every operand is loaded from global memory (L1/L2 serve
 // the neighbour rows shared by adjacent work items).  Launch bounds of two
-// resident CTAs per SM (128 registers) measured fastest on GB300.  With PF the loads of
-// the thread's next work item are issued before the current one is
-// computed (two items in flight, unrolled by hand so no operand is copied).
-template <int P, int V, bool MEAS, bool PF>
+// resident CTAs per SM (128 registers) measured fastest on GB300.  Prefetch
+// modes (PF):
+//   0  none;
+//   1  the loads of the thread's next work item are issued before the
+//      current one is computed (two items in flight in registers, unrolled by
+//      hand so no operand is copied).
+template <int P, int V, bool MEAS, int PF>
 __global__ void __launch_bounds__(kBlock, 2) sc_pass_kernel(const PassArgs a) {
     pdl_enter();
     using S = typename Tr<P>::S;
@@ -52,7 +56,7 @@ __global__ void __launch_bounds__(kBlock, 2) sc_pass_kernel(const PassArgs a) {
         }
     };
     uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (!PF) {
+    if (PF == 0) {
         for (; t < n_items; t += stride) {
             StencilItem<P, V> it;
             load_item<P, V>(a, t, own, oth, it);
@@ -70,6 +74,152 @@ __global__ void __launch_bounds__(kBlock, 2) sc_pass_kernel(const PassArgs a) {
             compute(B);
             t += stride;
             if (t >= n_items) break;
+        }
+    }
+    write_partials<C, MEAS>(a, acc.E(), acc.X(), acc.Y(), acc.Z(), acc.n);
+}
+
+// ----------------------------------------------------------------- pipelined stencil pass
+// The register stencil with one landing slot per thread in shared memory: the
+// operands of the thread's next work item travel global -> shared through
+// cp.async while the current item, already in registers, is computed.  Each
+// thread thus keeps one item of loads in flight during its arithmetic without
+// holding a second item in registers (which would not fit in 128 registers).
+// Only the issuing thread reads its slot, so cp.async.wait_all alone orders
+// the copy before the reads (no CTA barrier).  The slot is refilled after the
+// reads of the previous item: a thread's shared-memory reads and its later
+// cp.async go through the load/store pipe in program order, and the copy's
+// shared-memory write lands only when its global data returns.
+//
+// Slot layout (structure of arrays over the CTA's threads, so a warp's
+// accesses to one operand are consecutive): 18 vectors (own s[3], other
+// colour o[3], y-1, y+1, z-1, z+1 rows) at [j][thread], then 3 edge words at
+// [q][thread].  An edge word is one element, or for 2-byte storage the
+// aligned 4-byte pair holding it (cp.async copies 4, 8 or 16 bytes).
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+template <int B>
+__device__ __forceinline__ void cp_async_ca(uint32_t dst, const void *src) {
+    static_assert(B == 4 || B == 8 || B == 16, "cp.async copies 4, 8 or 16 bytes");
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(dst), "l"(src), "n"(B) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+template <int P>
+struct PipeEdge {
+    using S = typename Tr<P>::S;
+    using W = typename std::conditional<(sizeof(S) >= 4), S, uint32_t>::type;
+};
+
+template <int P, int V>
+struct PipeSlot {
+    using S = typename Tr<P>::S;
+    using VT = Vec<S, V>;
+    using W = typename PipeEdge<P>::W;
+    static constexpr size_t kVecBytes = 18u * kBlock * sizeof(VT);
+    static constexpr size_t kBytes = kVecBytes + 3u * kBlock * sizeof(W);
+};
+
+// Issue the copies of work item t's operands into this thread's slot.
+template <int P, int V>
+__device__ __forceinline__ ItemOffsets pipe_issue(const PassArgs &a, uint32_t t, const typename Tr<P>::S *const (&own)[3],
+                                                  const typename Tr<P>::S *const (&oth)[3], uint32_t slot_v,
+                                                  uint32_t slot_e) {
+    using S = typename Tr<P>::S;
+    using Sl = PipeSlot<P, V>;
+    constexpr int VB = (int)sizeof(typename Sl::VT);
+    constexpr int WB = (int)sizeof(typename Sl::W);
+    const uint32_t nxv = a.Lh / V;
+    const uint32_t row = a.div_nxv.div(t);
+    const uint32_t xv = t - row * nxv;
+    const uint32_t z = a.div_ly.div(row);
+    const uint32_t y = row - z * a.Ly;
+    const ItemOffsets f = item_offsets<V>(a, y, z, xv);
+    // for 2-byte storage the edge word starts at the even element of the pair
+    const uint32_t bed_w = (sizeof(S) >= 4) ? f.bed : (f.bed & ~1u);
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        cp_async_ca<VB>(slot_v + (uint32_t)((0 + q) * kBlock * VB), own[q] + f.b0);
+        cp_async_ca<VB>(slot_v + (uint32_t)((3 + q) * kBlock * VB), oth[q] + f.b0);
+        cp_async_ca<VB>(slot_v + (uint32_t)((6 + q) * kBlock * VB), oth[q] + f.bym);
+        cp_async_ca<VB>(slot_v + (uint32_t)((9 + q) * kBlock * VB), oth[q] + f.byp);
+        cp_async_ca<VB>(slot_v + (uint32_t)((12 + q) * kBlock * VB), oth[q] + f.bzm);
+        cp_async_ca<VB>(slot_v + (uint32_t)((15 + q) * kBlock * VB), oth[q] + f.bzp);
+        cp_async_ca<WB>(slot_e + (uint32_t)(q * kBlock * WB), oth[q] + bed_w);
+    }
+    cp_async_commit();
+    return f;
+}
+
+// Read this thread's slot (after cp.async.wait_all) into registers.
+template <int P, int V>
+__device__ __forceinline__ void pipe_read(const typename PipeSlot<P, V>::VT *sv, const typename PipeSlot<P, V>::W *se,
+                                          const ItemOffsets &f, StencilItem<P, V> &it) {
+    using S = typename Tr<P>::S;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        it.s[q] = sv[(0 + q) * kBlock];
+        it.o[q] = sv[(3 + q) * kBlock];
+        it.nym[q] = sv[(6 + q) * kBlock];
+        it.nyp[q] = sv[(9 + q) * kBlock];
+        it.nzm[q] = sv[(12 + q) * kBlock];
+        it.nzp[q] = sv[(15 + q) * kBlock];
+        if constexpr (sizeof(S) >= 4) {
+            it.ed[q] = to_c(se[q * kBlock]);
+        } else {
+            const uint32_t w = se[q * kBlock];
+            const unsigned short bits = (unsigned short)((f.bed & 1u) ? (w >> 16) : (w & 0xffffu));
+            it.ed[q] = to_c(__ushort_as_half(bits));
+        }
+    }
+    it.b0 = f.b0;
+    it.p = f.p;
+    it.site0 = f.site0;
+}
+
+template <int P, int V, bool MEAS>
+__global__ void __launch_bounds__(kBlock, 2) sc_pipe_kernel(const PassArgs a) {
+    pdl_enter();
+    using S = typename Tr<P>::S;
+    using C = typename Tr<P>::C;
+    using Sl = PipeSlot<P, V>;
+    using VT = typename Sl::VT;
+    using W = typename Sl::W;
+    extern __shared__ __align__(16) unsigned char pipe_smem[];
+    const uint32_t n_items = (uint32_t)a.Lz * a.Ly * (a.Lh / V);
+    const int c = a.colour;
+    C J, K, ex, ey, ez, beta;
+    load_params(a, J, K, ex, ey, ez, beta);
+    S *own_w[3] = {(S *)a.own[0], (S *)a.own[1], (S *)a.own[2]};
+    const S *const own[3] = {(const S *)a.own[0], (const S *)a.own[1], (const S *)a.own[2]};
+    const S *const oth[3] = {(const S *)a.oth[0], (const S *)a.oth[1], (const S *)a.oth[2]};
+    const VT *sv = reinterpret_cast<const VT *>(pipe_smem) + threadIdx.x;
+    const W *se = reinterpret_cast<const W *>(pipe_smem + Sl::kVecBytes) + threadIdx.x;
+    const uint32_t slot_v = smem_addr(sv);
+    const uint32_t slot_e = smem_addr(se);
+    SiteAcc<P> acc;
+    const uint32_t stride = gridDim.x * blockDim.x;
+    uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n_items) {
+        ItemOffsets f = pipe_issue<P, V>(a, t, own, oth, slot_v, slot_e);
+        while (true) {
+            cp_async_wait_all();
+            StencilItem<P, V> it;
+            pipe_read<P, V>(sv, se, f, it);
+            const uint32_t tn = t + stride;
+            const bool more = tn < n_items;
+            if (more) f = pipe_issue<P, V>(a, tn, own, oth, slot_v, slot_e);
+            if (update_item<P, V, MEAS>(it.s, it.o, it.nym, it.nyp, it.nzm, it.nzp, it.ed, it.p, it.site0, c, a, J, K,
+                                        ex, ey, ez, beta, acc)) {
+#pragma unroll
+                for (int q = 0; q < 3; ++q) *reinterpret_cast<VT *>(own_w[q] + it.b0) = it.s[q];
+            }
+            if (!more) break;
+            t = tn;
         }
     }
     write_partials<C, MEAS>(a, acc.E(), acc.X(), acc.Y(), acc.Z(), acc.n);
@@ -649,13 +799,16 @@ cudaError_t launch_pdl(void (*kernel)(KArgs...), int grid, int block, size_t sme
     return cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 
+template <int P, int V, int PF>
+cudaError_t launch_sc_pf(const PassArgs &a, int n_blocks, cudaStream_t s, bool meas) {
+    return meas ? launch_pdl(sc_pass_kernel<P, V, true, PF>, n_blocks, kBlock, 0, s, a)
+                : launch_pdl(sc_pass_kernel<P, V, false, PF>, n_blocks, kBlock, 0, s, a);
+}
+
 template <int P, int V>
-cudaError_t launch_sc_v(const PassArgs &a, int n_blocks, cudaStream_t s, bool meas, bool pf) {
-    if (pf)
-        return meas ? launch_pdl(sc_pass_kernel<P, V, true, true>, n_blocks, kBlock, 0, s, a)
-                    : launch_pdl(sc_pass_kernel<P, V, false, true>, n_blocks, kBlock, 0, s, a);
-    return meas ? launch_pdl(sc_pass_kernel<P, V, true, false>, n_blocks, kBlock, 0, s, a)
-                : launch_pdl(sc_pass_kernel<P, V, false, false>, n_blocks, kBlock, 0, s, a);
+cudaError_t launch_sc_v(const PassArgs &a, int n_blocks, cudaStream_t s, bool meas, int pf) {
+    if (pf == 1) return launch_sc_pf<P, V, 1>(a, n_blocks, s, meas);
+    return launch_sc_pf<P, V, 0>(a, n_blocks, s, meas);
 }
 
 template <int P, int V, int NC>
@@ -668,6 +821,13 @@ cudaError_t launch_staged_nc(const Layout &L, const PassArgs &a, cudaStream_t s,
 template <int P, int V>
 cudaError_t launch_staged_v(const Layout &L, const PassArgs &a, cudaStream_t s, bool meas) {
     return L.consumers == 128 ? launch_staged_nc<P, V, 128>(L, a, s, meas) : launch_staged_nc<P, V, 256>(L, a, s, meas);
+}
+
+template <int P, int V>
+cudaError_t launch_pipe_v(const PassArgs &a, int n_blocks, cudaStream_t s, bool meas) {
+    const size_t smem = PipeSlot<P, V>::kBytes;
+    return meas ? launch_pdl(sc_pipe_kernel<P, V, true>, n_blocks, kBlock, smem, s, a)
+                : launch_pdl(sc_pipe_kernel<P, V, false>, n_blocks, kBlock, smem, s, a);
 }
 
 template <int P, int V>
@@ -685,6 +845,16 @@ cudaError_t launch_pass_p(const Layout &L, const PassArgs &a, int n_blocks, cuda
         case 2: return launch_march_v<P, 2>(a, n_blocks, s, meas);
         case 4: if constexpr (P != HS_FP64) return launch_march_v<P, 4>(a, n_blocks, s, meas); break;
         case 8: if constexpr (P == HS_FP16) return launch_march_v<P, 8>(a, n_blocks, s, meas); break;
+        default: break;
+        }
+        return cudaErrorInvalidValue;
+    }
+    if (L.kernel == kPipe) {
+        switch (L.vec) {
+        case 1: if constexpr (P != HS_FP16) return launch_pipe_v<P, 1>(a, n_blocks, s, meas); break;
+        case 2: return launch_pipe_v<P, 2>(a, n_blocks, s, meas);
+        case 4: if constexpr (P != HS_FP64) return launch_pipe_v<P, 4>(a, n_blocks, s, meas); break;
+        case 8: if constexpr (P == HS_FP16) return launch_pipe_v<P, 8>(a, n_blocks, s, meas); break;
         default: break;
         }
         return cudaErrorInvalidValue;
@@ -781,15 +951,48 @@ static int64_t pass_items(const Layout &L) {
     return items;
 }
 
+template <int P, int V, int PF>
+static const void *sc_ptr_pf(bool meas) {
+    return meas ? (const void *)sc_pass_kernel<P, V, true, PF> : (const void *)sc_pass_kernel<P, V, false, PF>;
+}
+
 template <int P, int V>
-static const void *sc_ptr(bool meas, bool pf) {
-    if (pf) return meas ? (const void *)sc_pass_kernel<P, V, true, true> : (const void *)sc_pass_kernel<P, V, false, true>;
-    return meas ? (const void *)sc_pass_kernel<P, V, true, false> : (const void *)sc_pass_kernel<P, V, false, false>;
+static const void *sc_ptr(bool meas, int pf) {
+    if (pf == 1) return sc_ptr_pf<P, V, 1>(meas);
+    return sc_ptr_pf<P, V, 0>(meas);
 }
 
 template <int P, int V>
 static const void *march_ptr(bool meas) {
     return meas ? (const void *)sc_march_kernel<P, V, true> : (const void *)sc_march_kernel<P, V, false>;
+}
+
+template <int P, int V>
+static const void *pipe_ptr(bool meas) {
+    return meas ? (const void *)sc_pipe_kernel<P, V, true> : (const void *)sc_pipe_kernel<P, V, false>;
+}
+
+template <int P>
+static size_t pipe_bytes(int vec) {
+    switch (vec) {
+    case 1: if constexpr (P != HS_FP16) return PipeSlot<P, 1>::kBytes; break;
+    case 2: return PipeSlot<P, 2>::kBytes;
+    case 4: if constexpr (P != HS_FP64) return PipeSlot<P, 4>::kBytes; break;
+    case 8: if constexpr (P == HS_FP16) return PipeSlot<P, 8>::kBytes; break;
+    default: break;
+    }
+    return 0;
+}
+
+// 0 when the pipelined stencil has no variant for this precision and width
+// (a slot vector must be 4, 8 or 16 bytes).
+size_t pipe_smem_bytes(int precision, int vec) {
+    switch (precision) {
+    case HS_FP64: return pipe_bytes<HS_FP64>(vec);
+    case HS_FP32: return pipe_bytes<HS_FP32>(vec);
+    case HS_FP16: return pipe_bytes<HS_FP16>(vec);
+    default: return 0;
+    }
 }
 
 template <int P>
@@ -803,6 +1006,22 @@ static const void *pass_kernel_ptr(const Layout &L, bool meas) {
             break;
         case 8:
             if constexpr (P == HS_FP16) return march_ptr<P, 8>(meas);
+            break;
+        default: break;
+        }
+        return nullptr;
+    }
+    if (L.kernel == kPipe) {
+        switch (L.vec) {
+        case 1:
+            if constexpr (P != HS_FP16) return pipe_ptr<P, 1>(meas);
+            break;
+        case 2: return pipe_ptr<P, 2>(meas);
+        case 4:
+            if constexpr (P != HS_FP64) return pipe_ptr<P, 4>(meas);
+            break;
+        case 8:
+            if constexpr (P == HS_FP16) return pipe_ptr<P, 8>(meas);
             break;
         default: break;
         }
@@ -833,8 +1052,29 @@ int pass_occupancy(int precision, const Layout &L, int accumulate) {
     case HS_FP16: k = pass_kernel_ptr<HS_FP16>(L, accumulate != 0); break;
     default: break;
     }
+    if (!k) return 1;
+    size_t smem = 0;
+    if (L.kernel == kPipe) {
+        // opt in to the slots' dynamic shared memory and ask for a carveout
+        // that holds two CTAs' slots, leaving the rest of the SM's 256 KB to
+        // L1 (the neighbour rows shared by adjacent items)
+        smem = pipe_smem_bytes(precision, L.vec);
+        int dev = 0, per_sm = 0;
+        if (smem == 0 || cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
+            per_sm <= 0)
+            return 0;
+        cudaFuncAttributes fa{};
+        if (cudaFuncGetAttributes(&fa, k) != cudaSuccess) return 0;
+        const size_t per_cta = smem + fa.sharedSizeBytes + 1024;  // + the driver's reserved 1 KB
+        const int pct = std::min(100, (int)((200 * per_cta + (size_t)per_sm - 1) / (size_t)per_sm));
+        if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+            cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, pct) != cudaSuccess)
+            return 0;
+    }
     int blocks = 0;
-    if (!k || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k, kBlock, 0) != cudaSuccess) return 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k, kBlock, smem) != cudaSuccess) return 1;
+    if (L.kernel == kPipe) return blocks;
     return blocks > 0 ? blocks : 1;
 }
 

@@ -233,6 +233,8 @@ def _launch_configs(precision, dims):
         out += [dict(kernel="stencil", vec_width=v, blocks_per_sm=1), dict(kernel="stencil", vec_width=v),
                 dict(kernel="stencil", vec_width=v, prefetch=1), dict(kernel="stencil", vec_width=v, prefetch=1,
                                                                        blocks_per_sm=1)]
+        if 4 <= v * es <= 16:
+            out += [dict(kernel="pipe", vec_width=v), dict(kernel="pipe", vec_width=v, blocks_per_sm=1)]
         for ty in (1, 2, 4):
             if dims[1] % ty == 0:
                 out += [dict(kernel="march", vec_width=v, tile_y=ty), dict(kernel="march", vec_width=v, tile_y=ty,
@@ -254,7 +256,7 @@ def test_launch_configuration_does_not_change_results(precision, dims):
     the autotuner restores the state it perturbs."""
     outs = []
     cfgs = _launch_configs(precision, dims)
-    assert any(c["kernel"] == "staged" for c in cfgs)
+    assert all(any(c["kernel"] == k for c in cfgs) for k in ("staged", "pipe"))
     for cfg in cfgs:
         with hs.Lattice("sc", dims=dims, K=0.1, precision=precision, seed=6) as lat:
             lat.set_launch(**cfg)
