@@ -9,7 +9,8 @@
 // own FP64 reduction slot, so the per-member sums are taken in a fixed order
 // (bit-reproducible).  Colour passes are separated by a grid barrier (the
 // launch is cooperative, so every CTA is resident); every wait on it is
-// bounded and a timeout latches an error word that the host reports.  Data
+// bounded and a timeout latches an error word that the host reports.  A
+// sweep's per-member finalise runs inside the next barrier's wait.  Data
 // written by other CTAs in the same launch is read L2-only (measured faster
 // here than cached loads behind the barrier's GPU-scope fences).
 #include <cuda_runtime.h>
@@ -21,34 +22,42 @@ namespace {
 
 constexpr long long kBarrierCycles = 2000000000LL;  // about one second
 
-// Grid-wide barrier: generation read before arriving; the last arriver resets
-// the count and bumps the generation.  Bounded spin; returns false (and
-// latches the error word) if the generation does not change in time.
-__device__ bool grid_barrier(unsigned int *bar, unsigned int n_ctas, int *error, bool skip_arrival) {
-    __shared__ int s_ok;
+// Grid-wide barrier on a monotonic 64-bit arrival count (zeroed before the
+// launch): barrier k completes when the count reaches n_ctas (k + 1), so
+// nothing is reset inside the kernel.  Arrival: the CTA's threads meet, and
+// thread 0 fences (its CTA's earlier writes become visible GPU-wide first)
+// and adds 1.  Wait: thread 0 polls the count with acquire loads, bounded;
+// on a timeout it latches the error word.  The two halves are separate so a
+// CTA can do work that needs no other CTA between arriving and waiting.
+__device__ __forceinline__ unsigned long long ld_acquire_gpu(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void barrier_arrive(unsigned long long *cnt, bool skip_arrival) {
     __syncthreads();
+    if (threadIdx.x == 0 && !skip_arrival) {  // (test hook: a skipped arrival runs every wait out)
+        __threadfence();
+        atomicAdd(cnt, 1ull);
+    }
+}
+
+__device__ bool barrier_wait(const unsigned long long *cnt, unsigned long long target, int *error) {
+    __shared__ int s_ok;
     if (threadIdx.x == 0) {
         int ok = 1;
-        volatile unsigned int *gen = bar + 1;
-        const unsigned int g = *gen;
-        __threadfence();
-        // (test hook: a skipped arrival leaves every other CTA's wait to run out)
-        if (!skip_arrival && atomicAdd(bar, 1u) == n_ctas - 1u) {
-            atomicExch(bar, 0u);
-            __threadfence();
-            atomicAdd(bar + 1, 1u);
-        } else {
+        if (ld_acquire_gpu(cnt) < target) {
             const long long t0 = clock64();
-            for (uint32_t it = 0; *gen == g; ++it) {
+            for (uint32_t it = 0; ld_acquire_gpu(cnt) < target; ++it) {
                 if (it > (1u << 30) || clock64() - t0 > kBarrierCycles) {
                     ok = 0;
                     atomicExch(error, 1);
                     break;
                 }
-                __nanosleep(20);
+                __nanosleep(32);
             }
         }
-        __threadfence();
         s_ok = ok;
     }
     __syncthreads();
@@ -77,14 +86,64 @@ __device__ __forceinline__ PassArgs member_args(const BatchMember &m, int colour
     return a;
 }
 
+// Finalise sweep s for the members this CTA owns, one warp per member: sum
+// the member's segment slots of both colour passes in a fixed order and
+// update its FP64 accumulator.  Reads slot parity s & 1, which sweep s + 2
+// rewrites only after two more grid barriers that this CTA reaches after
+// finishing here.
+__device__ void finalize_sweep(const BatchArgs &b, int s) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int par = s & 1;
+    for (int r = blockIdx.x * (kBlock / 32) + warp; r < b.n_members; r += gridDim.x * (kBlock / 32)) {
+        const BatchMember &m = b.members[r];
+        double tot[kPartials] = {0.0, 0.0, 0.0, 0.0, 0.0};
+        for (int c = 0; c < 2; ++c)
+            for (int si = m.seg_begin + lane; si < m.seg_end; si += 32)
+#pragma unroll
+                for (int q = 0; q < kPartials; ++q)
+                    tot[q] += __ldcg(b.slots + (((size_t)par * 2 + c) * b.n_segs + si) * kPartials + q);
+#pragma unroll
+        for (int q = 0; q < kPartials; ++q) tot[q] = warp_sum(tot[q]);
+        if (lane == 0) {
+            DevAccum *A = m.acc;
+            A->accepted += tot[4];
+            const double mx = tot[1] / m.n_present, my = tot[2] / m.n_present, mz = tot[3] / m.n_present;
+            const double m2 = mx * mx + my * my + mz * mz;
+            const double am = sqrt(m2);
+            const double me = fabs(mx * m.e[0] + my * m.e[1] + mz * m.e[2]);
+            A->last[0] = tot[0];
+            A->last[1] = mx;
+            A->last[2] = my;
+            A->last[3] = mz;
+            A->last[4] = am;
+            A->last[5] = m2;
+            A->last[6] = m2 * m2;
+            A->last[7] = me;
+            if (s >= b.n_equil) {
+                A->moments[HS_SUM_E] += tot[0];
+                A->moments[HS_SUM_E2] += tot[0] * tot[0];
+                A->moments[HS_SUM_ABSM] += am;
+                A->moments[HS_SUM_M2] += m2;
+                A->moments[HS_SUM_M4] += m2 * m2;
+                A->moments[HS_SUM_MX] += mx;
+                A->moments[HS_SUM_MY] += my;
+                A->moments[HS_SUM_MZ] += mz;
+                A->moments[HS_SUM_ABSME] += me;
+                A->count += 1.0;
+            }
+        }
+    }
+}
+
 __global__ void __launch_bounds__(kBlock, 2) batch_kernel(const BatchArgs b) {
     constexpr int P = HS_FP32;
     constexpr int V = 4;
     using VT = Vec<float, V>;
     __shared__ double s_red[kBlock / 32][kPartials];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned long long *cnt = reinterpret_cast<unsigned long long *>(b.bar);
     for (int s = 0; s < b.n_total; ++s) {
-        const int par = s & 1;
+        const int par = s & 1;  // slot parity this sweep writes
         for (int c = 0; c < 2; ++c) {
             for (int si = b.cta_seg[blockIdx.x]; si < b.cta_seg[blockIdx.x + 1]; ++si) {
                 const BatchSeg sg = b.segs[si];
@@ -133,54 +192,20 @@ __global__ void __launch_bounds__(kBlock, 2) batch_kernel(const BatchArgs b) {
                 __syncthreads();
             }
             const bool skip = b.inject_skip && blockIdx.x == 0 && s == 0 && c == 0;
-            if (!grid_barrier(b.bar, gridDim.x, b.error, skip)) {  // uniform per CTA
+            barrier_arrive(cnt, skip);
+            // the previous sweep's finalise runs while this CTA waits for the
+            // others to finish the first pass of this sweep
+            if (c == 0 && s > 0) finalize_sweep(b, s - 1);
+            const unsigned long long k = 2ull * (unsigned long long)s + (unsigned long long)c;
+            if (!barrier_wait(cnt, (k + 1ull) * gridDim.x, b.error)) {  // uniform per CTA
                 if (threadIdx.x == 0)
                     for (int r = 0; r < b.n_members; ++r) atomicExch(&b.members[r].acc->error, 1);
                 return;
             }
         }
-        // finalise this sweep for the members this CTA owns, one warp per
-        // member (reads parity par; the next sweep writes the other parity)
-        for (int r = blockIdx.x * (kBlock / 32) + warp; r < b.n_members; r += gridDim.x * (kBlock / 32)) {
-            const BatchMember &m = b.members[r];
-            double tot[kPartials] = {0.0, 0.0, 0.0, 0.0, 0.0};
-            for (int c = 0; c < 2; ++c)
-                for (int si = m.seg_begin + lane; si < m.seg_end; si += 32)
-#pragma unroll
-                    for (int q = 0; q < kPartials; ++q)
-                        tot[q] += __ldcg(b.slots + (((size_t)par * 2 + c) * b.n_segs + si) * kPartials + q);
-#pragma unroll
-            for (int q = 0; q < kPartials; ++q) tot[q] = warp_sum(tot[q]);
-            if (lane == 0) {
-                DevAccum *A = m.acc;
-                A->accepted += tot[4];
-                const double mx = tot[1] / m.n_present, my = tot[2] / m.n_present, mz = tot[3] / m.n_present;
-                const double m2 = mx * mx + my * my + mz * mz;
-                const double am = sqrt(m2);
-                const double me = fabs(mx * m.e[0] + my * m.e[1] + mz * m.e[2]);
-                A->last[0] = tot[0];
-                A->last[1] = mx;
-                A->last[2] = my;
-                A->last[3] = mz;
-                A->last[4] = am;
-                A->last[5] = m2;
-                A->last[6] = m2 * m2;
-                A->last[7] = me;
-                if (s >= b.n_equil) {
-                    A->moments[HS_SUM_E] += tot[0];
-                    A->moments[HS_SUM_E2] += tot[0] * tot[0];
-                    A->moments[HS_SUM_ABSM] += am;
-                    A->moments[HS_SUM_M2] += m2;
-                    A->moments[HS_SUM_M4] += m2 * m2;
-                    A->moments[HS_SUM_MX] += mx;
-                    A->moments[HS_SUM_MY] += my;
-                    A->moments[HS_SUM_MZ] += mz;
-                    A->moments[HS_SUM_ABSME] += me;
-                    A->count += 1.0;
-                }
-            }
-        }
     }
+    // the last sweep's finalise, after its last barrier
+    if (b.n_total > 0) finalize_sweep(b, b.n_total - 1);
 }
 
 }  // namespace

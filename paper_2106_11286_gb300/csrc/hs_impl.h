@@ -143,7 +143,7 @@ struct BatchArgs {
     const int *cta_seg;      // CTA c owns segments [cta_seg[c], cta_seg[c+1])
     int n_segs;
     double *slots;           // [sweep parity][colour][segment][kPartials]
-    unsigned int *bar;       // grid barrier: [0] arrivals, [1] generation
+    unsigned int *bar;       // grid barrier: one 64-bit arrival count (two words, 8-byte aligned)
     int *error;              // latched device error (barrier timeout)
     int n_total, n_equil;    // sweeps, of which the first n_equil unmeasured
     int inject_skip;         // test hook: 1 = CTA 0 skips its first barrier arrival
