@@ -410,7 +410,7 @@ def run_variants(args, rank, stream, barrier_sync, world, dev):
         sec = _timed(stream, lambda: lat.sweep(1 / 0.9, args.csr_sweeps))
         kms, nl = hs.hs_read_timing(lat.h)
         mom, cnt = lat.read_accumulator()
-        per_attempt = 3 * 16 + 4 * 8 + 4   # 4-vector spins, 8 int32 neighbours, natural index
+        per_attempt = 3 * 16 + 4 * 8   # 4-vector spins, 8 int32 neighbours (the FP32 path keys Philox by rank)
         out["bcc_nanoparticle"] = {"value": round(n_present * args.csr_sweeps / (sec * 1e9), 3), "unit": UNIT,
                                    "n_spins": n_present, "colours": lat.info.n_colours, "sweeps": args.csr_sweeps,
                                    "hbm_frac": round(per_attempt * n_present / lat.info.n_colours / (kms / nl * 1e-3)
