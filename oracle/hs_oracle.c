@@ -187,28 +187,52 @@ static int wrap(int v, int L, int periodic, int *ok)
     return ((v % L) + L) % L;
 }
 
-int64_t or_sc_neighbours(int Lx, int Ly, int Lz, int periodic, int64_t *row_ptr, int32_t *col)
+/* Neighbours of sc site i in the fixed order -x, +x, -y, +y, -z, +z;
+ * returns how many exist (6 when periodic). */
+int or_sc_site_neighbours(int Lx, int Ly, int Lz, int periodic, int64_t i, int64_t *out)
 {
     static const int off[6][3] = {{-1, 0, 0}, {1, 0, 0}, {0, -1, 0}, {0, 1, 0}, {0, 0, -1}, {0, 0, 1}};
+    const int x = (int)(i % Lx);
+    const int y = (int)((i / Lx) % Ly);
+    const int z = (int)(i / ((int64_t)Lx * Ly));
+    int n = 0;
+    for (int k = 0; k < 6; ++k) {
+        int ok = 1;
+        int nx = wrap(x + off[k][0], Lx, periodic, &ok);
+        int ny = wrap(y + off[k][1], Ly, periodic, &ok);
+        int nz = wrap(z + off[k][2], Lz, periodic, &ok);
+        if (!ok)
+            continue;
+        out[n++] = ((int64_t)nz * Ly + ny) * Lx + nx;
+    }
+    return n;
+}
+
+/* The same for m sites: out[6t..6t+5] (unused slots -1), returns nothing. */
+void or_sc_sites_neighbours(int Lx, int Ly, int Lz, int periodic, int64_t m, const int64_t *sites, int64_t *out)
+{
+    for (int64_t t = 0; t < m; ++t) {
+        const int n = or_sc_site_neighbours(Lx, Ly, Lz, periodic, sites[t], &out[6 * t]);
+        for (int k = n; k < 6; ++k)
+            out[6 * t + k] = -1;
+    }
+}
+
+int64_t or_sc_neighbours(int Lx, int Ly, int Lz, int periodic, int64_t *row_ptr, int32_t *col)
+{
+    const int64_t n_sites = (int64_t)Lx * Ly * Lz;
     int64_t nnz = 0;
-    int64_t i = 0;
     row_ptr[0] = 0;
-    for (int z = 0; z < Lz; ++z)
-        for (int y = 0; y < Ly; ++y)
-            for (int x = 0; x < Lx; ++x, ++i) {
-                for (int k = 0; k < 6; ++k) {
-                    int ok = 1;
-                    int nx = wrap(x + off[k][0], Lx, periodic, &ok);
-                    int ny = wrap(y + off[k][1], Ly, periodic, &ok);
-                    int nz = wrap(z + off[k][2], Lz, periodic, &ok);
-                    if (!ok)
-                        continue;
-                    if (col)
-                        col[nnz] = (int32_t)(((int64_t)nz * Ly + ny) * Lx + nx);
-                    ++nnz;
-                }
-                row_ptr[i + 1] = nnz;
-            }
+    for (int64_t i = 0; i < n_sites; ++i) {
+        int64_t nb[6];
+        const int n = or_sc_site_neighbours(Lx, Ly, Lz, periodic, i, nb);
+        for (int k = 0; k < n; ++k) {
+            if (col)
+                col[nnz] = (int32_t)nb[k];
+            ++nnz;
+        }
+        row_ptr[i + 1] = nnz;
+    }
     return nnz;
 }
 
@@ -369,6 +393,65 @@ static double site_energy(const double s[3], const double h[3], double J, double
 }
 
 /* ------------------------------------------------------------------------ */
+/* Metropolis steps (ii)-(iii) at one site whose local field h (the sum of  */
+/* its present neighbours' spins, step (i)) is given: draw the trial from   */
+/* the schedule of `mode` (see or_sweep), take dH from Eq. 1 and accept if  */
+/* dH <= 0, else iff P <= exp(-beta dH).  Updates s in place on acceptance; */
+/* returns 1 if accepted.  *dH_out gets dH; *in_band is 1 for a dH > 0      */
+/* decision with |beta dH + ln P| < band.                                   */
+/* ------------------------------------------------------------------------ */
+int or_site_update(int mode, uint64_t seed, uint32_t replica, uint64_t site, uint64_t rank, uint64_t sweep,
+                   uint32_t colour, double J, double K, const double e[3], double beta, double band,
+                   const double h[3], double s[3], double *dH_out, int *in_band)
+{
+    double u[3];
+    or_trial_uniforms(mode, seed, replica, site, rank, sweep, colour, u);
+    double trial[3];
+    or_sphere_point(u[0], u[1], trial);
+    if (mode == 2) {
+        trial[0] = or_round_half(trial[0]);
+        trial[1] = or_round_half(trial[1]);
+        trial[2] = or_round_half(trial[2]);
+    }
+    double dH = site_energy(trial, h, J, K, e) - site_energy(s, h, J, K, e);
+    double P = u[2];
+    int accept;
+    *in_band = 0;
+    if (dH <= 0.0) {
+        accept = 1;
+    } else {
+        accept = (P <= exp(-beta * dH));
+        if (band > 0.0 && P > 0.0 && fabs(beta * dH + log(P)) < band)
+            *in_band = 1;
+    }
+    if (accept) {
+        s[0] = trial[0];
+        s[1] = trial[1];
+        s[2] = trial[2];
+    }
+    *dH_out = dH;
+    return accept;
+}
+
+/* The same for m sampled sites at once (site t: natural index site[t],
+ * rank rank[t] among the present sites of its colour colour[t], local field
+ * h[3t..3t+2], spin s[3t..3t+2] updated in place); accepted[t] and
+ * in_band[t] get the decisions. */
+void or_sites_update(int64_t m, const int64_t *site, const int64_t *rank, const int32_t *colour, const double *h,
+                     double *s, int mode, uint64_t seed, uint32_t replica, uint64_t sweep, double J, double K,
+                     const double e[3], double beta, double band, uint8_t *accepted, uint8_t *in_band)
+{
+    for (int64_t t = 0; t < m; ++t) {
+        double dH;
+        int b;
+        accepted[t] = (uint8_t)or_site_update(mode, seed, replica, (uint64_t)site[t], (uint64_t)rank[t], sweep,
+                                              (uint32_t)colour[t], J, K, e, beta, band, &h[3 * t], &s[3 * t], &dH,
+                                              &b);
+        in_band[t] = (uint8_t)b;
+    }
+}
+
+/* ------------------------------------------------------------------------ */
 /* One Metropolis sweep: colour classes 0..n_colours-1 in order, present    */
 /* sites of the class in ascending natural index.                           */
 /*   mode 0: FP64 random-number schedule, spins kept in FP64               */
@@ -406,37 +489,18 @@ int64_t or_sweep(int64_t n, const int64_t *row_ptr, const int32_t *col, const in
                 h[1] += S[3 * (int64_t)j + 1];
                 h[2] += S[3 * (int64_t)j + 2];
             }
-            /* step (ii): random new orientation */
-            double u[3];
-            or_trial_uniforms(mode, seed, replica, (uint64_t)i, my_rank, sweep, (uint32_t)c, u);
-            double trial[3];
-            or_sphere_point(u[0], u[1], trial);
-            if (mode == 2) {
-                trial[0] = or_round_half(trial[0]);
-                trial[1] = or_round_half(trial[1]);
-                trial[2] = or_round_half(trial[2]);
-            }
-            /* step (iii): energy change from Eq. 1 and the acceptance test */
-            double *s = &S[3 * i];
-            double dH = site_energy(trial, h, J, K, e) - site_energy(s, h, J, K, e);
-            double P = u[2];
-            int accept;
-            if (dH <= 0.0) {
-                accept = 1;
-            } else {
-                accept = (P <= exp(-beta * dH));
-                if (band > 0.0 && P > 0.0 && fabs(beta * dH + log(P)) < band) {
-                    ++bands;
-                    if (band_site)
-                        band_site[i] = 1;
-                }
-            }
-            if (accept) {
-                s[0] = trial[0];
-                s[1] = trial[1];
-                s[2] = trial[2];
+            /* steps (ii)-(iii) */
+            double dH;
+            int in_band;
+            if (or_site_update(mode, seed, replica, (uint64_t)i, my_rank, sweep, (uint32_t)c, J, K, e, beta, band,
+                               h, &S[3 * i], &dH, &in_band)) {
                 dH_total += dH;
                 ++accepted;
+            }
+            if (in_band) {
+                ++bands;
+                if (band_site)
+                    band_site[i] = 1;
             }
         }
     }

@@ -82,6 +82,13 @@ def lib():
                                ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int,
                                ctypes.c_double, dp, dp, i64p, u8p]
         L.or_sweep.restype = ctypes.c_int64
+        L.or_sc_sites_neighbours.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                             ctypes.c_int64, i64p, i64p]
+        L.or_sc_sites_neighbours.restype = None
+        L.or_sites_update.argtypes = [ctypes.c_int64, i64p, i64p, i32p, dp, dp, ctypes.c_int, ctypes.c_uint64,
+                                      ctypes.c_uint32, ctypes.c_uint64, ctypes.c_double, ctypes.c_double, dp,
+                                      ctypes.c_double, ctypes.c_double, u8p, u8p]
+        L.or_sites_update.restype = None
         L.or_energy.argtypes = [ctypes.c_int64, i64p, i32p, u8p, ctypes.c_double, ctypes.c_double, dp, dp]
         L.or_energy.restype = ctypes.c_double
         L.or_spin_sum.argtypes = [ctypes.c_int64, u8p, dp, dp]
@@ -208,6 +215,37 @@ def sweep(g: Graph, S: np.ndarray, *, J: float, K: float, e, beta: float, seed: 
                          _p(S, ctypes.c_double), ctypes.byref(sdh), ctypes.byref(nb),
                          _p(band_site, ctypes.c_uint8))
     return int(acc), sdh.value, nb.value
+
+
+def sc_site_neighbours(dims, periodic: bool, sites) -> np.ndarray:
+    """sc neighbours of the given natural indices, order -x, +x, -y, +y, -z, +z
+    (m x 6 int64, -1 where an open boundary drops one)."""
+    sites = np.ascontiguousarray(sites, dtype=np.int64)
+    out = np.empty((len(sites), 6), dtype=np.int64)
+    lib().or_sc_sites_neighbours(int(dims[0]), int(dims[1]), int(dims[2]), int(bool(periodic)), len(sites),
+                                 _p(sites, ctypes.c_int64), _p(out, ctypes.c_int64))
+    return out
+
+
+def sites_update(sites, ranks, colours, h, S, *, J: float, K: float, e, beta: float, seed: int,
+                 sweep_index: int, replica: int = 0, mode: int = MODE_FP64, band: float = 0.0):
+    """Metropolis steps (ii)-(iii) at sampled sites whose local fields h (m x 3,
+    step (i)) are given, exactly as one sweep applies them.  S (m x 3) is
+    updated in place; returns (accepted, in_band) as bool arrays."""
+    sites = np.ascontiguousarray(sites, dtype=np.int64)
+    ranks = np.ascontiguousarray(ranks, dtype=np.int64)
+    colours = np.ascontiguousarray(colours, dtype=np.int32)
+    h = np.ascontiguousarray(h, dtype=np.float64)
+    assert S.dtype == np.float64 and S.flags.c_contiguous and S.shape == (len(sites), 3)
+    ev = np.ascontiguousarray(e, dtype=np.float64)
+    ev = ev / np.linalg.norm(ev)
+    acc = np.zeros(len(sites), dtype=np.uint8)
+    band_flag = np.zeros(len(sites), dtype=np.uint8)
+    lib().or_sites_update(len(sites), _p(sites, ctypes.c_int64), _p(ranks, ctypes.c_int64),
+                          _p(colours, ctypes.c_int32), _p(h, ctypes.c_double), _p(S, ctypes.c_double), int(mode),
+                          int(seed), int(replica), int(sweep_index), float(J), float(K), _p(ev, ctypes.c_double),
+                          float(beta), float(band), _p(acc, ctypes.c_uint8), _p(band_flag, ctypes.c_uint8))
+    return acc.astype(bool), band_flag.astype(bool)
 
 
 def energy(g: Graph, S: np.ndarray, *, J: float, K: float, e) -> float:
