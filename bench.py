@@ -393,6 +393,29 @@ def run_variants(args, rank, stream, barrier_sync, world, dev):
         ladder[prec]["bias_E_per_spin_vs_fp64"] = ladder[prec]["E_per_spin"] - ladder["fp64"]["E_per_spin"]
         ladder[prec]["bias_absM_vs_fp64"] = ladder[prec]["absM"] - ladder["fp64"]["absM"]
     out["sc464"] = ladder
+    # (2b) beyond 10^8 spins on one GPU: sc 1024^3 (1,073,741,824 spins, 12.9 GB of FP32 state),
+    #      the headline's parameters, autotuned launch
+    if not args.no_big:
+        L6 = 1024
+        N6 = L6 ** 3
+        lat = hs.Lattice("sc", dims=(L6,) * 3, J=WORKLOAD["J"], K=WORKLOAD["K"], e=WORKLOAD["e"], precision="fp32",
+                         seed=6, replica=rank, stream=stream)
+        beta6 = 1.0 / WORKLOAD["T"]
+        lat.init()
+        lat.accumulate(True)
+        launch = lat.launch if args.no_autotune else lat.autotune(beta6, 2)
+        lat.sweep(beta6, 3)
+        lat.reset_accumulator()
+        hs.hs_enable_timing(lat.h, True)
+        sec = _timed(stream, lambda: lat.sweep(beta6, args.huge_sweeps))
+        kms, nl = hs.hs_read_timing(lat.h)
+        mom, cnt = lat.read_accumulator()
+        out["sc1024"] = {"value": round(N6 * args.huge_sweeps / (sec * 1e9), 3), "unit": UNIT, "n_spins": N6,
+                         "sweeps": args.huge_sweeps, "device_bytes": 3 * 2 * (N6 // 2) * 4,
+                         "hbm_frac": round(3 * BYTES_PER_SPIN["fp32"] * (N6 // 2) / (kms / nl * 1e-3) / 1e9 /
+                                           peaks["hbm_gbs"], 4),
+                         "E_per_spin": mom[0] / cnt / N6, "absM": mom[2] / cnt, "launch": launch}
+        lat.close()
     # (3) bcc nanoparticle: radius 110 in a 232^3-cell box, open surface, 1 % vacancies (seed 3),
     #     CSR neighbour list, K = 0.2 along (1,1,1), T = 0.9, FP32
     if not args.no_csr:
@@ -490,6 +513,8 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--no-big", action="store_true", help="skip the sc 1024^3 variant")
+    ap.add_argument("--huge-sweeps", type=int, default=20, help="timed sweeps of the sc 1024^3 variant")
     ap.add_argument("--no-csr", action="store_true")
     ap.add_argument("--batch-sweeps", type=int, default=2000)
     ap.add_argument("--big-sweeps", type=int, default=200)

@@ -1,0 +1,46 @@
+"""The scan module's statistics on synthetic samples with known answers
+(no GPU): jackknife errors, Binder cumulant limits, curve crossing, and the
+log-log slope that gives beta/nu at T_c."""
+import numpy as np
+import pytest
+
+from paper_2106_11286_gb300 import scan
+
+
+def test_jackknife_of_the_mean_is_the_standard_error():
+    x = np.random.default_rng(1).normal(3.0, 2.0, 400)
+    val, err = scan.jackknife(lambda m: m, x)
+    assert val == pytest.approx(x.mean())
+    assert err == pytest.approx(x.std(ddof=1) / np.sqrt(len(x)), rel=1e-12)
+
+
+def test_jackknife_of_a_ratio_matches_the_delta_method():
+    rng = np.random.default_rng(2)
+    a, b = rng.normal(4.0, 0.5, 4000), rng.normal(2.0, 0.3, 4000)
+    val, err = scan.jackknife(lambda p, q: p / q, a, b)
+    delta = np.sqrt((0.5 / 2.0) ** 2 + (4.0 * 0.3 / 4.0) ** 2) / np.sqrt(len(a))
+    assert val == pytest.approx(2.0, abs=4 * delta)
+    assert err == pytest.approx(delta, rel=0.1)
+
+
+def test_binder_limits():
+    # ordered phase: |M| fixed, <M^4> = <M^2>^2 -> U4 = 2/3
+    assert scan.binder(0.25, 0.0625) == pytest.approx(2.0 / 3.0)
+    # disordered phase: M an isotropic 3-component Gaussian, <|M|^4> / <|M|^2>^2 = 15 / 9
+    M = np.random.default_rng(3).normal(size=(400000, 3))
+    r2 = (M ** 2).sum(1)
+    assert scan.moment_ratio(r2.mean(), (r2 ** 2).mean()) == pytest.approx(5.0 / 3.0, rel=0.01)
+    assert scan.binder(r2.mean(), (r2 ** 2).mean()) == pytest.approx(4.0 / 9.0, abs=0.005)
+
+
+def test_crossing_of_two_lines():
+    T = np.linspace(1.0, 2.0, 11)
+    u1 = 0.6 - 0.2 * (T - 1.37)
+    u2 = 0.6 - 0.5 * (T - 1.37)
+    assert scan.crossing(T, u1, u2) == pytest.approx(1.37, abs=1e-12)
+    assert np.isnan(scan.crossing(T, u1, u1 + 1.0))
+
+
+def test_log_slope_recovers_a_power_law():
+    L = np.array([16, 24, 32, 48, 64])
+    assert scan.log_slope(L, 0.8 * L ** -0.518) == pytest.approx(-0.518, abs=1e-12)
