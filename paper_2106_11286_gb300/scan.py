@@ -127,6 +127,16 @@ def log_slope(x, y) -> float:
     return float(np.linalg.lstsq(A, ly, rcond=None)[0][0])
 
 
+def power_law_exponent(temps, M, Tc: float) -> float:
+    """The fit the paper applies to its M(T) curves: beta from
+    M ~ (Tc - T)^beta, least squares of log M on log(Tc - T) over the scan
+    points below Tc."""
+    t = np.asarray(temps, dtype=np.float64)
+    m = np.asarray(M, dtype=np.float64)
+    below = t < Tc
+    return log_slope(Tc - t[below], m[below])
+
+
 def fss_exponent(scan: Scan, j: int, sizes_idx=None):
     """-d log<|M|> / d log L at temperature index j (at T_c this is beta/nu),
     with a jackknife error over aligned samples of all sizes."""

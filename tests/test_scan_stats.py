@@ -44,3 +44,9 @@ def test_crossing_of_two_lines():
 def test_log_slope_recovers_a_power_law():
     L = np.array([16, 24, 32, 48, 64])
     assert scan.log_slope(L, 0.8 * L ** -0.518) == pytest.approx(-0.518, abs=1e-12)
+
+
+def test_power_law_fit_below_tc():
+    T = np.array([1.0, 1.1, 1.2, 1.3, 1.4, 1.5, 1.6])
+    M = np.where(T < 1.445, 1.3 * np.clip(1.445 - T, 1e-9, None) ** 0.364, 0.01)
+    assert scan.power_law_exponent(T, M, 1.445) == pytest.approx(0.364, abs=1e-12)
