@@ -314,6 +314,42 @@ int hs_sweep_sc_fp32_noalloc(float *planes, const int32_t dims[3], const hs_para
                              uint64_t seed, uint32_t replica, uint64_t first_sweep, int64_t n_sweeps,
                              double *d_out, void *cuda_stream);
 
+/* One colour pass of the current sweep (Metropolis steps (i)-(iii) over
+ * colour class `colour`); the pass of the last colour finalises the sweep's
+ * fused reductions and advances the sweep counter.  hs_sweep(h, beta, 1) is
+ * the passes 0 .. C-1 in order.  A z-slab (below) sweeps this way, its halo
+ * planes refreshed between the passes. */
+int hs_sweep_pass(hs_lattice *h, double beta, int colour);
+
+/* Domain decomposition of a periodic sc lattice along z: a slab handle owns
+ * the global planes z0 .. z0+nz-1 of an Lx x Ly x Lz lattice (dims as for
+ * hs_lattice_create, all even) and stores one halo plane of each colour
+ * below and above them.  Every own site keeps its global natural index,
+ * colour, neighbour order and random numbers, so a set of slabs that
+ * exchanges halos between colour passes reproduces the whole lattice's
+ * chain bit for bit.  A slab runs the register stencil; hs_sweep,
+ * hs_measure and hs_batch_create reject it, and hs_autotune leaves it
+ * unchanged.  hs_get_spins / hs_set_spins / hs_init_spins work on its own
+ * planes (Lx Ly nz spins in natural order).  Halos read as zero until
+ * first written. */
+int hs_slab_create(hs_lattice **out, const int32_t dims[3], int32_t z0, int32_t nz, const hs_params *p,
+                   int precision, uint64_t seed, uint32_t replica, void *cuda_stream);
+/* Device address and size of one component plane of a slab:
+ * which = 0 halo below, 1 first own plane, 2 last own plane, 3 halo above.
+ * Planes are [Ly][Lx/2] of the storage type in the colour-major layout; a
+ * multi-device run sends these (own 1 / 2 to the neighbours' halos 3 / 0). */
+int hs_slab_plane(const hs_lattice *h, int colour, int component, int which, void **dev_ptr, size_t *bytes);
+/* Copy the three component planes of colour `colour` from plane src_which of
+ * src to plane dst_which of dst (same lattice and device), on dst's stream:
+ * the halo exchange of slabs that share a device. */
+int hs_slab_copy_plane(hs_lattice *dst, int dst_which, const hs_lattice *src, int src_which, int colour);
+/* FP64 sums of the last finalised fused reduction (the last hs_sweep or
+ * hs_sweep_pass sweep, or hs_measure): out = {E share, sum S_x, sum S_y,
+ * sum S_z, accepted moves of that sweep}.  Summed over the slabs of a
+ * lattice they give its E (every bond is counted at its colour-1 end, which
+ * one slab owns) and M = sum S / N. */
+int hs_read_sums(hs_lattice *h, double out[5]);
+
 /* Test hooks for the bounded device-side waits (failure detection without a
  * GPU fault).  hs_lattice_inject_timeout: the next colour pass of a lattice
  * running the staged kernel expects 16 bytes more than it copies, so the

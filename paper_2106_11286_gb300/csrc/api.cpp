@@ -243,6 +243,11 @@ PassArgs base_args(const hs_lattice *h) {
     if (L.structured) {
         a.div_nxv = hs::FastDiv((uint32_t)(L.Lh / L.vec));
         a.div_ly = hs::FastDiv((uint32_t)L.Ly);
+        // a z-slab's array plane z holds global plane z - z_off + z0
+        a.nz = L.nz;
+        a.z_off = L.slab ? 1 : 0;
+        a.zpar = (L.z0 - a.z_off) & 1;
+        a.site_off = (uint32_t)((int64_t)(L.z0 - a.z_off) * L.Ly * L.Lx);
         a.ty = L.ty;
         a.zchunk = L.zchunk;
         a.n_units = L.n_units;
@@ -281,8 +286,20 @@ int setup_structured(hs_lattice *h) {
     L.Lz = h->dims[2];
     L.Lh = L.Lx / 2;
     L.vec = 1;
+    if (!L.slab) {
+        L.nz = L.Lz;
+        L.z0 = 0;
+        L.Lz_glob = L.Lz;
+    } else {
+        L.Lz = L.nz + 2;  // halo planes at array planes 0 and nz + 1
+    }
     const int64_t plane = (int64_t)L.Lz * L.Ly * L.Lh;
-    return h->alloc(&L.planes, (size_t)plane * 6 * es);
+    int st = h->alloc(&L.planes, (size_t)plane * 6 * es);
+    if (st == HS_OK && L.slab) {  // halos read as zero until the first exchange
+        cudaError_t e = cudaMemsetAsync(L.planes, 0, (size_t)plane * 6 * es, h->stream);
+        if (e != cudaSuccess) st = cuda_fail(e, "cudaMemsetAsync");
+    }
+    return st;
 }
 
 int setup_table(hs_lattice *h, Graph &g, const uint8_t *mask) {
@@ -530,9 +547,15 @@ int hs_colour_greedy(int64_t n, const int64_t *row_ptr, const int32_t *col_idx, 
     return HS_OK;
 }
 
-int hs_lattice_create(hs_lattice **out, int type, const int32_t dims[3], int periodic, const int64_t *row_ptr,
-                      const int32_t *col_idx, int64_t n_sites, const uint8_t *site_mask, const hs_params *p,
-                      int precision, uint64_t seed, uint32_t replica, void *cuda_stream) {
+namespace {
+// z-slab of a periodic sc lattice: own global planes z0 .. z0 + nz - 1
+struct SlabSpec {
+    int z0, nz;
+};
+
+int lattice_create(hs_lattice **out, int type, const int32_t dims[3], int periodic, const int64_t *row_ptr,
+                   const int32_t *col_idx, int64_t n_sites, const uint8_t *site_mask, const hs_params *p,
+                   int precision, uint64_t seed, uint32_t replica, void *cuda_stream, const SlabSpec *slab) {
     if (!out) return fail(HS_E_INVALID, "out is NULL");
     *out = nullptr;
     if (!p) return fail(HS_E_INVALID, "params are NULL");
@@ -588,10 +611,16 @@ int hs_lattice_create(hs_lattice **out, int type, const int32_t dims[3], int per
     int st = HS_OK;
     Layout &L = h->L;
     L.structured = structured;
+    if (slab) {
+        L.slab = true;
+        L.z0 = slab->z0;
+        L.nz = slab->nz;
+        L.Lz_glob = dims[2];
+    }
     try {
         if (structured) {
             L.n_colours = 2;
-            L.n_sites = L.n_present = (int64_t)dims[0] * dims[1] * dims[2];
+            L.n_sites = L.n_present = (int64_t)dims[0] * dims[1] * (slab ? slab->nz : dims[2]);
             st = setup_structured(h);
         } else {
             if (type == HS_CSR) {
@@ -632,6 +661,25 @@ int hs_lattice_create(hs_lattice **out, int type, const int32_t dims[3], int per
     *out = h;
     return HS_OK;
 }
+}  // namespace
+
+int hs_lattice_create(hs_lattice **out, int type, const int32_t dims[3], int periodic, const int64_t *row_ptr,
+                      const int32_t *col_idx, int64_t n_sites, const uint8_t *site_mask, const hs_params *p,
+                      int precision, uint64_t seed, uint32_t replica, void *cuda_stream) {
+    return lattice_create(out, type, dims, periodic, row_ptr, col_idx, n_sites, site_mask, p, precision, seed,
+                          replica, cuda_stream, nullptr);
+}
+
+int hs_slab_create(hs_lattice **out, const int32_t dims[3], int32_t z0, int32_t nz, const hs_params *p,
+                   int precision, uint64_t seed, uint32_t replica, void *cuda_stream) {
+    if (!out) return fail(HS_E_INVALID, "out is NULL");
+    *out = nullptr;
+    if (!dims) return fail(HS_E_INVALID, "dims are NULL");
+    if (nz < 1 || z0 < 0 || (int64_t)z0 + nz > dims[2]) return fail(HS_E_INVALID, "slab planes must lie in [0, Lz)");
+    const SlabSpec spec{z0, nz};
+    return lattice_create(out, HS_SC, dims, 1, nullptr, nullptr, 0, nullptr, p, precision, seed, replica,
+                          cuda_stream, &spec);
+}
 
 void hs_lattice_destroy(hs_lattice *h) { delete h; }
 
@@ -644,62 +692,132 @@ int hs_init_spins(hs_lattice *h, int mode) {
     return HS_OK;
 }
 
+namespace {
+// Launch colour pass c of sweep index `sweep` (the last colour finalises the
+// fused reductions).
+int run_pass(hs_lattice *h, PassArgs &a, uint32_t sweep, int c) {
+    const Layout &L = h->L;
+    a.sweep = sweep;
+    a.colour = c;
+    a.pass = c;
+    a.finish = (c == L.n_colours - 1);
+    if (L.structured) {
+        const size_t es = hs::storage_size(h->precision);
+        const int64_t plane = (int64_t)L.Lz * L.Ly * L.Lh;
+        char *base = static_cast<char *>(L.planes);
+        for (int q = 0; q < 3; ++q) {
+            a.own[q] = base + (size_t)(3 * c + q) * plane * es;
+            a.oth[q] = base + (size_t)(3 * (1 - c) + q) * plane * es;
+        }
+    } else {
+        a.begin = L.colour_begin[c];
+        a.end = L.colour_begin[c + 1];
+        a.colour_begin = L.colour_begin[c];
+    }
+    if (h->timing) {
+        int st = record_event(h);
+        if (st) return st;
+    }
+    a.inject_extra_tx = 0;
+    if (h->inject_timeout && L.kernel == hs::kStaged) {
+        a.inject_extra_tx = 16;
+        h->inject_timeout = 0;
+    }
+    HS_CUDA(hs::launch_pass(h->precision, L, a, h->n_blocks, h->stream));
+    if (h->timing) {
+        int st = record_event(h);
+        if (st) return st;
+    }
+    return HS_OK;
+}
+
+int check_beta(double beta) {
+    if (!(beta >= 0.0) || !std::isfinite(beta)) return fail(HS_E_INVALID, "beta must be finite and >= 0");
+    return HS_OK;
+}
+}  // namespace
+
 int hs_sweep(hs_lattice *h, double beta, int64_t n_sweeps) {
     if (!h) return fail(HS_E_INVALID, "null handle");
-    if (!(beta >= 0.0) || !std::isfinite(beta)) return fail(HS_E_INVALID, "beta must be finite and >= 0");
+    if (int st = check_beta(beta)) return st;
     if (n_sweeps < 0) return fail(HS_E_INVALID, "n_sweeps must be >= 0");
+    if (h->L.slab && n_sweeps > 0)
+        return fail(HS_E_INVALID, "a slab sweeps pass by pass (hs_sweep_pass), its halos refreshed in between");
     h->last_n_sweeps = n_sweeps;
     HS_CUDA(cudaMemsetAsync(&h->acc->accepted, 0, sizeof(double), h->stream));
     if (n_sweeps == 0 || h->L.n_present == 0) {
         h->sweep += (uint64_t)n_sweeps;
         return HS_OK;
     }
-    const Layout &L = h->L;
     PassArgs a = base_args(h);
     a.beta = beta;
     a.fbeta = (float)beta;
     a.accumulate = h->accumulate;
-    const size_t es = hs::storage_size(h->precision);
-    const int64_t plane = (int64_t)L.Lz * L.Ly * L.Lh;
-    for (int64_t s = 0; s < n_sweeps; ++s) {
-        a.sweep = (uint32_t)(h->sweep + (uint64_t)s);
-        for (int c = 0; c < L.n_colours; ++c) {
-            a.colour = c;
-            a.pass = c;
-            a.finish = (c == L.n_colours - 1);
-            if (L.structured) {
-                char *base = static_cast<char *>(L.planes);
-                for (int q = 0; q < 3; ++q) {
-                    a.own[q] = base + (size_t)(3 * c + q) * plane * es;
-                    a.oth[q] = base + (size_t)(3 * (1 - c) + q) * plane * es;
-                }
-            } else {
-                a.begin = L.colour_begin[c];
-                a.end = L.colour_begin[c + 1];
-                a.colour_begin = L.colour_begin[c];
-            }
-            if (h->timing) {
-                int st = record_event(h);
-                if (st) return st;
-            }
-            a.inject_extra_tx = 0;
-            if (h->inject_timeout && L.kernel == hs::kStaged) {
-                a.inject_extra_tx = 16;
-                h->inject_timeout = 0;
-            }
-            HS_CUDA(hs::launch_pass(h->precision, L, a, h->n_blocks, h->stream));
-            if (h->timing) {
-                int st = record_event(h);
-                if (st) return st;
-            }
-        }
-    }
+    for (int64_t s = 0; s < n_sweeps; ++s)
+        for (int c = 0; c < h->L.n_colours; ++c)
+            if (int st = run_pass(h, a, (uint32_t)(h->sweep + (uint64_t)s), c)) return st;
     h->sweep += (uint64_t)n_sweeps;
     return HS_OK;
 }
 
+int hs_sweep_pass(hs_lattice *h, double beta, int colour) {
+    if (!h) return fail(HS_E_INVALID, "null handle");
+    if (int st = check_beta(beta)) return st;
+    if (colour < 0 || colour >= h->L.n_colours) return fail(HS_E_INVALID, "colour out of range");
+    if (colour == 0) {
+        h->last_n_sweeps = 1;
+        HS_CUDA(cudaMemsetAsync(&h->acc->accepted, 0, sizeof(double), h->stream));
+    }
+    if (h->L.n_present > 0) {
+        PassArgs a = base_args(h);
+        a.beta = beta;
+        a.fbeta = (float)beta;
+        a.accumulate = h->accumulate;
+        if (int st = run_pass(h, a, (uint32_t)h->sweep, colour)) return st;
+    }
+    if (colour == h->L.n_colours - 1) h->sweep += 1;
+    return HS_OK;
+}
+
+int hs_slab_plane(const hs_lattice *h, int colour, int component, int which, void **dev_ptr, size_t *bytes) {
+    if (!h || !dev_ptr || !bytes) return fail(HS_E_INVALID, "null argument");
+    const Layout &L = h->L;
+    if (!L.slab) return fail(HS_E_INVALID, "not a slab");
+    if (colour < 0 || colour > 1 || component < 0 || component > 2 || which < 0 || which > 3)
+        return fail(HS_E_INVALID, "colour 0/1, component 0..2, which 0..3");
+    const size_t es = hs::storage_size(h->precision);
+    const size_t plane_elems = (size_t)L.Ly * L.Lh;
+    const int z = which == 0 ? 0 : (which == 1 ? 1 : (which == 2 ? L.nz : L.nz + 1));
+    *dev_ptr = static_cast<char *>(L.planes) + ((size_t)(3 * colour + component) * L.Lz + z) * plane_elems * es;
+    *bytes = plane_elems * es;
+    return HS_OK;
+}
+
+int hs_slab_copy_plane(hs_lattice *dst, int dst_which, const hs_lattice *src, int src_which, int colour) {
+    if (!dst || !src) return fail(HS_E_INVALID, "null handle");
+    if (!dst->L.slab || !src->L.slab) return fail(HS_E_INVALID, "not a slab");
+    if (dst->precision != src->precision || dst->L.Lx != src->L.Lx || dst->L.Ly != src->L.Ly ||
+        dst->device != src->device)
+        return fail(HS_E_INVALID, "slabs of different lattices or devices");
+    for (int q = 0; q < 3; ++q) {
+        void *d = nullptr, *sp = nullptr;
+        size_t nb = 0, ns = 0;
+        if (int st = hs_slab_plane(dst, colour, q, dst_which, &d, &nb)) return st;
+        if (int st = hs_slab_plane(src, colour, q, src_which, &sp, &ns)) return st;
+        HS_CUDA(cudaMemcpyAsync(d, sp, nb, cudaMemcpyDeviceToDevice, dst->stream));
+    }
+    return HS_OK;
+}
+
+int hs_read_sums(hs_lattice *h, double out[5]) {
+    if (!h || !out) return fail(HS_E_INVALID, "null argument");
+    HS_CUDA(cudaMemcpyAsync(out, h->acc->sums, 5 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    return check_device_error(h);
+}
+
 int hs_measure(hs_lattice *h, hs_measurement *out) {
     if (!h || !out) return fail(HS_E_INVALID, "null argument");
+    if (h->L.slab) return fail(HS_E_INVALID, "a slab measures through its fused sums (hs_read_sums)");
     std::memset(out, 0, sizeof(*out));
     out->n_sites = h->L.n_present;
     if (h->L.n_present == 0) return HS_OK;
@@ -840,6 +958,8 @@ int hs_set_launch(hs_lattice *h, const hs_launch *cfg) {
     if (!h || !cfg) return fail(HS_E_INVALID, "null argument");
     if (cfg->kernel < HS_KERNEL_AUTO || cfg->kernel > HS_KERNEL_PIPE)
         return fail(HS_E_INVALID, "unknown kernel kind");
+    if (h->L.slab && cfg->kernel != HS_KERNEL_AUTO && cfg->kernel != HS_KERNEL_STENCIL)
+        return fail(HS_E_INVALID, "a slab runs the register stencil");
     if (h->L.structured) {
         if (cfg->kernel == HS_KERNEL_TABLE) return fail(HS_E_INVALID, "sc stencil lattices have no table kernel");
         if (cfg->vec_width != 0 && !vec_ok(h, cfg->vec_width))
@@ -939,7 +1059,7 @@ std::vector<hs_launch> tune_candidates(hs_lattice *h) {
 int hs_autotune(hs_lattice *h, double beta, int n_trial_sweeps) {
     if (!h) return fail(HS_E_INVALID, "null handle");
     if (n_trial_sweeps < 1) return fail(HS_E_INVALID, "n_trial_sweeps must be >= 1");
-    if (h->L.n_present == 0) return HS_OK;
+    if (h->L.n_present == 0 || h->L.slab) return HS_OK;  // a slab keeps the register stencil
     const Layout &L = h->L;
     const TuneKey key{h->precision, L.structured ? 1 : 0, h->accumulate, L.structured ? L.Lx : L.n_present,
                       L.structured ? L.Ly : L.width, L.structured ? L.Lz : L.n_colours, h->n_sm};
@@ -1064,7 +1184,7 @@ int hs_batch_create(hs_batch **out, hs_lattice *const *members, int n_members) {
         if (!h) return fail(HS_E_INVALID, "null member");
         if (h->stream != members[0]->stream || h->device != members[0]->device)
             return fail(HS_E_INVALID, "members must share one stream and device");
-        if (!h->L.structured || h->precision != HS_FP32 || h->L.Lh % 4 != 0)
+        if (!h->L.structured || h->L.slab || h->precision != HS_FP32 || h->L.Lh % 4 != 0)
             return fail(HS_E_INVALID, "batch members must be FP32 unmasked periodic sc with Lx divisible by 8");
         for (int q = 0; q < r; ++q)
             if (members[q] == h) return fail(HS_E_INVALID, "a lattice appears twice in the batch");

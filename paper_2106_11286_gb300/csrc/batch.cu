@@ -107,6 +107,8 @@ __device__ void finalize_sweep(const BatchArgs &b, int s) {
         if (lane == 0) {
             DevAccum *A = m.acc;
             A->accepted += tot[4];
+#pragma unroll
+            for (int q = 0; q < kPartials; ++q) A->sums[q] = tot[q];
             const double mx = tot[1] / m.n_present, my = tot[2] / m.n_present, mz = tot[3] / m.n_present;
             const double m2 = mx * mx + my * my + mz * mz;
             const double am = sqrt(m2);

@@ -340,6 +340,8 @@ __device__ void finish_reduction(const PassArgs &a, bool measured) {
             for (int q = 0; q < kPartials; ++q) tot[q] += s_fin[w][q];
         DevAccum *A = a.acc;
         A->accepted += tot[4];
+#pragma unroll
+        for (int q = 0; q < kPartials; ++q) A->sums[q] = tot[q];
         if (measured) {
             // Eq. 2 with |S| = 1: M = sum S / N
             const double E = tot[0];
@@ -638,14 +640,14 @@ __device__ __forceinline__ ItemOffsets item_offsets(const PassArgs &a, uint32_t 
     const uint32_t zm = (z == 0) ? Lz - 1 : z - 1;
     const uint32_t zp = (z == Lz - 1) ? 0 : z + 1;
     ItemOffsets o;
-    o.p = (y + z + (uint32_t)a.colour) & 1u;
+    o.p = (y + z + (uint32_t)a.colour + (uint32_t)a.zpar) & 1u;
     o.b0 = row * Lh + xh0;
     o.bym = (z * Ly + ym) * Lh + xh0;
     o.byp = (z * Ly + yp) * Lh + xh0;
     o.bzm = (zm * Ly + y) * Lh + xh0;
     o.bzp = (zp * Ly + y) * Lh + xh0;
     o.bed = row * Lh + (o.p ? ((xh0 + V == Lh) ? 0 : xh0 + V) : ((xh0 == 0) ? Lh - 1 : xh0 - 1));
-    o.site0 = row * Lx + 2 * xh0 + o.p;
+    o.site0 = row * Lx + 2 * xh0 + o.p + a.site_off;
     return o;
 }
 
@@ -677,8 +679,9 @@ template <int P, int V, bool CG = false>
 __device__ __forceinline__ void load_item(const PassArgs &a, uint32_t t, const typename Tr<P>::S *const (&own)[3],
                                           const typename Tr<P>::S *const (&oth)[3], StencilItem<P, V> &it) {
     const uint32_t nxv = a.Lh / V;
-    const uint32_t row = a.div_nxv.div(t);
-    const uint32_t xv = t - row * nxv;
+    const uint32_t r = a.div_nxv.div(t);
+    const uint32_t xv = t - r * nxv;
+    const uint32_t row = r + (uint32_t)(a.z_off * a.Ly);  // a z-slab's own rows start after its halo plane
     const uint32_t z = a.div_ly.div(row);
     const uint32_t y = row - z * a.Ly;
     load_item_at<P, V, CG>(a, y, z, xv, own, oth, it);

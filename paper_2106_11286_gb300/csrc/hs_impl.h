@@ -55,6 +55,7 @@ struct DevAccum {
     double last[8];        // E, Mx, My, Mz, |M|, M2, M4, |M.e| of the last finalised reduction
     unsigned int done;     // CTA arrival counter of the finishing pass
     int error;             // latched device error code (0 = none)
+    double sums[5];        // E, sum S_x, sum S_y, sum S_z, accepted moves of the last finalised reduction
 };
 
 // Parameters of one colour pass.
@@ -64,6 +65,9 @@ struct PassArgs {
     const void *oth[3];
     int Lx, Ly, Lz, Lh;
     FastDiv div_nxv, div_ly;   // row = t / (Lh/V), z = row / Ly
+    int nz, z_off;             // planes updated, array plane of the first (1 for a z-slab: plane 0 is a halo)
+    int zpar;                  // parity of (global z - array z), for the colour of a row
+    uint32_t site_off;         // global natural index - (array row Lx + x), mod 2^32
     int ty, zchunk, n_units;   // staged stencil: slab rows, planes per unit, units
     int ring_o, ring_w;        // staged stencil: other / own ring slots
     // table layout
@@ -95,6 +99,8 @@ enum KernelKind { kStencil = 1, kStaged = 2, kTable = 3, kMarch = 4, kPipe = 5 }
 
 struct Layout {
     bool structured;
+    bool slab;              // z-slab of a periodic sc lattice: Lz = nz + 2 array planes, halos at 0 and nz + 1
+    int z0, nz, Lz_glob;    // first global plane, own planes, global Lz (slab); 0, Lz, Lz otherwise
     int kernel;             // KernelKind
     int vec;                // vector width of the stencil kernels
     int prefetch;           // register stencil: 0 none, 1 next work item's loads in flight

@@ -39,7 +39,7 @@ __global__ void __launch_bounds__(kBlock, 2) sc_pass_kernel(const PassArgs a) {
     using S = typename Tr<P>::S;
     using C = typename Tr<P>::C;
     using VT = Vec<S, V>;
-    const uint32_t n_items = (uint32_t)a.Lz * a.Ly * (a.Lh / V);  // < 2^31: n_sites < 2^32
+    const uint32_t n_items = (uint32_t)a.nz * a.Ly * (a.Lh / V);  // own planes only; < 2^31
     const int c = a.colour;
     C J, K, ex, ey, ez, beta;
     load_params(a, J, K, ex, ey, ez, beta);
@@ -685,22 +685,26 @@ __global__ void __launch_bounds__(kBlock) table_measure_kernel(const PassArgs a,
 }
 
 // ----------------------------------------------------------------- init / layout
+// Own sites of a periodic sc lattice or z-slab (nz planes from global plane
+// z0, stored from array plane z_off of Lz_arr): index i runs over them in
+// natural order; the global natural index is i + z0 Ly Lx.
 template <int P>
-__global__ void sc_init_kernel(void *planes, int Lx, int Ly, int Lz, int Lh, int mode, double e0, double e1,
-                               double e2, uint32_t k0, uint32_t k1, uint32_t replica) {
+__global__ void sc_init_kernel(void *planes, int Lx, int Ly, int nz, int Lz_arr, int z_off, int z0, int Lh, int mode,
+                               double e0, double e1, double e2, uint32_t k0, uint32_t k1, uint32_t replica) {
     using S = typename Tr<P>::S;
     S *pl = (S *)planes;
-    const int64_t plane = (int64_t)Lz * Ly * Lh;
-    const int64_t n = (int64_t)Lx * Ly * Lz;
+    const int64_t plane = (int64_t)Lz_arr * Ly * Lh;
+    const int64_t n = (int64_t)Lx * Ly * nz;
+    const int64_t glob0 = (int64_t)z0 * Ly * Lx;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const int x = (int)(i % Lx);
-        const int64_t row = i / Lx;
-        const int y = (int)(row % Ly), z = (int)(row / Ly);
-        const int c = (x + y + z) & 1;
-        const int64_t idx = row * Lh + (x >> 1);
+        const int64_t r = i / Lx;
+        const int y = (int)(r % Ly), z = (int)(r / Ly);
+        const int c = (x + y + z + z0) & 1;
+        const int64_t idx = (r + (int64_t)z_off * Ly) * Lh + (x >> 1);
         double v[3] = {e0, e1, e2};
         if (mode == HS_INIT_RANDOM) {
-            const uint4 w = philox10(make_uint4((uint32_t)i, 0u, kTagInit << 24, replica), k0, k1);
+            const uint4 w = philox10(make_uint4((uint32_t)(i + glob0), 0u, kTagInit << 24, replica), k0, k1);
             sphere_fp64(w, v[0], v[1], v[2]);
         }
         for (int q = 0; q < 3; ++q) pl[(int64_t)(3 * c + q) * plane + idx] = store_from_double<S>(v[q]);
@@ -730,17 +734,18 @@ __global__ void table_init_kernel(void *spins4, const uint32_t *nat, int64_t n_p
 }
 
 template <int P>
-__global__ void sc_convert_kernel(void *planes, double *xyz, int Lx, int Ly, int Lz, int Lh, int to_layout) {
+__global__ void sc_convert_kernel(void *planes, double *xyz, int Lx, int Ly, int nz, int Lz_arr, int z_off, int z0,
+                                  int Lh, int to_layout) {
     using S = typename Tr<P>::S;
     S *pl = (S *)planes;
-    const int64_t plane = (int64_t)Lz * Ly * Lh;
-    const int64_t n = (int64_t)Lx * Ly * Lz;
+    const int64_t plane = (int64_t)Lz_arr * Ly * Lh;
+    const int64_t n = (int64_t)Lx * Ly * nz;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const int x = (int)(i % Lx);
-        const int64_t row = i / Lx;
-        const int y = (int)(row % Ly), z = (int)(row / Ly);
-        const int c = (x + y + z) & 1;
-        const int64_t idx = row * Lh + (x >> 1);
+        const int64_t r = i / Lx;
+        const int y = (int)(r % Ly), z = (int)(r / Ly);
+        const int c = (x + y + z + z0) & 1;
+        const int64_t idx = (r + (int64_t)z_off * Ly) * Lh + (x >> 1);
         for (int q = 0; q < 3; ++q) {
             S *d = pl + (int64_t)(3 * c + q) * plane + idx;
             if (to_layout)
@@ -944,7 +949,7 @@ int staged_occupancy(int precision, int vec, size_t smem_bytes, int consumers) {
 }
 
 static int64_t pass_items(const Layout &L) {
-    if (L.structured) return (int64_t)L.Lz * L.Ly * (L.Lh / L.vec);
+    if (L.structured) return (int64_t)L.nz * L.Ly * (L.Lh / L.vec);
     int64_t items = 0;
     for (int c = 0; c < L.n_colours; ++c)
         items = std::max<int64_t>(items, L.colour_begin[c + 1] - L.colour_begin[c]);
@@ -1119,15 +1124,15 @@ cudaError_t launch_init(int precision, const Layout &L, int mode, const double e
         const int g = grid_for(L.n_sites);
         switch (precision) {
         case HS_FP64:
-            sc_init_kernel<HS_FP64><<<g, kBlock, 0, s>>>(L.planes, L.Lx, L.Ly, L.Lz, L.Lh, mode, e[0], e[1], e[2],
+            sc_init_kernel<HS_FP64><<<g, kBlock, 0, s>>>(L.planes, L.Lx, L.Ly, L.nz, L.Lz, L.slab ? 1 : 0, L.z0, L.Lh, mode, e[0], e[1], e[2],
                                                           key0, key1, replica);
             break;
         case HS_FP32:
-            sc_init_kernel<HS_FP32><<<g, kBlock, 0, s>>>(L.planes, L.Lx, L.Ly, L.Lz, L.Lh, mode, e[0], e[1], e[2],
+            sc_init_kernel<HS_FP32><<<g, kBlock, 0, s>>>(L.planes, L.Lx, L.Ly, L.nz, L.Lz, L.slab ? 1 : 0, L.z0, L.Lh, mode, e[0], e[1], e[2],
                                                           key0, key1, replica);
             break;
         case HS_FP16:
-            sc_init_kernel<HS_FP16><<<g, kBlock, 0, s>>>(L.planes, L.Lx, L.Ly, L.Lz, L.Lh, mode, e[0], e[1], e[2],
+            sc_init_kernel<HS_FP16><<<g, kBlock, 0, s>>>(L.planes, L.Lx, L.Ly, L.nz, L.Lz, L.slab ? 1 : 0, L.z0, L.Lh, mode, e[0], e[1], e[2],
                                                           key0, key1, replica);
             break;
         default: return cudaErrorInvalidValue;
@@ -1157,9 +1162,18 @@ static cudaError_t launch_convert(int precision, const Layout &L, double *xyz, i
     if (L.structured) {
         const int g = grid_for(L.n_sites);
         switch (precision) {
-        case HS_FP64: sc_convert_kernel<HS_FP64><<<g, kBlock, 0, s>>>(L.planes, xyz, L.Lx, L.Ly, L.Lz, L.Lh, to_layout); break;
-        case HS_FP32: sc_convert_kernel<HS_FP32><<<g, kBlock, 0, s>>>(L.planes, xyz, L.Lx, L.Ly, L.Lz, L.Lh, to_layout); break;
-        case HS_FP16: sc_convert_kernel<HS_FP16><<<g, kBlock, 0, s>>>(L.planes, xyz, L.Lx, L.Ly, L.Lz, L.Lh, to_layout); break;
+        case HS_FP64:
+            sc_convert_kernel<HS_FP64><<<g, kBlock, 0, s>>>(L.planes, xyz, L.Lx, L.Ly, L.nz, L.Lz, L.slab ? 1 : 0, L.z0,
+                                                          L.Lh, to_layout);
+            break;
+        case HS_FP32:
+            sc_convert_kernel<HS_FP32><<<g, kBlock, 0, s>>>(L.planes, xyz, L.Lx, L.Ly, L.nz, L.Lz, L.slab ? 1 : 0, L.z0,
+                                                          L.Lh, to_layout);
+            break;
+        case HS_FP16:
+            sc_convert_kernel<HS_FP16><<<g, kBlock, 0, s>>>(L.planes, xyz, L.Lx, L.Ly, L.nz, L.Lz, L.slab ? 1 : 0, L.z0,
+                                                          L.Lh, to_layout);
+            break;
         default: return cudaErrorInvalidValue;
         }
     } else {

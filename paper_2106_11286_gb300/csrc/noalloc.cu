@@ -78,6 +78,8 @@ extern "C" int hs_sweep_sc_fp32_noalloc(float *planes, const int32_t dims[3], co
     L.Lx = dims[0];
     L.Ly = dims[1];
     L.Lz = dims[2];
+    L.nz = dims[2];
+    L.Lz_glob = dims[2];
     L.Lh = dims[0] / 2;
     L.vec = (L.Lh % 4 == 0) ? 4 : ((L.Lh % 2 == 0) ? 2 : 1);
     L.n_sites = L.n_present = (int64_t)dims[0] * dims[1] * dims[2];
@@ -97,6 +99,7 @@ extern "C" int hs_sweep_sc_fp32_noalloc(float *planes, const int32_t dims[3], co
     a.Lx = L.Lx;
     a.Ly = L.Ly;
     a.Lz = L.Lz;
+    a.nz = L.nz;
     a.Lh = L.Lh;
     a.div_nxv = hs::FastDiv((uint32_t)(L.Lh / L.vec));
     a.div_ly = hs::FastDiv((uint32_t)L.Ly);

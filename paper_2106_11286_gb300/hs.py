@@ -77,6 +77,13 @@ SIGNATURES = {
     "hs_lattice_destroy": (None, [_vp]),
     "hs_init_spins": (ctypes.c_int, [_vp, ctypes.c_int]),
     "hs_sweep": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_int64]),
+    "hs_sweep_pass": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_int]),
+    "hs_slab_create": (ctypes.c_int, [ctypes.POINTER(_vp), _i32p, ctypes.c_int32, ctypes.c_int32,
+                                      ctypes.POINTER(hs_params), ctypes.c_int, ctypes.c_uint64, ctypes.c_uint32, _vp]),
+    "hs_slab_plane": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(_vp),
+                                     ctypes.POINTER(ctypes.c_size_t)]),
+    "hs_slab_copy_plane": (ctypes.c_int, [_vp, ctypes.c_int, _vp, ctypes.c_int, ctypes.c_int]),
+    "hs_read_sums": (ctypes.c_int, [_vp, _dp]),
     "hs_measure": (ctypes.c_int, [_vp, ctypes.POINTER(hs_measurement)]),
     "hs_accumulate": (ctypes.c_int, [_vp, ctypes.c_int]),
     "hs_reset_accumulator": (ctypes.c_int, [_vp]),
@@ -179,6 +186,42 @@ def hs_init_spins(h, mode=HS_INIT_RANDOM):
 
 def hs_sweep(h, beta, n_sweeps=1):
     _check(load().hs_sweep(h, float(beta), int(n_sweeps)))
+
+
+def hs_sweep_pass(h, beta, colour):
+    _check(load().hs_sweep_pass(h, float(beta), int(colour)))
+
+
+def hs_slab_create(dims, z0, nz, J=1.0, K=0.0, e=(0.0, 0.0, 1.0), precision=HS_FP64, seed=0, replica=0,
+                   stream=None):
+    L = load()
+    prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    d = np.ascontiguousarray(dims, dtype=np.int32)
+    p = hs_params(float(J), float(K), (ctypes.c_double * 3)(*[float(v) for v in e]))
+    h = _vp()
+    _check(L.hs_slab_create(ctypes.byref(h), _ptr(d, ctypes.c_int32), int(z0), int(nz), ctypes.byref(p), prec,
+                            int(seed), int(replica), _stream_handle(stream)))
+    return h
+
+
+# slab plane selectors of hs_slab_plane / hs_slab_copy_plane
+HALO_BELOW, FIRST_OWN, LAST_OWN, HALO_ABOVE = 0, 1, 2, 3
+
+
+def hs_slab_plane(h, colour, component, which):
+    ptr, nbytes = _vp(), ctypes.c_size_t(0)
+    _check(load().hs_slab_plane(h, int(colour), int(component), int(which), ctypes.byref(ptr), ctypes.byref(nbytes)))
+    return ptr.value, nbytes.value
+
+
+def hs_slab_copy_plane(dst, dst_which, src, src_which, colour):
+    _check(load().hs_slab_copy_plane(dst, int(dst_which), src, int(src_which), int(colour)))
+
+
+def hs_read_sums(h) -> np.ndarray:
+    out = np.zeros(5, dtype=np.float64)
+    _check(load().hs_read_sums(h, _ptr(out, ctypes.c_double)))
+    return out
 
 
 def hs_measure(h) -> dict:
@@ -382,3 +425,16 @@ class Lattice:
     @property
     def info(self):
         return hs_get_info(self.h)
+
+
+class Slab(Lattice):
+    """Owning wrapper of a z-slab: ``Slab(dims, z0, nz, J=.., precision=.., seed=..)``."""
+
+    def __init__(self, dims, z0, nz, **kw):
+        self.h = hs_slab_create(dims, z0, nz, **kw)
+
+    def sweep_pass(self, beta, colour):
+        hs_sweep_pass(self.h, beta, colour)
+
+    def read_sums(self):
+        return hs_read_sums(self.h)

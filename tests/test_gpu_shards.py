@@ -1,0 +1,126 @@
+"""z-slab domain decomposition on one GPU (the exchange a multi-device run
+performs), against the whole lattice.
+
+* A lattice cut into 1 .. 16 slabs (down to one plane each), halos exchanged
+  between colour passes, reproduces the whole lattice's chain bit for bit in
+  every precision; the slabs' fused sums add up to the whole lattice's E, M
+  and accepted moves.
+* Slabs initialise with the whole lattice's global indices.
+* The sc 256^3 workload in four slabs matches the whole lattice after a
+  sweep.
+* A one-rank torch.distributed slab (its own periodic neighbour) matches.
+"""
+import os
+import socket
+
+import numpy as np
+import pytest
+
+from helpers import storage_round
+from paper_2106_11286_gb300 import hs, inputs, shards
+
+pytestmark = pytest.mark.gpu
+
+PARAMS = dict(J=1.0, K=0.3, e=(0.3, -0.2, 1.0))
+
+
+def _whole_and_sharded(dims, n_slabs, precision, seed=5, sweeps=3, beta=0.9, start=7):
+    n = dims[0] * dims[1] * dims[2]
+    S0 = storage_round(inputs.random_unit_spins(n, 17), precision)
+    with hs.Lattice("sc", dims=dims, precision=precision, seed=seed, **PARAMS) as whole:
+        whole.set_spins(S0)
+        whole.set_sweep_counter(start)
+        whole.sweep(beta, sweeps)
+        want, want_sums = whole.get_spins(), hs.hs_read_sums(whole.h)
+    with shards.ShardedLattice(dims, n_slabs, precision=precision, seed=seed, **PARAMS) as sh:
+        sh.set_spins(S0)
+        sh.set_sweep_counter(start)
+        sh.sweep(beta, sweeps)
+        got, obs = sh.get_spins(), sh.last_observables()
+    return S0, want, want_sums, got, obs
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp16"])
+@pytest.mark.parametrize("n_slabs", [1, 2, 4, 16])
+def test_slabs_reproduce_the_whole_lattice(precision, n_slabs):
+    dims = (16, 12, 16)
+    S0, want, want_sums, got, obs = _whole_and_sharded(dims, n_slabs, precision)
+    assert not np.array_equal(want, S0)
+    assert np.array_equal(got, want)
+    n = dims[0] * dims[1] * dims[2]
+    # FP64 sums in another grouping; FP32 / FP16 per-thread partials also group differently
+    rel, atol = (1e-12, 1e-9) if precision == "fp64" else (2e-6, 1e-4)
+    assert obs["E"] == pytest.approx(want_sums[0], rel=rel, abs=atol)
+    np.testing.assert_allclose(obs["M"] * n, want_sums[1:4], rtol=rel, atol=atol)
+    assert obs["accepted"] == want_sums[4]
+
+
+def test_slab_init_uses_global_indices():
+    dims = (8, 6, 12)
+    with hs.Lattice("sc", dims=dims, precision="fp32", seed=3, replica=2) as whole:
+        whole.init()
+        want = whole.get_spins()
+    with shards.ShardedLattice(dims, 3, precision="fp32", seed=3, replica=2) as sh:
+        sh.init()
+        assert np.array_equal(sh.get_spins(), want)
+
+
+def test_256_workload_in_four_slabs():
+    dims = (256, 256, 256)
+    p = dict(J=1.0, K=0.05, e=(0.0, 0.0, 1.0))
+    with hs.Lattice("sc", dims=dims, precision="fp32", seed=2, **p) as whole:
+        whole.init()
+        S0 = whole.get_spins()
+        whole.sweep(1 / 1.2, 1)
+        want = whole.get_spins()
+    with shards.ShardedLattice(dims, 4, precision="fp32", seed=2, **p) as sh:
+        sh.set_spins(S0)
+        sh.sweep(1 / 1.2, 1)
+        assert np.array_equal(sh.get_spins(), want)
+
+
+def test_slab_api_limits():
+    with hs.Slab((8, 8, 8), 2, 4, precision="fp32") as s:
+        assert s.info.n_present == 8 * 8 * 4
+        with pytest.raises(hs.HSError):
+            s.sweep(1.0, 1)
+        with pytest.raises(hs.HSError):
+            s.measure()
+        with pytest.raises(hs.HSError):
+            s.set_launch(kernel="pipe")
+        with pytest.raises(hs.HSError):
+            hs.hs_batch_create([s.h])
+        with pytest.raises(hs.HSError):
+            hs.hs_slab_plane(s.h, 0, 0, 4)
+    with pytest.raises(hs.HSError):
+        hs.Slab((8, 8, 8), 6, 4)   # planes beyond Lz
+
+
+def test_one_rank_distributed_slab():
+    import torch
+    import torch.distributed as dist
+    sock = socket.socket()
+    sock.bind(("127.0.0.1", 0))
+    port = sock.getsockname()[1]
+    sock.close()
+    dims = (16, 8, 8)
+    n = dims[0] * dims[1] * dims[2]
+    S0 = storage_round(inputs.random_unit_spins(n, 4), "fp32")
+    with hs.Lattice("sc", dims=dims, precision="fp32", seed=8, **PARAMS) as whole:
+        whole.set_spins(S0)
+        whole.sweep(1.0, 2)
+        want, want_sums = whole.get_spins(), hs.hs_read_sums(whole.h)
+    dist.init_process_group("nccl", init_method=f"tcp://127.0.0.1:{port}", rank=0, world_size=1)
+    try:
+        ds = shards.DistributedSlab(dims, precision="fp32", seed=8, **PARAMS)
+        ds.slab.set_spins(S0)
+        ds.exchange(0)
+        ds.exchange(1)
+        ds.sweep(1.0, 2)
+        assert np.array_equal(ds.slab.get_spins(), want)
+        obs = ds.last_observables()
+        assert obs["E"] == pytest.approx(want_sums[0], rel=2e-6)
+        ds.slab.close()
+    finally:
+        dist.destroy_process_group()
+        torch.cuda.synchronize()
