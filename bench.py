@@ -416,6 +416,28 @@ def run_variants(args, rank, stream, barrier_sync, world, dev):
                                            peaks["hbm_gbs"], 4),
                          "E_per_spin": mom[0] / cnt / N6, "absM": mom[2] / cnt, "launch": launch}
         lat.close()
+    # (2c) sc 2048^3 FP32 (8,589,934,592 spins, 103 GB of state): beyond 2^31 sites, register stencil
+    if not args.no_big:
+        L7 = 2048
+        N7 = L7 ** 3
+        lat = hs.Lattice("sc", dims=(L7,) * 3, J=WORKLOAD["J"], K=WORKLOAD["K"], e=WORKLOAD["e"], precision="fp32",
+                         seed=7, replica=rank, stream=stream)
+        beta7 = 1.0 / WORKLOAD["T"]
+        lat.init()
+        lat.accumulate(True)
+        lat.sweep(beta7, 2)
+        lat.reset_accumulator()
+        hs.hs_enable_timing(lat.h, True)
+        sweeps7 = max(2, args.huge_sweeps // 4)
+        sec = _timed(stream, lambda: lat.sweep(beta7, sweeps7))
+        kms, nl = hs.hs_read_timing(lat.h)
+        mom, cnt = lat.read_accumulator()
+        out["sc2048"] = {"value": round(N7 * sweeps7 / (sec * 1e9), 3), "unit": UNIT, "n_spins": N7,
+                         "sweeps": sweeps7, "device_bytes": 3 * 2 * (N7 // 2) * 4,
+                         "hbm_frac": round(3 * BYTES_PER_SPIN["fp32"] * (N7 // 2) / (kms / nl * 1e-3) / 1e9 /
+                                           peaks["hbm_gbs"], 4),
+                         "E_per_spin": mom[0] / cnt / N7, "absM": mom[2] / cnt, "launch": lat.launch}
+        lat.close()
     # (3) bcc nanoparticle: radius 110 in a 232^3-cell box, open surface, 1 % vacancies (seed 3),
     #     CSR neighbour list, K = 0.2 along (1,1,1), T = 0.9, FP32
     if not args.no_csr:

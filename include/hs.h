@@ -343,6 +343,12 @@ int hs_slab_plane(const hs_lattice *h, int colour, int component, int which, voi
  * src to plane dst_which of dst (same lattice and device), on dst's stream:
  * the halo exchange of slabs that share a device. */
 int hs_slab_copy_plane(hs_lattice *dst, int dst_which, const hs_lattice *src, int src_which, int colour);
+/* Spins of n selected sites in FP64: out[3t .. 3t+2] = S of the site with
+ * global natural index sites[t] (host arrays, the caller's).  Periodic sc
+ * lattices and slabs (own sites only); HS_E_INVALID for any other site.
+ * Synchronises the handle's stream.  For lattices too large to copy whole. */
+int hs_get_sites(hs_lattice *h, int64_t n, const int64_t *sites, double *out);
+
 /* FP64 sums of the last finalised fused reduction (the last hs_sweep or
  * hs_sweep_pass sweep, or hs_measure): out = {E share, sum S_x, sum S_y,
  * sum S_z, accepted moves of that sweep}.  Summed over the slabs of a

@@ -330,6 +330,25 @@ void or_colour_structured(int kind, int Lx, int Ly, int Lz, int32_t *colour)
                     colour[i] = (kind == 0) ? ((x + y + z) & 1) : b;
 }
 
+/* For sampled sites of an Lx x Ly x Lz sc lattice (no vacancies): the colour
+ * (x + y + z) & 1 of or_colour_structured and the rank of the site among the
+ * sites of its colour in ascending natural index, the count or_sweep keeps.
+ * With Lx even, every pair of natural indices (2k, 2k+1) lies in one row and
+ * holds one site of each colour, so the sites of either colour before site i
+ * number floor(i / 2). */
+void or_sc_sites_colour_rank(int Lx, int Ly, int Lz, int64_t m, const int64_t *sites, int32_t *colour, int64_t *rank)
+{
+    (void)Lz;
+    for (int64_t t = 0; t < m; ++t) {
+        const int64_t i = sites[t];
+        const int x = (int)(i % Lx);
+        const int y = (int)((i / Lx) % Ly);
+        const int64_t z = i / ((int64_t)Lx * Ly);
+        colour[t] = (int32_t)((x + y + z) & 1);
+        rank[t] = i / 2;
+    }
+}
+
 /* Greedy colouring: present vertices in ascending natural index each take
  * the smallest colour not held by an already-coloured present neighbour.
  * Absent vertices get colour -1.  Returns the number of colours. */
@@ -371,6 +390,16 @@ int or_colour_greedy(int64_t n, const int64_t *row_ptr, const int32_t *col, cons
 /* the sphere from one Philox call with tag INIT at sweep 0, colour 0.     */
 /* Absent sites are zero.  S is n x 3, natural order.                       */
 /* ------------------------------------------------------------------------ */
+/* Initial spin of natural site i: a sphere point from one Philox block,
+ * counter (index lo, index hi, tag 1, replica); an initial spin has no
+ * sweep, so the sweep word carries the index's high half. */
+static void or_init_site(uint64_t seed, uint32_t replica, uint64_t i, double s[3])
+{
+    uint32_t r[4];
+    or_draw(seed, replica, i, i >> 32, OR_TAG_INIT, 0, 0, r);
+    or_sphere_point(or_u53(r[0], r[1]), or_u53(r[2], r[3]), s);
+}
+
 void or_init_spins(int64_t n, const uint8_t *mask, uint64_t seed, uint32_t replica, double *S)
 {
     for (int64_t i = 0; i < n; ++i) {
@@ -378,10 +407,15 @@ void or_init_spins(int64_t n, const uint8_t *mask, uint64_t seed, uint32_t repli
             S[3 * i] = S[3 * i + 1] = S[3 * i + 2] = 0.0;
             continue;
         }
-        uint32_t r[4];
-        or_draw(seed, replica, (uint64_t)i, 0, OR_TAG_INIT, 0, 0, r);
-        or_sphere_point(or_u53(r[0], r[1]), or_u53(r[2], r[3]), &S[3 * i]);
+        or_init_site(seed, replica, (uint64_t)i, &S[3 * i]);
     }
+}
+
+/* The same for m sampled natural indices (no vacancies). */
+void or_init_sites(int64_t m, const int64_t *sites, uint64_t seed, uint32_t replica, double *S)
+{
+    for (int64_t t = 0; t < m; ++t)
+        or_init_site(seed, replica, (uint64_t)sites[t], &S[3 * t]);
 }
 
 /* Single-site energy -J S.h - K (S.e)^2 for a given local field h. */

@@ -85,6 +85,11 @@ def lib():
         L.or_sc_sites_neighbours.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                              ctypes.c_int64, i64p, i64p]
         L.or_sc_sites_neighbours.restype = None
+        L.or_init_sites.argtypes = [ctypes.c_int64, i64p, ctypes.c_uint64, ctypes.c_uint32, dp]
+        L.or_init_sites.restype = None
+        L.or_sc_sites_colour_rank.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int64, i64p, i32p,
+                                              i64p]
+        L.or_sc_sites_colour_rank.restype = None
         L.or_sites_update.argtypes = [ctypes.c_int64, i64p, i64p, i32p, dp, dp, ctypes.c_int, ctypes.c_uint64,
                                       ctypes.c_uint32, ctypes.c_uint64, ctypes.c_double, ctypes.c_double, dp,
                                       ctypes.c_double, ctypes.c_double, u8p, u8p]
@@ -225,6 +230,27 @@ def sc_site_neighbours(dims, periodic: bool, sites) -> np.ndarray:
     lib().or_sc_sites_neighbours(int(dims[0]), int(dims[1]), int(dims[2]), int(bool(periodic)), len(sites),
                                  _p(sites, ctypes.c_int64), _p(out, ctypes.c_int64))
     return out
+
+
+def init_sites(sites, seed: int, replica: int = 0) -> np.ndarray:
+    """Initial spins (as init_spins draws them) of sampled natural indices."""
+    sites = np.ascontiguousarray(sites, dtype=np.int64)
+    S = np.zeros((len(sites), 3), dtype=np.float64)
+    lib().or_init_sites(len(sites), _p(sites, ctypes.c_int64), int(seed), int(replica), _p(S, ctypes.c_double))
+    return S
+
+
+def sc_sites_colour_rank(dims, sites):
+    """Colour and colour-class rank (ascending natural index) of sampled
+    sites of a periodic sc lattice with even Lx, without a whole-lattice
+    array."""
+    assert int(dims[0]) % 2 == 0
+    sites = np.ascontiguousarray(sites, dtype=np.int64)
+    colour = np.empty(len(sites), dtype=np.int32)
+    rank = np.empty(len(sites), dtype=np.int64)
+    lib().or_sc_sites_colour_rank(int(dims[0]), int(dims[1]), int(dims[2]), len(sites), _p(sites, ctypes.c_int64),
+                                  _p(colour, ctypes.c_int32), _p(rank, ctypes.c_int64))
+    return colour, rank
 
 
 def sites_update(sites, ranks, colours, h, S, *, J: float, K: float, e, beta: float, seed: int,

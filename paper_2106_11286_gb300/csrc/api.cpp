@@ -248,6 +248,7 @@ PassArgs base_args(const hs_lattice *h) {
         a.z_off = L.slab ? 1 : 0;
         a.zpar = (L.z0 - a.z_off) & 1;
         a.site_off = (uint32_t)((int64_t)(L.z0 - a.z_off) * L.Ly * L.Lx);
+        a.rank_off = (uint32_t)((int64_t)(L.z0 - a.z_off) * L.Ly * L.Lh);
         a.ty = L.ty;
         a.zchunk = L.zchunk;
         a.n_units = L.n_units;
@@ -407,6 +408,12 @@ int configure_launch(hs_lattice *h) {
     }
     L.vec = r.vec_width ? r.vec_width : default_vec(h);
     int kind = r.kernel;
+    if (L.n_sites > 2147483647LL) {  // beyond 2^31 sites: the register stencil, with 32-bit work items
+        if (kind != HS_KERNEL_AUTO && kind != HS_KERNEL_STENCIL)
+            return fail(HS_E_INVALID, "lattices beyond 2^31 sites run the register stencil");
+        if ((int64_t)L.nz * L.Ly * (L.Lh / L.vec) >= 4294967296LL)
+            return fail(HS_E_INVALID, "vector width too small: more than 2^32 work items");
+    }
     // automatic choice: the register stencil (measured faster than the staged
     // kernel on GB300 at 256^3 and 464^3; hs_autotune compares both)
     if (kind == HS_KERNEL_AUTO) kind = HS_KERNEL_STENCIL;
@@ -576,7 +583,17 @@ int lattice_create(hs_lattice **out, int type, const int32_t dims[3], int period
         for (int a = 0; a < 3; ++a)
             if (dims[a] < 1) return fail(HS_E_INVALID, "dims must be >= 1");
         const double total = (double)dims[0] * dims[1] * dims[2] * nb;
-        if (total >= 2147483647.0) return fail(HS_E_INVALID, "more than 2^31 - 1 sites");
+        // FP32 / FP16 periodic sc: 32-bit element offsets within a colour plane
+        // and 32-bit colour ranks (up to 2^33 sites); everything else: 32-bit
+        // signed site indices
+        const bool wide = type == HS_SC && periodic && site_mask == nullptr && precision != HS_FP64;
+        if (wide) {
+            const double rows = slab ? (double)(slab->nz + 2) : (double)dims[2];
+            if ((double)dims[2] * dims[1] * (dims[0] / 2) > 4294967296.0 || rows * dims[1] * (dims[0] / 2) > 4294967296.0)
+                return fail(HS_E_INVALID, "more than 2^32 sites of one colour");
+        } else if (total >= 2147483647.0) {
+            return fail(HS_E_INVALID, "more than 2^31 - 1 sites");
+        }
         if (type == HS_SC && periodic) {
             for (int a = 0; a < 3; ++a)
                 if (dims[a] % 2 != 0)
@@ -806,6 +823,33 @@ int hs_slab_copy_plane(hs_lattice *dst, int dst_which, const hs_lattice *src, in
         if (int st = hs_slab_plane(src, colour, q, src_which, &sp, &ns)) return st;
         HS_CUDA(cudaMemcpyAsync(d, sp, nb, cudaMemcpyDeviceToDevice, dst->stream));
     }
+    return HS_OK;
+}
+
+int hs_get_sites(hs_lattice *h, int64_t n, const int64_t *sites, double *out) {
+    if (!h || (n > 0 && (!sites || !out))) return fail(HS_E_INVALID, "null argument");
+    if (n < 0) return fail(HS_E_INVALID, "negative count");
+    const Layout &L = h->L;
+    if (!L.structured) return fail(HS_E_INVALID, "site gathers need a periodic sc lattice or slab");
+    const int64_t plane = (int64_t)L.Lx * L.Ly;
+    for (int64_t t = 0; t < n; ++t) {
+        const int64_t z = sites[t] / plane;
+        if (sites[t] < 0 || z < L.z0 || z >= (int64_t)L.z0 + L.nz) return fail(HS_E_INVALID, "site not owned");
+    }
+    if (n == 0) return HS_OK;
+    int64_t *d_sites = nullptr;
+    double *d_out = nullptr;
+    cudaError_t e = cudaMalloc(&d_sites, (size_t)n * sizeof(int64_t));
+    if (e == cudaSuccess) e = cudaMalloc(&d_out, (size_t)n * 3 * sizeof(double));
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d_sites, sites, (size_t)n * sizeof(int64_t), cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = hs::launch_gather_sites(h->precision, L, n, d_sites, d_out, h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(out, d_out, (size_t)n * 3 * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    cudaFree(d_sites);
+    cudaFree(d_out);
+    if (e != cudaSuccess) return cuda_fail(e, "hs_get_sites");
     return HS_OK;
 }
 

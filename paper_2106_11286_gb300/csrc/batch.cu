@@ -166,7 +166,7 @@ __global__ void __launch_bounds__(kBlock, 2) batch_kernel(const BatchArgs b) {
                 for (uint32_t t = sg.begin + threadIdx.x; t < sg.end; t += kBlock) {
                     StencilItem<P, V> it;
                     load_item<P, V, true>(a, t, own, oth, it);
-                    if (update_item<P, V, true>(it.s, it.o, it.nym, it.nyp, it.nzm, it.nzp, it.ed, it.p, it.site0, c,
+                    if (update_item<P, V, true>(it.s, it.o, it.nym, it.nyp, it.nzm, it.nzp, it.ed, it.p, it.site0, it.rank0, c,
                                                 a, J, K, ex, ey, ez, beta, acc)) {
 #pragma unroll
                         for (int q = 0; q < 3; ++q) *reinterpret_cast<VT *>(own_w[q] + it.b0) = it.s[q];

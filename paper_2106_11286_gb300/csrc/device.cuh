@@ -440,15 +440,19 @@ __device__ __forceinline__ float neg_beta_log2e(float beta) { return f_mul(-beta
 
 // Metropolis steps (ii)-(iii) for the V sites of one work item, given the
 // item's own spins s, the other colour's same row o (+ the edge element ed
-// beyond it), and the other colour's rows at y-1, y+1, z-1, z+1.  Updates s
-// in place; returns whether any site was accepted.
+// beyond it), and the other colour's rows at y-1, y+1, z-1, z+1.  site0 is
+// the natural index of the item's first site (the FP64 schedule's counter),
+// rank0 its rank within its colour class (the FP32 / FP16 schedule's; on a
+// periodic sc lattice the natural index halved, kept separately so that it
+// stays exact beyond 2^32 sites).  Updates s in place; returns whether any
+// site was accepted.
 template <int P, int V, bool MEAS>
 __device__ __forceinline__ bool update_item(Vec<typename Tr<P>::S, V> (&s)[3], const Vec<typename Tr<P>::S, V> (&o)[3],
                                             const Vec<typename Tr<P>::S, V> (&nym)[3],
                                             const Vec<typename Tr<P>::S, V> (&nyp)[3],
                                             const Vec<typename Tr<P>::S, V> (&nzm)[3],
                                             const Vec<typename Tr<P>::S, V> (&nzp)[3], const typename Tr<P>::C (&ed)[3],
-                                            uint32_t p, uint32_t site0, int c, const PassArgs &a,
+                                            uint32_t p, uint32_t site0, uint32_t rank0, int c, const PassArgs &a,
                                             typename Tr<P>::C J, typename Tr<P>::C K, typename Tr<P>::C ex,
                                             typename Tr<P>::C ey, typename Tr<P>::C ez, typename Tr<P>::C beta,
                                             SiteAcc<P> &acc) {
@@ -524,7 +528,6 @@ __device__ __forceinline__ bool update_item(Vec<typename Tr<P>::S, V> (&s)[3], c
             }
         };
         // ranks of the item's sites in their colour class: rank0 + k
-        const uint32_t rank0 = site0 >> 1;
         if (V >= 2 && (rank0 & 1u) == 0u) {
 #pragma unroll
             for (int j = 0; j < V / 2; ++j) {  // one Philox block and packed arithmetic per pair
@@ -619,7 +622,7 @@ template <int P, int V>
 struct StencilItem {
     Vec<typename Tr<P>::S, V> s[3], o[3], nym[3], nyp[3], nzm[3], nzp[3];
     typename Tr<P>::C ed[3];
-    uint32_t b0, p, site0;
+    uint32_t b0, p, site0, rank0;
 };
 
 // Element offsets (within a colour plane) of the operands of the work item at
@@ -627,7 +630,7 @@ struct StencilItem {
 // vector at the same offset), the other colour's rows at y-1, y+1, z-1, z+1,
 // and the edge element beyond the row vector on the side parity p picks.
 struct ItemOffsets {
-    uint32_t b0, bym, byp, bzm, bzp, bed, p, site0;
+    uint32_t b0, bym, byp, bzm, bzp, bed, p, site0, rank0;
 };
 
 template <int V>
@@ -648,6 +651,7 @@ __device__ __forceinline__ ItemOffsets item_offsets(const PassArgs &a, uint32_t 
     o.bzp = (zp * Ly + y) * Lh + xh0;
     o.bed = row * Lh + (o.p ? ((xh0 + V == Lh) ? 0 : xh0 + V) : ((xh0 == 0) ? Lh - 1 : xh0 - 1));
     o.site0 = row * Lx + 2 * xh0 + o.p + a.site_off;
+    o.rank0 = row * Lh + xh0 + a.rank_off;  // (row Lx + 2 xh0 + p) / 2 + the slab's offset
     return o;
 }
 
@@ -672,6 +676,7 @@ __device__ __forceinline__ void load_item_at(const PassArgs &a, uint32_t y, uint
     it.b0 = f.b0;
     it.p = f.p;
     it.site0 = f.site0;
+    it.rank0 = f.rank0;
 }
 
 // The work item with linear index t = (z Ly + y) (Lh/V) + xv.

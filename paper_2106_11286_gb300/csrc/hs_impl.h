@@ -68,6 +68,7 @@ struct PassArgs {
     int nz, z_off;             // planes updated, array plane of the first (1 for a z-slab: plane 0 is a halo)
     int zpar;                  // parity of (global z - array z), for the colour of a row
     uint32_t site_off;         // global natural index - (array row Lx + x), mod 2^32
+    uint32_t rank_off;         // colour rank of a site - (array row Lh + x / 2), mod 2^32
     int ty, zchunk, n_units;   // staged stencil: slab rows, planes per unit, units
     int ring_o, ring_w;        // staged stencil: other / own ring slots
     // table layout
@@ -167,6 +168,8 @@ int set_last_error(int code, const std::string &msg);
 cudaError_t launch_pass(int precision, const Layout &L, const PassArgs &a, int n_blocks, cudaStream_t s);
 cudaError_t launch_init(int precision, const Layout &L, int mode, const double e[3], uint32_t key0,
                         uint32_t key1, uint32_t replica, cudaStream_t s);
+cudaError_t launch_gather_sites(int precision, const Layout &L, int64_t n, const int64_t *d_sites, double *d_out,
+                                cudaStream_t s);
 cudaError_t launch_scatter(int precision, const Layout &L, const double *d_xyz, cudaStream_t s);
 cudaError_t launch_gather(int precision, const Layout &L, double *d_xyz, cudaStream_t s);
 cudaError_t launch_measure(int precision, const Layout &L, const PassArgs &a, int n_blocks, cudaStream_t s);

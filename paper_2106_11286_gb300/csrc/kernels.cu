@@ -49,7 +49,7 @@ __global__ void __launch_bounds__(kBlock, 2) sc_pass_kernel(const PassArgs a) {
     SiteAcc<P> acc;
     const uint32_t stride = gridDim.x * blockDim.x;
     auto compute = [&](StencilItem<P, V> &it) {
-        if (update_item<P, V, MEAS>(it.s, it.o, it.nym, it.nyp, it.nzm, it.nzp, it.ed, it.p, it.site0, c, a, J, K,
+        if (update_item<P, V, MEAS>(it.s, it.o, it.nym, it.nyp, it.nzm, it.nzp, it.ed, it.p, it.site0, it.rank0, c, a, J, K,
                                     ex, ey, ez, beta, acc)) {
 #pragma unroll
             for (int q = 0; q < 3; ++q) *reinterpret_cast<VT *>(own_w[q] + it.b0) = it.s[q];
@@ -179,6 +179,7 @@ __device__ __forceinline__ void pipe_read(const typename PipeSlot<P, V>::VT *sv,
     it.b0 = f.b0;
     it.p = f.p;
     it.site0 = f.site0;
+    it.rank0 = f.rank0;
 }
 
 template <int P, int V, bool MEAS>
@@ -213,7 +214,7 @@ __global__ void __launch_bounds__(kBlock, 2) sc_pipe_kernel(const PassArgs a) {
             const uint32_t tn = t + stride;
             const bool more = tn < n_items;
             if (more) f = pipe_issue<P, V>(a, tn, own, oth, slot_v, slot_e);
-            if (update_item<P, V, MEAS>(it.s, it.o, it.nym, it.nyp, it.nzm, it.nzp, it.ed, it.p, it.site0, c, a, J, K,
+            if (update_item<P, V, MEAS>(it.s, it.o, it.nym, it.nyp, it.nzm, it.nzp, it.ed, it.p, it.site0, it.rank0, c, a, J, K,
                                         ex, ey, ez, beta, acc)) {
 #pragma unroll
                 for (int q = 0; q < 3; ++q) *reinterpret_cast<VT *>(own_w[q] + it.b0) = it.s[q];
@@ -278,7 +279,7 @@ __global__ void __launch_bounds__(kBlock, 2) sc_march_kernel(const PassArgs a) {
             StencilItem<P, V> item;
             load_item_at<P, V>(a, y0 + yl, z, xv, own, oth, item);
             if (update_item<P, V, MEAS>(item.s, item.o, item.nym, item.nyp, item.nzm, item.nzp, item.ed, item.p,
-                                        item.site0, c, a, J, K, ex, ey, ez, beta, acc)) {
+                                        item.site0, item.rank0, c, a, J, K, ex, ey, ez, beta, acc)) {
 #pragma unroll
                 for (int k = 0; k < 3; ++k) *reinterpret_cast<VT *>(own_w[k] + item.b0) = item.s[k];
             }
@@ -507,7 +508,8 @@ __global__ void __launch_bounds__(StagedShape<NC>::threads, StagedShape<NC>::min
                         ed[q] = to_c(r0[xe]);
                     }
                     const uint32_t site0 = (uint32_t)((z * Ly + y) * Lx + 2 * xh0) + p;
-                    if (update_item<P, V, MEAS>(sv, o, nym, nyp, nzm, nzp, ed, p, site0, c, a, J, K, ex, ey, ez, beta,
+                    const uint32_t rank0 = (uint32_t)((z * Ly + y) * Lh + xh0);
+                    if (update_item<P, V, MEAS>(sv, o, nym, nyp, nzm, nzp, ed, p, site0, rank0, c, a, J, K, ex, ey, ez, beta,
                                                 acc)) {
                         const size_t gi = ((size_t)z * Ly + y) * Lh + xh0;
 #pragma unroll
@@ -704,7 +706,9 @@ __global__ void sc_init_kernel(void *planes, int Lx, int Ly, int nz, int Lz_arr,
         const int64_t idx = (r + (int64_t)z_off * Ly) * Lh + (x >> 1);
         double v[3] = {e0, e1, e2};
         if (mode == HS_INIT_RANDOM) {
-            const uint4 w = philox10(make_uint4((uint32_t)(i + glob0), 0u, kTagInit << 24, replica), k0, k1);
+            // counter (index lo, index hi, tag 1, replica): an initial spin has no sweep
+            const uint64_t gi = (uint64_t)(i + glob0);
+            const uint4 w = philox10(make_uint4((uint32_t)gi, (uint32_t)(gi >> 32), kTagInit << 24, replica), k0, k1);
             sphere_fp64(w, v[0], v[1], v[2]);
         }
         for (int q = 0; q < 3; ++q) pl[(int64_t)(3 * c + q) * plane + idx] = store_from_double<S>(v[q]);
@@ -753,6 +757,25 @@ __global__ void sc_convert_kernel(void *planes, double *xyz, int Lx, int Ly, int
             else
                 xyz[3 * i + q] = (double)to_c(*d);
         }
+    }
+}
+
+// Spins of selected sites (global natural indices, own sites of the lattice
+// or slab), in FP64, for lattices too large to copy whole.
+template <int P>
+__global__ void sc_gather_kernel(const void *planes, int Lx, int Ly, int Lz_arr, int z_off, int z0, int Lh, int64_t n,
+                                 const int64_t *sites, double *out) {
+    using S = typename Tr<P>::S;
+    const S *pl = (const S *)planes;
+    const int64_t plane = (int64_t)Lz_arr * Ly * Lh;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = sites[t];
+        const int x = (int)(i % Lx);
+        const int64_t r = i / Lx;
+        const int y = (int)(r % Ly), z = (int)(r / Ly);
+        const int c = (x + y + z) & 1;
+        const int64_t idx = ((int64_t)(z - z0 + z_off) * Ly + y) * Lh + (x >> 1);
+        for (int q = 0; q < 3; ++q) out[3 * t + q] = (double)to_c(pl[(int64_t)(3 * c + q) * plane + idx]);
     }
 }
 
@@ -1184,6 +1207,25 @@ static cudaError_t launch_convert(int precision, const Layout &L, double *xyz, i
         case HS_FP16: table_convert_kernel<HS_FP16><<<g, kBlock, 0, s>>>(L.spins4, L.nat, L.n_present, xyz, to_layout); break;
         default: return cudaErrorInvalidValue;
         }
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather_sites(int precision, const Layout &L, int64_t n, const int64_t *d_sites, double *d_out,
+                                cudaStream_t s) {
+    const int g = grid_for(n);
+    const int z_off = L.slab ? 1 : 0;
+    switch (precision) {
+    case HS_FP64:
+        sc_gather_kernel<HS_FP64><<<g, kBlock, 0, s>>>(L.planes, L.Lx, L.Ly, L.Lz, z_off, L.z0, L.Lh, n, d_sites, d_out);
+        break;
+    case HS_FP32:
+        sc_gather_kernel<HS_FP32><<<g, kBlock, 0, s>>>(L.planes, L.Lx, L.Ly, L.Lz, z_off, L.z0, L.Lh, n, d_sites, d_out);
+        break;
+    case HS_FP16:
+        sc_gather_kernel<HS_FP16><<<g, kBlock, 0, s>>>(L.planes, L.Lx, L.Ly, L.Lz, z_off, L.z0, L.Lh, n, d_sites, d_out);
+        break;
+    default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
 }

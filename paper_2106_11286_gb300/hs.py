@@ -84,6 +84,7 @@ SIGNATURES = {
                                      ctypes.POINTER(ctypes.c_size_t)]),
     "hs_slab_copy_plane": (ctypes.c_int, [_vp, ctypes.c_int, _vp, ctypes.c_int, ctypes.c_int]),
     "hs_read_sums": (ctypes.c_int, [_vp, _dp]),
+    "hs_get_sites": (ctypes.c_int, [_vp, ctypes.c_int64, _i64p, _dp]),
     "hs_measure": (ctypes.c_int, [_vp, ctypes.POINTER(hs_measurement)]),
     "hs_accumulate": (ctypes.c_int, [_vp, ctypes.c_int]),
     "hs_reset_accumulator": (ctypes.c_int, [_vp]),
@@ -216,6 +217,13 @@ def hs_slab_plane(h, colour, component, which):
 
 def hs_slab_copy_plane(dst, dst_which, src, src_which, colour):
     _check(load().hs_slab_copy_plane(dst, int(dst_which), src, int(src_which), int(colour)))
+
+
+def hs_get_sites(h, sites) -> np.ndarray:
+    idx = np.ascontiguousarray(sites, dtype=np.int64)
+    out = np.zeros((len(idx), 3), dtype=np.float64)
+    _check(load().hs_get_sites(h, len(idx), _ptr(idx, ctypes.c_int64), _ptr(out, ctypes.c_double)))
+    return out
 
 
 def hs_read_sums(h) -> np.ndarray:
@@ -389,6 +397,9 @@ class Lattice:
 
     def sweep(self, beta, n=1):
         hs_sweep(self.h, beta, n)
+
+    def get_sites(self, sites):
+        return hs_get_sites(self.h, sites)
 
     def measure(self):
         return hs_measure(self.h)

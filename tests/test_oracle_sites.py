@@ -51,3 +51,26 @@ def test_sc_site_neighbours_match_the_table(orc, dims, periodic):
     for i in range(g.n):
         row = g.col[g.row_ptr[i]:g.row_ptr[i + 1]]
         assert list(nb[i][nb[i] >= 0]) == list(row)
+
+
+@pytest.mark.parametrize("dims", [(6, 4, 8), (2, 6, 4), (8, 3, 5)])
+def test_sc_sites_colour_rank_matches_counting(orc, dims):
+    colour = orc.colour_structured("sc", dims)
+    n = len(colour)
+    want_rank = np.empty(n, dtype=np.int64)
+    for c in (0, 1):   # rank = how many sites of the same colour come first
+        want_rank[colour == c] = np.arange(int((colour == c).sum()))
+    got_colour, got_rank = orc.sc_sites_colour_rank(dims, np.arange(n))
+    assert np.array_equal(got_colour, colour)
+    assert np.array_equal(got_rank, want_rank)
+
+
+def test_init_sites_match_init_spins(orc):
+    g = orc.lattice("sc", (6, 4, 8))
+    S = orc.init_spins(g, seed=12, replica=3)
+    idx = np.array([0, 7, 100, g.n - 1])
+    assert np.array_equal(orc.init_sites(idx, seed=12, replica=3), S[idx])
+    # beyond 2^32 the index's high half enters the counter: no repeat of the low half
+    far = orc.init_sites(np.array([5, 5 + 2 ** 32]), seed=12, replica=3)
+    assert not np.array_equal(far[0], far[1])
+    assert np.allclose(np.linalg.norm(far, axis=1), 1.0, atol=1e-15)
