@@ -67,6 +67,16 @@ KERNEL_NAMES = {1: "sc_pass_kernel", 2: "sc_staged_kernel", 3: "table_pass_kerne
                 5: "sc_pipe_kernel"}
 
 
+def kernel_label(launch, precision_code=1, measure=1):
+    """Template label of the colour-pass kernel a launch configuration runs
+    (as ncu names it), for matching the stored traffic to the timed kernel."""
+    name = KERNEL_NAMES.get(launch["kernel"], "sc_pass_kernel")
+    if launch["kernel"] == 1:
+        pf = {1: 1, 3: 2}.get(launch["prefetch"], 0)
+        return f"{name}<{precision_code}, {launch['vec_width']}, {measure}, {pf}>"
+    return name
+
+
 def read_traffic(kernel=None):
     """DRAM bytes per launch from the committed ncu summary, if it was taken
     on the current kernel sources and on this kernel (else None)."""
@@ -78,7 +88,7 @@ def read_traffic(kernel=None):
                 kv[k.strip()] = v.strip()
         if kv.get("sources_sha") != kernels_sha():
             return None
-        if kernel is not None and not kv.get("kernel", "").startswith(kernel + "<"):
+        if kernel is not None and kv.get("kernel", "") != kernel and not kv.get("kernel", "").startswith(kernel + "<"):
             return None
         return float(kv["dram_bytes_per_launch"])
     except (OSError, KeyError, ValueError):
@@ -232,10 +242,10 @@ def run_ours(args):
     peaks, peak_kind = measured_peaks()
     achieved_gbs = alg_bytes / (kernel_ms * 1e-3) / 1e9
     kname = KERNEL_NAMES.get(launch["kernel"], "sc_pass_kernel") if launch else "sc_pass_kernel"
-    traffic = read_traffic(kname)
+    traffic = read_traffic(kernel_label(launch) if launch else None)
     roofline = {"bound": "hbm", "achieved": round(achieved_gbs, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": round(achieved_gbs / peaks["hbm_gbs"], 4), "traffic": traffic,
-                "peak_source": f"{peak_kind} copy bandwidth", "kernel": f"{kname}<fp32>",
+                "peak_source": f"{peak_kind} copy bandwidth", "kernel": kernel_label(launch) if launch else kname,
                 "kernel_ms": round(kernel_ms, 5), "alg_bytes_per_launch": alg_bytes,
                 "kernel_timing": "timed-region CUDA events / colour-pass launches (the region holds only them)",
                 "kernel_ms_bracketed": round(kernel_ms_bracketed, 5),

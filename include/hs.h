@@ -237,7 +237,11 @@ typedef struct {
     int tile_y;        /* staged / march: rows per CTA slab (divides Ly) */
     int chunk_z;       /* staged: planes per CTA work unit */
     int prefetch;      /* stencil: 1 = issue the next work item's loads before
-                          computing the current one, 2 = off, 0 = automatic */
+                          computing the current one, 3 = split prefetch (the
+                          next item's own, same-row and z+-1 rows loaded once
+                          the current item's fields are summed), 2 = off,
+                          0 = automatic (split prefetch for FP32 when a
+                          CTA's work items span at least 8 rows, else off) */
     int ring;          /* staged: shared-memory slots of the other colour's
                           planes (4..8; the own colour gets ring - 2) */
     int consumers;     /* staged: consumer warps per CTA, 4 or 8 (plus one

@@ -489,7 +489,14 @@ int configure_launch(hs_lattice *h) {
         return HS_OK;
     }
     L.kernel = hs::kStencil;  // before the occupancy query, which looks at the kind
-    L.prefetch = (r.prefetch == 1) ? 1 : 0;
+    // request 1 = next item in registers, 3 = split prefetch, 2 = off;
+    // automatic: split prefetch when a CTA's items span 8 rows or more, so the
+    // y-1 / y+1 rows it loads late are mostly its own (measured faster at
+    // 256^3 FP32, slower at 464^3 and 1024^3)
+    if (r.prefetch == 0)
+        L.prefetch = (h->precision == HS_FP32 && L.Lh / L.vec <= hs::kBlock / 8) ? 2 : 0;
+    else
+        L.prefetch = r.prefetch == 1 ? 1 : (r.prefetch == 3 ? 2 : 0);
     int bps = r.blocks_per_sm;
     const int occ = std::min(hs::pass_occupancy(h->precision, L, 0), hs::pass_occupancy(h->precision, L, 1));
     if (bps <= 0 || bps > occ) bps = occ;
@@ -1015,7 +1022,7 @@ int hs_set_launch(hs_lattice *h, const hs_launch *cfg) {
     if (cfg->blocks_per_sm < 0 || cfg->blocks_per_sm > 2048 / hs::kBlock)
         return fail(HS_E_INVALID, "blocks_per_sm out of range");
     if (cfg->tile_y < 0 || cfg->chunk_z < 0) return fail(HS_E_INVALID, "negative tile");
-    if (cfg->prefetch < 0 || cfg->prefetch > 2) return fail(HS_E_INVALID, "prefetch must be 0, 1 or 2");
+    if (cfg->prefetch < 0 || cfg->prefetch > 3) return fail(HS_E_INVALID, "prefetch must be 0, 1, 2 or 3");
     if (cfg->ring != 0 && (cfg->ring < 4 || cfg->ring > 8)) return fail(HS_E_INVALID, "ring must be 0 or in [4, 8]");
     if (cfg->consumers != 0 && cfg->consumers != 4 && cfg->consumers != 8)
         return fail(HS_E_INVALID, "consumer warps must be 0, 4 or 8");
@@ -1040,7 +1047,7 @@ int hs_get_launch(const hs_lattice *h, hs_launch *out) {
     out->blocks_per_sm = (h->n_blocks + h->n_sm - 1) / std::max(h->n_sm, 1);
     out->tile_y = (L.kernel == hs::kStaged || L.kernel == hs::kMarch) ? L.ty : 0;
     out->chunk_z = L.kernel == hs::kStaged ? L.zchunk : 0;
-    out->prefetch = (L.kernel == hs::kStencil) ? (L.prefetch == 1 ? 1 : 2) : 0;
+    out->prefetch = (L.kernel == hs::kStencil) ? (L.prefetch == 1 ? 1 : (L.prefetch == 2 ? 3 : 2)) : 0;
     out->ring = L.kernel == hs::kStaged ? L.ring_o : 0;
     out->consumers = L.kernel == hs::kStaged ? L.consumers / 32 : 0;
     return HS_OK;
@@ -1069,7 +1076,7 @@ std::vector<hs_launch> tune_candidates(hs_lattice *h) {
     for (int v : {1, 2, 4, 8}) {
         if (!vec_ok(h, v)) continue;
         for (int b = 1; b <= 8; ++b)
-            for (int pf : {1, 2}) out.push_back({HS_KERNEL_STENCIL, v, b, 0, 0, pf, 0, 0});
+            for (int pf : {1, 2, 3}) out.push_back({HS_KERNEL_STENCIL, v, b, 0, 0, pf, 0, 0});
         if (hs::pipe_smem_bytes(h->precision, v) != 0)
             for (int b = 1; b <= 2; ++b) out.push_back({HS_KERNEL_PIPE, v, b, 0, 0, 0, 0, 0});
         for (int ty : {2, 4, 8, 16})

@@ -438,43 +438,80 @@ struct SiteAcc<HS_FP64> {
 // -beta log2(e), rounded once; every FP32 path uses this same value.
 __device__ __forceinline__ float neg_beta_log2e(float beta) { return f_mul(-beta, 1.44269504088896341f); }
 
-// Metropolis steps (ii)-(iii) for the V sites of one work item, given the
-// item's own spins s, the other colour's same row o (+ the edge element ed
-// beyond it), and the other colour's rows at y-1, y+1, z-1, z+1.  site0 is
-// the natural index of the item's first site (the FP64 schedule's counter),
-// rank0 its rank within its colour class (the FP32 / FP16 schedule's; on a
-// periodic sc lattice the natural index halved, kept separately so that it
-// stays exact beyond 2^32 sites).  Updates s in place; returns whether any
-// site was accepted.
-template <int P, int V, bool MEAS>
-__device__ __forceinline__ bool update_item(Vec<typename Tr<P>::S, V> (&s)[3], const Vec<typename Tr<P>::S, V> (&o)[3],
+// Step (i) for the V sites of one work item: the local field h[q][k] of site
+// k, the sum of its neighbours in the order -x, +x, -y, +y, -z, +z, from the
+// other colour's same row o (+ the edge element ed beyond it; row parity p
+// picks (xh-1, xh) or (xh, xh+1) for the x neighbours) and its rows at y-1,
+// y+1, z-1, z+1.  FP32 / FP16 add two sites at a time as the lanes of float2
+// (identical per lane to the scalar adds).
+template <int P, int V>
+__device__ __forceinline__ void item_fields(const Vec<typename Tr<P>::S, V> (&o)[3],
                                             const Vec<typename Tr<P>::S, V> (&nym)[3],
                                             const Vec<typename Tr<P>::S, V> (&nyp)[3],
                                             const Vec<typename Tr<P>::S, V> (&nzm)[3],
                                             const Vec<typename Tr<P>::S, V> (&nzp)[3], const typename Tr<P>::C (&ed)[3],
-                                            uint32_t p, uint32_t site0, uint32_t rank0, int c, const PassArgs &a,
-                                            typename Tr<P>::C J, typename Tr<P>::C K, typename Tr<P>::C ex,
-                                            typename Tr<P>::C ey, typename Tr<P>::C ez, typename Tr<P>::C beta,
-                                            SiteAcc<P> &acc) {
+                                            uint32_t p, typename Tr<P>::C (&h)[3][V]) {
+    using C = typename Tr<P>::C;
+    auto xm_of = [&](int k, int q) -> C { return p ? to_c(o[q].v[k]) : (k == 0 ? ed[q] : to_c(o[q].v[k - 1])); };
+    auto xp_of = [&](int k, int q) -> C { return p ? (k == V - 1 ? ed[q] : to_c(o[q].v[k + 1])) : to_c(o[q].v[k]); };
+    if constexpr (P == HS_FP64) {
+#pragma unroll
+        for (int k = 0; k < V; ++k)
+#pragma unroll
+            for (int q = 0; q < 3; ++q)
+                h[q][k] = ((((xm_of(k, q) + xp_of(k, q)) + to_c(nym[q].v[k])) + to_c(nyp[q].v[k])) +
+                           to_c(nzm[q].v[k])) +
+                          to_c(nzp[q].v[k]);
+    } else if constexpr (V >= 2) {
+#pragma unroll
+        for (int j = 0; j < V / 2; ++j) {
+            const int k0 = 2 * j, k1 = 2 * j + 1;
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                const float2 xm = make_float2(xm_of(k0, q), xm_of(k1, q));
+                const float2 xp = make_float2(xp_of(k0, q), xp_of(k1, q));
+                const float2 ym = make_float2(to_c(nym[q].v[k0]), to_c(nym[q].v[k1]));
+                const float2 yp = make_float2(to_c(nyp[q].v[k0]), to_c(nyp[q].v[k1]));
+                const float2 zm = make_float2(to_c(nzm[q].v[k0]), to_c(nzm[q].v[k1]));
+                const float2 zp = make_float2(to_c(nzp[q].v[k0]), to_c(nzp[q].v[k1]));
+                const float2 hh = f_add(f_add(f_add(f_add(f_add(xm, xp), ym), yp), zm), zp);
+                h[q][k0] = hh.x;
+                h[q][k1] = hh.y;
+            }
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < 3; ++q)
+            h[q][0] = f_add(f_add(f_add(f_add(f_add(xm_of(0, q), xp_of(0, q)), to_c(nym[q].v[0])), to_c(nyp[q].v[0])),
+                                  to_c(nzm[q].v[0])),
+                            to_c(nzp[q].v[0]));
+    }
+}
+
+// Metropolis steps (ii)-(iii) for the V sites of one work item, given the
+// item's own spins s and the local fields h of step (i).  site0 is the
+// natural index of the item's first site (the FP64 schedule's counter), rank0
+// its rank within its colour class (the FP32 / FP16 schedule's; on a periodic
+// sc lattice the natural index halved, kept separately so that it stays exact
+// beyond 2^32 sites).  Updates s in place; returns whether any site was
+// accepted.
+template <int P, int V, bool MEAS>
+__device__ __forceinline__ bool update_item_h(Vec<typename Tr<P>::S, V> (&s)[3], const typename Tr<P>::C (&h)[3][V],
+                                              uint32_t site0, uint32_t rank0, int c, const PassArgs &a,
+                                              typename Tr<P>::C J, typename Tr<P>::C K, typename Tr<P>::C ex,
+                                              typename Tr<P>::C ey, typename Tr<P>::C ez, typename Tr<P>::C beta,
+                                              SiteAcc<P> &acc) {
     using S = typename Tr<P>::S;
     using C = typename Tr<P>::C;
     bool any = false;
-    // the x neighbours of site k: row parity p picks (xh-1, xh) or (xh, xh+1)
-    auto xm_of = [&](int k, int q) -> C { return p ? to_c(o[q].v[k]) : (k == 0 ? ed[q] : to_c(o[q].v[k - 1])); };
-    auto xp_of = [&](int k, int q) -> C { return p ? (k == V - 1 ? ed[q] : to_c(o[q].v[k + 1])) : to_c(o[q].v[k]); };
     if constexpr (P == HS_FP64) {
 #pragma unroll
         for (int k = 0; k < V; ++k) {
             C tx, ty, tz, u;
             draw_trial<P>(site0 + 2u * k, a.sweep, (uint32_t)c, a.replica, a.key0, a.key1, tx, ty, tz, u);
-            C h[3];
-#pragma unroll
-            for (int q = 0; q < 3; ++q)
-                h[q] = ((((xm_of(k, q) + xp_of(k, q)) + to_c(nym[q].v[k])) + to_c(nyp[q].v[k])) +
-                        to_c(nzm[q].v[k])) +
-                       to_c(nzp[q].v[k]);
             C sx = to_c(s[0].v[k]), sy = to_c(s[1].v[k]), sz = to_c(s[2].v[k]);
-            const SiteDots<C> d = metropolis<C>(sx, sy, sz, tx, ty, tz, h[0], h[1], h[2], J, K, ex, ey, ez, beta, u);
+            const SiteDots<C> d =
+                metropolis<C>(sx, sy, sz, tx, ty, tz, h[0][k], h[1][k], h[2][k], J, K, ex, ey, ez, beta, u);
             if (d.acc) {
                 sx = tx;
                 sy = ty;
@@ -501,14 +538,9 @@ __device__ __forceinline__ bool update_item(Vec<typename Tr<P>::S, V> (&s)[3], c
         const float nb = neg_beta_log2e(beta);
         // one site in lane x of the accumulators
         auto single = [&](int k, float tx, float ty, float tz, float u) {
-            float h[3];
-#pragma unroll
-            for (int q = 0; q < 3; ++q)
-                h[q] = f_add(f_add(f_add(f_add(f_add(xm_of(k, q), xp_of(k, q)), to_c(nym[q].v[k])), to_c(nyp[q].v[k])),
-                                     to_c(nzm[q].v[k])),
-                             to_c(nzp[q].v[k]));
             const float sx = to_c(s[0].v[k]), sy = to_c(s[1].v[k]), sz = to_c(s[2].v[k]);
-            const Dots32<float> d = site_math32<float>(sx, sy, sz, tx, ty, tz, h[0], h[1], h[2], J, K, ex, ey, ez);
+            const Dots32<float> d =
+                site_math32<float>(sx, sy, sz, tx, ty, tz, h[0][k], h[1][k], h[2][k], J, K, ex, ey, ez);
             const bool ac = accept32(d.dH, u, nb);
             if (ac) {
                 s[0].v[k] = to_store<S, C>(tx);
@@ -538,21 +570,14 @@ __device__ __forceinline__ bool update_item(Vec<typename Tr<P>::S, V> (&s)[3], c
                 half_ints(w.z, w.w, zi.y, vi.y, ui.y);
                 float2 tx, ty, tz, u;
                 trial32<P, float2>(zi, vi, ui, tx, ty, tz, u);
-                float2 h[3];
+                float2 hp[3];
 #pragma unroll
-                for (int q = 0; q < 3; ++q) {
-                    const float2 xm = make_float2(xm_of(k0, q), xm_of(k1, q));
-                    const float2 xp = make_float2(xp_of(k0, q), xp_of(k1, q));
-                    const float2 ym = make_float2(to_c(nym[q].v[k0]), to_c(nym[q].v[k1]));
-                    const float2 yp = make_float2(to_c(nyp[q].v[k0]), to_c(nyp[q].v[k1]));
-                    const float2 zm = make_float2(to_c(nzm[q].v[k0]), to_c(nzm[q].v[k1]));
-                    const float2 zp = make_float2(to_c(nzp[q].v[k0]), to_c(nzp[q].v[k1]));
-                    h[q] = f_add(f_add(f_add(f_add(f_add(xm, xp), ym), yp), zm), zp);
-                }
+                for (int q = 0; q < 3; ++q) hp[q] = make_float2(h[q][k0], h[q][k1]);
                 const float2 sx = make_float2(to_c(s[0].v[k0]), to_c(s[0].v[k1]));
                 const float2 sy = make_float2(to_c(s[1].v[k0]), to_c(s[1].v[k1]));
                 const float2 sz = make_float2(to_c(s[2].v[k0]), to_c(s[2].v[k1]));
-                const Dots32<float2> d = site_math32<float2>(sx, sy, sz, tx, ty, tz, h[0], h[1], h[2], J, K, ex, ey, ez);
+                const Dots32<float2> d =
+                    site_math32<float2>(sx, sy, sz, tx, ty, tz, hp[0], hp[1], hp[2], J, K, ex, ey, ez);
                 const bool a0 = accept32(d.dH.x, u.x, nb);
                 const bool a1 = accept32(d.dH.y, u.y, nb);
                 if (a0) {
@@ -589,6 +614,22 @@ __device__ __forceinline__ bool update_item(Vec<typename Tr<P>::S, V> (&s)[3], c
         }
     }
     return any;
+}
+
+// The same from the raw operands: step (i) then steps (ii)-(iii).
+template <int P, int V, bool MEAS>
+__device__ __forceinline__ bool update_item(Vec<typename Tr<P>::S, V> (&s)[3], const Vec<typename Tr<P>::S, V> (&o)[3],
+                                            const Vec<typename Tr<P>::S, V> (&nym)[3],
+                                            const Vec<typename Tr<P>::S, V> (&nyp)[3],
+                                            const Vec<typename Tr<P>::S, V> (&nzm)[3],
+                                            const Vec<typename Tr<P>::S, V> (&nzp)[3], const typename Tr<P>::C (&ed)[3],
+                                            uint32_t p, uint32_t site0, uint32_t rank0, int c, const PassArgs &a,
+                                            typename Tr<P>::C J, typename Tr<P>::C K, typename Tr<P>::C ex,
+                                            typename Tr<P>::C ey, typename Tr<P>::C ez, typename Tr<P>::C beta,
+                                            SiteAcc<P> &acc) {
+    typename Tr<P>::C h[3][V];
+    item_fields<P, V>(o, nym, nyp, nzm, nzp, ed, p, h);
+    return update_item_h<P, V, MEAS>(s, h, site0, rank0, c, a, J, K, ex, ey, ez, beta, acc);
 }
 
 // Vector load, optionally L2-only (ld.global.cg).  A kernel that reads data

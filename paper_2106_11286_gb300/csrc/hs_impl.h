@@ -104,7 +104,7 @@ struct Layout {
     int z0, nz, Lz_glob;    // first global plane, own planes, global Lz (slab); 0, Lz, Lz otherwise
     int kernel;             // KernelKind
     int vec;                // vector width of the stencil kernels
-    int prefetch;           // register stencil: 0 none, 1 next work item's loads in flight
+    int prefetch;           // register stencil: 0 none, 1 next work item in registers, 2 split prefetch
     int ty, zchunk, n_units, grid;  // staged stencil tiling and grid
     int ring_o, ring_w;             // staged stencil ring depths
     int consumers;                  // staged stencil consumer threads (128 or 256)

@@ -32,7 +32,14 @@ namespace {
 //   0  none;
 //   1  the loads of the thread's next work item are issued before the
 //      current one is computed (two items in flight in registers, unrolled by
-//      hand so no operand is copied).
+//      hand so no operand is copied);
+//   2  split prefetch: as soon as the current item's local fields are summed
+//      (its neighbour vectors are dead then), the next item's own row,
+//      same-row and z-1 / z+1 rows -- the operands most often in DRAM -- are
+//      loaded, so they travel during the current item's Metropolis
+//      arithmetic; the y-1 / y+1 rows (the rows of neighbouring work items
+//      of the same CTA, usually in L1 or L2) are loaded when an item is
+//      taken up.
 template <int P, int V, bool MEAS, int PF>
 __global__ void __launch_bounds__(kBlock, 2) sc_pass_kernel(const PassArgs a) {
     pdl_enter();
@@ -61,6 +68,53 @@ __global__ void __launch_bounds__(kBlock, 2) sc_pass_kernel(const PassArgs a) {
             StencilItem<P, V> it;
             load_item<P, V>(a, t, own, oth, it);
             compute(it);
+        }
+    } else if (PF == 2) {
+        struct PartA {
+            VT s[3], o[3], nzm[3], nzp[3];
+            C ed[3];
+            ItemOffsets f;
+        };
+        auto load_a = [&](uint32_t tt, PartA &A) {
+            const uint32_t nxv = a.Lh / V;
+            const uint32_t r = a.div_nxv.div(tt);
+            const uint32_t xv = tt - r * nxv;
+            const uint32_t row = r + (uint32_t)(a.z_off * a.Ly);
+            const uint32_t z = a.div_ly.div(row);
+            A.f = item_offsets<V>(a, row - z * a.Ly, z, xv);
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                A.s[q] = *reinterpret_cast<const VT *>(own[q] + A.f.b0);
+                A.o[q] = *reinterpret_cast<const VT *>(oth[q] + A.f.b0);
+                A.nzm[q] = *reinterpret_cast<const VT *>(oth[q] + A.f.bzm);
+                A.nzp[q] = *reinterpret_cast<const VT *>(oth[q] + A.f.bzp);
+                A.ed[q] = to_c(oth[q][A.f.bed]);
+            }
+        };
+        if (t < n_items) {
+            PartA A;
+            load_a(t, A);
+            while (true) {
+                VT nym[3], nyp[3];
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    nym[q] = *reinterpret_cast<const VT *>(oth[q] + A.f.bym);
+                    nyp[q] = *reinterpret_cast<const VT *>(oth[q] + A.f.byp);
+                }
+                C h[3][V];
+                item_fields<P, V>(A.o, nym, nyp, A.nzm, A.nzp, A.ed, A.f.p, h);
+                VT sv[3] = {A.s[0], A.s[1], A.s[2]};
+                const uint32_t b0 = A.f.b0, site0 = A.f.site0, rank0 = A.f.rank0;
+                const uint32_t tn = t + stride;
+                const bool more = tn < n_items;
+                if (more) load_a(tn, A);
+                if (update_item_h<P, V, MEAS>(sv, h, site0, rank0, c, a, J, K, ex, ey, ez, beta, acc)) {
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) *reinterpret_cast<VT *>(own_w[q] + b0) = sv[q];
+                }
+                if (!more) break;
+                t = tn;
+            }
         }
     } else if (t < n_items) {
         StencilItem<P, V> A, B;
@@ -836,6 +890,7 @@ cudaError_t launch_sc_pf(const PassArgs &a, int n_blocks, cudaStream_t s, bool m
 template <int P, int V>
 cudaError_t launch_sc_v(const PassArgs &a, int n_blocks, cudaStream_t s, bool meas, int pf) {
     if (pf == 1) return launch_sc_pf<P, V, 1>(a, n_blocks, s, meas);
+    if (pf == 2) return launch_sc_pf<P, V, 2>(a, n_blocks, s, meas);
     return launch_sc_pf<P, V, 0>(a, n_blocks, s, meas);
 }
 
@@ -987,6 +1042,7 @@ static const void *sc_ptr_pf(bool meas) {
 template <int P, int V>
 static const void *sc_ptr(bool meas, int pf) {
     if (pf == 1) return sc_ptr_pf<P, V, 1>(meas);
+    if (pf == 2) return sc_ptr_pf<P, V, 2>(meas);
     return sc_ptr_pf<P, V, 0>(meas);
 }
 

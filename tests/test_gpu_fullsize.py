@@ -62,6 +62,7 @@ FP32_LAUNCHES = {
     "autotuned": "autotuned",
     "stencil": dict(kernel="stencil", vec_width=4),
     "stencil_prefetch": dict(kernel="stencil", vec_width=4, prefetch=1),
+    "stencil_split": dict(kernel="stencil", vec_width=4, prefetch=3),
     "pipe": dict(kernel="pipe", vec_width=4),
     "march": dict(kernel="march", vec_width=4),
     "staged": dict(kernel="staged", vec_width=4),

@@ -231,6 +231,7 @@ def _launch_configs(precision, dims):
         if lh % v:
             continue
         out += [dict(kernel="stencil", vec_width=v, blocks_per_sm=1), dict(kernel="stencil", vec_width=v),
+                dict(kernel="stencil", vec_width=v, prefetch=3),
                 dict(kernel="stencil", vec_width=v, prefetch=1), dict(kernel="stencil", vec_width=v, prefetch=1,
                                                                        blocks_per_sm=1)]
         if 4 <= v * es <= 16:
