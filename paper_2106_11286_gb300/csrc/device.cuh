@@ -733,5 +733,48 @@ __device__ __forceinline__ void load_item(const PassArgs &a, uint32_t t, const t
     load_item_at<P, V, CG>(a, y, z, xv, own, oth, it);
 }
 
+// Split loading of the work item with linear index t (see the split
+// prefetch of the stencil kernels): part A -- the own row, the other colour's
+// same row (+ edge element) and its rows at z-1 and z+1 -- is loaded ahead;
+// part B -- the rows at y-1 and y+1 -- when the item is taken up.
+template <int P, int V>
+struct SplitItem {
+    Vec<typename Tr<P>::S, V> s[3], o[3], nzm[3], nzp[3];
+    typename Tr<P>::C ed[3];
+    ItemOffsets f;
+};
+
+template <int P, int V, bool CG = false>
+__device__ __forceinline__ void load_split_a(const PassArgs &a, uint32_t t, const typename Tr<P>::S *const (&own)[3],
+                                             const typename Tr<P>::S *const (&oth)[3], SplitItem<P, V> &A) {
+    using S = typename Tr<P>::S;
+    using VT = Vec<S, V>;
+    const uint32_t nxv = a.Lh / V;
+    const uint32_t r = a.div_nxv.div(t);
+    const uint32_t xv = t - r * nxv;
+    const uint32_t row = r + (uint32_t)(a.z_off * a.Ly);
+    const uint32_t z = a.div_ly.div(row);
+    A.f = item_offsets<V>(a, row - z * a.Ly, z, xv);
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        A.s[q] = ld_val<VT, CG>(reinterpret_cast<const VT *>(own[q] + A.f.b0));
+        A.o[q] = ld_val<VT, CG>(reinterpret_cast<const VT *>(oth[q] + A.f.b0));
+        A.nzm[q] = ld_val<VT, CG>(reinterpret_cast<const VT *>(oth[q] + A.f.bzm));
+        A.nzp[q] = ld_val<VT, CG>(reinterpret_cast<const VT *>(oth[q] + A.f.bzp));
+        A.ed[q] = to_c(ld_val<S, CG>(oth[q] + A.f.bed));
+    }
+}
+
+template <int P, int V, bool CG = false>
+__device__ __forceinline__ void load_split_b(const SplitItem<P, V> &A, const typename Tr<P>::S *const (&oth)[3],
+                                             Vec<typename Tr<P>::S, V> (&nym)[3], Vec<typename Tr<P>::S, V> (&nyp)[3]) {
+    using VT = Vec<typename Tr<P>::S, V>;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        nym[q] = ld_val<VT, CG>(reinterpret_cast<const VT *>(oth[q] + A.f.bym));
+        nyp[q] = ld_val<VT, CG>(reinterpret_cast<const VT *>(oth[q] + A.f.byp));
+    }
+}
+
 }  // namespace
 }  // namespace hs

@@ -70,44 +70,19 @@ __global__ void __launch_bounds__(kBlock, 2) sc_pass_kernel(const PassArgs a) {
             compute(it);
         }
     } else if (PF == 2) {
-        struct PartA {
-            VT s[3], o[3], nzm[3], nzp[3];
-            C ed[3];
-            ItemOffsets f;
-        };
-        auto load_a = [&](uint32_t tt, PartA &A) {
-            const uint32_t nxv = a.Lh / V;
-            const uint32_t r = a.div_nxv.div(tt);
-            const uint32_t xv = tt - r * nxv;
-            const uint32_t row = r + (uint32_t)(a.z_off * a.Ly);
-            const uint32_t z = a.div_ly.div(row);
-            A.f = item_offsets<V>(a, row - z * a.Ly, z, xv);
-#pragma unroll
-            for (int q = 0; q < 3; ++q) {
-                A.s[q] = *reinterpret_cast<const VT *>(own[q] + A.f.b0);
-                A.o[q] = *reinterpret_cast<const VT *>(oth[q] + A.f.b0);
-                A.nzm[q] = *reinterpret_cast<const VT *>(oth[q] + A.f.bzm);
-                A.nzp[q] = *reinterpret_cast<const VT *>(oth[q] + A.f.bzp);
-                A.ed[q] = to_c(oth[q][A.f.bed]);
-            }
-        };
         if (t < n_items) {
-            PartA A;
-            load_a(t, A);
+            SplitItem<P, V> A;
+            load_split_a<P, V>(a, t, own, oth, A);
             while (true) {
                 VT nym[3], nyp[3];
-#pragma unroll
-                for (int q = 0; q < 3; ++q) {
-                    nym[q] = *reinterpret_cast<const VT *>(oth[q] + A.f.bym);
-                    nyp[q] = *reinterpret_cast<const VT *>(oth[q] + A.f.byp);
-                }
+                load_split_b<P, V>(A, oth, nym, nyp);
                 C h[3][V];
                 item_fields<P, V>(A.o, nym, nyp, A.nzm, A.nzp, A.ed, A.f.p, h);
                 VT sv[3] = {A.s[0], A.s[1], A.s[2]};
                 const uint32_t b0 = A.f.b0, site0 = A.f.site0, rank0 = A.f.rank0;
                 const uint32_t tn = t + stride;
                 const bool more = tn < n_items;
-                if (more) load_a(tn, A);
+                if (more) load_split_a<P, V>(a, tn, own, oth, A);  // the neighbour vectors are dead now
                 if (update_item_h<P, V, MEAS>(sv, h, site0, rank0, c, a, J, K, ex, ey, ez, beta, acc)) {
 #pragma unroll
                     for (int q = 0; q < 3; ++q) *reinterpret_cast<VT *>(own_w[q] + b0) = sv[q];
