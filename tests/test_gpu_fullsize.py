@@ -118,13 +118,18 @@ def colour464(orc):
     return colour, ranks
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp16"])
-def test_464_sampled_sites(orc, colour464, precision):
+@pytest.mark.parametrize("precision,launch", [("fp64", None), ("fp32", None), ("fp16", None),
+                                             ("fp32", dict(kernel="stencil", vec_width=4, prefetch=3))],
+                         ids=["fp64", "fp32", "fp16", "fp32-split"])
+def test_464_sampled_sites(orc, colour464, precision, launch):
     colour, ranks = colour464
     beta, seed, sweep_index = 1.0, 5, 3
     with hs.Lattice("sc", dims=DIMS464, precision=precision, seed=seed, **PARAMS464) as lat:
         lat.init()
-        lat.autotune(beta, 2)
+        if launch is None:
+            lat.autotune(beta, 2)
+        else:
+            lat.set_launch(**launch)
         lat.set_sweep_counter(sweep_index)
         S0 = lat.get_spins()
         lat.sweep(beta, 1)

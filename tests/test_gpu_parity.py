@@ -250,7 +250,9 @@ def _launch_configs(precision, dims):
 
 
 @pytest.mark.parametrize("precision,dims", [("fp32", (16, 8, 6)), ("fp16", (32, 8, 4)), ("fp64", (8, 12, 8)),
-                                            ("fp32", (8, 4, 2))])
+                                            ("fp32", (8, 4, 2)),
+                                            # rows of 36 vectors: split prefetch on rows wider than a warp
+                                            ("fp32", (288, 16, 4)), ("fp16", (288, 8, 6))])
 def test_launch_configuration_does_not_change_results(precision, dims):
     """A site's random numbers and arithmetic depend only on its natural index,
     so every kernel, vector width, slab and chunk gives bit-identical chains;
