@@ -10,6 +10,11 @@
  * What it follows (arXiv 2106.11286):
  *   - Eq. 1:  H = -J sum_<ij> S_i.S_j - K sum_i (S_i.e)^2, |S_i| = 1
  *             (each nearest-neighbour bond counted once).
+ *   - The effective shape anisotropy the paper names as the stand-in for
+ *             dipolar coupling (introduction, GPU implementation paragraph),
+ *             read as a general on-site quadratic term -sum_i S_i^T A S_i
+ *             with one symmetric 3x3 tensor A for every site, stored as
+ *             (Axx, Ayy, Azz, Axy, Axz, Ayz); A = NULL means no such term.
  *   - Metropolis steps (i)-(iii): pick a site, propose a new orientation at
  *             random, accept if dH <= 0, else accept iff P <= exp(-beta dH)
  *             with P uniform in [0,1).
@@ -418,12 +423,27 @@ void or_init_sites(int64_t m, const int64_t *sites, uint64_t seed, uint32_t repl
         or_init_site(seed, replica, (uint64_t)sites[t], &S[3 * t]);
 }
 
-/* Single-site energy -J S.h - K (S.e)^2 for a given local field h. */
-static double site_energy(const double s[3], const double h[3], double J, double K, const double e[3])
+/* S^T A S for the symmetric tensor A = (Axx, Ayy, Azz, Axy, Axz, Ayz):
+ * the matrix-vector product A S, then its dot product with S. */
+static double quad_form(const double A[6], const double s[3])
+{
+    double As0 = A[0] * s[0] + A[3] * s[1] + A[4] * s[2];
+    double As1 = A[3] * s[0] + A[1] * s[1] + A[5] * s[2];
+    double As2 = A[4] * s[0] + A[5] * s[1] + A[2] * s[2];
+    return s[0] * As0 + s[1] * As1 + s[2] * As2;
+}
+
+/* Single-site energy -J S.h - K (S.e)^2 - S^T A S for a given local field h
+ * (the last term only when A is given). */
+static double site_energy(const double s[3], const double h[3], double J, double K, const double e[3],
+                          const double *A)
 {
     double sh = s[0] * h[0] + s[1] * h[1] + s[2] * h[2];
     double se = s[0] * e[0] + s[1] * e[1] + s[2] * e[2];
-    return -J * sh - K * se * se;
+    double E = -J * sh - K * se * se;
+    if (A)
+        E -= quad_form(A, s);
+    return E;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -435,8 +455,8 @@ static double site_energy(const double s[3], const double h[3], double J, double
 /* decision with |beta dH + ln P| < band.                                   */
 /* ------------------------------------------------------------------------ */
 int or_site_update(int mode, uint64_t seed, uint32_t replica, uint64_t site, uint64_t rank, uint64_t sweep,
-                   uint32_t colour, double J, double K, const double e[3], double beta, double band,
-                   const double h[3], double s[3], double *dH_out, int *in_band)
+                   uint32_t colour, double J, double K, const double e[3], const double *A, double beta,
+                   double band, const double h[3], double s[3], double *dH_out, int *in_band)
 {
     double u[3];
     or_trial_uniforms(mode, seed, replica, site, rank, sweep, colour, u);
@@ -447,7 +467,7 @@ int or_site_update(int mode, uint64_t seed, uint32_t replica, uint64_t site, uin
         trial[1] = or_round_half(trial[1]);
         trial[2] = or_round_half(trial[2]);
     }
-    double dH = site_energy(trial, h, J, K, e) - site_energy(s, h, J, K, e);
+    double dH = site_energy(trial, h, J, K, e, A) - site_energy(s, h, J, K, e, A);
     double P = u[2];
     int accept;
     *in_band = 0;
@@ -473,14 +493,15 @@ int or_site_update(int mode, uint64_t seed, uint32_t replica, uint64_t site, uin
  * in_band[t] get the decisions. */
 void or_sites_update(int64_t m, const int64_t *site, const int64_t *rank, const int32_t *colour, const double *h,
                      double *s, int mode, uint64_t seed, uint32_t replica, uint64_t sweep, double J, double K,
-                     const double e[3], double beta, double band, uint8_t *accepted, uint8_t *in_band)
+                     const double e[3], const double *A, double beta, double band, uint8_t *accepted,
+                     uint8_t *in_band)
 {
     for (int64_t t = 0; t < m; ++t) {
         double dH;
         int b;
         accepted[t] = (uint8_t)or_site_update(mode, seed, replica, (uint64_t)site[t], (uint64_t)rank[t], sweep,
-                                              (uint32_t)colour[t], J, K, e, beta, band, &h[3 * t], &s[3 * t], &dH,
-                                              &b);
+                                              (uint32_t)colour[t], J, K, e, A, beta, band, &h[3 * t], &s[3 * t],
+                                              &dH, &b);
         in_band[t] = (uint8_t)b;
     }
 }
@@ -498,7 +519,7 @@ void or_sites_update(int64_t m, const int64_t *site, const int64_t *rank, const 
 /* (optional, n bytes) is set to 1 at those sites.                          */
 /* ------------------------------------------------------------------------ */
 int64_t or_sweep(int64_t n, const int64_t *row_ptr, const int32_t *col, const int32_t *colour,
-                 int n_colours, const uint8_t *mask, double J, double K, const double e[3],
+                 int n_colours, const uint8_t *mask, double J, double K, const double e[3], const double *A,
                  double beta, uint64_t seed, uint32_t replica, uint64_t sweep, int mode, double band,
                  double *S, double *sum_dH, int64_t *n_band, uint8_t *band_site)
 {
@@ -526,8 +547,8 @@ int64_t or_sweep(int64_t n, const int64_t *row_ptr, const int32_t *col, const in
             /* steps (ii)-(iii) */
             double dH;
             int in_band;
-            if (or_site_update(mode, seed, replica, (uint64_t)i, my_rank, sweep, (uint32_t)c, J, K, e, beta, band,
-                               h, &S[3 * i], &dH, &in_band)) {
+            if (or_site_update(mode, seed, replica, (uint64_t)i, my_rank, sweep, (uint32_t)c, J, K, e, A, beta,
+                               band, h, &S[3 * i], &dH, &in_band)) {
                 dH_total += dH;
                 ++accepted;
             }
@@ -547,11 +568,11 @@ int64_t or_sweep(int64_t n, const int64_t *row_ptr, const int32_t *col, const in
 
 /* Total energy, Eq. 1, full recompute: every undirected bond once (pairs
  * listed as j > i in a symmetric neighbour list), plus the anisotropy of
- * every present site. */
+ * every present site (and its tensor term when A is given). */
 double or_energy(int64_t n, const int64_t *row_ptr, const int32_t *col, const uint8_t *mask, double J,
-                 double K, const double e[3], const double *S)
+                 double K, const double e[3], const double *A, const double *S)
 {
-    double exch = 0.0, anis = 0.0;
+    double exch = 0.0, anis = 0.0, tens = 0.0;
     for (int64_t i = 0; i < n; ++i) {
         if (mask && !mask[i])
             continue;
@@ -567,8 +588,10 @@ double or_energy(int64_t n, const int64_t *row_ptr, const int32_t *col, const ui
         }
         double se = si[0] * e[0] + si[1] * e[1] + si[2] * e[2];
         anis += se * se;
+        if (A)
+            tens += quad_form(A, si);
     }
-    return -J * exch - K * anis;
+    return -J * exch - K * anis - tens;
 }
 
 /* Sum of the present spins (numerator of Eq. 2); returns the count N. */

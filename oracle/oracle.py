@@ -78,7 +78,7 @@ def lib():
         L.or_init_spins.argtypes = [ctypes.c_int64, u8p, ctypes.c_uint64, ctypes.c_uint32, dp]
         L.or_init_spins.restype = None
         L.or_sweep.argtypes = [ctypes.c_int64, i64p, i32p, i32p, ctypes.c_int, u8p,
-                               ctypes.c_double, ctypes.c_double, dp, ctypes.c_double,
+                               ctypes.c_double, ctypes.c_double, dp, dp, ctypes.c_double,
                                ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int,
                                ctypes.c_double, dp, dp, i64p, u8p]
         L.or_sweep.restype = ctypes.c_int64
@@ -91,10 +91,10 @@ def lib():
                                               i64p]
         L.or_sc_sites_colour_rank.restype = None
         L.or_sites_update.argtypes = [ctypes.c_int64, i64p, i64p, i32p, dp, dp, ctypes.c_int, ctypes.c_uint64,
-                                      ctypes.c_uint32, ctypes.c_uint64, ctypes.c_double, ctypes.c_double, dp,
+                                      ctypes.c_uint32, ctypes.c_uint64, ctypes.c_double, ctypes.c_double, dp, dp,
                                       ctypes.c_double, ctypes.c_double, u8p, u8p]
         L.or_sites_update.restype = None
-        L.or_energy.argtypes = [ctypes.c_int64, i64p, i32p, u8p, ctypes.c_double, ctypes.c_double, dp, dp]
+        L.or_energy.argtypes = [ctypes.c_int64, i64p, i32p, u8p, ctypes.c_double, ctypes.c_double, dp, dp, dp]
         L.or_energy.restype = ctypes.c_double
         L.or_spin_sum.argtypes = [ctypes.c_int64, u8p, dp, dp]
         L.or_spin_sum.restype = ctypes.c_int64
@@ -106,6 +106,20 @@ def _p(a, ctype):
     if a is None:
         return None
     return a.ctypes.data_as(ctypes.POINTER(ctype))
+
+
+def _tensor(A):
+    """The on-site anisotropy tensor as the C side takes it: None, or the six
+    entries (Axx, Ayy, Azz, Axy, Axz, Ayz) of the symmetric A in S^T A S
+    (a 3x3 array is accepted and must be symmetric)."""
+    if A is None:
+        return None
+    A = np.asarray(A, dtype=np.float64)
+    if A.shape == (3, 3):
+        assert np.array_equal(A, A.T)
+        A = np.array([A[0, 0], A[1, 1], A[2, 2], A[0, 1], A[0, 2], A[1, 2]])
+    assert A.shape == (6,)
+    return np.ascontiguousarray(A)
 
 
 # --------------------------------------------------------------------------- RNG
@@ -206,16 +220,18 @@ def init_spins(g: Graph, seed: int, replica: int = 0) -> np.ndarray:
 
 def sweep(g: Graph, S: np.ndarray, *, J: float, K: float, e, beta: float, seed: int,
           sweep_index: int, replica: int = 0, mode: int = MODE_FP64, band: float = 0.0,
-          band_site: np.ndarray | None = None):
-    """One Metropolis sweep in place.  Returns (accepted, sum of accepted dH, band count)."""
+          band_site: np.ndarray | None = None, A=None):
+    """One Metropolis sweep in place.  Returns (accepted, sum of accepted dH, band count).
+    A: optional on-site anisotropy tensor (see _tensor)."""
     assert S.dtype == np.float64 and S.flags.c_contiguous and S.shape == (g.n, 3)
     ev = np.ascontiguousarray(e, dtype=np.float64)
     ev = ev / np.linalg.norm(ev)
+    At = _tensor(A)
     sdh = ctypes.c_double(0.0)
     nb = ctypes.c_int64(0)
     acc = lib().or_sweep(g.n, _p(g.row_ptr, ctypes.c_int64), _p(g.col, ctypes.c_int32),
                          _p(g.colour, ctypes.c_int32), g.n_colours, _p(g.mask, ctypes.c_uint8),
-                         float(J), float(K), _p(ev, ctypes.c_double), float(beta), int(seed),
+                         float(J), float(K), _p(ev, ctypes.c_double), _p(At, ctypes.c_double), float(beta), int(seed),
                          int(replica), int(sweep_index), int(mode), float(band),
                          _p(S, ctypes.c_double), ctypes.byref(sdh), ctypes.byref(nb),
                          _p(band_site, ctypes.c_uint8))
@@ -254,7 +270,7 @@ def sc_sites_colour_rank(dims, sites):
 
 
 def sites_update(sites, ranks, colours, h, S, *, J: float, K: float, e, beta: float, seed: int,
-                 sweep_index: int, replica: int = 0, mode: int = MODE_FP64, band: float = 0.0):
+                 sweep_index: int, replica: int = 0, mode: int = MODE_FP64, band: float = 0.0, A=None):
     """Metropolis steps (ii)-(iii) at sampled sites whose local fields h (m x 3,
     step (i)) are given, exactly as one sweep applies them.  S (m x 3) is
     updated in place; returns (accepted, in_band) as bool arrays."""
@@ -267,20 +283,23 @@ def sites_update(sites, ranks, colours, h, S, *, J: float, K: float, e, beta: fl
     ev = ev / np.linalg.norm(ev)
     acc = np.zeros(len(sites), dtype=np.uint8)
     band_flag = np.zeros(len(sites), dtype=np.uint8)
+    At = _tensor(A)
     lib().or_sites_update(len(sites), _p(sites, ctypes.c_int64), _p(ranks, ctypes.c_int64),
                           _p(colours, ctypes.c_int32), _p(h, ctypes.c_double), _p(S, ctypes.c_double), int(mode),
                           int(seed), int(replica), int(sweep_index), float(J), float(K), _p(ev, ctypes.c_double),
-                          float(beta), float(band), _p(acc, ctypes.c_uint8), _p(band_flag, ctypes.c_uint8))
+                          _p(At, ctypes.c_double), float(beta), float(band), _p(acc, ctypes.c_uint8),
+                          _p(band_flag, ctypes.c_uint8))
     return acc.astype(bool), band_flag.astype(bool)
 
 
-def energy(g: Graph, S: np.ndarray, *, J: float, K: float, e) -> float:
+def energy(g: Graph, S: np.ndarray, *, J: float, K: float, e, A=None) -> float:
     ev = np.ascontiguousarray(e, dtype=np.float64)
     ev = ev / np.linalg.norm(ev)
     S = np.ascontiguousarray(S, dtype=np.float64)
+    At = _tensor(A)
     return lib().or_energy(g.n, _p(g.row_ptr, ctypes.c_int64), _p(g.col, ctypes.c_int32),
                            _p(g.mask, ctypes.c_uint8), float(J), float(K),
-                           _p(ev, ctypes.c_double), _p(S, ctypes.c_double))
+                           _p(ev, ctypes.c_double), _p(At, ctypes.c_double), _p(S, ctypes.c_double))
 
 
 def spin_sum(g: Graph, S: np.ndarray):
@@ -290,9 +309,9 @@ def spin_sum(g: Graph, S: np.ndarray):
     return out, int(n)
 
 
-def measure(g: Graph, S: np.ndarray, *, J: float, K: float, e) -> dict:
+def measure(g: Graph, S: np.ndarray, *, J: float, K: float, e, A=None) -> dict:
     """Instantaneous observables: E (Eq. 1) and M (Eq. 2, |S| = 1) with its moments."""
-    E = energy(g, S, J=J, K=K, e=e)
+    E = energy(g, S, J=J, K=K, e=e, A=A)
     tot, n = spin_sum(g, S)
     M = tot / n
     absM = float(np.sqrt(M @ M))
