@@ -9,6 +9,10 @@
  *           accept if dH <= 0, else accept iff P <= exp(-beta dH), P uniform
  *           in [0,1).
  *   Eq. 2   M = (1 / (N |S|)) sum_i S_i with N the number of present spins.
+ *   Optional on-site tensor term -sum_i S_i^T A S_i (one symmetric 3x3 A
+ *           for all sites): the effective shape anisotropy the paper offers
+ *           in place of dipolar coupling (introduction), read as a general
+ *           quadratic on-site anisotropy; see hs_set_anisotropy_tensor.
  *
  * Parallel decomposition (the paper's own racy block scheme is replaced):
  * the neighbour graph is split into colour classes (independent sets); a
@@ -253,6 +257,22 @@ typedef struct {
  * fit in shared memory; HS_E_INVALID otherwise. */
 int hs_set_launch(hs_lattice *h, const hs_launch *cfg);
 int hs_get_launch(const hs_lattice *h, hs_launch *out);
+
+/* On-site anisotropy tensor: adds -sum_i S_i^T A S_i to Eq. 1 (to dH in
+ * Metropolis step (iii), to E in hs_measure and in the fused per-sweep
+ * reductions), with A symmetric, given as its six entries
+ * A = (Axx, Ayy, Azz, Axy, Axz, Ayz); S^T A S = Axx x^2 + Ayy y^2 + Azz z^2
+ * + 2 (Axy xy + Axz xz + Ayz yz).  A = NULL or all zeros removes the term.
+ * The uniaxial term is the special case A = K e e^T.  Kernels: the register
+ * stencil without prefetch (periodic sc) and the neighbour table (everything
+ * else); the staged, pipelined and z-march kernels and hs_batch_create reject
+ * a lattice that has the term.  Setting the tensor resets the launch
+ * configuration to automatic.  Entries must be finite (HS_E_INVALID
+ * otherwise; nothing changes then).  The FP32 / FP16 kernels use the entries
+ * rounded to FP32.  hs_get_anisotropy_tensor reads them back (zeros when
+ * the term is off). */
+int hs_set_anisotropy_tensor(hs_lattice *h, const double A[6]);
+int hs_get_anisotropy_tensor(const hs_lattice *h, double A[6]);
 
 /* Autotuner: time every valid launch configuration (kernel, vector width,
  * CTAs per SM or slab rows and z chunk) for n_trial_sweeps sweeps at beta

@@ -196,6 +196,8 @@ struct hs_lattice {
     uint64_t sweep = 0;
     int accumulate = 0;
     int64_t last_n_sweeps = 0;
+    int tensor = 0;                // on-site anisotropy tensor term on
+    double tA[6] = {0, 0, 0, 0, 0, 0};
     Layout L{};
     int n_blocks = 1;
     int inject_timeout = 0;  // test hook, consumed by the next staged pass
@@ -272,6 +274,11 @@ PassArgs base_args(const hs_lattice *h) {
     a.key0 = (uint32_t)h->seed;
     a.key1 = (uint32_t)(h->seed >> 32);
     a.replica = h->replica;
+    a.tensor = h->tensor;
+    for (int q = 0; q < 6; ++q) {
+        a.A[q] = h->tA[q];
+        a.fA[q] = (float)h->tA[q];
+    }
     a.partials = h->partials;
     a.n_blocks = h->n_blocks;
     a.n_present = (double)L.n_present;
@@ -398,6 +405,7 @@ bool staged_ok(const hs_lattice *h) {
 int configure_launch(hs_lattice *h) {
     Layout &L = h->L;
     const hs_launch &r = h->req;
+    L.tensor = h->tensor;
     if (!L.structured) {
         L.kernel = hs::kTable;
         int bps = r.blocks_per_sm;
@@ -417,6 +425,8 @@ int configure_launch(hs_lattice *h) {
     // automatic choice: the register stencil (measured faster than the staged
     // kernel on GB300 at 256^3 and 464^3; hs_autotune compares both)
     if (kind == HS_KERNEL_AUTO) kind = HS_KERNEL_STENCIL;
+    if (h->tensor && (kind != HS_KERNEL_STENCIL || r.prefetch == 1 || r.prefetch == 3))
+        return fail(HS_E_INVALID, "the anisotropy tensor term runs on the register stencil without prefetch");
     if (kind == HS_KERNEL_STAGED) {
         if (!staged_ok(h)) return fail(HS_E_INVALID, "staged kernel needs Lx/2 * storage bytes divisible by 16");
         const int ring = r.ring ? r.ring : 5;
@@ -493,7 +503,9 @@ int configure_launch(hs_lattice *h) {
     // automatic: split prefetch when a CTA's items span 8 rows or more, so the
     // y-1 / y+1 rows it loads late are mostly its own (measured faster at
     // 256^3 FP32, slower at 464^3 and 1024^3)
-    if (r.prefetch == 0)
+    if (h->tensor)
+        L.prefetch = 0;
+    else if (r.prefetch == 0)
         L.prefetch = (h->precision == HS_FP32 && L.Lh / L.vec <= hs::kBlock / 8) ? 2 : 0;
     else
         L.prefetch = r.prefetch == 1 ? 1 : (r.prefetch == 3 ? 2 : 0);
@@ -1039,6 +1051,42 @@ int hs_set_launch(hs_lattice *h, const hs_launch *cfg) {
     return st;
 }
 
+int hs_set_anisotropy_tensor(hs_lattice *h, const double A[6]) {
+    if (!h) return fail(HS_E_INVALID, "null handle");
+    double t[6] = {0, 0, 0, 0, 0, 0};
+    if (A)
+        for (int q = 0; q < 6; ++q) {
+            if (!std::isfinite(A[q])) return fail(HS_E_INVALID, "tensor entries must be finite");
+            t[q] = A[q];
+        }
+    int on = 0;
+    for (int q = 0; q < 6; ++q) on |= (t[q] != 0.0);
+    const int keep_on = h->tensor;
+    double keep_t[6];
+    for (int q = 0; q < 6; ++q) keep_t[q] = h->tA[q];
+    const hs_launch keep_req = h->req;
+    const Layout keep_l = h->L;
+    const int keep_b = h->n_blocks;
+    h->tensor = on;
+    for (int q = 0; q < 6; ++q) h->tA[q] = t[q];
+    h->req = hs_launch{};  // back to the automatic launch, which takes the tensor into account
+    int st = configure_launch(h);
+    if (st) {
+        h->tensor = keep_on;
+        for (int q = 0; q < 6; ++q) h->tA[q] = keep_t[q];
+        h->req = keep_req;
+        h->L = keep_l;
+        h->n_blocks = keep_b;
+    }
+    return st;
+}
+
+int hs_get_anisotropy_tensor(const hs_lattice *h, double A[6]) {
+    if (!h || !A) return fail(HS_E_INVALID, "null argument");
+    for (int q = 0; q < 6; ++q) A[q] = h->tensor ? h->tA[q] : 0.0;
+    return HS_OK;
+}
+
 int hs_get_launch(const hs_lattice *h, hs_launch *out) {
     if (!h || !out) return fail(HS_E_INVALID, "null argument");
     const Layout &L = h->L;
@@ -1055,11 +1103,11 @@ int hs_get_launch(const hs_lattice *h, hs_launch *out) {
 
 namespace {
 struct TuneKey {
-    int precision, structured, accumulate;
+    int precision, structured, accumulate, tensor;
     int64_t a, b, c, d;
     bool operator<(const TuneKey &o) const {
-        return std::tie(precision, structured, accumulate, a, b, c, d) <
-               std::tie(o.precision, o.structured, o.accumulate, o.a, o.b, o.c, o.d);
+        return std::tie(precision, structured, accumulate, tensor, a, b, c, d) <
+               std::tie(o.precision, o.structured, o.accumulate, o.tensor, o.a, o.b, o.c, o.d);
     }
 };
 std::mutex g_tune_mu;
@@ -1112,7 +1160,7 @@ int hs_autotune(hs_lattice *h, double beta, int n_trial_sweeps) {
     if (n_trial_sweeps < 1) return fail(HS_E_INVALID, "n_trial_sweeps must be >= 1");
     if (h->L.n_present == 0 || h->L.slab) return HS_OK;  // a slab keeps the register stencil
     const Layout &L = h->L;
-    const TuneKey key{h->precision, L.structured ? 1 : 0, h->accumulate, L.structured ? L.Lx : L.n_present,
+    const TuneKey key{h->precision, L.structured ? 1 : 0, h->accumulate, h->tensor, L.structured ? L.Lx : L.n_present,
                       L.structured ? L.Ly : L.width, L.structured ? L.Lz : L.n_colours, h->n_sm};
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -1237,6 +1285,7 @@ int hs_batch_create(hs_batch **out, hs_lattice *const *members, int n_members) {
             return fail(HS_E_INVALID, "members must share one stream and device");
         if (!h->L.structured || h->L.slab || h->precision != HS_FP32 || h->L.Lh % 4 != 0)
             return fail(HS_E_INVALID, "batch members must be FP32 unmasked periodic sc with Lx divisible by 8");
+        if (h->tensor) return fail(HS_E_INVALID, "batch members take no anisotropy tensor term");
         for (int q = 0; q < r; ++q)
             if (members[q] == h) return fail(HS_E_INVALID, "a lattice appears twice in the batch");
     }

@@ -207,17 +207,43 @@ __device__ __forceinline__ void draw_trial_rank(uint32_t rank, uint32_t sweep, u
 template <typename T>
 struct Dots32 {
     T sh, th, se, pe, dH;
+    T qs, qt;  // S^T A S and S'^T A S' (tensor term only)
 };
 
+// The on-site anisotropy tensor term S^T A S of a general symmetric A (the
+// effective shape anisotropy the paper offers in place of dipolar coupling),
+// A = (xx, yy, zz, xy, xz, yz): the product A S row by row, then its dot
+// product with S.
 template <typename T>
+__device__ __forceinline__ T quad32(T x, T y, T z, const float (&A)[6]) {
+    const T ax = f_fma(splat<T>(A[4]), z, f_fma(splat<T>(A[3]), y, f_mul(splat<T>(A[0]), x)));
+    const T ay = f_fma(splat<T>(A[5]), z, f_fma(splat<T>(A[1]), y, f_mul(splat<T>(A[3]), x)));
+    const T az = f_fma(splat<T>(A[2]), z, f_fma(splat<T>(A[5]), y, f_mul(splat<T>(A[4]), x)));
+    return f_fma(z, az, f_fma(y, ay, f_mul(x, ax)));
+}
+__device__ __forceinline__ double quad64(double x, double y, double z, const double (&A)[6]) {
+    const double ax = A[0] * x + A[3] * y + A[4] * z;
+    const double ay = A[3] * x + A[1] * y + A[5] * z;
+    const double az = A[4] * x + A[5] * y + A[2] * z;
+    return x * ax + y * ay + z * az;
+}
+
+// TEN adds the tensor term: dH += S^T A S - S'^T A S'.
+template <typename T, bool TEN = false>
 __device__ __forceinline__ Dots32<T> site_math32(T sx, T sy, T sz, T tx, T ty, T tz, T hx, T hy, T hz, float J,
-                                                 float K, float ex, float ey, float ez) {
+                                                 float K, float ex, float ey, float ez, const float *A = nullptr) {
     Dots32<T> d;
     d.sh = f_fma(sz, hz, f_fma(sy, hy, f_mul(sx, hx)));
     d.th = f_fma(tz, hz, f_fma(ty, hy, f_mul(tx, hx)));
     d.se = f_fma(sz, splat<T>(ez), f_fma(sy, splat<T>(ey), f_mul(sx, splat<T>(ex))));
     d.pe = f_fma(tz, splat<T>(ez), f_fma(ty, splat<T>(ey), f_mul(tx, splat<T>(ex))));
     d.dH = f_fma(splat<T>(K), f_mul(f_sub(d.se, d.pe), f_add(d.se, d.pe)), f_mul(splat<T>(J), f_sub(d.sh, d.th)));
+    if constexpr (TEN) {
+        const float(&At)[6] = *reinterpret_cast<const float(*)[6]>(A);
+        d.qs = quad32<T>(sx, sy, sz, At);
+        d.qt = quad32<T>(tx, ty, tz, At);
+        d.dH = f_add(d.dH, f_sub(d.qs, d.qt));
+    }
     return d;
 }
 
@@ -238,6 +264,7 @@ template <> __device__ __forceinline__ __half to_store<__half, float>(float v) {
 template <typename C>
 struct SiteDots {
     C sh, th, se, pe;
+    C qs, qt;  // tensor term only
     bool acc;
 };
 
@@ -259,15 +286,21 @@ __device__ __forceinline__ bool accept64(double x, double u) {
     return u <= exp(x);
 }
 
-template <typename C>
+template <typename C, bool TEN = false>
 __device__ __forceinline__ SiteDots<C> metropolis(C sx, C sy, C sz, C tx, C ty, C tz, C hx, C hy, C hz, C J, C K,
-                                                  C ex, C ey, C ez, C beta, C u) {
+                                                  C ex, C ey, C ez, C beta, C u, const double *A = nullptr) {
     SiteDots<C> d;
     d.sh = sx * hx + sy * hy + sz * hz;
     d.th = tx * hx + ty * hy + tz * hz;
     d.se = sx * ex + sy * ey + sz * ez;
     d.pe = tx * ex + ty * ey + tz * ez;
-    const C dH = J * (d.sh - d.th) + K * ((d.se - d.pe) * (d.se + d.pe));
+    C dH = J * (d.sh - d.th) + K * ((d.se - d.pe) * (d.se + d.pe));
+    if constexpr (TEN) {
+        const double(&At)[6] = *reinterpret_cast<const double(*)[6]>(A);
+        d.qs = quad64(sx, sy, sz, At);
+        d.qt = quad64(tx, ty, tz, At);
+        dH += d.qs - d.qt;
+    }
     d.acc = (dH <= C(0)) || accept64(-beta * dH, u);
     return d;
 }
@@ -495,7 +528,7 @@ __device__ __forceinline__ void item_fields(const Vec<typename Tr<P>::S, V> (&o)
 // sc lattice the natural index halved, kept separately so that it stays exact
 // beyond 2^32 sites).  Updates s in place; returns whether any site was
 // accepted.
-template <int P, int V, bool MEAS>
+template <int P, int V, bool MEAS, bool TEN = false>
 __device__ __forceinline__ bool update_item_h(Vec<typename Tr<P>::S, V> (&s)[3], const typename Tr<P>::C (&h)[3][V],
                                               uint32_t site0, uint32_t rank0, int c, const PassArgs &a,
                                               typename Tr<P>::C J, typename Tr<P>::C K, typename Tr<P>::C ex,
@@ -510,8 +543,8 @@ __device__ __forceinline__ bool update_item_h(Vec<typename Tr<P>::S, V> (&s)[3],
             C tx, ty, tz, u;
             draw_trial<P>(site0 + 2u * k, a.sweep, (uint32_t)c, a.replica, a.key0, a.key1, tx, ty, tz, u);
             C sx = to_c(s[0].v[k]), sy = to_c(s[1].v[k]), sz = to_c(s[2].v[k]);
-            const SiteDots<C> d =
-                metropolis<C>(sx, sy, sz, tx, ty, tz, h[0][k], h[1][k], h[2][k], J, K, ex, ey, ez, beta, u);
+            const SiteDots<C> d = metropolis<C, TEN>(sx, sy, sz, tx, ty, tz, h[0][k], h[1][k], h[2][k], J, K, ex,
+                                                     ey, ez, beta, u, a.A);
             if (d.acc) {
                 sx = tx;
                 sy = ty;
@@ -527,6 +560,7 @@ __device__ __forceinline__ bool update_item_h(Vec<typename Tr<P>::S, V> (&s)[3],
                 // every sc bond, pass 0 only the anisotropy term
                 const C e_new = d.acc ? d.pe : d.se;
                 C ei = -K * e_new * e_new;
+                if (TEN) ei -= d.acc ? d.qt : d.qs;
                 if (c == 1) ei -= J * (d.acc ? d.th : d.sh);
                 acc.e += ei;
                 acc.x += sx;
@@ -539,8 +573,8 @@ __device__ __forceinline__ bool update_item_h(Vec<typename Tr<P>::S, V> (&s)[3],
         // one site in lane x of the accumulators
         auto single = [&](int k, float tx, float ty, float tz, float u) {
             const float sx = to_c(s[0].v[k]), sy = to_c(s[1].v[k]), sz = to_c(s[2].v[k]);
-            const Dots32<float> d =
-                site_math32<float>(sx, sy, sz, tx, ty, tz, h[0][k], h[1][k], h[2][k], J, K, ex, ey, ez);
+            const Dots32<float> d = site_math32<float, TEN>(sx, sy, sz, tx, ty, tz, h[0][k], h[1][k], h[2][k], J, K,
+                                                            ex, ey, ez, a.fA);
             const bool ac = accept32(d.dH, u, nb);
             if (ac) {
                 s[0].v[k] = to_store<S, C>(tx);
@@ -552,6 +586,7 @@ __device__ __forceinline__ bool update_item_h(Vec<typename Tr<P>::S, V> (&s)[3],
             if (MEAS) {
                 const float en = ac ? d.pe : d.se;
                 float ei = f_mul(-K, f_mul(en, en));
+                if (TEN) ei = f_sub(ei, ac ? d.qt : d.qs);
                 if (c == 1) ei = f_fma(-J, ac ? d.th : d.sh, ei);
                 acc.e.x = f_add(acc.e.x, ei);
                 acc.x.x = f_add(acc.x.x, ac ? tx : sx);
@@ -577,7 +612,7 @@ __device__ __forceinline__ bool update_item_h(Vec<typename Tr<P>::S, V> (&s)[3],
                 const float2 sy = make_float2(to_c(s[1].v[k0]), to_c(s[1].v[k1]));
                 const float2 sz = make_float2(to_c(s[2].v[k0]), to_c(s[2].v[k1]));
                 const Dots32<float2> d =
-                    site_math32<float2>(sx, sy, sz, tx, ty, tz, hp[0], hp[1], hp[2], J, K, ex, ey, ez);
+                    site_math32<float2, TEN>(sx, sy, sz, tx, ty, tz, hp[0], hp[1], hp[2], J, K, ex, ey, ez, a.fA);
                 const bool a0 = accept32(d.dH.x, u.x, nb);
                 const bool a1 = accept32(d.dH.y, u.y, nb);
                 if (a0) {
@@ -596,6 +631,7 @@ __device__ __forceinline__ bool update_item_h(Vec<typename Tr<P>::S, V> (&s)[3],
                 if (MEAS) {
                     const float2 en = make_float2(a0 ? d.pe.x : d.se.x, a1 ? d.pe.y : d.se.y);
                     float2 ei = f_mul(splat<float2>(-K), f_mul(en, en));
+                    if (TEN) ei = f_sub(ei, make_float2(a0 ? d.qt.x : d.qs.x, a1 ? d.qt.y : d.qs.y));
                     if (c == 1)
                         ei = f_fma(splat<float2>(-J), make_float2(a0 ? d.th.x : d.sh.x, a1 ? d.th.y : d.sh.y), ei);
                     acc.e = f_add(acc.e, ei);
@@ -617,7 +653,7 @@ __device__ __forceinline__ bool update_item_h(Vec<typename Tr<P>::S, V> (&s)[3],
 }
 
 // The same from the raw operands: step (i) then steps (ii)-(iii).
-template <int P, int V, bool MEAS>
+template <int P, int V, bool MEAS, bool TEN = false>
 __device__ __forceinline__ bool update_item(Vec<typename Tr<P>::S, V> (&s)[3], const Vec<typename Tr<P>::S, V> (&o)[3],
                                             const Vec<typename Tr<P>::S, V> (&nym)[3],
                                             const Vec<typename Tr<P>::S, V> (&nyp)[3],
@@ -629,7 +665,7 @@ __device__ __forceinline__ bool update_item(Vec<typename Tr<P>::S, V> (&s)[3], c
                                             SiteAcc<P> &acc) {
     typename Tr<P>::C h[3][V];
     item_fields<P, V>(o, nym, nyp, nzm, nzp, ed, p, h);
-    return update_item_h<P, V, MEAS>(s, h, site0, rank0, c, a, J, K, ex, ey, ez, beta, acc);
+    return update_item_h<P, V, MEAS, TEN>(s, h, site0, rank0, c, a, J, K, ex, ey, ez, beta, acc);
 }
 
 // Vector load, optionally L2-only (ld.global.cg).  A kernel that reads data

@@ -85,6 +85,9 @@ struct PassArgs {
     double J, K, e[3];
     double beta;
     float fJ, fK, fe[3], fbeta;  // the same in FP32 for the FP32 / FP16 kernels
+    int tensor;             // 1: the on-site anisotropy tensor term is on
+    double A[6];            // its symmetric tensor (xx, yy, zz, xy, xz, yz)
+    float fA[6];
     uint32_t key0, key1, replica, sweep;
     double *partials;       // [n_colours][n_blocks][kPartials]
     int pass;               // colour index = partial slot
@@ -105,6 +108,8 @@ struct Layout {
     int kernel;             // KernelKind
     int vec;                // vector width of the stencil kernels
     int prefetch;           // register stencil: 0 none, 1 next work item in registers, 2 split prefetch
+    int tensor;             // 1: the on-site anisotropy tensor term is on (register stencil without
+                            //    prefetch, or the neighbour table)
     int ty, zchunk, n_units, grid;  // staged stencil tiling and grid
     int ring_o, ring_w;             // staged stencil ring depths
     int consumers;                  // staged stencil consumer threads (128 or 256)

@@ -40,7 +40,8 @@ namespace {
 //      arithmetic; the y-1 / y+1 rows (the rows of neighbouring work items
 //      of the same CTA, usually in L1 or L2) are loaded when an item is
 //      taken up.
-template <int P, int V, bool MEAS, int PF>
+//   TEN adds the on-site anisotropy tensor term (built with PF = 0 only).
+template <int P, int V, bool MEAS, int PF, bool TEN = false>
 __global__ void __launch_bounds__(kBlock, 2) sc_pass_kernel(const PassArgs a) {
     pdl_enter();
     using S = typename Tr<P>::S;
@@ -56,8 +57,8 @@ __global__ void __launch_bounds__(kBlock, 2) sc_pass_kernel(const PassArgs a) {
     SiteAcc<P> acc;
     const uint32_t stride = gridDim.x * blockDim.x;
     auto compute = [&](StencilItem<P, V> &it) {
-        if (update_item<P, V, MEAS>(it.s, it.o, it.nym, it.nyp, it.nzm, it.nzp, it.ed, it.p, it.site0, it.rank0, c, a, J, K,
-                                    ex, ey, ez, beta, acc)) {
+        if (update_item<P, V, MEAS, TEN>(it.s, it.o, it.nym, it.nyp, it.nzm, it.nzp, it.ed, it.p, it.site0, it.rank0, c, a,
+                                         J, K, ex, ey, ez, beta, acc)) {
 #pragma unroll
             for (int q = 0; q < 3; ++q) *reinterpret_cast<VT *>(own_w[q] + it.b0) = it.s[q];
         }
@@ -83,7 +84,7 @@ __global__ void __launch_bounds__(kBlock, 2) sc_pass_kernel(const PassArgs a) {
                 const uint32_t tn = t + stride;
                 const bool more = tn < n_items;
                 if (more) load_split_a<P, V>(a, tn, own, oth, A);  // the neighbour vectors are dead now
-                if (update_item_h<P, V, MEAS>(sv, h, site0, rank0, c, a, J, K, ex, ey, ez, beta, acc)) {
+                if (update_item_h<P, V, MEAS, TEN>(sv, h, site0, rank0, c, a, J, K, ex, ey, ez, beta, acc)) {
 #pragma unroll
                     for (int q = 0; q < 3; ++q) *reinterpret_cast<VT *>(own_w[q] + b0) = sv[q];
                 }
@@ -588,7 +589,8 @@ __global__ void __launch_bounds__(StagedShape<NC>::threads, StagedShape<NC>::min
 // five CTAs per SM in 48 registers without spilling (measured 51.8 -> 56.0
 // attempts/ns on the FP32 bcc nanoparticle, 45.2 -> 48.0 on bcc 128^3,
 // 65.0 -> 68.3 FP16); FP64 would spill and keeps four.
-template <int P, bool MEAS>
+// TEN adds the on-site anisotropy tensor term.
+template <int P, bool MEAS, bool TEN = false>
 __global__ void __launch_bounds__(kBlock, P == HS_FP64 ? 1 : 5) table_pass_kernel(const PassArgs a) {
     pdl_enter();
     using S = typename Tr<P>::S;
@@ -622,11 +624,12 @@ __global__ void __launch_bounds__(kBlock, P == HS_FP64 ? 1 : 5) table_pass_kerne
         bool accepted;
         if constexpr (P == HS_FP64) {
             draw_trial<P>(__ldg(a.nat + i), a.sweep, (uint32_t)a.colour, a.replica, a.key0, a.key1, tx, ty, tz, u);
-            accepted = metropolis<C>(sx, sy, sz, tx, ty, tz, hx, hy, hz, J, K, ex, ey, ez, beta, u).acc;
+            accepted = metropolis<C, TEN>(sx, sy, sz, tx, ty, tz, hx, hy, hz, J, K, ex, ey, ez, beta, u, a.A).acc;
         } else {
             draw_trial_rank<P>((uint32_t)(i - a.colour_begin), a.sweep, (uint32_t)a.colour, a.replica, a.key0,
                                a.key1, tx, ty, tz, u);
-            const Dots32<float> d = site_math32<float>(sx, sy, sz, tx, ty, tz, hx, hy, hz, J, K, ex, ey, ez);
+            const Dots32<float> d =
+                site_math32<float, TEN>(sx, sy, sz, tx, ty, tz, hx, hy, hz, J, K, ex, ey, ez, a.fA);
             accepted = accept32(d.dH, u, neg_beta_log2e(beta));
         }
         if (accepted) {
@@ -642,6 +645,12 @@ __global__ void __launch_bounds__(kBlock, P == HS_FP64 ? 1 : 5) table_pass_kerne
         if (MEAS) {
             const C se = sx * ex + sy * ey + sz * ez;
             accE += -J * (sx * lx + sy * ly + sz * lz) - K * se * se;
+            if constexpr (TEN) {
+                if constexpr (P == HS_FP64)
+                    accE -= quad64(sx, sy, sz, a.A);
+                else
+                    accE -= quad32<float>(sx, sy, sz, a.fA);
+            }
             accX += sx;
             accY += sy;
             accZ += sz;
@@ -688,6 +697,7 @@ __global__ void __launch_bounds__(kBlock) sc_measure_kernel(const PassArgs a, co
         }
         const double se = s[0] * a.e[0] + s[1] * a.e[1] + s[2] * a.e[2];
         accE += -0.5 * a.J * (s[0] * h[0] + s[1] * h[1] + s[2] * h[2]) - a.K * se * se;
+        if (a.tensor) accE -= quad64(s[0], s[1], s[2], a.A);
         accX += s[0];
         accY += s[1];
         accZ += s[2];
@@ -713,6 +723,7 @@ __global__ void __launch_bounds__(kBlock) table_measure_kernel(const PassArgs a,
         const double s0 = to_c(sv.v[0]), s1 = to_c(sv.v[1]), s2 = to_c(sv.v[2]);
         const double se = s0 * a.e[0] + s1 * a.e[1] + s2 * a.e[2];
         accE += -0.5 * a.J * (s0 * h[0] + s1 * h[1] + s2 * h[2]) - a.K * se * se;
+        if (a.tensor) accE -= quad64(s0, s1, s2, a.A);
         accX += s0;
         accY += s1;
         accZ += s2;
@@ -868,7 +879,10 @@ cudaError_t launch_sc_pf(const PassArgs &a, int n_blocks, cudaStream_t s, bool m
 }
 
 template <int P, int V>
-cudaError_t launch_sc_v(const PassArgs &a, int n_blocks, cudaStream_t s, bool meas, int pf) {
+cudaError_t launch_sc_v(const PassArgs &a, int n_blocks, cudaStream_t s, bool meas, int pf, bool ten) {
+    if (ten)
+        return meas ? launch_pdl(sc_pass_kernel<P, V, true, 0, true>, n_blocks, kBlock, 0, s, a)
+                    : launch_pdl(sc_pass_kernel<P, V, false, 0, true>, n_blocks, kBlock, 0, s, a);
     if (pf == 1) return launch_sc_pf<P, V, 1>(a, n_blocks, s, meas);
     if (pf == 2) return launch_sc_pf<P, V, 2>(a, n_blocks, s, meas);
     return launch_sc_pf<P, V, 0>(a, n_blocks, s, meas);
@@ -934,14 +948,17 @@ cudaError_t launch_pass_p(const Layout &L, const PassArgs &a, int n_blocks, cuda
     }
     if (L.kernel == kStencil) {
         switch (L.vec) {
-        case 1: return launch_sc_v<P, 1>(a, n_blocks, s, meas, L.prefetch);
-        case 2: return launch_sc_v<P, 2>(a, n_blocks, s, meas, L.prefetch);
-        case 4: if constexpr (P != HS_FP64) return launch_sc_v<P, 4>(a, n_blocks, s, meas, L.prefetch); break;
-        case 8: if constexpr (P == HS_FP16) return launch_sc_v<P, 8>(a, n_blocks, s, meas, L.prefetch); break;
+        case 1: return launch_sc_v<P, 1>(a, n_blocks, s, meas, L.prefetch, L.tensor != 0);
+        case 2: return launch_sc_v<P, 2>(a, n_blocks, s, meas, L.prefetch, L.tensor != 0);
+        case 4: if constexpr (P != HS_FP64) return launch_sc_v<P, 4>(a, n_blocks, s, meas, L.prefetch, L.tensor != 0); break;
+        case 8: if constexpr (P == HS_FP16) return launch_sc_v<P, 8>(a, n_blocks, s, meas, L.prefetch, L.tensor != 0); break;
         default: break;
         }
         return cudaErrorInvalidValue;
     }
+    if (L.tensor)
+        return meas ? launch_pdl(table_pass_kernel<P, true, true>, n_blocks, kBlock, 0, s, a)
+                    : launch_pdl(table_pass_kernel<P, false, true>, n_blocks, kBlock, 0, s, a);
     return meas ? launch_pdl(table_pass_kernel<P, true>, n_blocks, kBlock, 0, s, a)
                 : launch_pdl(table_pass_kernel<P, false>, n_blocks, kBlock, 0, s, a);
 }
@@ -1020,7 +1037,9 @@ static const void *sc_ptr_pf(bool meas) {
 }
 
 template <int P, int V>
-static const void *sc_ptr(bool meas, int pf) {
+static const void *sc_ptr(bool meas, int pf, bool ten) {
+    if (ten)
+        return meas ? (const void *)sc_pass_kernel<P, V, true, 0, true> : (const void *)sc_pass_kernel<P, V, false, 0, true>;
     if (pf == 1) return sc_ptr_pf<P, V, 1>(meas);
     if (pf == 2) return sc_ptr_pf<P, V, 2>(meas);
     return sc_ptr_pf<P, V, 0>(meas);
@@ -1093,18 +1112,20 @@ static const void *pass_kernel_ptr(const Layout &L, bool meas) {
     }
     if (L.kernel == kStencil) {
         switch (L.vec) {
-        case 1: return sc_ptr<P, 1>(meas, L.prefetch);
-        case 2: return sc_ptr<P, 2>(meas, L.prefetch);
+        case 1: return sc_ptr<P, 1>(meas, L.prefetch, L.tensor != 0);
+        case 2: return sc_ptr<P, 2>(meas, L.prefetch, L.tensor != 0);
         case 4:
-            if constexpr (P != HS_FP64) return sc_ptr<P, 4>(meas, L.prefetch);
+            if constexpr (P != HS_FP64) return sc_ptr<P, 4>(meas, L.prefetch, L.tensor != 0);
             break;
         case 8:
-            if constexpr (P == HS_FP16) return sc_ptr<P, 8>(meas, L.prefetch);
+            if constexpr (P == HS_FP16) return sc_ptr<P, 8>(meas, L.prefetch, L.tensor != 0);
             break;
         default: break;
         }
         return nullptr;
     }
+    if (L.tensor)
+        return meas ? (const void *)table_pass_kernel<P, true, true> : (const void *)table_pass_kernel<P, false, true>;
     return meas ? (const void *)table_pass_kernel<P, true> : (const void *)table_pass_kernel<P, false>;
 }
 

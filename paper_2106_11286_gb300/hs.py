@@ -99,6 +99,8 @@ SIGNATURES = {
     "hs_read_timing": (ctypes.c_int, [_vp, _dp, _i64p]),
     "hs_set_launch": (ctypes.c_int, [_vp, ctypes.POINTER(hs_launch)]),
     "hs_get_launch": (ctypes.c_int, [_vp, ctypes.POINTER(hs_launch)]),
+    "hs_set_anisotropy_tensor": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_double)]),
+    "hs_get_anisotropy_tensor": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_double)]),
     "hs_autotune": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_int]),
     "hs_colour_greedy": (ctypes.c_int, [ctypes.c_int64, _i64p, _i32p, _u8p, _i32p, ctypes.POINTER(ctypes.c_int)]),
     "hs_batch_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.c_int]),
@@ -315,6 +317,34 @@ def hs_get_launch(h) -> dict:
     return cfg.as_dict()
 
 
+def tensor_entries(A):
+    """The six entries (Axx, Ayy, Azz, Axy, Axz, Ayz) of a symmetric on-site
+    anisotropy tensor given as six numbers or a symmetric 3x3 array."""
+    A = np.asarray(A, dtype=np.float64)
+    if A.shape == (3, 3):
+        if not np.array_equal(A, A.T):
+            raise ValueError("the anisotropy tensor must be symmetric")
+        A = np.array([A[0, 0], A[1, 1], A[2, 2], A[0, 1], A[0, 2], A[1, 2]])
+    if A.shape != (6,):
+        raise ValueError("the anisotropy tensor takes 6 entries or a 3x3 array")
+    return np.ascontiguousarray(A)
+
+
+def hs_set_anisotropy_tensor(h, A):
+    """-sum_i S_i^T A S_i on every site (A = None removes the term)."""
+    if A is None:
+        _check(load().hs_set_anisotropy_tensor(h, None))
+        return
+    t = tensor_entries(A)
+    _check(load().hs_set_anisotropy_tensor(h, _ptr(t, ctypes.c_double)))
+
+
+def hs_get_anisotropy_tensor(h) -> np.ndarray:
+    t = np.zeros(6, dtype=np.float64)
+    _check(load().hs_get_anisotropy_tensor(h, _ptr(t, ctypes.c_double)))
+    return t
+
+
 def hs_autotune(h, beta, n_trial_sweeps=3):
     _check(load().hs_autotune(h, float(beta), int(n_trial_sweeps)))
 
@@ -372,8 +402,14 @@ def hs_batch_inject_timeout(b, on=True):
 class Lattice:
     """Owning wrapper: ``Lattice("sc", dims=(16,16,16), J=1, K=0.1, precision="fp64", seed=1)``."""
 
-    def __init__(self, type, **kw):
+    def __init__(self, type, A=None, **kw):
         self.h = hs_lattice_create(type, **kw)
+        if A is not None:
+            try:
+                hs_set_anisotropy_tensor(self.h, A)
+            except Exception:
+                self.close()
+                raise
 
     def close(self):
         if self.h:
@@ -429,6 +465,9 @@ class Lattice:
     def set_launch(self, **cfg):
         hs_set_launch(self.h, **cfg)
 
+    def set_anisotropy_tensor(self, A):
+        hs_set_anisotropy_tensor(self.h, A)
+
     @property
     def launch(self):
         return hs_get_launch(self.h)
@@ -441,8 +480,14 @@ class Lattice:
 class Slab(Lattice):
     """Owning wrapper of a z-slab: ``Slab(dims, z0, nz, J=.., precision=.., seed=..)``."""
 
-    def __init__(self, dims, z0, nz, **kw):
+    def __init__(self, dims, z0, nz, A=None, **kw):
         self.h = hs_slab_create(dims, z0, nz, **kw)
+        if A is not None:
+            try:
+                hs_set_anisotropy_tensor(self.h, A)
+            except Exception:
+                self.close()
+                raise
 
     def sweep_pass(self, beta, colour):
         hs_sweep_pass(self.h, beta, colour)

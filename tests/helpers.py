@@ -11,12 +11,12 @@ def oracle_graph(orc, kind, dims=None, periodic=True, row_ptr=None, col=None, ma
 
 
 def make_gpu(kind, dims=None, periodic=True, row_ptr=None, col=None, mask=None, *, J, K, e, precision, seed,
-             replica=0):
+             replica=0, A=None):
     if kind == "csr":
         return hs.Lattice("csr", row_ptr=row_ptr, col_idx=col, site_mask=mask, J=J, K=K, e=e,
-                          precision=precision, seed=seed, replica=replica)
+                          precision=precision, seed=seed, replica=replica, A=A)
     return hs.Lattice(kind, dims=dims, periodic=periodic, site_mask=mask, J=J, K=K, e=e, precision=precision,
-                      seed=seed, replica=replica)
+                      seed=seed, replica=replica, A=A)
 
 
 def storage_round(S, precision):
