@@ -228,10 +228,23 @@ enum hs_kernel {
     HS_KERNEL_MARCH = 4,   /* sc: register stencil walking each CTA's slab along z
                               (neighbour rows reused from L1, next plane
                               prefetched into L2) */
-    HS_KERNEL_PIPE = 5     /* sc: register stencil whose next work item is copied
+    HS_KERNEL_PIPE = 5,    /* sc: register stencil whose next work item is copied
                               global -> shared (cp.async, one slot per thread)
                               while the current one is computed; needs 4..16
                               bytes of storage per vector */
+    HS_KERNEL_WAVE = 6     /* sc, FP32 (vector width 4) or FP16 (8), whole
+                              lattices without a tensor term, Lz >= 3, fewer
+                              than 2^31 sites: one persistent cooperative launch
+                              runs up to 256 sweeps; groups of colour passes
+                              follow each other plane by plane (a pass starts
+                              plane z once the previous pass has finished
+                              planes z-1, z, z+1), so planes are reused from L2.
+                              tile_y = work items per compute thread and unit
+                              (1..8, default 2), chunk_z = passes per group
+                              (1..32, default from the SM count), ring = lag in
+                              planes between consecutive passes of a group
+                              (3..64, default 5).  hs_sweep_pass runs the
+                              register stencil. */
 };
 typedef struct {
     int kernel;        /* hs_kernel; the table kernel is the only one for non-sc */

@@ -99,7 +99,7 @@ struct PassArgs {
     int inject_extra_tx;    // test hook: extra bytes the first staged fill expects
 };
 
-enum KernelKind { kStencil = 1, kStaged = 2, kTable = 3, kMarch = 4, kPipe = 5 };
+enum KernelKind { kStencil = 1, kStaged = 2, kTable = 3, kMarch = 4, kPipe = 5, kWave = 6 };
 
 struct Layout {
     bool structured;
@@ -110,6 +110,13 @@ struct Layout {
     int prefetch;           // register stencil: 0 none, 1 next work item in registers, 2 split prefetch
     int tensor;             // 1: the on-site anisotropy tensor term is on (register stencil without
                             //    prefetch, or the neighbour table)
+    // wavefront kernel (kWave): work units of wave_ipu items, wave_U per colour plane, groups of
+    // wave_D passes, lag wave_lag planes, wave_grid CTAs; device buffers owned by the handle
+    int wave_k, wave_ipu, wave_U, wave_D, wave_lag, wave_grid;
+    uint32_t *wave_cnt;     // [Lz] completed units per plane
+    uint32_t *wave_order;   // ticket orders of groups of 1..wave_D passes, concatenated
+    double *wave_slots;     // [wave_max_pass][wave_grid][kPartials]
+    int wave_max_pass;
     int ty, zchunk, n_units, grid;  // staged stencil tiling and grid
     int ring_o, ring_w;             // staged stencil ring depths
     int consumers;                  // staged stencil consumer threads (128 or 256)
@@ -160,6 +167,33 @@ struct BatchArgs {
     int n_total, n_equil;    // sweeps, of which the first n_equil unmeasured
     int inject_skip;         // test hook: 1 = CTA 0 skips its first barrier arrival
 };
+
+// ---- wavefront kernel (wave.cu)
+// One launch runs n_pass colour passes (whole sweeps) of a periodic FP32 /
+// FP16 sc lattice.  Passes go in groups of D; a unit of work is
+// (pass p, plane z, item range); unit tickets are ordered group by group,
+// inside a group by (position k + lag d, d) with pass d of the group at plane
+// (p + k) mod Lz, so every unit's inputs -- pass p - 1 at planes z-1, z, z+1 --
+// come from earlier tickets.  CTA b takes tickets b, b + grid, ...
+struct WaveArgs {
+    PassArgs a;              // layout, parameters, keys (colour and sweep set per unit)
+    void *planes;            // the six colour-major planes
+    uint32_t n_pi;           // work items of one colour plane: Ly (Lh / V)
+    uint32_t ipu, U;         // items per unit, units per plane
+    uint32_t D, D_last, n_full, n_pass, n_tickets;
+    const uint32_t *order_full, *order_last;  // (d << 20) | k per plane-unit, ticket order
+    uint32_t sweep0;         // sweep index of pass 0
+    uint32_t *cnt;           // [Lz] units completed per plane (zeroed before the launch)
+    double *slots;           // [n_pass][grid][kPartials] per-CTA pass sums (zeroed before the launch)
+    int *error;              // latched device error word
+    DevAccum *acc;
+    int accumulate;
+    double n_present, e[3];
+};
+cudaError_t launch_wave(int precision, int vec, const WaveArgs &w, int grid, cudaStream_t s);
+cudaError_t launch_wave_finalize(const WaveArgs &w, int grid, cudaStream_t s);
+int wave_occupancy(int precision, int vec);  // resident CTAs per SM (0 = no variant)
+constexpr int kWaveComputeWarps = 15;        // per CTA, plus one control warp
 
 cudaError_t launch_batch(const BatchArgs &b, int grid, cudaStream_t s);
 int batch_occupancy();

@@ -334,51 +334,7 @@ __global__ void __launch_bounds__(kBlock, 2) sc_march_kernel(const PassArgs a) {
 // latches the device error word, and the producer waits (bounded) for the
 // copies it has in flight before the CTA retires.
 
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
 
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try(uint64_t *bar, uint32_t parity) {
-    uint32_t done;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(done)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return done != 0;
-}
-
-// Bounded wait on one phase of an mbarrier: gives up after about one second
-// of clock (or 2^26 polls), or as soon as another thread raised the abort
-// flag; a timeout raises the flag itself.
-constexpr long long kWaitCycles = 2000000000LL;
-
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag) {
-    if (mbar_try(bar, parity)) return true;
-    const long long t0 = clock64();
-    for (uint32_t it = 0; it < (1u << 26); ++it) {
-        if (mbar_try(bar, parity)) return true;
-        if (*abort_flag) return false;
-        if (clock64() - t0 > kWaitCycles) break;
-    }
-    *abort_flag = 1;
-    return false;
-}
 
 __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
@@ -946,7 +902,7 @@ cudaError_t launch_pass_p(const Layout &L, const PassArgs &a, int n_blocks, cuda
         }
         return cudaErrorInvalidValue;
     }
-    if (L.kernel == kStencil) {
+    if (L.kernel == kStencil || L.kernel == kWave) {  // the wavefront kernel's single passes
         switch (L.vec) {
         case 1: return launch_sc_v<P, 1>(a, n_blocks, s, meas, L.prefetch, L.tensor != 0);
         case 2: return launch_sc_v<P, 2>(a, n_blocks, s, meas, L.prefetch, L.tensor != 0);
@@ -1110,7 +1066,7 @@ static const void *pass_kernel_ptr(const Layout &L, bool meas) {
         }
         return nullptr;
     }
-    if (L.kernel == kStencil) {
+    if (L.kernel == kStencil || L.kernel == kWave) {
         switch (L.vec) {
         case 1: return sc_ptr<P, 1>(meas, L.prefetch, L.tensor != 0);
         case 2: return sc_ptr<P, 2>(meas, L.prefetch, L.tensor != 0);

@@ -54,7 +54,7 @@ class hs_launch(ctypes.Structure):
 
 
 HS_KERNEL_AUTO, HS_KERNEL_STENCIL, HS_KERNEL_STAGED, HS_KERNEL_TABLE, HS_KERNEL_MARCH = 0, 1, 2, 3, 4
-KERNELS = {"auto": 0, "stencil": 1, "staged": 2, "table": 3, "march": 4, "pipe": 5}
+KERNELS = {"auto": 0, "stencil": 1, "staged": 2, "table": 3, "march": 4, "pipe": 5, "wave": 6}
 
 
 class hs_info(ctypes.Structure):
