@@ -64,7 +64,7 @@ def kernels_sha() -> str:
 
 # colour-pass kernel of each hs_kernel kind (hs_get_launch's "kernel")
 KERNEL_NAMES = {1: "sc_pass_kernel", 2: "sc_staged_kernel", 3: "table_pass_kernel", 4: "sc_march_kernel",
-                5: "sc_pipe_kernel"}
+                5: "sc_pipe_kernel", 6: "sc_wave_kernel"}
 
 
 def kernel_label(launch, precision_code=1, measure=1):
@@ -73,7 +73,7 @@ def kernel_label(launch, precision_code=1, measure=1):
     name = KERNEL_NAMES.get(launch["kernel"], "sc_pass_kernel")
     if launch["kernel"] == 1:
         pf = {1: 1, 3: 2}.get(launch["prefetch"], 0)
-        return f"{name}<{precision_code}, {launch['vec_width']}, {measure}, {pf}>"
+        return f"{name}<{precision_code}, {launch['vec_width']}, {measure}, {pf}, 0>"
     return name
 
 
