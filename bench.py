@@ -319,13 +319,14 @@ def run_ours(args):
         dist.barrier()
     if rank != 0:
         return None
-    cpu = None if (args.no_cpu_baseline or world > 1) else cpu_baseline(args)
+    cpu, spin_err = (None, None) if (args.no_cpu_baseline or world > 1) else cpu_baseline(args)
+    precision = None if (args.no_precision or world > 1) else precision_runs(args)
     line = {"metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(tot_s * 1e3 / args.steps, 5), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": config_dict(args, world), "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": int(2 * args.steps), "clocks": clk.summary(), "fp64": fp64, "physics": physics,
-            "variants": variants}
+            "precision": precision, "spin_error_per_sweep": spin_err, "variants": variants}
     return line
 
 
@@ -477,24 +478,91 @@ def run_variants(args, rank, stream, barrier_sync, world, dev):
 
 
 # ------------------------------------------------------------------ CPU oracle
+def _one_sweep_gpu(precision, L, params, beta):
+    """Storage-rounded start state and the state after one GPU sweep."""
+    from paper_2106_11286_gb300 import hs
+    with hs.Lattice("sc", dims=(L, L, L), precision=precision, **params) as lat:
+        lat.init()
+        S0 = lat.get_spins()
+        lat.sweep(beta, 1)
+        return S0, lat.get_spins()
+
+
+def _spin_error(S0, G, O):
+    """One sweep from S0 on the GPU (G) and in the oracle (O): the fraction of
+    sites whose accept decision differs, and |G - O| over the sites where both
+    took the same decision (accepted: trial rounding; rejected: exactly 0)."""
+    import numpy as np
+    acc_g = np.any(G != S0, axis=1)
+    acc_o = np.any(O != S0, axis=1)
+    same = acc_g == acc_o
+    d = np.linalg.norm(G[same] - O[same], axis=1)
+    return {"decision_mismatch_frac": float((~same).mean()), "err_max": float(d.max()),
+            "err_rms": float(np.sqrt((d * d).mean())), "accept_rate": float(acc_o.mean())}
+
+
 def cpu_baseline(args, sweeps=None, L=None):
     """The oracle as it stands, single-threaded, on a bounded sample of the
-    workload: a few sweeps of the full 256^3 lattice."""
+    workload: a few sweeps of the full 256^3 lattice, started from the FP32
+    path's own (rounded) initial state.  The same leg measures the spin error
+    per sweep of each GPU precision against the FP64 oracle: one sweep of the
+    full lattice from the same state in both (the FP32 and FP16 paths against
+    the oracle run with their random-number schedule and storage rounding)."""
     from oracle import oracle as orc
     w = WORKLOAD
     L = L or w["L"]
     sweeps = sweeps or args.cpu_sweeps
+    beta = 1.0 / w["T"]
+    params = dict(J=w["J"], K=w["K"], e=w["e"], seed=w["seed"])
     g = orc.lattice("sc", (L, L, L))
-    S = orc.init_spins(g, seed=w["seed"])
-    t = time.perf_counter()
+    starts = {p: _one_sweep_gpu(p, L, params, beta) for p in ("fp32", "fp16", "fp64")}
+    S = starts["fp32"][0].copy()
+    dt = 0.0
+    after_one = None
     for s in range(sweeps):
-        orc.sweep(g, S, J=w["J"], K=w["K"], e=w["e"], beta=1.0 / w["T"], seed=w["seed"], sweep_index=s,
-                  mode=orc.MODE_FP32)
-    dt = time.perf_counter() - t
+        t = time.perf_counter()
+        orc.sweep(g, S, J=w["J"], K=w["K"], e=w["e"], beta=beta, seed=w["seed"], sweep_index=s, mode=orc.MODE_FP32)
+        dt += time.perf_counter() - t
+        if s == 0:
+            after_one = S.copy()
     n = g.n * sweeps
-    return {"value": round(n / (dt * 1e9), 6), "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{sweeps} sweeps of the sc {L}^3 lattice ({n} attempts), FP64 oracle with the FP32 "
-                      f"random-number schedule, 1 thread, {dt:.1f} s"}
+    out = {"value": round(n / (dt * 1e9), 6), "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": f"{sweeps} sweeps of the sc {L}^3 lattice ({n} attempts), FP64 oracle with the FP32 "
+                     f"random-number schedule, 1 thread, {dt:.1f} s"}
+    errors = {"fp32": _spin_error(starts["fp32"][0], starts["fp32"][1], after_one)}
+    for prec, mode in (("fp16", orc.MODE_FP16), ("fp64", orc.MODE_FP64)):
+        S0, G = starts[prec]
+        O = S0.copy()
+        orc.sweep(g, O, J=w["J"], K=w["K"], e=w["e"], beta=beta, seed=w["seed"], sweep_index=0, mode=mode)
+        errors[prec] = _spin_error(S0, G, O)
+    errors["what"] = (f"one sweep of the sc {L}^3 workload from the same state on the GPU and in the FP64 oracle "
+                      "(FP32 / FP16: the oracle with that path's random-number schedule and storage rounding)")
+    return out, errors
+
+
+def precision_runs(args):
+    """<E>/N and <|M|> of the 256^3 workload in FP64, FP32 and FP16 over the
+    same sweeps from each path's own rounded start (the FP64 path is the
+    reference; it is pinned to the oracle element by element in the tests)."""
+    from paper_2106_11286_gb300 import hs
+    w = WORKLOAD
+    L, beta = w["L"], 1.0 / w["T"]
+    params = dict(J=w["J"], K=w["K"], e=w["e"], seed=w["seed"])
+    out = {}
+    for prec in ("fp64", "fp32", "fp16"):
+        with hs.Lattice("sc", dims=(L, L, L), precision=prec, **params) as lat:
+            lat.init()
+            lat.accumulate(True)
+            lat.sweep(beta, args.precision_sweeps)
+            mom, count = lat.read_accumulator()
+        n = float(L) ** 3
+        out[prec] = {"E_per_spin": mom[0] / count / n, "absM": mom[2] / count}
+    for prec in ("fp32", "fp16"):
+        out[prec]["bias_E_per_spin_vs_fp64"] = out[prec]["E_per_spin"] - out["fp64"]["E_per_spin"]
+        out[prec]["bias_absM_vs_fp64"] = out[prec]["absM"] - out["fp64"]["absM"]
+    out["sweeps"] = args.precision_sweeps
+    out["what"] = "measured every sweep from the start (no equilibration skipped), seed 2, T = 1.2"
+    return out
 
 
 def run_reference(args):
@@ -544,6 +612,8 @@ def main(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-precision", action="store_true", help="skip the FP64/FP32/FP16 runs of the workload")
+    ap.add_argument("--precision-sweeps", type=int, default=500)
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-big", action="store_true", help="skip the sc 1024^3 variant")
     ap.add_argument("--huge-sweeps", type=int, default=20, help="timed sweeps of the sc 1024^3 variant")

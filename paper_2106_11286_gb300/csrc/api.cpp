@@ -201,6 +201,7 @@ struct hs_lattice {
     double *wave_slots = nullptr;
     int wave_cnt_n = 0;
     size_t wave_order_n = 0, wave_slots_n = 0;
+    double2 *sc_tab = nullptr;     // FP64: sin, cos(pi j / 128) table of the trial orientation
     int tensor = 0;                // on-site anisotropy tensor term on
     double tA[6] = {0, 0, 0, 0, 0, 0};
     Layout L{};
@@ -279,6 +280,7 @@ PassArgs base_args(const hs_lattice *h) {
     a.key0 = (uint32_t)h->seed;
     a.key1 = (uint32_t)(h->seed >> 32);
     a.replica = h->replica;
+    a.sc_tab = h->sc_tab;
     a.tensor = h->tensor;
     for (int q = 0; q < 6; ++q) {
         a.A[q] = h->tA[q];
@@ -755,6 +757,20 @@ int lattice_create(hs_lattice **out, int type, const int32_t dims[3], int period
         if (st == HS_OK) st = configure_launch(h);
     }
     if (st == HS_OK) st = h->alloc(&h->acc, sizeof(DevAccum));
+    if (st == HS_OK && precision == HS_FP64) {
+        // sin, cos(pi j / 128) for the FP64 trial's table lookup, from long double on the host
+        const long double pi = 3.141592653589793238462643383279502884L;
+        double2 tab[256];
+        for (int j = 0; j < 256; ++j) {
+            const long double a = pi * (long double)j / 128.0L;
+            tab[j] = make_double2((double)sinl(a), (double)cosl(a));
+        }
+        st = h->alloc(&h->sc_tab, sizeof(tab));
+        if (st == HS_OK) {
+            cudaError_t e = cudaMemcpy(h->sc_tab, tab, sizeof(tab), cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) st = cuda_fail(e, "cudaMemcpy");
+        }
+    }
     if (st == HS_OK) {
         cudaError_t e = cudaMemsetAsync(h->acc, 0, sizeof(DevAccum), h->stream);
         if (e != cudaSuccess) st = cuda_fail(e, "cudaMemsetAsync");

@@ -84,21 +84,45 @@ __device__ __forceinline__ void sphere_fp64(uint4 w, double &x, double &y, doubl
     y = r * sn;
 }
 
-// Trial orientation and acceptance uniform of one site (Metropolis step (ii)).
-template <int P>
-__device__ __forceinline__ void draw_trial(uint32_t site, uint32_t sweep, uint32_t colour, uint32_t replica,
-                                           uint32_t k0, uint32_t k1, typename Tr<P>::C &tx,
-                                           typename Tr<P>::C &ty, typename Tr<P>::C &tz,
-                                           typename Tr<P>::C &u);
+// sin(pi t), cos(pi t) for t = m 2^-52 in [0, 2) (m < 2^53), by table lookup
+// and angle addition (Tang, "Table-lookup algorithms for elementary functions
+// and their error analysis", 1991): t = j/128 + b with j = m >> 45 and
+// b = (m mod 2^45) 2^-52 in [0, 1/128) exact; sin, cos(pi j/128) come from a
+// 256-entry table (correctly rounded on the host), sin, cos(x) of x = pi b
+// (|x| < 0.0246) from their Taylor series up to x^7 and x^6, whose first
+// omitted terms are below 1e-20 and 4e-18.  Error a few units in the last
+// place, against the FP64 ALU cost of about 14 operations.
+__device__ __forceinline__ void sincospi_tab(uint64_t m, const double2 *tab, double &sn, double &cs) {
+    const uint32_t j = (uint32_t)(m >> 45);
+    const double b = (double)(int64_t)(m & ((1ull << 45) - 1)) * 0x1p-52;
+    const double x = b * 3.141592653589793;
+    const double x2 = x * x;
+    const double sx = x * fma(x2, fma(x2, fma(x2, -1.0 / 5040.0, 1.0 / 120.0), -1.0 / 6.0), 1.0);
+    const double cx = fma(x2, fma(x2, fma(x2, -1.0 / 720.0, 1.0 / 24.0), -0.5), 1.0);
+    const double2 t = __ldg(tab + j);
+    sn = fma(t.y, sx, t.x * cx);
+    cs = fma(-t.x, sx, t.y * cx);
+}
 
-template <>
-__device__ __forceinline__ void draw_trial<HS_FP64>(uint32_t site, uint32_t sweep, uint32_t colour,
-                                                    uint32_t replica, uint32_t k0, uint32_t k1, double &tx,
-                                                    double &ty, double &tz, double &u) {
+// Trial orientation and acceptance uniform of one site, FP64 schedule
+// (Metropolis step (ii)); the same sphere point as sphere_fp64, with
+// phi = pi v = pi t - pi (t = v + 1) from the table: sin(pi v) = -sin(pi t),
+// cos(pi v) = -cos(pi t).
+__device__ __forceinline__ void draw_trial64(uint32_t site, uint32_t sweep, uint32_t colour, uint32_t replica,
+                                             uint32_t k0, uint32_t k1, const double2 *tab, double &tx, double &ty,
+                                             double &tz, double &u) {
     const uint32_t w2 = (kTagTrial << 24) | (colour << 8);
     const uint4 a = philox10(make_uint4(site, sweep, w2, replica), k0, k1);
     const uint4 b = philox10(make_uint4(site, sweep, w2 | 1u, replica), k0, k1);
-    sphere_fp64(a, tx, ty, tz);
+    const int64_t two52 = int64_t(1) << 52;
+    const int64_t iz = (int64_t)((((uint64_t)(a.x >> 5)) << 26) | (uint64_t)(a.y >> 6));
+    const uint64_t iv = (((uint64_t)(a.z >> 5)) << 26) | (uint64_t)(a.w >> 6);
+    tz = (double)(iz - two52) * 0x1p-52;
+    const double r = sqrt((1.0 - tz) * (1.0 + tz));
+    double sn, cs;
+    sincospi_tab(iv, tab, sn, cs);
+    tx = -(r * cs);
+    ty = -(r * sn);
     const uint64_t ip = (((uint64_t)(b.x >> 5)) << 26) | (uint64_t)(b.y >> 6);
     u = (double)ip * 0x1p-53;
 }
@@ -590,7 +614,7 @@ __device__ __forceinline__ bool update_item_h(Vec<typename Tr<P>::S, V> (&s)[3],
 #pragma unroll
         for (int k = 0; k < V; ++k) {
             C tx, ty, tz, u;
-            draw_trial<P>(site0 + 2u * k, a.sweep, (uint32_t)c, a.replica, a.key0, a.key1, tx, ty, tz, u);
+            draw_trial64(site0 + 2u * k, a.sweep, (uint32_t)c, a.replica, a.key0, a.key1, a.sc_tab, tx, ty, tz, u);
             C sx = to_c(s[0].v[k]), sy = to_c(s[1].v[k]), sz = to_c(s[2].v[k]);
             const SiteDots<C> d = metropolis<C, TEN>(sx, sy, sz, tx, ty, tz, h[0][k], h[1][k], h[2][k], J, K, ex,
                                                      ey, ez, beta, u, a.A);

@@ -88,6 +88,7 @@ struct PassArgs {
     int tensor;             // 1: the on-site anisotropy tensor term is on
     double A[6];            // its symmetric tensor (xx, yy, zz, xy, xz, yz)
     float fA[6];
+    const double2 *sc_tab;  // FP64 trial: sin, cos(pi j / 128), j = 0..255
     uint32_t key0, key1, replica, sweep;
     double *partials;       // [n_colours][n_blocks][kPartials]
     int pass;               // colour index = partial slot
