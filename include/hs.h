@@ -396,7 +396,10 @@ int hs_read_sums(hs_lattice *h, double out[5]);
 /* Test hooks for the bounded device-side waits (failure detection without a
  * GPU fault).  hs_lattice_inject_timeout: the next colour pass of a lattice
  * running the staged kernel expects 16 bytes more than it copies, so the
- * consumers' bounded mbarrier wait runs out (about one second).
+ * consumers' bounded mbarrier wait runs out (about one second); on a lattice
+ * running the wavefront kernel, CTA 0 of the next launch does not count its
+ * first finished unit, so every unit that needs it (and, in turn, the rest of
+ * the launch) waits until its bounded wait runs out.
  * hs_batch_inject_timeout: in the next hs_batch_run one CTA skips its first
  * grid-barrier arrival, so every other CTA's bounded wait runs out.  Either
  * way the kernel latches its error word and returns; the next synchronising

@@ -889,6 +889,8 @@ int run_wave(hs_lattice *h, const PassArgs &a, int64_t n_sweeps) {
         w.accumulate = h->accumulate;
         w.n_present = (double)L.n_present;
         for (int q = 0; q < 3; ++q) w.e[q] = h->p.e[q];
+        w.inject_skip = h->inject_timeout;
+        h->inject_timeout = 0;
         HS_CUDA(cudaMemsetAsync(L.wave_cnt, 0, lz * sizeof(uint32_t), h->stream));
         HS_CUDA(cudaMemsetAsync(L.wave_slots, 0, (size_t)w.n_pass * grid * hs::kPartials * sizeof(double),
                                 h->stream));
@@ -1587,7 +1589,8 @@ int hs_batch_inject_timeout(hs_batch *b, int on) {
 
 int hs_lattice_inject_timeout(hs_lattice *h, int on) {
     if (!h) return fail(HS_E_INVALID, "null handle");
-    if (on && h->L.kernel != hs::kStaged) return fail(HS_E_INVALID, "the hook needs the staged kernel");
+    if (on && h->L.kernel != hs::kStaged && h->L.kernel != hs::kWave)
+        return fail(HS_E_INVALID, "the hook needs the staged or the wavefront kernel");
     h->inject_timeout = on ? 1 : 0;
     return HS_OK;
 }

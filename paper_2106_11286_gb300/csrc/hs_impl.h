@@ -190,6 +190,7 @@ struct WaveArgs {
     DevAccum *acc;
     int accumulate;
     double n_present, e[3];
+    int inject_skip;         // test hook: CTA 0 does not count its first finished unit
 };
 cudaError_t launch_wave(int precision, int vec, const WaveArgs &w, int grid, cudaStream_t s);
 cudaError_t launch_wave_finalize(const WaveArgs &w, int grid, cudaStream_t s);

@@ -172,7 +172,8 @@ __device__ void wave_control(const WaveArgs &w, uint32_t n_mine, uint64_t *ready
         for (uint32_t f = 0; f < n_fin; ++f, ++j_done) {
             const uint32_t slot = j_done % kWaveRing;
             const WaveUnit u = desc[slot];
-            if (lane == 0) asm volatile("red.relaxed.gpu.global.add.u32 [%0], 1;" ::"l"(w.cnt + u.z) : "memory");
+            const bool skip = w.inject_skip && blockIdx.x == 0 && j_done == 0;  // test hook
+            if (lane == 0 && !skip) asm volatile("red.relaxed.gpu.global.add.u32 [%0], 1;" ::"l"(w.cnt + u.z) : "memory");
             const uint32_t g = u.p / w.D;
             if (g != group) {
                 flush(group);
