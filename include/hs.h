@@ -318,6 +318,20 @@ int hs_batch_create(hs_batch **out, hs_lattice *const *members, int n_members);
 int hs_batch_run(hs_batch *b, const double *betas, int64_t n_sweeps, int64_t n_equil);
 void hs_batch_destroy(hs_batch *b);
 
+/* Batch autotuner: the batch's work split -- its members' work items (4
+ * sites of one row of one colour), concatenated and cut into one contiguous
+ * range per CTA -- is timed for every CTA count per SM (1 up to the kernel's
+ * occupancy) and both cut rules (at any item, or moved to the nearest row
+ * boundary), for n_trial_sweeps sweeps at the given betas after one warm-up
+ * sweep; the fastest is kept.  Every member's spins, sweep counter and
+ * accumulator are restored, so the members' chains are as if the call had not
+ * happened (spins are identical under every split; the FP64 sums are taken in
+ * each split's own fixed order).  Synchronous.  hs_batch_get_layout reads the
+ * split in use (hs_batch_create starts with the maximum CTAs per SM and cuts at
+ * any item). */
+int hs_batch_autotune(hs_batch *b, const double *betas, int n_trial_sweeps);
+int hs_batch_get_layout(const hs_batch *b, int *ctas_per_sm, int *align_rows);
+
 /* Allocation-free sweep (the paper has no counterpart; it is a service to
  * callers that cannot allocate device memory themselves: a host framework
  * whose caching allocator or fixed budget owns all device memory, or a

@@ -1394,6 +1394,7 @@ struct hs_batch {
     int graph_total = -1, graph_equil = -1;
     bool graph_failed = false;
     int inject_timeout = 0;  // test hook, consumed by the next run
+    int occ = 1, ctas_per_sm = 1, align_rows = 0;  // work split (batch_layout)
     ~hs_batch() {
         cudaStreamSynchronize(stream);
         if (exec) cudaGraphExecDestroy(exec);
@@ -1424,6 +1425,83 @@ hs::BatchArgs batch_args(const hs_batch *b, int n_total, int n_equil) {
 }
 }  // namespace
 
+namespace {
+// Work split of a batch (the batch's tile shape): the members' work items (4
+// sites of one row of one colour), concatenated, are cut into one contiguous
+// range per CTA, ctas_per_sm CTAs per SM; with align_rows the cuts are moved
+// to the nearest row boundary of the member they fall in, so no row is split
+// between two CTAs.  Segment = (CTA, member) piece, with its own FP64 slot.
+int batch_layout(hs_batch *b, int ctas_per_sm, int align_rows) {
+    const int n = (int)b->members.size();
+    const int grid = b->members[0]->n_sm * ctas_per_sm;
+    std::vector<int64_t> items(n), offset(n + 1, 0), row(n);
+    for (int r = 0; r < n; ++r) {
+        const Layout &L = b->members[r]->L;
+        row[r] = L.Lh / 4;
+        items[r] = (int64_t)L.Lz * L.Ly * row[r];
+        offset[r + 1] = offset[r] + items[r];
+    }
+    const int64_t total = offset[n];
+    const int64_t chunk = (total + grid - 1) / grid;
+    std::vector<int64_t> bnd(grid + 1);
+    bnd[0] = 0;
+    bnd[grid] = total;
+    int r = 0;
+    for (int c = 1; c < grid; ++c) {
+        int64_t pos = std::min<int64_t>((int64_t)c * chunk, total);
+        if (align_rows && pos < total) {
+            while (offset[r + 1] <= pos) ++r;
+            const int64_t rel = pos - offset[r];
+            pos = offset[r] + std::min<int64_t>(items[r], (rel + row[r] / 2) / row[r] * row[r]);
+        }
+        bnd[c] = std::max(pos, bnd[c - 1]);
+    }
+    std::vector<hs::BatchSeg> segs;
+    std::vector<int> cta_seg(grid + 1, 0);
+    int c = 0;
+    for (int m = 0; m < n; ++m) {
+        b->host_members[m].seg_begin = (int)segs.size();
+        for (int64_t g = offset[m]; g < offset[m + 1];) {
+            while (bnd[c + 1] <= g) ++c;
+            const int64_t g_end = std::min(offset[m + 1], bnd[c + 1]);
+            segs.push_back({m, (uint32_t)(g - offset[m]), (uint32_t)(g_end - offset[m])});
+            ++cta_seg[c + 1];
+            g = g_end;
+        }
+        b->host_members[m].seg_end = (int)segs.size();
+    }
+    for (int k = 0; k < grid; ++k) cta_seg[k + 1] += cta_seg[k];
+    HS_CUDA(cudaStreamSynchronize(b->stream));
+    cudaFree(b->d_segs);
+    cudaFree(b->d_cta_seg);
+    cudaFree(b->d_slots);
+    b->d_segs = nullptr;
+    b->d_cta_seg = nullptr;
+    b->d_slots = nullptr;
+    if (b->exec) {
+        cudaGraphExecDestroy(b->exec);
+        b->exec = nullptr;
+    }
+    b->graph_total = b->graph_equil = -1;
+    b->grid = grid;
+    b->n_segs = (int)segs.size();
+    b->ctas_per_sm = ctas_per_sm;
+    b->align_rows = align_rows;
+    cudaError_t e;
+    if ((e = cudaMalloc(&b->d_segs, sizeof(hs::BatchSeg) * segs.size())) != cudaSuccess ||
+        (e = cudaMalloc(&b->d_cta_seg, sizeof(int) * cta_seg.size())) != cudaSuccess ||
+        (e = cudaMalloc(&b->d_slots, sizeof(double) * 4 * segs.size() * hs::kPartials)) != cudaSuccess)
+        return cuda_fail(e, "cudaMalloc(batch)");
+    if ((e = cudaMemcpyAsync(b->d_segs, segs.data(), sizeof(hs::BatchSeg) * segs.size(), cudaMemcpyHostToDevice,
+                             b->stream)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(b->d_cta_seg, cta_seg.data(), sizeof(int) * cta_seg.size(), cudaMemcpyHostToDevice,
+                             b->stream)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(b->stream)) != cudaSuccess)
+        return cuda_fail(e, "batch upload");
+    return HS_OK;
+}
+}  // namespace
+
 int hs_batch_create(hs_batch **out, hs_lattice *const *members, int n_members) {
     if (!out) return fail(HS_E_INVALID, "out is NULL");
     *out = nullptr;
@@ -1445,18 +1523,7 @@ int hs_batch_create(hs_batch **out, hs_lattice *const *members, int n_members) {
     if (!b) return fail(HS_E_OOM, "host allocation failed");
     b->members.assign(members, members + n_members);
     b->stream = members[0]->stream;
-    b->grid = members[0]->n_sm * occ;
-    // items of all members, concatenated, cut into one equal chunk per CTA
-    std::vector<int64_t> items(n_members), offset(n_members + 1, 0);
-    for (int r = 0; r < n_members; ++r) {
-        const Layout &L = members[r]->L;
-        items[r] = (int64_t)L.Lz * L.Ly * (L.Lh / 4);
-        offset[r + 1] = offset[r] + items[r];
-    }
-    const int64_t total = offset[n_members];
-    const int64_t chunk = (total + b->grid - 1) / b->grid;
-    std::vector<hs::BatchSeg> segs;
-    std::vector<int> seg_cta;
+    b->occ = occ;
     b->host_members.resize(n_members);
     for (int r = 0; r < n_members; ++r) {
         hs::BatchMember &m = b->host_members[r];
@@ -1480,40 +1547,22 @@ int hs_batch_create(hs_batch **out, hs_lattice *const *members, int n_members) {
         m.replica = h->replica;
         m.n_present = (double)L.n_present;
         m.acc = h->acc;
-        m.seg_begin = (int)segs.size();
-        for (int64_t g = offset[r]; g < offset[r + 1];) {
-            const int64_t cta = g / chunk;
-            const int64_t g_end = std::min(offset[r + 1], (cta + 1) * chunk);
-            segs.push_back({r, (uint32_t)(g - offset[r]), (uint32_t)(g_end - offset[r])});
-            seg_cta.push_back((int)cta);
-            g = g_end;
-        }
-        m.seg_end = (int)segs.size();
     }
-    b->n_segs = (int)segs.size();
-    std::vector<int> cta_seg(b->grid + 1, 0);
-    for (int c : seg_cta) ++cta_seg[c + 1];
-    for (int c = 0; c < b->grid; ++c) cta_seg[c + 1] += cta_seg[c];
-    auto cleanup = [&](int code) {
-        delete b;
-        return code;
-    };
     cudaError_t e;
     if ((e = cudaMalloc(&b->d_members, sizeof(hs::BatchMember) * n_members)) != cudaSuccess ||
-        (e = cudaMalloc(&b->d_segs, sizeof(hs::BatchSeg) * segs.size())) != cudaSuccess ||
-        (e = cudaMalloc(&b->d_cta_seg, sizeof(int) * cta_seg.size())) != cudaSuccess ||
-        (e = cudaMalloc(&b->d_slots, sizeof(double) * 4 * segs.size() * hs::kPartials)) != cudaSuccess ||
         (e = cudaMalloc(&b->d_bar, 2 * sizeof(unsigned int))) != cudaSuccess ||
-        (e = cudaMalloc(&b->d_error, sizeof(int))) != cudaSuccess)
-        return cleanup(cuda_fail(e, "cudaMalloc(batch)"));
-    if ((e = cudaMemcpyAsync(b->d_segs, segs.data(), sizeof(hs::BatchSeg) * segs.size(), cudaMemcpyHostToDevice,
-                             b->stream)) != cudaSuccess ||
-        (e = cudaMemcpyAsync(b->d_cta_seg, cta_seg.data(), sizeof(int) * cta_seg.size(), cudaMemcpyHostToDevice,
-                             b->stream)) != cudaSuccess ||
-        (e = cudaStreamSynchronize(b->stream)) != cudaSuccess)
-        return cleanup(cuda_fail(e, "batch upload"));
-    if ((e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
-        return cleanup(cuda_fail(e, "cudaStreamCreate"));
+        (e = cudaMalloc(&b->d_error, sizeof(int))) != cudaSuccess) {
+        delete b;
+        return cuda_fail(e, "cudaMalloc(batch)");
+    }
+    if ((e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking)) != cudaSuccess) {
+        delete b;
+        return cuda_fail(e, "cudaStreamCreate");
+    }
+    if (int st = batch_layout(b, occ, 0)) {
+        delete b;
+        return st;
+    }
     *out = b;
     return HS_OK;
 }
@@ -1576,6 +1625,97 @@ int hs_batch_run(hs_batch *b, const double *betas, int64_t n_sweeps, int64_t n_e
         HS_CUDA(hs::launch_batch(args, b->grid, b->stream));
     }
     for (int r = 0; r < n; ++r) b->members[r]->sweep += (uint64_t)n_total;
+    return HS_OK;
+}
+
+// Batch autotuner: time every work split (1 .. occupancy CTAs per SM, cuts
+// at any item or at row boundaries) for n_trial_sweeps sweeps after one
+// warm-up sweep, keep the fastest, and put every member's spins, sweep counter
+// and accumulator back as they were.
+int hs_batch_autotune(hs_batch *b, const double *betas, int n_trial_sweeps) {
+    if (!b || !betas) return fail(HS_E_INVALID, "null argument");
+    if (n_trial_sweeps < 1) return fail(HS_E_INVALID, "n_trial_sweeps must be >= 1");
+    const int n = (int)b->members.size();
+    struct Saved {
+        void *planes = nullptr;
+        size_t bytes = 0;
+        uint64_t sweep = 0;
+        int64_t last_n = 0;
+        DevAccum acc{};
+    };
+    std::vector<Saved> saved(n);
+    auto release = [&]() {
+        for (Saved &sv : saved) cudaFree(sv.planes);
+    };
+    for (int r = 0; r < n; ++r) {
+        hs_lattice *h = b->members[r];
+        const Layout &L = h->L;
+        saved[r].bytes = (size_t)6 * L.Lz * L.Ly * L.Lh * sizeof(float);
+        saved[r].sweep = h->sweep;
+        saved[r].last_n = h->last_n_sweeps;
+        cudaError_t e = cudaMalloc(&saved[r].planes, saved[r].bytes);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(saved[r].planes, L.planes, saved[r].bytes, cudaMemcpyDeviceToDevice, b->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(&saved[r].acc, h->acc, sizeof(DevAccum), cudaMemcpyDeviceToHost, b->stream);
+        if (e != cudaSuccess) {
+            release();
+            return cuda_fail(e, "batch autotune backup");
+        }
+    }
+    auto restore = [&]() -> int {
+        for (int r = 0; r < n; ++r) {
+            hs_lattice *h = b->members[r];
+            HS_CUDA(cudaMemcpyAsync(h->L.planes, saved[r].planes, saved[r].bytes, cudaMemcpyDeviceToDevice,
+                                    b->stream));
+            HS_CUDA(cudaMemcpyAsync(h->acc, &saved[r].acc, sizeof(DevAccum), cudaMemcpyHostToDevice, b->stream));
+            h->sweep = saved[r].sweep;
+            h->last_n_sweeps = saved[r].last_n;
+        }
+        HS_CUDA(cudaStreamSynchronize(b->stream));
+        return HS_OK;
+    };
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int st = HS_OK;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) st = fail(HS_E_CUDA, "events");
+    int best_c = b->ctas_per_sm, best_a = b->align_rows;
+    float best_ms = 0.f;
+    bool have = false;
+    if (st == HS_OK && cudaStreamSynchronize(b->stream) != cudaSuccess) st = fail(HS_E_CUDA, "synchronise");
+    for (int c = 1; st == HS_OK && c <= b->occ; ++c)
+        for (int al = 0; st == HS_OK && al <= 1; ++al) {
+            if ((st = batch_layout(b, c, al))) break;
+            if ((st = hs_batch_run(b, betas, 1, 0))) break;
+            if ((st = hs_batch_run(b, betas, n_trial_sweeps, 0))) break;  // graph capture for this count
+            cudaEventRecord(e0, b->stream);
+            if ((st = hs_batch_run(b, betas, n_trial_sweeps, 0))) break;
+            cudaEventRecord(e1, b->stream);
+            if (cudaEventSynchronize(e1) != cudaSuccess) {
+                st = fail(HS_E_CUDA, "batch autotune timing");
+                break;
+            }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (!have || ms < best_ms) {
+                have = true;
+                best_ms = ms;
+                best_c = c;
+                best_a = al;
+            }
+            if ((st = restore())) break;
+        }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (st == HS_OK) st = batch_layout(b, best_c, best_a);
+    const int st2 = restore();
+    release();
+    return st ? st : st2;
+}
+
+int hs_batch_get_layout(const hs_batch *b, int *ctas_per_sm, int *align_rows) {
+    if (!b || !ctas_per_sm || !align_rows) return fail(HS_E_INVALID, "null argument");
+    *ctas_per_sm = b->ctas_per_sm;
+    *align_rows = b->align_rows;
     return HS_OK;
 }
 

@@ -106,6 +106,8 @@ SIGNATURES = {
     "hs_batch_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.c_int]),
     "hs_batch_run": (ctypes.c_int, [_vp, _dp, ctypes.c_int64, ctypes.c_int64]),
     "hs_batch_destroy": (None, [_vp]),
+    "hs_batch_autotune": (ctypes.c_int, [_vp, _dp, ctypes.c_int]),
+    "hs_batch_get_layout": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     "hs_sweep_sc_fp32_noalloc": (ctypes.c_int, [_vp, _i32p, ctypes.POINTER(hs_params), ctypes.c_double,
                                                  ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int64,
                                                  _vp, _vp]),
@@ -384,6 +386,19 @@ def hs_batch_create(members):
 def hs_batch_run(b, betas, n_sweeps, n_equil=0):
     bt = np.ascontiguousarray(betas, dtype=np.float64)
     _check(load().hs_batch_run(b, _ptr(bt, ctypes.c_double), int(n_sweeps), int(n_equil)))
+
+
+def hs_batch_autotune(b, betas, n_trial_sweeps=3):
+    bt = np.ascontiguousarray(betas, dtype=np.float64)
+    _check(load().hs_batch_autotune(b, _ptr(bt, ctypes.c_double), int(n_trial_sweeps)))
+    return hs_batch_get_layout(b)
+
+
+def hs_batch_get_layout(b) -> dict:
+    c = ctypes.c_int(0)
+    a = ctypes.c_int(0)
+    _check(load().hs_batch_get_layout(b, ctypes.byref(c), ctypes.byref(a)))
+    return {"ctas_per_sm": c.value, "align_rows": a.value}
 
 
 def hs_batch_destroy(b):

@@ -61,6 +61,44 @@ def test_batch_matches_individual_sweeps():
             m.close()
 
 
+def test_batch_autotune_keeps_the_chains():
+    """The batch autotuner times every work split and restores every member:
+    afterwards the batch continues exactly as an untuned one; every split
+    gives the same spins."""
+    dims = [(16, 16, 16), (24, 24, 24), (8, 8, 8), (32, 16, 8), (48, 48, 48)]
+    betas = [0.6, 0.8, 1.0, 1.2, 0.9]
+    a = _members(dims, betas)
+    b = _members(dims, betas)
+    for m in a + b:
+        m.init()
+        m.accumulate(True)
+    ba = hs.hs_batch_create([m.h for m in a])
+    bb = hs.hs_batch_create([m.h for m in b])
+    try:
+        assert hs.hs_batch_get_layout(bb) == {"ctas_per_sm": 2, "align_rows": 0}
+        hs.hs_batch_run(ba, betas, 2, 1)
+        hs.hs_batch_run(bb, betas, 2, 1)
+        before = [m.get_spins() for m in a]
+        layout = hs.hs_batch_autotune(ba, betas, 2)
+        assert layout["ctas_per_sm"] in (1, 2) and layout["align_rows"] in (0, 1)
+        for m, s in zip(a, before):
+            assert np.array_equal(m.get_spins(), s)
+            assert m.info.sweep == 3
+        hs.hs_batch_run(ba, betas, 4, 0)
+        hs.hs_batch_run(bb, betas, 4, 0)
+        for x, y in zip(a, b):
+            assert np.array_equal(x.get_spins(), y.get_spins())
+            mx, cx = x.read_accumulator()
+            my, cy = y.read_accumulator()
+            assert cx == cy == 6
+            np.testing.assert_allclose(mx, my, rtol=2e-6, atol=1e-9)
+    finally:
+        hs.hs_batch_destroy(ba)
+        hs.hs_batch_destroy(bb)
+        for m in a + b:
+            m.close()
+
+
 def test_batch_rejects_unsupported_members():
     with hs.Lattice("sc", dims=(8, 8, 8), precision="fp64") as x:
         with pytest.raises(hs.HSError):
