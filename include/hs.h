@@ -258,7 +258,10 @@ typedef struct {
                           next item's own, same-row and z+-1 rows loaded once
                           the current item's fields are summed), 2 = off,
                           0 = automatic (split prefetch for FP32 when a
-                          CTA's work items span at least 8 rows, else off) */
+                          CTA's work items span at least 8 rows, else off);
+                          table: 1 = ask L2 for the next site's table row
+                          and spin ahead, 2 = off, 0 = automatic (on for FP32
+                          tables of at most 8 neighbours) */
     int ring;          /* staged: shared-memory slots of the other colour's
                           planes (4..8; the own colour gets ring - 2) */
     int consumers;     /* staged: consumer warps per CTA, 4 or 8 (plus one

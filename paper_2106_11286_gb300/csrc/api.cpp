@@ -483,6 +483,10 @@ int configure_launch(hs_lattice *h) {
     L.tensor = h->tensor;
     if (!L.structured) {
         L.kernel = hs::kTable;
+        // request 1 = L2 prefetch of the next site's table row, 2 = off, 0 = automatic (on for FP32 tables of
+        // at most 8 neighbours: measured faster there, slower for FP16 and for fcc's 12)
+        if (r.prefetch == 3) return fail(HS_E_INVALID, "split prefetch is a stencil option");
+        L.prefetch = r.prefetch == 0 ? ((h->precision == HS_FP32 && L.width <= 8) ? 1 : 0) : (r.prefetch == 1 ? 1 : 0);
         int bps = r.blocks_per_sm;
         const int occ = std::min(hs::pass_occupancy(h->precision, L, 0), hs::pass_occupancy(h->precision, L, 1));
         if (bps <= 0 || bps > occ) bps = occ;
@@ -1244,7 +1248,9 @@ int hs_get_launch(const hs_lattice *h, hs_launch *out) {
         out->tile_y = L.wave_k;
         out->chunk_z = L.wave_D;
     }
-    out->prefetch = (L.kernel == hs::kStencil) ? (L.prefetch == 1 ? 1 : (L.prefetch == 2 ? 3 : 2)) : 0;
+    out->prefetch = (L.kernel == hs::kStencil || L.kernel == hs::kTable)
+                        ? (L.prefetch == 1 ? 1 : (L.prefetch == 2 ? 3 : 2))
+                        : 0;
     out->ring = L.kernel == hs::kStaged ? L.ring_o : (L.kernel == hs::kWave ? L.wave_lag : 0);
     out->consumers = L.kernel == hs::kStaged ? L.consumers / 32 : 0;
     return HS_OK;
@@ -1267,7 +1273,8 @@ std::vector<hs_launch> tune_candidates(hs_lattice *h) {
     std::vector<hs_launch> out;
     const Layout &L = h->L;
     if (!L.structured) {
-        for (int b = 1; b <= 8; ++b) out.push_back({HS_KERNEL_TABLE, 1, b, 0, 0, 0, 0, 0});
+        for (int b = 1; b <= 8; ++b)
+            for (int pf : {1, 2}) out.push_back({HS_KERNEL_TABLE, 1, b, 0, 0, pf, 0, 0});
         return out;
     }
     for (int lag : {5, 8}) out.push_back({HS_KERNEL_WAVE, 0, 0, 2, 0, 0, lag, 0});  // rejected where it has no variant
