@@ -291,11 +291,13 @@ int hs_set_anisotropy_tensor(hs_lattice *h, const double A[6]);
 int hs_get_anisotropy_tensor(const hs_lattice *h, double A[6]);
 
 /* Autotuner: time every valid launch configuration (kernel, vector width,
- * CTAs per SM or slab rows and z chunk) for n_trial_sweeps sweeps at beta
- * and keep the fastest.  The spins, the accumulator and the
- * sweep counter are restored afterwards, so the chain is exactly as if the
- * call had not happened.  Choices are cached per (precision, shape, SM
- * count) for the life of the process.  Synchronous. */
+ * CTAs per SM, prefetch, slab rows and z chunk, wavefront groups) for
+ * n_trial_sweeps sweeps at beta, each from the same saved state and sweep
+ * counter (one warm-up sweep first); the three fastest are timed again over
+ * twice the sweeps and the fastest of those is kept.  The spins, the
+ * accumulator and the sweep counter are restored afterwards, so the chain is
+ * exactly as if the call had not happened.  Choices are cached per
+ * (precision, shape, SM count) for the life of the process.  Synchronous. */
 int hs_autotune(hs_lattice *h, double beta, int n_trial_sweeps);
 
 /* Host-only helper (no device needed): the greedy colouring the library
