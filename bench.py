@@ -387,6 +387,8 @@ def run_variants(args, rank, stream, barrier_sync, world, dev):
                          stream=stream)
         lat.init()
         lat.accumulate(True)
+        lat.sweep(1.0, 10)  # tune on a state past the random start (the acceptance rate, and with it the
+        #                    store traffic, falls as the lattice orders)
         launch = lat.launch if args.no_autotune else lat.autotune(1.0, 2)
         lat.sweep(1.0, 3)
         lat.reset_accumulator()
