@@ -38,9 +38,11 @@ class Scan:
 
 def run_scan(sizes, temps, *, n_equil: int, n_blocks: int, block_sweeps: int, replicas: int = 1, J: float = 1.0,
              K: float = 0.0, e=(0.0, 0.0, 1.0), precision: str = "fp32", seed: int = 2024, stream=None) -> Scan:
-    """Advance every (L, T, replica) sc lattice (L^3, periodic) together and
-    collect block means.  Returns a Scan whose sample arrays have
-    n_blocks * replicas entries per (L, T)."""
+    """Advance every (L, T, replica) sc lattice (L^3, periodic) and collect
+    block means.  FP32 lattices advance together in one hs_batch; FP64 and
+    FP16 lattices (which the batched kernel does not take) one after the
+    other with hs_sweep, block by block.  Returns a Scan whose sample arrays
+    have n_blocks * replicas entries per (L, T)."""
     sizes, temps = tuple(int(L) for L in sizes), tuple(float(T) for T in temps)
     members, betas, where = [], [], []
     for i, L in enumerate(sizes):
@@ -58,13 +60,22 @@ def run_scan(sizes, temps, *, n_equil: int, n_blocks: int, block_sweeps: int, re
     try:
         for m in members:
             m.init()
-        batch = hs.hs_batch_create([m.h for m in members])
-        if n_equil:
-            hs.hs_batch_run(batch, betas, 0, n_equil)
+        if precision == "fp32":
+            batch = hs.hs_batch_create([m.h for m in members])
+            if n_equil:
+                hs.hs_batch_run(batch, betas, 0, n_equil)
+        else:
+            for m, b in zip(members, betas):
+                m.sweep(b, n_equil)
+                m.accumulate(True)
         for _ in range(n_blocks):
             for m in members:
                 m.reset_accumulator()
-            hs.hs_batch_run(batch, betas, block_sweeps, 0)
+            if batch is not None:
+                hs.hs_batch_run(batch, betas, block_sweeps, 0)
+            else:
+                for m, b in zip(members, betas):
+                    m.sweep(b, block_sweeps)
             for m, key in zip(members, where):
                 mom, cnt = m.read_accumulator()
                 n_sites = m.info.n_present
@@ -118,6 +129,24 @@ def crossing(temps, u_small, u_large) -> float:
         return float("nan")
     k = idx[0]
     return float(t[k] + (t[k + 1] - t[k]) * d[k] / (d[k] - d[k + 1]))
+
+
+def binder_crossing(scan: Scan, i_small: int, i_large: int):
+    """T_c estimate from the crossing of the Binder cumulants U4(T) of sizes
+    i_small and i_large (linear interpolation between scan temperatures),
+    with a delete-one jackknife error over aligned samples of every (L, T)."""
+    nT = len(scan.temps)
+    keys = [(i, j) for i in (i_small, i_large) for j in range(nT)]
+    n = min(len(scan.M2[k]) for k in keys)
+    cols = []
+    for k in keys:
+        cols += [scan.M2[k][:n], scan.M4[k][:n]]
+
+    def estimate(*means):
+        u = [binder(means[2 * q], means[2 * q + 1]) for q in range(len(keys))]
+        return crossing(scan.temps, u[:nT], u[nT:])
+
+    return jackknife(estimate, *cols)
 
 
 def log_slope(x, y) -> float:

@@ -50,3 +50,24 @@ def test_power_law_fit_below_tc():
     T = np.array([1.0, 1.1, 1.2, 1.3, 1.4, 1.5, 1.6])
     M = np.where(T < 1.445, 1.3 * np.clip(1.445 - T, 1e-9, None) ** 0.364, 0.01)
     assert scan.power_law_exponent(T, M, 1.445) == pytest.approx(0.364, abs=1e-12)
+
+
+def test_binder_crossing_of_synthetic_curves():
+    """Two sizes whose U4(T) are straight lines crossing at T = 1.445; M4 is
+    built from U4 with M2 fixed, samples scattered symmetrically around the
+    means so the jackknife error is finite and the estimate exact."""
+    temps = (1.40, 1.43, 1.46, 1.49)
+    sc = scan.Scan(sizes=(8, 16), temps=temps, replicas=1, block_sweeps=1)
+    rng = np.random.default_rng(0)
+    for i, slope in enumerate((-1.0, -3.0)):
+        for j, T in enumerate(temps):
+            u = 0.60 + slope * (T - 1.445)
+            m2 = 0.1
+            m4 = (1 - u) * 3 * m2 * m2
+            d = rng.normal(size=10) * 1e-4
+            d = np.concatenate([d, -d])
+            sc.M2[(i, j)] = np.full(20, m2)
+            sc.M4[(i, j)] = m4 * (1 + d)
+    tc, err = scan.binder_crossing(sc, 0, 1)
+    assert tc == pytest.approx(1.445, abs=1e-9)
+    assert 0 < err < 1e-3
