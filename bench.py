@@ -319,12 +319,13 @@ def run_ours(args):
         return None
     cpu, spin_err = (None, None) if (args.no_cpu_baseline or world > 1) else cpu_baseline(args)
     precision = None if (args.no_precision or world > 1) else precision_runs(args)
+    tc = None if (args.no_precision or world > 1) else tc_runs(args)
     line = {"metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(tot_s * 1e3 / args.steps, 5), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": config_dict(args, world), "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": int(2 * args.steps), "clocks": clk.summary(), "fp64": fp64, "physics": physics,
-            "precision": precision, "spin_error_per_sweep": spin_err, "variants": variants}
+            "precision": precision, "tc": tc, "spin_error_per_sweep": spin_err, "variants": variants}
     return line
 
 
@@ -533,6 +534,25 @@ def cpu_baseline(args, sweeps=None, L=None):
     return out, errors
 
 
+def tc_runs(args):
+    """T_c of each precision path from the Binder-cumulant crossing of sc
+    L = 8 and 16 (K = 0, T = 1.38 .. 1.50, 6 replicas, 2000 + 8 x 1000
+    sweeps), with jackknife errors: FP32 batched, FP64 and FP16 lattice by
+    lattice."""
+    from paper_2106_11286_gb300 import scan
+    out = {}
+    for prec in ("fp64", "fp32", "fp16"):
+        sc = scan.run_scan((8, 16), (1.38, 1.42, 1.46, 1.50), n_equil=2000, n_blocks=8, block_sweeps=1000,
+                           replicas=6, precision=prec, seed=91)
+        tc, err = scan.binder_crossing(sc, 0, 1)
+        out[prec] = {"tc": round(tc, 5), "err": round(err, 5)}
+    for prec in ("fp32", "fp16"):
+        out[prec]["diff_vs_fp64_sigma"] = round((out[prec]["tc"] - out["fp64"]["tc"]) /
+                                                (out[prec]["err"] ** 2 + out["fp64"]["err"] ** 2) ** 0.5, 2)
+    out["what"] = "Binder-cumulant crossing of sc L = 8 and 16, K = 0; literature T_c = 1.443 J"
+    return out
+
+
 def precision_runs(args):
     """<E>/N and <|M|> of the 256^3 workload in FP64, FP32 and FP16 over the
     same sweeps from each path's own rounded start (the FP64 path is the
@@ -605,7 +625,8 @@ def main(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
-    ap.add_argument("--no-precision", action="store_true", help="skip the FP64/FP32/FP16 runs of the workload")
+    ap.add_argument("--no-precision", action="store_true",
+                    help="skip the FP64/FP32/FP16 runs of the workload and the T_c scans")
     ap.add_argument("--precision-sweeps", type=int, default=500)
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-big", action="store_true", help="skip the sc 1024^3 variant")
