@@ -246,6 +246,8 @@ def _launch_configs(precision, dims):
                     out += [dict(kernel="staged", vec_width=v, tile_y=ty),
                             dict(kernel="staged", vec_width=v, tile_y=ty, chunk_z=1, ring=4),
                             dict(kernel="staged", vec_width=v, tile_y=ty, chunk_z=3, ring=6, consumers=8)]
+        if v * es == 16 and precision != "fp64" and dims[2] >= 3:
+            out += [dict(kernel="wave", vec_width=v), dict(kernel="wave", vec_width=v, tile_y=1, chunk_z=3, ring=3)]
     return out
 
 
@@ -282,6 +284,26 @@ def test_launch_configuration_does_not_change_results(precision, dims):
         lat.sweep(0.9, 4)
         assert np.array_equal(lat.get_spins(), outs[0][0])
         assert lat.read_accumulator()[1] == 6
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp16", "fp64"])
+@pytest.mark.parametrize("kind,dims", [("bcc", (6, 5, 4)), ("fcc", (4, 3, 4)), ("sc_masked", (8, 8, 6))])
+def test_table_launch_configuration_does_not_change_results(precision, kind, dims):
+    """The neighbour-table kernel: CTAs per SM and the L2 prefetch of the next
+    site's row give bit-identical chains."""
+    mask = inputs.vacancy_mask(int(np.prod(dims)), 0.1, 4) if kind == "sc_masked" else None
+    lattice = "sc" if kind == "sc_masked" else kind
+    outs = []
+    cfgs = [dict(kernel="table", blocks_per_sm=b, prefetch=pf) for b in (1, 0) for pf in (1, 2)]
+    for cfg in cfgs:
+        with hs.Lattice(lattice, dims=dims, site_mask=mask, K=0.1, precision=precision, seed=8) as lat:
+            lat.set_launch(**cfg)
+            assert lat.launch["prefetch"] == cfg["prefetch"]
+            lat.init()
+            lat.sweep(0.9, 5)
+            outs.append(lat.get_spins())
+    for S, cfg in zip(outs[1:], cfgs[1:]):
+        assert np.array_equal(S, outs[0]), cfg
 
 
 def test_staged_kernel_parity_large(orc):
