@@ -250,6 +250,15 @@ def run_ours(args):
                 "kernel_timing": "timed-region CUDA events / colour-pass launches (the region holds only them)",
                 "kernel_ms_bracketed": round(kernel_ms_bracketed, 5),
                 "frac_of_8TBs_nominal": round(achieved_gbs / 8000.0, 4), "launch": launch}
+    # the other bounds of the same launches: the acceptance-weighted minimum 2 s + a s per attempt (rejected
+    # sites need no store) and the traffic measured by ncu
+    acc_rate = meas["accept_rate"]
+    s_fp32 = BYTES_PER_SPIN["fp32"]
+    min_bytes = (2 * s_fp32 + acc_rate * s_fp32) * (N // 2)
+    roofline["alg_bytes_per_launch_acceptance_weighted"] = int(min_bytes)
+    roofline["frac_acceptance_weighted"] = round(min_bytes / (kernel_ms * 1e-3) / 1e9 / peaks["hbm_gbs"], 4)
+    if traffic:
+        roofline["frac_ncu_traffic"] = round(traffic / (kernel_ms * 1e-3) / 1e9 / peaks["hbm_gbs"], 4)
     physics = {"E_per_spin": mom[0] / count / N, "absM": mom[2] / count, "accept_rate": meas["accept_rate"],
                "sweeps_averaged": count}
     lat.close()
