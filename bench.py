@@ -326,12 +326,12 @@ def run_ours(args):
         dist.barrier()
     if rank != 0:
         return None
-    # kernels launched in the timed region: two colour passes per sweep, or (wavefront kernel) one
-    # persistent launch plus its one-CTA finalisation per 256 sweeps
+    # kernels launched in the timed region: two colour passes per sweep and the one-CTA fold of the last
+    # sweep's sums, or (wavefront kernel) one persistent launch plus its one-CTA finalisation per 256 sweeps
     if launch and launch.get("kernel") == 6:
         gpu_launches = 2 * ((args.steps + 255) // 256)
     else:
-        gpu_launches = 2 * args.steps
+        gpu_launches = 2 * args.steps + 1
     cpu, spin_err = (None, None) if (args.no_cpu_baseline or world > 1) else cpu_baseline(args)
     precision = None if (args.no_precision or world > 1) else precision_runs(args)
     tc = None if (args.no_precision or world > 1) else tc_runs(args)

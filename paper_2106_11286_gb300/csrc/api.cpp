@@ -757,7 +757,7 @@ int lattice_create(hs_lattice **out, int type, const int32_t dims[3], int period
     }
     if (st == HS_OK) {
         h->max_blocks = h->n_sm * (2048 / hs::kBlock);
-        st = h->alloc(&h->partials, (size_t)L.n_colours * h->max_blocks * hs::kPartials * sizeof(double));
+        st = h->alloc(&h->partials, (size_t)2 * L.n_colours * h->max_blocks * hs::kPartials * sizeof(double));
         if (st == HS_OK) st = configure_launch(h);
     }
     if (st == HS_OK) st = h->alloc(&h->acc, sizeof(DevAccum));
@@ -823,14 +823,19 @@ int hs_init_spins(hs_lattice *h, int mode) {
 }
 
 namespace {
-// Launch colour pass c of sweep index `sweep` (the last colour finalises the
-// fused reductions).
-int run_pass(hs_lattice *h, PassArgs &a, uint32_t sweep, int c) {
+// Launch colour pass c of sweep index `sweep`.  Its CTAs' partial sums go to
+// the slots of parity sweep & 1.  deferred = 0: the last colour's last CTA to
+// arrive finalises the sweep inside the kernel.  deferred = 1 (hs_sweep): the
+// first colour's last CTA folds the previous sweep's slots, if there is one,
+// and the caller folds the last sweep after the loop.
+int run_pass(hs_lattice *h, PassArgs &a, uint32_t sweep, int c, bool deferred = false, bool has_prev = false) {
     const Layout &L = h->L;
     a.sweep = sweep;
     a.colour = c;
     a.pass = c;
-    a.finish = (c == L.n_colours - 1);
+    a.parity = (int)(sweep & 1u);
+    a.finish = deferred ? 0 : (c == L.n_colours - 1);
+    a.fin_prev = (deferred && has_prev && c == 0) ? 1 : 0;
     if (L.structured) {
         const size_t es = hs::storage_size(h->precision);
         const int64_t plane = (int64_t)L.Lz * L.Ly * L.Lh;
@@ -938,7 +943,9 @@ int hs_sweep(hs_lattice *h, double beta, int64_t n_sweeps) {
     }
     for (int64_t s = 0; s < n_sweeps; ++s)
         for (int c = 0; c < h->L.n_colours; ++c)
-            if (int st = run_pass(h, a, (uint32_t)(h->sweep + (uint64_t)s), c)) return st;
+            if (int st = run_pass(h, a, (uint32_t)(h->sweep + (uint64_t)s), c, true, s > 0)) return st;
+    // the last sweep's slots: one CTA after the loop
+    HS_CUDA(hs::launch_fold(a, (int)((h->sweep + (uint64_t)n_sweeps - 1) & 1u), h->stream));
     h->sweep += (uint64_t)n_sweeps;
     return HS_OK;
 }

@@ -409,26 +409,19 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
-// Finalise a sweep (or a standalone measurement): the last CTA to arrive sums
-// every CTA's slots of every pass in a fixed order, so the FP64 totals do not
-// depend on scheduling.
+// Fold one sweep's (or a standalone measurement's) slots into the
+// accumulator, executed by one whole CTA: every CTA's slots of every pass of
+// slot parity `parity`, summed in a fixed order (so the FP64 totals do not
+// depend on scheduling), then the accepted count, the raw sums and, when
+// measured, Eq. 2's M with its moments.
 template <int NT = kBlock>
-__device__ void finish_reduction(const PassArgs &a, bool measured) {
-    __shared__ int s_last;
+__device__ void reduce_slots(const PassArgs &a, int parity, bool measured, bool accumulate) {
     __shared__ double s_fin[NT / 32][kPartials];
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        const unsigned ticket = atomicAdd(&a.acc->done, 1u);
-        s_last = (ticket == (unsigned)a.n_blocks - 1u);
-    }
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
     double t[kPartials] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    const double *base = a.partials + (size_t)parity * a.n_colours * a.n_blocks * kPartials;
     for (int p = 0; p < a.n_colours; ++p)
         for (int b = threadIdx.x; b < a.n_blocks; b += NT) {
-            const double *slot = a.partials + ((size_t)p * a.n_blocks + b) * kPartials;
+            const double *slot = base + ((size_t)p * a.n_blocks + b) * kPartials;
 #pragma unroll
             for (int q = 0; q < kPartials; ++q) t[q] += __ldcg(slot + q);
         }
@@ -465,7 +458,7 @@ __device__ void finish_reduction(const PassArgs &a, bool measured) {
             A->last[5] = m2;
             A->last[6] = m2 * m2;
             A->last[7] = me;
-            if (a.accumulate) {
+            if (accumulate) {
                 A->moments[HS_SUM_E] += E;
                 A->moments[HS_SUM_E2] += E * E;
                 A->moments[HS_SUM_ABSM] += am;
@@ -478,8 +471,25 @@ __device__ void finish_reduction(const PassArgs &a, bool measured) {
                 A->count += 1.0;
             }
         }
-        A->done = 0u;
     }
+}
+
+// Finalise a single colour pass sequence or a standalone measurement inside
+// its last kernel: the last CTA to arrive folds the slots.
+template <int NT = kBlock>
+__device__ void finish_reduction(const PassArgs &a, bool measured) {
+    __shared__ int s_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned ticket = atomicAdd(&a.acc->done, 1u);
+        s_last = (ticket == (unsigned)a.n_blocks - 1u);
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    reduce_slots<NT>(a, a.parity, measured, a.accumulate != 0);
+    if (threadIdx.x == 0) a.acc->done = 0u;
 }
 
 // NT = threads of the CTA (a multiple of 32).
@@ -506,9 +516,19 @@ __device__ __forceinline__ void write_partials(const PassArgs &a, C e, C x, C y,
         double s = 0.0;
 #pragma unroll
         for (int w = 0; w < NT / 32; ++w) s += s_w[w][threadIdx.x];
-        a.partials[((size_t)a.pass * a.n_blocks + blockIdx.x) * kPartials + threadIdx.x] = s;
+        a.partials[(((size_t)a.parity * a.n_colours + a.pass) * a.n_blocks + blockIdx.x) * kPartials + threadIdx.x] =
+            s;
     }
-    if (a.finish) finish_reduction<NT>(a, MEAS);
+    if (a.finish) {
+        finish_reduction<NT>(a, MEAS);
+    } else if (a.fin_prev && blockIdx.x == gridDim.x - 1) {
+        // the previous sweep's passes completed before this kernel's loads
+        // (programmatic-launch wait); the last CTA, which has the fewest
+        // grid-stride items, folds its slots (the other parity) after its own
+        // work, so no kernel ends with a serial reduction
+        __syncthreads();
+        reduce_slots<NT>(a, a.parity ^ 1, a.accumulate != 0, a.accumulate != 0);
+    }
 }
 
 // ----------------------------------------------------------------- stencil pass

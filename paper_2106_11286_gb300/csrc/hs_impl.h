@@ -90,10 +90,12 @@ struct PassArgs {
     float fA[6];
     const double2 *sc_tab;  // FP64 trial: sin, cos(pi j / 128), j = 0..255
     uint32_t key0, key1, replica, sweep;
-    double *partials;       // [n_colours][n_blocks][kPartials]
+    double *partials;       // [2 parities][n_colours][n_blocks][kPartials]
     int pass;               // colour index = partial slot
+    int parity;             // slot parity: the sweep index & 1 (0 for single measurements)
     int n_blocks;
-    int finish;             // 1: last pass of the sweep, reduce and finalise
+    int finish;             // 1: last pass of the sequence, the last CTA to arrive reduces and finalises
+    int fin_prev;           // 1: the last CTA folds the previous sweep's slots (other parity) after its work
     int accumulate;         // 1: add the moments to the accumulator
     double n_present;
     DevAccum *acc;
@@ -214,6 +216,8 @@ cudaError_t launch_gather_sites(int precision, const Layout &L, int64_t n, const
 cudaError_t launch_scatter(int precision, const Layout &L, const double *d_xyz, cudaStream_t s);
 cudaError_t launch_gather(int precision, const Layout &L, double *d_xyz, cudaStream_t s);
 cudaError_t launch_measure(int precision, const Layout &L, const PassArgs &a, int n_blocks, cudaStream_t s);
+// Fold the slots of parity `parity` (one sweep of a.n_colours passes) into the accumulator (one CTA).
+cudaError_t launch_fold(const PassArgs &a, int parity, cudaStream_t s);
 int pass_blocks(int precision, const Layout &L, int n_sm, int blocks_per_sm);
 int pass_occupancy(int precision, const Layout &L, int accumulate);
 size_t staged_smem_bytes(int precision, int ty, int Lh, int ring_o, int ring_w);

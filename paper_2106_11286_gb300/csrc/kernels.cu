@@ -12,8 +12,13 @@
 // site): nothing of the generator lives in memory.
 //
 // Reductions: per-thread partials -> warp shuffle -> CTA (FP64) -> one slot
-// per CTA and pass; the last CTA of the finishing pass sums the slots in a
-// fixed order (bit-reproducible) and updates the FP64 accumulator.
+// per CTA and pass (two slot sets, by sweep parity).  Within hs_sweep the last
+// CTA of the next sweep's first pass -- the one with the fewest grid-stride
+// items -- folds a sweep's slots in a fixed order (bit-reproducible) into the
+// FP64 accumulator after its own work, and one CTA folds the last sweep after
+// the loop, so no pass ends waiting for a serial reduction (a last-arriving
+// CTA reducing inside the finishing pass cost 8 % at 256^3).  Single passes
+// and standalone measurements keep the last-arriving-CTA form.
 #include <cuda_fp16.h>
 #include <stdint.h>
 
@@ -698,6 +703,12 @@ __global__ void __launch_bounds__(kBlock) table_measure_kernel(const PassArgs a,
     write_partials<double, true>(a, accE, accX, accY, accZ, 0u);
 }
 
+// ----------------------------------------------------------------- fold
+// One sweep's slots into the accumulator, after the sweep's last pass.
+__global__ void __launch_bounds__(kBlock) fold_slots_kernel(const PassArgs a, int parity) {
+    reduce_slots<kBlock>(a, parity, a.accumulate != 0, a.accumulate != 0);
+}
+
 // ----------------------------------------------------------------- init / layout
 // Own sites of a periodic sc lattice or z-slab (nz planes from global plane
 // z0, stored from array plane z_off of Lz_arr): index i runs over them in
@@ -957,6 +968,11 @@ const void *staged_ptr(int vec, bool meas, int consumers) {
 }
 
 }  // namespace
+
+cudaError_t launch_fold(const PassArgs &a, int parity, cudaStream_t s) {
+    fold_slots_kernel<<<1, kBlock, 0, s>>>(a, parity);
+    return cudaGetLastError();
+}
 
 size_t storage_size(int precision) {
     return precision == HS_FP64 ? 8 : (precision == HS_FP32 ? 4 : 2);
