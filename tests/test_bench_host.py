@@ -1,0 +1,46 @@
+"""Host logic of bench.py that needs no GPU: the kernel labels that tie the
+stored ncu traffic to the timed launch, the source-hash gate on that traffic,
+and the per-sweep spin-error measure."""
+import numpy as np
+import pytest
+
+import bench
+
+
+def test_kernel_labels():
+    base = dict(kernel=1, vec_width=4, prefetch=3)
+    assert bench.kernel_label(base) == "sc_pass_kernel<1, 4, 1, 2, 0>"
+    assert bench.kernel_label(dict(base, prefetch=1)) == "sc_pass_kernel<1, 4, 1, 1, 0>"
+    assert bench.kernel_label(dict(base, prefetch=2)) == "sc_pass_kernel<1, 4, 1, 0, 0>"
+    assert bench.kernel_label(dict(kernel=5, vec_width=8, prefetch=0)) == "sc_pipe_kernel"
+    assert bench.kernel_label(dict(kernel=6, vec_width=4, prefetch=0)) == "sc_wave_kernel"
+
+
+def test_traffic_only_for_the_captured_sources_and_kernel(tmp_path, monkeypatch):
+    f = tmp_path / "traffic.txt"
+    f.write_text(f"kernel: sc_pass_kernel<1, 4, 1, 2, 0>\nsources_sha: {bench.kernels_sha()}\n"
+                 "dram_bytes_per_launch: 123\n")
+    monkeypatch.setattr(bench, "TRAFFIC_FILE", str(f))
+    assert bench.read_traffic("sc_pass_kernel<1, 4, 1, 2, 0>") == 123.0
+    assert bench.read_traffic("sc_pass_kernel<1, 4, 1, 0, 0>") is None
+    f.write_text("kernel: sc_pass_kernel<1, 4, 1, 2, 0>\nsources_sha: 0000\ndram_bytes_per_launch: 123\n")
+    assert bench.read_traffic("sc_pass_kernel<1, 4, 1, 2, 0>") is None
+
+
+def test_committed_traffic_matches_the_sources():
+    """The stored capture belongs to the current kernel sources (else the bench
+    reports no traffic)."""
+    assert bench.read_traffic("sc_pass_kernel<1, 4, 1, 2, 0>") is not None
+
+
+def test_spin_error_measure():
+    rng = np.random.default_rng(3)
+    S0 = rng.normal(size=(100, 3))
+    G, O = S0.copy(), S0.copy()
+    G[:40] += 1.0                 # both accept sites 0..39, O slightly differently
+    O[:40] += 1.0 + 1e-6
+    G[40:45] += 1.0               # the GPU alone accepts five sites
+    out = bench._spin_error(S0, G, O)
+    assert out["decision_mismatch_frac"] == pytest.approx(0.05)
+    assert out["err_max"] == pytest.approx(np.sqrt(3) * 1e-6, rel=1e-6)
+    assert out["accept_rate"] == pytest.approx(0.40)
