@@ -224,9 +224,9 @@ def run_ours(args):
     ms = t0.elapsed_time(t1)
     mom, count = lat.read_accumulator()
     # Mean launch duration of the dominant kernel from the CUDA events of the
-    # timed region: it holds nothing but colour-pass launches of that kernel
-    # (2 per step), so region time / launches, inter-launch gaps included,
-    # bounds the achieved bandwidth from below.  A second, identical run with
+    # timed region: it holds colour-pass launches of that kernel (2 per step)
+    # and one one-CTA fold of the last sweep's sums, so region time / launches,
+    # inter-launch gaps included, bounds the achieved bandwidth from below.  A second, identical run with
     # every launch bracketed by its own events is reported beside it (those
     # events delay each launch and break the overlap of consecutive passes).
     hs.hs_enable_timing(lat.h, True)
