@@ -211,6 +211,7 @@ def run_ours(args):
     # project autotuner (restores the chain); off for profiling runs, which
     # want a fixed launch sequence
     launch = lat.launch if args.no_autotune else lat.autotune(beta, 3)
+    fold = lat.info.fold_sweeps
     lat.sweep(beta, args.warmup)
     lat.reset_accumulator()
     t0 = torch.cuda.Event(enable_timing=True)
@@ -225,8 +226,9 @@ def run_ours(args):
     mom, count = lat.read_accumulator()
     # Mean launch duration of the dominant kernel from the CUDA events of the
     # timed region: it holds colour-pass launches of that kernel (2 per step)
-    # and one one-CTA fold of the last sweep's sums, so region time / launches,
-    # inter-launch gaps included, bounds the achieved bandwidth from below.  A second, identical run with
+    # and the ring folds of the fused sums (two small launches per fold_sweeps
+    # steps), so region time / launches, inter-launch gaps included, bounds the
+    # achieved bandwidth from below.  A second, identical run with
     # every launch bracketed by its own events is reported beside it (those
     # events delay each launch and break the overlap of consecutive passes).
     hs.hs_enable_timing(lat.h, True)
@@ -248,7 +250,7 @@ def run_ours(args):
                 "peak_source": f"{peak_kind} copy bandwidth", "kernel": kernel_label(launch) if launch else kname,
                 "kernel_ms": round(kernel_ms, 5), "alg_bytes_per_launch": alg_bytes,
                 "kernel_timing": "timed-region CUDA events / colour-pass launches (the region holds only them and "
-                                 "one one-CTA fold of the last sweep's sums)",
+                                 f"the ring folds of the fused sums, one per {fold} sweeps)",
                 "kernel_ms_bracketed": round(kernel_ms_bracketed, 5),
                 "frac_of_8TBs_nominal": round(achieved_gbs / 8000.0, 4), "launch": launch}
     # the other bounds of the same launches: the acceptance-weighted minimum 2 s + a s per attempt (rejected
@@ -278,7 +280,7 @@ def run_ours(args):
         barrier_sync()
         ms64 = t0.elapsed_time(t1)
         a64, s64 = aggregate(float(N) * args.fp64_steps, ms64 / 1e3, world, dev)
-        km64 = ms64 / (2 * args.fp64_steps)  # the region holds colour-pass launches and one one-CTA fold
+        km64 = ms64 / (2 * args.fp64_steps)  # the region holds colour-pass launches and the ring folds
         gbs64 = 3 * BYTES_PER_SPIN["fp64"] * (N // 2) / (km64 * 1e-3) / 1e9
         fp64 = {"value": round(a64 / (s64 * 1e9), 4), "unit": UNIT, "steps": args.fp64_steps,
                 "ms_per_step": round(ms64 / args.fp64_steps, 4), "kernel_ms": round(km64, 4),
@@ -312,10 +314,17 @@ def run_ours(args):
             e2e_step()
         barrier_sync()
         se = time.perf_counter() - te
+        # the host-to-device part alone (copy + conversion into the planes), for the breakdown
+        barrier_sync()
+        th = time.perf_counter()
+        hs.load().hs_set_spins(lat.h, host.data_ptr())
+        barrier_sync()
+        h2d_ms = (time.perf_counter() - th) * 1e3
         ea, es = aggregate(float(N) * sweeps * args.e2e_steps, se, world, dev)
         e2e = {"value": round(ea / (es * 1e9), 4), "unit": UNIT, "h2d_bytes_per_step": int(N * 3 * 8),
                "d2h_bytes_per_step": int(hs.HS_N_MOMENTS * 8 + 8), "sweeps_per_step": sweeps,
-               "steps": args.e2e_steps,
+               "steps": args.e2e_steps, "ms_per_step": round(se * 1e3 / args.e2e_steps, 3),
+               "set_spins_ms": round(h2d_ms, 3),
                "what": "hs_set_spins from pinned host FP64 state, hs_sweep x sweeps_per_step, "
                        "hs_read_accumulator to host; wall clock"}
         lat.close()
@@ -327,12 +336,13 @@ def run_ours(args):
         dist.barrier()
     if rank != 0:
         return None
-    # kernels launched in the timed region: two colour passes per sweep and the one-CTA fold of the last
-    # sweep's sums, or (wavefront kernel) one persistent launch plus its one-CTA finalisation per 256 sweeps
+    # kernels launched in the timed region: two colour passes per sweep and the ring folds of the fused
+    # sums (a per-sweep sum kernel and an apply kernel per fold_sweeps sweeps), or (wavefront kernel) one
+    # persistent launch plus its one-CTA finalisation per 256 sweeps
     if launch and launch.get("kernel") == 6:
         gpu_launches = 2 * ((args.steps + 255) // 256)
     else:
-        gpu_launches = 2 * args.steps + 1
+        gpu_launches = 2 * args.steps + 2 * ((args.steps + fold - 1) // fold)
     cpu, spin_err = (None, None) if (args.no_cpu_baseline or world > 1) else cpu_baseline(args)
     precision = None if (args.no_precision or world > 1) else precision_runs(args)
     tc = None if (args.no_precision or world > 1) else tc_runs(args)

@@ -127,6 +127,8 @@ typedef struct {
     int64_t n_present; /* N */
     int64_t device_bytes; /* device memory held by the handle */
     uint64_t sweep;    /* next sweep index (Philox counter word 1) */
+    int fold_sweeps;   /* hs_sweep folds the fused per-sweep sums into the accumulator
+                          after every fold_sweeps sweeps (1..64) and after its last one */
 } hs_info;
 
 /*

@@ -209,6 +209,7 @@ struct hs_lattice {
     int inject_timeout = 0;  // test hook, consumed by the next staged pass
     hs_launch req{};        // requested launch configuration (0 = automatic)
     int max_blocks = 1;     // capacity of the partials buffer
+    int fold_ring = 1;      // sweeps per ring fold (slot sets of the partials buffer)
     double *partials = nullptr;
     DevAccum *acc = nullptr;
     double *stage = nullptr;  // 3 * n_sites doubles, lazily for host copies
@@ -287,6 +288,7 @@ PassArgs base_args(const hs_lattice *h) {
         a.fA[q] = (float)h->tA[q];
     }
     a.partials = h->partials;
+    a.sweep_tot = h->partials + (size_t)h->fold_ring * L.n_colours * h->max_blocks * hs::kPartials;
     a.n_blocks = h->n_blocks;
     a.n_present = (double)L.n_present;
     a.acc = h->acc;
@@ -757,7 +759,12 @@ int lattice_create(hs_lattice **out, int type, const int32_t dims[3], int period
     }
     if (st == HS_OK) {
         h->max_blocks = h->n_sm * (2048 / hs::kBlock);
-        st = h->alloc(&h->partials, (size_t)2 * L.n_colours * h->max_blocks * hs::kPartials * sizeof(double));
+        // ring of per-sweep slot sets (at most 8 MB, at most kRingMax sweeps),
+        // then the ring fold's per-sweep totals
+        const size_t slot_doubles = (size_t)L.n_colours * h->max_blocks * hs::kPartials;
+        const size_t fit = (size_t)(8u << 20) / (slot_doubles * sizeof(double));
+        h->fold_ring = (int)std::max<size_t>(1, std::min<size_t>(hs::kRingMax, fit));
+        st = h->alloc(&h->partials, (slot_doubles + hs::kPartials) * (size_t)h->fold_ring * sizeof(double));
         if (st == HS_OK) st = configure_launch(h);
     }
     if (st == HS_OK) st = h->alloc(&h->acc, sizeof(DevAccum));
@@ -824,18 +831,16 @@ int hs_init_spins(hs_lattice *h, int mode) {
 
 namespace {
 // Launch colour pass c of sweep index `sweep`.  Its CTAs' partial sums go to
-// the slots of parity sweep & 1.  deferred = 0: the last colour's last CTA to
+// ring slot `slot`.  deferred = 0 (slot 0): the last colour's last CTA to
 // arrive finalises the sweep inside the kernel.  deferred = 1 (hs_sweep): the
-// first colour's last CTA folds the previous sweep's slots, if there is one,
-// and the caller folds the last sweep after the loop.
-int run_pass(hs_lattice *h, PassArgs &a, uint32_t sweep, int c, bool deferred = false, bool has_prev = false) {
+// caller folds the ring after each full group of sweeps and after its loop.
+int run_pass(hs_lattice *h, PassArgs &a, uint32_t sweep, int c, bool deferred = false, int slot = 0) {
     const Layout &L = h->L;
     a.sweep = sweep;
     a.colour = c;
     a.pass = c;
-    a.parity = (int)(sweep & 1u);
+    a.slot = slot;
     a.finish = deferred ? 0 : (c == L.n_colours - 1);
-    a.fin_prev = (deferred && has_prev && c == 0) ? 1 : 0;
     if (L.structured) {
         const size_t es = hs::storage_size(h->precision);
         const int64_t plane = (int64_t)L.Lz * L.Ly * L.Lh;
@@ -941,11 +946,18 @@ int hs_sweep(hs_lattice *h, double beta, int64_t n_sweeps) {
         h->sweep += (uint64_t)n_sweeps;
         return HS_OK;
     }
-    for (int64_t s = 0; s < n_sweeps; ++s)
+    // sweep s writes ring slot s mod ring; each full ring, and the rest after
+    // the loop, is folded into the accumulator in sweep order
+    int pending = 0;
+    for (int64_t s = 0; s < n_sweeps; ++s) {
         for (int c = 0; c < h->L.n_colours; ++c)
-            if (int st = run_pass(h, a, (uint32_t)(h->sweep + (uint64_t)s), c, true, s > 0)) return st;
-    // the last sweep's slots: one CTA after the loop
-    HS_CUDA(hs::launch_fold(a, (int)((h->sweep + (uint64_t)n_sweeps - 1) & 1u), h->stream));
+            if (int st = run_pass(h, a, (uint32_t)(h->sweep + (uint64_t)s), c, true, pending)) return st;
+        if (++pending == h->fold_ring) {
+            HS_CUDA(hs::launch_fold(a, pending, h->stream));
+            pending = 0;
+        }
+    }
+    if (pending > 0) HS_CUDA(hs::launch_fold(a, pending, h->stream));
     h->sweep += (uint64_t)n_sweeps;
     return HS_OK;
 }
@@ -1148,6 +1160,7 @@ int hs_get_info(const hs_lattice *h, hs_info *out) {
     out->n_present = h->L.n_present;
     out->device_bytes = h->device_bytes;
     out->sweep = h->sweep;
+    out->fold_sweeps = h->fold_ring;
     return HS_OK;
 }
 

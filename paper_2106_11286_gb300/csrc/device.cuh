@@ -409,21 +409,20 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
-// Fold one sweep's (or a standalone measurement's) slots into the
-// accumulator, executed by one whole CTA: every CTA's slots of every pass of
-// slot parity `parity`, summed in a fixed order (so the FP64 totals do not
-// depend on scheduling), then the accepted count, the raw sums and, when
-// measured, Eq. 2's M with its moments.
+// Totals of one ring slot (one sweep of a.n_colours passes, or a standalone
+// measurement), executed by one whole CTA: every CTA's partials of every
+// pass, summed in a fixed order (so the FP64 totals do not depend on
+// scheduling); the result is valid in thread 0.
 template <int NT = kBlock>
-__device__ void reduce_slots(const PassArgs &a, int parity, bool measured, bool accumulate) {
+__device__ void slot_totals(const PassArgs &a, int slot, double (&tot)[kPartials]) {
     __shared__ double s_fin[NT / 32][kPartials];
     double t[kPartials] = {0.0, 0.0, 0.0, 0.0, 0.0};
-    const double *base = a.partials + (size_t)parity * a.n_colours * a.n_blocks * kPartials;
+    const double *base = a.partials + (size_t)slot * a.n_colours * a.n_blocks * kPartials;
     for (int p = 0; p < a.n_colours; ++p)
         for (int b = threadIdx.x; b < a.n_blocks; b += NT) {
-            const double *slot = base + ((size_t)p * a.n_blocks + b) * kPartials;
+            const double *ps = base + ((size_t)p * a.n_blocks + b) * kPartials;
 #pragma unroll
-            for (int q = 0; q < kPartials; ++q) t[q] += __ldcg(slot + q);
+            for (int q = 0; q < kPartials; ++q) t[q] += __ldcg(ps + q);
         }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
@@ -432,47 +431,82 @@ __device__ void reduce_slots(const PassArgs &a, int parity, bool measured, bool 
 #pragma unroll
         for (int q = 0; q < kPartials; ++q) s_fin[warp][q] = t[q];
     __syncthreads();
-    if (threadIdx.x == 0) {
-        double tot[kPartials] = {0.0, 0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+    for (int q = 0; q < kPartials; ++q) tot[q] = 0.0;
+    if (threadIdx.x == 0)
         for (int w = 0; w < NT / 32; ++w)
 #pragma unroll
             for (int q = 0; q < kPartials; ++q) tot[q] += s_fin[w][q];
-        DevAccum *A = a.acc;
-        A->accepted += tot[4];
+}
+
+// Apply one sweep's totals to an accumulator (one thread): the accepted
+// count, the raw sums and, when measured, Eq. 2's M with its moments.  Acc is
+// DevAccum in device memory or AccRegs, a register copy of its fields.
+template <class Acc>
+__device__ __forceinline__ void apply_totals(Acc &A, const double (&tot)[kPartials], double n_present,
+                                             const double (&e)[3], bool measured, bool accumulate) {
+    A.accepted += tot[4];
 #pragma unroll
-        for (int q = 0; q < kPartials; ++q) A->sums[q] = tot[q];
-        if (measured) {
-            // Eq. 2 with |S| = 1: M = sum S / N
-            const double E = tot[0];
-            const double mx = tot[1] / a.n_present;
-            const double my = tot[2] / a.n_present;
-            const double mz = tot[3] / a.n_present;
-            const double m2 = mx * mx + my * my + mz * mz;
-            const double am = sqrt(m2);
-            const double me = fabs(mx * a.e[0] + my * a.e[1] + mz * a.e[2]);
-            A->last[0] = E;
-            A->last[1] = mx;
-            A->last[2] = my;
-            A->last[3] = mz;
-            A->last[4] = am;
-            A->last[5] = m2;
-            A->last[6] = m2 * m2;
-            A->last[7] = me;
-            if (accumulate) {
-                A->moments[HS_SUM_E] += E;
-                A->moments[HS_SUM_E2] += E * E;
-                A->moments[HS_SUM_ABSM] += am;
-                A->moments[HS_SUM_M2] += m2;
-                A->moments[HS_SUM_M4] += m2 * m2;
-                A->moments[HS_SUM_MX] += mx;
-                A->moments[HS_SUM_MY] += my;
-                A->moments[HS_SUM_MZ] += mz;
-                A->moments[HS_SUM_ABSME] += me;
-                A->count += 1.0;
-            }
-        }
+    for (int q = 0; q < kPartials; ++q) A.sums[q] = tot[q];
+    if (!measured) return;
+    // Eq. 2 with |S| = 1: M = sum S / N
+    const double E = tot[0];
+    const double mx = tot[1] / n_present;
+    const double my = tot[2] / n_present;
+    const double mz = tot[3] / n_present;
+    const double m2 = mx * mx + my * my + mz * mz;
+    const double am = sqrt(m2);
+    const double me = fabs(mx * e[0] + my * e[1] + mz * e[2]);
+    A.last[0] = E;
+    A.last[1] = mx;
+    A.last[2] = my;
+    A.last[3] = mz;
+    A.last[4] = am;
+    A.last[5] = m2;
+    A.last[6] = m2 * m2;
+    A.last[7] = me;
+    if (accumulate) {
+        A.moments[HS_SUM_E] += E;
+        A.moments[HS_SUM_E2] += E * E;
+        A.moments[HS_SUM_ABSM] += am;
+        A.moments[HS_SUM_M2] += m2;
+        A.moments[HS_SUM_M4] += m2 * m2;
+        A.moments[HS_SUM_MX] += mx;
+        A.moments[HS_SUM_MY] += my;
+        A.moments[HS_SUM_MZ] += mz;
+        A.moments[HS_SUM_ABSME] += me;
+        A.count += 1.0;
     }
 }
+
+// The fields of DevAccum that apply_totals updates, held in registers while
+// one thread applies many sweeps (one read and one write of device memory).
+struct AccRegs {
+    double moments[HS_N_MOMENTS];
+    double count, accepted;
+    double last[8];
+    double sums[kPartials];
+    __device__ __forceinline__ void load(const DevAccum *A) {
+#pragma unroll
+        for (int q = 0; q < HS_N_MOMENTS; ++q) moments[q] = A->moments[q];
+        count = A->count;
+        accepted = A->accepted;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) last[q] = A->last[q];
+#pragma unroll
+        for (int q = 0; q < kPartials; ++q) sums[q] = A->sums[q];
+    }
+    __device__ __forceinline__ void store(DevAccum *A) const {
+#pragma unroll
+        for (int q = 0; q < HS_N_MOMENTS; ++q) A->moments[q] = moments[q];
+        A->count = count;
+        A->accepted = accepted;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) A->last[q] = last[q];
+#pragma unroll
+        for (int q = 0; q < kPartials; ++q) A->sums[q] = sums[q];
+    }
+};
 
 // Finalise a single colour pass sequence or a standalone measurement inside
 // its last kernel: the last CTA to arrive folds the slots.
@@ -488,8 +522,12 @@ __device__ void finish_reduction(const PassArgs &a, bool measured) {
     __syncthreads();
     if (!s_last) return;
     __threadfence();
-    reduce_slots<NT>(a, a.parity, measured, a.accumulate != 0);
-    if (threadIdx.x == 0) a.acc->done = 0u;
+    double tot[kPartials];
+    slot_totals<NT>(a, a.slot, tot);
+    if (threadIdx.x == 0) {
+        apply_totals(*a.acc, tot, a.n_present, a.e, measured, a.accumulate != 0);
+        a.acc->done = 0u;
+    }
 }
 
 // NT = threads of the CTA (a multiple of 32).
@@ -516,19 +554,9 @@ __device__ __forceinline__ void write_partials(const PassArgs &a, C e, C x, C y,
         double s = 0.0;
 #pragma unroll
         for (int w = 0; w < NT / 32; ++w) s += s_w[w][threadIdx.x];
-        a.partials[(((size_t)a.parity * a.n_colours + a.pass) * a.n_blocks + blockIdx.x) * kPartials + threadIdx.x] =
-            s;
+        a.partials[(((size_t)a.slot * a.n_colours + a.pass) * a.n_blocks + blockIdx.x) * kPartials + threadIdx.x] = s;
     }
-    if (a.finish) {
-        finish_reduction<NT>(a, MEAS);
-    } else if (a.fin_prev && blockIdx.x == gridDim.x - 1) {
-        // the previous sweep's passes completed before this kernel's loads
-        // (programmatic-launch wait); the last CTA, which has the fewest
-        // grid-stride items, folds its slots (the other parity) after its own
-        // work, so no kernel ends with a serial reduction
-        __syncthreads();
-        reduce_slots<NT>(a, a.parity ^ 1, a.accumulate != 0, a.accumulate != 0);
-    }
+    if (a.finish) finish_reduction<NT>(a, MEAS);
 }
 
 // ----------------------------------------------------------------- stencil pass

@@ -23,6 +23,7 @@
 namespace hs {
 
 constexpr int kPartials = 5;  // E, Sx, Sy, Sz, accepted
+constexpr int kRingMax = 64;  // sweeps whose slots a ring fold takes at most
 constexpr int kBlock = 256;   // threads per CTA of the sweep kernels
 
 // Division by a runtime constant d (1 <= d < 2^31) of numerators n < 2^31
@@ -90,12 +91,12 @@ struct PassArgs {
     float fA[6];
     const double2 *sc_tab;  // FP64 trial: sin, cos(pi j / 128), j = 0..255
     uint32_t key0, key1, replica, sweep;
-    double *partials;       // [2 parities][n_colours][n_blocks][kPartials]
+    double *partials;       // [ring slots][n_colours][n_blocks][kPartials]
+    double *sweep_tot;      // [ring slots][kPartials]: per-sweep totals of a ring fold
     int pass;               // colour index = partial slot
-    int parity;             // slot parity: the sweep index & 1 (0 for single measurements)
+    int slot;               // ring slot: the sweep's index within its fold group (0 for single passes)
     int n_blocks;
     int finish;             // 1: last pass of the sequence, the last CTA to arrive reduces and finalises
-    int fin_prev;           // 1: the last CTA folds the previous sweep's slots (other parity) after its work
     int accumulate;         // 1: add the moments to the accumulator
     double n_present;
     DevAccum *acc;
@@ -216,8 +217,10 @@ cudaError_t launch_gather_sites(int precision, const Layout &L, int64_t n, const
 cudaError_t launch_scatter(int precision, const Layout &L, const double *d_xyz, cudaStream_t s);
 cudaError_t launch_gather(int precision, const Layout &L, double *d_xyz, cudaStream_t s);
 cudaError_t launch_measure(int precision, const Layout &L, const PassArgs &a, int n_blocks, cudaStream_t s);
-// Fold the slots of parity `parity` (one sweep of a.n_colours passes) into the accumulator (one CTA).
-cudaError_t launch_fold(const PassArgs &a, int parity, cudaStream_t s);
+// Fold ring slots 0 .. n_slots-1 (sweeps of a.n_colours passes each, in sweep
+// order) into the accumulator: one CTA per slot sums it, then one thread
+// applies the totals in order.  1 <= n_slots <= kRingMax.
+cudaError_t launch_fold(const PassArgs &a, int n_slots, cudaStream_t s);
 int pass_blocks(int precision, const Layout &L, int n_sm, int blocks_per_sm);
 int pass_occupancy(int precision, const Layout &L, int accumulate);
 size_t staged_smem_bytes(int precision, int ty, int Lh, int ring_o, int ring_w);

@@ -12,13 +12,14 @@
 // site): nothing of the generator lives in memory.
 //
 // Reductions: per-thread partials -> warp shuffle -> CTA (FP64) -> one slot
-// per CTA and pass (two slot sets, by sweep parity).  Within hs_sweep the last
-// CTA of the next sweep's first pass -- the one with the fewest grid-stride
-// items -- folds a sweep's slots in a fixed order (bit-reproducible) into the
-// FP64 accumulator after its own work, and one CTA folds the last sweep after
-// the loop, so no pass ends waiting for a serial reduction (a last-arriving
-// CTA reducing inside the finishing pass cost 8 % at 256^3).  Single passes
-// and standalone measurements keep the last-arriving-CTA form.
+// per CTA and pass, in a ring of slot sets, one per sweep of a group of up to
+// 64.  Within hs_sweep the passes only write slots; after each full group
+// (and after the loop) a ring fold sums every sweep's slots in a fixed order
+// (bit-reproducible), one CTA per sweep, and one thread applies the totals to
+// the FP64 accumulator in sweep order, so no pass carries a serial reduction
+// (a last-arriving CTA reducing inside the finishing pass cost 8 % at 256^3,
+// a fold in the next sweep's first pass 5 %).  Single passes and standalone
+// measurements keep the last-arriving-CTA form.
 #include <cuda_fp16.h>
 #include <stdint.h>
 
@@ -704,9 +705,30 @@ __global__ void __launch_bounds__(kBlock) table_measure_kernel(const PassArgs a,
 }
 
 // ----------------------------------------------------------------- fold
-// One sweep's slots into the accumulator, after the sweep's last pass.
-__global__ void __launch_bounds__(kBlock) fold_slots_kernel(const PassArgs a, int parity) {
-    reduce_slots<kBlock>(a, parity, a.accumulate != 0, a.accumulate != 0);
+// Ring fold, after the last pass of a group of sweeps: CTA i sums ring slot i
+// (sweep i of the group) into its per-sweep totals ...
+__global__ void __launch_bounds__(kBlock) fold_sum_kernel(const PassArgs a) {
+    double tot[kPartials];
+    slot_totals<kBlock>(a, blockIdx.x, tot);
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int q = 0; q < kPartials; ++q) a.sweep_tot[(size_t)blockIdx.x * kPartials + q] = tot[q];
+}
+
+// ... and one thread applies them to the accumulator in sweep order, the
+// accumulator held in registers over the group.
+__global__ void fold_apply_kernel(const PassArgs a, int n_slots) {
+    if (threadIdx.x != 0) return;
+    AccRegs R;
+    R.load(a.acc);
+    const bool acc = a.accumulate != 0;
+    for (int i = 0; i < n_slots; ++i) {
+        double tot[kPartials];
+#pragma unroll
+        for (int q = 0; q < kPartials; ++q) tot[q] = a.sweep_tot[(size_t)i * kPartials + q];
+        apply_totals(R, tot, a.n_present, a.e, acc, acc);
+    }
+    R.store(a.acc);
 }
 
 // ----------------------------------------------------------------- init / layout
@@ -969,8 +991,12 @@ const void *staged_ptr(int vec, bool meas, int consumers) {
 
 }  // namespace
 
-cudaError_t launch_fold(const PassArgs &a, int parity, cudaStream_t s) {
-    fold_slots_kernel<<<1, kBlock, 0, s>>>(a, parity);
+cudaError_t launch_fold(const PassArgs &a, int n_slots, cudaStream_t s) {
+    if (n_slots < 1 || n_slots > kRingMax) return cudaErrorInvalidValue;
+    fold_sum_kernel<<<n_slots, kBlock, 0, s>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    fold_apply_kernel<<<1, 32, 0, s>>>(a, n_slots);
     return cudaGetLastError();
 }
 

@@ -60,7 +60,7 @@ KERNELS = {"auto": 0, "stencil": 1, "staged": 2, "table": 3, "march": 4, "pipe":
 class hs_info(ctypes.Structure):
     _fields_ = [("type", ctypes.c_int), ("precision", ctypes.c_int), ("n_colours", ctypes.c_int),
                 ("structured", ctypes.c_int), ("n_sites", ctypes.c_int64), ("n_present", ctypes.c_int64),
-                ("device_bytes", ctypes.c_int64), ("sweep", ctypes.c_uint64)]
+                ("device_bytes", ctypes.c_int64), ("sweep", ctypes.c_uint64), ("fold_sweeps", ctypes.c_int)]
 
 
 _vp = ctypes.c_void_p

@@ -164,6 +164,41 @@ def test_accumulator_matches_oracle(orc):
     np.testing.assert_allclose(mom, want, rtol=1e-10, atol=1e-10)
 
 
+def test_ring_fold_over_many_sweeps(orc):
+    """More sweeps than one ring fold takes (64): the fused moments equal the
+    oracle's per-sweep recompute, and the same chain cut into calls at other
+    points (so the folds group other sweeps) gives bit-identical moments."""
+    dims = (8, 8, 8)
+    g = orc.lattice("sc", dims)
+    beta, n = 0.8, 139
+    with make_gpu("sc", dims, precision="fp64", seed=4, **PARAMS) as lat:
+        lat.init()
+        S = lat.get_spins()
+        lat.accumulate(True)
+        lat.reset_accumulator()
+        lat.sweep(beta, n)
+        mom, count = lat.read_accumulator()
+        last = hs.hs_read_sums(lat.h)
+    with make_gpu("sc", dims, precision="fp64", seed=4, **PARAMS) as lat:
+        lat.init()
+        lat.accumulate(True)
+        lat.reset_accumulator()
+        for k in (1, 63, 64, 11):
+            lat.sweep(beta, k)
+        mom2, count2 = lat.read_accumulator()
+        last2 = hs.hs_read_sums(lat.h)
+    assert count == count2 == n
+    np.testing.assert_array_equal(mom2, mom)
+    np.testing.assert_array_equal(last2, last)
+    want = np.zeros(9)
+    for s in range(n):
+        orc.sweep(g, S, beta=beta, seed=4, sweep_index=s, **PARAMS)
+        m = orc.measure(g, S, **PARAMS)
+        want += [m["E"], m["E"] ** 2, m["absM"], m["M2"], m["M4"], *m["M"], m["absMe"]]
+    np.testing.assert_allclose(mom, want, rtol=1e-9, atol=1e-9)
+    assert last[0] == pytest.approx(m["E"], rel=1e-10, abs=1e-9)
+
+
 def test_table_path_accumulator(orc):
     case = CASES["bcc_sphere"]
     g = oracle_graph(orc, "csr", row_ptr=case["row_ptr"], col=case["col"], mask=case["mask"])
