@@ -760,11 +760,11 @@ int lattice_create(hs_lattice **out, int type, const int32_t dims[3], int period
     if (st == HS_OK) {
         h->max_blocks = h->n_sm * (2048 / hs::kBlock);
         // ring of per-sweep slot sets (at most 8 MB, at most kRingMax sweeps),
-        // then the ring fold's per-sweep totals
+        // then the ring fold's per-sweep records
         const size_t slot_doubles = (size_t)L.n_colours * h->max_blocks * hs::kPartials;
         const size_t fit = (size_t)(8u << 20) / (slot_doubles * sizeof(double));
         h->fold_ring = (int)std::max<size_t>(1, std::min<size_t>(hs::kRingMax, fit));
-        st = h->alloc(&h->partials, (slot_doubles + hs::kPartials) * (size_t)h->fold_ring * sizeof(double));
+        st = h->alloc(&h->partials, (slot_doubles + hs::kSweepRecord) * (size_t)h->fold_ring * sizeof(double));
         if (st == HS_OK) st = configure_launch(h);
     }
     if (st == HS_OK) st = h->alloc(&h->acc, sizeof(DevAccum));

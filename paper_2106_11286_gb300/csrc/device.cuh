@@ -439,47 +439,52 @@ __device__ void slot_totals(const PassArgs &a, int slot, double (&tot)[kPartials
             for (int q = 0; q < kPartials; ++q) tot[q] += s_fin[w][q];
 }
 
-// Apply one sweep's totals to an accumulator (one thread): the accepted
-// count, the raw sums and, when measured, Eq. 2's M with its moments.  Acc is
-// DevAccum in device memory or AccRegs, a register copy of its fields.
-template <class Acc>
-__device__ __forceinline__ void apply_totals(Acc &A, const double (&tot)[kPartials], double n_present,
-                                             const double (&e)[3], bool measured, bool accumulate) {
-    A.accepted += tot[4];
-#pragma unroll
-    for (int q = 0; q < kPartials; ++q) A.sums[q] = tot[q];
-    if (!measured) return;
-    // Eq. 2 with |S| = 1: M = sum S / N
-    const double E = tot[0];
+// Eq. 2 with |S| = 1 from one sweep's totals: o = E, Mx, My, Mz, |M|, M2, M4,
+// |M.e| with M = sum S / N.
+__device__ __forceinline__ void sweep_observables(const double (&tot)[kPartials], double n_present,
+                                                  const double (&e)[3], double (&o)[8]) {
     const double mx = tot[1] / n_present;
     const double my = tot[2] / n_present;
     const double mz = tot[3] / n_present;
     const double m2 = mx * mx + my * my + mz * mz;
-    const double am = sqrt(m2);
-    const double me = fabs(mx * e[0] + my * e[1] + mz * e[2]);
-    A.last[0] = E;
-    A.last[1] = mx;
-    A.last[2] = my;
-    A.last[3] = mz;
-    A.last[4] = am;
-    A.last[5] = m2;
-    A.last[6] = m2 * m2;
-    A.last[7] = me;
+    o[0] = tot[0];
+    o[1] = mx;
+    o[2] = my;
+    o[3] = mz;
+    o[4] = sqrt(m2);
+    o[5] = m2;
+    o[6] = m2 * m2;
+    o[7] = fabs(mx * e[0] + my * e[1] + mz * e[2]);
+}
+
+// Apply one sweep to an accumulator (one thread): the accepted count, the raw
+// sums and, when measured, the observables o of sweep_observables and their
+// moments.  Acc is DevAccum in device memory or AccRegs, a register copy of
+// its fields.
+template <class Acc>
+__device__ __forceinline__ void apply_sweep(Acc &A, const double (&tot)[kPartials], const double (&o)[8],
+                                            bool measured, bool accumulate) {
+    A.accepted += tot[4];
+#pragma unroll
+    for (int q = 0; q < kPartials; ++q) A.sums[q] = tot[q];
+    if (!measured) return;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) A.last[q] = o[q];
     if (accumulate) {
-        A.moments[HS_SUM_E] += E;
-        A.moments[HS_SUM_E2] += E * E;
-        A.moments[HS_SUM_ABSM] += am;
-        A.moments[HS_SUM_M2] += m2;
-        A.moments[HS_SUM_M4] += m2 * m2;
-        A.moments[HS_SUM_MX] += mx;
-        A.moments[HS_SUM_MY] += my;
-        A.moments[HS_SUM_MZ] += mz;
-        A.moments[HS_SUM_ABSME] += me;
+        A.moments[HS_SUM_E] += o[0];
+        A.moments[HS_SUM_E2] += o[0] * o[0];
+        A.moments[HS_SUM_ABSM] += o[4];
+        A.moments[HS_SUM_M2] += o[5];
+        A.moments[HS_SUM_M4] += o[6];
+        A.moments[HS_SUM_MX] += o[1];
+        A.moments[HS_SUM_MY] += o[2];
+        A.moments[HS_SUM_MZ] += o[3];
+        A.moments[HS_SUM_ABSME] += o[7];
         A.count += 1.0;
     }
 }
 
-// The fields of DevAccum that apply_totals updates, held in registers while
+// The fields of DevAccum that apply_sweep updates, held in registers while
 // one thread applies many sweeps (one read and one write of device memory).
 struct AccRegs {
     double moments[HS_N_MOMENTS];
@@ -525,7 +530,9 @@ __device__ void finish_reduction(const PassArgs &a, bool measured) {
     double tot[kPartials];
     slot_totals<NT>(a, a.slot, tot);
     if (threadIdx.x == 0) {
-        apply_totals(*a.acc, tot, a.n_present, a.e, measured, a.accumulate != 0);
+        double o[8];
+        sweep_observables(tot, a.n_present, a.e, o);
+        apply_sweep(*a.acc, tot, o, measured, a.accumulate != 0);
         a.acc->done = 0u;
     }
 }

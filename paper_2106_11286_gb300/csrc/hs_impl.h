@@ -24,6 +24,7 @@ namespace hs {
 
 constexpr int kPartials = 5;  // E, Sx, Sy, Sz, accepted
 constexpr int kRingMax = 64;  // sweeps whose slots a ring fold takes at most
+constexpr int kSweepRecord = kPartials + 8;  // a ring fold's per-sweep record: totals, observables
 constexpr int kBlock = 256;   // threads per CTA of the sweep kernels
 
 // Division by a runtime constant d (1 <= d < 2^31) of numerators n < 2^31
@@ -92,7 +93,7 @@ struct PassArgs {
     const double2 *sc_tab;  // FP64 trial: sin, cos(pi j / 128), j = 0..255
     uint32_t key0, key1, replica, sweep;
     double *partials;       // [ring slots][n_colours][n_blocks][kPartials]
-    double *sweep_tot;      // [ring slots][kPartials]: per-sweep totals of a ring fold
+    double *sweep_tot;      // [ring slots][kSweepRecord]: per-sweep records of a ring fold
     int pass;               // colour index = partial slot
     int slot;               // ring slot: the sweep's index within its fold group (0 for single passes)
     int n_blocks;

@@ -706,27 +706,37 @@ __global__ void __launch_bounds__(kBlock) table_measure_kernel(const PassArgs a,
 
 // ----------------------------------------------------------------- fold
 // Ring fold, after the last pass of a group of sweeps: CTA i sums ring slot i
-// (sweep i of the group) into its per-sweep totals ...
+// (sweep i of the group) and writes that sweep's record (its totals and
+// observables) ...
 __global__ void __launch_bounds__(kBlock) fold_sum_kernel(const PassArgs a) {
     double tot[kPartials];
     slot_totals<kBlock>(a, blockIdx.x, tot);
-    if (threadIdx.x == 0)
+    if (threadIdx.x == 0) {
+        double o[8];
+        sweep_observables(tot, a.n_present, a.e, o);
+        double *rec = a.sweep_tot + (size_t)blockIdx.x * kSweepRecord;
 #pragma unroll
-        for (int q = 0; q < kPartials; ++q) a.sweep_tot[(size_t)blockIdx.x * kPartials + q] = tot[q];
+        for (int q = 0; q < kPartials; ++q) rec[q] = tot[q];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) rec[kPartials + q] = o[q];
+    }
 }
 
-// ... and one thread applies them to the accumulator in sweep order, the
-// accumulator held in registers over the group.
+// ... and one thread applies the records to the accumulator in sweep order,
+// the accumulator held in registers over the group.
 __global__ void fold_apply_kernel(const PassArgs a, int n_slots) {
     if (threadIdx.x != 0) return;
     AccRegs R;
     R.load(a.acc);
     const bool acc = a.accumulate != 0;
     for (int i = 0; i < n_slots; ++i) {
-        double tot[kPartials];
+        const double *rec = a.sweep_tot + (size_t)i * kSweepRecord;
+        double tot[kPartials], o[8];
 #pragma unroll
-        for (int q = 0; q < kPartials; ++q) tot[q] = a.sweep_tot[(size_t)i * kPartials + q];
-        apply_totals(R, tot, a.n_present, a.e, acc, acc);
+        for (int q = 0; q < kPartials; ++q) tot[q] = rec[q];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) o[q] = rec[kPartials + q];
+        apply_sweep(R, tot, o, acc, acc);
     }
     R.store(a.acc);
 }
