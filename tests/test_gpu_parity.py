@@ -219,6 +219,24 @@ def test_table_path_accumulator(orc):
     np.testing.assert_allclose(mom, want, rtol=1e-10, atol=1e-10)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp16"])
+@pytest.mark.parametrize("kind,dims", [("sc", (10, 6, 4)), ("bcc", (3, 3, 2))])
+def test_set_spins_from_page_locked_memory(precision, kind, dims):
+    """Page-locked host input stores the same state as pageable input."""
+    import torch
+    with make_gpu(kind, dims, precision=precision, seed=1, **PARAMS) as lat:
+        S = inputs.random_unit_spins(lat.info.n_sites, 5)
+        lat.set_spins(S)
+        want = lat.get_spins()
+        pinned = torch.from_numpy(S.copy()).pin_memory()
+        assert pinned.is_pinned()
+        lat.init()
+        assert not np.array_equal(lat.get_spins(), want)
+        hs.hs_set_spins(lat.h, pinned.numpy())
+        got = lat.get_spins()
+    np.testing.assert_array_equal(got, want)
+
+
 def test_edge_cases():
     # every site a vacancy: nothing to do, nothing fails
     with hs.Lattice("bcc", dims=(2, 2, 2), site_mask=np.zeros(16, np.uint8)) as lat:
