@@ -30,8 +30,9 @@
  *     index = natural site index (FP64 schedule, initial spins) or the
  *     site's rank within its colour class halved (FP32 schedule).
  *
- * Build: gcc -O2 -ffp-contract=off -fPIC -shared (no FMA contraction, so
- * every product and sum is the one written here).
+ * Build: gcc -O2 -ffp-contract=off -fopenmp -fPIC -shared (no FMA
+ * contraction, so every product and sum is the one written here; OpenMP only
+ * shares one colour class among threads in or_sweep_parallel).
  */
 #include <math.h>
 #include <stdint.h>
@@ -123,8 +124,8 @@ static void or_sphere_point(double uz, double uphi, double s[3])
  *   its half r & 1, i.e. words a = 2(r&1) and b = a+1.  u_z and u_phi are
  *   the top 21 bits of a and b, P the two low 11-bit fields (a's above b's),
  *   22 bits: u = k 2^-21, P = k 2^-22. */
-static void or_trial_uniforms(int mode, uint64_t seed, uint32_t replica, uint64_t site, uint64_t rank,
-                              uint64_t sweep, uint32_t colour, double u[3])
+void or_trial_uniforms(int mode, uint64_t seed, uint32_t replica, uint64_t site, uint64_t rank, uint64_t sweep,
+                       uint32_t colour, double u[3])
 {
     uint32_t r[4];
     if (mode == 0) {
@@ -451,8 +452,10 @@ static double site_energy(const double s[3], const double h[3], double J, double
 /* its present neighbours' spins, step (i)) is given: draw the trial from   */
 /* the schedule of `mode` (see or_sweep), take dH from Eq. 1 and accept if  */
 /* dH <= 0, else iff P <= exp(-beta dH).  Updates s in place on acceptance; */
-/* returns 1 if accepted.  *dH_out gets dH; *in_band is 1 for a dH > 0      */
-/* decision with |beta dH + ln P| < band.                                   */
+/* returns 1 if accepted.  *dH_out gets dH; *in_band is 1 for a decision   */
+/* with P > 0 and |beta dH + ln P| < band, on either side of dH = 0: a dH   */
+/* just below zero with P just below 1 is as close to the acceptance        */
+/* boundary exp(-beta dH) = P as a dH just above zero.                      */
 /* ------------------------------------------------------------------------ */
 int or_site_update(int mode, uint64_t seed, uint32_t replica, uint64_t site, uint64_t rank, uint64_t sweep,
                    uint32_t colour, double J, double K, const double e[3], const double *A, double beta,
@@ -470,14 +473,11 @@ int or_site_update(int mode, uint64_t seed, uint32_t replica, uint64_t site, uin
     double dH = site_energy(trial, h, J, K, e, A) - site_energy(s, h, J, K, e, A);
     double P = u[2];
     int accept;
-    *in_band = 0;
-    if (dH <= 0.0) {
+    if (dH <= 0.0)
         accept = 1;
-    } else {
+    else
         accept = (P <= exp(-beta * dH));
-        if (band > 0.0 && P > 0.0 && fabs(beta * dH + log(P)) < band)
-            *in_band = 1;
-    }
+    *in_band = (band > 0.0 && P > 0.0 && fabs(beta * dH + log(P)) < band);
     if (accept) {
         s[0] = trial[0];
         s[1] = trial[1];
@@ -515,8 +515,8 @@ void or_sites_update(int64_t m, const int64_t *site, const int64_t *rank, const 
 /*   mode 2: FP32 schedule, the trial spin rounded to binary16 per          */
 /*           component before dH (the stored state is the rounded one)     */
 /* Outputs: returns accepted moves; *sum_dH gets the sum of accepted dH;    */
-/* *n_band counts dH > 0 decisions with |beta dH + ln P| < band; band_site  */
-/* (optional, n bytes) is set to 1 at those sites.                          */
+/* *n_band counts decisions with |beta dH + ln P| < band (either sign of    */
+/* dH); band_site (optional, n bytes) is set to 1 at those sites.           */
 /* ------------------------------------------------------------------------ */
 int64_t or_sweep(int64_t n, const int64_t *row_ptr, const int32_t *col, const int32_t *colour,
                  int n_colours, const uint8_t *mask, double J, double K, const double e[3], const double *A,
@@ -559,6 +559,68 @@ int64_t or_sweep(int64_t n, const int64_t *row_ptr, const int32_t *col, const in
             }
         }
     }
+    if (sum_dH)
+        *sum_dH = dH_total;
+    if (n_band)
+        *n_band = bands;
+    return accepted;
+}
+
+/* ------------------------------------------------------------------------ */
+/* The same sweep with the sites of one colour class shared among          */
+/* n_threads OpenMP threads.  A class is an independent set: its sites     */
+/* read only other classes' spins, which do not change during the class,  */
+/* and every random number is keyed by the site (or by its class rank,     */
+/* counted here before the class starts), so the spins, the accepted count */
+/* and the band flags equal or_sweep's bit for bit whatever the thread     */
+/* count; only *sum_dH is added in another order.                          */
+/* ------------------------------------------------------------------------ */
+int64_t or_sweep_parallel(int64_t n, const int64_t *row_ptr, const int32_t *col, const int32_t *colour,
+                          int n_colours, const uint8_t *mask, double J, double K, const double e[3],
+                          const double *A, double beta, uint64_t seed, uint32_t replica, uint64_t sweep, int mode,
+                          double band, double *S, double *sum_dH, int64_t *n_band, uint8_t *band_site,
+                          int n_threads)
+{
+    int64_t accepted = 0;
+    double dH_total = 0.0;
+    int64_t bands = 0;
+    int64_t *rank = (int64_t *)malloc((size_t)(n > 0 ? n : 1) * sizeof(int64_t));
+    if (!rank)
+        return -1;
+    if (n_threads < 1)
+        n_threads = 1;
+    for (int c = 0; c < n_colours; ++c) {
+        int64_t count = 0;
+        for (int64_t i = 0; i < n; ++i)
+            rank[i] = (colour[i] == c && !(mask && !mask[i])) ? count++ : -1;
+#pragma omp parallel for schedule(static) num_threads(n_threads) reduction(+ : accepted, dH_total, bands)
+        for (int64_t i = 0; i < n; ++i) {
+            if (rank[i] < 0)
+                continue;
+            double h[3] = {0.0, 0.0, 0.0};
+            for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
+                int32_t j = col[k];
+                if (mask && !mask[j])
+                    continue;
+                h[0] += S[3 * (int64_t)j];
+                h[1] += S[3 * (int64_t)j + 1];
+                h[2] += S[3 * (int64_t)j + 2];
+            }
+            double dH;
+            int in_band;
+            if (or_site_update(mode, seed, replica, (uint64_t)i, (uint64_t)rank[i], sweep, (uint32_t)c, J, K, e, A,
+                               beta, band, h, &S[3 * i], &dH, &in_band)) {
+                dH_total += dH;
+                ++accepted;
+            }
+            if (in_band) {
+                ++bands;
+                if (band_site)
+                    band_site[i] = 1;
+            }
+        }
+    }
+    free(rank);
     if (sum_dH)
         *sum_dH = dH_total;
     if (n_band)

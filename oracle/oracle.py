@@ -31,7 +31,7 @@ _SRC = os.path.join(_HERE, "hs_oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
 
 MODE_FP64 = 0   # two Philox calls, three 53-bit uniforms, FP64 spins
-MODE_FP32 = 1   # one Philox call, three 24-bit uniforms, FP64 spins
+MODE_FP32 = 1   # one Philox block per two same-colour sites: 21/21/22-bit uniforms, FP64 spins
 MODE_FP16 = 2   # FP32 schedule, trial spin rounded to binary16
 
 
@@ -40,7 +40,7 @@ def build(force: bool = False) -> str:
     if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
         return _LIB
     tmp = _LIB + f".tmp{os.getpid()}"
-    cmd = ["gcc", "-O2", "-std=c11", "-D_GNU_SOURCE", "-ffp-contract=off", "-fno-fast-math",
+    cmd = ["gcc", "-O2", "-std=c11", "-D_GNU_SOURCE", "-ffp-contract=off", "-fno-fast-math", "-fopenmp",
            "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB)
@@ -82,6 +82,11 @@ def lib():
                                ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int,
                                ctypes.c_double, dp, dp, i64p, u8p]
         L.or_sweep.restype = ctypes.c_int64
+        L.or_sweep_parallel.argtypes = L.or_sweep.argtypes + [ctypes.c_int]
+        L.or_sweep_parallel.restype = ctypes.c_int64
+        L.or_trial_uniforms.argtypes = [ctypes.c_int, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint64,
+                                        ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32, dp]
+        L.or_trial_uniforms.restype = None
         L.or_sc_sites_neighbours.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                              ctypes.c_int64, i64p, i64p]
         L.or_sc_sites_neighbours.restype = None
@@ -142,6 +147,17 @@ def u24(a: int) -> float:
 
 def round_half(x: float) -> float:
     return lib().or_round_half(x)
+
+
+def trial_uniforms(mode: int, *, seed: int, replica: int, site: int, rank: int, sweep_index: int,
+                   colour: int) -> tuple[float, float, float]:
+    """(u_z, u_phi, P) of one trial move as the sweep draws them (Metropolis
+    steps (ii)-(iii)): FP64 schedule keyed by the natural site index, FP32
+    schedule by the site's rank in its colour class."""
+    u = np.zeros(3, dtype=np.float64)
+    lib().or_trial_uniforms(int(mode), int(seed), int(replica), int(site), int(rank), int(sweep_index), int(colour),
+                            _p(u, ctypes.c_double))
+    return float(u[0]), float(u[1]), float(u[2])
 
 
 # --------------------------------------------------------------------------- lattices
@@ -235,6 +251,29 @@ def sweep(g: Graph, S: np.ndarray, *, J: float, K: float, e, beta: float, seed: 
                          int(replica), int(sweep_index), int(mode), float(band),
                          _p(S, ctypes.c_double), ctypes.byref(sdh), ctypes.byref(nb),
                          _p(band_site, ctypes.c_uint8))
+    return int(acc), sdh.value, nb.value
+
+
+def sweep_parallel(g: Graph, S: np.ndarray, *, J: float, K: float, e, beta: float, seed: int,
+                   sweep_index: int, replica: int = 0, mode: int = MODE_FP64, band: float = 0.0,
+                   band_site: np.ndarray | None = None, A=None, threads: int | None = None):
+    """``sweep`` with each colour class's sites shared among OpenMP threads
+    (default: every core).  Spins, accepted count and band flags equal
+    ``sweep``'s bit for bit; the sum of accepted dH is added in another order."""
+    assert S.dtype == np.float64 and S.flags.c_contiguous and S.shape == (g.n, 3)
+    ev = np.ascontiguousarray(e, dtype=np.float64)
+    ev = ev / np.linalg.norm(ev)
+    At = _tensor(A)
+    sdh = ctypes.c_double(0.0)
+    nb = ctypes.c_int64(0)
+    acc = lib().or_sweep_parallel(g.n, _p(g.row_ptr, ctypes.c_int64), _p(g.col, ctypes.c_int32),
+                                  _p(g.colour, ctypes.c_int32), g.n_colours, _p(g.mask, ctypes.c_uint8),
+                                  float(J), float(K), _p(ev, ctypes.c_double), _p(At, ctypes.c_double), float(beta),
+                                  int(seed), int(replica), int(sweep_index), int(mode), float(band),
+                                  _p(S, ctypes.c_double), ctypes.byref(sdh), ctypes.byref(nb),
+                                  _p(band_site, ctypes.c_uint8), int(threads or os.cpu_count() or 1))
+    if acc < 0:
+        raise MemoryError("or_sweep_parallel: rank array allocation failed")
     return int(acc), sdh.value, nb.value
 
 

@@ -149,11 +149,10 @@ def test_464_sampled_sites(orc, colour464, precision, launch):
         got = S1[sites]
         acc_gpu = np.any(got != S0[sites], axis=1)
         assert 0.1 < acc.mean() < 0.9
-        # decisions differ only inside the band; reduced precisions may also
-        # flip a dH ~ 0 decision the oracle takes on the dH <= 0 side (where it
-        # flags no band) when P is within the trial-rounding error of 1
+        # decisions differ only inside the band, which the oracle flags on
+        # either side of dH = 0
         unexplained = int(np.sum((acc_gpu != acc) & ~band))
-        assert unexplained <= (0 if precision == "fp64" else 3), (precision, c, unexplained)
+        assert unexplained == 0, (precision, c, unexplained)
         both = acc & acc_gpu
         assert np.abs(got[both] - want[both]).max() <= TOL3[precision]
         rej = ~acc & ~acc_gpu

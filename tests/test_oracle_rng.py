@@ -95,3 +95,72 @@ def test_round_half_matches_numpy(orc):
     xs = np.concatenate([xs, mids, -mids])
     for x in xs:
         assert orc.round_half(float(x)) == float(np.float16(x)), x
+
+
+def _words(orc, *, index, sweep_index, colour, call, replica, seed):
+    """One Philox block of the trial schedule: counter (index, sweep,
+    tag 0 << 24 | colour << 8 | call, replica), key (seed lo, seed hi)."""
+    ctr = [index & 0xFFFFFFFF, sweep_index & 0xFFFFFFFF, (colour << 8) | call, replica]
+    return [int(w) for w in orc.philox(ctr, [seed & 0xFFFFFFFF, seed >> 32])]
+
+
+_DRAWS = [(seed, replica, rank, sweep_index, colour)
+          for seed in (1, 2, 0x1234567890AB) for replica in (0, 5) for rank in (0, 1, 2, 3, 4097, 2 ** 31 + 1)
+          for sweep_index in (0, 499) for colour in (0, 1, 3)]
+
+
+def test_fp32_schedule_fields_exact(orc):
+    """FP32/FP16 schedule: a site of class rank r takes half r & 1 of block
+    r >> 1, words a = w[2(r&1)], b = w[2(r&1)+1]; u_z = (a >> 11) 2^-21,
+    u_phi = (b >> 11) 2^-21, P = ((a & 0x7FF) << 11 | (b & 0x7FF)) 2^-22.
+    Checked the other way round: the three uniforms, scaled to integers,
+    must rebuild both words of the right half exactly, so a swapped half, a
+    field taken twice from one word or a dropped bit fails."""
+    for seed, replica, rank, sweep_index, colour in _DRAWS:
+        uz, uphi, P = orc.trial_uniforms(1, seed=seed, replica=replica, site=12345, rank=rank,
+                                         sweep_index=sweep_index, colour=colour)
+        kz, kphi, kp = Fraction(uz) * 2 ** 21, Fraction(uphi) * 2 ** 21, Fraction(P) * 2 ** 22
+        for k, top in ((kz, 2 ** 21), (kphi, 2 ** 21), (kp, 2 ** 22)):
+            assert k.denominator == 1 and 0 <= k < top
+        kz, kphi, kp = int(kz), int(kphi), int(kp)
+        w = _words(orc, index=rank >> 1, sweep_index=sweep_index, colour=colour, call=0, replica=replica, seed=seed)
+        half = rank & 1
+        assert (kz << 11) | (kp >> 11) == w[2 * half]
+        assert (kphi << 11) | (kp & 0x7FF) == w[2 * half + 1]
+        # the site's natural index plays no part in this schedule
+        assert orc.trial_uniforms(1, seed=seed, replica=replica, site=7, rank=rank, sweep_index=sweep_index,
+                                  colour=colour) == (uz, uphi, P)
+        # FP16 draws the same numbers
+        assert orc.trial_uniforms(2, seed=seed, replica=replica, site=7, rank=rank, sweep_index=sweep_index,
+                                  colour=colour) == (uz, uphi, P)
+
+
+def test_fp32_schedule_halves_of_one_block_share_nothing(orc):
+    """Ranks 2k and 2k+1 read disjoint halves of one block: together their six
+    fields hold all 128 bits of it."""
+    for k in (0, 1, 77):
+        a = orc.trial_uniforms(1, seed=2, replica=0, site=0, rank=2 * k, sweep_index=3, colour=1)
+        b = orc.trial_uniforms(1, seed=2, replica=0, site=0, rank=2 * k + 1, sweep_index=3, colour=1)
+        w = _words(orc, index=k, sweep_index=3, colour=1, call=0, replica=0, seed=2)
+        bits = []
+        for uz, uphi, P in (a, b):
+            kz, kphi, kp = int(uz * 2 ** 21), int(uphi * 2 ** 21), int(P * 2 ** 22)
+            bits += [(kz << 11) | (kp >> 11), (kphi << 11) | (kp & 0x7FF)]
+        assert bits == w
+
+
+def test_fp64_schedule_fields_exact(orc):
+    """FP64 schedule: keyed by the natural index; u_z from words 0, 1 and u_phi
+    from words 2, 3 of call 0, P from words 0, 1 of call 1, each the 53-bit
+    map (w0 >> 5) 2^26 + (w1 >> 6) over 2^53.  The uniforms, scaled to
+    integers, must rebuild the top 27 + 26 bits of those words."""
+    for seed, replica, site, sweep_index, colour in _DRAWS:
+        uz, uphi, P = orc.trial_uniforms(0, seed=seed, replica=replica, site=site, rank=999,
+                                         sweep_index=sweep_index, colour=colour)
+        w0 = _words(orc, index=site, sweep_index=sweep_index, colour=colour, call=0, replica=replica, seed=seed)
+        w1 = _words(orc, index=site, sweep_index=sweep_index, colour=colour, call=1, replica=replica, seed=seed)
+        for u, (a, b) in ((uz, (w0[0], w0[1])), (uphi, (w0[2], w0[3])), (P, (w1[0], w1[1]))):
+            k = Fraction(u) * 2 ** 53
+            assert k.denominator == 1
+            k = int(k)
+            assert k >> 26 == a >> 5 and k & (2 ** 26 - 1) == b >> 6

@@ -74,3 +74,68 @@ def test_init_sites_match_init_spins(orc):
     far = orc.init_sites(np.array([5, 5 + 2 ** 32]), seed=12, replica=3)
     assert not np.array_equal(far[0], far[1])
     assert np.allclose(np.linalg.norm(far, axis=1), 1.0, atol=1e-15)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_band_flag_is_two_sided(orc, mode):
+    """With J = K = 0 every dH is exactly 0, so every move is accepted through
+    the dH <= 0 branch; a decision is still as close to the boundary
+    P = exp(-beta dH) as |ln P|, and the flag must say so exactly when
+    |ln P| < band (a one-sided flag would never set one here)."""
+    m = 4000
+    sites = np.arange(m, dtype=np.int64)
+    ranks = np.arange(m, dtype=np.int64)
+    colours = np.zeros(m, dtype=np.int32)
+    h = inputs.random_unit_spins(m, 3)
+    S = inputs.random_unit_spins(m, 4)
+    band = 0.3
+    acc, flag = orc.sites_update(sites, ranks, colours, h, S, J=0.0, K=0.0, e=(0, 0, 1), beta=1.0, seed=6,
+                                 sweep_index=2, mode=mode, band=band)
+    assert acc.all()
+    P = np.array([orc.trial_uniforms(mode, seed=6, replica=0, site=int(i), rank=int(i), sweep_index=2,
+                                     colour=0)[2] for i in sites])
+    want = (P > 0) & (np.abs(np.log(np.where(P > 0, P, 1.0))) < band)
+    assert np.array_equal(flag, want)
+    assert 0.1 < want.mean() < 0.5   # 1 - exp(-0.3) = 0.26 of the draws
+
+
+def test_band_flag_both_sides_of_zero(orc):
+    """On a lattice the flag marks accepted decisions with dH on either side of
+    0 whenever |beta dH + ln P| < band; with a wide band both signs occur."""
+    dims = (8, 8, 8)
+    S = inputs.random_unit_spins(8 * 8 * 8, 5)
+    sites = np.arange(len(S))
+    colour, rank = orc.sc_sites_colour_rank(dims, sites)
+    h = S[orc.sc_site_neighbours(dims, True, sites)].sum(axis=1)
+    new = S.copy()
+    acc, flag = orc.sites_update(sites, rank, colour, h, new, beta=2.0, seed=3, sweep_index=1, mode=1,
+                                 band=0.5, **PARAMS)
+    # dH of the accepted moves, from Eq. 1's single-site energy of old and new spin
+    ev = np.asarray(PARAMS["e"]) / np.linalg.norm(PARAMS["e"])
+
+    def e_site(s):
+        return -PARAMS["J"] * (s * h).sum(1) - PARAMS["K"] * (s @ ev) ** 2
+    dH = e_site(new) - e_site(S)
+    assert np.any(flag & acc & (dH <= 0)) and np.any(flag & acc & (dH > 0))
+
+
+@pytest.mark.parametrize("mode", [0, 1, 2])
+@pytest.mark.parametrize("threads", [1, 3, 8])
+def test_parallel_sweep_is_bit_identical(orc, mode, threads):
+    rp, col, mask = inputs.bcc_nanoparticle(radius=4, box=10, vacancy_fraction=0.05, seed=2)
+    cases = [(orc.lattice("sc", (8, 6, 4)), None), (orc.lattice("fcc", (3, 3, 2)), None),
+             (orc.csr_graph(rp, col, mask), None)]
+    for g, _ in cases:
+        S0 = orc.init_spins(g, seed=4)
+        if mode == 2:
+            S0 = S0.astype(np.float16).astype(np.float64)
+        a, b = S0.copy(), S0.copy()
+        fa = np.zeros(g.n, dtype=np.uint8)
+        fb = np.zeros(g.n, dtype=np.uint8)
+        ra = orc.sweep(g, a, beta=1.1, seed=8, sweep_index=4, mode=mode, band=1e-2, band_site=fa, **PARAMS)
+        rb = orc.sweep_parallel(g, b, beta=1.1, seed=8, sweep_index=4, mode=mode, band=1e-2, band_site=fb,
+                                threads=threads, **PARAMS)
+        assert np.array_equal(a, b)
+        assert np.array_equal(fa, fb)
+        assert ra[0] == rb[0] and ra[2] == rb[2]
+        assert rb[1] == pytest.approx(ra[1], rel=1e-12, abs=1e-12)
