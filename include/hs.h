@@ -365,8 +365,14 @@ int hs_batch_get_layout(const hs_batch *b, int *ctas_per_sm, int *align_rows);
  * call on a device looks up the array's device address (cudaGetSymbolAddress,
  * once per device, with that device current); make that first call before
  * any stream capture.  A device that would need more CTAs than the scratch
- * holds is rejected with HS_E_INVALID.  Asynchronous on cuda_stream;
- * errors are reported through hs_last_error. */
+ * holds is rejected with HS_E_INVALID.  planes must start on a 4 * vec byte
+ * boundary, vec being the vector width the kernel takes for this Lx (4 when
+ * Lx/2 is a multiple of 4, else 2 when it is even, else 1), and d_out on an
+ * 8-byte boundary; a misaligned pointer (a view with a storage offset, say)
+ * is rejected with HS_E_INVALID before anything is launched.  The device
+ * address is cached for the life of the process: after cudaDeviceReset do
+ * not call this entry point again.  Asynchronous on cuda_stream; errors are
+ * reported through hs_last_error. */
 #define HS_NOALLOC_MAX_CTAS 1024
 int hs_sweep_sc_fp32_noalloc(float *planes, const int32_t dims[3], const hs_params *p, double beta,
                              uint64_t seed, uint32_t replica, uint64_t first_sweep, int64_t n_sweeps,

@@ -12,6 +12,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstdint>
 #include <mutex>
 #include <string>
 
@@ -36,6 +37,9 @@ int fail(int code, const std::string &msg) { return hs::set_last_error(code, msg
 
 // Device address of the scratch array on the current device, looked up once
 // per device (host code only sees a stand-in symbol, not a device address).
+// The cached address belongs to the module as loaded in the device's
+// current context; cudaDeviceReset unloads it, so after a reset the entry
+// point must not be called again in this process.
 int scratch_address(int dev, void **out) {
     std::lock_guard<std::mutex> lk(g_mu);
     if (!g_scratch[dev]) {
@@ -82,6 +86,14 @@ extern "C" int hs_sweep_sc_fp32_noalloc(float *planes, const int32_t dims[3], co
     L.Lz_glob = dims[2];
     L.Lh = dims[0] / 2;
     L.vec = (L.Lh % 4 == 0) ? 4 : ((L.Lh % 2 == 0) ? 2 : 1);
+    // the kernel moves vec floats per vector load and store, so every plane
+    // (a multiple of vec floats from the base) must start on that boundary
+    if ((uintptr_t)planes % (sizeof(float) * (size_t)L.vec) != 0)
+        return fail(HS_E_INVALID, "planes must be aligned to " + std::to_string(4 * L.vec) +
+                                      " bytes for this Lx (vector width " + std::to_string(L.vec) + ")");
+    if ((uintptr_t)d_out % alignof(double) != 0) return fail(HS_E_INVALID, "d_out must be 8-byte aligned");
+    // split prefetch when a CTA's items span 8 rows or more, as for a handle
+    L.prefetch = (L.Lh / L.vec <= hs::kBlock / 8) ? 2 : 0;
     L.n_sites = L.n_present = (int64_t)dims[0] * dims[1] * dims[2];
     L.planes = planes;
     const int occ = hs::pass_occupancy(HS_FP32, L, 1);

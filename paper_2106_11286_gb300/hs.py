@@ -368,8 +368,19 @@ def hs_colour_greedy(row_ptr, col_idx, site_mask=None):
 def hs_sweep_sc_fp32_noalloc(planes, dims, beta, n_sweeps, d_out, *, J=1.0, K=0.0, e=(0.0, 0.0, 1.0), seed=0,
                              replica=0, first_sweep=0, stream=None):
     """planes: CUDA float32 tensor (6 * Lz * Ly * Lx/2, stencil layout); d_out:
-    CUDA float64 tensor with HS_N_MOMENTS + 2 elements.  Allocates nothing."""
+    CUDA float64 tensor with HS_N_MOMENTS + 2 elements.  Allocates nothing.
+    Both are checked (dtype, device, contiguity, size) before the call; the
+    library checks the pointers' alignment."""
     d = np.ascontiguousarray(dims, dtype=np.int32)
+    if d.shape != (3,):
+        raise ValueError("dims must hold three sizes")
+    want = 6 * int(d[2]) * int(d[1]) * (int(d[0]) // 2)
+    for name, t, dtype, numel_ok in (("planes", planes, "torch.float32", lambda n: n == want),
+                                     ("d_out", d_out, "torch.float64", lambda n: n >= HS_N_MOMENTS + 2)):
+        if str(t.dtype) != dtype or t.device.type != "cuda" or not t.is_contiguous() or not numel_ok(t.numel()):
+            raise ValueError(f"{name} must be a contiguous CUDA {dtype} tensor of "
+                             + (f"{want} elements" if name == "planes" else f"at least {HS_N_MOMENTS + 2} elements")
+                             + f", got {t.dtype} on {t.device} with {t.numel()} elements")
     p = hs_params(float(J), float(K), (ctypes.c_double * 3)(*[float(v) for v in e]))
     _check(load().hs_sweep_sc_fp32_noalloc(planes.data_ptr(), _ptr(d, ctypes.c_int32), ctypes.byref(p),
                                            float(beta), int(seed), int(replica), int(first_sweep), int(n_sweeps),
