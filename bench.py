@@ -38,6 +38,9 @@ WORKLOAD = dict(name="sc256_fp32", kind="sc", L=256, J=1.0, K=0.05, e=(0.0, 0.0,
 METRIC = "Metropolis spin-update attempts/ns (sc 256^3, FP32 spins, FP64 reductions)"
 UNIT = "attempts/ns"
 BYTES_PER_SPIN = {"fp64": 24, "fp32": 12, "fp16": 6}
+# bytes per attempt the FP32 neighbour-table layout moves: 16-byte padded spin 4-vectors read twice and
+# written once, 8 int32 table entries
+TABLE_LAYOUT_BYTES = 3 * 16 + 8 * 4
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "sc_pass_fp32_sc256_traffic.txt")
 
 
@@ -216,13 +219,18 @@ def run_ours(args):
     lat.reset_accumulator()
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
-    barrier_sync()
+    # args.repeats regions of exactly K steps each, every one bracketed by a
+    # barrier and a device synchronisation; the headline is the median region
+    region_ms = []
     with ClockSampler(local) as clk:
-        t0.record(stream)
-        lat.sweep(beta, args.steps)
-        t1.record(stream)
-        barrier_sync()
-    ms = t0.elapsed_time(t1)
+        for _ in range(args.repeats):
+            barrier_sync()
+            t0.record(stream)
+            lat.sweep(beta, args.steps)
+            t1.record(stream)
+            barrier_sync()
+            region_ms.append(t0.elapsed_time(t1))
+    ms = statistics.median(region_ms)
     mom, count = lat.read_accumulator()
     # Mean launch duration of the dominant kernel from the CUDA events of the
     # timed region: it holds colour-pass launches of that kernel (2 per step)
@@ -252,6 +260,7 @@ def run_ours(args):
                 "kernel_timing": "timed-region CUDA events / colour-pass launches (the region holds only them and "
                                  f"the ring folds of the fused sums, one per {fold} sweeps)",
                 "kernel_ms_bracketed": round(kernel_ms_bracketed, 5),
+                "regions_ms": [round(x, 4) for x in region_ms],
                 "frac_of_8TBs_nominal": round(achieved_gbs / 8000.0, 4), "launch": launch}
     # the other bounds of the same launches: the acceptance-weighted minimum 2 s + a s per attempt (rejected
     # sites need no store) and the traffic measured by ncu
@@ -282,10 +291,12 @@ def run_ours(args):
         a64, s64 = aggregate(float(N) * args.fp64_steps, ms64 / 1e3, world, dev)
         km64 = ms64 / (2 * args.fp64_steps)  # the region holds colour-pass launches and the ring folds
         gbs64 = 3 * BYTES_PER_SPIN["fp64"] * (N // 2) / (km64 * 1e-3) / 1e9
-        fp64 = {"value": round(a64 / (s64 * 1e9), 4), "unit": UNIT, "steps": args.fp64_steps,
+        v64 = a64 / (s64 * 1e9)
+        fp64 = {"value": round(v64, 4), "unit": UNIT, "steps": args.fp64_steps,
                 "ms_per_step": round(ms64 / args.fp64_steps, 4), "kernel_ms": round(km64, 4),
                 "hbm_GBs": round(gbs64, 1), "hbm_frac": round(gbs64 / peaks["hbm_gbs"], 4),
-                "bound": "fp64 ALU (GB300 FP64 rate), see roofline notes"}
+                "launch": lat64.launch}
+        fp64.update(fp64_roofline(v64, stream))
         lat64.close()
 
     # ---- end to end through the C ABI with host buffers
@@ -346,17 +357,24 @@ def run_ours(args):
     cpu, spin_err = (None, None) if (args.no_cpu_baseline or world > 1) else cpu_baseline(args)
     precision = None if (args.no_precision or world > 1) else precision_runs(args)
     tc = None if (args.no_precision or world > 1) else tc_runs(args)
+    config1 = None if (args.no_precision or world > 1) else config1_run(args)
+    beta_exp = None if (args.no_beta or world > 1) else beta_runs(args)
+    # the compact summaries come last, so the tail of the line shows them
     line = {"metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(tot_s * 1e3 / args.steps, 5), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": config_dict(args, world), "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-            "gpu_launches": gpu_launches, "clocks": clk.summary(), "fp64": fp64, "physics": physics,
-            "precision": precision, "tc": tc, "spin_error_per_sweep": spin_err, "variants": variants}
+            "config": config_dict(args, world), "gpu_launches": gpu_launches, "clocks": clk.summary(),
+            "variants": variants, "e2e": e2e, "cpu_baseline": cpu, "physics": physics, "fp64": fp64,
+            "tc": tc, "beta_exponent": beta_exp, "config1_sc16_fp64": config1, "precision": precision,
+            "spin_error_per_sweep": spin_err, "roofline": roofline}
     return line
 
 
 # ------------------------------------------------------------------ other forms of the metric
 BATCH_SIZES = (16, 24, 32, 48, 64, 96)
+# M(T) scan of the critical exponent: temperatures (J = 1, k_B = 1) and the highest one in the power-law fit
+BETA_TEMPS = (1.20, 1.25, 1.30, 1.34, 1.37, 1.40, 1.42, 1.43, 1.44, 1.45, 1.46)
+BETA_FIT_TMAX = 1.40
 
 
 def _timed(stream, fn):
@@ -426,9 +444,7 @@ def run_variants(args, rank, stream, barrier_sync, world, dev):
                         "E_per_spin": mom[0] / cnt / N5, "absM": mom[2] / cnt,
                         "kernel": KERNEL_NAMES.get(launch["kernel"], "?"), "launch": launch}
         lat.close()
-    for prec in ("fp16", "fp32"):
-        ladder[prec]["bias_E_per_spin_vs_fp64"] = ladder[prec]["E_per_spin"] - ladder["fp64"]["E_per_spin"]
-        ladder[prec]["bias_absM_vs_fp64"] = ladder[prec]["absM"] - ladder["fp64"]["absM"]
+    ladder["note"] = "one seed each; the bias against FP64 with errors over seeds is under precision.sc464"
     out["sc464"] = ladder
     # (2b) beyond 10^8 spins on one GPU: sc 1024^3 (1,073,741,824 spins, 12.9 GB of FP32 state),
     #      the headline's parameters, autotuned launch
@@ -486,14 +502,65 @@ def run_variants(args, rank, stream, barrier_sync, world, dev):
         lat.reset_accumulator()
         sec = _timed(stream, lambda: lat.sweep(1 / 0.9, args.csr_sweeps))
         mom, cnt = lat.read_accumulator()
-        per_attempt = 3 * 16 + 4 * 8   # 4-vector spins, 8 int32 neighbours (the FP32 path keys Philox by rank)
-        out["bcc_nanoparticle"] = {"value": round(n_present * args.csr_sweeps / (sec * 1e9), 3), "unit": UNIT,
+        # algorithmic bytes per attempt: 3 s with s = 12 B of FP32 spin, plus z = 8 int32 neighbour
+        # indices and the row's 4-byte offset (the FP32 path keys Philox by colour rank)
+        per_attempt = 3 * BYTES_PER_SPIN["fp32"] + 8 * 4 + 4
+        v = n_present * args.csr_sweeps / (sec * 1e9)
+        out["bcc_nanoparticle"] = {"value": round(v, 3), "unit": UNIT,
                                    "n_spins": n_present, "colours": lat.info.n_colours, "sweeps": args.csr_sweeps,
-                                   "hbm_frac": round(per_attempt * n_present * args.csr_sweeps / sec / 1e9 /
-                                                     peaks["hbm_gbs"], 4),
+                                   "alg_bytes_per_attempt": per_attempt,
+                                   "hbm_frac": round(per_attempt * v / peaks["hbm_gbs"], 4),
+                                   "layout_bytes_per_attempt": TABLE_LAYOUT_BYTES,
+                                   "hbm_frac_layout_bytes": round(TABLE_LAYOUT_BYTES * v / peaks["hbm_gbs"], 4),
                                    "E_per_spin": mom[0] / cnt / n_present, "absM": mom[2] / cnt,
                                    "launch": launch}
         lat.close()
+    return out
+
+
+# ------------------------------------------------------------------ FP64 roofline
+FP64_OPS_FILE = os.path.join(ROOT, "profiles", "sc_pass_fp64_sc256_ops.txt")
+
+
+def read_fp64_ops():
+    """FP64 pipe instructions per attempt of the FP64 colour-pass kernel (DADD,
+    DMUL and DFMA each take one issue slot of the FP64 pipe), from the
+    committed ncu instruction counts, if they were taken on the current
+    kernel sources; else None."""
+    try:
+        kv = {}
+        for line in open(FP64_OPS_FILE):
+            if ":" in line and not line.startswith("#"):
+                k, v = line.split(":", 1)
+                kv[k.strip()] = v.strip()
+        if kv.get("sources_sha") != kernels_sha():
+            return None
+        return {"inst": float(kv["fp64_inst_per_attempt"]), "flop": float(kv["fp64_flop_per_attempt"]),
+                "kernel": kv.get("kernel", "")}
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+def fp64_roofline(value, stream):
+    """The FP64 path against the FP64 pipe.  hs_measure_alu_peak times DFMA
+    chains on every SM in the same run; one DFMA is one FP64 pipe
+    instruction, so peak instructions/s = measured FLOP/s / 2.  With the
+    kernel's FP64 instructions per attempt (ncu counts of DADD + DMUL + DFMA)
+    that bounds the attempts/ns; frac = achieved FP64 instructions/s over
+    that peak."""
+    from paper_2106_11286_gb300 import hs
+    peak = max(hs.hs_measure_alu_peak(hs.ALU_FP64, stream) for _ in range(3))
+    out = {"fp64_peak_tflops_measured": round(peak / 1e12, 4)}
+    ops = read_fp64_ops()
+    if ops:
+        peak_inst = peak / 2.0
+        achieved = value * 1e9 * ops["inst"]
+        out.update({"bound": "alu", "unit": "FP64 inst/s", "fp64_inst_per_attempt": ops["inst"],
+                    "fp64_flop_per_attempt": ops["flop"], "achieved": round(achieved / 1e12, 4),
+                    "peak": round(peak_inst / 1e12, 4), "frac": round(achieved / peak_inst, 4),
+                    "alu_bound_attempts_per_ns": round(peak_inst / ops["inst"] / 1e9, 3),
+                    "peak_source": "measured DFMA chains (hs_measure_alu_peak), 1 instruction = 2 FLOP",
+                    "kernel": ops["kernel"]})
     return out
 
 
@@ -521,13 +588,26 @@ def _spin_error(S0, G, O):
             "err_rms": float(np.sqrt((d * d).mean())), "accept_rate": float(acc_o.mean())}
 
 
+def host_cores() -> int:
+    """Host cores this process may run on (its CPU affinity)."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
 def cpu_baseline(args, sweeps=None, L=None):
-    """The oracle as it stands, single-threaded, on a bounded sample of the
-    workload: a few sweeps of the full 256^3 lattice, started from the FP32
-    path's own (rounded) initial state.  The same leg measures the spin error
-    per sweep of each GPU precision against the FP64 oracle: one sweep of the
-    full lattice from the same state in both (the FP32 and FP16 paths against
-    the oracle run with their random-number schedule and storage rounding)."""
+    """The oracle as it stands on a bounded sample of the workload (sweeps of
+    the full 256^3 lattice, started from the FP32 path's own rounded initial
+    state): once on one thread and once with each colour class shared among
+    every host core (the oracle's OpenMP sweep, bit-identical to the serial
+    one).  The all-core figure is the baseline value.  The same leg measures
+    the spin error per sweep of each GPU precision against the FP64 oracle:
+    one sweep of the full lattice from the same state in both (the FP32 and
+    FP16 paths against the oracle run with their random-number schedule and
+    storage rounding)."""
+    import numpy as np
+
     from oracle import oracle as orc
     w = WORKLOAD
     L = L or w["L"]
@@ -536,24 +616,36 @@ def cpu_baseline(args, sweeps=None, L=None):
     params = dict(J=w["J"], K=w["K"], e=w["e"], seed=w["seed"])
     g = orc.lattice("sc", (L, L, L))
     starts = {p: _one_sweep_gpu(p, L, params, beta) for p in ("fp32", "fp16", "fp64")}
-    S = starts["fp32"][0].copy()
-    dt = 0.0
-    after_one = None
+    cores = host_cores()
+    kw = dict(J=w["J"], K=w["K"], e=w["e"], beta=beta, seed=w["seed"], mode=orc.MODE_FP32)
+    S1 = starts["fp32"][0].copy()
+    t = time.perf_counter()
     for s in range(sweeps):
-        t = time.perf_counter()
-        orc.sweep(g, S, J=w["J"], K=w["K"], e=w["e"], beta=beta, seed=w["seed"], sweep_index=s, mode=orc.MODE_FP32)
-        dt += time.perf_counter() - t
+        orc.sweep(g, S1, sweep_index=s, **kw)
         if s == 0:
-            after_one = S.copy()
-    n = g.n * sweeps
-    out = {"value": round(n / (dt * 1e9), 6), "unit": UNIT, "cores": 1, "kind": "oracle",
-           "sample": f"{sweeps} sweeps of the sc {L}^3 lattice ({n} attempts), FP64 oracle with the FP32 "
-                     f"random-number schedule, 1 thread, {dt:.1f} s"}
+            after_one = S1.copy()
+    dt1 = time.perf_counter() - t
+    par_sweeps = max(sweeps, args.cpu_parallel_sweeps)
+    Sp = starts["fp32"][0].copy()
+    t = time.perf_counter()
+    for s in range(par_sweeps):
+        orc.sweep_parallel(g, Sp, sweep_index=s, threads=cores, **kw)
+        if s == sweeps - 1:
+            same = bool(np.array_equal(Sp, S1))
+    dtp = time.perf_counter() - t
+    n1, npar = g.n * sweeps, g.n * par_sweeps
+    out = {"value": round(npar / (dtp * 1e9), 6), "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": f"{par_sweeps} sweeps of the sc {L}^3 lattice ({npar} attempts), FP64 oracle with the FP32 "
+                     f"random-number schedule, each colour class shared among {cores} OpenMP threads, {dtp:.1f} s",
+           "nproc": os.cpu_count(), "bit_identical_to_serial": same,
+           "single_thread": {"value": round(n1 / (dt1 * 1e9), 6), "cores": 1,
+                             "sample": f"{sweeps} sweeps of the same lattice ({n1} attempts), {dt1:.1f} s"}}
     errors = {"fp32": _spin_error(starts["fp32"][0], starts["fp32"][1], after_one)}
     for prec, mode in (("fp16", orc.MODE_FP16), ("fp64", orc.MODE_FP64)):
         S0, G = starts[prec]
         O = S0.copy()
-        orc.sweep(g, O, J=w["J"], K=w["K"], e=w["e"], beta=beta, seed=w["seed"], sweep_index=0, mode=mode)
+        orc.sweep_parallel(g, O, J=w["J"], K=w["K"], e=w["e"], beta=beta, seed=w["seed"], sweep_index=0, mode=mode,
+                           threads=cores)
         errors[prec] = _spin_error(S0, G, O)
     errors["what"] = (f"one sweep of the sc {L}^3 workload from the same state on the GPU and in the FP64 oracle "
                       "(FP32 / FP16: the oracle with that path's random-number schedule and storage rounding)")
@@ -579,28 +671,149 @@ def tc_runs(args):
     return out
 
 
-def precision_runs(args):
-    """<E>/N and <|M|> of the 256^3 workload in FP64, FP32 and FP16 over the
-    same sweeps from each path's own rounded start (the FP64 path is the
-    reference; it is pinned to the oracle element by element in the tests)."""
+def _seeded_means(L, K, T, sweeps, precision, seeds, n_equil=0):
+    """<E>/N and <|M|> of an sc L^3 lattice (J = 1, e = z) over `sweeps`
+    measured sweeps after n_equil unmeasured ones, one independent chain per
+    seed from its own random start; returns the per-seed means."""
     from paper_2106_11286_gb300 import hs
-    w = WORKLOAD
-    L, beta = w["L"], 1.0 / w["T"]
-    params = dict(J=w["J"], K=w["K"], e=w["e"], seed=w["seed"])
-    out = {}
-    for prec in ("fp64", "fp32", "fp16"):
-        with hs.Lattice("sc", dims=(L, L, L), precision=prec, **params) as lat:
+    E, M, Mz = [], [], []
+    for seed in seeds:
+        with hs.Lattice("sc", dims=(L, L, L), J=1.0, K=K, e=(0.0, 0.0, 1.0), precision=precision, seed=seed) as lat:
             lat.init()
+            if n_equil:
+                lat.sweep(1.0 / T, n_equil)
             lat.accumulate(True)
-            lat.sweep(beta, args.precision_sweeps)
+            lat.sweep(1.0 / T, sweeps)
             mom, count = lat.read_accumulator()
-        n = float(L) ** 3
-        out[prec] = {"E_per_spin": mom[0] / count / n, "absM": mom[2] / count}
-    for prec in ("fp32", "fp16"):
-        out[prec]["bias_E_per_spin_vs_fp64"] = out[prec]["E_per_spin"] - out["fp64"]["E_per_spin"]
-        out[prec]["bias_absM_vs_fp64"] = out[prec]["absM"] - out["fp64"]["absM"]
-    out["sweeps"] = args.precision_sweeps
-    out["what"] = "measured every sweep from the start (no equilibration skipped), seed 2, T = 1.2"
+        E.append(mom[hs.MOMENTS.index("sum_E")] / count / float(L) ** 3)
+        M.append(mom[hs.MOMENTS.index("sum_absM")] / count)
+        Mz.append(mom[hs.MOMENTS.index("sum_absMe")] / count)
+    return E, M, Mz
+
+
+def _mean_err(x):
+    import numpy as np
+    x = np.asarray(x, dtype=np.float64)
+    return float(x.mean()), float(x.std(ddof=1) / np.sqrt(len(x))) if len(x) > 1 else float("nan")
+
+
+def _compare(per_prec):
+    """Means with their standard errors over seeds, and each reduced
+    precision's difference from FP64 in units of the combined error."""
+    out = {}
+    for prec, (E, M) in per_prec.items():
+        e, de = _mean_err(E)
+        m, dm = _mean_err(M)
+        out[prec] = {"E_per_spin": e, "E_err": de, "absM": m, "absM_err": dm}
+    for prec in out:
+        if prec == "fp64":
+            continue
+        r, f = out[prec], out["fp64"]
+        r["E_diff_sigma"] = round((r["E_per_spin"] - f["E_per_spin"]) / (r["E_err"] ** 2 + f["E_err"] ** 2) ** 0.5, 2)
+        r["absM_diff_sigma"] = round((r["absM"] - f["absM"]) / (r["absM_err"] ** 2 + f["absM_err"] ** 2) ** 0.5, 2)
+    return out
+
+
+def precision_runs(args):
+    """The precision comparison at the two workloads that state it, each path
+    over the same independent seeds (the FP64 path is pinned to the oracle
+    element by element in the tests):
+      sc256: sc 256^3, K = 0.05, T = 1.2, 500 sweeps measured from the start;
+      sc464: sc 464^3, K = 0.1, T = 1.0, 200 sweeps measured from the start.
+    <E>/N and <|M|> per seed, their mean and standard error over seeds, and the
+    FP32 / FP16 difference from FP64 in units of the combined error (the
+    spec bar is |diff| < 3 sigma)."""
+    seeds = [1000 + k for k in range(args.precision_seeds)]
+    out = {}
+    for name, L, K, T, sweeps in (("sc256", WORKLOAD["L"], WORKLOAD["K"], WORKLOAD["T"], args.precision_sweeps),
+                                  ("sc464", 464, 0.1, 1.0, args.big_sweeps)):
+        per = {}
+        for prec in ("fp64", "fp32", "fp16"):
+            E, M, _ = _seeded_means(L, K, T, sweeps, prec, seeds)
+            per[prec] = (E, M)
+        out[name] = _compare(per)
+        out[name]["sweeps"] = sweeps
+    out["seeds"] = len(seeds)
+    out["what"] = "means over independent seeds (random starts, every sweep measured), errors = std / sqrt(seeds)"
+    return out
+
+
+def config1_run(args):
+    """sc 16^3 periodic, J = 1, K = 0.1, e = z, T = 1.0, random start from
+    seed 1, 1000 equilibration + 1000 measured sweeps, FP64: <E>/N, <|M|>,
+    <M_z> and <|M_z|>, with the attempts/ns of the 2000 sweeps (CUDA events;
+    a 4096-spin lattice is launch- and latency-bound, so no HBM fraction).
+    The FP32 and FP16 paths over the same independent seeds give the 3-sigma
+    comparison at this size."""
+    import torch
+
+    from paper_2106_11286_gb300 import hs
+    L, K, T = 16, 0.1, 1.0
+    N = L ** 3
+    stream = torch.cuda.current_stream()
+    with hs.Lattice("sc", dims=(L, L, L), J=1.0, K=K, e=(0.0, 0.0, 1.0), precision="fp64", seed=1) as lat:
+        lat.init()
+        launch = lat.autotune(1.0 / T, 20)   # restores the state and the sweep counter
+        lat.sweep(1.0 / T, 5)
+        lat.init()   # the chain below starts from the seed's random state again
+        lat.set_sweep_counter(0)
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        t0.record(stream)
+        lat.sweep(1.0 / T, 1000)
+        lat.accumulate(True)
+        lat.sweep(1.0 / T, 1000)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        ms = t0.elapsed_time(t1)
+        mom, cnt = lat.read_accumulator()
+    out = {"E_per_spin": mom[hs.MOMENTS.index("sum_E")] / cnt / N, "absM": mom[hs.MOMENTS.index("sum_absM")] / cnt,
+           "Mz": mom[hs.MOMENTS.index("sum_Mz")] / cnt, "absMz": mom[hs.MOMENTS.index("sum_absMe")] / cnt,
+           "sweeps": [1000, 1000], "value": round(N * 2000 / (ms * 1e6), 4), "unit": UNIT,
+           "ms": round(ms, 3), "launch": launch}
+    seeds = list(range(1, 1 + args.precision_seeds))
+    per = {}
+    for prec in ("fp64", "fp32", "fp16"):
+        E, M, _ = _seeded_means(L, K, T, 1000, prec, seeds, n_equil=1000)
+        per[prec] = (E, M)
+    out["precision"] = _compare(per)
+    return out
+
+
+def beta_runs(args):
+    """The paper's M(T) curves and its critical exponent: sc 64^3 and 128^3
+    (and 256^3 below T_c), K = 0.01 (the paper's anisotropy), ordered start,
+    temperatures from 1.20 to just above T_c, all in one persistent FP32
+    batch per call.  T_c comes from the Binder crossing of 64^3 and 128^3;
+    beta from the paper's log-log fit of <|M|> on T_c - T over the points
+    T <= 1.40, jackknife errors over blocks (T_c's error included)."""
+    from paper_2106_11286_gb300 import scan
+    temps = BETA_TEMPS
+    fit_idx = [j for j, T in enumerate(temps) if T <= BETA_FIT_TMAX]
+    t = time.perf_counter()
+    sc = scan.run_scan((64, 128), temps, n_equil=args.beta_equil, n_blocks=args.beta_blocks,
+                       block_sweeps=args.beta_block_sweeps, replicas=2, K=0.01, seed=77, init="aligned")
+    tc, tc_err = scan.binder_crossing(sc, 0, 1)
+    b128, e128, _ = scan.beta_fit(sc, 1, fit_idx, tc_sizes=(0, 1))
+    p128, pe128, _ = scan.beta_fit(sc, 1, fit_idx, tc=1.445)
+    out = {"tc": round(tc, 4), "tc_err": round(tc_err, 4), "tc_from": "Binder crossing of 64^3 and 128^3",
+           "beta_128": round(b128, 4), "beta_128_err": round(e128, 4),
+           "beta_128_at_paper_tc": round(p128, 4), "beta_128_at_paper_tc_err": round(pe128, 4)}
+    curves = {"64": [round(float(sc.absM[(0, j)].mean()), 5) for j in range(len(temps))],
+              "128": [round(float(sc.absM[(1, j)].mean()), 5) for j in range(len(temps))]}
+    if not args.no_big:
+        big = scan.run_scan((256,), [temps[j] for j in fit_idx], n_equil=args.beta_equil // 2,
+                            n_blocks=max(4, args.beta_blocks // 2), block_sweeps=args.beta_block_sweeps, replicas=1,
+                            K=0.01, seed=78, init="aligned")
+        b256, e256, _ = scan.beta_fit(big, 0, range(len(fit_idx)), tc=tc)
+        out.update({"beta_256_at_tc": round(b256, 4), "beta_256_stat_err": round(e256, 4)})
+        curves["256"] = [round(float(big.absM[(0, j)].mean()), 5) for j in range(len(fit_idx))]
+    out.update({"paper": {"beta": "0.364 +- 0.002", "tc": 1.445, "K": 0.01},
+                "fit_temps": [temps[j] for j in fit_idx], "temps": list(temps), "absM": curves,
+                "seconds": round(time.perf_counter() - t, 1),
+                "what": "paper's log-log fit of <|M|> on T_c - T; K = 0.01, J = 1, e = z; 2 replicas of 64^3 and "
+                        "128^3 per temperature, 1 of 256^3 (fit at the crossing T_c, its error not propagated)"})
     return out
 
 
@@ -608,18 +821,20 @@ def run_reference(args):
     world, rank, _ = dist_setup()
     if rank != 0:
         return None
-    # bounded sample per step: an even sub-lattice sized so all steps take about a minute at ~150 ns/attempt
-    total = max(args.steps + args.warmup, 1)
-    L = int(round((4e8 / total) ** (1 / 3)))
-    L = max(8, min(WORKLOAD["L"], L - (L % 2)))
     from oracle import oracle as orc
     w = WORKLOAD
+    cores = host_cores()
+    # bounded sample per step: the workload's lattice, or an even sub-lattice of it sized so all steps take
+    # about a minute at ~150 ns per attempt and core
+    total = max(args.steps + args.warmup, 1)
+    L = int(round((4e8 * cores / total) ** (1 / 3)))
+    L = max(8, min(w["L"], L - (L % 2)))
     g = orc.lattice("sc", (L, L, L))
     S = orc.init_spins(g, seed=w["seed"])
 
     def step(s):
-        orc.sweep(g, S, J=w["J"], K=w["K"], e=w["e"], beta=1.0 / w["T"], seed=w["seed"], sweep_index=s,
-                  mode=orc.MODE_FP32)
+        orc.sweep_parallel(g, S, J=w["J"], K=w["K"], e=w["e"], beta=1.0 / w["T"], seed=w["seed"], sweep_index=s,
+                           mode=orc.MODE_FP32, threads=cores)
     for s in range(args.warmup):
         step(s)
     t = time.perf_counter()
@@ -628,13 +843,51 @@ def run_reference(args):
     dt = time.perf_counter() - t
     n = g.n * args.steps
     value = n / (dt * 1e9)
+    sample = (f"each step one oracle sweep of an sc {L}^3 " + ("lattice (the workload itself)" if L == w["L"] else
+                                                               "sub-lattice of the workload") +
+              f", each colour class shared among {cores} OpenMP threads")
     return {"impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt * 1e3 / max(args.steps, 1), 4),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": config_dict(args, world),
-            "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"each step one oracle sweep of an sc {L}^3 sub-lattice of the workload"},
+            "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample, "nproc": os.cpu_count()},
             "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+# ------------------------------------------------------------------ single cases for ncu captures
+CASES = {
+    # name: (L, precision, K, T, seed)
+    "sc256_fp32": (256, "fp32", 0.05, 1.2, 2),
+    "sc256_fp64": (256, "fp64", 0.05, 1.2, 2),
+    "sc464_fp16": (464, "fp16", 0.1, 1.0, 5),
+    "sc464_fp32": (464, "fp32", 0.1, 1.0, 5),
+}
+
+
+def run_case(args):
+    """One workload alone in its autotuned launch (tuned after 10 sweeps, as
+    the bench's variants are), then args.steps sweeps: a fixed, short launch
+    sequence for an ncu capture of its colour-pass kernel.  Prints the launch
+    and the attempts/ns of the swept region."""
+    import torch
+
+    from paper_2106_11286_gb300 import hs
+    L, prec, K, T, seed = CASES[args.case]
+    with hs.Lattice("sc", dims=(L,) * 3, J=1.0, K=K, e=(0, 0, 1), precision=prec, seed=seed) as lat:
+        lat.init()
+        lat.accumulate(True)
+        lat.sweep(1.0 / T, 10)
+        if args.launch:
+            kernel, vec, blocks = (int(x) for x in args.launch.split(","))
+            lat.set_launch(kernel=kernel, vec_width=vec, blocks_per_sm=blocks)
+            launch = lat.launch
+        else:
+            launch = lat.launch if args.no_autotune else lat.autotune(1.0 / T, 2)
+        lat.sweep(1.0 / T, args.warmup)
+        sec = _timed(torch.cuda.current_stream(), lambda: lat.sweep(1.0 / T, args.steps))
+    return {"case": args.case, "launch": launch, "kernel": KERNEL_NAMES.get(launch["kernel"], "?"),
+            "value": round(L ** 3 * args.steps / (sec * 1e9), 3), "unit": UNIT, "steps": args.steps}
 
 
 def main(argv=None):
@@ -661,10 +914,25 @@ def main(argv=None):
     ap.add_argument("--batch-sweeps", type=int, default=2000)
     ap.add_argument("--big-sweeps", type=int, default=200)
     ap.add_argument("--csr-sweeps", type=int, default=500)
+    ap.add_argument("--repeats", type=int, default=5, help="timed regions of K steps; the headline is their median")
+    ap.add_argument("--precision-seeds", type=int, default=8)
+    ap.add_argument("--cpu-parallel-sweeps", type=int, default=10)
+    ap.add_argument("--no-beta", action="store_true", help="skip the M(T) scan and the fit of beta")
+    ap.add_argument("--beta-equil", type=int, default=3000)
+    ap.add_argument("--beta-blocks", type=int, default=10)
+    ap.add_argument("--beta-block-sweeps", type=int, default=500)
+    ap.add_argument("--case", choices=sorted(CASES), help="run one workload alone (for ncu captures)")
+    ap.add_argument("--launch", help="with --case: fixed launch 'kernel,vec_width,blocks_per_sm' (hs_kernel codes), "
+                                     "no autotuning")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
-    line = run_reference(args) if args.impl == "reference" else run_ours(args)
+    if args.repeats < 1:
+        ap.error("--repeats must be >= 1")
+    if args.case:
+        line = run_case(args)
+    else:
+        line = run_reference(args) if args.impl == "reference" else run_ours(args)
     if line is not None:
         print(json.dumps(line), flush=True)
 

@@ -328,16 +328,23 @@ void hs_batch_destroy(hs_batch *b);
 /* Batch autotuner: the batch's work split -- its members' work items (4
  * sites of one row of one colour), concatenated and cut into one contiguous
  * range per CTA -- is timed for every CTA count per SM (1 up to the kernel's
- * occupancy) and both cut rules (at any item, or moved to the nearest row
- * boundary), for n_trial_sweeps sweeps at the given betas after one warm-up
- * sweep; the fastest is kept.  Every member's spins, sweep counter and
- * accumulator are restored, so the members' chains are as if the call had not
- * happened (spins are identical under every split; the FP64 sums are taken in
- * each split's own fixed order).  Synchronous.  hs_batch_get_layout reads the
- * split in use (hs_batch_create starts with the maximum CTAs per SM and cuts at
- * any item). */
+ * occupancy), both cut rules (at any item, or moved to the nearest row
+ * boundary) and both load schedules of the kernel (one work item of loads
+ * at a time, or split prefetch: the next item's own, same-row and z+-1 rows
+ * load during the current item's arithmetic), for n_trial_sweeps sweeps at
+ * the given betas after one warm-up sweep; the fastest is kept.  Every
+ * member's spins, sweep counter and accumulator are restored, so the members'
+ * chains are as if the call had not happened (spins are identical under
+ * every split and schedule; the FP64 sums are taken in each split's own fixed
+ * order).  Synchronous.  hs_batch_get_layout reads the split and schedule in
+ * use (hs_batch_create starts with the maximum CTAs per SM, cuts at any item
+ * and no prefetch). */
 int hs_batch_autotune(hs_batch *b, const double *betas, int n_trial_sweeps);
-int hs_batch_get_layout(const hs_batch *b, int *ctas_per_sm, int *align_rows);
+int hs_batch_get_layout(const hs_batch *b, int *ctas_per_sm, int *align_rows, int *prefetch);
+/* Set the split and schedule by hand: ctas_per_sm in 1 .. the kernel's
+ * occupancy, align_rows and prefetch 0 or 1 (HS_E_INVALID otherwise).  The
+ * members' chains do not depend on it.  Synchronises the batch's stream. */
+int hs_batch_set_layout(hs_batch *b, int ctas_per_sm, int align_rows, int prefetch);
 
 /* Allocation-free sweep (the paper has no counterpart; it is a service to
  * callers that cannot allocate device memory themselves: a host framework
@@ -407,6 +414,28 @@ int hs_slab_plane(const hs_lattice *h, int colour, int component, int which, voi
  * src to plane dst_which of dst (same lattice and device), on dst's stream:
  * the halo exchange of slabs that share a device. */
 int hs_slab_copy_plane(hs_lattice *dst, int dst_which, const hs_lattice *src, int src_which, int colour);
+/* One message per halo transfer between processes: hs_slab_pack copies the
+ * three component planes (x, y, z) of colour `colour` at plane `which` (as
+ * for hs_slab_plane) back to back into the caller's device buffer d_buf
+ * (3 x the plane bytes hs_slab_plane reports); hs_slab_unpack copies such a
+ * buffer into plane `which` of this slab.  Device-to-device copies ordered on
+ * the handle's stream, so a stream-ordered send (NCCL) of d_buf needs no host
+ * synchronisation. */
+int hs_slab_pack(const hs_lattice *h, int colour, int which, void *d_buf);
+int hs_slab_unpack(hs_lattice *h, int colour, int which, const void *d_buf);
+
+/* Stream-ordered forms of the sums exchange of a multi-process lattice:
+ * hs_read_sums_device copies the last finalised sweep's five sums (as
+ * hs_read_sums) to device memory d_out; after the caller's allreduce over
+ * the processes, hs_accumulate_sums takes the five totals d_tot (device
+ * memory) of one sweep of the whole lattice of n_sites present spins and adds
+ * that sweep's E and M moments (Eq. 1, Eq. 2) to this handle's accumulator,
+ * as a single lattice does with its own sums; hs_read_accumulator reads them.
+ * Keep the slab's own accumulation off (hs_accumulate(h, 0)), or its
+ * per-slab observables are added too.  Asynchronous. */
+int hs_read_sums_device(hs_lattice *h, double *d_out);
+int hs_accumulate_sums(hs_lattice *h, const double *d_tot, int64_t n_sites);
+
 /* Spins of n selected sites in FP64: out[3t .. 3t+2] = S of the site with
  * global natural index sites[t] (host arrays, the caller's).  Periodic sc
  * lattices and slabs (own sites only); HS_E_INVALID for any other site.
@@ -419,6 +448,17 @@ int hs_get_sites(hs_lattice *h, int64_t n, const int64_t *sites, double *out);
  * lattice they give its E (every bond is counted at its colour-1 end, which
  * one slab owns) and M = sum S / N. */
 int hs_read_sums(hs_lattice *h, double out[5]);
+
+/* Measured arithmetic peak of the current device, for the roofline of a
+ * path bound by arithmetic rather than memory (the FP64 sweep: the paper
+ * runs in double precision, and GB300's FP64 rate, not its HBM, bounds it).
+ * kind 0: FP64 fused multiply-add (DFMA); 1: FP32 FFMA; 2: packed FP32
+ * (two lanes per instruction, the form the FP32 / FP16 sweep kernels use).
+ * Runs independent FMA chains on every SM (8 CTAs of 256 threads per SM,
+ * 8 chains per thread), a warm-up launch, then one launch timed with CUDA
+ * events on cuda_stream; *flops_per_s = 2 x FMAs / time.  Allocates and
+ * frees a small device buffer; synchronous.  HS_E_INVALID for another kind. */
+int hs_measure_alu_peak(int kind, void *cuda_stream, double *flops_per_s);
 
 /* Test hooks for the bounded device-side waits (failure detection without a
  * GPU fault).  hs_lattice_inject_timeout: the next colour pass of a lattice

@@ -27,6 +27,7 @@
 #include <vector>
 
 #include "hs_impl.h"
+#include "slab.h"
 
 namespace {
 std::string &g_error_ref();
@@ -974,7 +975,9 @@ int hs_sweep_pass(hs_lattice *h, double beta, int colour) {
         PassArgs a = base_args(h);
         a.beta = beta;
         a.fbeta = (float)beta;
-        a.accumulate = h->accumulate;
+        // a slab always measures its fused sums (the observables of a lattice split into slabs come from
+        // all slabs' sums); only accumulation adds its own moments
+        a.accumulate = h->accumulate ? 1 : (h->L.slab ? 2 : 0);
         if (int st = run_pass(h, a, (uint32_t)h->sweep, colour)) return st;
     }
     if (colour == h->L.n_colours - 1) h->sweep += 1;
@@ -1008,6 +1011,42 @@ int hs_slab_copy_plane(hs_lattice *dst, int dst_which, const hs_lattice *src, in
         if (int st = hs_slab_plane(src, colour, q, src_which, &sp, &ns)) return st;
         HS_CUDA(cudaMemcpyAsync(d, sp, nb, cudaMemcpyDeviceToDevice, dst->stream));
     }
+    return HS_OK;
+}
+
+int hs_slab_pack(const hs_lattice *h, int colour, int which, void *d_buf) {
+    if (!h || !d_buf) return fail(HS_E_INVALID, "null argument");
+    for (int q = 0; q < 3; ++q) {
+        void *sp = nullptr;
+        size_t nb = 0;
+        if (int st = hs_slab_plane(h, colour, q, which, &sp, &nb)) return st;
+        HS_CUDA(cudaMemcpyAsync(static_cast<char *>(d_buf) + q * nb, sp, nb, cudaMemcpyDeviceToDevice, h->stream));
+    }
+    return HS_OK;
+}
+
+int hs_slab_unpack(hs_lattice *h, int colour, int which, const void *d_buf) {
+    if (!h || !d_buf) return fail(HS_E_INVALID, "null argument");
+    for (int q = 0; q < 3; ++q) {
+        void *dp = nullptr;
+        size_t nb = 0;
+        if (int st = hs_slab_plane(h, colour, q, which, &dp, &nb)) return st;
+        HS_CUDA(cudaMemcpyAsync(dp, static_cast<const char *>(d_buf) + q * nb, nb, cudaMemcpyDeviceToDevice,
+                                h->stream));
+    }
+    return HS_OK;
+}
+
+int hs_read_sums_device(hs_lattice *h, double *d_out) {
+    if (!h || !d_out) return fail(HS_E_INVALID, "null argument");
+    HS_CUDA(cudaMemcpyAsync(d_out, h->acc->sums, 5 * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    return HS_OK;
+}
+
+int hs_accumulate_sums(hs_lattice *h, const double *d_tot, int64_t n_sites) {
+    if (!h || !d_tot) return fail(HS_E_INVALID, "null argument");
+    if (n_sites < 1) return fail(HS_E_INVALID, "n_sites must be >= 1");
+    HS_CUDA(hs::launch_slab_apply(h->acc, d_tot, (double)n_sites, h->p.e, h->stream));
     return HS_OK;
 }
 
@@ -1443,6 +1482,7 @@ struct hs_batch {
     bool graph_failed = false;
     int inject_timeout = 0;  // test hook, consumed by the next run
     int occ = 1, ctas_per_sm = 1, align_rows = 0;  // work split (batch_layout)
+    int prefetch = 0;                              // 1: split prefetch variant of the kernel
     ~hs_batch() {
         cudaStreamSynchronize(stream);
         if (exec) cudaGraphExecDestroy(exec);
@@ -1565,7 +1605,7 @@ int hs_batch_create(hs_batch **out, hs_lattice *const *members, int n_members) {
         for (int q = 0; q < r; ++q)
             if (members[q] == h) return fail(HS_E_INVALID, "a lattice appears twice in the batch");
     }
-    const int occ = hs::batch_occupancy();
+    const int occ = std::min(hs::batch_occupancy(0), hs::batch_occupancy(1));
     if (occ < 1) return fail(HS_E_CUDA, "batch kernel does not fit on an SM");
     hs_batch *b = new (std::nothrow) hs_batch();
     if (!b) return fail(HS_E_OOM, "host allocation failed");
@@ -1639,7 +1679,7 @@ int hs_batch_run(hs_batch *b, const double *betas, int64_t n_sweeps, int64_t n_e
     if (b->inject_timeout) {  // test hook: launched directly, never captured
         args.inject_skip = 1;
         b->inject_timeout = 0;
-        HS_CUDA(hs::launch_batch(args, b->grid, b->stream));
+        HS_CUDA(hs::launch_batch(args, b->grid, b->stream, b->prefetch));
         for (int r = 0; r < n; ++r) b->members[r]->sweep += (uint64_t)n_total;
         return HS_OK;
     }
@@ -1653,7 +1693,7 @@ int hs_batch_run(hs_batch *b, const double *betas, int64_t n_sweeps, int64_t n_e
         cudaGraph_t graph = nullptr;
         bool ok = cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
         if (ok) {
-            const cudaError_t le = hs::launch_batch(args, b->grid, b->cap_stream);
+            const cudaError_t le = hs::launch_batch(args, b->grid, b->cap_stream, b->prefetch);
             ok = (cudaStreamEndCapture(b->cap_stream, &graph) == cudaSuccess) && le == cudaSuccess;
         }
         if (ok) ok = cudaGraphInstantiate(&b->exec, graph, 0) == cudaSuccess;
@@ -1670,7 +1710,7 @@ int hs_batch_run(hs_batch *b, const double *betas, int64_t n_sweeps, int64_t n_e
     if (b->exec) {
         HS_CUDA(cudaGraphLaunch(b->exec, b->stream));
     } else {
-        HS_CUDA(hs::launch_batch(args, b->grid, b->stream));
+        HS_CUDA(hs::launch_batch(args, b->grid, b->stream, b->prefetch));
     }
     for (int r = 0; r < n; ++r) b->members[r]->sweep += (uint64_t)n_total;
     return HS_OK;
@@ -1726,12 +1766,14 @@ int hs_batch_autotune(hs_batch *b, const double *betas, int n_trial_sweeps) {
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     int st = HS_OK;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) st = fail(HS_E_CUDA, "events");
-    int best_c = b->ctas_per_sm, best_a = b->align_rows;
+    int best_c = b->ctas_per_sm, best_a = b->align_rows, best_pf = b->prefetch;
     float best_ms = 0.f;
     bool have = false;
     if (st == HS_OK && cudaStreamSynchronize(b->stream) != cudaSuccess) st = fail(HS_E_CUDA, "synchronise");
+    for (int pf = 0; st == HS_OK && pf <= 1; ++pf)
     for (int c = 1; st == HS_OK && c <= b->occ; ++c)
         for (int al = 0; st == HS_OK && al <= 1; ++al) {
+            b->prefetch = pf;
             if ((st = batch_layout(b, c, al))) break;
             if ((st = hs_batch_run(b, betas, 1, 0))) break;
             if ((st = hs_batch_run(b, betas, n_trial_sweeps, 0))) break;  // graph capture for this count
@@ -1749,21 +1791,33 @@ int hs_batch_autotune(hs_batch *b, const double *betas, int n_trial_sweeps) {
                 best_ms = ms;
                 best_c = c;
                 best_a = al;
+                best_pf = pf;
             }
             if ((st = restore())) break;
         }
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
+    b->prefetch = best_pf;
     if (st == HS_OK) st = batch_layout(b, best_c, best_a);
     const int st2 = restore();
     release();
     return st ? st : st2;
 }
 
-int hs_batch_get_layout(const hs_batch *b, int *ctas_per_sm, int *align_rows) {
-    if (!b || !ctas_per_sm || !align_rows) return fail(HS_E_INVALID, "null argument");
+int hs_batch_set_layout(hs_batch *b, int ctas_per_sm, int align_rows, int prefetch) {
+    if (!b) return fail(HS_E_INVALID, "null handle");
+    if (ctas_per_sm < 1 || ctas_per_sm > b->occ) return fail(HS_E_INVALID, "ctas_per_sm out of range");
+    if ((align_rows != 0 && align_rows != 1) || (prefetch != 0 && prefetch != 1))
+        return fail(HS_E_INVALID, "align_rows and prefetch must be 0 or 1");
+    b->prefetch = prefetch;
+    return batch_layout(b, ctas_per_sm, align_rows);
+}
+
+int hs_batch_get_layout(const hs_batch *b, int *ctas_per_sm, int *align_rows, int *prefetch) {
+    if (!b || !ctas_per_sm || !align_rows || !prefetch) return fail(HS_E_INVALID, "null argument");
     *ctas_per_sm = b->ctas_per_sm;
     *align_rows = b->align_rows;
+    *prefetch = b->prefetch;
     return HS_OK;
 }
 

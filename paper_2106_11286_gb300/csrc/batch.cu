@@ -137,11 +137,20 @@ __device__ void finalize_sweep(const BatchArgs &b, int s) {
     }
 }
 
+// PF = 2: split prefetch inside a segment, as in the single-lattice stencil:
+// once the current item's local fields are summed, the next item's own row,
+// same-row, z-1 and z+1 rows are loaded and travel during the current item's
+// arithmetic (all L2-only loads).  PF = 0: one item of loads at a time.
+template <int PF>
 __global__ void __launch_bounds__(kBlock, 2) batch_kernel(const BatchArgs b) {
     constexpr int P = HS_FP32;
     constexpr int V = 4;
     using VT = Vec<float, V>;
+    using C = float;
     __shared__ double s_red[kBlock / 32][kPartials];
+    // the current segment's member parameters, read from shared memory where
+    // used rather than held in registers
+    __shared__ PassArgs s_args;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     unsigned long long *cnt = reinterpret_cast<unsigned long long *>(b.bar);
     for (int s = 0; s < b.n_total; ++s) {
@@ -150,7 +159,10 @@ __global__ void __launch_bounds__(kBlock, 2) batch_kernel(const BatchArgs b) {
             for (int si = b.cta_seg[blockIdx.x]; si < b.cta_seg[blockIdx.x + 1]; ++si) {
                 const BatchSeg sg = b.segs[si];
                 const BatchMember &m = b.members[sg.member];
-                const PassArgs a = member_args(m, c, m.sweep0 + (uint32_t)s);
+                // the previous segment's last use of s_args is before its reduction's barriers
+                if (threadIdx.x == 0) s_args = member_args(m, c, m.sweep0 + (uint32_t)s);
+                __syncthreads();
+                const PassArgs &a = s_args;
                 const size_t plane = (size_t)m.Lz * m.Ly * m.Lh;
                 float *own_w[3];
                 const float *own[3], *oth[3];
@@ -163,13 +175,38 @@ __global__ void __launch_bounds__(kBlock, 2) batch_kernel(const BatchArgs b) {
                 float J, K, ex, ey, ez, beta;
                 load_params(a, J, K, ex, ey, ez, beta);
                 SiteAcc<P> acc;
-                for (uint32_t t = sg.begin + threadIdx.x; t < sg.end; t += kBlock) {
-                    StencilItem<P, V> it;
-                    load_item<P, V, true>(a, t, own, oth, it);
-                    if (update_item<P, V, true>(it.s, it.o, it.nym, it.nyp, it.nzm, it.nzp, it.ed, it.p, it.site0, it.rank0, c,
-                                                a, J, K, ex, ey, ez, beta, acc)) {
+                if constexpr (PF == 2) {
+                    uint32_t t = sg.begin + threadIdx.x;
+                    if (t < sg.end) {
+                        SplitItem<P, V> A;
+                        load_split_a<P, V, true>(a, t, own, oth, A);
+                        while (true) {
+                            VT nym[3], nyp[3];
+                            load_split_b<P, V, true>(A, oth, nym, nyp);
+                            C h[3][V];
+                            item_fields<P, V>(A.o, nym, nyp, A.nzm, A.nzp, A.ed, A.f.p, h);
+                            VT sv[3] = {A.s[0], A.s[1], A.s[2]};
+                            const uint32_t b0 = A.f.b0, site0 = A.f.site0, rank0 = A.f.rank0;
+                            const uint32_t tn = t + kBlock;
+                            const bool more = tn < sg.end;
+                            if (more) load_split_a<P, V, true>(a, tn, own, oth, A);  // neighbour vectors are dead
+                            if (update_item_h<P, V, true>(sv, h, site0, rank0, c, a, J, K, ex, ey, ez, beta, acc)) {
 #pragma unroll
-                        for (int q = 0; q < 3; ++q) *reinterpret_cast<VT *>(own_w[q] + it.b0) = it.s[q];
+                                for (int q = 0; q < 3; ++q) *reinterpret_cast<VT *>(own_w[q] + b0) = sv[q];
+                            }
+                            if (!more) break;
+                            t = tn;
+                        }
+                    }
+                } else {
+                    for (uint32_t t = sg.begin + threadIdx.x; t < sg.end; t += kBlock) {
+                        StencilItem<P, V> it;
+                        load_item<P, V, true>(a, t, own, oth, it);
+                        if (update_item<P, V, true>(it.s, it.o, it.nym, it.nyp, it.nzm, it.nzp, it.ed, it.p, it.site0,
+                                                    it.rank0, c, a, J, K, ex, ey, ez, beta, acc)) {
+#pragma unroll
+                            for (int q = 0; q < 3; ++q) *reinterpret_cast<VT *>(own_w[q] + it.b0) = it.s[q];
+                        }
                     }
                 }
                 // segment partials: warp shuffle -> CTA (FP64) -> slot
@@ -212,13 +249,14 @@ __global__ void __launch_bounds__(kBlock, 2) batch_kernel(const BatchArgs b) {
 
 }  // namespace
 
-int batch_occupancy() {
+int batch_occupancy(int prefetch) {
     int blocks = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, batch_kernel, kBlock, 0) != cudaSuccess) return 0;
+    const void *k = prefetch ? (const void *)batch_kernel<2> : (const void *)batch_kernel<0>;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k, kBlock, 0) != cudaSuccess) return 0;
     return blocks;
 }
 
-cudaError_t launch_batch(const BatchArgs &b, int grid, cudaStream_t s) {
+cudaError_t launch_batch(const BatchArgs &b, int grid, cudaStream_t s, int prefetch) {
     cudaLaunchConfig_t cfg{};
     cfg.gridDim = dim3((unsigned)grid);
     cfg.blockDim = dim3(kBlock);
@@ -229,7 +267,7 @@ cudaError_t launch_batch(const BatchArgs &b, int grid, cudaStream_t s) {
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, batch_kernel, b);
+    return prefetch ? cudaLaunchKernelEx(&cfg, batch_kernel<2>, b) : cudaLaunchKernelEx(&cfg, batch_kernel<0>, b);
 }
 
 }  // namespace hs

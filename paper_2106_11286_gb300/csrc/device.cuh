@@ -532,7 +532,7 @@ __device__ void finish_reduction(const PassArgs &a, bool measured) {
     if (threadIdx.x == 0) {
         double o[8];
         sweep_observables(tot, a.n_present, a.e, o);
-        apply_sweep(*a.acc, tot, o, measured, a.accumulate != 0);
+        apply_sweep(*a.acc, tot, o, measured, a.accumulate == 1);
         a.acc->done = 0u;
     }
 }

@@ -98,7 +98,8 @@ struct PassArgs {
     int slot;               // ring slot: the sweep's index within its fold group (0 for single passes)
     int n_blocks;
     int finish;             // 1: last pass of the sequence, the last CTA to arrive reduces and finalises
-    int accumulate;         // 1: add the moments to the accumulator
+    int accumulate;         // 0: no fused measurement; 1: measure and add the moments to the accumulator;
+                            // 2: measure only (the sums; a slab whose moments come from all slabs' sums)
     double n_present;
     DevAccum *acc;
     int inject_extra_tx;    // test hook: extra bytes the first staged fill expects
@@ -201,8 +202,10 @@ cudaError_t launch_wave_finalize(const WaveArgs &w, int grid, cudaStream_t s);
 int wave_occupancy(int precision, int vec);  // resident CTAs per SM (0 = no variant)
 constexpr int kWaveComputeWarps = 15;        // per CTA, plus one control warp
 
-cudaError_t launch_batch(const BatchArgs &b, int grid, cudaStream_t s);
-int batch_occupancy();
+// prefetch 0: one work item of loads at a time; 1: split prefetch (the
+// next item's DRAM-heavy rows load during the current item's arithmetic)
+cudaError_t launch_batch(const BatchArgs &b, int grid, cudaStream_t s, int prefetch);
+int batch_occupancy(int prefetch);
 
 size_t storage_size(int precision);
 

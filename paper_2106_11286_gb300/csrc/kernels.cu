@@ -728,7 +728,7 @@ __global__ void fold_apply_kernel(const PassArgs a, int n_slots) {
     if (threadIdx.x != 0) return;
     AccRegs R;
     R.load(a.acc);
-    const bool acc = a.accumulate != 0;
+    const bool acc = a.accumulate == 1;
     for (int i = 0; i < n_slots; ++i) {
         const double *rec = a.sweep_tot + (size_t)i * kSweepRecord;
         double tot[kPartials], o[8];

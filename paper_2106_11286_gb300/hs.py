@@ -107,12 +107,19 @@ SIGNATURES = {
     "hs_batch_run": (ctypes.c_int, [_vp, _dp, ctypes.c_int64, ctypes.c_int64]),
     "hs_batch_destroy": (None, [_vp]),
     "hs_batch_autotune": (ctypes.c_int, [_vp, _dp, ctypes.c_int]),
-    "hs_batch_get_layout": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+    "hs_batch_get_layout": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                           ctypes.POINTER(ctypes.c_int)]),
+    "hs_batch_set_layout": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     "hs_sweep_sc_fp32_noalloc": (ctypes.c_int, [_vp, _i32p, ctypes.POINTER(hs_params), ctypes.c_double,
                                                  ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int64,
                                                  _vp, _vp]),
     "hs_lattice_inject_timeout": (ctypes.c_int, [_vp, ctypes.c_int]),
     "hs_batch_inject_timeout": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "hs_measure_alu_peak": (ctypes.c_int, [ctypes.c_int, _vp, ctypes.POINTER(ctypes.c_double)]),
+    "hs_slab_pack": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _vp]),
+    "hs_slab_unpack": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _vp]),
+    "hs_read_sums_device": (ctypes.c_int, [_vp, _vp]),
+    "hs_accumulate_sums": (ctypes.c_int, [_vp, _vp, ctypes.c_int64]),
     "hs_last_error": (ctypes.c_char_p, []),
     "hs_api_version": (ctypes.c_int, []),
 }
@@ -221,6 +228,28 @@ def hs_slab_plane(h, colour, component, which):
 
 def hs_slab_copy_plane(dst, dst_which, src, src_which, colour):
     _check(load().hs_slab_copy_plane(dst, int(dst_which), src, int(src_which), int(colour)))
+
+
+def hs_slab_pack(h, colour, which, d_buf):
+    """Copy the three component planes of one boundary / halo plane into the
+    device buffer d_buf (a CUDA tensor or a device address)."""
+    _check(load().hs_slab_pack(h, int(colour), int(which), _dev_ptr(d_buf)))
+
+
+def hs_slab_unpack(h, colour, which, d_buf):
+    _check(load().hs_slab_unpack(h, int(colour), int(which), _dev_ptr(d_buf)))
+
+
+def hs_read_sums_device(h, d_out):
+    _check(load().hs_read_sums_device(h, _dev_ptr(d_out)))
+
+
+def hs_accumulate_sums(h, d_tot, n_sites):
+    _check(load().hs_accumulate_sums(h, _dev_ptr(d_tot), int(n_sites)))
+
+
+def _dev_ptr(x) -> int:
+    return x.data_ptr() if hasattr(x, "data_ptr") else int(x)
 
 
 def hs_get_sites(h, sites) -> np.ndarray:
@@ -387,6 +416,17 @@ def hs_sweep_sc_fp32_noalloc(planes, dims, beta, n_sweeps, d_out, *, J=1.0, K=0.
                                            d_out.data_ptr(), _stream_handle(stream)))
 
 
+ALU_FP64, ALU_FP32, ALU_FP32X2 = 0, 1, 2
+
+
+def hs_measure_alu_peak(kind, stream=None) -> float:
+    """Measured FLOP/s of DFMA (kind 0), FFMA (1) or packed FFMA2 (2) chains on
+    every SM of the current device."""
+    v = ctypes.c_double(0.0)
+    _check(load().hs_measure_alu_peak(int(kind), _stream_handle(stream), ctypes.byref(v)))
+    return v.value
+
+
 def hs_batch_create(members):
     arr = (_vp * len(members))(*[m.value if isinstance(m, _vp) else m for m in members])
     b = _vp()
@@ -408,8 +448,13 @@ def hs_batch_autotune(b, betas, n_trial_sweeps=3):
 def hs_batch_get_layout(b) -> dict:
     c = ctypes.c_int(0)
     a = ctypes.c_int(0)
-    _check(load().hs_batch_get_layout(b, ctypes.byref(c), ctypes.byref(a)))
-    return {"ctas_per_sm": c.value, "align_rows": a.value}
+    pf = ctypes.c_int(0)
+    _check(load().hs_batch_get_layout(b, ctypes.byref(c), ctypes.byref(a), ctypes.byref(pf)))
+    return {"ctas_per_sm": c.value, "align_rows": a.value, "prefetch": pf.value}
+
+
+def hs_batch_set_layout(b, ctas_per_sm, align_rows=0, prefetch=0):
+    _check(load().hs_batch_set_layout(b, int(ctas_per_sm), int(align_rows), int(prefetch)))
 
 
 def hs_batch_destroy(b):

@@ -37,12 +37,17 @@ class Scan:
 
 
 def run_scan(sizes, temps, *, n_equil: int, n_blocks: int, block_sweeps: int, replicas: int = 1, J: float = 1.0,
-             K: float = 0.0, e=(0.0, 0.0, 1.0), precision: str = "fp32", seed: int = 2024, stream=None) -> Scan:
+             K: float = 0.0, e=(0.0, 0.0, 1.0), precision: str = "fp32", seed: int = 2024, stream=None,
+             init: str = "random") -> Scan:
     """Advance every (L, T, replica) sc lattice (L^3, periodic) and collect
     block means.  FP32 lattices advance together in one hs_batch; FP64 and
     FP16 lattices (which the batched kernel does not take) one after the
-    other with hs_sweep, block by block.  Returns a Scan whose sample arrays
-    have n_blocks * replicas entries per (L, T)."""
+    other with hs_sweep, block by block.  init = "random" starts from
+    independent uniform spins, "aligned" from every spin along e (the ordered
+    state, which reaches equilibrium below T_c without coarsening).  Returns a
+    Scan whose sample arrays have n_blocks * replicas entries per (L, T)."""
+    if init not in ("random", "aligned"):
+        raise ValueError("init must be 'random' or 'aligned'")
     sizes, temps = tuple(int(L) for L in sizes), tuple(float(T) for T in temps)
     members, betas, where = [], [], []
     for i, L in enumerate(sizes):
@@ -59,7 +64,7 @@ def run_scan(sizes, temps, *, n_equil: int, n_blocks: int, block_sweeps: int, re
     batch = None
     try:
         for m in members:
-            m.init()
+            m.init(hs.HS_INIT_RANDOM if init == "random" else hs.HS_INIT_ALIGNED)
         if precision == "fp32":
             batch = hs.hs_batch_create([m.h for m in members])
             if n_equil:
@@ -164,6 +169,45 @@ def power_law_exponent(temps, M, Tc: float) -> float:
     m = np.asarray(M, dtype=np.float64)
     below = t < Tc
     return log_slope(Tc - t[below], m[below])
+
+
+def beta_fit(scan: Scan, i_fit: int, temps_idx, tc=None, tc_sizes=None):
+    """The paper's fit of its M(T) curves: beta from <|M|> ~ (T_c - T)^beta,
+    least squares of log <|M|> on log(T_c - T) over the temperatures
+    temps_idx (all below T_c) of size i_fit.  T_c is either given (tc) or
+    taken from the Binder-cumulant crossing of the sizes tc_sizes = (i_small,
+    i_large) within the same estimate, so its error enters beta's.  Returns
+    (beta, error, T_c) with a delete-one jackknife over aligned samples."""
+    temps_idx = list(temps_idx)
+    nT = len(scan.temps)
+    cols = [scan.absM[(i_fit, j)] for j in temps_idx]
+    keys = []
+    if tc is None:
+        if tc_sizes is None:
+            raise ValueError("give tc or tc_sizes")
+        keys = [(i, j) for i in tc_sizes for j in range(nT)]
+        for k in keys:
+            cols += [scan.M2[k], scan.M4[k]]
+    n = min(len(c) for c in cols)
+    cols = [c[:n] for c in cols]
+    t_fit = np.asarray([scan.temps[j] for j in temps_idx])
+    nf = len(temps_idx)
+
+    def t_c(means):
+        if tc is not None:
+            return float(tc)
+        u = [binder(means[nf + 2 * q], means[nf + 2 * q + 1]) for q in range(len(keys))]
+        return crossing(scan.temps, u[:nT], u[nT:])
+
+    def estimate(*means):
+        T_c = t_c(means)
+        if not np.isfinite(T_c) or np.any(t_fit >= T_c):
+            return float("nan")
+        return log_slope(T_c - t_fit, np.asarray(means[:nf]))
+
+    b, err = jackknife(estimate, *cols)
+    T_c, _ = jackknife(lambda *m: t_c(m), *cols)
+    return b, err, T_c
 
 
 def fss_exponent(scan: Scan, j: int, sizes_idx=None):

@@ -110,69 +110,158 @@ class ShardedLattice:
         return combine_sums([s.read_sums() for s in self.slabs], n_sites, self.e)
 
 
-class _DevicePlane:
-    """A device plane as a CUDA array (no copy), for torch.as_tensor."""
-
-    def __init__(self, ptr: int, nbytes: int, dtype):
-        itemsize = np.dtype(dtype).itemsize
-        self.__cuda_array_interface__ = {"shape": (nbytes // itemsize,), "typestr": np.dtype(dtype).str,
-                                         "data": (ptr, False), "version": 3}
-
-
 class DistributedSlab:
     """One slab per process (rank r of a torch.distributed group of W ranks
-    owns planes r nz .. (r+1) nz - 1): halos move by point-to-point sends of
-    the device planes, observables by an allreduce of the five sums."""
+    owns planes r nz .. (r+1) nz - 1).
 
-    _DTYPES = {"fp64": np.float64, "fp32": np.float32, "fp16": np.float16}
+    After each colour pass the slab packs the colour's first and last own
+    planes into one message each (hs_slab_pack: the three component planes
+    back to back), exchanges them with its two neighbours and unpacks what it
+    receives into its halos.  transport "nccl" sends the device buffers with
+    stream-ordered NCCL point-to-point operations, so the host never waits for
+    the GPU; "host" stages them through host memory for a CPU backend (gloo),
+    which synchronises.  "auto" picks "nccl" when the group's backend is NCCL.
+    With accumulation on, every sweep's five fused sums are allreduced and the
+    whole lattice's E and M moments are added to this slab's accumulator on
+    the device (hs_accumulate_sums), so every rank holds the global moments."""
+
+    _DTYPES = {"fp64": "float64", "fp32": "float32", "fp16": "float16"}
 
     def __init__(self, dims, *, J=1.0, K=0.0, e=(0.0, 0.0, 1.0), precision="fp32", seed=0, replica=0,
-                 stream=None):
+                 stream=None, transport="auto"):
+        import torch
         import torch.distributed as dist
-        self.dist = dist
+        self.torch, self.dist = torch, dist
         self.rank, self.world = dist.get_rank(), dist.get_world_size()
         Lx, Ly, Lz = (int(d) for d in dims)
         if Lz % self.world:
             raise ValueError("the rank count must divide Lz")
+        if transport == "auto":
+            transport = "nccl" if dist.get_backend() == "nccl" else "host"
+        if transport not in ("nccl", "host"):
+            raise ValueError("transport must be 'auto', 'nccl' or 'host'")
+        self.transport = transport
         self.dims, self.e = (Lx, Ly, Lz), e
+        self.n_sites = Lx * Ly * Lz
         self.nz = Lz // self.world
-        self.dtype = self._DTYPES[precision]
+        self.stream = stream
         self.slab = hs.Slab(self.dims, self.rank * self.nz, self.nz, J=J, K=K, e=e, precision=precision, seed=seed,
                             replica=replica, stream=stream)
-        self.stream = stream
+        self.slab.accumulate(False)   # global moments come from the allreduced sums
+        self.accumulating = False
+        dtype = getattr(torch, self._DTYPES[precision])
+        _, plane_bytes = hs.hs_slab_plane(self.slab.h, 0, 0, hs.FIRST_OWN)
+        n = 3 * plane_bytes // torch.empty(0, dtype=dtype).element_size()
+        dev = torch.device("cuda", torch.cuda.current_device())
+        self.buf = {k: torch.empty(n, dtype=dtype, device=dev) for k in ("send_lo", "send_hi", "recv_lo", "recv_hi")}
+        self.sums = torch.zeros(5, dtype=torch.float64, device=dev)
+        if transport == "host":
+            self.hbuf = {k: torch.empty(n, dtype=dtype).pin_memory() for k in self.buf}
+            self.hsums = torch.zeros(5, dtype=torch.float64)
 
-    def _plane(self, colour, component, which):
-        import torch
-        ptr, nbytes = hs.hs_slab_plane(self.slab.h, colour, component, which)
-        return torch.as_tensor(_DevicePlane(ptr, nbytes, self.dtype), device="cuda")
+    def _stream_ctx(self):
+        return self.torch.cuda.stream(self.stream) if self.stream is not None else _nullcontext()
+
+    def init(self, mode=hs.HS_INIT_RANDOM):
+        self.slab.init(mode)
+        self.exchange(0)
+        self.exchange(1)
+
+    def set_spins(self, S_own):
+        """This rank's own planes (Lx Ly nz spins in natural order)."""
+        self.slab.set_spins(S_own)
+        self.exchange(0)
+        self.exchange(1)
+
+    def get_spins(self):
+        return self.slab.get_spins()
+
+    def set_sweep_counter(self, n):
+        self.slab.set_sweep_counter(n)
+
+    def accumulate(self, on=True):
+        self.accumulating = bool(on)
+
+    def reset_accumulator(self):
+        self.slab.reset_accumulator()
+
+    def read_accumulator(self):
+        """The whole lattice's moments (hs_moment order) and sweep count."""
+        return self.slab.read_accumulator()
 
     def exchange(self, colour: int):
-        import torch
+        with self._stream_ctx():
+            self._exchange(colour)
+
+    def _exchange(self, colour: int):
+        h = self.slab.h
         if self.world == 1:  # the slab is its own periodic neighbour
             for _, src_which, _, dst_which in halo_plan(1):
-                hs.hs_slab_copy_plane(self.slab.h, dst_which, self.slab.h, src_which, colour)
+                hs.hs_slab_copy_plane(h, dst_which, h, src_which, colour)
             return
-        torch.cuda.synchronize()  # the pass has written the planes the sends read
-        reqs = []
-        for src, src_which, dst, dst_which in halo_plan(self.world):
-            for q in range(3):
-                if src == self.rank:
-                    reqs.append(self.dist.isend(self._plane(colour, q, src_which), dst))
-                if dst == self.rank:
-                    reqs.append(self.dist.irecv(self._plane(colour, q, dst_which), src))
-        for r in reqs:
-            r.wait()
-        torch.cuda.synchronize()
+        lo, hi = (self.rank - 1) % self.world, (self.rank + 1) % self.world
+        b = self.buf
+        hs.hs_slab_pack(h, colour, hs.FIRST_OWN, b["send_lo"])   # -> the halo above of the slab below
+        hs.hs_slab_pack(h, colour, hs.LAST_OWN, b["send_hi"])    # -> the halo below of the slab above
+        # posting order: sends (to lo, to hi), receives (from hi, from lo); with two ranks lo == hi, and
+        # the peer's first message (its first own plane) is the one for this rank's halo above
+        if self.transport == "nccl":
+            with self._stream_ctx():
+                ops = [self.dist.P2POp(self.dist.isend, b["send_lo"], lo),
+                       self.dist.P2POp(self.dist.isend, b["send_hi"], hi),
+                       self.dist.P2POp(self.dist.irecv, b["recv_hi"], hi),
+                       self.dist.P2POp(self.dist.irecv, b["recv_lo"], lo)]
+                for r in self.dist.batch_isend_irecv(ops):
+                    r.wait()   # the current stream waits on the transfers; the host does not
+        else:
+            hb = self.hbuf
+            for k in ("send_lo", "send_hi"):
+                hb[k].copy_(b[k])
+            reqs = [self.dist.isend(hb["send_lo"], lo, tag=0), self.dist.isend(hb["send_hi"], hi, tag=1),
+                    self.dist.irecv(hb["recv_hi"], hi, tag=0), self.dist.irecv(hb["recv_lo"], lo, tag=1)]
+            for r in reqs:
+                r.wait()
+            for k in ("recv_hi", "recv_lo"):
+                b[k].copy_(hb[k])
+        hs.hs_slab_unpack(h, colour, hs.HALO_ABOVE, b["recv_hi"])
+        hs.hs_slab_unpack(h, colour, hs.HALO_BELOW, b["recv_lo"])
+
+    def _accumulate_sweep(self):
+        h = self.slab.h
+        hs.hs_read_sums_device(h, self.sums)
+        if self.transport == "nccl":
+            with self._stream_ctx():
+                self.dist.all_reduce(self.sums)
+        else:
+            self.hsums.copy_(self.sums)
+            self.dist.all_reduce(self.hsums)
+            self.sums.copy_(self.hsums)
+        hs.hs_accumulate_sums(h, self.sums, self.n_sites)
 
     def sweep(self, beta, n=1):
-        for _ in range(n):
-            for c in (0, 1):
-                self.slab.sweep_pass(beta, c)
-                self.exchange(c)
+        with self._stream_ctx():
+            for _ in range(n):
+                for c in (0, 1):
+                    self.slab.sweep_pass(beta, c)
+                    self._exchange(c)
+                if self.accumulating:
+                    self._accumulate_sweep()
 
     def last_observables(self) -> dict:
-        import torch
-        sums = torch.as_tensor(self.slab.read_sums(), dtype=torch.float64, device="cuda")
+        """E, M, |M|, ... of the last sweep of the whole lattice (host)."""
+        sums = self.torch.as_tensor(self.slab.read_sums(), dtype=self.torch.float64)
+        if self.transport == "nccl":
+            sums = sums.cuda()
         self.dist.all_reduce(sums)
-        n_sites = self.dims[0] * self.dims[1] * self.dims[2]
-        return combine_sums([sums.cpu().numpy()], n_sites, self.e)
+        return combine_sums([sums.cpu().numpy()], self.n_sites, self.e)
+
+    def close(self):
+        self.slab.close()
+
+
+class _nullcontext:
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        return False

@@ -75,7 +75,7 @@ def test_batch_autotune_keeps_the_chains():
     ba = hs.hs_batch_create([m.h for m in a])
     bb = hs.hs_batch_create([m.h for m in b])
     try:
-        assert hs.hs_batch_get_layout(bb) == {"ctas_per_sm": 2, "align_rows": 0}
+        assert hs.hs_batch_get_layout(bb) == {"ctas_per_sm": 2, "align_rows": 0, "prefetch": 0}
         hs.hs_batch_run(ba, betas, 2, 1)
         hs.hs_batch_run(bb, betas, 2, 1)
         before = [m.get_spins() for m in a]
@@ -92,6 +92,42 @@ def test_batch_autotune_keeps_the_chains():
             my, cy = y.read_accumulator()
             assert cx == cy == 6
             np.testing.assert_allclose(mx, my, rtol=2e-6, atol=1e-9)
+    finally:
+        hs.hs_batch_destroy(ba)
+        hs.hs_batch_destroy(bb)
+        for m in a + b:
+            m.close()
+
+
+@pytest.mark.parametrize("ctas,align,prefetch", [(1, 0, 1), (2, 1, 1), (2, 0, 1), (1, 1, 0)])
+def test_batch_layouts_give_identical_chains(ctas, align, prefetch):
+    """Every work split and load schedule (split prefetch included) gives the
+    spins of the default layout bit for bit, and the same moments up to the
+    order of the FP64 segment sums."""
+    dims = [(16, 16, 16), (24, 24, 24), (8, 8, 8), (32, 16, 8), (48, 48, 48), (96, 96, 96)]
+    betas = [0.6, 0.8, 1.0, 1.2, 0.9, 0.7]
+    a = _members(dims, betas)
+    b = _members(dims, betas)
+    for m in a + b:
+        m.init()
+        m.accumulate(True)
+    ba = hs.hs_batch_create([m.h for m in a])
+    bb = hs.hs_batch_create([m.h for m in b])
+    try:
+        hs.hs_batch_set_layout(bb, ctas, align, prefetch)
+        assert hs.hs_batch_get_layout(bb) == {"ctas_per_sm": ctas, "align_rows": align, "prefetch": prefetch}
+        hs.hs_batch_run(ba, betas, 3, 2)
+        hs.hs_batch_run(bb, betas, 3, 2)
+        for x, y in zip(a, b):
+            assert np.array_equal(x.get_spins(), y.get_spins())
+            mx, cx = x.read_accumulator()
+            my, cy = y.read_accumulator()
+            assert cx == cy == 3
+            np.testing.assert_allclose(mx, my, rtol=2e-6, atol=1e-9)
+        with pytest.raises(hs.HSError):
+            hs.hs_batch_set_layout(bb, 0, 0, 0)
+        with pytest.raises(hs.HSError):
+            hs.hs_batch_set_layout(bb, 1, 0, 2)
     finally:
         hs.hs_batch_destroy(ba)
         hs.hs_batch_destroy(bb)

@@ -30,6 +30,7 @@ def _whole_and_sharded(dims, n_slabs, precision, seed=5, sweeps=3, beta=0.9, sta
     with hs.Lattice("sc", dims=dims, precision=precision, seed=seed, **PARAMS) as whole:
         whole.set_spins(S0)
         whole.set_sweep_counter(start)
+        whole.accumulate(True)   # the fused sums (a slab always measures them)
         whole.sweep(beta, sweeps)
         want, want_sums = whole.get_spins(), hs.hs_read_sums(whole.h)
     with shards.ShardedLattice(dims, n_slabs, precision=precision, seed=seed, **PARAMS) as sh:
@@ -47,6 +48,7 @@ def test_slabs_reproduce_the_whole_lattice(precision, n_slabs):
     S0, want, want_sums, got, obs = _whole_and_sharded(dims, n_slabs, precision)
     assert not np.array_equal(want, S0)
     assert np.array_equal(got, want)
+    assert want_sums[0] != 0.0
     n = dims[0] * dims[1] * dims[2]
     # FP64 sums in another grouping; FP32 / FP16 per-thread partials also group differently
     rel, atol = (1e-12, 1e-9) if precision == "fp64" else (2e-6, 1e-4)
@@ -108,8 +110,10 @@ def test_one_rank_distributed_slab():
     S0 = storage_round(inputs.random_unit_spins(n, 4), "fp32")
     with hs.Lattice("sc", dims=dims, precision="fp32", seed=8, **PARAMS) as whole:
         whole.set_spins(S0)
+        whole.accumulate(True)   # the fused sums (a slab always measures them)
         whole.sweep(1.0, 2)
         want, want_sums = whole.get_spins(), hs.hs_read_sums(whole.h)
+    assert want_sums[0] != 0.0
     dist.init_process_group("nccl", init_method=f"tcp://127.0.0.1:{port}", rank=0, world_size=1)
     try:
         ds = shards.DistributedSlab(dims, precision="fp32", seed=8, **PARAMS)

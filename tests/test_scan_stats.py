@@ -71,3 +71,32 @@ def test_binder_crossing_of_synthetic_curves():
     tc, err = scan.binder_crossing(sc, 0, 1)
     assert tc == pytest.approx(1.445, abs=1e-9)
     assert 0 < err < 1e-3
+
+
+def test_beta_fit_recovers_a_planted_exponent():
+    """beta_fit on synthetic block means of <|M|> = B (T_c - T)^beta with a
+    planted beta and T_c, noise-free and with noise; the T_c of the crossing
+    branch comes from planted Binder cumulants that cross at T_c."""
+    import numpy as np
+
+    from paper_2106_11286_gb300 import scan
+    rng = np.random.default_rng(5)
+    temps = (1.0, 1.1, 1.2, 1.3, 1.4, 1.45, 1.5, 1.55)
+    tc, beta = 1.47, 0.36
+    s = scan.Scan((8, 16), temps, 1, 100)
+    for i, L in enumerate((8, 16)):
+        for j, T in enumerate(temps):
+            m = 0.9 * max(tc - T, 1e-3) ** beta
+            s.absM[(i, j)] = m * (1 + 1e-4 * rng.standard_normal(12))
+            # U4 = 1 - m4 / (3 m2^2), linear in T with a slope growing with L, so
+            # the two sizes cross exactly at tc (linear interpolation is exact)
+            u = 0.6 + 0.01 * L * (tc - T)
+            m2 = np.full(12, 0.5)
+            s.M2[(i, j)] = m2
+            s.M4[(i, j)] = 3 * (1 - u) * m2 ** 2
+    fit = [j for j, T in enumerate(temps) if T <= 1.4]
+    b, err, t = scan.beta_fit(s, 1, fit, tc=tc)
+    assert b == pytest.approx(beta, abs=5e-4) and err < 1e-3
+    b2, err2, t2 = scan.beta_fit(s, 1, fit, tc_sizes=(0, 1))
+    assert t2 == pytest.approx(tc, abs=1e-12)
+    assert b2 == pytest.approx(beta, abs=5e-4)
