@@ -151,6 +151,8 @@ __global__ void __launch_bounds__(kBlock, 2) batch_kernel(const BatchArgs b) {
     // the current segment's member parameters, read from shared memory where
     // used rather than held in registers
     __shared__ PassArgs s_args;
+    // and its plane pointers (own colour x, y, z, then the other colour's)
+    __shared__ float *s_planes[6];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     unsigned long long *cnt = reinterpret_cast<unsigned long long *>(b.bar);
     for (int s = 0; s < b.n_total; ++s) {
@@ -160,18 +162,20 @@ __global__ void __launch_bounds__(kBlock, 2) batch_kernel(const BatchArgs b) {
                 const BatchSeg sg = b.segs[si];
                 const BatchMember &m = b.members[sg.member];
                 // the previous segment's last use of s_args is before its reduction's barriers
-                if (threadIdx.x == 0) s_args = member_args(m, c, m.sweep0 + (uint32_t)s);
+                if (threadIdx.x == 0) {
+                    s_args = member_args(m, c, m.sweep0 + (uint32_t)s);
+                    const size_t plane = (size_t)m.Lz * m.Ly * m.Lh;
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) {
+                        s_planes[q] = m.planes + (size_t)(3 * c + q) * plane;
+                        s_planes[3 + q] = m.planes + (size_t)(3 * (1 - c) + q) * plane;
+                    }
+                }
                 __syncthreads();
                 const PassArgs &a = s_args;
-                const size_t plane = (size_t)m.Lz * m.Ly * m.Lh;
-                float *own_w[3];
-                const float *own[3], *oth[3];
-#pragma unroll
-                for (int q = 0; q < 3; ++q) {
-                    own_w[q] = m.planes + (size_t)(3 * c + q) * plane;
-                    own[q] = own_w[q];
-                    oth[q] = m.planes + (size_t)(3 * (1 - c) + q) * plane;
-                }
+                float *const(&own_w)[3] = *reinterpret_cast<float *const(*)[3]>(&s_planes[0]);
+                const float *const(&own)[3] = *reinterpret_cast<const float *const(*)[3]>(&s_planes[0]);
+                const float *const(&oth)[3] = *reinterpret_cast<const float *const(*)[3]>(&s_planes[3]);
                 float J, K, ex, ey, ez, beta;
                 load_params(a, J, K, ex, ey, ez, beta);
                 SiteAcc<P> acc;
