@@ -329,22 +329,27 @@ void hs_batch_destroy(hs_batch *b);
  * sites of one row of one colour), concatenated and cut into one contiguous
  * range per CTA -- is timed for every CTA count per SM (1 up to the kernel's
  * occupancy), both cut rules (at any item, or moved to the nearest row
- * boundary) and both load schedules of the kernel (one work item of loads
- * at a time, or split prefetch: the next item's own, same-row and z+-1 rows
- * load during the current item's arithmetic), for n_trial_sweeps sweeps at
- * the given betas after one warm-up sweep; the fastest is kept.  Every
- * member's spins, sweep counter and accumulator are restored, so the members'
- * chains are as if the call had not happened (spins are identical under
- * every split and schedule; the FP64 sums are taken in each split's own fixed
- * order).  Synchronous.  hs_batch_get_layout reads the split and schedule in
- * use (hs_batch_create starts with the maximum CTAs per SM, cuts at any item
- * and no prefetch). */
+ * boundary), both load schedules of the kernel (one work item of loads at a
+ * time, or split prefetch: the next item's own, same-row and z+-1 rows load
+ * during the current item's arithmetic) and both colour schedules (schedule
+ * 0: every sweep in one persistent cooperative launch, passes separated by
+ * the bounded grid barrier, captured in a CUDA graph; schedule 1: one launch
+ * per colour pass of every member, consecutive launches chained by
+ * programmatic dependent launch), for n_trial_sweeps sweeps at the given
+ * betas after one warm-up sweep; the fastest is kept.  Colour 0 then colour
+ * 1 in every sweep under all of them.  Every member's spins, sweep counter
+ * and accumulator are restored, so the members' chains are as if the call
+ * had not happened (spins are identical under every choice; the FP64 sums
+ * are taken in each split's own fixed order).  Synchronous.
+ * hs_batch_get_layout reads the choice in use (hs_batch_create starts with
+ * the maximum CTAs per SM, cuts at any item, no prefetch, schedule 0). */
 int hs_batch_autotune(hs_batch *b, const double *betas, int n_trial_sweeps);
-int hs_batch_get_layout(const hs_batch *b, int *ctas_per_sm, int *align_rows, int *prefetch);
-/* Set the split and schedule by hand: ctas_per_sm in 1 .. the kernel's
- * occupancy, align_rows and prefetch 0 or 1 (HS_E_INVALID otherwise).  The
- * members' chains do not depend on it.  Synchronises the batch's stream. */
-int hs_batch_set_layout(hs_batch *b, int ctas_per_sm, int align_rows, int prefetch);
+int hs_batch_get_layout(const hs_batch *b, int *ctas_per_sm, int *align_rows, int *prefetch, int *schedule);
+/* Set the choice by hand: ctas_per_sm in 1 .. the kernel's occupancy,
+ * align_rows, prefetch and schedule 0 or 1 (HS_E_INVALID otherwise).  The
+ * members' chains do not depend on it.  The timeout test hook always runs
+ * the persistent schedule.  Synchronises the batch's stream. */
+int hs_batch_set_layout(hs_batch *b, int ctas_per_sm, int align_rows, int prefetch, int schedule);
 
 /* Allocation-free sweep (the paper has no counterpart; it is a service to
  * callers that cannot allocate device memory themselves: a host framework

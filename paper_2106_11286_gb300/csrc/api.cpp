@@ -1483,6 +1483,7 @@ struct hs_batch {
     int inject_timeout = 0;  // test hook, consumed by the next run
     int occ = 1, ctas_per_sm = 1, align_rows = 0;  // work split (batch_layout)
     int prefetch = 0;                              // 1: split prefetch variant of the kernel
+    int schedule = 0;                              // 0: one persistent launch, 1: a launch per colour pass
     ~hs_batch() {
         cudaStreamSynchronize(stream);
         if (exec) cudaGraphExecDestroy(exec);
@@ -1676,6 +1677,11 @@ int hs_batch_run(hs_batch *b, const double *betas, int64_t n_sweeps, int64_t n_e
     HS_CUDA(cudaMemsetAsync(b->d_bar, 0, 2 * sizeof(unsigned int), b->stream));
     HS_CUDA(cudaMemsetAsync(b->d_error, 0, sizeof(int), b->stream));
     hs::BatchArgs args = batch_args(b, n_total, n_eq);
+    if (b->schedule == 1 && !b->inject_timeout) {  // chained launches on the stream, no graph
+        HS_CUDA(hs::launch_batch_passes(args, b->grid, b->stream, b->prefetch));
+        for (int r = 0; r < n; ++r) b->members[r]->sweep += (uint64_t)n_total;
+        return HS_OK;
+    }
     if (b->inject_timeout) {  // test hook: launched directly, never captured
         args.inject_skip = 1;
         b->inject_timeout = 0;
@@ -1766,14 +1772,16 @@ int hs_batch_autotune(hs_batch *b, const double *betas, int n_trial_sweeps) {
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     int st = HS_OK;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) st = fail(HS_E_CUDA, "events");
-    int best_c = b->ctas_per_sm, best_a = b->align_rows, best_pf = b->prefetch;
+    int best_c = b->ctas_per_sm, best_a = b->align_rows, best_pf = b->prefetch, best_sc = b->schedule;
     float best_ms = 0.f;
     bool have = false;
     if (st == HS_OK && cudaStreamSynchronize(b->stream) != cudaSuccess) st = fail(HS_E_CUDA, "synchronise");
+    for (int sc = 0; st == HS_OK && sc <= 1; ++sc)
     for (int pf = 0; st == HS_OK && pf <= 1; ++pf)
     for (int c = 1; st == HS_OK && c <= b->occ; ++c)
         for (int al = 0; st == HS_OK && al <= 1; ++al) {
             b->prefetch = pf;
+            b->schedule = sc;
             if ((st = batch_layout(b, c, al))) break;
             if ((st = hs_batch_run(b, betas, 1, 0))) break;
             if ((st = hs_batch_run(b, betas, n_trial_sweeps, 0))) break;  // graph capture for this count
@@ -1792,32 +1800,36 @@ int hs_batch_autotune(hs_batch *b, const double *betas, int n_trial_sweeps) {
                 best_c = c;
                 best_a = al;
                 best_pf = pf;
+                best_sc = sc;
             }
             if ((st = restore())) break;
         }
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     b->prefetch = best_pf;
+    b->schedule = best_sc;
     if (st == HS_OK) st = batch_layout(b, best_c, best_a);
     const int st2 = restore();
     release();
     return st ? st : st2;
 }
 
-int hs_batch_set_layout(hs_batch *b, int ctas_per_sm, int align_rows, int prefetch) {
+int hs_batch_set_layout(hs_batch *b, int ctas_per_sm, int align_rows, int prefetch, int schedule) {
     if (!b) return fail(HS_E_INVALID, "null handle");
     if (ctas_per_sm < 1 || ctas_per_sm > b->occ) return fail(HS_E_INVALID, "ctas_per_sm out of range");
-    if ((align_rows != 0 && align_rows != 1) || (prefetch != 0 && prefetch != 1))
-        return fail(HS_E_INVALID, "align_rows and prefetch must be 0 or 1");
+    if ((align_rows != 0 && align_rows != 1) || (prefetch != 0 && prefetch != 1) || (schedule != 0 && schedule != 1))
+        return fail(HS_E_INVALID, "align_rows, prefetch and schedule must be 0 or 1");
     b->prefetch = prefetch;
+    b->schedule = schedule;
     return batch_layout(b, ctas_per_sm, align_rows);
 }
 
-int hs_batch_get_layout(const hs_batch *b, int *ctas_per_sm, int *align_rows, int *prefetch) {
-    if (!b || !ctas_per_sm || !align_rows || !prefetch) return fail(HS_E_INVALID, "null argument");
+int hs_batch_get_layout(const hs_batch *b, int *ctas_per_sm, int *align_rows, int *prefetch, int *schedule) {
+    if (!b || !ctas_per_sm || !align_rows || !prefetch || !schedule) return fail(HS_E_INVALID, "null argument");
     *ctas_per_sm = b->ctas_per_sm;
     *align_rows = b->align_rows;
     *prefetch = b->prefetch;
+    *schedule = b->schedule;
     return HS_OK;
 }
 

@@ -137,103 +137,115 @@ __device__ void finalize_sweep(const BatchArgs &b, int s) {
     }
 }
 
-// PF = 2: split prefetch inside a segment, as in the single-lattice stencil:
-// once the current item's local fields are summed, the next item's own row,
-// same-row, z-1 and z+1 rows are loaded and travel during the current item's
-// arithmetic (all L2-only loads).  PF = 0: one item of loads at a time.
-template <int PF>
-__global__ void __launch_bounds__(kBlock, 2) batch_kernel(const BatchArgs b) {
+// One colour pass c of batch sweep s over this CTA's segments: every item of
+// each segment (Metropolis steps (i)-(iii) of one member), then the
+// segment's partial sums -> its FP64 slot.  CG: L2-only loads, for the
+// persistent kernel, which reads data other CTAs wrote earlier in the same
+// launch; a launch per pass loads through L1 (kernel boundaries keep it
+// coherent).  PF = 2: split prefetch inside a segment, as in the
+// single-lattice stencil: once the current item's local fields are summed,
+// the next item's own row, same-row, z-1 and z+1 rows are loaded and travel
+// during the current item's arithmetic.  PF = 0: one item of loads at a time.
+template <int PF, bool CG>
+__device__ __forceinline__ void batch_pass(const BatchArgs &b, int s, int c) {
     constexpr int P = HS_FP32;
     constexpr int V = 4;
     using VT = Vec<float, V>;
     using C = float;
     __shared__ double s_red[kBlock / 32][kPartials];
-    // the current segment's member parameters, read from shared memory where
-    // used rather than held in registers
+    // the current segment's member parameters and plane pointers (own colour
+    // x, y, z, then the other colour's), read from shared memory where used
+    // rather than held in registers
     __shared__ PassArgs s_args;
-    // and its plane pointers (own colour x, y, z, then the other colour's)
     __shared__ float *s_planes[6];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int par = s & 1;  // slot parity this sweep writes
+    for (int si = b.cta_seg[blockIdx.x]; si < b.cta_seg[blockIdx.x + 1]; ++si) {
+        const BatchSeg sg = b.segs[si];
+        const BatchMember &m = b.members[sg.member];
+        // the previous segment's last use of s_args is before its reduction's barriers
+        if (threadIdx.x == 0) {
+            s_args = member_args(m, c, m.sweep0 + (uint32_t)s);
+            const size_t plane = (size_t)m.Lz * m.Ly * m.Lh;
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                s_planes[q] = m.planes + (size_t)(3 * c + q) * plane;
+                s_planes[3 + q] = m.planes + (size_t)(3 * (1 - c) + q) * plane;
+            }
+        }
+        __syncthreads();
+        const PassArgs &a = s_args;
+        float *const(&own_w)[3] = *reinterpret_cast<float *const(*)[3]>(&s_planes[0]);
+        const float *const(&own)[3] = *reinterpret_cast<const float *const(*)[3]>(&s_planes[0]);
+        const float *const(&oth)[3] = *reinterpret_cast<const float *const(*)[3]>(&s_planes[3]);
+        float J, K, ex, ey, ez, beta;
+        load_params(a, J, K, ex, ey, ez, beta);
+        SiteAcc<P> acc;
+        if constexpr (PF == 2) {
+            uint32_t t = sg.begin + threadIdx.x;
+            if (t < sg.end) {
+                SplitItem<P, V> A;
+                load_split_a<P, V, CG>(a, t, own, oth, A);
+                while (true) {
+                    VT nym[3], nyp[3];
+                    load_split_b<P, V, CG>(A, oth, nym, nyp);
+                    C h[3][V];
+                    item_fields<P, V>(A.o, nym, nyp, A.nzm, A.nzp, A.ed, A.f.p, h);
+                    VT sv[3] = {A.s[0], A.s[1], A.s[2]};
+                    const uint32_t b0 = A.f.b0, site0 = A.f.site0, rank0 = A.f.rank0;
+                    const uint32_t tn = t + kBlock;
+                    const bool more = tn < sg.end;
+                    if (more) load_split_a<P, V, CG>(a, tn, own, oth, A);  // the neighbour vectors are dead
+                    if (update_item_h<P, V, true>(sv, h, site0, rank0, c, a, J, K, ex, ey, ez, beta, acc)) {
+#pragma unroll
+                        for (int q = 0; q < 3; ++q) *reinterpret_cast<VT *>(own_w[q] + b0) = sv[q];
+                    }
+                    if (!more) break;
+                    t = tn;
+                }
+            }
+        } else {
+            for (uint32_t t = sg.begin + threadIdx.x; t < sg.end; t += kBlock) {
+                StencilItem<P, V> it;
+                load_item<P, V, CG>(a, t, own, oth, it);
+                if (update_item<P, V, true>(it.s, it.o, it.nym, it.nyp, it.nzm, it.nzp, it.ed, it.p, it.site0,
+                                            it.rank0, c, a, J, K, ex, ey, ez, beta, acc)) {
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) *reinterpret_cast<VT *>(own_w[q] + it.b0) = it.s[q];
+                }
+            }
+        }
+        // segment partials: warp shuffle -> CTA (FP64) -> slot
+        const float accE = warp_sum(acc.E());
+        const float accX = warp_sum(acc.X());
+        const float accY = warp_sum(acc.Y());
+        const float accZ = warp_sum(acc.Z());
+        const unsigned nacc = __reduce_add_sync(0xffffffffu, acc.n);
+        if (lane == 0) {
+            s_red[warp][0] = accE;
+            s_red[warp][1] = accX;
+            s_red[warp][2] = accY;
+            s_red[warp][3] = accZ;
+            s_red[warp][4] = (double)nacc;
+        }
+        __syncthreads();
+        if (threadIdx.x < kPartials) {
+            double t = 0.0;
+            for (int w = 0; w < kBlock / 32; ++w) t += s_red[w][threadIdx.x];
+            b.slots[(((size_t)par * 2 + c) * b.n_segs + si) * kPartials + threadIdx.x] = t;
+        }
+        __syncthreads();
+    }
+}
+
+// The persistent schedule: every sweep and colour pass in one cooperative
+// launch, passes separated by the bounded grid barrier.
+template <int PF>
+__global__ void __launch_bounds__(kBlock, 2) batch_kernel(const BatchArgs b) {
     unsigned long long *cnt = reinterpret_cast<unsigned long long *>(b.bar);
     for (int s = 0; s < b.n_total; ++s) {
-        const int par = s & 1;  // slot parity this sweep writes
         for (int c = 0; c < 2; ++c) {
-            for (int si = b.cta_seg[blockIdx.x]; si < b.cta_seg[blockIdx.x + 1]; ++si) {
-                const BatchSeg sg = b.segs[si];
-                const BatchMember &m = b.members[sg.member];
-                // the previous segment's last use of s_args is before its reduction's barriers
-                if (threadIdx.x == 0) {
-                    s_args = member_args(m, c, m.sweep0 + (uint32_t)s);
-                    const size_t plane = (size_t)m.Lz * m.Ly * m.Lh;
-#pragma unroll
-                    for (int q = 0; q < 3; ++q) {
-                        s_planes[q] = m.planes + (size_t)(3 * c + q) * plane;
-                        s_planes[3 + q] = m.planes + (size_t)(3 * (1 - c) + q) * plane;
-                    }
-                }
-                __syncthreads();
-                const PassArgs &a = s_args;
-                float *const(&own_w)[3] = *reinterpret_cast<float *const(*)[3]>(&s_planes[0]);
-                const float *const(&own)[3] = *reinterpret_cast<const float *const(*)[3]>(&s_planes[0]);
-                const float *const(&oth)[3] = *reinterpret_cast<const float *const(*)[3]>(&s_planes[3]);
-                float J, K, ex, ey, ez, beta;
-                load_params(a, J, K, ex, ey, ez, beta);
-                SiteAcc<P> acc;
-                if constexpr (PF == 2) {
-                    uint32_t t = sg.begin + threadIdx.x;
-                    if (t < sg.end) {
-                        SplitItem<P, V> A;
-                        load_split_a<P, V, true>(a, t, own, oth, A);
-                        while (true) {
-                            VT nym[3], nyp[3];
-                            load_split_b<P, V, true>(A, oth, nym, nyp);
-                            C h[3][V];
-                            item_fields<P, V>(A.o, nym, nyp, A.nzm, A.nzp, A.ed, A.f.p, h);
-                            VT sv[3] = {A.s[0], A.s[1], A.s[2]};
-                            const uint32_t b0 = A.f.b0, site0 = A.f.site0, rank0 = A.f.rank0;
-                            const uint32_t tn = t + kBlock;
-                            const bool more = tn < sg.end;
-                            if (more) load_split_a<P, V, true>(a, tn, own, oth, A);  // neighbour vectors are dead
-                            if (update_item_h<P, V, true>(sv, h, site0, rank0, c, a, J, K, ex, ey, ez, beta, acc)) {
-#pragma unroll
-                                for (int q = 0; q < 3; ++q) *reinterpret_cast<VT *>(own_w[q] + b0) = sv[q];
-                            }
-                            if (!more) break;
-                            t = tn;
-                        }
-                    }
-                } else {
-                    for (uint32_t t = sg.begin + threadIdx.x; t < sg.end; t += kBlock) {
-                        StencilItem<P, V> it;
-                        load_item<P, V, true>(a, t, own, oth, it);
-                        if (update_item<P, V, true>(it.s, it.o, it.nym, it.nyp, it.nzm, it.nzp, it.ed, it.p, it.site0,
-                                                    it.rank0, c, a, J, K, ex, ey, ez, beta, acc)) {
-#pragma unroll
-                            for (int q = 0; q < 3; ++q) *reinterpret_cast<VT *>(own_w[q] + it.b0) = it.s[q];
-                        }
-                    }
-                }
-                // segment partials: warp shuffle -> CTA (FP64) -> slot
-                const float accE = warp_sum(acc.E());
-                const float accX = warp_sum(acc.X());
-                const float accY = warp_sum(acc.Y());
-                const float accZ = warp_sum(acc.Z());
-                const unsigned nacc = __reduce_add_sync(0xffffffffu, acc.n);
-                if (lane == 0) {
-                    s_red[warp][0] = accE;
-                    s_red[warp][1] = accX;
-                    s_red[warp][2] = accY;
-                    s_red[warp][3] = accZ;
-                    s_red[warp][4] = (double)nacc;
-                }
-                __syncthreads();
-                if (threadIdx.x < kPartials) {
-                    double t = 0.0;
-                    for (int w = 0; w < kBlock / 32; ++w) t += s_red[w][threadIdx.x];
-                    b.slots[(((size_t)par * 2 + c) * b.n_segs + si) * kPartials + threadIdx.x] = t;
-                }
-                __syncthreads();
-            }
+            batch_pass<PF, true>(b, s, c);
             const bool skip = b.inject_skip && blockIdx.x == 0 && s == 0 && c == 0;
             barrier_arrive(cnt, skip);
             // the previous sweep's finalise runs while this CTA waits for the
@@ -251,13 +263,60 @@ __global__ void __launch_bounds__(kBlock, 2) batch_kernel(const BatchArgs b) {
     if (b.n_total > 0) finalize_sweep(b, b.n_total - 1);
 }
 
+// The per-pass schedule: one launch per colour pass of every member, the
+// launches chained by programmatic dependent launch (a launch's CTAs are
+// scheduled as the previous one's retire and wait for its completion before
+// touching memory).  Pass 0 of sweep s first finalises sweep s - 1, whose
+// passes have completed by then; the slots it reads (parity (s-1) & 1) are
+// rewritten only by pass 0 of sweep s + 1, two completed launches later.
+template <int PF>
+__global__ void __launch_bounds__(kBlock, 2) batch_pass_kernel(const BatchArgs b, int s, int c) {
+    pdl_enter();
+    if (c == 0 && s > 0) finalize_sweep(b, s - 1);
+    batch_pass<PF, false>(b, s, c);
+}
+
+// The last sweep's finalise of the per-pass schedule.
+__global__ void __launch_bounds__(kBlock) batch_finalize_kernel(const BatchArgs b, int s) {
+    pdl_enter();
+    finalize_sweep(b, s);
+}
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_chained(void (*kernel)(KArgs...), int grid, cudaStream_t s, Args... args) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(kBlock);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 }  // namespace
 
 int batch_occupancy(int prefetch) {
-    int blocks = 0;
+    int blocks = 0, blocks_pass = 0;
     const void *k = prefetch ? (const void *)batch_kernel<2> : (const void *)batch_kernel<0>;
+    const void *kp = prefetch ? (const void *)batch_pass_kernel<2> : (const void *)batch_pass_kernel<0>;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k, kBlock, 0) != cudaSuccess) return 0;
-    return blocks;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_pass, kp, kBlock, 0) != cudaSuccess) return 0;
+    return blocks < blocks_pass ? blocks : blocks_pass;
+}
+
+cudaError_t launch_batch_passes(const BatchArgs &b, int grid, cudaStream_t s, int prefetch) {
+    for (int sw = 0; sw < b.n_total; ++sw)
+        for (int c = 0; c < 2; ++c) {
+            const cudaError_t e = prefetch ? launch_chained(batch_pass_kernel<2>, grid, s, b, sw, c)
+                                           : launch_chained(batch_pass_kernel<0>, grid, s, b, sw, c);
+            if (e != cudaSuccess) return e;
+        }
+    if (b.n_total > 0) return launch_chained(batch_finalize_kernel, grid, s, b, b.n_total - 1);
+    return cudaSuccess;
 }
 
 cudaError_t launch_batch(const BatchArgs &b, int grid, cudaStream_t s, int prefetch) {

@@ -205,6 +205,8 @@ constexpr int kWaveComputeWarps = 15;        // per CTA, plus one control warp
 // prefetch 0: one work item of loads at a time; 1: split prefetch (the
 // next item's DRAM-heavy rows load during the current item's arithmetic)
 cudaError_t launch_batch(const BatchArgs &b, int grid, cudaStream_t s, int prefetch);
+// the per-pass schedule: 2 n_total chained pass launches and a finalise launch
+cudaError_t launch_batch_passes(const BatchArgs &b, int grid, cudaStream_t s, int prefetch);
 int batch_occupancy(int prefetch);
 
 size_t storage_size(int precision);

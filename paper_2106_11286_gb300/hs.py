@@ -108,8 +108,8 @@ SIGNATURES = {
     "hs_batch_destroy": (None, [_vp]),
     "hs_batch_autotune": (ctypes.c_int, [_vp, _dp, ctypes.c_int]),
     "hs_batch_get_layout": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
-                                           ctypes.POINTER(ctypes.c_int)]),
-    "hs_batch_set_layout": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+                                           ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+    "hs_batch_set_layout": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     "hs_sweep_sc_fp32_noalloc": (ctypes.c_int, [_vp, _i32p, ctypes.POINTER(hs_params), ctypes.c_double,
                                                  ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int64,
                                                  _vp, _vp]),
@@ -449,12 +449,13 @@ def hs_batch_get_layout(b) -> dict:
     c = ctypes.c_int(0)
     a = ctypes.c_int(0)
     pf = ctypes.c_int(0)
-    _check(load().hs_batch_get_layout(b, ctypes.byref(c), ctypes.byref(a), ctypes.byref(pf)))
-    return {"ctas_per_sm": c.value, "align_rows": a.value, "prefetch": pf.value}
+    sc = ctypes.c_int(0)
+    _check(load().hs_batch_get_layout(b, ctypes.byref(c), ctypes.byref(a), ctypes.byref(pf), ctypes.byref(sc)))
+    return {"ctas_per_sm": c.value, "align_rows": a.value, "prefetch": pf.value, "schedule": sc.value}
 
 
-def hs_batch_set_layout(b, ctas_per_sm, align_rows=0, prefetch=0):
-    _check(load().hs_batch_set_layout(b, int(ctas_per_sm), int(align_rows), int(prefetch)))
+def hs_batch_set_layout(b, ctas_per_sm, align_rows=0, prefetch=0, schedule=0):
+    _check(load().hs_batch_set_layout(b, int(ctas_per_sm), int(align_rows), int(prefetch), int(schedule)))
 
 
 def hs_batch_destroy(b):
