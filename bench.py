@@ -66,8 +66,7 @@ def kernels_sha() -> str:
 
 
 # colour-pass kernel of each hs_kernel kind (hs_get_launch's "kernel")
-KERNEL_NAMES = {1: "sc_pass_kernel", 2: "sc_staged_kernel", 3: "table_pass_kernel", 4: "sc_march_kernel",
-                5: "sc_pipe_kernel", 6: "sc_wave_kernel"}
+KERNEL_NAMES = {1: "sc_pass_kernel", 3: "table_pass_kernel", 4: "sc_march_kernel", 5: "sc_pipe_kernel"}
 
 
 def kernel_label(launch, precision_code=1, measure=1):
@@ -341,19 +340,22 @@ def run_ours(args):
         lat.close()
 
     variants = None if args.no_variants else run_variants(args, rank, stream, barrier_sync, world, dev)
+    if variants is not None:
+        variants["noalloc"] = noalloc_run(args, stream)
+        if world > 1:
+            try:
+                variants["slab_strong"] = slab_strong_run(args, rank, world, stream, barrier_sync)
+            except Exception as ex:  # the replica figure above stands on its own
+                variants["slab_strong"] = {"error": repr(ex)[:300]}
 
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
     if rank != 0:
         return None
-    # kernels launched in the timed region: two colour passes per sweep and the ring folds of the fused
-    # sums (a per-sweep sum kernel and an apply kernel per fold_sweeps sweeps), or (wavefront kernel) one
-    # persistent launch plus its one-CTA finalisation per 256 sweeps
-    if launch and launch.get("kernel") == 6:
-        gpu_launches = 2 * ((args.steps + 255) // 256)
-    else:
-        gpu_launches = 2 * args.steps + 2 * ((args.steps + fold - 1) // fold)
+    # kernels launched in one timed region: two colour passes per sweep and the ring folds of the fused
+    # sums (a per-sweep sum kernel and an apply kernel per fold_sweeps sweeps)
+    gpu_launches = 2 * args.steps + 2 * ((args.steps + fold - 1) // fold)
     cpu, spin_err = (None, None) if (args.no_cpu_baseline or world > 1) else cpu_baseline(args)
     precision = None if (args.no_precision or world > 1) else precision_runs(args)
     tc = None if (args.no_precision or world > 1) else tc_runs(args)
@@ -562,6 +564,71 @@ def fp64_roofline(value, stream):
                     "peak_source": "measured DFMA chains (hs_measure_alu_peak), 1 instruction = 2 FLOP",
                     "kernel": ops["kernel"]})
     return out
+
+
+def noalloc_run(args, stream):
+    """The allocation-free entry point on the headline workload (sc 256^3
+    FP32, caller-held planes, static reduction scratch): attempts/ns of
+    args.steps sweeps in one call, beside the handle path's."""
+    import torch
+
+    from paper_2106_11286_gb300 import hs
+    w = WORKLOAD
+    L = w["L"]
+    dims = (L, L, L)
+    planes = torch.empty(6 * L * L * (L // 2), dtype=torch.float32, device="cuda")
+    with hs.Lattice("sc", dims=dims, precision="fp32", seed=w["seed"], J=w["J"], K=w["K"], e=w["e"],
+                    stream=stream) as lat:
+        lat.init()
+        S = lat.get_spins()
+    # the stencil layout: planes [colour][xyz][z][y][x/2], colour (x + y + z) & 1
+    St = torch.from_numpy(S.reshape(L, L, L, 3)).to("cuda", torch.float32)
+    z, y, x = torch.meshgrid(torch.arange(L, device="cuda"), torch.arange(L, device="cuda"),
+                             torch.arange(L, device="cuda"), indexing="ij")
+    col = (x + y + z) & 1
+    P = planes.view(2, 3, L, L, L // 2)
+    for c in (0, 1):
+        m = col == c
+        for q in range(3):
+            P[c, q][z[m], y[m], x[m] // 2] = St[..., q][m]
+    out = torch.zeros(hs.HS_N_MOMENTS + 2, dtype=torch.float64, device="cuda")
+    beta = 1.0 / w["T"]
+    kw = dict(J=w["J"], K=w["K"], e=w["e"], seed=w["seed"], stream=stream)
+    hs.hs_sweep_sc_fp32_noalloc(planes, dims, beta, args.warmup, out, first_sweep=0, **kw)
+    sec = _timed(stream, lambda: hs.hs_sweep_sc_fp32_noalloc(planes, dims, beta, args.steps, out,
+                                                              first_sweep=args.warmup, **kw))
+    del St, z, y, x, col
+    return {"value": round(L ** 3 * args.steps / (sec * 1e9), 3), "unit": UNIT, "sweeps": args.steps,
+            "what": "hs_sweep_sc_fp32_noalloc on the headline workload: register stencil, split prefetch, "
+                    "reductions finished by the last-arriving CTA of each sweep in static scratch"}
+
+
+def slab_strong_run(args, rank, world, stream, barrier_sync):
+    """One sc 1024^3 FP32 lattice split into z-slabs, one per rank, halos
+    exchanged with NCCL after every colour pass (shards.DistributedSlab):
+    strong scaling of one lattice, beside the replica figure."""
+    from paper_2106_11286_gb300 import shards
+    L = 1024
+    w = WORKLOAD
+    ds = shards.DistributedSlab((L, L, L), J=w["J"], K=w["K"], e=w["e"], precision="fp32", seed=6,
+                                stream=stream)
+    try:
+        ds.init()
+        beta = 1.0 / w["T"]
+        ds.sweep(beta, 3)
+        barrier_sync()
+        t = time.perf_counter()
+        ds.sweep(beta, args.huge_sweeps)
+        barrier_sync()
+        sec = time.perf_counter() - t
+        import torch
+        _, s_max = aggregate(0.0, sec, world, torch.device("cuda", torch.cuda.current_device()))
+    finally:
+        ds.close()
+    return {"value": round(float(L) ** 3 * args.huge_sweeps / (s_max * 1e9), 3), "unit": UNIT, "ranks": world,
+            "n_spins": L ** 3, "sweeps": args.huge_sweeps, "scaling": "strong",
+            "what": "one sc 1024^3 FP32 lattice in z-slabs, packed halo planes by stream-ordered NCCL "
+                    "send/recv after every colour pass; wall clock over the slowest rank"}
 
 
 # ------------------------------------------------------------------ CPU oracle

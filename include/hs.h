@@ -224,37 +224,22 @@ int hs_read_timing(hs_lattice *h, double *ms, int64_t *launches);
 enum hs_kernel {
     HS_KERNEL_AUTO = 0,
     HS_KERNEL_STENCIL = 1, /* sc: operands loaded through L1/L2 into registers */
-    HS_KERNEL_STAGED = 2,  /* sc: other-colour planes staged in shared memory by
-                              bulk async copies, CTAs march along z */
     HS_KERNEL_TABLE = 3,   /* neighbour-table kernel (bcc, fcc, CSR, masked) */
-    HS_KERNEL_MARCH = 4,   /* sc: register stencil walking each CTA's slab along z
-                              (neighbour rows reused from L1, next plane
-                              prefetched into L2) */
-    HS_KERNEL_PIPE = 5,    /* sc: register stencil whose next work item is copied
+    HS_KERNEL_MARCH = 4,   /* sc: register stencil walking each CTA's slab of
+                              tile_y rows along z (rows reused from L1, next
+                              plane prefetched into L2); spreads a small
+                              lattice's pass over more SMs */
+    HS_KERNEL_PIPE = 5     /* sc: register stencil whose next work item is copied
                               global -> shared (cp.async, one slot per thread)
                               while the current one is computed; needs 4..16
                               bytes of storage per vector */
-    HS_KERNEL_WAVE = 6     /* sc, FP32 (vector width 4) or FP16 (8), whole
-                              lattices without a tensor term, Lz >= 3, fewer
-                              than 2^31 sites: one persistent cooperative launch
-                              runs up to 256 sweeps; groups of colour passes
-                              follow each other plane by plane (a pass starts
-                              plane z once the previous pass has finished
-                              planes z-1, z, z+1), so planes are reused from L2.
-                              tile_y = work items per compute thread and unit
-                              (1..8, default 2), chunk_z = passes per group
-                              (1..32, default from the SM count), ring = lag in
-                              planes between consecutive passes of a group
-                              (3..64, default 5).  hs_sweep_pass runs the
-                              register stencil. */
 };
 typedef struct {
     int kernel;        /* hs_kernel; the table kernel is the only one for non-sc */
     int vec_width;     /* sc kernels: sites per thread, 1/2/4/8, dividing Lx/2,
                           at most 16 bytes of storage per load */
-    int blocks_per_sm; /* stencil / pipe / table: resident CTAs per SM (0 = max) */
-    int tile_y;        /* staged / march: rows per CTA slab (divides Ly) */
-    int chunk_z;       /* staged: planes per CTA work unit */
+    int blocks_per_sm; /* resident CTAs per SM (0 = max) */
+    int tile_y;        /* z-march: rows per CTA slab (divides Ly; 0 = automatic) */
     int prefetch;      /* stencil: 1 = issue the next work item's loads before
                           computing the current one, 3 = split prefetch (the
                           next item's own, same-row and z+-1 rows loaded once
@@ -264,15 +249,10 @@ typedef struct {
                           table: 1 = ask L2 for the next site's table row
                           and spin ahead, 2 = off, 0 = automatic (on for FP32
                           tables of at most 8 neighbours) */
-    int ring;          /* staged: shared-memory slots of the other colour's
-                          planes (4..8; the own colour gets ring - 2) */
-    int consumers;     /* staged: consumer warps per CTA, 4 or 8 (plus one
-                          producer warp) */
 } hs_launch;
 
-/* Set (fields 0 = automatic) or read the launch configuration.  The staged
- * kernel needs Lx/2 * storage bytes to be a multiple of 16 and its slabs to
- * fit in shared memory; HS_E_INVALID otherwise. */
+/* Set (fields 0 = automatic) or read the launch configuration.  Kernel
+ * codes 2 and 6 are not used (HS_E_INVALID). */
 int hs_set_launch(hs_lattice *h, const hs_launch *cfg);
 int hs_get_launch(const hs_lattice *h, hs_launch *out);
 
@@ -283,8 +263,8 @@ int hs_get_launch(const hs_lattice *h, hs_launch *out);
  * + 2 (Axy xy + Axz xz + Ayz yz).  A = NULL or all zeros removes the term.
  * The uniaxial term is the special case A = K e e^T.  Kernels: the register
  * stencil without prefetch (periodic sc) and the neighbour table (everything
- * else); the staged, pipelined and z-march kernels and hs_batch_create reject
- * a lattice that has the term.  Setting the tensor resets the launch
+ * else); the pipelined and z-march kernels and hs_batch_create reject a
+ * lattice that has the term.  Setting the tensor resets the launch
  * configuration to automatic.  Entries must be finite (HS_E_INVALID
  * otherwise; nothing changes then).  The FP32 / FP16 kernels use the entries
  * rounded to FP32.  hs_get_anisotropy_tensor reads them back (zeros when
@@ -293,7 +273,7 @@ int hs_set_anisotropy_tensor(hs_lattice *h, const double A[6]);
 int hs_get_anisotropy_tensor(const hs_lattice *h, double A[6]);
 
 /* Autotuner: time every valid launch configuration (kernel, vector width,
- * CTAs per SM, prefetch, slab rows and z chunk, wavefront groups) for
+ * CTAs per SM, z-march slab rows, prefetch) for
  * n_trial_sweeps sweeps at beta, each from the same saved state and sweep
  * counter (one warm-up sweep first); the three fastest are timed again over
  * twice the sweeps and the fastest of those is kept.  The spins, the
@@ -465,20 +445,13 @@ int hs_read_sums(hs_lattice *h, double out[5]);
  * frees a small device buffer; synchronous.  HS_E_INVALID for another kind. */
 int hs_measure_alu_peak(int kind, void *cuda_stream, double *flops_per_s);
 
-/* Test hooks for the bounded device-side waits (failure detection without a
- * GPU fault).  hs_lattice_inject_timeout: the next colour pass of a lattice
- * running the staged kernel expects 16 bytes more than it copies, so the
- * consumers' bounded mbarrier wait runs out (about one second); on a lattice
- * running the wavefront kernel, CTA 0 of the next launch does not count its
- * first finished unit, so every unit that needs it (and, in turn, the rest of
- * the launch) waits until its bounded wait runs out.
- * hs_batch_inject_timeout: in the next hs_batch_run one CTA skips its first
- * grid-barrier arrival, so every other CTA's bounded wait runs out.  Either
- * way the kernel latches its error word and returns; the next synchronising
- * call on the lattice (each member) reports HS_E_TIMEOUT and clears it, the
- * CUDA context stays usable, and the spins of the interrupted sweep are left
- * part-updated. */
-int hs_lattice_inject_timeout(hs_lattice *h, int on);
+/* Test hook for the bounded device-side waits (failure detection without a
+ * GPU fault): in the next hs_batch_run (persistent schedule) one CTA skips
+ * its first grid-barrier arrival, so every other CTA's bounded wait runs out
+ * (about one second).  The kernel latches its error word and returns; the
+ * next synchronising call on each member reports HS_E_TIMEOUT and clears it,
+ * the CUDA context stays usable, and the spins of the interrupted sweep are
+ * left part-updated. */
 int hs_batch_inject_timeout(hs_batch *b, int on);
 
 const char *hs_last_error(void);

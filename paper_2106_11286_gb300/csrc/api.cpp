@@ -197,17 +197,11 @@ struct hs_lattice {
     uint64_t sweep = 0;
     int accumulate = 0;
     int64_t last_n_sweeps = 0;
-    uint32_t *wave_cnt = nullptr;  // wavefront kernel buffers (allocated on first use)
-    uint32_t *wave_order = nullptr;
-    double *wave_slots = nullptr;
-    int wave_cnt_n = 0;
-    size_t wave_order_n = 0, wave_slots_n = 0;
     double2 *sc_tab = nullptr;     // FP64: sin, cos(pi j / 128) table of the trial orientation
     int tensor = 0;                // on-site anisotropy tensor term on
     double tA[6] = {0, 0, 0, 0, 0, 0};
     Layout L{};
     int n_blocks = 1;
-    int inject_timeout = 0;  // test hook, consumed by the next staged pass
     hs_launch req{};        // requested launch configuration (0 = automatic)
     int max_blocks = 1;     // capacity of the partials buffer
     int fold_ring = 1;      // sweeps per ring fold (slot sets of the partials buffer)
@@ -260,10 +254,6 @@ PassArgs base_args(const hs_lattice *h) {
         a.site_off = (uint32_t)((int64_t)(L.z0 - a.z_off) * L.Ly * L.Lx);
         a.rank_off = (uint32_t)((int64_t)(L.z0 - a.z_off) * L.Ly * L.Lh);
         a.ty = L.ty;
-        a.zchunk = L.zchunk;
-        a.n_units = L.n_units;
-        a.ring_o = L.ring_o;
-        a.ring_w = L.ring_w;
     }
     a.spins4 = L.spins4;
     a.nbr = L.nbr;
@@ -402,84 +392,6 @@ int default_vec(const hs_lattice *h) {
     return 1;
 }
 
-bool staged_ok(const hs_lattice *h) {
-    const Layout &L = h->L;
-    return L.structured && ((size_t)L.Lh * hs::storage_size(h->precision)) % 16 == 0;
-}
-
-// Resolve the requested configuration into kernel, vector width and grid.
-// Stencil / table: blocks_per_sm resident CTAs (0 = occupancy limit of the
-// slower pass variant) on every SM.  Staged: slabs of tile_y rows (default:
-// the largest of 8, 4, 2, 1 dividing Ly whose slabs fit two CTAs per SM),
-// z chunks sized so that all units fit in one wave.
-// Wavefront kernel: work units of k items per compute thread, D passes per
-// group (default: enough plane-units per diagonal of the ticket order to give
-// every CTA one), lag 5 planes.  Its buffers are allocated here.  Single
-// colour passes (hs_sweep_pass) still run the register stencil, configured
-// as the automatic stencil.
-int configure_wave(hs_lattice *h) {
-    Layout &L = h->L;
-    const hs_launch &r = h->req;
-    if (L.slab || h->tensor) return fail(HS_E_INVALID, "the wavefront kernel runs whole periodic sc lattices without a tensor term");
-    if (h->precision == HS_FP16 && r.vec_width == 0 && L.Lh % 8 == 0) L.vec = 8;
-    if (!((h->precision == HS_FP32 && L.vec == 4) || (h->precision == HS_FP16 && L.vec == 8)))
-        return fail(HS_E_INVALID, "the wavefront kernel needs FP32 with vector width 4 or FP16 with 8");
-    if (L.n_sites > 2147483647LL) return fail(HS_E_INVALID, "the wavefront kernel needs fewer than 2^31 sites");
-    if (L.Lz < 3) return fail(HS_E_INVALID, "the wavefront kernel needs Lz >= 3");
-    if (hs::wave_occupancy(h->precision, L.vec) < 1) return fail(HS_E_CUDA, "the wavefront kernel does not fit on an SM");
-    const int k = r.tile_y ? r.tile_y : 2;
-    if (k < 1 || k > 8) return fail(HS_E_INVALID, "wavefront items per thread (tile_y) must be in [1, 8]");
-    const int lag = r.ring ? r.ring : 5;
-    if (lag < 3 || lag > 64) return fail(HS_E_INVALID, "wavefront lag (ring) must be in [3, 64]");
-    const int64_t n_pi = (int64_t)L.Ly * (L.Lh / L.vec);
-    const int64_t ipu0 = (int64_t)32 * hs::kWaveComputeWarps * k;
-    const int64_t U = (n_pi + ipu0 - 1) / ipu0;
-    const int64_t ipu = (n_pi + U - 1) / U;
-    const int grid = h->n_sm;
-    int D = r.chunk_z ? r.chunk_z : (int)std::min<int64_t>(32, std::max<int64_t>(2, (grid + U - 1) / U));
-    if (D < 1 || D > 32) return fail(HS_E_INVALID, "wavefront passes per group (chunk_z) must be in [1, 32]");
-    // the register stencil for single passes
-    L.kernel = hs::kStencil;
-    L.prefetch = (h->precision == HS_FP32 && L.Lh / L.vec <= hs::kBlock / 8) ? 2 : 0;
-    const int occ = std::min(hs::pass_occupancy(h->precision, L, 0), hs::pass_occupancy(h->precision, L, 1));
-    h->n_blocks = std::min(hs::pass_blocks(h->precision, L, h->n_sm, occ), h->max_blocks);
-    // buffers: counters, ticket orders of groups of 1..D passes, per-CTA pass sums
-    const int max_pass = 512;
-    std::vector<uint32_t> order;
-    for (int dg = 1; dg <= D; ++dg)
-        for (int m = 0; m < L.Lz + lag * (dg - 1); ++m)
-            for (int d = 0; d < dg; ++d) {
-                const int kk = m - lag * d;
-                if (kk >= 0 && kk < L.Lz) order.push_back(((uint32_t)d << 20) | (uint32_t)kk);
-            }
-    if (!h->wave_cnt || h->wave_cnt_n < L.Lz) {
-        if (int st = h->alloc(&h->wave_cnt, (size_t)L.Lz * sizeof(uint32_t))) return st;
-        h->wave_cnt_n = L.Lz;
-    }
-    if (!h->wave_order || h->wave_order_n < order.size()) {
-        if (int st = h->alloc(&h->wave_order, order.size() * sizeof(uint32_t))) return st;
-        h->wave_order_n = order.size();
-    }
-    const size_t n_slots = (size_t)max_pass * grid * hs::kPartials;
-    if (!h->wave_slots || h->wave_slots_n < n_slots) {
-        if (int st = h->alloc(&h->wave_slots, n_slots * sizeof(double))) return st;
-        h->wave_slots_n = n_slots;
-    }
-    HS_CUDA(cudaMemcpy(h->wave_order, order.data(), order.size() * sizeof(uint32_t), cudaMemcpyHostToDevice));
-    L.kernel = hs::kWave;
-    L.wave_k = k;
-    L.wave_ipu = (int)ipu;
-    L.wave_U = (int)U;
-    L.wave_D = D;
-    L.wave_lag = lag;
-    L.wave_grid = grid;
-    L.wave_cnt = h->wave_cnt;
-    L.wave_order = h->wave_order;
-    L.wave_slots = h->wave_slots;
-    L.wave_max_pass = max_pass;
-    return HS_OK;
-}
-
 int configure_launch(hs_lattice *h) {
     Layout &L = h->L;
     const hs_launch &r = h->req;
@@ -504,50 +416,10 @@ int configure_launch(hs_lattice *h) {
         if ((int64_t)L.nz * L.Ly * (L.Lh / L.vec) >= 4294967296LL)
             return fail(HS_E_INVALID, "vector width too small: more than 2^32 work items");
     }
-    // automatic choice: the register stencil (measured faster than the staged
-    // kernel on GB300 at 256^3 and 464^3; hs_autotune compares both)
+    // automatic choice: the register stencil (hs_autotune also times the pipelined one)
     if (kind == HS_KERNEL_AUTO) kind = HS_KERNEL_STENCIL;
     if (h->tensor && (kind != HS_KERNEL_STENCIL || r.prefetch == 1 || r.prefetch == 3))
         return fail(HS_E_INVALID, "the anisotropy tensor term runs on the register stencil without prefetch");
-    if (kind == HS_KERNEL_STAGED) {
-        if (!staged_ok(h)) return fail(HS_E_INVALID, "staged kernel needs Lx/2 * storage bytes divisible by 16");
-        const int ring = r.ring ? r.ring : 5;
-        if (ring < 4 || ring > 8) return fail(HS_E_INVALID, "ring must be in [4, 8]");
-        const int consumers = r.consumers ? 32 * r.consumers : 128;
-        if (consumers != 128 && consumers != 256) return fail(HS_E_INVALID, "consumer warps must be 4 or 8");
-        int ty = r.tile_y;
-        if (ty == 0) {  // smallest slab whose items fill the consumer warps
-            const int nxv = L.Lh / L.vec;
-            for (int c : {1, 2, 4, 8, 16})
-                if (L.Ly % c == 0 && c * nxv >= consumers) {
-                    ty = c;
-                    break;
-                }
-            if (ty == 0) ty = L.Ly;
-        }
-        if (ty < 1 || L.Ly % ty != 0) return fail(HS_E_INVALID, "tile_y must divide Ly");
-        const size_t smem = hs::staged_smem_bytes(h->precision, ty, L.Lh, ring, ring - 2);
-        const int occ = hs::staged_occupancy(h->precision, L.vec, smem, consumers);
-        if (occ < 1) return fail(HS_E_INVALID, "staged slabs do not fit in shared memory");
-        const int slots = h->n_sm * occ;
-        const int n_yslab = L.Ly / ty;
-        int zc = r.chunk_z;
-        if (zc <= 0) {
-            const int n_chunks = std::max(1, slots / n_yslab);
-            zc = (L.Lz + n_chunks - 1) / n_chunks;
-        }
-        zc = std::min(std::max(zc, 1), L.Lz);
-        L.kernel = hs::kStaged;
-        L.ty = ty;
-        L.zchunk = zc;
-        L.ring_o = ring;
-        L.ring_w = ring - 2;
-        L.consumers = consumers;
-        L.n_units = n_yslab * ((L.Lz + zc - 1) / zc);
-        L.grid = std::min(L.n_units, slots);
-        h->n_blocks = L.grid;
-        return HS_OK;
-    }
     if (kind == HS_KERNEL_MARCH) {
         const int nxv = L.Lh / L.vec;
         int ty = r.tile_y;
@@ -569,7 +441,6 @@ int configure_launch(hs_lattice *h) {
         h->n_blocks = (int)std::min<int64_t>(std::min<int64_t>(slabs, (int64_t)h->n_sm * bps), h->max_blocks);
         return HS_OK;
     }
-    if (kind == HS_KERNEL_WAVE) return configure_wave(h);
     if (kind == HS_KERNEL_PIPE) {
         if (hs::pipe_smem_bytes(h->precision, L.vec) == 0)
             return fail(HS_E_INVALID, "pipelined stencil needs 4 to 16 bytes of storage per vector");
@@ -859,63 +730,10 @@ int run_pass(hs_lattice *h, PassArgs &a, uint32_t sweep, int c, bool deferred = 
         int st = record_event(h);
         if (st) return st;
     }
-    a.inject_extra_tx = 0;
-    if (h->inject_timeout && L.kernel == hs::kStaged) {
-        a.inject_extra_tx = 16;
-        h->inject_timeout = 0;
-    }
     HS_CUDA(hs::launch_pass(h->precision, L, a, h->n_blocks, h->stream));
     if (h->timing) {
         int st = record_event(h);
         if (st) return st;
-    }
-    return HS_OK;
-}
-
-// n_sweeps whole sweeps with the wavefront kernel: launches of at most
-// wave_max_pass passes, each after zeroing its counters and sums and followed
-// by the one-CTA finalisation of its sweeps.
-int run_wave(hs_lattice *h, const PassArgs &a, int64_t n_sweeps) {
-    const Layout &L = h->L;
-    const int grid = L.wave_grid;
-    int64_t done = 0;
-    while (done < n_sweeps) {
-        const int64_t sweeps = std::min<int64_t>(n_sweeps - done, L.wave_max_pass / 2);
-        hs::WaveArgs w{};
-        w.a = a;
-        w.a.colour = 0;
-        w.planes = L.planes;
-        w.n_pi = (uint32_t)(L.Ly * (L.Lh / L.vec));
-        w.ipu = (uint32_t)L.wave_ipu;
-        w.U = (uint32_t)L.wave_U;
-        w.D = (uint32_t)L.wave_D;
-        w.n_pass = (uint32_t)(2 * sweeps);
-        w.n_full = w.n_pass / w.D;
-        w.D_last = w.n_pass - w.n_full * w.D;
-        w.n_tickets = w.n_pass * (uint32_t)L.Lz * w.U;
-        const size_t lz = (size_t)L.Lz;
-        w.order_full = L.wave_order + lz * (size_t)(w.D * (w.D - 1) / 2);
-        w.order_last = w.D_last ? L.wave_order + lz * (size_t)(w.D_last * (w.D_last - 1) / 2) : w.order_full;
-        w.sweep0 = (uint32_t)(h->sweep + (uint64_t)done);
-        w.cnt = L.wave_cnt;
-        w.slots = L.wave_slots;
-        w.error = &h->acc->error;
-        w.acc = h->acc;
-        w.accumulate = h->accumulate;
-        w.n_present = (double)L.n_present;
-        for (int q = 0; q < 3; ++q) w.e[q] = h->p.e[q];
-        w.inject_skip = h->inject_timeout;
-        h->inject_timeout = 0;
-        HS_CUDA(cudaMemsetAsync(L.wave_cnt, 0, lz * sizeof(uint32_t), h->stream));
-        HS_CUDA(cudaMemsetAsync(L.wave_slots, 0, (size_t)w.n_pass * grid * hs::kPartials * sizeof(double),
-                                h->stream));
-        if (h->timing)
-            if (int st = record_event(h)) return st;
-        HS_CUDA(hs::launch_wave(h->precision, L.vec, w, grid, h->stream));
-        if (h->timing)
-            if (int st = record_event(h)) return st;
-        HS_CUDA(hs::launch_wave_finalize(w, grid, h->stream));
-        done += sweeps;
     }
     return HS_OK;
 }
@@ -942,11 +760,6 @@ int hs_sweep(hs_lattice *h, double beta, int64_t n_sweeps) {
     a.beta = beta;
     a.fbeta = (float)beta;
     a.accumulate = h->accumulate;
-    if (h->L.kernel == hs::kWave) {
-        if (int st = run_wave(h, a, n_sweeps)) return st;
-        h->sweep += (uint64_t)n_sweeps;
-        return HS_OK;
-    }
     // sweep s writes ring slot s mod ring; each full ring, and the rest after
     // the loop, is folded into the accumulator in sweep order
     int pending = 0;
@@ -1225,7 +1038,8 @@ int hs_read_timing(hs_lattice *h, double *ms, int64_t *launches) {
 // ---------------------------------------------------------------- launch configuration
 int hs_set_launch(hs_lattice *h, const hs_launch *cfg) {
     if (!h || !cfg) return fail(HS_E_INVALID, "null argument");
-    if (cfg->kernel < HS_KERNEL_AUTO || cfg->kernel > HS_KERNEL_WAVE)
+    if (cfg->kernel != HS_KERNEL_AUTO && cfg->kernel != HS_KERNEL_STENCIL && cfg->kernel != HS_KERNEL_TABLE &&
+        cfg->kernel != HS_KERNEL_MARCH && cfg->kernel != HS_KERNEL_PIPE)
         return fail(HS_E_INVALID, "unknown kernel kind");
     if (h->L.slab && cfg->kernel != HS_KERNEL_AUTO && cfg->kernel != HS_KERNEL_STENCIL)
         return fail(HS_E_INVALID, "a slab runs the register stencil");
@@ -1233,18 +1047,13 @@ int hs_set_launch(hs_lattice *h, const hs_launch *cfg) {
         if (cfg->kernel == HS_KERNEL_TABLE) return fail(HS_E_INVALID, "sc stencil lattices have no table kernel");
         if (cfg->vec_width != 0 && !vec_ok(h, cfg->vec_width))
             return fail(HS_E_INVALID, "vector width must divide Lx/2, 16 bytes at most");
-    } else if (cfg->kernel == HS_KERNEL_STENCIL || cfg->kernel == HS_KERNEL_STAGED ||
-               cfg->kernel == HS_KERNEL_MARCH || cfg->kernel == HS_KERNEL_PIPE || cfg->kernel == HS_KERNEL_WAVE) {
+    } else if (cfg->kernel == HS_KERNEL_STENCIL || cfg->kernel == HS_KERNEL_MARCH || cfg->kernel == HS_KERNEL_PIPE) {
         return fail(HS_E_INVALID, "stencil kernels need an unmasked periodic sc lattice");
     }
     if (cfg->blocks_per_sm < 0 || cfg->blocks_per_sm > 2048 / hs::kBlock)
         return fail(HS_E_INVALID, "blocks_per_sm out of range");
-    if (cfg->tile_y < 0 || cfg->chunk_z < 0) return fail(HS_E_INVALID, "negative tile");
+    if (cfg->tile_y < 0) return fail(HS_E_INVALID, "negative tile_y");
     if (cfg->prefetch < 0 || cfg->prefetch > 3) return fail(HS_E_INVALID, "prefetch must be 0, 1, 2 or 3");
-    if (cfg->kernel != HS_KERNEL_WAVE && cfg->ring != 0 && (cfg->ring < 4 || cfg->ring > 8))
-        return fail(HS_E_INVALID, "ring must be 0 or in [4, 8]");
-    if (cfg->consumers != 0 && cfg->consumers != 4 && cfg->consumers != 8)
-        return fail(HS_E_INVALID, "consumer warps must be 0, 4 or 8");
     const hs_launch keep = h->req;
     const Layout keep_l = h->L;
     const int keep_b = h->n_blocks;
@@ -1300,18 +1109,10 @@ int hs_get_launch(const hs_lattice *h, hs_launch *out) {
     out->kernel = L.kernel;
     out->vec_width = L.structured ? L.vec : 1;
     out->blocks_per_sm = (h->n_blocks + h->n_sm - 1) / std::max(h->n_sm, 1);
-    out->tile_y = (L.kernel == hs::kStaged || L.kernel == hs::kMarch) ? L.ty : 0;
-    out->chunk_z = L.kernel == hs::kStaged ? L.zchunk : 0;
-    if (L.kernel == hs::kWave) {
-        out->blocks_per_sm = 1;
-        out->tile_y = L.wave_k;
-        out->chunk_z = L.wave_D;
-    }
+    out->tile_y = L.kernel == hs::kMarch ? L.ty : 0;
     out->prefetch = (L.kernel == hs::kStencil || L.kernel == hs::kTable)
                         ? (L.prefetch == 1 ? 1 : (L.prefetch == 2 ? 3 : 2))
                         : 0;
-    out->ring = L.kernel == hs::kStaged ? L.ring_o : (L.kernel == hs::kWave ? L.wave_lag : 0);
-    out->consumers = L.kernel == hs::kStaged ? L.consumers / 32 : 0;
     return HS_OK;
 }
 
@@ -1333,39 +1134,18 @@ std::vector<hs_launch> tune_candidates(hs_lattice *h) {
     const Layout &L = h->L;
     if (!L.structured) {
         for (int b = 1; b <= 8; ++b)
-            for (int pf : {1, 2}) out.push_back({HS_KERNEL_TABLE, 1, b, 0, 0, pf, 0, 0});
+            for (int pf : {1, 2}) out.push_back({HS_KERNEL_TABLE, 1, b, 0, pf});
         return out;
     }
-    for (int lag : {5, 8}) out.push_back({HS_KERNEL_WAVE, 0, 0, 2, 0, 0, lag, 0});  // rejected where it has no variant
     for (int v : {1, 2, 4, 8}) {
         if (!vec_ok(h, v)) continue;
         for (int b = 1; b <= 8; ++b)
-            for (int pf : {1, 2, 3}) out.push_back({HS_KERNEL_STENCIL, v, b, 0, 0, pf, 0, 0});
+            for (int pf : {1, 2, 3}) out.push_back({HS_KERNEL_STENCIL, v, b, 0, pf});
         if (hs::pipe_smem_bytes(h->precision, v) != 0)
-            for (int b = 1; b <= 2; ++b) out.push_back({HS_KERNEL_PIPE, v, b, 0, 0, 0, 0, 0});
+            for (int b = 1; b <= 2; ++b) out.push_back({HS_KERNEL_PIPE, v, b, 0, 0});
         for (int ty : {2, 4, 8, 16})
             if (L.Ly % ty == 0 && ty * (L.Lh / v) >= 64)
-                for (int b : {1, 2}) out.push_back({HS_KERNEL_MARCH, v, b, ty, 0, 0, 0, 0});
-        if (!staged_ok(h)) continue;
-        for (int cw : {4, 8}) {
-            for (int ty : {1, 2, 4, 8, 16}) {
-                if (L.Ly % ty != 0 || ty * (L.Lh / v) < 32 * cw) continue;
-                for (int ring : {4, 5, 6}) {
-                    const size_t smem = hs::staged_smem_bytes(h->precision, ty, L.Lh, ring, ring - 2);
-                    const int occ = hs::staged_occupancy(h->precision, v, smem, 32 * cw);
-                    if (occ < 1) continue;
-                    const int slots = h->n_sm * occ;
-                    const int n_yslab = L.Ly / ty;
-                    const int n_chunks = std::max(1, slots / n_yslab);
-                    const int zc = (L.Lz + n_chunks - 1) / n_chunks;
-                    for (int f : {1, 2}) {
-                        const int z = std::max(1, zc / f);
-                        if (f > 1 && z == zc) continue;
-                        out.push_back({HS_KERNEL_STAGED, v, 0, ty, z, 0, ring, cw});
-                    }
-                }
-            }
-        }
+                for (int b : {1, 2}) out.push_back({HS_KERNEL_MARCH, v, b, ty, 0});
     }
     return out;
 }
@@ -1838,14 +1618,6 @@ void hs_batch_destroy(hs_batch *b) { delete b; }
 int hs_batch_inject_timeout(hs_batch *b, int on) {
     if (!b) return fail(HS_E_INVALID, "null handle");
     b->inject_timeout = on ? 1 : 0;
-    return HS_OK;
-}
-
-int hs_lattice_inject_timeout(hs_lattice *h, int on) {
-    if (!h) return fail(HS_E_INVALID, "null handle");
-    if (on && h->L.kernel != hs::kStaged && h->L.kernel != hs::kWave)
-        return fail(HS_E_INVALID, "the hook needs the staged or the wavefront kernel");
-    h->inject_timeout = on ? 1 : 0;
     return HS_OK;
 }
 

@@ -348,55 +348,6 @@ __device__ __forceinline__ void load_params(const PassArgs &a, float &J, float &
     beta = a.fbeta;
 }
 
-// ----------------------------------------------------------------- mbarriers
-// Shared-memory mbarrier helpers (arrive has release, a completed wait
-// acquire semantics at CTA scope).
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try(uint64_t *bar, uint32_t parity) {
-    uint32_t done;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(done)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return done != 0;
-}
-
-// Bounded wait on one phase of an mbarrier: gives up after about one second
-// of clock (or 2^26 polls), or as soon as another thread raised the abort
-// flag; a timeout raises the flag itself.
-constexpr long long kWaitCycles = 2000000000LL;
-
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag) {
-    if (mbar_try(bar, parity)) return true;
-    const long long t0 = clock64();
-    for (uint32_t it = 0; it < (1u << 26); ++it) {
-        if (mbar_try(bar, parity)) return true;
-        if (*abort_flag) return false;
-        if (clock64() - t0 > kWaitCycles) break;
-    }
-    *abort_flag = 1;
-    return false;
-}
-
 // ----------------------------------------------------------------- reduction
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll

@@ -71,8 +71,7 @@ struct PassArgs {
     int zpar;                  // parity of (global z - array z), for the colour of a row
     uint32_t site_off;         // global natural index - (array row Lx + x), mod 2^32
     uint32_t rank_off;         // colour rank of a site - (array row Lh + x / 2), mod 2^32
-    int ty, zchunk, n_units;   // staged stencil: slab rows, planes per unit, units
-    int ring_o, ring_w;        // staged stencil: other / own ring slots
+    int ty;                    // z-march stencil: rows per plane-slab
     // table layout
     void *spins4;           // 4-vectors, renumbered order
     const int32_t *nbr;     // [width][n_pad]
@@ -102,10 +101,10 @@ struct PassArgs {
                             // 2: measure only (the sums; a slab whose moments come from all slabs' sums)
     double n_present;
     DevAccum *acc;
-    int inject_extra_tx;    // test hook: extra bytes the first staged fill expects
 };
 
-enum KernelKind { kStencil = 1, kStaged = 2, kTable = 3, kMarch = 4, kPipe = 5, kWave = 6 };
+// codes as in hs_kernel (include/hs.h)
+enum KernelKind { kStencil = 1, kTable = 3, kMarch = 4, kPipe = 5 };
 
 struct Layout {
     bool structured;
@@ -116,16 +115,7 @@ struct Layout {
     int prefetch;           // register stencil: 0 none, 1 next work item in registers, 2 split prefetch
     int tensor;             // 1: the on-site anisotropy tensor term is on (register stencil without
                             //    prefetch, or the neighbour table)
-    // wavefront kernel (kWave): work units of wave_ipu items, wave_U per colour plane, groups of
-    // wave_D passes, lag wave_lag planes, wave_grid CTAs; device buffers owned by the handle
-    int wave_k, wave_ipu, wave_U, wave_D, wave_lag, wave_grid;
-    uint32_t *wave_cnt;     // [Lz] completed units per plane
-    uint32_t *wave_order;   // ticket orders of groups of 1..wave_D passes, concatenated
-    double *wave_slots;     // [wave_max_pass][wave_grid][kPartials]
-    int wave_max_pass;
-    int ty, zchunk, n_units, grid;  // staged stencil tiling and grid
-    int ring_o, ring_w;             // staged stencil ring depths
-    int consumers;                  // staged stencil consumer threads (128 or 256)
+    int ty;                 // z-march stencil: rows per plane-slab
     int n_colours;
     int64_t n_sites, n_present;
     // stencil
@@ -174,34 +164,6 @@ struct BatchArgs {
     int inject_skip;         // test hook: 1 = CTA 0 skips its first barrier arrival
 };
 
-// ---- wavefront kernel (wave.cu)
-// One launch runs n_pass colour passes (whole sweeps) of a periodic FP32 /
-// FP16 sc lattice.  Passes go in groups of D; a unit of work is
-// (pass p, plane z, item range); unit tickets are ordered group by group,
-// inside a group by (position k + lag d, d) with pass d of the group at plane
-// (p + k) mod Lz, so every unit's inputs -- pass p - 1 at planes z-1, z, z+1 --
-// come from earlier tickets.  CTA b takes tickets b, b + grid, ...
-struct WaveArgs {
-    PassArgs a;              // layout, parameters, keys (colour and sweep set per unit)
-    void *planes;            // the six colour-major planes
-    uint32_t n_pi;           // work items of one colour plane: Ly (Lh / V)
-    uint32_t ipu, U;         // items per unit, units per plane
-    uint32_t D, D_last, n_full, n_pass, n_tickets;
-    const uint32_t *order_full, *order_last;  // (d << 20) | k per plane-unit, ticket order
-    uint32_t sweep0;         // sweep index of pass 0
-    uint32_t *cnt;           // [Lz] units completed per plane (zeroed before the launch)
-    double *slots;           // [n_pass][grid][kPartials] per-CTA pass sums (zeroed before the launch)
-    int *error;              // latched device error word
-    DevAccum *acc;
-    int accumulate;
-    double n_present, e[3];
-    int inject_skip;         // test hook: CTA 0 does not count its first finished unit
-};
-cudaError_t launch_wave(int precision, int vec, const WaveArgs &w, int grid, cudaStream_t s);
-cudaError_t launch_wave_finalize(const WaveArgs &w, int grid, cudaStream_t s);
-int wave_occupancy(int precision, int vec);  // resident CTAs per SM (0 = no variant)
-constexpr int kWaveComputeWarps = 15;        // per CTA, plus one control warp
-
 // prefetch 0: one work item of loads at a time; 1: split prefetch (the
 // next item's DRAM-heavy rows load during the current item's arithmetic)
 cudaError_t launch_batch(const BatchArgs &b, int grid, cudaStream_t s, int prefetch);
@@ -229,8 +191,6 @@ cudaError_t launch_measure(int precision, const Layout &L, const PassArgs &a, in
 cudaError_t launch_fold(const PassArgs &a, int n_slots, cudaStream_t s);
 int pass_blocks(int precision, const Layout &L, int n_sm, int blocks_per_sm);
 int pass_occupancy(int precision, const Layout &L, int accumulate);
-size_t staged_smem_bytes(int precision, int ty, int Lh, int ring_o, int ring_w);
-int staged_occupancy(int precision, int vec, size_t smem_bytes, int consumers);  // 0 = does not fit
 size_t pipe_smem_bytes(int precision, int vec);  // dynamic shared memory of the pipelined stencil
 
 }  // namespace hs

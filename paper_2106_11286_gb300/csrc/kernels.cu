@@ -265,7 +265,10 @@ __global__ void __launch_bounds__(kBlock, 2) sc_pipe_kernel(const PassArgs a) {
 // ----------------------------------------------------------------- z-marching stencil pass
 // Register stencil in slab order: the plane-slabs (ty rows of one z plane)
 // of every y slab, z fastest, are split into equal contiguous ranges, one per
-// CTA, so a CTA walks along z.  The other colour's rows at z and z+1, loaded
+// CTA, so a CTA walks along z.  On small lattices it spreads a pass over more
+// SMs than the grid-stride stencil, whose CTAs each take 256 work items (the
+// autotuner picks it for the 16^3 FP64 lattice, which is bound by the FP64
+// pipe of the SMs it runs on).  The other colour's rows at z and z+1, loaded
 // as the z+-1 neighbours of plane z, come back from L1 for plane z+1; only
 // the own plane z+1 and the other colour's plane z+2 are new, and thread 0
 // asks the bulk-copy engine to prefetch those into L2 one plane ahead.
@@ -322,225 +325,6 @@ __global__ void __launch_bounds__(kBlock, 2) sc_march_kernel(const PassArgs a) {
         }
     }
     write_partials<C, MEAS>(a, acc.E(), acc.X(), acc.Y(), acc.Z(), acc.n);
-}
-
-// ----------------------------------------------------------------- staged stencil pass
-// The other colour's planes (and the updated colour's own planes) are staged
-// in shared memory by the bulk-copy (TMA) engine.  A CTA owns a slab of ty
-// rows (full x) of a chunk of z planes and marches along z.  Warp roles:
-//   producer (1 warp): streams planes into two rings -- other-colour slabs of
-//     ty+2 rows (halo rows y0-1 and y0+ty wrap periodically) and own-colour
-//     slabs of ty rows -- as far ahead as free slots allow;
-//   consumers (8 warps): update plane z from the other colour's slabs z-1,
-//     z, z+1 and the own slab z, store accepted vectors to global memory and
-//     hand slots back.
-// Each slot has a "full" mbarrier (bytes landed) and an "empty" mbarrier (all
-// consumer warps done); there is no CTA-wide barrier in the loop.  Every wait
-// is bounded; a timeout raises a shared abort flag that every waiter polls,
-// latches the device error word, and the producer waits (bounded) for the
-// copies it has in flight before the CTA retires.
-
-
-
-__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                     smem_u32(dst)),
-                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
-                 : "memory");
-}
-
-constexpr int kStagedMaxRing = 8;
-
-// CTA shape of the staged kernel: NC consumer threads (4 or 8 warps) plus one
-// producer warp; the minimum resident CTAs keep registers within 128 (4
-// consumer warps, 3 CTAs / SM) or 112 (8 consumer warps, 2 CTAs / SM).
-template <int NC> struct StagedShape;
-template <> struct StagedShape<128> { static constexpr int threads = 160, min_ctas = 3; };
-template <> struct StagedShape<256> { static constexpr int threads = 288, min_ctas = 1; };
-
-// Producer warp: copy plane z of the other colour (ty+2 rows per component)
-// or of the own colour (ty rows) into a slot.  Lane 0 posts the byte count,
-// then lanes issue one row-block copy each.
-template <typename S>
-__device__ __forceinline__ void stage_plane(uint64_t *full, S *dst, const PassArgs &a, int ty, int y0, int z,
-                                            bool other, uint32_t extra_tx = 0) {
-    const int lane = threadIdx.x & 31;
-    const int Ly = a.Ly, Lz = a.Lz, Lh = a.Lh;
-    z = (z % Lz + Lz) % Lz;
-    const uint32_t row_bytes = (uint32_t)Lh * sizeof(S);
-    if (lane == 0) mbar_expect_tx(full, (uint32_t)(3 * (other ? ty + 2 : ty)) * row_bytes + extra_tx);
-    __syncwarp();
-    if (other) {
-        if (lane < 9) {
-            const int q = lane / 3, part = lane % 3;
-            const S *plane = static_cast<const S *>(a.oth[q]);
-            S *d = dst + (size_t)q * (ty + 2) * Lh;
-            if (part == 0) {
-                bulk_g2s(d + Lh, plane + ((size_t)z * Ly + y0) * Lh, (uint32_t)ty * row_bytes, full);
-            } else if (part == 1) {
-                const int y = (y0 == 0) ? Ly - 1 : y0 - 1;
-                bulk_g2s(d, plane + ((size_t)z * Ly + y) * Lh, row_bytes, full);
-            } else {
-                const int y = (y0 + ty == Ly) ? 0 : y0 + ty;
-                bulk_g2s(d + (size_t)(ty + 1) * Lh, plane + ((size_t)z * Ly + y) * Lh, row_bytes, full);
-            }
-        }
-    } else if (lane < 3) {
-        const S *plane = static_cast<const S *>(a.own[lane]);
-        bulk_g2s(dst + (size_t)lane * ty * Lh, plane + ((size_t)z * Ly + y0) * Lh, (uint32_t)ty * row_bytes, full);
-    }
-}
-
-template <int P, int V, bool MEAS, int NC>
-__global__ void __launch_bounds__(StagedShape<NC>::threads, StagedShape<NC>::min_ctas)
-    sc_staged_kernel(const PassArgs a) {
-    pdl_enter();
-    constexpr int kStagedConsumers = NC;
-    constexpr int kStagedThreads = StagedShape<NC>::threads;
-    using S = typename Tr<P>::S;
-    using C = typename Tr<P>::C;
-    using VT = Vec<S, V>;
-    extern __shared__ __align__(128) unsigned char hs_dyn_smem[];
-    __shared__ __align__(8) uint64_t full_o[kStagedMaxRing], empty_o[kStagedMaxRing];
-    __shared__ __align__(8) uint64_t full_w[kStagedMaxRing], empty_w[kStagedMaxRing];
-    __shared__ int s_abort;
-    volatile int *abort_flag = &s_abort;
-    const int Lh = a.Lh, Ly = a.Ly, Lx = a.Lx, ty = a.ty;
-    const int NO = a.ring_o, NW = a.ring_w;
-    const int nxv = Lh / V;
-    const int items = ty * nxv;
-    const int n_yslab = Ly / ty;
-    const int c = a.colour;
-    const size_t oslab = (size_t)3 * (ty + 2) * Lh;  // elements per other-colour slot
-    const size_t wslab = (size_t)3 * ty * Lh;        // elements per own-colour slot
-    S *oth_s = reinterpret_cast<S *>(hs_dyn_smem);
-    S *own_s = oth_s + (size_t)NO * oslab;
-    S *own_g[3] = {(S *)a.own[0], (S *)a.own[1], (S *)a.own[2]};
-    const bool producer = threadIdx.x >= kStagedConsumers;
-    const int lane = threadIdx.x & 31;
-    if (threadIdx.x == 0) {
-        for (int i = 0; i < NO; ++i) {
-            mbar_init(&full_o[i], 1);
-            mbar_init(&empty_o[i], kStagedConsumers / 32);
-        }
-        for (int i = 0; i < NW; ++i) {
-            mbar_init(&full_w[i], 1);
-            mbar_init(&empty_w[i], kStagedConsumers / 32);
-        }
-        s_abort = 0;
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    __syncthreads();
-    C J, K, ex, ey, ez, beta;
-    load_params(a, J, K, ex, ey, ez, beta);
-    SiteAcc<P> acc;
-    uint32_t go = 0, gw = 0;              // planes passed through the other / own rings so far
-    uint32_t issued_o = 0, issued_w = 0;  // planes the producer has put in flight
-    for (int unit = blockIdx.x; unit < a.n_units && !*abort_flag; unit += gridDim.x) {
-        const int y0 = (unit % n_yslab) * ty;
-        const int z0 = (unit / n_yslab) * a.zchunk;
-        const int z1 = min(a.Lz, z0 + a.zchunk);
-        const int n_w = z1 - z0, n_o = n_w + 2;  // own planes z0..z1-1, other planes z0-1..z1
-        if (producer) {
-            // in order of need: other 0, 1, 2, own 0, other 3, own 1, ...
-            int io = 0, iw = 0;
-            while (io < n_o || iw < n_w) {
-                const bool own_next = iw < n_w && io >= min(iw + 3, n_o);
-                if (own_next) {
-                    const uint32_t g = gw + iw, slot = g % NW, fill = g / NW;
-                    if (fill > 0 && !mbar_wait(&empty_w[slot], (fill - 1) & 1, abort_flag)) break;
-                    stage_plane<S>(&full_w[slot], own_s + slot * wslab, a, ty, y0, z0 + iw, false);
-                    ++iw;
-                    issued_w = g + 1;
-                } else {
-                    const uint32_t g = go + io, slot = g % NO, fill = g / NO;
-                    if (fill > 0 && !mbar_wait(&empty_o[slot], (fill - 1) & 1, abort_flag)) break;
-                    // test hook: CTA 0's first fill expects bytes that never come
-                    const uint32_t extra = (g == 0 && blockIdx.x == 0) ? (uint32_t)a.inject_extra_tx : 0u;
-                    stage_plane<S>(&full_o[slot], oth_s + slot * oslab, a, ty, y0, z0 - 1 + io, true, extra);
-                    ++io;
-                    issued_o = g + 1;
-                }
-            }
-        } else {
-            for (int j = 0; j < n_w; ++j) {
-                const uint32_t gm = go + j, g0 = gm + 1, gp = gm + 2, gwj = gw + j;
-                bool ok = true;
-                if (j == 0) {
-                    ok = mbar_wait(&full_o[gm % NO], (gm / NO) & 1, abort_flag) &&
-                         mbar_wait(&full_o[g0 % NO], (g0 / NO) & 1, abort_flag);
-                }
-                ok = ok && mbar_wait(&full_o[gp % NO], (gp / NO) & 1, abort_flag) &&
-                     mbar_wait(&full_w[gwj % NW], (gwj / NW) & 1, abort_flag);
-                if (!ok) break;
-                const int z = z0 + j;
-                const S *Om = oth_s + (gm % NO) * oslab;  // plane z-1
-                const S *O0 = oth_s + (g0 % NO) * oslab;  // plane z
-                const S *Op = oth_s + (gp % NO) * oslab;  // plane z+1
-                const S *W = own_s + (gwj % NW) * wslab;  // own plane z
-                const size_t cs = (size_t)(ty + 2) * Lh;  // component stride (other)
-                const size_t ws = (size_t)ty * Lh;        // component stride (own)
-                for (int it = threadIdx.x; it < items; it += kStagedConsumers) {
-                    const int yl = (int)a.div_nxv.div((uint32_t)it);
-                    const int xh0 = (it - yl * nxv) * V;
-                    const int y = y0 + yl;
-                    const uint32_t p = (uint32_t)(y + z + c) & 1u;
-                    const int xe = p ? ((xh0 + V == Lh) ? 0 : xh0 + V) : ((xh0 == 0) ? Lh - 1 : xh0 - 1);
-                    VT sv[3], o[3], nym[3], nyp[3], nzm[3], nzp[3];
-                    C ed[3];
-#pragma unroll
-                    for (int q = 0; q < 3; ++q) {
-                        const S *r0 = O0 + q * cs + (size_t)(yl + 1) * Lh;
-                        sv[q] = *reinterpret_cast<const VT *>(W + q * ws + (size_t)yl * Lh + xh0);
-                        o[q] = *reinterpret_cast<const VT *>(r0 + xh0);
-                        nym[q] = *reinterpret_cast<const VT *>(r0 - Lh + xh0);
-                        nyp[q] = *reinterpret_cast<const VT *>(r0 + Lh + xh0);
-                        nzm[q] = *reinterpret_cast<const VT *>(Om + q * cs + (size_t)(yl + 1) * Lh + xh0);
-                        nzp[q] = *reinterpret_cast<const VT *>(Op + q * cs + (size_t)(yl + 1) * Lh + xh0);
-                        ed[q] = to_c(r0[xe]);
-                    }
-                    const uint32_t site0 = (uint32_t)((z * Ly + y) * Lx + 2 * xh0) + p;
-                    const uint32_t rank0 = (uint32_t)((z * Ly + y) * Lh + xh0);
-                    if (update_item<P, V, MEAS>(sv, o, nym, nyp, nzm, nzp, ed, p, site0, rank0, c, a, J, K, ex, ey, ez, beta,
-                                                acc)) {
-                        const size_t gi = ((size_t)z * Ly + y) * Lh + xh0;
-#pragma unroll
-                        for (int q = 0; q < 3; ++q) *reinterpret_cast<VT *>(own_g[q] + gi) = sv[q];
-                    }
-                }
-                __syncwarp();
-                if (lane == 0) {  // this warp is done with other plane z-1 and own plane z
-                    mbar_arrive(&empty_o[gm % NO]);
-                    mbar_arrive(&empty_w[gwj % NW]);
-                }
-            }
-            __syncwarp();
-            if (lane == 0 && !*abort_flag) {  // the unit's last two other planes
-                mbar_arrive(&empty_o[(go + n_w) % NO]);
-                mbar_arrive(&empty_o[(go + n_w + 1) % NO]);
-            }
-        }
-        go += n_o;
-        gw += n_w;
-    }
-    if (*abort_flag) {
-        if (threadIdx.x == 0) atomicExch(&a.acc->error, 1);
-        if (producer && lane == 0) {
-            // copies issued into each slot may still land: bounded wait on the
-            // last fill of every slot before the CTA retires
-            int dummy = 0;
-            volatile int *no_abort = &dummy;
-            for (uint32_t s2 = 0; s2 < (uint32_t)NO && s2 < issued_o; ++s2) {
-                const uint32_t fills = (issued_o - s2 + NO - 1) / NO;
-                mbar_wait(&full_o[s2], (fills - 1) & 1, no_abort);
-            }
-            for (uint32_t s2 = 0; s2 < (uint32_t)NW && s2 < issued_w; ++s2) {
-                const uint32_t fills = (issued_w - s2 + NW - 1) / NW;
-                mbar_wait(&full_w[s2], (fills - 1) & 1, no_abort);
-            }
-        }
-    }
-    write_partials<C, MEAS, kStagedThreads>(a, acc.E(), acc.X(), acc.Y(), acc.Z(), acc.n);
 }
 
 // ----------------------------------------------------------------- table pass
@@ -898,18 +682,6 @@ cudaError_t launch_sc_v(const PassArgs &a, int n_blocks, cudaStream_t s, bool me
     return launch_sc_pf<P, V, 0>(a, n_blocks, s, meas);
 }
 
-template <int P, int V, int NC>
-cudaError_t launch_staged_nc(const Layout &L, const PassArgs &a, cudaStream_t s, bool meas) {
-    const size_t smem = staged_smem_bytes(P, L.ty, L.Lh, L.ring_o, L.ring_w);
-    return meas ? launch_pdl(sc_staged_kernel<P, V, true, NC>, L.grid, StagedShape<NC>::threads, smem, s, a)
-                : launch_pdl(sc_staged_kernel<P, V, false, NC>, L.grid, StagedShape<NC>::threads, smem, s, a);
-}
-
-template <int P, int V>
-cudaError_t launch_staged_v(const Layout &L, const PassArgs &a, cudaStream_t s, bool meas) {
-    return L.consumers == 128 ? launch_staged_nc<P, V, 128>(L, a, s, meas) : launch_staged_nc<P, V, 256>(L, a, s, meas);
-}
-
 template <int P, int V>
 cudaError_t launch_pipe_v(const PassArgs &a, int n_blocks, cudaStream_t s, bool meas) {
     const size_t smem = PipeSlot<P, V>::kBytes;
@@ -946,17 +718,7 @@ cudaError_t launch_pass_p(const Layout &L, const PassArgs &a, int n_blocks, cuda
         }
         return cudaErrorInvalidValue;
     }
-    if (L.kernel == kStaged) {
-        switch (L.vec) {
-        case 1: return launch_staged_v<P, 1>(L, a, s, meas);
-        case 2: return launch_staged_v<P, 2>(L, a, s, meas);
-        case 4: if constexpr (P != HS_FP64) return launch_staged_v<P, 4>(L, a, s, meas); break;
-        case 8: if constexpr (P == HS_FP16) return launch_staged_v<P, 8>(L, a, s, meas); break;
-        default: break;
-        }
-        return cudaErrorInvalidValue;
-    }
-    if (L.kernel == kStencil || L.kernel == kWave) {  // the wavefront kernel's single passes
+    if (L.kernel == kStencil) {
         switch (L.vec) {
         case 1: return launch_sc_v<P, 1>(a, n_blocks, s, meas, L.prefetch, L.tensor != 0);
         case 2: return launch_sc_v<P, 2>(a, n_blocks, s, meas, L.prefetch, L.tensor != 0);
@@ -976,29 +738,6 @@ cudaError_t launch_pass_p(const Layout &L, const PassArgs &a, int n_blocks, cuda
                 : launch_pdl(table_pass_kernel<P, false>, n_blocks, kBlock, 0, s, a);
 }
 
-template <int P, int NC>
-const void *staged_ptr_nc(int vec, bool meas) {
-    switch (vec) {
-    case 1: return meas ? (const void *)sc_staged_kernel<P, 1, true, NC> : (const void *)sc_staged_kernel<P, 1, false, NC>;
-    case 2: return meas ? (const void *)sc_staged_kernel<P, 2, true, NC> : (const void *)sc_staged_kernel<P, 2, false, NC>;
-    case 4:
-        if constexpr (P != HS_FP64)
-            return meas ? (const void *)sc_staged_kernel<P, 4, true, NC> : (const void *)sc_staged_kernel<P, 4, false, NC>;
-        break;
-    case 8:
-        if constexpr (P == HS_FP16)
-            return meas ? (const void *)sc_staged_kernel<P, 8, true, NC> : (const void *)sc_staged_kernel<P, 8, false, NC>;
-        break;
-    default: break;
-    }
-    return nullptr;
-}
-
-template <int P>
-const void *staged_ptr(int vec, bool meas, int consumers) {
-    return consumers == 128 ? staged_ptr_nc<P, 128>(vec, meas) : staged_ptr_nc<P, 256>(vec, meas);
-}
-
 }  // namespace
 
 cudaError_t launch_fold(const PassArgs &a, int n_slots, cudaStream_t s) {
@@ -1012,37 +751,6 @@ cudaError_t launch_fold(const PassArgs &a, int n_slots, cudaStream_t s) {
 
 size_t storage_size(int precision) {
     return precision == HS_FP64 ? 8 : (precision == HS_FP32 ? 4 : 2);
-}
-
-// ring_o other-colour slots of ty+2 rows and ring_w own-colour slots of ty
-// rows, 3 components each, rows of Lh elements.
-size_t staged_smem_bytes(int precision, int ty, int Lh, int ring_o, int ring_w) {
-    return (size_t)(ring_o * 3 * (ty + 2) + ring_w * 3 * ty) * (size_t)Lh * storage_size(precision);
-}
-
-int staged_occupancy(int precision, int vec, size_t smem_bytes, int consumers) {
-    int dev = 0, optin = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
-    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return 0;
-    if (smem_bytes + 2048 > (size_t)optin) return 0;
-    int occ = 8;
-    for (int m = 0; m < 2; ++m) {
-        const void *k = nullptr;
-        switch (precision) {
-        case HS_FP64: k = staged_ptr<HS_FP64>(vec, m != 0, consumers); break;
-        case HS_FP32: k = staged_ptr<HS_FP32>(vec, m != 0, consumers); break;
-        case HS_FP16: k = staged_ptr<HS_FP16>(vec, m != 0, consumers); break;
-        default: break;
-        }
-        if (!k) return 0;
-        if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes) != cudaSuccess)
-            return 0;
-        int b = 0;
-        const int threads = consumers == 128 ? StagedShape<128>::threads : StagedShape<256>::threads;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k, threads, smem_bytes) != cudaSuccess) return 0;
-        occ = std::min(occ, b);
-    }
-    return occ;
 }
 
 static int64_t pass_items(const Layout &L) {
@@ -1132,7 +840,7 @@ static const void *pass_kernel_ptr(const Layout &L, bool meas) {
         }
         return nullptr;
     }
-    if (L.kernel == kStencil || L.kernel == kWave) {
+    if (L.kernel == kStencil) {
         switch (L.vec) {
         case 1: return sc_ptr<P, 1>(meas, L.prefetch, L.tensor != 0);
         case 2: return sc_ptr<P, 2>(meas, L.prefetch, L.tensor != 0);

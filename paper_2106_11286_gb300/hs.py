@@ -46,15 +46,14 @@ class hs_measurement(ctypes.Structure):
 
 class hs_launch(ctypes.Structure):
     _fields_ = [("kernel", ctypes.c_int), ("vec_width", ctypes.c_int), ("blocks_per_sm", ctypes.c_int),
-                ("tile_y", ctypes.c_int), ("chunk_z", ctypes.c_int), ("prefetch", ctypes.c_int),
-                ("ring", ctypes.c_int), ("consumers", ctypes.c_int)]
+                ("tile_y", ctypes.c_int), ("prefetch", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
-HS_KERNEL_AUTO, HS_KERNEL_STENCIL, HS_KERNEL_STAGED, HS_KERNEL_TABLE, HS_KERNEL_MARCH = 0, 1, 2, 3, 4
-KERNELS = {"auto": 0, "stencil": 1, "staged": 2, "table": 3, "march": 4, "pipe": 5, "wave": 6}
+HS_KERNEL_AUTO, HS_KERNEL_STENCIL, HS_KERNEL_TABLE, HS_KERNEL_MARCH, HS_KERNEL_PIPE = 0, 1, 3, 4, 5
+KERNELS = {"auto": 0, "stencil": 1, "table": 3, "march": 4, "pipe": 5}
 
 
 class hs_info(ctypes.Structure):
@@ -113,7 +112,6 @@ SIGNATURES = {
     "hs_sweep_sc_fp32_noalloc": (ctypes.c_int, [_vp, _i32p, ctypes.POINTER(hs_params), ctypes.c_double,
                                                  ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int64,
                                                  _vp, _vp]),
-    "hs_lattice_inject_timeout": (ctypes.c_int, [_vp, ctypes.c_int]),
     "hs_batch_inject_timeout": (ctypes.c_int, [_vp, ctypes.c_int]),
     "hs_measure_alu_peak": (ctypes.c_int, [ctypes.c_int, _vp, ctypes.POINTER(ctypes.c_double)]),
     "hs_slab_pack": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _vp]),
@@ -334,11 +332,9 @@ def hs_read_timing(h):
     return ms.value, n.value
 
 
-def hs_set_launch(h, kernel=0, vec_width=0, blocks_per_sm=0, tile_y=0, chunk_z=0, prefetch=0, ring=0,
-                  consumers=0):
+def hs_set_launch(h, kernel=0, vec_width=0, blocks_per_sm=0, tile_y=0, prefetch=0):
     k = KERNELS[kernel] if isinstance(kernel, str) else int(kernel)
-    cfg = hs_launch(k, int(vec_width), int(blocks_per_sm), int(tile_y), int(chunk_z), int(prefetch), int(ring),
-                    int(consumers))
+    cfg = hs_launch(k, int(vec_width), int(blocks_per_sm), int(tile_y), int(prefetch))
     _check(load().hs_set_launch(h, ctypes.byref(cfg)))
 
 
@@ -460,10 +456,6 @@ def hs_batch_set_layout(b, ctas_per_sm, align_rows=0, prefetch=0, schedule=0):
 
 def hs_batch_destroy(b):
     load().hs_batch_destroy(b)
-
-
-def hs_lattice_inject_timeout(h, on=True):
-    _check(load().hs_lattice_inject_timeout(h, int(bool(on))))
 
 
 def hs_batch_inject_timeout(b, on=True):

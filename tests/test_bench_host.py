@@ -13,7 +13,7 @@ def test_kernel_labels():
     assert bench.kernel_label(dict(base, prefetch=1)) == "sc_pass_kernel<1, 4, 1, 1, 0>"
     assert bench.kernel_label(dict(base, prefetch=2)) == "sc_pass_kernel<1, 4, 1, 0, 0>"
     assert bench.kernel_label(dict(kernel=5, vec_width=8, prefetch=0)) == "sc_pipe_kernel"
-    assert bench.kernel_label(dict(kernel=6, vec_width=4, prefetch=0)) == "sc_wave_kernel"
+    assert bench.kernel_label(dict(kernel=3, vec_width=1, prefetch=1)) == "table_pass_kernel"
 
 
 def test_traffic_only_for_the_captured_sources_and_kernel(tmp_path, monkeypatch):

@@ -65,7 +65,6 @@ FP32_LAUNCHES = {
     "stencil_split": dict(kernel="stencil", vec_width=4, prefetch=3),
     "pipe": dict(kernel="pipe", vec_width=4),
     "march": dict(kernel="march", vec_width=4),
-    "staged": dict(kernel="staged", vec_width=4),
 }
 
 

@@ -293,14 +293,6 @@ def _launch_configs(precision, dims):
             if dims[1] % ty == 0:
                 out += [dict(kernel="march", vec_width=v, tile_y=ty), dict(kernel="march", vec_width=v, tile_y=ty,
                                                                            blocks_per_sm=1)]
-        if (lh * es) % 16 == 0:
-            for ty in (1, 2, 4):
-                if dims[1] % ty == 0:
-                    out += [dict(kernel="staged", vec_width=v, tile_y=ty),
-                            dict(kernel="staged", vec_width=v, tile_y=ty, chunk_z=1, ring=4),
-                            dict(kernel="staged", vec_width=v, tile_y=ty, chunk_z=3, ring=6, consumers=8)]
-        if v * es == 16 and precision != "fp64" and dims[2] >= 3:
-            out += [dict(kernel="wave", vec_width=v), dict(kernel="wave", vec_width=v, tile_y=1, chunk_z=3, ring=3)]
     return out
 
 
@@ -310,11 +302,11 @@ def _launch_configs(precision, dims):
                                             ("fp32", (288, 16, 4)), ("fp16", (288, 8, 6))])
 def test_launch_configuration_does_not_change_results(precision, dims):
     """A site's random numbers and arithmetic depend only on its natural index,
-    so every kernel, vector width, slab and chunk gives bit-identical chains;
-    the autotuner restores the state it perturbs."""
+    so every kernel, vector width, CTA count, slab and prefetch mode gives
+    bit-identical chains; the autotuner restores the state it perturbs."""
     outs = []
     cfgs = _launch_configs(precision, dims)
-    assert all(any(c["kernel"] == k for c in cfgs) for k in ("staged", "pipe"))
+    assert all(any(c["kernel"] == k for c in cfgs) for k in ("stencil", "pipe", "march"))
     for cfg in cfgs:
         with hs.Lattice("sc", dims=dims, K=0.1, precision=precision, seed=6) as lat:
             lat.set_launch(**cfg)
@@ -357,20 +349,3 @@ def test_table_launch_configuration_does_not_change_results(precision, kind, dim
             outs.append(lat.get_spins())
     for S, cfg in zip(outs[1:], cfgs[1:]):
         assert np.array_equal(S, outs[0]), cfg
-
-
-def test_staged_kernel_parity_large(orc):
-    """Staged kernel on a lattice with several slabs and chunks, one FP64 sweep
-    against the oracle."""
-    dims = (16, 24, 20)
-    g = orc.lattice("sc", dims)
-    S0 = inputs.random_unit_spins(g.n, 12)
-    with hs.Lattice("sc", dims=dims, precision="fp64", seed=3, **PARAMS) as lat:
-        lat.set_launch(kernel="staged", tile_y=4, chunk_z=3, ring=4)
-        lat.set_spins(S0)
-        lat.sweep(0.7, 1)
-        got = lat.get_spins()
-    want = S0.copy()
-    band = np.zeros(g.n, dtype=np.uint8)
-    orc.sweep(g, want, beta=0.7, seed=3, sweep_index=0, band=1e-9, band_site=band, **PARAMS)
-    check_sweep_parity(g, S0, got, want, band, 1e-12)

@@ -87,7 +87,7 @@ def test_tensor_launch_rules():
                                       [0.15, -0.20, 0.05, 0.30, -0.10, 0.25])
         L = lat.launch
         assert L["kernel"] == hs.KERNELS["stencil"] and L["prefetch"] == 2
-        for bad in (dict(kernel="staged"), dict(kernel="pipe"), dict(kernel="march"),
+        for bad in (dict(kernel="pipe"), dict(kernel="march"), dict(kernel=2), dict(kernel=6),
                     dict(kernel="stencil", prefetch=3)):
             with pytest.raises(hs.HSError):
                 lat.set_launch(**bad)
