@@ -307,9 +307,14 @@ void hs_batch_destroy(hs_batch *b);
 
 /* Batch autotuner: the batch's work split -- its members' work items (4
  * sites of one row of one colour), concatenated and cut into one contiguous
- * range per CTA -- is timed for every CTA count per SM (1 up to the kernel's
- * occupancy), both cut rules (at any item, or moved to the nearest row
- * boundary), both load schedules of the kernel (one work item of loads at a
+ * range per CTA, or interleaved -- is timed for every CTA count per SM (1 up
+ * to the kernel's occupancy), the three splits (align_rows 0: contiguous
+ * ranges cut at any item; 1: cut at the nearest row boundary; 2: contiguous
+ * ranges of whole 256-item blocks cut at equal estimated cost (an item of a
+ * member with r work items per row weighs 1 + 3 / r), then the blocks of the
+ * CTAs that hold nothing but one member dealt out to them round-robin, so
+ * they sweep that member side by side in grid-stride order), both load
+ * schedules of the kernel (one work item of loads at a
  * time, or split prefetch: the next item's own, same-row and z+-1 rows load
  * during the current item's arithmetic) and both colour schedules (schedule
  * 0: every sweep in one persistent cooperative launch, passes separated by
@@ -322,11 +327,12 @@ void hs_batch_destroy(hs_batch *b);
  * had not happened (spins are identical under every choice; the FP64 sums
  * are taken in each split's own fixed order).  Synchronous.
  * hs_batch_get_layout reads the choice in use (hs_batch_create starts with
- * the maximum CTAs per SM, cuts at any item, no prefetch, schedule 0). */
+ * the maximum CTAs per SM, the interleaved split (align_rows 2), no
+ * prefetch, schedule 0). */
 int hs_batch_autotune(hs_batch *b, const double *betas, int n_trial_sweeps);
 int hs_batch_get_layout(const hs_batch *b, int *ctas_per_sm, int *align_rows, int *prefetch, int *schedule);
 /* Set the choice by hand: ctas_per_sm in 1 .. the kernel's occupancy,
- * align_rows, prefetch and schedule 0 or 1 (HS_E_INVALID otherwise).  The
+ * align_rows 0, 1 or 2, prefetch and schedule 0 or 1 (HS_E_INVALID otherwise).  The
  * members' chains do not depend on it.  The timeout test hook always runs
  * the persistent schedule.  Synchronises the batch's stream. */
 int hs_batch_set_layout(hs_batch *b, int ctas_per_sm, int align_rows, int prefetch, int schedule);

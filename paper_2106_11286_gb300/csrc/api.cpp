@@ -1300,6 +1300,74 @@ namespace {
 // range per CTA, ctas_per_sm CTAs per SM; with align_rows the cuts are moved
 // to the nearest row boundary of the member they fall in, so no row is split
 // between two CTAs.  Segment = (CTA, member) piece, with its own FP64 slot.
+// Interleaved split (align_rows 2): a contiguous split at whole blocks of
+// kBlock items, cut at equal estimated cost per CTA (an item of a member with
+// r work items per row weighs 1 + 3 / r: on the 64-replica batch of L = 16 ...
+// 96, weights of 1 + 2 / r, 1 + 3 / r and 1 + 4.5 / r measured 133.7, 136.4
+// and 135.9 attempts/ns, equal weights 128.1), then, within each member, the blocks of the CTAs that hold
+// nothing but that member are dealt out to them round-robin (CTA j of G takes
+// blocks j, j + G, ...), so those CTAs sweep the member side by side in
+// grid-stride order, as one lattice's grid-stride loop does, instead of on
+// separate fronts; a CTA shared with another member keeps its contiguous
+// piece.  Every CTA keeps its share (to within one block).  segs come
+// out member by member in ascending CTA order, seg_cta holds each one's CTA.
+void interleaved_layout(int grid, const std::vector<int64_t> &items, const std::vector<int64_t> &row,
+                        std::vector<hs::BatchSeg> &segs, std::vector<int> &seg_cta) {
+    const int n = (int)items.size();
+    const int64_t K = hs::kBlock;
+    std::vector<int64_t> nb(n), A(n + 1, 0);
+    std::vector<double> w(n), cw(n + 1, 0.0);
+    for (int m = 0; m < n; ++m) {
+        nb[m] = (items[m] + K - 1) / K;
+        A[m + 1] = A[m] + nb[m];
+        // estimated cost of an item: short rows (small members) cost more per
+        // site (their operands stay in L2 latency, their rows have more edges)
+        w[m] = 1.0 + 3.0 / (double)row[m];
+        cw[m + 1] = cw[m] + (double)nb[m] * w[m];
+    }
+    const int64_t B = A[n];
+    // cut points in blocks at equal estimated cost per CTA
+    std::vector<int64_t> cut(grid + 1, 0);
+    for (int c = 1, m = 0; c < grid; ++c) {
+        const double T = (double)c * cw[n] / grid;
+        while (m < n - 1 && cw[m + 1] <= T) ++m;
+        const int64_t blk = A[m] + (int64_t)((T - cw[m]) / w[m] + 0.5);
+        cut[c] = std::min(B, std::max(cut[c - 1], blk));
+    }
+    cut[grid] = B;
+    int c = 0;
+    for (int m = 0; m < n; ++m) {
+        const int64_t a0 = A[m], a1 = A[m + 1];
+        while (cut[c + 1] <= a0) ++c;
+        struct Piece { int cta; int64_t p0, p1; bool full; };
+        std::vector<Piece> pieces;
+        for (int cc = c; cc < grid && cut[cc] < a1; ++cc) {
+            const int64_t p0 = std::max(cut[cc], a0), p1 = std::min(cut[cc + 1], a1);
+            if (p1 > p0) pieces.push_back({cc, p0, p1, p0 == cut[cc] && p1 == cut[cc + 1]});
+        }
+        int G = 0;
+        int64_t F0 = 0, F1 = 0;
+        for (const Piece &p : pieces)
+            if (p.full) {
+                if (G == 0) F0 = p.p0;
+                F1 = p.p1;
+                ++G;
+            }
+        int j = 0;
+        for (const Piece &p : pieces) {
+            if (p.full && G >= 2) {
+                segs.push_back({m, (uint32_t)((F0 - a0 + j) * K), (uint32_t)std::min((F1 - a0) * K, items[m]),
+                                (uint32_t)(G * K)});
+                ++j;
+            } else {
+                segs.push_back({m, (uint32_t)((p.p0 - a0) * K), (uint32_t)std::min((p.p1 - a0) * K, items[m]),
+                                (uint32_t)K});
+            }
+            seg_cta.push_back(p.cta);
+        }
+    }
+}
+
 int batch_layout(hs_batch *b, int ctas_per_sm, int align_rows) {
     const int n = (int)b->members.size();
     const int grid = b->members[0]->n_sm * ctas_per_sm;
@@ -1311,6 +1379,21 @@ int batch_layout(hs_batch *b, int ctas_per_sm, int align_rows) {
         offset[r + 1] = offset[r] + items[r];
     }
     const int64_t total = offset[n];
+    std::vector<hs::BatchSeg> segs;
+    std::vector<int> cta_seg(grid + 1, 0);
+    if (align_rows == 2) {
+        // segments member by member and in ascending CTA order: each CTA's and
+        // each member's are contiguous (kernel and finalise)
+        std::vector<int> seg_cta;
+        interleaved_layout(grid, items, row, segs, seg_cta);
+        for (int m = 0; m < n; ++m) b->host_members[m].seg_begin = b->host_members[m].seg_end = 0;
+        for (size_t k = 0; k < segs.size(); ++k) {
+            hs::BatchMember &hm = b->host_members[segs[k].member];
+            if (k == 0 || segs[k - 1].member != segs[k].member) hm.seg_begin = (int)k;
+            hm.seg_end = (int)k + 1;
+            ++cta_seg[seg_cta[k] + 1];
+        }
+    } else {
     const int64_t chunk = (total + grid - 1) / grid;
     std::vector<int64_t> bnd(grid + 1);
     bnd[0] = 0;
@@ -1325,19 +1408,18 @@ int batch_layout(hs_batch *b, int ctas_per_sm, int align_rows) {
         }
         bnd[c] = std::max(pos, bnd[c - 1]);
     }
-    std::vector<hs::BatchSeg> segs;
-    std::vector<int> cta_seg(grid + 1, 0);
     int c = 0;
     for (int m = 0; m < n; ++m) {
         b->host_members[m].seg_begin = (int)segs.size();
         for (int64_t g = offset[m]; g < offset[m + 1];) {
             while (bnd[c + 1] <= g) ++c;
             const int64_t g_end = std::min(offset[m + 1], bnd[c + 1]);
-            segs.push_back({m, (uint32_t)(g - offset[m]), (uint32_t)(g_end - offset[m])});
+            segs.push_back({m, (uint32_t)(g - offset[m]), (uint32_t)(g_end - offset[m]), (uint32_t)hs::kBlock});
             ++cta_seg[c + 1];
             g = g_end;
         }
         b->host_members[m].seg_end = (int)segs.size();
+    }
     }
     for (int k = 0; k < grid; ++k) cta_seg[k + 1] += cta_seg[k];
     HS_CUDA(cudaStreamSynchronize(b->stream));
@@ -1428,7 +1510,7 @@ int hs_batch_create(hs_batch **out, hs_lattice *const *members, int n_members) {
         delete b;
         return cuda_fail(e, "cudaStreamCreate");
     }
-    if (int st = batch_layout(b, occ, 0)) {
+    if (int st = batch_layout(b, occ, 2)) {  // the interleaved split, measured fastest on every tested batch
         delete b;
         return st;
     }
@@ -1559,7 +1641,7 @@ int hs_batch_autotune(hs_batch *b, const double *betas, int n_trial_sweeps) {
     for (int sc = 0; st == HS_OK && sc <= 1; ++sc)
     for (int pf = 0; st == HS_OK && pf <= 1; ++pf)
     for (int c = 1; st == HS_OK && c <= b->occ; ++c)
-        for (int al = 0; st == HS_OK && al <= 1; ++al) {
+        for (int al = 0; st == HS_OK && al <= 2; ++al) {
             b->prefetch = pf;
             b->schedule = sc;
             if ((st = batch_layout(b, c, al))) break;
@@ -1597,8 +1679,8 @@ int hs_batch_autotune(hs_batch *b, const double *betas, int n_trial_sweeps) {
 int hs_batch_set_layout(hs_batch *b, int ctas_per_sm, int align_rows, int prefetch, int schedule) {
     if (!b) return fail(HS_E_INVALID, "null handle");
     if (ctas_per_sm < 1 || ctas_per_sm > b->occ) return fail(HS_E_INVALID, "ctas_per_sm out of range");
-    if ((align_rows != 0 && align_rows != 1) || (prefetch != 0 && prefetch != 1) || (schedule != 0 && schedule != 1))
-        return fail(HS_E_INVALID, "align_rows, prefetch and schedule must be 0 or 1");
+    if (align_rows < 0 || align_rows > 2 || (prefetch != 0 && prefetch != 1) || (schedule != 0 && schedule != 1))
+        return fail(HS_E_INVALID, "align_rows must be 0, 1 or 2, prefetch and schedule 0 or 1");
     b->prefetch = prefetch;
     b->schedule = schedule;
     return batch_layout(b, ctas_per_sm, align_rows);

@@ -193,7 +193,7 @@ __device__ __forceinline__ void batch_pass(const BatchArgs &b, int s, int c) {
                     item_fields<P, V>(A.o, nym, nyp, A.nzm, A.nzp, A.ed, A.f.p, h);
                     VT sv[3] = {A.s[0], A.s[1], A.s[2]};
                     const uint32_t b0 = A.f.b0, site0 = A.f.site0, rank0 = A.f.rank0;
-                    const uint32_t tn = t + kBlock;
+                    const uint32_t tn = t + sg.stride;
                     const bool more = tn < sg.end;
                     if (more) load_split_a<P, V, CG>(a, tn, own, oth, A);  // the neighbour vectors are dead
                     if (update_item_h<P, V, true>(sv, h, site0, rank0, c, a, J, K, ex, ey, ez, beta, acc)) {
@@ -205,7 +205,7 @@ __device__ __forceinline__ void batch_pass(const BatchArgs &b, int s, int c) {
                 }
             }
         } else {
-            for (uint32_t t = sg.begin + threadIdx.x; t < sg.end; t += kBlock) {
+            for (uint32_t t = sg.begin + threadIdx.x; t < sg.end; t += sg.stride) {
                 StencilItem<P, V> it;
                 load_item<P, V, CG>(a, t, own, oth, it);
                 if (update_item<P, V, true>(it.s, it.o, it.nym, it.nyp, it.nzm, it.nzp, it.ed, it.p, it.site0,

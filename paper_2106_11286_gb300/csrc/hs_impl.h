@@ -145,10 +145,13 @@ struct BatchMember {
     int seg_begin, seg_end;  // the member's segments (contiguous)
 };
 
-// Item range [begin, end) of one member's colour pass processed by one CTA.
+// Items begin, begin + stride, ... (< end) of one member's colour pass,
+// each the first of kBlock consecutive items that one CTA's threads take
+// together: stride kBlock for a contiguous range; a multiple of kBlock when
+// several CTAs sweep one member side by side.
 struct BatchSeg {
     int member;
-    uint32_t begin, end;
+    uint32_t begin, end, stride;
 };
 
 struct BatchArgs {
