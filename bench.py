@@ -13,7 +13,10 @@ between steps.
 Prints one JSON line (rank 0).  Under torchrun (N > 1) every rank advances
 its own replica of the workload (replica index = rank; no data-path
 collective) and the whole-job value is the attempts of all ranks over the
-slowest rank's time ("scaling": "weak").
+slowest rank's time ("scaling": "weak"); beside it, variants.slab_strong
+times one sc 1024^3 lattice split into z-slabs over the ranks, halos
+exchanged by NCCL after every colour pass (strong scaling).  The headline is
+the median of --repeats regions of exactly --steps steps.
 
 ``--impl reference`` times the CPU oracle (the plain FP64 C program that
 defines the expected results) on this machine's host cores instead, each step
