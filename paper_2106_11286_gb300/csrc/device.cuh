@@ -166,7 +166,17 @@ __device__ __forceinline__ void sincos_l(float2 a, float2 &s, float2 &c) {
 }
 __device__ __forceinline__ float half_round(float x) { return __half2float(__float2half_rn(x)); }
 __device__ __forceinline__ float half_round_l(float x) { return half_round(x); }
-__device__ __forceinline__ float2 half_round_l(float2 x) { return make_float2(half_round(x.x), half_round(x.y)); }
+// both lanes rounded to binary16 by one packed conversion (each lane rounded
+// to nearest even, as the scalar form), then widened exactly
+__device__ __forceinline__ float2 half_round_l(float2 x) { return __half22float2(__float22half2_rn(x)); }
+
+// c + a for a binary16 a, with one rounding: the mixed-precision add widens a
+// exactly, so the result equals f_add(c, (float)a) bit for bit.
+__device__ __forceinline__ float add_half(float c, __half a) {
+    float d;
+    asm("add.rn.f32.f16 %0, %1, %2;" : "=f"(d) : "h"(__half_as_ushort(a)), "f"(c));
+    return d;
+}
 
 // FP32 schedule: one Philox block serves two sites of the same colour.  The
 // site of rank r within its colour class (ascending natural index) uses
@@ -574,6 +584,23 @@ __device__ __forceinline__ void item_fields(const Vec<typename Tr<P>::S, V> (&o)
                 h[q][k] = ((((xm_of(k, q) + xp_of(k, q)) + to_c(nym[q].v[k])) + to_c(nyp[q].v[k])) +
                            to_c(nzm[q].v[k])) +
                           to_c(nzp[q].v[k]);
+    } else if constexpr (P == HS_FP16) {
+        // binary16 operands added straight into the FP32 sum (add_half: one
+        // rounding per add, the same sums as widening each operand first)
+#pragma unroll
+        for (int k = 0; k < V; ++k)
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                float t = xm_of(k, q);
+                if (k == V - 1)
+                    t = p ? f_add(t, ed[q]) : add_half(t, o[q].v[k]);
+                else
+                    t = add_half(t, p ? o[q].v[k + 1] : o[q].v[k]);
+                t = add_half(t, nym[q].v[k]);
+                t = add_half(t, nyp[q].v[k]);
+                t = add_half(t, nzm[q].v[k]);
+                h[q][k] = add_half(t, nzp[q].v[k]);
+            }
     } else if constexpr (V >= 2) {
 #pragma unroll
         for (int j = 0; j < V / 2; ++j) {
