@@ -15,7 +15,9 @@ its own replica of the workload (replica index = rank; no data-path
 collective) and the whole-job value is the attempts of all ranks over the
 slowest rank's time ("scaling": "weak"); beside it, variants.slab_strong
 times one sc 1024^3 lattice split into z-slabs over the ranks, halos
-exchanged by NCCL after every colour pass (strong scaling).  The headline is
+exchanged by NCCL after every colour pass (strong scaling; one rank: one
+slab, its own periodic neighbour), and the same with the boundary planes
+updated first and their exchange beside the interior update.  The headline is
 the median of --repeats regions of exactly --steps steps.
 
 ``--impl reference`` times the CPU oracle (the plain FP64 C program that
@@ -82,9 +84,14 @@ def kernel_label(launch, precision_code=1, measure=1):
     return name
 
 
-def read_traffic(kernel=None):
+ORDERS = {1: "ascending", 2: "alternating"}
+
+
+def read_traffic(kernel=None, order=None, key="dram_bytes_per_launch"):
     """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel sources and on this kernel (else None)."""
+    on the current kernel sources, on this kernel and in this order of the
+    work items (hs_launch.order), else None.  key: the live figure (caches
+    as the previous pass left them) or cold_dram_bytes_per_launch."""
     try:
         kv = {}
         for line in open(TRAFFIC_FILE):
@@ -95,7 +102,9 @@ def read_traffic(kernel=None):
             return None
         if kernel is not None and kv.get("kernel", "") != kernel and not kv.get("kernel", "").startswith(kernel + "<"):
             return None
-        return float(kv["dram_bytes_per_launch"])
+        if order is not None and kv.get("order") != ORDERS.get(order):
+            return None
+        return float(kv[key])
     except (OSError, KeyError, ValueError):
         return None
 
@@ -254,7 +263,8 @@ def run_ours(args):
     peaks, peak_kind = measured_peaks()
     achieved_gbs = alg_bytes / (kernel_ms * 1e-3) / 1e9
     kname = KERNEL_NAMES.get(launch["kernel"], "sc_pass_kernel") if launch else "sc_pass_kernel"
-    traffic = read_traffic(kernel_label(launch) if launch else None)
+    traffic = read_traffic(kernel_label(launch), launch.get("order")) if launch else None
+    traffic_cold = read_traffic(kernel_label(launch), launch.get("order"), "cold_dram_bytes_per_launch") if launch else None
     roofline = {"bound": "hbm", "achieved": round(achieved_gbs, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": round(achieved_gbs / peaks["hbm_gbs"], 4), "traffic": traffic,
                 "peak_source": f"{peak_kind} copy bandwidth", "kernel": kernel_label(launch) if launch else kname,
@@ -263,7 +273,11 @@ def run_ours(args):
                                  f"the ring folds of the fused sums, one per {fold} sweeps)",
                 "kernel_ms_bracketed": round(kernel_ms_bracketed, 5),
                 "regions_ms": [round(x, 4) for x in region_ms],
-                "frac_of_8TBs_nominal": round(achieved_gbs / 8000.0, 4), "launch": launch}
+                "frac_of_8TBs_nominal": round(achieved_gbs / 8000.0, 4), "launch": launch,
+                "traffic_what": "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch with the caches as the "
+                                "previous pass left them (--cache-control none), the timed steady state; "
+                                "traffic_cold: the same launch from a flushed L2",
+                "traffic_cold": traffic_cold}
     # the other bounds of the same launches: the acceptance-weighted minimum 2 s + a s per attempt (rejected
     # sites need no store) and the traffic measured by ncu
     acc_rate = meas["accept_rate"]
@@ -345,11 +359,12 @@ def run_ours(args):
     variants = None if args.no_variants else run_variants(args, rank, stream, barrier_sync, world, dev)
     if variants is not None:
         variants["noalloc"] = noalloc_run(args, stream)
-        if world > 1:
-            try:
-                variants["slab_strong"] = slab_strong_run(args, rank, world, stream, barrier_sync)
-            except Exception as ex:  # the replica figure above stands on its own
-                variants["slab_strong"] = {"error": repr(ex)[:300]}
+        try:
+            strong = slab_strong_run(args, rank, world, stream, barrier_sync, overlap=False)
+            strong["overlap_value"] = slab_strong_run(args, rank, world, stream, barrier_sync, overlap=True)["value"]
+            variants["slab_strong"] = strong
+        except Exception as ex:  # the replica figure above stands on its own
+            variants["slab_strong"] = {"error": repr(ex)[:300]}
 
     if world > 1:
         import torch.distributed as dist
@@ -606,15 +621,17 @@ def noalloc_run(args, stream):
                     "reductions finished by the last-arriving CTA of each sweep in static scratch"}
 
 
-def slab_strong_run(args, rank, world, stream, barrier_sync):
+def slab_strong_run(args, rank, world, stream, barrier_sync, overlap=True):
     """One sc 1024^3 FP32 lattice split into z-slabs, one per rank, halos
     exchanged with NCCL after every colour pass (shards.DistributedSlab):
-    strong scaling of one lattice, beside the replica figure."""
+    strong scaling of one lattice, beside the replica figure.  overlap: the
+    boundary planes first, their exchange on a communication stream beside
+    the interior update (one rank: the slab's own halo copies)."""
     from paper_2106_11286_gb300 import shards
     L = 1024
     w = WORKLOAD
     ds = shards.DistributedSlab((L, L, L), J=w["J"], K=w["K"], e=w["e"], precision="fp32", seed=6,
-                                stream=stream)
+                                stream=stream, overlap=overlap)
     try:
         ds.init()
         beta = 1.0 / w["T"]
@@ -629,9 +646,12 @@ def slab_strong_run(args, rank, world, stream, barrier_sync):
     finally:
         ds.close()
     return {"value": round(float(L) ** 3 * args.huge_sweeps / (s_max * 1e9), 3), "unit": UNIT, "ranks": world,
-            "n_spins": L ** 3, "sweeps": args.huge_sweeps, "scaling": "strong",
+            "n_spins": L ** 3, "sweeps": args.huge_sweeps, "scaling": "strong", "overlap": overlap,
             "what": "one sc 1024^3 FP32 lattice in z-slabs, packed halo planes by stream-ordered NCCL "
-                    "send/recv after every colour pass; wall clock over the slowest rank"}
+                    "send/recv after every colour pass" + (", boundary planes first, the exchange beside the "
+                                                           "interior update" if overlap else "") +
+                    "; wall clock over the slowest rank (overlap_value: boundary planes first, the exchange "
+                    "beside the interior update)"}
 
 
 # ------------------------------------------------------------------ CPU oracle
@@ -853,7 +873,7 @@ def config1_run(args):
 
 def beta_runs(args):
     """The paper's M(T) curves and its critical exponent: sc 64^3 and 128^3
-    (and 256^3 below T_c), K = 0.01 (the paper's anisotropy), ordered start,
+    (and 256^3 and 512^3 below T_c), K = 0.01 (the paper's anisotropy), ordered start,
     temperatures from 1.20 to just above T_c, all in one persistent FP32
     batch per call.  T_c comes from the Binder crossing of 64^3 and 128^3;
     beta from the paper's log-log fit of <|M|> on T_c - T over the points
@@ -879,11 +899,19 @@ def beta_runs(args):
         b256, e256, _ = scan.beta_fit(big, 0, range(len(fit_idx)), tc=tc)
         out.update({"beta_256_at_tc": round(b256, 4), "beta_256_stat_err": round(e256, 4)})
         curves["256"] = [round(float(big.absM[(0, j)].mean()), 5) for j in range(len(fit_idx))]
+        # the paper's largest lattice: 512^3 (1.3 x 10^8 spins per temperature, 9.7 GB for the six)
+        huge = scan.run_scan((512,), [temps[j] for j in fit_idx], n_equil=args.beta_equil // 3,
+                             n_blocks=4, block_sweeps=args.beta_block_sweeps // 2, replicas=1, K=0.01, seed=79,
+                             init="aligned")
+        b512, e512, _ = scan.beta_fit(huge, 0, range(len(fit_idx)), tc=tc)
+        out.update({"beta_512_at_tc": round(b512, 4), "beta_512_stat_err": round(e512, 4)})
+        curves["512"] = [round(float(huge.absM[(0, j)].mean()), 5) for j in range(len(fit_idx))]
     out.update({"paper": {"beta": "0.364 +- 0.002", "tc": 1.445, "K": 0.01},
                 "fit_temps": [temps[j] for j in fit_idx], "temps": list(temps), "absM": curves,
                 "seconds": round(time.perf_counter() - t, 1),
                 "what": "paper's log-log fit of <|M|> on T_c - T; K = 0.01, J = 1, e = z; 2 replicas of 64^3 and "
-                        "128^3 per temperature, 1 of 256^3 (fit at the crossing T_c, its error not propagated)"})
+                        "128^3 per temperature, 1 of 256^3 and of 512^3 (fit at the crossing T_c, its error not "
+                        "propagated)"})
     return out
 
 

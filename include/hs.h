@@ -244,11 +244,17 @@ typedef struct {
                           computing the current one, 3 = split prefetch (the
                           next item's own, same-row and z+-1 rows loaded once
                           the current item's fields are summed), 2 = off,
-                          0 = automatic (split prefetch for FP32 when a
-                          CTA's work items span at least 8 rows, else off);
+                          0 = automatic (off);
                           table: 1 = ask L2 for the next site's table row
                           and spin ahead, 2 = off, 0 = automatic (on for FP32
                           tables of at most 8 neighbours) */
+    int order;         /* stencil: order of the work items over a sweep:
+                          1 = every pass in ascending (z, y, x) order,
+                          2 = alternating (the passes of colour 1 descending,
+                          so each pass begins on the planes that the pass
+                          before it touched last, which are still in L2),
+                          0 = automatic (alternating; ascending with the
+                          split prefetch) */
 } hs_launch;
 
 /* Set (fields 0 = automatic) or read the launch configuration.  Kernel
@@ -402,18 +408,56 @@ int hs_slab_create(hs_lattice **out, const int32_t dims[3], int32_t z0, int32_t 
  * multi-device run sends these (own 1 / 2 to the neighbours' halos 3 / 0). */
 int hs_slab_plane(const hs_lattice *h, int colour, int component, int which, void **dev_ptr, size_t *bytes);
 /* Copy the three component planes of colour `colour` from plane src_which of
- * src to plane dst_which of dst (same lattice and device), on dst's stream:
+ * src to plane dst_which of dst (same lattice and device), on dst's
+ * communication stream (hs_slab_set_comm_stream; by default its stream):
  * the halo exchange of slabs that share a device. */
 int hs_slab_copy_plane(hs_lattice *dst, int dst_which, const hs_lattice *src, int src_which, int colour);
 /* One message per halo transfer between processes: hs_slab_pack copies the
  * three component planes (x, y, z) of colour `colour` at plane `which` (as
  * for hs_slab_plane) back to back into the caller's device buffer d_buf
  * (3 x the plane bytes hs_slab_plane reports); hs_slab_unpack copies such a
- * buffer into plane `which` of this slab.  Device-to-device copies ordered on
- * the handle's stream, so a stream-ordered send (NCCL) of d_buf needs no host
- * synchronisation. */
+ * buffer into plane `which` of this slab.  One strided device-to-device copy
+ * each, ordered on the handle's communication stream (hs_slab_set_comm_stream;
+ * by default its stream), so a stream-ordered send (NCCL) of d_buf needs no
+ * host synchronisation. */
 int hs_slab_pack(const hs_lattice *h, int colour, int which, void *d_buf);
 int hs_slab_unpack(hs_lattice *h, int colour, int which, const void *d_buf);
+
+/* Boundary-first colour pass of a slab.  A colour pass updates only sites of
+ * its colour and reads only the other colour, so its order over the planes
+ * does not change the result: the pass may run as part HS_PART_BOUNDARY
+ * (the first and last own planes) followed by HS_PART_INTERIOR (the planes
+ * between them), both on the slab's stream.  Once the boundary part is done
+ * the colour's boundary planes are final, so their messages can travel
+ * (hs_slab_pack on the communication stream, a send, hs_slab_unpack of the
+ * received halos of the same colour) while the interior part runs: the
+ * interior part reads and writes neither those planes nor the halos of its
+ * own colour.  The next colour's pass must follow both the interior part
+ * (stream order) and the unpacked halos (the caller's event).
+ * HS_PART_WHOLE is the whole pass in one launch (= hs_sweep_pass).  Each
+ * part keeps its own partial sums; the launch that completes the last
+ * colour's pass finalises the sweep from the parts run in it, so the fused
+ * sums and the spins equal those of whole passes bit for bit.
+ * HS_E_INVALID: a part other than HS_PART_WHOLE on a non-slab lattice, an
+ * interior part not directly after the boundary part of the same colour,
+ * or a boundary or whole part while an interior part is due.  A slab of one
+ * or two planes has no interior: its boundary part covers it and its
+ * interior part launches nothing. */
+#define HS_PART_WHOLE 0
+#define HS_PART_BOUNDARY 1
+#define HS_PART_INTERIOR 2
+int hs_sweep_pass_part(hs_lattice *h, double beta, int colour, int part);
+/* CTAs that the interior part leaves unlaunched (0 <= ctas < the pass's CTA
+ * count; default 0), so that the communication's copy and send kernels find
+ * free SMs beside it instead of waiting for its persistent CTAs to retire. */
+int hs_slab_reserve_ctas(hs_lattice *h, int32_t ctas);
+/* Stream on which hs_slab_pack, hs_slab_unpack and hs_slab_copy_plane (into
+ * this slab) run: by default the slab's own stream; NULL selects the legacy
+ * default stream, as elsewhere in this API.  With a separate stream the
+ * caller orders those copies against the passes with events, keeps the
+ * stream alive while the slab uses it, and synchronises it before
+ * hs_lattice_destroy (which waits only for the slab's own stream). */
+int hs_slab_set_comm_stream(hs_lattice *h, void *cuda_stream);
 
 /* Stream-ordered forms of the sums exchange of a multi-process lattice:
  * hs_read_sums_device copies the last finalised sweep's five sums (as

@@ -208,6 +208,12 @@ struct hs_lattice {
     double *partials = nullptr;
     DevAccum *acc = nullptr;
     double *stage = nullptr;  // 3 * n_sites doubles, lazily for host copies
+    // z-slab: parts of colour passes and the halo copies
+    uint64_t sets_written = 0;      // partial sets written in the current sweep
+    int interior_due = -1;          // colour whose interior part must come next (-1: none)
+    int reserve = 0;                // CTAs the interior part leaves unlaunched
+    cudaStream_t comm = nullptr;    // stream of the pack / unpack / plane copies
+    int64_t max_pitch = 0;          // largest pitch of a strided copy (device attribute)
     int64_t device_bytes = 0;
     std::vector<void *> allocations;
     // timing
@@ -392,8 +398,19 @@ int default_vec(const hs_lattice *h) {
     return 1;
 }
 
+// Zero a slab's partial sets: a launch of fewer CTAs than the set's stride
+// relies on the rest of its set reading zero.
+int clear_slab_sets(hs_lattice *h) {
+    if (!h->L.slab || !h->partials) return HS_OK;
+    const size_t n = (size_t)2 * hs::kSlabSets * h->max_blocks * hs::kPartials;
+    HS_CUDA(cudaMemsetAsync(h->partials, 0, n * sizeof(double), h->stream));
+    return HS_OK;
+}
+
 int configure_launch(hs_lattice *h) {
     Layout &L = h->L;
+    if (L.slab && (h->sets_written != 0 || h->interior_due >= 0))
+        return fail(HS_E_INVALID, "a slab's sweep is in progress");
     const hs_launch &r = h->req;
     L.tensor = h->tensor;
     if (!L.structured) {
@@ -453,21 +470,19 @@ int configure_launch(hs_lattice *h) {
         return HS_OK;
     }
     L.kernel = hs::kStencil;  // before the occupancy query, which looks at the kind
-    // request 1 = next item in registers, 3 = split prefetch, 2 = off;
-    // automatic: split prefetch when a CTA's items span 8 rows or more, so the
-    // y-1 / y+1 rows it loads late are mostly its own (measured faster at
-    // 256^3 FP32, slower at 464^3 and 1024^3)
-    if (h->tensor)
+    // request 1 = next item in registers, 3 = split prefetch, 2 = off; automatic: off (with the alternating
+    // order, which lets each pass start on data in L2, no prefetch measured fastest at 256^3 and 464^3 FP32)
+    if (h->tensor || r.prefetch == 0)
         L.prefetch = 0;
-    else if (r.prefetch == 0)
-        L.prefetch = (h->precision == HS_FP32 && L.Lh / L.vec <= hs::kBlock / 8) ? 2 : 0;
     else
         L.prefetch = r.prefetch == 1 ? 1 : (r.prefetch == 3 ? 2 : 0);
+    // automatic order: alternating, except with the split prefetch, which measured slower in descending passes
+    L.order = r.order != 0 ? r.order : (L.prefetch == 2 ? 1 : 2);
     int bps = r.blocks_per_sm;
     const int occ = std::min(hs::pass_occupancy(h->precision, L, 0), hs::pass_occupancy(h->precision, L, 1));
     if (bps <= 0 || bps > occ) bps = occ;
     h->n_blocks = std::min(hs::pass_blocks(h->precision, L, h->n_sm, bps), h->max_blocks);
-    return HS_OK;
+    return clear_slab_sets(h);  // the parts' grids follow the launch configuration
 }
 
 int flush_timing(hs_lattice *h) {
@@ -591,12 +606,16 @@ int lattice_create(hs_lattice **out, int type, const int32_t dims[3], int period
     h->seed = seed;
     h->replica = replica;
     h->stream = (cudaStream_t)cuda_stream;
+    h->comm = h->stream;
     {
+        int pitch = 0;
         cudaError_t e = cudaDeviceGetAttribute(&h->n_sm, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&pitch, cudaDevAttrMaxPitch, dev);
         if (e != cudaSuccess) {
             delete h;
             return cuda_fail(e, "cudaDeviceGetAttribute");
         }
+        h->max_pitch = pitch;
     }
     int st = HS_OK;
     Layout &L = h->L;
@@ -636,6 +655,8 @@ int lattice_create(hs_lattice **out, int type, const int32_t dims[3], int period
         const size_t slot_doubles = (size_t)L.n_colours * h->max_blocks * hs::kPartials;
         const size_t fit = (size_t)(8u << 20) / (slot_doubles * sizeof(double));
         h->fold_ring = (int)std::max<size_t>(1, std::min<size_t>(hs::kRingMax, fit));
+        // a slab sweeps pass by pass (no ring) but keeps kSlabSets partial sets per colour in slot 0
+        if (L.slab) h->fold_ring = std::max(h->fold_ring, hs::kSlabSets);
         st = h->alloc(&h->partials, (slot_doubles + hs::kSweepRecord) * (size_t)h->fold_ring * sizeof(double));
         if (st == HS_OK) st = configure_launch(h);
     }
@@ -721,6 +742,11 @@ int run_pass(hs_lattice *h, PassArgs &a, uint32_t sweep, int c, bool deferred = 
             a.own[q] = base + (size_t)(3 * c + q) * plane * es;
             a.oth[q] = base + (size_t)(3 * (1 - c) + q) * plane * es;
         }
+        // alternating order: colour 1 runs from the last work item down, so it starts on the planes that
+        // colour 0 touched last (in L2), and the next sweep's colour 0 starts where colour 1 ended
+        a.rev = (L.kernel == hs::kStencil && L.order == 2 && c == 1)
+                    ? (uint32_t)((int64_t)a.nz * L.Ly * (L.Lh / L.vec) - 1)
+                    : 0u;
     } else {
         a.begin = L.colour_begin[c];
         a.end = L.colour_begin[c + 1];
@@ -776,24 +802,114 @@ int hs_sweep(hs_lattice *h, double beta, int64_t n_sweeps) {
     return HS_OK;
 }
 
-int hs_sweep_pass(hs_lattice *h, double beta, int colour) {
+namespace {
+// CTAs of a stencil launch over n_planes own planes of a slab, at most cap.
+int plane_grid(const hs_lattice *h, int n_planes, int cap) {
+    const int64_t items = (int64_t)n_planes * h->L.Ly * (h->L.Lh / h->L.vec);
+    return (int)std::max<int64_t>(1, std::min<int64_t>((items + hs::kBlock - 1) / hs::kBlock, cap));
+}
+
+// One launch of colour c of a slab over its own array planes z_first ..
+// z_first + n_planes - 1 (1 .. nz), on `grid` CTAs, its partials in set
+// `set` of that colour.  finish: this launch completes the sweep, so its
+// last CTA folds the sets written in it.
+int run_slab_launch(hs_lattice *h, PassArgs a, int c, int set, int z_first, int n_planes, int grid, bool finish) {
+    const Layout &L = h->L;
+    a.sweep = (uint32_t)h->sweep;
+    a.colour = c;
+    a.n_colours = 2 * hs::kSlabSets;
+    a.pass = hs::kSlabSets * c + set;
+    a.slot = 0;
+    a.z_off = z_first;
+    a.nz = n_planes;
+    h->sets_written |= 1ull << a.pass;
+    a.finish = finish ? 1 : 0;
+    a.skip_sets = ~h->sets_written;
+    const size_t es = hs::storage_size(h->precision);
+    const int64_t plane = (int64_t)L.Lz * L.Ly * L.Lh;
+    char *base = static_cast<char *>(L.planes);
+    for (int q = 0; q < 3; ++q) {
+        a.own[q] = base + (size_t)(3 * c + q) * plane * es;
+        a.oth[q] = base + (size_t)(3 * (1 - c) + q) * plane * es;
+    }
+    if (h->timing) {
+        int st = record_event(h);
+        if (st) return st;
+    }
+    HS_CUDA(hs::launch_pass(h->precision, L, a, grid, h->stream));
+    if (h->timing) {
+        int st = record_event(h);
+        if (st) return st;
+    }
+    return HS_OK;
+}
+
+}  // namespace
+
+int hs_sweep_pass(hs_lattice *h, double beta, int colour) { return hs_sweep_pass_part(h, beta, colour, HS_PART_WHOLE); }
+
+int hs_sweep_pass_part(hs_lattice *h, double beta, int colour, int part) {
     if (!h) return fail(HS_E_INVALID, "null handle");
     if (int st = check_beta(beta)) return st;
     if (colour < 0 || colour >= h->L.n_colours) return fail(HS_E_INVALID, "colour out of range");
-    if (colour == 0) {
+    if (part != HS_PART_WHOLE && part != HS_PART_BOUNDARY && part != HS_PART_INTERIOR)
+        return fail(HS_E_INVALID, "part must be HS_PART_WHOLE, HS_PART_BOUNDARY or HS_PART_INTERIOR");
+    const Layout &L = h->L;
+    if (part != HS_PART_WHOLE && !L.slab) return fail(HS_E_INVALID, "boundary and interior parts are slab passes");
+    if (part == HS_PART_INTERIOR ? h->interior_due != colour : h->interior_due >= 0)
+        return fail(HS_E_INVALID, "a boundary part must be followed by the interior part of its colour");
+    const bool last = colour == L.n_colours - 1;
+    if (colour == 0 && part != HS_PART_INTERIOR) {
         h->last_n_sweeps = 1;
+        h->sets_written = 0;
         HS_CUDA(cudaMemsetAsync(&h->acc->accepted, 0, sizeof(double), h->stream));
     }
-    if (h->L.n_present > 0) {
+    if (L.n_present > 0) {
         PassArgs a = base_args(h);
         a.beta = beta;
         a.fbeta = (float)beta;
         // a slab always measures its fused sums (the observables of a lattice split into slabs come from
         // all slabs' sums); only accumulation adds its own moments
-        a.accumulate = h->accumulate ? 1 : (h->L.slab ? 2 : 0);
-        if (int st = run_pass(h, a, (uint32_t)h->sweep, colour)) return st;
+        a.accumulate = h->accumulate ? 1 : (L.slab ? 2 : 0);
+        if (!L.slab) {
+            if (int st = run_pass(h, a, (uint32_t)h->sweep, colour)) return st;
+        } else if (part == HS_PART_WHOLE) {
+            if (int st = run_slab_launch(h, a, colour, 3, 1, L.nz, h->n_blocks, last)) return st;
+        } else if (part == HS_PART_BOUNDARY) {
+            if (L.nz <= 2) {  // the boundary planes are the whole slab: one launch, no interior
+                if (int st = run_slab_launch(h, a, colour, 0, 1, L.nz, plane_grid(h, L.nz, h->n_blocks), last))
+                    return st;
+            } else {
+                const int g = plane_grid(h, 1, h->n_blocks);
+                if (int st = run_slab_launch(h, a, colour, 0, 1, 1, g, false)) return st;
+                if (int st = run_slab_launch(h, a, colour, 1, L.nz, 1, g, false)) return st;
+            }
+        } else if (L.nz > 2) {
+            const int g = plane_grid(h, L.nz - 2, std::max(1, h->n_blocks - h->reserve));
+            if (int st = run_slab_launch(h, a, colour, 2, 2, L.nz - 2, g, last)) return st;
+        }
     }
-    if (colour == h->L.n_colours - 1) h->sweep += 1;
+    h->interior_due = part == HS_PART_BOUNDARY ? colour : -1;
+    if (last && part != HS_PART_BOUNDARY) {
+        h->sweep += 1;
+        h->sets_written = 0;
+    }
+    return HS_OK;
+}
+
+int hs_slab_reserve_ctas(hs_lattice *h, int32_t ctas) {
+    if (!h) return fail(HS_E_INVALID, "null handle");
+    if (!h->L.slab) return fail(HS_E_INVALID, "not a slab");
+    if (ctas < 0 || ctas >= h->n_blocks) return fail(HS_E_INVALID, "reserve 0 .. the pass's CTAs - 1");
+    if (h->sets_written != 0 || h->interior_due >= 0) return fail(HS_E_INVALID, "a sweep is in progress");
+    h->reserve = ctas;
+    return clear_slab_sets(h);
+}
+
+int hs_slab_set_comm_stream(hs_lattice *h, void *cuda_stream) {
+    if (!h) return fail(HS_E_INVALID, "null handle");
+    if (!h->L.slab) return fail(HS_E_INVALID, "not a slab");
+    h->comm = (cudaStream_t)cuda_stream;
     return HS_OK;
 }
 
@@ -811,43 +927,56 @@ int hs_slab_plane(const hs_lattice *h, int colour, int component, int which, voi
     return HS_OK;
 }
 
+namespace {
+// Copy the three component planes of one colour at one z plane between
+// (dst, dst_pitch) and (src, src_pitch) -- addresses of component x, pitch
+// = bytes from one component's plane to the next -- as one strided copy, or
+// three when a pitch exceeds the device's largest.
+int copy_components(const hs_lattice *h, void *dst, size_t dst_pitch, const void *src, size_t src_pitch,
+                    size_t bytes, cudaStream_t s) {
+    if ((int64_t)std::max(dst_pitch, src_pitch) <= h->max_pitch) {
+        HS_CUDA(cudaMemcpy2DAsync(dst, dst_pitch, src, src_pitch, bytes, 3, cudaMemcpyDeviceToDevice, s));
+        return HS_OK;
+    }
+    for (int q = 0; q < 3; ++q)
+        HS_CUDA(cudaMemcpyAsync(static_cast<char *>(dst) + q * dst_pitch, static_cast<const char *>(src) + q * src_pitch,
+                                bytes, cudaMemcpyDeviceToDevice, s));
+    return HS_OK;
+}
+
+// bytes from one component's plane array to the next (the colour-major layout)
+size_t component_pitch(const hs_lattice *h) {
+    return (size_t)h->L.Lz * h->L.Ly * h->L.Lh * hs::storage_size(h->precision);
+}
+}  // namespace
+
 int hs_slab_copy_plane(hs_lattice *dst, int dst_which, const hs_lattice *src, int src_which, int colour) {
     if (!dst || !src) return fail(HS_E_INVALID, "null handle");
     if (!dst->L.slab || !src->L.slab) return fail(HS_E_INVALID, "not a slab");
     if (dst->precision != src->precision || dst->L.Lx != src->L.Lx || dst->L.Ly != src->L.Ly ||
         dst->device != src->device)
         return fail(HS_E_INVALID, "slabs of different lattices or devices");
-    for (int q = 0; q < 3; ++q) {
-        void *d = nullptr, *sp = nullptr;
-        size_t nb = 0, ns = 0;
-        if (int st = hs_slab_plane(dst, colour, q, dst_which, &d, &nb)) return st;
-        if (int st = hs_slab_plane(src, colour, q, src_which, &sp, &ns)) return st;
-        HS_CUDA(cudaMemcpyAsync(d, sp, nb, cudaMemcpyDeviceToDevice, dst->stream));
-    }
-    return HS_OK;
+    void *d = nullptr, *sp = nullptr;
+    size_t nb = 0, ns = 0;
+    if (int st = hs_slab_plane(dst, colour, 0, dst_which, &d, &nb)) return st;
+    if (int st = hs_slab_plane(src, colour, 0, src_which, &sp, &ns)) return st;
+    return copy_components(dst, d, component_pitch(dst), sp, component_pitch(src), nb, dst->comm);
 }
 
 int hs_slab_pack(const hs_lattice *h, int colour, int which, void *d_buf) {
     if (!h || !d_buf) return fail(HS_E_INVALID, "null argument");
-    for (int q = 0; q < 3; ++q) {
-        void *sp = nullptr;
-        size_t nb = 0;
-        if (int st = hs_slab_plane(h, colour, q, which, &sp, &nb)) return st;
-        HS_CUDA(cudaMemcpyAsync(static_cast<char *>(d_buf) + q * nb, sp, nb, cudaMemcpyDeviceToDevice, h->stream));
-    }
-    return HS_OK;
+    void *sp = nullptr;
+    size_t nb = 0;
+    if (int st = hs_slab_plane(h, colour, 0, which, &sp, &nb)) return st;
+    return copy_components(h, d_buf, nb, sp, component_pitch(h), nb, h->comm);
 }
 
 int hs_slab_unpack(hs_lattice *h, int colour, int which, const void *d_buf) {
     if (!h || !d_buf) return fail(HS_E_INVALID, "null argument");
-    for (int q = 0; q < 3; ++q) {
-        void *dp = nullptr;
-        size_t nb = 0;
-        if (int st = hs_slab_plane(h, colour, q, which, &dp, &nb)) return st;
-        HS_CUDA(cudaMemcpyAsync(dp, static_cast<const char *>(d_buf) + q * nb, nb, cudaMemcpyDeviceToDevice,
-                                h->stream));
-    }
-    return HS_OK;
+    void *dp = nullptr;
+    size_t nb = 0;
+    if (int st = hs_slab_plane(h, colour, 0, which, &dp, &nb)) return st;
+    return copy_components(h, dp, component_pitch(h), d_buf, nb, nb, h->comm);
 }
 
 int hs_read_sums_device(hs_lattice *h, double *d_out) {
@@ -1054,6 +1183,7 @@ int hs_set_launch(hs_lattice *h, const hs_launch *cfg) {
         return fail(HS_E_INVALID, "blocks_per_sm out of range");
     if (cfg->tile_y < 0) return fail(HS_E_INVALID, "negative tile_y");
     if (cfg->prefetch < 0 || cfg->prefetch > 3) return fail(HS_E_INVALID, "prefetch must be 0, 1, 2 or 3");
+    if (cfg->order < 0 || cfg->order > 2) return fail(HS_E_INVALID, "order must be 0, 1 or 2");
     const hs_launch keep = h->req;
     const Layout keep_l = h->L;
     const int keep_b = h->n_blocks;
@@ -1113,6 +1243,7 @@ int hs_get_launch(const hs_lattice *h, hs_launch *out) {
     out->prefetch = (L.kernel == hs::kStencil || L.kernel == hs::kTable)
                         ? (L.prefetch == 1 ? 1 : (L.prefetch == 2 ? 3 : 2))
                         : 0;
+    out->order = L.kernel == hs::kStencil ? L.order : 0;
     return HS_OK;
 }
 

@@ -372,19 +372,21 @@ __device__ __forceinline__ double warp_sum(double v) {
 
 // Totals of one ring slot (one sweep of a.n_colours passes, or a standalone
 // measurement), executed by one whole CTA: every CTA's partials of every
-// pass, summed in a fixed order (so the FP64 totals do not depend on
-// scheduling); the result is valid in thread 0.
+// partial set not in a.skip_sets, summed in a fixed order (so the FP64
+// totals do not depend on scheduling); the result is valid in thread 0.
 template <int NT = kBlock>
 __device__ void slot_totals(const PassArgs &a, int slot, double (&tot)[kPartials]) {
     __shared__ double s_fin[NT / 32][kPartials];
     double t[kPartials] = {0.0, 0.0, 0.0, 0.0, 0.0};
     const double *base = a.partials + (size_t)slot * a.n_colours * a.n_blocks * kPartials;
-    for (int p = 0; p < a.n_colours; ++p)
+    for (int p = 0; p < a.n_colours; ++p) {
+        if ((a.skip_sets >> p) & 1ull) continue;
         for (int b = threadIdx.x; b < a.n_blocks; b += NT) {
             const double *ps = base + ((size_t)p * a.n_blocks + b) * kPartials;
 #pragma unroll
             for (int q = 0; q < kPartials; ++q) t[q] += __ldcg(ps + q);
         }
+    }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int q = 0; q < kPartials; ++q) t[q] = warp_sum(t[q]);
@@ -475,7 +477,9 @@ struct AccRegs {
 };
 
 // Finalise a single colour pass sequence or a standalone measurement inside
-// its last kernel: the last CTA to arrive folds the slots.
+// its last kernel: the last of its CTAs to arrive folds the slots.  Every
+// earlier launch of the sequence ran on the same stream and has completed
+// (griddepcontrol.wait at kernel entry), so only this launch's CTAs count.
 template <int NT = kBlock>
 __device__ void finish_reduction(const PassArgs &a, bool measured) {
     __shared__ int s_last;
@@ -483,7 +487,7 @@ __device__ void finish_reduction(const PassArgs &a, bool measured) {
     __syncthreads();
     if (threadIdx.x == 0) {
         const unsigned ticket = atomicAdd(&a.acc->done, 1u);
-        s_last = (ticket == (unsigned)a.n_blocks - 1u);
+        s_last = (ticket == gridDim.x - 1u);
     }
     __syncthreads();
     if (!s_last) return;
@@ -862,10 +866,12 @@ __device__ __forceinline__ void load_item_at(const PassArgs &a, uint32_t y, uint
     it.rank0 = f.rank0;
 }
 
-// The work item with linear index t = (z Ly + y) (Lh/V) + xv.
+// The work item with linear index t = (z Ly + y) (Lh/V) + xv (rev - t in a
+// descending pass).
 template <int P, int V, bool CG = false>
 __device__ __forceinline__ void load_item(const PassArgs &a, uint32_t t, const typename Tr<P>::S *const (&own)[3],
                                           const typename Tr<P>::S *const (&oth)[3], StencilItem<P, V> &it) {
+    t = a.rev ? a.rev - t : t;  // a descending pass
     const uint32_t nxv = a.Lh / V;
     const uint32_t r = a.div_nxv.div(t);
     const uint32_t xv = t - r * nxv;
@@ -891,6 +897,7 @@ __device__ __forceinline__ void load_split_a(const PassArgs &a, uint32_t t, cons
                                              const typename Tr<P>::S *const (&oth)[3], SplitItem<P, V> &A) {
     using S = typename Tr<P>::S;
     using VT = Vec<S, V>;
+    t = a.rev ? a.rev - t : t;  // a descending pass
     const uint32_t nxv = a.Lh / V;
     const uint32_t r = a.div_nxv.div(t);
     const uint32_t xv = t - r * nxv;

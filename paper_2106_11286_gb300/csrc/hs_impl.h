@@ -26,6 +26,9 @@ constexpr int kPartials = 5;  // E, Sx, Sy, Sz, accepted
 constexpr int kRingMax = 64;  // sweeps whose slots a ring fold takes at most
 constexpr int kSweepRecord = kPartials + 8;  // a ring fold's per-sweep record: totals, observables
 constexpr int kBlock = 256;   // threads per CTA of the sweep kernels
+// partial-sum sets per colour of a z-slab: first own plane, last own plane,
+// the planes between them, the whole slab in one launch
+constexpr int kSlabSets = 4;
 
 // Division by a runtime constant d (1 <= d < 2^31) of numerators n < 2^31
 // by multiply-high and shift: with l = ceil(log2 d) and m = ceil(2^(31+l)/d)
@@ -72,6 +75,8 @@ struct PassArgs {
     uint32_t site_off;         // global natural index - (array row Lx + x), mod 2^32
     uint32_t rank_off;         // colour rank of a site - (array row Lh + x / 2), mod 2^32
     int ty;                    // z-march stencil: rows per plane-slab
+    uint32_t rev;              // register stencil: nonzero = work items in descending order, item t taken as
+                               // rev - t (rev = items - 1)
     // table layout
     void *spins4;           // 4-vectors, renumbered order
     const int32_t *nbr;     // [width][n_pad]
@@ -91,12 +96,15 @@ struct PassArgs {
     float fA[6];
     const double2 *sc_tab;  // FP64 trial: sin, cos(pi j / 128), j = 0..255
     uint32_t key0, key1, replica, sweep;
-    double *partials;       // [ring slots][n_colours][n_blocks][kPartials]
+    double *partials;       // [ring slots][n_colours][n_blocks][kPartials]; a slab has kSlabSets sets per colour
+                            // (pass = kSlabSets colour + set, n_colours = 2 kSlabSets); a launch of fewer CTAs
+                            // than n_blocks leaves the rest of its set zero
     double *sweep_tot;      // [ring slots][kSweepRecord]: per-sweep records of a ring fold
     int pass;               // colour index = partial slot
     int slot;               // ring slot: the sweep's index within its fold group (0 for single passes)
     int n_blocks;
-    int finish;             // 1: last pass of the sequence, the last CTA to arrive reduces and finalises
+    int finish;             // 1: last launch of the sequence, its last CTA to arrive reduces and finalises
+    uint64_t skip_sets;     // finaliser: partial sets of the slot left out (bit p = set p; not written this sweep)
     int accumulate;         // 0: no fused measurement; 1: measure and add the moments to the accumulator;
                             // 2: measure only (the sums; a slab whose moments come from all slabs' sums)
     double n_present;
@@ -116,6 +124,7 @@ struct Layout {
     int tensor;             // 1: the on-site anisotropy tensor term is on (register stencil without
                             //    prefetch, or the neighbour table)
     int ty;                 // z-march stencil: rows per plane-slab
+    int order;              // register stencil: 1 ascending passes, 2 alternating (colour 1 descending)
     int n_colours;
     int64_t n_sites, n_present;
     // stencil

@@ -46,7 +46,7 @@ class hs_measurement(ctypes.Structure):
 
 class hs_launch(ctypes.Structure):
     _fields_ = [("kernel", ctypes.c_int), ("vec_width", ctypes.c_int), ("blocks_per_sm", ctypes.c_int),
-                ("tile_y", ctypes.c_int), ("prefetch", ctypes.c_int)]
+                ("tile_y", ctypes.c_int), ("prefetch", ctypes.c_int), ("order", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -115,6 +115,9 @@ SIGNATURES = {
     "hs_batch_inject_timeout": (ctypes.c_int, [_vp, ctypes.c_int]),
     "hs_measure_alu_peak": (ctypes.c_int, [ctypes.c_int, _vp, ctypes.POINTER(ctypes.c_double)]),
     "hs_slab_pack": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _vp]),
+    "hs_sweep_pass_part": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_int, ctypes.c_int]),
+    "hs_slab_reserve_ctas": (ctypes.c_int, [_vp, ctypes.c_int32]),
+    "hs_slab_set_comm_stream": (ctypes.c_int, [_vp, _vp]),
     "hs_slab_unpack": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _vp]),
     "hs_read_sums_device": (ctypes.c_int, [_vp, _vp]),
     "hs_accumulate_sums": (ctypes.c_int, [_vp, _vp, ctypes.c_int64]),
@@ -200,6 +203,24 @@ def hs_sweep(h, beta, n_sweeps=1):
 
 def hs_sweep_pass(h, beta, colour):
     _check(load().hs_sweep_pass(h, float(beta), int(colour)))
+
+
+# parts of a slab's colour pass (hs_sweep_pass_part)
+HS_PART_WHOLE, HS_PART_BOUNDARY, HS_PART_INTERIOR = 0, 1, 2
+
+
+def hs_sweep_pass_part(h, beta, colour, part):
+    _check(load().hs_sweep_pass_part(h, float(beta), int(colour), int(part)))
+
+
+def hs_slab_reserve_ctas(h, ctas):
+    _check(load().hs_slab_reserve_ctas(h, int(ctas)))
+
+
+def hs_slab_set_comm_stream(h, stream):
+    """Stream of the slab's pack / unpack / plane copies (a torch.cuda.Stream,
+    a raw handle, or None for the legacy default stream)."""
+    _check(load().hs_slab_set_comm_stream(h, _stream_handle(stream)))
 
 
 def hs_slab_create(dims, z0, nz, J=1.0, K=0.0, e=(0.0, 0.0, 1.0), precision=HS_FP64, seed=0, replica=0,
@@ -332,9 +353,9 @@ def hs_read_timing(h):
     return ms.value, n.value
 
 
-def hs_set_launch(h, kernel=0, vec_width=0, blocks_per_sm=0, tile_y=0, prefetch=0):
+def hs_set_launch(h, kernel=0, vec_width=0, blocks_per_sm=0, tile_y=0, prefetch=0, order=0):
     k = KERNELS[kernel] if isinstance(kernel, str) else int(kernel)
-    cfg = hs_launch(k, int(vec_width), int(blocks_per_sm), int(tile_y), int(prefetch))
+    cfg = hs_launch(k, int(vec_width), int(blocks_per_sm), int(tile_y), int(prefetch), int(order))
     _check(load().hs_set_launch(h, ctypes.byref(cfg)))
 
 
@@ -555,6 +576,15 @@ class Slab(Lattice):
 
     def sweep_pass(self, beta, colour):
         hs_sweep_pass(self.h, beta, colour)
+
+    def sweep_part(self, beta, colour, part):
+        hs_sweep_pass_part(self.h, beta, colour, part)
+
+    def reserve_ctas(self, ctas):
+        hs_slab_reserve_ctas(self.h, ctas)
+
+    def set_comm_stream(self, stream):
+        hs_slab_set_comm_stream(self.h, stream)
 
     def read_sums(self):
         return hs_read_sums(self.h)

@@ -13,6 +13,13 @@ the scalar allreduce of a multi-device run.
 slabs that share one device (plane copies on the device), and
 ``DistributedSlab`` for one slab per process with torch.distributed
 point-to-point sends of device planes.
+
+With ``overlap=True`` both update the boundary planes first
+(hs_sweep_pass_part): once a colour's first and last own planes are final,
+their exchange runs on a communication stream while the interior planes are
+updated on the compute stream, and the next colour pass waits for both.  The
+chain is the same bit for bit: a colour pass reads only the other colour, so
+the order of its planes does not matter.
 """
 from __future__ import annotations
 
@@ -42,12 +49,34 @@ def combine_sums(sums, n_sites: int, e_axis) -> dict:
             "accepted": float(tot[4])}
 
 
+class _Overlap:
+    """The compute stream of a set of slabs (their own), a communication
+    stream for their halo copies, and the two events that order them."""
+
+    def __init__(self, stream):
+        import torch
+        self.compute = stream if stream is not None else torch.cuda.default_stream()
+        self.comm = torch.cuda.Stream()
+        self.ev_ready, self.ev_done = torch.cuda.Event(), torch.cuda.Event()
+
+    def begin(self):
+        """The communication stream waits for the compute stream's work so far."""
+        self.ev_ready.record(self.compute)
+        self.comm.wait_event(self.ev_ready)
+
+    def end(self):
+        """The compute stream waits for the communication stream's work so far."""
+        self.ev_done.record(self.comm)
+        self.compute.wait_event(self.ev_done)
+
+
 class ShardedLattice:
     """A periodic sc lattice as ``n_slabs`` z-slabs on the current device,
-    halos exchanged by device copies between colour passes."""
+    halos exchanged by device copies between colour passes (on a separate
+    stream, beside the interior update, with ``overlap=True``)."""
 
     def __init__(self, dims, n_slabs: int, *, J=1.0, K=0.0, e=(0.0, 0.0, 1.0), precision="fp32", seed=0,
-                 replica=0, stream=None):
+                 replica=0, stream=None, overlap=False):
         Lx, Ly, Lz = (int(d) for d in dims)
         if n_slabs < 1 or Lz % n_slabs:
             raise ValueError("the slab count must divide Lz")
@@ -57,8 +86,14 @@ class ShardedLattice:
         self.slabs = [hs.Slab(self.dims, k * self.nz, self.nz, J=J, K=K, e=e, precision=precision, seed=seed,
                               replica=replica, stream=stream) for k in range(n_slabs)]
         self.plan = halo_plan(n_slabs)
+        self.ov = _Overlap(stream) if overlap else None
+        if self.ov is not None:
+            for s in self.slabs:
+                s.set_comm_stream(self.ov.comm)
 
     def close(self):
+        if self.ov is not None:
+            self.ov.comm.synchronize()   # no halo copy in flight when the planes are freed
         for s in self.slabs:
             s.close()
 
@@ -68,9 +103,19 @@ class ShardedLattice:
     def __exit__(self, *a):
         self.close()
 
-    def exchange(self, colour: int):
+    def _copies(self, colour: int):
         for src, src_which, dst, dst_which in self.plan:
             hs.hs_slab_copy_plane(self.slabs[dst].h, dst_which, self.slabs[src].h, src_which, colour)
+
+    def exchange(self, colour: int):
+        """The halo copies of one colour, ordered after the work so far and
+        before the work that follows."""
+        if self.ov is None:
+            self._copies(colour)
+            return
+        self.ov.begin()
+        self._copies(colour)
+        self.ov.end()
 
     def init(self, mode=hs.HS_INIT_RANDOM):
         for s in self.slabs:
@@ -100,9 +145,18 @@ class ShardedLattice:
     def sweep(self, beta, n=1):
         for _ in range(n):
             for c in (0, 1):
+                if self.ov is None:
+                    for s in self.slabs:
+                        s.sweep_pass(beta, c)
+                    self._copies(c)
+                    continue
                 for s in self.slabs:
-                    s.sweep_pass(beta, c)
-                self.exchange(c)
+                    s.sweep_part(beta, c, hs.HS_PART_BOUNDARY)
+                self.ov.begin()
+                self._copies(c)          # boundary planes -> halos, beside the interior update
+                for s in self.slabs:
+                    s.sweep_part(beta, c, hs.HS_PART_INTERIOR)
+                self.ov.end()
 
     def last_observables(self) -> dict:
         """E, M, |M|, ... of the last sweep, from the slabs' fused sums."""
@@ -123,12 +177,19 @@ class DistributedSlab:
     which synchronises.  "auto" picks "nccl" when the group's backend is NCCL.
     With accumulation on, every sweep's five fused sums are allreduced and the
     whole lattice's E and M moments are added to this slab's accumulator on
-    the device (hs_accumulate_sums), so every rank holds the global moments."""
+    the device (hs_accumulate_sums), so every rank holds the global moments.
+
+    overlap=True updates the two boundary planes first and runs the exchange
+    (pack, transfer, unpack) on a communication stream while the interior
+    planes are updated; with the host transport the interior update is
+    queued before the host waits for the boundary messages.  reserve_ctas
+    leaves that many CTAs of the interior update unlaunched, so the copy and
+    NCCL kernels find free SMs beside it."""
 
     _DTYPES = {"fp64": "float64", "fp32": "float32", "fp16": "float16"}
 
     def __init__(self, dims, *, J=1.0, K=0.0, e=(0.0, 0.0, 1.0), precision="fp32", seed=0, replica=0,
-                 stream=None, transport="auto"):
+                 stream=None, transport="auto", overlap=False, reserve_ctas=0):
         import torch
         import torch.distributed as dist
         self.torch, self.dist = torch, dist
@@ -158,6 +219,11 @@ class DistributedSlab:
         if transport == "host":
             self.hbuf = {k: torch.empty(n, dtype=dtype).pin_memory() for k in self.buf}
             self.hsums = torch.zeros(5, dtype=torch.float64)
+        self.ov = _Overlap(stream) if overlap else None
+        if self.ov is not None:
+            self.slab.set_comm_stream(self.ov.comm)
+        if reserve_ctas:
+            self.slab.reserve_ctas(reserve_ctas)
 
     def _stream_ctx(self):
         return self.torch.cuda.stream(self.stream) if self.stream is not None else _nullcontext()
@@ -190,14 +256,28 @@ class DistributedSlab:
         return self.slab.read_accumulator()
 
     def exchange(self, colour: int):
-        with self._stream_ctx():
+        """The halo exchange of one colour, ordered after the work so far and
+        before the work that follows."""
+        if self.ov is None:
+            with self._stream_ctx():
+                self._exchange(colour)
+            return
+        self.ov.begin()
+        with self.torch.cuda.stream(self.ov.comm):
             self._exchange(colour)
+        self.ov.end()
 
-    def _exchange(self, colour: int):
+    def _exchange(self, colour: int, interior=None):
+        """Pack, transfer and unpack one colour's boundary planes on the
+        current stream (the slab's communication stream when it has one).
+        interior: queued on the compute stream once the host needs the GPU
+        no more before it blocks (the host transport's overlap)."""
         h = self.slab.h
         if self.world == 1:  # the slab is its own periodic neighbour
             for _, src_which, _, dst_which in halo_plan(1):
                 hs.hs_slab_copy_plane(h, dst_which, h, src_which, colour)
+            if interior is not None:
+                interior()
             return
         lo, hi = (self.rank - 1) % self.world, (self.rank + 1) % self.world
         b = self.buf
@@ -206,23 +286,28 @@ class DistributedSlab:
         # posting order: sends (to lo, to hi), receives (from hi, from lo); with two ranks lo == hi, and
         # the peer's first message (its first own plane) is the one for this rank's halo above
         if self.transport == "nccl":
-            with self._stream_ctx():
-                ops = [self.dist.P2POp(self.dist.isend, b["send_lo"], lo),
-                       self.dist.P2POp(self.dist.isend, b["send_hi"], hi),
-                       self.dist.P2POp(self.dist.irecv, b["recv_hi"], hi),
-                       self.dist.P2POp(self.dist.irecv, b["recv_lo"], lo)]
-                for r in self.dist.batch_isend_irecv(ops):
-                    r.wait()   # the current stream waits on the transfers; the host does not
+            if interior is not None:
+                interior()
+            ops = [self.dist.P2POp(self.dist.isend, b["send_lo"], lo),
+                   self.dist.P2POp(self.dist.isend, b["send_hi"], hi),
+                   self.dist.P2POp(self.dist.irecv, b["recv_hi"], hi),
+                   self.dist.P2POp(self.dist.irecv, b["recv_lo"], lo)]
+            for r in self.dist.batch_isend_irecv(ops):
+                r.wait()   # the current stream waits on the transfers; the host does not
         else:
             hb = self.hbuf
+            cur = self.torch.cuda.current_stream()
             for k in ("send_lo", "send_hi"):
-                hb[k].copy_(b[k])
+                hb[k].copy_(b[k], non_blocking=True)
+            if interior is not None:
+                interior()
+            cur.synchronize()
             reqs = [self.dist.isend(hb["send_lo"], lo, tag=0), self.dist.isend(hb["send_hi"], hi, tag=1),
                     self.dist.irecv(hb["recv_hi"], hi, tag=0), self.dist.irecv(hb["recv_lo"], lo, tag=1)]
             for r in reqs:
                 r.wait()
             for k in ("recv_hi", "recv_lo"):
-                b[k].copy_(hb[k])
+                b[k].copy_(hb[k], non_blocking=True)
         hs.hs_slab_unpack(h, colour, hs.HALO_ABOVE, b["recv_hi"])
         hs.hs_slab_unpack(h, colour, hs.HALO_BELOW, b["recv_lo"])
 
@@ -242,8 +327,15 @@ class DistributedSlab:
         with self._stream_ctx():
             for _ in range(n):
                 for c in (0, 1):
-                    self.slab.sweep_pass(beta, c)
-                    self._exchange(c)
+                    if self.ov is None:
+                        self.slab.sweep_pass(beta, c)
+                        self._exchange(c)
+                        continue
+                    self.slab.sweep_part(beta, c, hs.HS_PART_BOUNDARY)
+                    self.ov.begin()
+                    with self.torch.cuda.stream(self.ov.comm):
+                        self._exchange(c, interior=lambda c=c: self.slab.sweep_part(beta, c, hs.HS_PART_INTERIOR))
+                    self.ov.end()
                 if self.accumulating:
                     self._accumulate_sweep()
 
@@ -256,6 +348,8 @@ class DistributedSlab:
         return combine_sums([sums.cpu().numpy()], self.n_sites, self.e)
 
     def close(self):
+        if self.ov is not None:
+            self.ov.comm.synchronize()
         self.slab.close()
 
 

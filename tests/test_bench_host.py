@@ -19,9 +19,12 @@ def test_kernel_labels():
 def test_traffic_only_for_the_captured_sources_and_kernel(tmp_path, monkeypatch):
     f = tmp_path / "traffic.txt"
     f.write_text(f"kernel: sc_pass_kernel<1, 4, 1, 2, 0>\nsources_sha: {bench.kernels_sha()}\n"
-                 "dram_bytes_per_launch: 123\n")
+                 "order: ascending\ndram_bytes_per_launch: 123\ncold_dram_bytes_per_launch: 456\n")
     monkeypatch.setattr(bench, "TRAFFIC_FILE", str(f))
     assert bench.read_traffic("sc_pass_kernel<1, 4, 1, 2, 0>") == 123.0
+    assert bench.read_traffic("sc_pass_kernel<1, 4, 1, 2, 0>", 1) == 123.0
+    assert bench.read_traffic("sc_pass_kernel<1, 4, 1, 2, 0>", 1, "cold_dram_bytes_per_launch") == 456.0
+    assert bench.read_traffic("sc_pass_kernel<1, 4, 1, 2, 0>", 2) is None     # captured in the other order
     assert bench.read_traffic("sc_pass_kernel<1, 4, 1, 0, 0>") is None
     f.write_text("kernel: sc_pass_kernel<1, 4, 1, 2, 0>\nsources_sha: 0000\ndram_bytes_per_launch: 123\n")
     assert bench.read_traffic("sc_pass_kernel<1, 4, 1, 2, 0>") is None
@@ -30,7 +33,7 @@ def test_traffic_only_for_the_captured_sources_and_kernel(tmp_path, monkeypatch)
 def test_committed_traffic_matches_the_sources():
     """The stored capture belongs to the current kernel sources (else the bench
     reports no traffic)."""
-    assert bench.read_traffic("sc_pass_kernel<1, 4, 1, 2, 0>") is not None
+    assert bench.read_traffic("sc_pass_kernel<1, 4, 1, 0, 0>", 2) is not None
 
 
 def test_spin_error_measure():

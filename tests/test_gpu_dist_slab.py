@@ -11,7 +11,9 @@ sc 16 x 8 x 12 periodic, J = 1, K = 0.1, e = (0.3, -0.2, 1): after three
 sweeps the slabs, concatenated in rank order, equal the whole lattice's spins
 bit for bit, and every rank's accumulator holds the whole lattice's moments
 (FP64 sums added in another order; FP32 per-thread partials grouped
-differently).
+differently).  The same holds with the boundary-first schedule (overlap:
+boundary planes updated first, the exchange on a communication stream with
+the interior update queued before the host waits for the messages).
 """
 import multiprocessing as mp
 import os
@@ -31,13 +33,14 @@ PARAMS = dict(J=1.0, K=0.1, e=(0.3, -0.2, 1.0))
 SWEEPS = 3
 
 
-def _worker(rank, world, port, precision, S0, q):
+def _worker(rank, world, port, precision, overlap, S0, q):
     sys.path.insert(0, ROOT)
     try:
         import torch.distributed as dist
         dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank, world_size=world)
         from paper_2106_11286_gb300 import shards
-        ds = shards.DistributedSlab(DIMS, precision=precision, seed=8, transport="host", **PARAMS)
+        ds = shards.DistributedSlab(DIMS, precision=precision, seed=8, transport="host", overlap=overlap,
+                                    **PARAMS)
         plane, nz = DIMS[0] * DIMS[1], DIMS[2] // world
         ds.set_spins(S0[rank * nz * plane:(rank + 1) * nz * plane])
         ds.accumulate(True)
@@ -51,8 +54,9 @@ def _worker(rank, world, port, precision, S0, q):
         q.put((rank, repr(ex), None, None, None))
 
 
+@pytest.mark.parametrize("overlap", [False, True])
 @pytest.mark.parametrize("precision,rtol", [("fp64", 1e-12), ("fp32", 2e-6)])
-def test_two_process_slabs_reproduce_the_whole_lattice(precision, rtol):
+def test_two_process_slabs_reproduce_the_whole_lattice(precision, rtol, overlap):
     n = DIMS[0] * DIMS[1] * DIMS[2]
     S0 = inputs.random_unit_spins(n, 21)
     if precision == "fp32":
@@ -70,7 +74,7 @@ def test_two_process_slabs_reproduce_the_whole_lattice(precision, rtol):
     s.close()
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
-    procs = [ctx.Process(target=_worker, args=(r, 2, port, precision, S0, q)) for r in range(2)]
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, precision, overlap, S0, q)) for r in range(2)]
     for p in procs:
         p.start()
     try:

@@ -286,7 +286,10 @@ def _launch_configs(precision, dims):
         out += [dict(kernel="stencil", vec_width=v, blocks_per_sm=1), dict(kernel="stencil", vec_width=v),
                 dict(kernel="stencil", vec_width=v, prefetch=3),
                 dict(kernel="stencil", vec_width=v, prefetch=1), dict(kernel="stencil", vec_width=v, prefetch=1,
-                                                                       blocks_per_sm=1)]
+                                                                       blocks_per_sm=1),
+                # every pass ascending, and the split prefetch alternating, against the automatic orders
+                dict(kernel="stencil", vec_width=v, order=1), dict(kernel="stencil", vec_width=v, prefetch=3, order=2),
+                dict(kernel="stencil", vec_width=v, prefetch=1, order=1)]
         if 4 <= v * es <= 16:
             out += [dict(kernel="pipe", vec_width=v), dict(kernel="pipe", vec_width=v, blocks_per_sm=1)]
         for ty in (1, 2, 4):
@@ -302,8 +305,9 @@ def _launch_configs(precision, dims):
                                             ("fp32", (288, 16, 4)), ("fp16", (288, 8, 6))])
 def test_launch_configuration_does_not_change_results(precision, dims):
     """A site's random numbers and arithmetic depend only on its natural index,
-    so every kernel, vector width, CTA count, slab and prefetch mode gives
-    bit-identical chains; the autotuner restores the state it perturbs."""
+    so every kernel, vector width, CTA count, slab, prefetch mode and order
+    of the work items gives bit-identical chains; the autotuner restores the
+    state it perturbs."""
     outs = []
     cfgs = _launch_configs(precision, dims)
     assert all(any(c["kernel"] == k for c in cfgs) for k in ("stencil", "pipe", "march"))
@@ -312,6 +316,8 @@ def test_launch_configuration_does_not_change_results(precision, dims):
             lat.set_launch(**cfg)
             got = lat.launch
             assert got["vec_width"] == cfg["vec_width"] and got["kernel"] == hs.KERNELS[cfg["kernel"]]
+            if cfg["kernel"] == "stencil":
+                assert got["order"] == cfg.get("order", 1 if cfg.get("prefetch") == 3 else 2)
             lat.init()
             lat.accumulate(True)
             lat.sweep(0.9, 6)
