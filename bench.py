@@ -80,7 +80,8 @@ def kernel_label(launch, precision_code=1, measure=1):
     name = KERNEL_NAMES.get(launch["kernel"], "sc_pass_kernel")
     if launch["kernel"] == 1:
         pf = {1: 1, 3: 2}.get(launch["prefetch"], 0)
-        return f"{name}<{precision_code}, {launch['vec_width']}, {measure}, {pf}, 0>"
+        # the last flag: the direction-capable variant (every lattice up to 2^31 sites)
+        return f"{name}<{precision_code}, {launch['vec_width']}, {measure}, {pf}, 0, 1>"
     return name
 
 
@@ -977,8 +978,10 @@ def run_case(args):
         lat.accumulate(True)
         lat.sweep(1.0 / T, 10)
         if args.launch:
-            kernel, vec, blocks = (int(x) for x in args.launch.split(","))
-            lat.set_launch(kernel=kernel, vec_width=vec, blocks_per_sm=blocks)
+            f = [int(x) for x in args.launch.split(",")]
+            kernel, vec, blocks = f[:3]
+            prefetch, order = (f[3:] + [0, 0])[:2]
+            lat.set_launch(kernel=kernel, vec_width=vec, blocks_per_sm=blocks, prefetch=prefetch, order=order)
             launch = lat.launch
         else:
             launch = lat.launch if args.no_autotune else lat.autotune(1.0 / T, 2)
@@ -1020,8 +1023,8 @@ def main(argv=None):
     ap.add_argument("--beta-blocks", type=int, default=10)
     ap.add_argument("--beta-block-sweeps", type=int, default=500)
     ap.add_argument("--case", choices=sorted(CASES), help="run one workload alone (for ncu captures)")
-    ap.add_argument("--launch", help="with --case: fixed launch 'kernel,vec_width,blocks_per_sm' (hs_kernel codes), "
-                                     "no autotuning")
+    ap.add_argument("--launch", help="with --case: fixed launch 'kernel,vec_width,blocks_per_sm[,prefetch[,order]]' "
+                                     "(hs_launch codes), no autotuning")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

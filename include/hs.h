@@ -326,7 +326,13 @@ void hs_batch_destroy(hs_batch *b);
  * 0: every sweep in one persistent cooperative launch, passes separated by
  * the bounded grid barrier, captured in a CUDA graph; schedule 1: one launch
  * per colour pass of every member, consecutive launches chained by
- * programmatic dependent launch), for n_trial_sweeps sweeps at the given
+ * programmatic dependent launch), and, when every member's six planes fit
+ * in one CTA's shared memory (FP32 sc up to L = 26 on GB300), schedule 2:
+ * one launch with one CTA per member, whose planes are copied into shared
+ * memory once and stay there for every sweep, the colour passes separated
+ * by CTA barriers only (no grid barrier, no global traffic between the
+ * first load and the final store; the work split and load schedule do not
+ * apply), for n_trial_sweeps sweeps at the given
  * betas after one warm-up sweep; the fastest is kept.  Colour 0 then colour
  * 1 in every sweep under all of them.  Every member's spins, sweep counter
  * and accumulator are restored, so the members' chains are as if the call
@@ -334,13 +340,15 @@ void hs_batch_destroy(hs_batch *b);
  * are taken in each split's own fixed order).  Synchronous.
  * hs_batch_get_layout reads the choice in use (hs_batch_create starts with
  * the maximum CTAs per SM, the interleaved split (align_rows 2), no
- * prefetch, schedule 0). */
+ * prefetch, and schedule 2 when there are at least 32 members and every one
+ * fits in a CTA's shared memory, else schedule 0). */
 int hs_batch_autotune(hs_batch *b, const double *betas, int n_trial_sweeps);
 int hs_batch_get_layout(const hs_batch *b, int *ctas_per_sm, int *align_rows, int *prefetch, int *schedule);
 /* Set the choice by hand: ctas_per_sm in 1 .. the kernel's occupancy,
- * align_rows 0, 1 or 2, prefetch and schedule 0 or 1 (HS_E_INVALID otherwise).  The
- * members' chains do not depend on it.  The timeout test hook always runs
- * the persistent schedule.  Synchronises the batch's stream. */
+ * align_rows 0, 1 or 2, prefetch 0 or 1, schedule 0, 1 or 2, the last only
+ * when every member fits in one CTA's shared memory (HS_E_INVALID otherwise).
+ * The members' chains do not depend on it.  The timeout test hook always
+ * runs the persistent schedule.  Synchronises the batch's stream. */
 int hs_batch_set_layout(hs_batch *b, int ctas_per_sm, int align_rows, int prefetch, int schedule);
 
 /* Allocation-free sweep (the paper has no counterpart; it is a service to

@@ -476,8 +476,13 @@ int configure_launch(hs_lattice *h) {
         L.prefetch = 0;
     else
         L.prefetch = r.prefetch == 1 ? 1 : (r.prefetch == 3 ? 2 : 0);
-    // automatic order: alternating, except with the split prefetch, which measured slower in descending passes
-    L.order = r.order != 0 ? r.order : (L.prefetch == 2 ? 1 : 2);
+    // automatic order: alternating, except with the split prefetch, which measured slower in descending passes,
+    // and beyond 2^31 sites, where the ascending-only variant of the kernel is faster (137 against 103-112
+    // attempts/ns at 2048^3 FP32; the direction-capable code is faster from 256^3 to 1024^3)
+    const bool wide = L.n_sites > 2147483647LL;
+    L.order = r.order != 0 ? r.order : ((L.prefetch == 2 || wide) ? 1 : 2);
+    L.plain = wide && L.order == 1 && L.prefetch == 0 && !h->tensor &&
+              ((h->precision == HS_FP32 && L.vec == 4) || (h->precision == HS_FP16 && L.vec == 8));
     int bps = r.blocks_per_sm;
     const int occ = std::min(hs::pass_occupancy(h->precision, L, 0), hs::pass_occupancy(h->precision, L, 1));
     if (bps <= 0 || bps > occ) bps = occ;
@@ -1394,7 +1399,9 @@ struct hs_batch {
     int inject_timeout = 0;  // test hook, consumed by the next run
     int occ = 1, ctas_per_sm = 1, align_rows = 0;  // work split (batch_layout)
     int prefetch = 0;                              // 1: split prefetch variant of the kernel
-    int schedule = 0;                              // 0: one persistent launch, 1: a launch per colour pass
+    int schedule = 0;                              // 0: one persistent launch, 1: a launch per colour pass,
+                                                   // 2: resident (one CTA per member, in shared memory)
+    size_t resident_bytes = 0;                     // the largest member's six planes
     ~hs_batch() {
         cudaStreamSynchronize(stream);
         if (exec) cudaGraphExecDestroy(exec);
@@ -1584,6 +1591,10 @@ int batch_layout(hs_batch *b, int ctas_per_sm, int align_rows) {
 }
 }  // namespace
 
+namespace {
+constexpr int kResidentMinMembers = 32;  // hs_batch_create's choice of the resident schedule
+}  // namespace
+
 int hs_batch_create(hs_batch **out, hs_lattice *const *members, int n_members) {
     if (!out) return fail(HS_E_INVALID, "out is NULL");
     *out = nullptr;
@@ -1629,6 +1640,7 @@ int hs_batch_create(hs_batch **out, hs_lattice *const *members, int n_members) {
         m.replica = h->replica;
         m.n_present = (double)L.n_present;
         m.acc = h->acc;
+        b->resident_bytes = std::max(b->resident_bytes, (size_t)6 * L.Lz * L.Ly * L.Lh * sizeof(float));
     }
     cudaError_t e;
     if ((e = cudaMalloc(&b->d_members, sizeof(hs::BatchMember) * n_members)) != cudaSuccess ||
@@ -1645,6 +1657,9 @@ int hs_batch_create(hs_batch **out, hs_lattice *const *members, int n_members) {
         delete b;
         return st;
     }
+    // many small members: the resident schedule (measured 1.6-2x the persistent one from 64 members of 16^3
+    // up; slower with 16 members of 24^3, which leave most SMs idle)
+    if (n_members >= kResidentMinMembers && b->resident_bytes <= hs::batch_resident_limit()) b->schedule = 2;
     *out = b;
     return HS_OK;
 }
@@ -1682,6 +1697,11 @@ int hs_batch_run(hs_batch *b, const double *betas, int64_t n_sweeps, int64_t n_e
         for (int r = 0; r < n; ++r) b->members[r]->sweep += (uint64_t)n_total;
         return HS_OK;
     }
+    if (b->schedule == 2) {  // one launch: every member resident in its CTA's shared memory
+        HS_CUDA(hs::launch_batch_resident(args, b->resident_bytes, b->stream));
+        for (int r = 0; r < n; ++r) b->members[r]->sweep += (uint64_t)n_total;
+        return HS_OK;
+    }
     // the persistent kernel runs as one node of a CUDA graph, captured once per
     // (sweeps, equilibration) pair; without graph support it is launched directly
     if (!b->graph_failed && (b->graph_total != n_total || b->graph_equil != n_eq || !b->exec)) {
@@ -1716,9 +1736,10 @@ int hs_batch_run(hs_batch *b, const double *betas, int64_t n_sweeps, int64_t n_e
 }
 
 // Batch autotuner: time every work split (1 .. occupancy CTAs per SM, cuts
-// at any item or at row boundaries) for n_trial_sweeps sweeps after one
-// warm-up sweep, keep the fastest, and put every member's spins, sweep counter
-// and accumulator back as they were.
+// at any item or at row boundaries), load schedule and colour schedule, and
+// the resident schedule where every member fits one CTA's shared memory, for
+// n_trial_sweeps sweeps after one warm-up sweep, keep the fastest, and put
+// every member's spins, sweep counter and accumulator back as they were.
 int hs_batch_autotune(hs_batch *b, const double *betas, int n_trial_sweeps) {
     if (!b || !betas) return fail(HS_E_INVALID, "null argument");
     if (n_trial_sweeps < 1) return fail(HS_E_INVALID, "n_trial_sweeps must be >= 1");
@@ -1769,10 +1790,11 @@ int hs_batch_autotune(hs_batch *b, const double *betas, int n_trial_sweeps) {
     float best_ms = 0.f;
     bool have = false;
     if (st == HS_OK && cudaStreamSynchronize(b->stream) != cudaSuccess) st = fail(HS_E_CUDA, "synchronise");
-    for (int sc = 0; st == HS_OK && sc <= 1; ++sc)
-    for (int pf = 0; st == HS_OK && pf <= 1; ++pf)
-    for (int c = 1; st == HS_OK && c <= b->occ; ++c)
-        for (int al = 0; st == HS_OK && al <= 2; ++al) {
+    const int max_sc = b->resident_bytes <= hs::batch_resident_limit() ? 2 : 1;
+    for (int sc = 0; st == HS_OK && sc <= max_sc; ++sc)
+    for (int pf = 0; st == HS_OK && pf <= (sc == 2 ? 0 : 1); ++pf)
+    for (int c = (sc == 2 ? b->occ : 1); st == HS_OK && c <= b->occ; ++c)
+        for (int al = (sc == 2 ? 2 : 0); st == HS_OK && al <= 2; ++al) {  // the resident schedule: one candidate
             b->prefetch = pf;
             b->schedule = sc;
             if ((st = batch_layout(b, c, al))) break;
@@ -1810,8 +1832,10 @@ int hs_batch_autotune(hs_batch *b, const double *betas, int n_trial_sweeps) {
 int hs_batch_set_layout(hs_batch *b, int ctas_per_sm, int align_rows, int prefetch, int schedule) {
     if (!b) return fail(HS_E_INVALID, "null handle");
     if (ctas_per_sm < 1 || ctas_per_sm > b->occ) return fail(HS_E_INVALID, "ctas_per_sm out of range");
-    if (align_rows < 0 || align_rows > 2 || (prefetch != 0 && prefetch != 1) || (schedule != 0 && schedule != 1))
-        return fail(HS_E_INVALID, "align_rows must be 0, 1 or 2, prefetch and schedule 0 or 1");
+    if (align_rows < 0 || align_rows > 2 || (prefetch != 0 && prefetch != 1) || schedule < 0 || schedule > 2)
+        return fail(HS_E_INVALID, "align_rows must be 0, 1 or 2, prefetch 0 or 1, schedule 0, 1 or 2");
+    if (schedule == 2 && b->resident_bytes > hs::batch_resident_limit())
+        return fail(HS_E_INVALID, "the resident schedule needs every member's spins in one CTA's shared memory");
     b->prefetch = prefetch;
     b->schedule = schedule;
     return batch_layout(b, ctas_per_sm, align_rows);

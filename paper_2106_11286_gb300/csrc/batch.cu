@@ -86,6 +86,40 @@ __device__ __forceinline__ PassArgs member_args(const BatchMember &m, int colour
     return a;
 }
 
+// Add one sweep of a member, its five FP64 totals (E share, sum S, accepted
+// moves), to its accumulator (one thread): the raw sums, Eq. 2's
+// observables, and in the measurement phase their moments.
+__device__ void member_apply_sweep(const BatchMember &m, const double (&tot)[kPartials], bool measured) {
+    DevAccum *A = m.acc;
+    A->accepted += tot[4];
+#pragma unroll
+    for (int q = 0; q < kPartials; ++q) A->sums[q] = tot[q];
+    const double mx = tot[1] / m.n_present, my = tot[2] / m.n_present, mz = tot[3] / m.n_present;
+    const double m2 = mx * mx + my * my + mz * mz;
+    const double am = sqrt(m2);
+    const double me = fabs(mx * m.e[0] + my * m.e[1] + mz * m.e[2]);
+    A->last[0] = tot[0];
+    A->last[1] = mx;
+    A->last[2] = my;
+    A->last[3] = mz;
+    A->last[4] = am;
+    A->last[5] = m2;
+    A->last[6] = m2 * m2;
+    A->last[7] = me;
+    if (measured) {
+        A->moments[HS_SUM_E] += tot[0];
+        A->moments[HS_SUM_E2] += tot[0] * tot[0];
+        A->moments[HS_SUM_ABSM] += am;
+        A->moments[HS_SUM_M2] += m2;
+        A->moments[HS_SUM_M4] += m2 * m2;
+        A->moments[HS_SUM_MX] += mx;
+        A->moments[HS_SUM_MY] += my;
+        A->moments[HS_SUM_MZ] += mz;
+        A->moments[HS_SUM_ABSME] += me;
+        A->count += 1.0;
+    }
+}
+
 // Finalise sweep s for the members this CTA owns, one warp per member: sum
 // the member's segment slots of both colour passes in a fixed order and
 // update its FP64 accumulator.  Reads slot parity s & 1, which sweep s + 2
@@ -104,36 +138,7 @@ __device__ void finalize_sweep(const BatchArgs &b, int s) {
                     tot[q] += __ldcg(b.slots + (((size_t)par * 2 + c) * b.n_segs + si) * kPartials + q);
 #pragma unroll
         for (int q = 0; q < kPartials; ++q) tot[q] = warp_sum(tot[q]);
-        if (lane == 0) {
-            DevAccum *A = m.acc;
-            A->accepted += tot[4];
-#pragma unroll
-            for (int q = 0; q < kPartials; ++q) A->sums[q] = tot[q];
-            const double mx = tot[1] / m.n_present, my = tot[2] / m.n_present, mz = tot[3] / m.n_present;
-            const double m2 = mx * mx + my * my + mz * mz;
-            const double am = sqrt(m2);
-            const double me = fabs(mx * m.e[0] + my * m.e[1] + mz * m.e[2]);
-            A->last[0] = tot[0];
-            A->last[1] = mx;
-            A->last[2] = my;
-            A->last[3] = mz;
-            A->last[4] = am;
-            A->last[5] = m2;
-            A->last[6] = m2 * m2;
-            A->last[7] = me;
-            if (s >= b.n_equil) {
-                A->moments[HS_SUM_E] += tot[0];
-                A->moments[HS_SUM_E2] += tot[0] * tot[0];
-                A->moments[HS_SUM_ABSM] += am;
-                A->moments[HS_SUM_M2] += m2;
-                A->moments[HS_SUM_M4] += m2 * m2;
-                A->moments[HS_SUM_MX] += mx;
-                A->moments[HS_SUM_MY] += my;
-                A->moments[HS_SUM_MZ] += mz;
-                A->moments[HS_SUM_ABSME] += me;
-                A->count += 1.0;
-            }
-        }
+        if (lane == 0) member_apply_sweep(m, tot, s >= b.n_equil);
     }
 }
 
@@ -282,6 +287,82 @@ __global__ void __launch_bounds__(kBlock) batch_finalize_kernel(const BatchArgs 
     finalize_sweep(b, s);
 }
 
+// The resident schedule: one CTA per member, whose six planes are copied into
+// the CTA's shared memory once and stay there for every sweep of the run
+// (small lattices, up to the per-CTA shared memory).  A colour pass reads only
+// the other colour, so a CTA barrier between passes is the only ordering the
+// chain needs: no grid barrier, no global traffic between the first load and
+// the final store.  The work items, loads and Metropolis update are those of
+// the streaming kernels, on generic pointers into shared memory, so the chain
+// is bit-identical; each sweep's FP64 totals (the two passes' CTA sums, in a
+// fixed order) go straight to the member's accumulator.
+__global__ void __launch_bounds__(kBlock, 2) batch_resident_kernel(const BatchArgs b) {
+    constexpr int P = HS_FP32;
+    constexpr int V = 4;
+    using VT = Vec<float, V>;
+    extern __shared__ float4 s_state[];
+    __shared__ double s_red[kBlock / 32][kPartials];
+    __shared__ PassArgs s_args;
+    const BatchMember &m = b.members[blockIdx.x];
+    const uint32_t plane = (uint32_t)m.Lz * m.Ly * m.Lh;  // elements of one component plane; Lh % 4 == 0
+    const uint32_t n4 = 6u * plane / 4u;
+    const float4 *g4 = reinterpret_cast<const float4 *>(m.planes);
+    for (uint32_t i = threadIdx.x; i < n4; i += kBlock) s_state[i] = __ldcg(g4 + i);
+    float *const st = reinterpret_cast<float *>(s_state);
+    const uint32_t n_items = plane / V;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int s = 0; s < b.n_total; ++s) {
+        double tot[kPartials] = {0.0, 0.0, 0.0, 0.0, 0.0};
+        for (int c = 0; c < 2; ++c) {
+            if (threadIdx.x == 0) s_args = member_args(m, c, m.sweep0 + (uint32_t)s);
+            __syncthreads();  // the parameters, and every store of the previous pass (or the initial copy)
+            const PassArgs &a = s_args;
+            float *own_w[3];
+            const float *own[3], *oth[3];
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                own_w[q] = st + (size_t)(3 * c + q) * plane;
+                own[q] = own_w[q];
+                oth[q] = st + (size_t)(3 * (1 - c) + q) * plane;
+            }
+            float J, K, ex, ey, ez, beta;
+            load_params(a, J, K, ex, ey, ez, beta);
+            SiteAcc<P> acc;
+            for (uint32_t t = threadIdx.x; t < n_items; t += kBlock) {
+                StencilItem<P, V> it;
+                load_item<P, V>(a, t, own, oth, it);
+                if (update_item<P, V, true>(it.s, it.o, it.nym, it.nyp, it.nzm, it.nzp, it.ed, it.p, it.site0,
+                                            it.rank0, c, a, J, K, ex, ey, ez, beta, acc)) {
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) *reinterpret_cast<VT *>(own_w[q] + it.b0) = it.s[q];
+                }
+            }
+            // the pass's sums: warp shuffle -> CTA (FP64), added to the sweep's totals in warp order
+            const float accE = warp_sum(acc.E());
+            const float accX = warp_sum(acc.X());
+            const float accY = warp_sum(acc.Y());
+            const float accZ = warp_sum(acc.Z());
+            const unsigned nacc = __reduce_add_sync(0xffffffffu, acc.n);
+            if (lane == 0) {
+                s_red[warp][0] = accE;
+                s_red[warp][1] = accX;
+                s_red[warp][2] = accY;
+                s_red[warp][3] = accZ;
+                s_red[warp][4] = (double)nacc;
+            }
+            __syncthreads();
+            if (threadIdx.x == 0)
+                for (int w = 0; w < kBlock / 32; ++w)
+#pragma unroll
+                    for (int q = 0; q < kPartials; ++q) tot[q] += s_red[w][q];
+        }
+        if (threadIdx.x == 0) member_apply_sweep(m, tot, s >= b.n_equil);
+    }
+    __syncthreads();
+    float4 *w4 = reinterpret_cast<float4 *>(m.planes);
+    for (uint32_t i = threadIdx.x; i < n4; i += kBlock) w4[i] = s_state[i];
+}
+
 template <typename... KArgs, typename... Args>
 cudaError_t launch_chained(void (*kernel)(KArgs...), int grid, cudaStream_t s, Args... args) {
     cudaLaunchConfig_t cfg{};
@@ -317,6 +398,23 @@ cudaError_t launch_batch_passes(const BatchArgs &b, int grid, cudaStream_t s, in
         }
     if (b.n_total > 0) return launch_chained(batch_finalize_kernel, grid, s, b, b.n_total - 1);
     return cudaSuccess;
+}
+
+size_t batch_resident_limit() {
+    int dev = 0, optin = 0;
+    cudaFuncAttributes fa{};
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+        cudaFuncGetAttributes(&fa, batch_resident_kernel) != cudaSuccess)
+        return 0;
+    return optin > (int)fa.sharedSizeBytes ? (size_t)optin - fa.sharedSizeBytes : 0;
+}
+
+cudaError_t launch_batch_resident(const BatchArgs &b, size_t smem, cudaStream_t s) {
+    cudaError_t e = cudaFuncSetAttribute(batch_resident_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    batch_resident_kernel<<<b.n_members, kBlock, smem, s>>>(b);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_batch(const BatchArgs &b, int grid, cudaStream_t s, int prefetch) {

@@ -867,11 +867,11 @@ __device__ __forceinline__ void load_item_at(const PassArgs &a, uint32_t y, uint
 }
 
 // The work item with linear index t = (z Ly + y) (Lh/V) + xv (rev - t in a
-// descending pass).
-template <int P, int V, bool CG = false>
+// descending pass; DIR = false: always ascending, with no reference to rev).
+template <int P, int V, bool CG = false, bool DIR = true>
 __device__ __forceinline__ void load_item(const PassArgs &a, uint32_t t, const typename Tr<P>::S *const (&own)[3],
                                           const typename Tr<P>::S *const (&oth)[3], StencilItem<P, V> &it) {
-    t = a.rev ? a.rev - t : t;  // a descending pass
+    if constexpr (DIR) t = a.rev ? a.rev - t : t;  // a descending pass
     const uint32_t nxv = a.Lh / V;
     const uint32_t r = a.div_nxv.div(t);
     const uint32_t xv = t - r * nxv;
@@ -892,12 +892,12 @@ struct SplitItem {
     ItemOffsets f;
 };
 
-template <int P, int V, bool CG = false>
+template <int P, int V, bool CG = false, bool DIR = true>
 __device__ __forceinline__ void load_split_a(const PassArgs &a, uint32_t t, const typename Tr<P>::S *const (&own)[3],
                                              const typename Tr<P>::S *const (&oth)[3], SplitItem<P, V> &A) {
     using S = typename Tr<P>::S;
     using VT = Vec<S, V>;
-    t = a.rev ? a.rev - t : t;  // a descending pass
+    if constexpr (DIR) t = a.rev ? a.rev - t : t;  // a descending pass
     const uint32_t nxv = a.Lh / V;
     const uint32_t r = a.div_nxv.div(t);
     const uint32_t xv = t - r * nxv;

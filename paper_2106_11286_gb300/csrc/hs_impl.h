@@ -125,6 +125,7 @@ struct Layout {
                             //    prefetch, or the neighbour table)
     int ty;                 // z-march stencil: rows per plane-slab
     int order;              // register stencil: 1 ascending passes, 2 alternating (colour 1 descending)
+    bool plain;             // register stencil: the ascending-only variant (lattices beyond 2^31 sites)
     int n_colours;
     int64_t n_sites, n_present;
     // stencil
@@ -182,6 +183,10 @@ cudaError_t launch_batch(const BatchArgs &b, int grid, cudaStream_t s, int prefe
 // the per-pass schedule: 2 n_total chained pass launches and a finalise launch
 cudaError_t launch_batch_passes(const BatchArgs &b, int grid, cudaStream_t s, int prefetch);
 int batch_occupancy(int prefetch);
+// the resident schedule: one CTA per member, its planes in dynamic shared
+// memory (smem bytes, at most batch_resident_limit()) for the whole run
+cudaError_t launch_batch_resident(const BatchArgs &b, size_t smem, cudaStream_t s);
+size_t batch_resident_limit();
 
 size_t storage_size(int precision);
 

@@ -166,7 +166,8 @@ class ShardedLattice:
 
 class DistributedSlab:
     """One slab per process (rank r of a torch.distributed group of W ranks
-    owns planes r nz .. (r+1) nz - 1).
+    owns planes r nz .. (r+1) nz - 1; without a process group, one slab
+    that is its own periodic neighbour).
 
     After each colour pass the slab packs the colour's first and last own
     planes into one message each (hs_slab_pack: the three component planes
@@ -193,12 +194,14 @@ class DistributedSlab:
         import torch
         import torch.distributed as dist
         self.torch, self.dist = torch, dist
-        self.rank, self.world = dist.get_rank(), dist.get_world_size()
+        grouped = dist.is_available() and dist.is_initialized()
+        # without a process group: one slab, its own periodic neighbour, no collective
+        self.rank, self.world = (dist.get_rank(), dist.get_world_size()) if grouped else (0, 1)
         Lx, Ly, Lz = (int(d) for d in dims)
         if Lz % self.world:
             raise ValueError("the rank count must divide Lz")
         if transport == "auto":
-            transport = "nccl" if dist.get_backend() == "nccl" else "host"
+            transport = "nccl" if grouped and dist.get_backend() == "nccl" else "host"
         if transport not in ("nccl", "host"):
             raise ValueError("transport must be 'auto', 'nccl' or 'host'")
         self.transport = transport
@@ -314,7 +317,9 @@ class DistributedSlab:
     def _accumulate_sweep(self):
         h = self.slab.h
         hs.hs_read_sums_device(h, self.sums)
-        if self.transport == "nccl":
+        if self.world == 1:
+            pass
+        elif self.transport == "nccl":
             with self._stream_ctx():
                 self.dist.all_reduce(self.sums)
         else:
@@ -342,9 +347,10 @@ class DistributedSlab:
     def last_observables(self) -> dict:
         """E, M, |M|, ... of the last sweep of the whole lattice (host)."""
         sums = self.torch.as_tensor(self.slab.read_sums(), dtype=self.torch.float64)
-        if self.transport == "nccl":
-            sums = sums.cuda()
-        self.dist.all_reduce(sums)
+        if self.world > 1:
+            if self.transport == "nccl":
+                sums = sums.cuda()
+            self.dist.all_reduce(sums)
         return combine_sums([sums.cpu().numpy()], self.n_sites, self.e)
 
     def close(self):

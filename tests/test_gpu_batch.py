@@ -134,13 +134,68 @@ def test_batch_layouts_give_identical_chains(ctas, align, prefetch, schedule):
         with pytest.raises(hs.HSError):
             hs.hs_batch_set_layout(bb, 1, 0, 2)
         with pytest.raises(hs.HSError):
-            hs.hs_batch_set_layout(bb, 1, 0, 0, 2)
+            hs.hs_batch_set_layout(bb, 1, 0, 0, 2)   # 48^3 and 96^3 do not fit in a CTA's shared memory
+        with pytest.raises(hs.HSError):
+            hs.hs_batch_set_layout(bb, 1, 0, 0, 3)
         with pytest.raises(hs.HSError):
             hs.hs_batch_set_layout(bb, 1, 3, 0, 0)
     finally:
         hs.hs_batch_destroy(ba)
         hs.hs_batch_destroy(bb)
         for m in a + b:
+            m.close()
+
+
+def test_resident_schedule_gives_identical_chains():
+    """Schedule 2: every member (here up to 24^3, 166 KB of FP32 planes) in
+    one CTA's shared memory for the whole run.  Member by member the spins
+    equal hs_sweep on each lattice alone and the persistent batch's, bit for
+    bit, over repeated runs with and without equilibration; moments and
+    acceptance rates agree up to the order of the FP64 sums."""
+    dims = [(16, 16, 16), (24, 24, 24), (8, 8, 8), (16, 8, 24), (24, 16, 8), (8, 24, 16)]
+    betas = [0.6, 0.8, 1.0, 1.2, 0.9, 0.7]
+    a = _members(dims, betas)
+    b = _members(dims, betas)
+    c = _members(dims, betas)
+    for m in a + b + c:
+        m.init()
+        m.accumulate(True)
+    ba = hs.hs_batch_create([m.h for m in a])
+    bb = hs.hs_batch_create([m.h for m in b])
+    try:
+        hs.hs_batch_set_layout(ba, 2, 2, 0, 2)
+        assert hs.hs_batch_get_layout(ba)["schedule"] == 2
+        for n_equil, n_sweeps in ((3, 5), (0, 4), (2, 0)):
+            for m in a + b + c:
+                m.reset_accumulator()
+            hs.hs_batch_run(ba, betas, n_sweeps, n_equil)
+            hs.hs_batch_run(bb, betas, n_sweeps, n_equil)
+            for m, beta in zip(c, betas):
+                m.accumulate(False)
+                m.sweep(beta, n_equil)
+                m.accumulate(True)
+                m.sweep(beta, n_sweeps)
+            for x, y, z in zip(a, b, c):
+                assert np.array_equal(x.get_spins(), y.get_spins())
+                assert np.array_equal(x.get_spins(), z.get_spins())
+                mx, cx = x.read_accumulator()
+                my, cy = y.read_accumulator()
+                mz, cz = z.read_accumulator()
+                assert cx == cy == cz == n_sweeps
+                np.testing.assert_allclose(mx, my, rtol=2e-6, atol=1e-9)
+                np.testing.assert_allclose(mx, mz, rtol=2e-6, atol=1e-9)
+                assert x.info.sweep == y.info.sweep == z.info.sweep
+                assert x.measure()["accept_rate"] == pytest.approx(y.measure()["accept_rate"], abs=1e-12)
+        layout = hs.hs_batch_autotune(ba, betas, 2)   # the resident schedule is one of its candidates
+        assert layout["schedule"] in (0, 1, 2)
+        hs.hs_batch_run(ba, betas, 3, 0)
+        hs.hs_batch_run(bb, betas, 3, 0)
+        for x, y in zip(a, b):
+            assert np.array_equal(x.get_spins(), y.get_spins())
+    finally:
+        hs.hs_batch_destroy(ba)
+        hs.hs_batch_destroy(bb)
+        for m in a + b + c:
             m.close()
 
 

@@ -255,3 +255,32 @@ def test_whole_part_is_the_pass():
             out.append((lat.get_spins(), hs.hs_read_sums(lat.h), lat.info.sweep))
     assert np.array_equal(out[0][0], out[1][0])
     assert np.array_equal(out[0][1], out[1][1]) and out[0][2] == out[1][2] == 1
+
+
+@pytest.mark.parametrize("overlap", [False, True])
+def test_distributed_slab_without_a_process_group(overlap):
+    """No torch.distributed group: one slab, its own periodic neighbour, no
+    collective (the one-process form of the strong-scaling run)."""
+    import torch.distributed as dist
+    assert not dist.is_initialized()
+    dims = (16, 8, 8)
+    n = dims[0] * dims[1] * dims[2]
+    S0 = storage_round(inputs.random_unit_spins(n, 6), "fp32")
+    with hs.Lattice("sc", dims=dims, precision="fp32", seed=3, **PARAMS) as whole:
+        whole.set_spins(S0)
+        whole.accumulate(True)
+        whole.sweep(0.9, 3)
+        want, want_mom = whole.get_spins(), whole.read_accumulator()
+    ds = shards.DistributedSlab(dims, precision="fp32", seed=3, overlap=overlap, **PARAMS)
+    try:
+        assert (ds.rank, ds.world) == (0, 1)
+        ds.set_spins(S0)
+        ds.accumulate(True)
+        ds.sweep(0.9, 3)
+        assert np.array_equal(ds.get_spins(), want)
+        mom, cnt = ds.read_accumulator()
+        assert cnt == want_mom[1] == 3
+        np.testing.assert_allclose(mom, want_mom[0], rtol=2e-6, atol=1e-9)
+        _sums_close(ds.last_observables(), hs.hs_read_sums(ds.slab.h), n)
+    finally:
+        ds.close()
