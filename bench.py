@@ -444,6 +444,46 @@ def run_variants(args, rank, stream, barrier_sync, world, dev):
                       "hbm_frac": round(n_spins * args.batch_sweeps * 36 / sec / 1e9 / peaks["hbm_gbs"], 4),
                       "what": "one persistent cooperative kernel (CUDA graph), FP32 spins, FP64 moments",
                       "binder_u4": {str(L): v for L, v in u4.items()}}
+    # (1b) the same 64 replicas as FP64 and as FP16 batches (the FP32 batch against plain FP64 in one form),
+    #      their default layout, fewer sweeps for FP64 (bound by the FP64 pipe)
+    per_prec = {}
+    for prec, sweeps in (("fp64", max(2, args.batch_sweeps // 20)), ("fp16", args.batch_sweeps // 2)):
+        lats = [hs.Lattice("sc", dims=(BATCH_SIZES[r % 6],) * 3, J=1.0, K=0.0, precision=prec, seed=4,
+                           replica=64 * rank + r, stream=stream) for r in range(64)]
+        for m in lats:
+            m.init()
+        batch = hs.hs_batch_create([m.h for m in lats])
+        hs.hs_batch_run(batch, betas, 2, 2)
+        sec = _timed(stream, lambda: hs.hs_batch_run(batch, betas, sweeps, 0))
+        per_prec[prec] = {"value": round(n_spins * sweeps / (sec * 1e9), 3), "sweeps": sweeps,
+                          "layout": hs.hs_batch_get_layout(batch),
+                          "hbm_frac": round(n_spins * sweeps * 3 * BYTES_PER_SPIN[prec] / sec / 1e9 / peaks["hbm_gbs"], 4)}
+        hs.hs_batch_destroy(batch)
+        for m in lats:
+            m.close()
+    out["batched"]["precisions"] = per_prec
+    # (1c) many small lattices: 304 replicas of 16^3 (K = 0, T 1.30 ... 1.60), the resident schedule (the default
+    #      for 32 or more members that fit a CTA's shared memory) against the persistent one
+    lats = [hs.Lattice("sc", dims=(16,) * 3, J=1.0, K=0.0, precision="fp32", seed=8, replica=304 * rank + r,
+                       stream=stream) for r in range(304)]
+    betas16 = [1.0 / (1.30 + 0.30 * r / 303) for r in range(304)]
+    for m in lats:
+        m.init()
+    batch = hs.hs_batch_create([m.h for m in lats])
+    small = {"replicas": 304, "n_spins_total": 304 * 16 ** 3, "sweeps": args.batch_sweeps // 4}
+    for name, sched in (("resident", 2), ("persistent", 0)):
+        hs.hs_batch_set_layout(batch, 2, 2, 0, sched)
+        hs.hs_batch_run(batch, betas16, 2, 2)
+        sec = _timed(stream, lambda: hs.hs_batch_run(batch, betas16, small["sweeps"], 0))
+        small[name] = round(small["n_spins_total"] * small["sweeps"] / (sec * 1e9), 3)
+    small["value"] = small["resident"]
+    small["unit"] = UNIT
+    small["what"] = ("one CTA per replica, its 48 KB of FP32 planes in shared memory for every sweep (batch "
+                     "schedule 2); persistent: the streaming kernel with a grid barrier per colour pass")
+    hs.hs_batch_destroy(batch)
+    for m in lats:
+        m.close()
+    out["batched_small"] = small
     # (2) sc 464^3, K = 0.1, T = 1.0, 200 sweeps: FP16 vs FP32 vs FP64 (bias against FP64)
     L5 = 464
     N5 = L5 ** 3

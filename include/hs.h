@@ -297,10 +297,10 @@ int hs_colour_greedy(int64_t n, const int64_t *row_ptr, const int32_t *col_idx,
 /* Batched replicas: many independent lattices advanced together by one
  * persistent kernel (cooperative launch, captured once in a CUDA graph per
  * (n_sweeps, n_equil) pair), each member at its own beta, with its own seed,
- * replica, sweep counter and accumulator.  Members must be FP32 unmasked
- * periodic sc lattices with Lx divisible by 8 (any sizes, mixed), created on
- * one stream and device; they stay owned by the caller and must outlive the
- * batch.  hs_batch_run performs n_equil sweeps, then n_sweeps sweeps whose
+ * replica, sweep counter and accumulator.  Members must be unmasked periodic
+ * sc lattices of one precision (FP64, FP32 or FP16; any sizes, mixed) with
+ * Lx divisible by 8 (FP32, FP16) or 4 (FP64), created on one stream and
+ * device; they stay owned by the caller and must outlive the batch.  hs_batch_run performs n_equil sweeps, then n_sweeps sweeps whose
  * moments are added to each member's accumulator (as hs_sweep with
  * accumulation on would), with the same random numbers and arithmetic as
  * hs_sweep on each member alone.  Colour passes are separated by a grid-wide
@@ -327,7 +327,8 @@ void hs_batch_destroy(hs_batch *b);
  * the bounded grid barrier, captured in a CUDA graph; schedule 1: one launch
  * per colour pass of every member, consecutive launches chained by
  * programmatic dependent launch), and, when every member's six planes fit
- * in one CTA's shared memory (FP32 sc up to L = 26 on GB300), schedule 2:
+ * in one CTA's shared memory (on GB300 cubes up to L = 24 in FP32, 20 in
+ * FP64, 32 in FP16), schedule 2:
  * one launch with one CTA per member, whose planes are copied into shared
  * memory once and stay there for every sweep, the colour passes separated
  * by CTA barriers only (no grid barrier, no global traffic between the

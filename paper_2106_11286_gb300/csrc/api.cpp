@@ -26,6 +26,7 @@
 #include <string>
 #include <vector>
 
+#include "batch.h"
 #include "hs_impl.h"
 #include "slab.h"
 
@@ -1402,6 +1403,7 @@ struct hs_batch {
     int schedule = 0;                              // 0: one persistent launch, 1: a launch per colour pass,
                                                    // 2: resident (one CTA per member, in shared memory)
     size_t resident_bytes = 0;                     // the largest member's six planes
+    int precision = HS_FP32;                       // every member's
     ~hs_batch() {
         cudaStreamSynchronize(stream);
         if (exec) cudaGraphExecDestroy(exec);
@@ -1512,7 +1514,7 @@ int batch_layout(hs_batch *b, int ctas_per_sm, int align_rows) {
     std::vector<int64_t> items(n), offset(n + 1, 0), row(n);
     for (int r = 0; r < n; ++r) {
         const Layout &L = b->members[r]->L;
-        row[r] = L.Lh / 4;
+        row[r] = L.Lh / hs::batch_vec(b->precision);
         items[r] = (int64_t)L.Lz * L.Ly * row[r];
         offset[r + 1] = offset[r] + items[r];
     }
@@ -1604,43 +1606,50 @@ int hs_batch_create(hs_batch **out, hs_lattice *const *members, int n_members) {
         if (!h) return fail(HS_E_INVALID, "null member");
         if (h->stream != members[0]->stream || h->device != members[0]->device)
             return fail(HS_E_INVALID, "members must share one stream and device");
-        if (!h->L.structured || h->L.slab || h->precision != HS_FP32 || h->L.Lh % 4 != 0)
-            return fail(HS_E_INVALID, "batch members must be FP32 unmasked periodic sc with Lx divisible by 8");
+        if (!h->L.structured || h->L.slab || h->L.Lh % hs::batch_vec(h->precision) != 0)
+            return fail(HS_E_INVALID,
+                        "batch members must be unmasked periodic sc with Lx divisible by 8 (FP32, FP16) or 4 (FP64)");
+        if (h->precision != members[0]->precision) return fail(HS_E_INVALID, "batch members must share one precision");
         if (h->tensor) return fail(HS_E_INVALID, "batch members take no anisotropy tensor term");
         for (int q = 0; q < r; ++q)
             if (members[q] == h) return fail(HS_E_INVALID, "a lattice appears twice in the batch");
     }
-    const int occ = std::min(hs::batch_occupancy(0), hs::batch_occupancy(1));
+    const int precision = members[0]->precision;
+    const int occ = std::min(hs::batch_occupancy(precision, 0), hs::batch_occupancy(precision, 1));
     if (occ < 1) return fail(HS_E_CUDA, "batch kernel does not fit on an SM");
     hs_batch *b = new (std::nothrow) hs_batch();
     if (!b) return fail(HS_E_OOM, "host allocation failed");
     b->members.assign(members, members + n_members);
     b->stream = members[0]->stream;
+    b->precision = precision;
     b->occ = occ;
     b->host_members.resize(n_members);
     for (int r = 0; r < n_members; ++r) {
         hs::BatchMember &m = b->host_members[r];
         const hs_lattice *h = members[r];
         const Layout &L = h->L;
-        m.planes = static_cast<float *>(L.planes);
+        m.planes = L.planes;
         m.Lx = L.Lx;
         m.Ly = L.Ly;
         m.Lz = L.Lz;
         m.Lh = L.Lh;
-        m.div_nxv = hs::FastDiv((uint32_t)(L.Lh / 4));
+        m.div_nxv = hs::FastDiv((uint32_t)(L.Lh / hs::batch_vec(precision)));
         m.div_ly = hs::FastDiv((uint32_t)L.Ly);
         m.fJ = (float)h->p.J;
         m.fK = (float)h->p.K;
+        m.J = h->p.J;
+        m.K = h->p.K;
         for (int q = 0; q < 3; ++q) {
             m.fe[q] = (float)h->p.e[q];
             m.e[q] = h->p.e[q];
         }
+        m.sc_tab = h->sc_tab;
         m.key0 = (uint32_t)h->seed;
         m.key1 = (uint32_t)(h->seed >> 32);
         m.replica = h->replica;
         m.n_present = (double)L.n_present;
         m.acc = h->acc;
-        b->resident_bytes = std::max(b->resident_bytes, (size_t)6 * L.Lz * L.Ly * L.Lh * sizeof(float));
+        b->resident_bytes = std::max(b->resident_bytes, (size_t)6 * L.Lz * L.Ly * L.Lh * hs::storage_size(precision));
     }
     cudaError_t e;
     if ((e = cudaMalloc(&b->d_members, sizeof(hs::BatchMember) * n_members)) != cudaSuccess ||
@@ -1659,7 +1668,7 @@ int hs_batch_create(hs_batch **out, hs_lattice *const *members, int n_members) {
     }
     // many small members: the resident schedule (measured 1.6-2x the persistent one from 64 members of 16^3
     // up; slower with 16 members of 24^3, which leave most SMs idle)
-    if (n_members >= kResidentMinMembers && b->resident_bytes <= hs::batch_resident_limit()) b->schedule = 2;
+    if (n_members >= kResidentMinMembers && b->resident_bytes <= hs::batch_resident_limit(precision)) b->schedule = 2;
     *out = b;
     return HS_OK;
 }
@@ -1675,6 +1684,7 @@ int hs_batch_run(hs_batch *b, const double *betas, int64_t n_sweeps, int64_t n_e
     for (int r = 0; r < n; ++r) {
         hs_lattice *h = b->members[r];
         b->host_members[r].fbeta = (float)betas[r];
+        b->host_members[r].beta = betas[r];
         b->host_members[r].sweep0 = (uint32_t)h->sweep;
         h->last_n_sweeps = n_total;
         HS_CUDA(cudaMemsetAsync(&h->acc->accepted, 0, sizeof(double), b->stream));
@@ -1686,19 +1696,19 @@ int hs_batch_run(hs_batch *b, const double *betas, int64_t n_sweeps, int64_t n_e
     HS_CUDA(cudaMemsetAsync(b->d_error, 0, sizeof(int), b->stream));
     hs::BatchArgs args = batch_args(b, n_total, n_eq);
     if (b->schedule == 1 && !b->inject_timeout) {  // chained launches on the stream, no graph
-        HS_CUDA(hs::launch_batch_passes(args, b->grid, b->stream, b->prefetch));
+        HS_CUDA(hs::launch_batch_passes(b->precision, args, b->grid, b->stream, b->prefetch));
         for (int r = 0; r < n; ++r) b->members[r]->sweep += (uint64_t)n_total;
         return HS_OK;
     }
     if (b->inject_timeout) {  // test hook: launched directly, never captured
         args.inject_skip = 1;
         b->inject_timeout = 0;
-        HS_CUDA(hs::launch_batch(args, b->grid, b->stream, b->prefetch));
+        HS_CUDA(hs::launch_batch(b->precision, args, b->grid, b->stream, b->prefetch));
         for (int r = 0; r < n; ++r) b->members[r]->sweep += (uint64_t)n_total;
         return HS_OK;
     }
     if (b->schedule == 2) {  // one launch: every member resident in its CTA's shared memory
-        HS_CUDA(hs::launch_batch_resident(args, b->resident_bytes, b->stream));
+        HS_CUDA(hs::launch_batch_resident(b->precision, args, b->resident_bytes, b->stream));
         for (int r = 0; r < n; ++r) b->members[r]->sweep += (uint64_t)n_total;
         return HS_OK;
     }
@@ -1712,7 +1722,7 @@ int hs_batch_run(hs_batch *b, const double *betas, int64_t n_sweeps, int64_t n_e
         cudaGraph_t graph = nullptr;
         bool ok = cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
         if (ok) {
-            const cudaError_t le = hs::launch_batch(args, b->grid, b->cap_stream, b->prefetch);
+            const cudaError_t le = hs::launch_batch(b->precision, args, b->grid, b->cap_stream, b->prefetch);
             ok = (cudaStreamEndCapture(b->cap_stream, &graph) == cudaSuccess) && le == cudaSuccess;
         }
         if (ok) ok = cudaGraphInstantiate(&b->exec, graph, 0) == cudaSuccess;
@@ -1729,7 +1739,7 @@ int hs_batch_run(hs_batch *b, const double *betas, int64_t n_sweeps, int64_t n_e
     if (b->exec) {
         HS_CUDA(cudaGraphLaunch(b->exec, b->stream));
     } else {
-        HS_CUDA(hs::launch_batch(args, b->grid, b->stream, b->prefetch));
+        HS_CUDA(hs::launch_batch(b->precision, args, b->grid, b->stream, b->prefetch));
     }
     for (int r = 0; r < n; ++r) b->members[r]->sweep += (uint64_t)n_total;
     return HS_OK;
@@ -1758,7 +1768,7 @@ int hs_batch_autotune(hs_batch *b, const double *betas, int n_trial_sweeps) {
     for (int r = 0; r < n; ++r) {
         hs_lattice *h = b->members[r];
         const Layout &L = h->L;
-        saved[r].bytes = (size_t)6 * L.Lz * L.Ly * L.Lh * sizeof(float);
+        saved[r].bytes = (size_t)6 * L.Lz * L.Ly * L.Lh * hs::storage_size(b->precision);
         saved[r].sweep = h->sweep;
         saved[r].last_n = h->last_n_sweeps;
         cudaError_t e = cudaMalloc(&saved[r].planes, saved[r].bytes);
@@ -1790,7 +1800,7 @@ int hs_batch_autotune(hs_batch *b, const double *betas, int n_trial_sweeps) {
     float best_ms = 0.f;
     bool have = false;
     if (st == HS_OK && cudaStreamSynchronize(b->stream) != cudaSuccess) st = fail(HS_E_CUDA, "synchronise");
-    const int max_sc = b->resident_bytes <= hs::batch_resident_limit() ? 2 : 1;
+    const int max_sc = b->resident_bytes <= hs::batch_resident_limit(b->precision) ? 2 : 1;
     for (int sc = 0; st == HS_OK && sc <= max_sc; ++sc)
     for (int pf = 0; st == HS_OK && pf <= (sc == 2 ? 0 : 1); ++pf)
     for (int c = (sc == 2 ? b->occ : 1); st == HS_OK && c <= b->occ; ++c)
@@ -1834,7 +1844,7 @@ int hs_batch_set_layout(hs_batch *b, int ctas_per_sm, int align_rows, int prefet
     if (ctas_per_sm < 1 || ctas_per_sm > b->occ) return fail(HS_E_INVALID, "ctas_per_sm out of range");
     if (align_rows < 0 || align_rows > 2 || (prefetch != 0 && prefetch != 1) || schedule < 0 || schedule > 2)
         return fail(HS_E_INVALID, "align_rows must be 0, 1 or 2, prefetch 0 or 1, schedule 0, 1 or 2");
-    if (schedule == 2 && b->resident_bytes > hs::batch_resident_limit())
+    if (schedule == 2 && b->resident_bytes > hs::batch_resident_limit(b->precision))
         return fail(HS_E_INVALID, "the resident schedule needs every member's spins in one CTA's shared memory");
     b->prefetch = prefetch;
     b->schedule = schedule;

@@ -1,9 +1,10 @@
-// Batched replicas in one persistent kernel: many FP32 periodic sc lattices of
-// uneven size, each at its own beta, advanced sweep by sweep (Metropolis
-// steps (i)-(iii) of arXiv 2106.11286, colour class by colour class) with the
-// E / M moments of Eq. 1 / Eq. 2 accumulated per member in FP64.
+// Batched replicas in one persistent kernel: many periodic sc lattices of one
+// precision (FP64, FP32 or FP16) and uneven size, each at its own beta,
+// advanced sweep by sweep (Metropolis steps (i)-(iii) of arXiv 2106.11286,
+// colour class by colour class) with the E / M moments of Eq. 1 / Eq. 2
+// accumulated per member in FP64.
 //
-// Work split: the members' items (4 sites of a row of one colour) are
+// Work split: the members' items (2 FP64 or 4 FP32 / FP16 sites of a row of one colour) are
 // concatenated and cut into equal contiguous chunks, one per CTA; a chunk may
 // cover several members, and each (CTA, member) piece is a segment with its
 // own FP64 reduction slot, so the per-member sums are taken in a fixed order
@@ -15,6 +16,7 @@
 // here than cached loads behind the barrier's GPU-scope fences).
 #include <cuda_runtime.h>
 
+#include "batch.h"
 #include "device.cuh"
 
 namespace hs {
@@ -79,6 +81,13 @@ __device__ __forceinline__ PassArgs member_args(const BatchMember &m, int colour
     a.fe[1] = m.fe[1];
     a.fe[2] = m.fe[2];
     a.fbeta = m.fbeta;
+    a.J = m.J;
+    a.K = m.K;
+    a.e[0] = m.e[0];
+    a.e[1] = m.e[1];
+    a.e[2] = m.e[2];
+    a.beta = m.beta;
+    a.sc_tab = m.sc_tab;
     a.key0 = m.key0;
     a.key1 = m.key1;
     a.replica = m.replica;
@@ -151,18 +160,21 @@ __device__ void finalize_sweep(const BatchArgs &b, int s) {
 // single-lattice stencil: once the current item's local fields are summed,
 // the next item's own row, same-row, z-1 and z+1 rows are loaded and travel
 // during the current item's arithmetic.  PF = 0: one item of loads at a time.
-template <int PF, bool CG>
+template <int P>
+constexpr int kBatchVec = (P == HS_FP64) ? 2 : 4;  // batch_vec()
+
+template <int P, int PF, bool CG>
 __device__ __forceinline__ void batch_pass(const BatchArgs &b, int s, int c) {
-    constexpr int P = HS_FP32;
-    constexpr int V = 4;
-    using VT = Vec<float, V>;
-    using C = float;
+    constexpr int V = kBatchVec<P>;
+    using S = typename Tr<P>::S;
+    using VT = Vec<S, V>;
+    using C = typename Tr<P>::C;
     __shared__ double s_red[kBlock / 32][kPartials];
     // the current segment's member parameters and plane pointers (own colour
     // x, y, z, then the other colour's), read from shared memory where used
     // rather than held in registers
     __shared__ PassArgs s_args;
-    __shared__ float *s_planes[6];
+    __shared__ S *s_planes[6];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int par = s & 1;  // slot parity this sweep writes
     for (int si = b.cta_seg[blockIdx.x]; si < b.cta_seg[blockIdx.x + 1]; ++si) {
@@ -172,18 +184,19 @@ __device__ __forceinline__ void batch_pass(const BatchArgs &b, int s, int c) {
         if (threadIdx.x == 0) {
             s_args = member_args(m, c, m.sweep0 + (uint32_t)s);
             const size_t plane = (size_t)m.Lz * m.Ly * m.Lh;
+            S *const base = static_cast<S *>(m.planes);
 #pragma unroll
             for (int q = 0; q < 3; ++q) {
-                s_planes[q] = m.planes + (size_t)(3 * c + q) * plane;
-                s_planes[3 + q] = m.planes + (size_t)(3 * (1 - c) + q) * plane;
+                s_planes[q] = base + (size_t)(3 * c + q) * plane;
+                s_planes[3 + q] = base + (size_t)(3 * (1 - c) + q) * plane;
             }
         }
         __syncthreads();
         const PassArgs &a = s_args;
-        float *const(&own_w)[3] = *reinterpret_cast<float *const(*)[3]>(&s_planes[0]);
-        const float *const(&own)[3] = *reinterpret_cast<const float *const(*)[3]>(&s_planes[0]);
-        const float *const(&oth)[3] = *reinterpret_cast<const float *const(*)[3]>(&s_planes[3]);
-        float J, K, ex, ey, ez, beta;
+        S *const(&own_w)[3] = *reinterpret_cast<S *const(*)[3]>(&s_planes[0]);
+        const S *const(&own)[3] = *reinterpret_cast<const S *const(*)[3]>(&s_planes[0]);
+        const S *const(&oth)[3] = *reinterpret_cast<const S *const(*)[3]>(&s_planes[3]);
+        C J, K, ex, ey, ez, beta;
         load_params(a, J, K, ex, ey, ez, beta);
         SiteAcc<P> acc;
         if constexpr (PF == 2) {
@@ -221,10 +234,10 @@ __device__ __forceinline__ void batch_pass(const BatchArgs &b, int s, int c) {
             }
         }
         // segment partials: warp shuffle -> CTA (FP64) -> slot
-        const float accE = warp_sum(acc.E());
-        const float accX = warp_sum(acc.X());
-        const float accY = warp_sum(acc.Y());
-        const float accZ = warp_sum(acc.Z());
+        const C accE = warp_sum(acc.E());
+        const C accX = warp_sum(acc.X());
+        const C accY = warp_sum(acc.Y());
+        const C accZ = warp_sum(acc.Z());
         const unsigned nacc = __reduce_add_sync(0xffffffffu, acc.n);
         if (lane == 0) {
             s_red[warp][0] = accE;
@@ -245,12 +258,12 @@ __device__ __forceinline__ void batch_pass(const BatchArgs &b, int s, int c) {
 
 // The persistent schedule: every sweep and colour pass in one cooperative
 // launch, passes separated by the bounded grid barrier.
-template <int PF>
+template <int P, int PF>
 __global__ void __launch_bounds__(kBlock, 2) batch_kernel(const BatchArgs b) {
     unsigned long long *cnt = reinterpret_cast<unsigned long long *>(b.bar);
     for (int s = 0; s < b.n_total; ++s) {
         for (int c = 0; c < 2; ++c) {
-            batch_pass<PF, true>(b, s, c);
+            batch_pass<P, PF, true>(b, s, c);
             const bool skip = b.inject_skip && blockIdx.x == 0 && s == 0 && c == 0;
             barrier_arrive(cnt, skip);
             // the previous sweep's finalise runs while this CTA waits for the
@@ -274,11 +287,11 @@ __global__ void __launch_bounds__(kBlock, 2) batch_kernel(const BatchArgs b) {
 // touching memory).  Pass 0 of sweep s first finalises sweep s - 1, whose
 // passes have completed by then; the slots it reads (parity (s-1) & 1) are
 // rewritten only by pass 0 of sweep s + 1, two completed launches later.
-template <int PF>
+template <int P, int PF>
 __global__ void __launch_bounds__(kBlock, 2) batch_pass_kernel(const BatchArgs b, int s, int c) {
     pdl_enter();
     if (c == 0 && s > 0) finalize_sweep(b, s - 1);
-    batch_pass<PF, false>(b, s, c);
+    batch_pass<P, PF, false>(b, s, c);
 }
 
 // The last sweep's finalise of the per-pass schedule.
@@ -296,19 +309,22 @@ __global__ void __launch_bounds__(kBlock) batch_finalize_kernel(const BatchArgs 
 // the streaming kernels, on generic pointers into shared memory, so the chain
 // is bit-identical; each sweep's FP64 totals (the two passes' CTA sums, in a
 // fixed order) go straight to the member's accumulator.
+template <int P>
 __global__ void __launch_bounds__(kBlock, 2) batch_resident_kernel(const BatchArgs b) {
-    constexpr int P = HS_FP32;
-    constexpr int V = 4;
-    using VT = Vec<float, V>;
-    extern __shared__ float4 s_state[];
+    constexpr int V = kBatchVec<P>;
+    using S = typename Tr<P>::S;
+    using VT = Vec<S, V>;
+    using C = typename Tr<P>::C;
+    extern __shared__ uint4 s_state[];
     __shared__ double s_red[kBlock / 32][kPartials];
     __shared__ PassArgs s_args;
     const BatchMember &m = b.members[blockIdx.x];
-    const uint32_t plane = (uint32_t)m.Lz * m.Ly * m.Lh;  // elements of one component plane; Lh % 4 == 0
-    const uint32_t n4 = 6u * plane / 4u;
-    const float4 *g4 = reinterpret_cast<const float4 *>(m.planes);
-    for (uint32_t i = threadIdx.x; i < n4; i += kBlock) s_state[i] = __ldcg(g4 + i);
-    float *const st = reinterpret_cast<float *>(s_state);
+    const uint32_t plane = (uint32_t)m.Lz * m.Ly * m.Lh;  // elements of one component plane; Lh % V == 0
+    // six planes in 16-byte chunks (6 plane sizeof(S) is a multiple of 48 bytes)
+    const uint32_t n16 = (uint32_t)(6u * (size_t)plane * sizeof(S) / 16u);
+    const uint4 *g16 = static_cast<const uint4 *>(m.planes);
+    for (uint32_t i = threadIdx.x; i < n16; i += kBlock) s_state[i] = __ldcg(g16 + i);
+    S *const st = reinterpret_cast<S *>(s_state);
     const uint32_t n_items = plane / V;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int s = 0; s < b.n_total; ++s) {
@@ -317,15 +333,15 @@ __global__ void __launch_bounds__(kBlock, 2) batch_resident_kernel(const BatchAr
             if (threadIdx.x == 0) s_args = member_args(m, c, m.sweep0 + (uint32_t)s);
             __syncthreads();  // the parameters, and every store of the previous pass (or the initial copy)
             const PassArgs &a = s_args;
-            float *own_w[3];
-            const float *own[3], *oth[3];
+            S *own_w[3];
+            const S *own[3], *oth[3];
 #pragma unroll
             for (int q = 0; q < 3; ++q) {
                 own_w[q] = st + (size_t)(3 * c + q) * plane;
                 own[q] = own_w[q];
                 oth[q] = st + (size_t)(3 * (1 - c) + q) * plane;
             }
-            float J, K, ex, ey, ez, beta;
+            C J, K, ex, ey, ez, beta;
             load_params(a, J, K, ex, ey, ez, beta);
             SiteAcc<P> acc;
             for (uint32_t t = threadIdx.x; t < n_items; t += kBlock) {
@@ -338,10 +354,10 @@ __global__ void __launch_bounds__(kBlock, 2) batch_resident_kernel(const BatchAr
                 }
             }
             // the pass's sums: warp shuffle -> CTA (FP64), added to the sweep's totals in warp order
-            const float accE = warp_sum(acc.E());
-            const float accX = warp_sum(acc.X());
-            const float accY = warp_sum(acc.Y());
-            const float accZ = warp_sum(acc.Z());
+            const C accE = warp_sum(acc.E());
+            const C accX = warp_sum(acc.X());
+            const C accY = warp_sum(acc.Y());
+            const C accZ = warp_sum(acc.Z());
             const unsigned nacc = __reduce_add_sync(0xffffffffu, acc.n);
             if (lane == 0) {
                 s_red[warp][0] = accE;
@@ -359,8 +375,8 @@ __global__ void __launch_bounds__(kBlock, 2) batch_resident_kernel(const BatchAr
         if (threadIdx.x == 0) member_apply_sweep(m, tot, s >= b.n_equil);
     }
     __syncthreads();
-    float4 *w4 = reinterpret_cast<float4 *>(m.planes);
-    for (uint32_t i = threadIdx.x; i < n4; i += kBlock) w4[i] = s_state[i];
+    uint4 *w16 = static_cast<uint4 *>(m.planes);
+    for (uint32_t i = threadIdx.x; i < n16; i += kBlock) w16[i] = s_state[i];
 }
 
 template <typename... KArgs, typename... Args>
@@ -380,44 +396,51 @@ cudaError_t launch_chained(void (*kernel)(KArgs...), int grid, cudaStream_t s, A
 
 }  // namespace
 
-int batch_occupancy(int prefetch) {
+namespace {
+template <int P>
+int occupancy_p(int prefetch) {
     int blocks = 0, blocks_pass = 0;
-    const void *k = prefetch ? (const void *)batch_kernel<2> : (const void *)batch_kernel<0>;
-    const void *kp = prefetch ? (const void *)batch_pass_kernel<2> : (const void *)batch_pass_kernel<0>;
+    const void *k = prefetch ? (const void *)batch_kernel<P, 2> : (const void *)batch_kernel<P, 0>;
+    const void *kp = prefetch ? (const void *)batch_pass_kernel<P, 2> : (const void *)batch_pass_kernel<P, 0>;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k, kBlock, 0) != cudaSuccess) return 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_pass, kp, kBlock, 0) != cudaSuccess) return 0;
     return blocks < blocks_pass ? blocks : blocks_pass;
 }
 
-cudaError_t launch_batch_passes(const BatchArgs &b, int grid, cudaStream_t s, int prefetch) {
+template <int P>
+cudaError_t passes_p(const BatchArgs &b, int grid, cudaStream_t s, int prefetch) {
     for (int sw = 0; sw < b.n_total; ++sw)
         for (int c = 0; c < 2; ++c) {
-            const cudaError_t e = prefetch ? launch_chained(batch_pass_kernel<2>, grid, s, b, sw, c)
-                                           : launch_chained(batch_pass_kernel<0>, grid, s, b, sw, c);
+            const cudaError_t e = prefetch ? launch_chained(batch_pass_kernel<P, 2>, grid, s, b, sw, c)
+                                           : launch_chained(batch_pass_kernel<P, 0>, grid, s, b, sw, c);
             if (e != cudaSuccess) return e;
         }
     if (b.n_total > 0) return launch_chained(batch_finalize_kernel, grid, s, b, b.n_total - 1);
     return cudaSuccess;
 }
 
-size_t batch_resident_limit() {
+template <int P>
+size_t resident_limit_p() {
     int dev = 0, optin = 0;
     cudaFuncAttributes fa{};
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
-        cudaFuncGetAttributes(&fa, batch_resident_kernel) != cudaSuccess)
+        cudaFuncGetAttributes(&fa, batch_resident_kernel<P>) != cudaSuccess)
         return 0;
     return optin > (int)fa.sharedSizeBytes ? (size_t)optin - fa.sharedSizeBytes : 0;
 }
 
-cudaError_t launch_batch_resident(const BatchArgs &b, size_t smem, cudaStream_t s) {
-    cudaError_t e = cudaFuncSetAttribute(batch_resident_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+template <int P>
+cudaError_t resident_p(const BatchArgs &b, size_t smem, cudaStream_t s) {
+    cudaError_t e = cudaFuncSetAttribute(batch_resident_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
     if (e != cudaSuccess) return e;
-    batch_resident_kernel<<<b.n_members, kBlock, smem, s>>>(b);
+    batch_resident_kernel<P><<<b.n_members, kBlock, smem, s>>>(b);
     return cudaGetLastError();
 }
 
-cudaError_t launch_batch(const BatchArgs &b, int grid, cudaStream_t s, int prefetch) {
+template <int P>
+cudaError_t persistent_p(const BatchArgs &b, int grid, cudaStream_t s, int prefetch) {
     cudaLaunchConfig_t cfg{};
     cfg.gridDim = dim3((unsigned)grid);
     cfg.blockDim = dim3(kBlock);
@@ -428,7 +451,53 @@ cudaError_t launch_batch(const BatchArgs &b, int grid, cudaStream_t s, int prefe
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return prefetch ? cudaLaunchKernelEx(&cfg, batch_kernel<2>, b) : cudaLaunchKernelEx(&cfg, batch_kernel<0>, b);
+    return prefetch ? cudaLaunchKernelEx(&cfg, batch_kernel<P, 2>, b) : cudaLaunchKernelEx(&cfg, batch_kernel<P, 0>, b);
+}
+}  // namespace
+
+int batch_occupancy(int precision, int prefetch) {
+    switch (precision) {
+    case HS_FP64: return occupancy_p<HS_FP64>(prefetch);
+    case HS_FP32: return occupancy_p<HS_FP32>(prefetch);
+    case HS_FP16: return occupancy_p<HS_FP16>(prefetch);
+    default: return 0;
+    }
+}
+
+cudaError_t launch_batch_passes(int precision, const BatchArgs &b, int grid, cudaStream_t s, int prefetch) {
+    switch (precision) {
+    case HS_FP64: return passes_p<HS_FP64>(b, grid, s, prefetch);
+    case HS_FP32: return passes_p<HS_FP32>(b, grid, s, prefetch);
+    case HS_FP16: return passes_p<HS_FP16>(b, grid, s, prefetch);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+size_t batch_resident_limit(int precision) {
+    switch (precision) {
+    case HS_FP64: return resident_limit_p<HS_FP64>();
+    case HS_FP32: return resident_limit_p<HS_FP32>();
+    case HS_FP16: return resident_limit_p<HS_FP16>();
+    default: return 0;
+    }
+}
+
+cudaError_t launch_batch_resident(int precision, const BatchArgs &b, size_t smem, cudaStream_t s) {
+    switch (precision) {
+    case HS_FP64: return resident_p<HS_FP64>(b, smem, s);
+    case HS_FP32: return resident_p<HS_FP32>(b, smem, s);
+    case HS_FP16: return resident_p<HS_FP16>(b, smem, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_batch(int precision, const BatchArgs &b, int grid, cudaStream_t s, int prefetch) {
+    switch (precision) {
+    case HS_FP64: return persistent_p<HS_FP64>(b, grid, s, prefetch);
+    case HS_FP32: return persistent_p<HS_FP32>(b, grid, s, prefetch);
+    case HS_FP16: return persistent_p<HS_FP16>(b, grid, s, prefetch);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 }  // namespace hs

@@ -140,54 +140,6 @@ struct Layout {
     int64_t colour_begin[65];  // renumbered colour ranges (n_colours + 1 entries)
 };
 
-// ---- batched persistent kernel (batch.cu)
-// One member lattice (FP32 periodic sc, stencil layout, vector width 4).
-struct BatchMember {
-    float *planes;
-    int Lx, Ly, Lz, Lh;
-    FastDiv div_nxv, div_ly;
-    float fJ, fK, fe[3], fbeta;
-    double e[3];
-    uint32_t key0, key1, replica;
-    uint32_t sweep0;        // the member's sweep index at batch sweep 0
-    double n_present;
-    DevAccum *acc;
-    int seg_begin, seg_end;  // the member's segments (contiguous)
-};
-
-// Items begin, begin + stride, ... (< end) of one member's colour pass,
-// each the first of kBlock consecutive items that one CTA's threads take
-// together: stride kBlock for a contiguous range; a multiple of kBlock when
-// several CTAs sweep one member side by side.
-struct BatchSeg {
-    int member;
-    uint32_t begin, end, stride;
-};
-
-struct BatchArgs {
-    const BatchMember *members;
-    int n_members;
-    const BatchSeg *segs;
-    const int *cta_seg;      // CTA c owns segments [cta_seg[c], cta_seg[c+1])
-    int n_segs;
-    double *slots;           // [sweep parity][colour][segment][kPartials]
-    unsigned int *bar;       // grid barrier: one 64-bit arrival count (two words, 8-byte aligned)
-    int *error;              // latched device error (barrier timeout)
-    int n_total, n_equil;    // sweeps, of which the first n_equil unmeasured
-    int inject_skip;         // test hook: 1 = CTA 0 skips its first barrier arrival
-};
-
-// prefetch 0: one work item of loads at a time; 1: split prefetch (the
-// next item's DRAM-heavy rows load during the current item's arithmetic)
-cudaError_t launch_batch(const BatchArgs &b, int grid, cudaStream_t s, int prefetch);
-// the per-pass schedule: 2 n_total chained pass launches and a finalise launch
-cudaError_t launch_batch_passes(const BatchArgs &b, int grid, cudaStream_t s, int prefetch);
-int batch_occupancy(int prefetch);
-// the resident schedule: one CTA per member, its planes in dynamic shared
-// memory (smem bytes, at most batch_resident_limit()) for the whole run
-cudaError_t launch_batch_resident(const BatchArgs &b, size_t smem, cudaStream_t s);
-size_t batch_resident_limit();
-
 size_t storage_size(int precision);
 
 // Record the thread-local message returned by hs_last_error; returns code.

@@ -40,9 +40,9 @@ def run_scan(sizes, temps, *, n_equil: int, n_blocks: int, block_sweeps: int, re
              K: float = 0.0, e=(0.0, 0.0, 1.0), precision: str = "fp32", seed: int = 2024, stream=None,
              init: str = "random") -> Scan:
     """Advance every (L, T, replica) sc lattice (L^3, periodic) and collect
-    block means.  FP32 lattices advance together in one hs_batch; FP64 and
-    FP16 lattices (which the batched kernel does not take) one after the
-    other with hs_sweep, block by block.  init = "random" starts from
+    block means.  The lattices advance together in one hs_batch (one
+    precision; L divisible by 8, or by 4 in FP64), else one after the other
+    with hs_sweep, block by block: the same chains either way.  init = "random" starts from
     independent uniform spins, "aligned" from every spin along e (the ordered
     state, which reaches equilibrium below T_c without coarsening).  Returns a
     Scan whose sample arrays have n_blocks * replicas entries per (L, T)."""
@@ -65,7 +65,7 @@ def run_scan(sizes, temps, *, n_equil: int, n_blocks: int, block_sweeps: int, re
     try:
         for m in members:
             m.init(hs.HS_INIT_RANDOM if init == "random" else hs.HS_INIT_ALIGNED)
-        if precision == "fp32":
+        if all(L % (4 if precision == "fp64" else 8) == 0 for L in sizes):   # the batch's row rule
             batch = hs.hs_batch_create([m.h for m in members])
             if n_equil:
                 hs.hs_batch_run(batch, betas, 0, n_equil)

@@ -1,4 +1,5 @@
-"""Batched replicas (one persistent kernel for many lattices of uneven size).
+"""Batched replicas (one persistent kernel for many lattices of uneven size,
+in one precision: FP64, FP32 or FP16).
 
 * The batch reproduces, member by member, what hs_sweep does on each lattice
   alone: identical spins, moments within the FP32 partial-sum tolerance.
@@ -16,16 +17,20 @@ from paper_2106_11286_gb300 import hs
 pytestmark = pytest.mark.gpu
 
 
-def _members(dims_list, betas, K=0.1, seed=11):
-    return [hs.Lattice("sc", dims=d, J=1.0, K=K, e=(0, 0, 1), precision="fp32", seed=seed, replica=r)
+def _members(dims_list, betas, K=0.1, seed=11, precision="fp32"):
+    return [hs.Lattice("sc", dims=d, J=1.0, K=K, e=(0, 0, 1), precision=precision, seed=seed, replica=r)
             for r, d in enumerate(dims_list)]
 
 
-def test_batch_matches_individual_sweeps():
+RTOL = {"fp64": 1e-12, "fp32": 2e-6, "fp16": 2e-6}   # moments: FP64 sums taken in another order
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64", "fp16"])
+def test_batch_matches_individual_sweeps(precision):
     dims = [(16, 16, 16), (24, 24, 24), (8, 8, 8), (32, 16, 8), (40, 8, 12)]
     betas = [0.6, 0.8, 1.0, 1.2, 0.9]
-    a = _members(dims, betas)
-    b = _members(dims, betas)
+    a = _members(dims, betas, precision=precision)
+    b = _members(dims, betas, precision=precision)
     for x, y in zip(a, b):
         x.init()
         y.init()
@@ -51,7 +56,7 @@ def test_batch_matches_individual_sweeps():
                 mx, cx = x.read_accumulator()
                 my, cy = y.read_accumulator()
                 assert cx == cy == n_sweeps
-                np.testing.assert_allclose(mx, my, rtol=2e-6, atol=1e-9)
+                np.testing.assert_allclose(mx, my, rtol=RTOL[precision], atol=1e-9)
                 assert x.info.sweep == y.info.sweep
                 # a batch run's acceptance rate covers all of its sweeps
                 assert x.measure()["accept_rate"] == pytest.approx(rate, abs=1e-12)
@@ -146,17 +151,20 @@ def test_batch_layouts_give_identical_chains(ctas, align, prefetch, schedule):
             m.close()
 
 
-def test_resident_schedule_gives_identical_chains():
-    """Schedule 2: every member (here up to 24^3, 166 KB of FP32 planes) in
-    one CTA's shared memory for the whole run.  Member by member the spins
-    equal hs_sweep on each lattice alone and the persistent batch's, bit for
-    bit, over repeated runs with and without equilibration; moments and
-    acceptance rates agree up to the order of the FP64 sums."""
-    dims = [(16, 16, 16), (24, 24, 24), (8, 8, 8), (16, 8, 24), (24, 16, 8), (8, 24, 16)]
+@pytest.mark.parametrize("precision", ["fp32", "fp64", "fp16"])
+def test_resident_schedule_gives_identical_chains(precision):
+    """Schedule 2: every member (here up to 24^3, 166 KB of FP32 planes; up
+    to 16^3, 98 KB, in FP64) in one CTA's shared memory for the whole run.
+    Member by member the spins equal hs_sweep on each lattice alone and the
+    persistent batch's, bit for bit, over repeated runs with and without
+    equilibration; moments and acceptance rates agree up to the order of the
+    FP64 sums."""
+    big = (12, 12, 12) if precision == "fp64" else (24, 24, 24)
+    dims = [(16, 16, 16), big, (8, 8, 8), (16, 8, 24), (24, 16, 8), (8, 24, 16)]
     betas = [0.6, 0.8, 1.0, 1.2, 0.9, 0.7]
-    a = _members(dims, betas)
-    b = _members(dims, betas)
-    c = _members(dims, betas)
+    a = _members(dims, betas, precision=precision)
+    b = _members(dims, betas, precision=precision)
+    c = _members(dims, betas, precision=precision)
     for m in a + b + c:
         m.init()
         m.accumulate(True)
@@ -182,8 +190,8 @@ def test_resident_schedule_gives_identical_chains():
                 my, cy = y.read_accumulator()
                 mz, cz = z.read_accumulator()
                 assert cx == cy == cz == n_sweeps
-                np.testing.assert_allclose(mx, my, rtol=2e-6, atol=1e-9)
-                np.testing.assert_allclose(mx, mz, rtol=2e-6, atol=1e-9)
+                np.testing.assert_allclose(mx, my, rtol=RTOL[precision], atol=1e-9)
+                np.testing.assert_allclose(mx, mz, rtol=RTOL[precision], atol=1e-9)
                 assert x.info.sweep == y.info.sweep == z.info.sweep
                 assert x.measure()["accept_rate"] == pytest.approx(y.measure()["accept_rate"], abs=1e-12)
         layout = hs.hs_batch_autotune(ba, betas, 2)   # the resident schedule is one of its candidates
@@ -199,13 +207,54 @@ def test_resident_schedule_gives_identical_chains():
             m.close()
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp16"])
+@pytest.mark.parametrize("ctas,align,prefetch,schedule", [(2, 2, 0, 0), (1, 0, 1, 0), (2, 1, 1, 1), (2, 2, 0, 1)])
+def test_batch_layouts_other_precisions(precision, ctas, align, prefetch, schedule):
+    """FP64 and FP16 batches: each work split, load and colour schedule gives
+    the spins of hs_sweep on each member alone, bit for bit."""
+    dims = [(16, 16, 16), (24, 24, 24), (8, 8, 8), (32, 16, 8), (48, 48, 48)]
+    betas = [0.6, 0.8, 1.0, 1.2, 0.9]
+    a = _members(dims, betas, precision=precision)
+    c = _members(dims, betas, precision=precision)
+    for m in a + c:
+        m.init()
+        m.accumulate(True)
+    ba = hs.hs_batch_create([m.h for m in a])
+    try:
+        hs.hs_batch_set_layout(ba, ctas, align, prefetch, schedule)
+        hs.hs_batch_run(ba, betas, 3, 2)
+        for m, beta in zip(c, betas):
+            m.accumulate(False)
+            m.sweep(beta, 2)
+            m.accumulate(True)
+            m.sweep(beta, 3)
+        for x, z in zip(a, c):
+            assert np.array_equal(x.get_spins(), z.get_spins())
+            mx, cx = x.read_accumulator()
+            mz, cz = z.read_accumulator()
+            assert cx == cz == 3
+            np.testing.assert_allclose(mx, mz, rtol=RTOL[precision], atol=1e-9)
+    finally:
+        hs.hs_batch_destroy(ba)
+        for m in a + c:
+            m.close()
+
+
 def test_batch_rejects_unsupported_members():
-    with hs.Lattice("sc", dims=(8, 8, 8), precision="fp64") as x:
+    with hs.Lattice("sc", dims=(8, 8, 8), precision="fp64") as x, \
+            hs.Lattice("sc", dims=(8, 8, 8), precision="fp32") as y:
+        with pytest.raises(hs.HSError):
+            hs.hs_batch_create([x.h, y.h])                        # two precisions
+    for precision in ("fp32", "fp16"):
+        with hs.Lattice("sc", dims=(12, 8, 8), precision=precision) as x:   # Lx/2 = 6 not divisible by 4
+            with pytest.raises(hs.HSError):
+                hs.hs_batch_create([x.h])
+    with hs.Lattice("sc", dims=(6, 8, 8), precision="fp64") as x:   # Lx/2 = 3 not divisible by 2
         with pytest.raises(hs.HSError):
             hs.hs_batch_create([x.h])
-    with hs.Lattice("sc", dims=(12, 8, 8), precision="fp32") as x:   # Lx/2 = 6 not divisible by 4
+    with hs.Lattice("sc", dims=(8, 8, 8), precision="fp32", site_mask=np.ones(512, dtype=np.uint8)) as x:
         with pytest.raises(hs.HSError):
-            hs.hs_batch_create([x.h])
+            hs.hs_batch_create([x.h])                              # the neighbour-table layout
 
 
 def _crossing(Ts, u_small, u_large):
