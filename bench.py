@@ -463,7 +463,7 @@ def run_variants(args, rank, stream, barrier_sync, world, dev):
             m.close()
     out["batched"]["precisions"] = per_prec
     # (1c) many small lattices: 304 replicas of 16^3 (K = 0, T 1.30 ... 1.60), the resident schedule (the default
-    #      for 32 or more members that fit a CTA's shared memory) against the persistent one
+    #      for 16 or more members that fit a CTA's shared memory) against the persistent one
     lats = [hs.Lattice("sc", dims=(16,) * 3, J=1.0, K=0.0, precision="fp32", seed=8, replica=304 * rank + r,
                        stream=stream) for r in range(304)]
     betas16 = [1.0 / (1.30 + 0.30 * r / 303) for r in range(304)]
@@ -1004,6 +1004,38 @@ CASES = {
 }
 
 
+# batch cases: name -> (replicas, L, precision, schedule)
+BATCH_CASES = {"batch304x16_resident": (304, 16, "fp32", 2), "batch304x16_persistent": (304, 16, "fp32", 0)}
+
+
+def run_batch_case(args):
+    """One batch of small replicas (K = 0, T 1.30 ... 1.60) in a fixed
+    schedule: 2 + 2 warm-up sweeps, then one batch run of args.steps sweeps
+    (one kernel launch in the resident schedule), for an ncu capture."""
+    import torch
+
+    from paper_2106_11286_gb300 import hs
+    n, L, prec, sched = BATCH_CASES[args.case]
+    lats = [hs.Lattice("sc", dims=(L,) * 3, J=1.0, K=0.0, precision=prec, seed=8, replica=r) for r in range(n)]
+    try:
+        betas = [1.0 / (1.30 + 0.30 * r / (n - 1)) for r in range(n)]
+        for m in lats:
+            m.init()
+        batch = hs.hs_batch_create([m.h for m in lats])
+        try:
+            hs.hs_batch_set_layout(batch, 2, 2, 0, sched)
+            hs.hs_batch_run(batch, betas, 2, 2)
+            sec = _timed(torch.cuda.current_stream(), lambda: hs.hs_batch_run(batch, betas, args.steps, 0))
+            layout = hs.hs_batch_get_layout(batch)
+        finally:
+            hs.hs_batch_destroy(batch)
+    finally:
+        for m in lats:
+            m.close()
+    return {"case": args.case, "layout": layout, "value": round(n * L ** 3 * args.steps / (sec * 1e9), 3),
+            "unit": UNIT, "steps": args.steps}
+
+
 def run_case(args):
     """One workload alone in its autotuned launch (tuned after 10 sweeps, as
     the bench's variants are), then args.steps sweeps: a fixed, short launch
@@ -1012,6 +1044,8 @@ def run_case(args):
     import torch
 
     from paper_2106_11286_gb300 import hs
+    if args.case in BATCH_CASES:
+        return run_batch_case(args)
     L, prec, K, T, seed = CASES[args.case]
     with hs.Lattice("sc", dims=(L,) * 3, J=1.0, K=K, e=(0, 0, 1), precision=prec, seed=seed) as lat:
         lat.init()
@@ -1062,7 +1096,7 @@ def main(argv=None):
     ap.add_argument("--beta-equil", type=int, default=3000)
     ap.add_argument("--beta-blocks", type=int, default=10)
     ap.add_argument("--beta-block-sweeps", type=int, default=500)
-    ap.add_argument("--case", choices=sorted(CASES), help="run one workload alone (for ncu captures)")
+    ap.add_argument("--case", choices=sorted(CASES) + sorted(BATCH_CASES), help="run one workload alone (for ncu captures)")
     ap.add_argument("--launch", help="with --case: fixed launch 'kernel,vec_width,blocks_per_sm[,prefetch[,order]]' "
                                      "(hs_launch codes), no autotuning")
     args = ap.parse_args(argv)

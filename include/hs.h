@@ -341,7 +341,7 @@ void hs_batch_destroy(hs_batch *b);
  * are taken in each split's own fixed order).  Synchronous.
  * hs_batch_get_layout reads the choice in use (hs_batch_create starts with
  * the maximum CTAs per SM, the interleaved split (align_rows 2), no
- * prefetch, and schedule 2 when there are at least 32 members and every one
+ * prefetch, and schedule 2 when there are at least 16 members and every one
  * fits in a CTA's shared memory, else schedule 0). */
 int hs_batch_autotune(hs_batch *b, const double *betas, int n_trial_sweeps);
 int hs_batch_get_layout(const hs_batch *b, int *ctas_per_sm, int *align_rows, int *prefetch, int *schedule);

@@ -1594,7 +1594,7 @@ int batch_layout(hs_batch *b, int ctas_per_sm, int align_rows) {
 }  // namespace
 
 namespace {
-constexpr int kResidentMinMembers = 32;  // hs_batch_create's choice of the resident schedule
+constexpr int kResidentMinMembers = 16;  // hs_batch_create's choice of the resident schedule
 }  // namespace
 
 int hs_batch_create(hs_batch **out, hs_lattice *const *members, int n_members) {
@@ -1666,8 +1666,8 @@ int hs_batch_create(hs_batch **out, hs_lattice *const *members, int n_members) {
         delete b;
         return st;
     }
-    // many small members: the resident schedule (measured 1.6-2x the persistent one from 64 members of 16^3
-    // up; slower with 16 members of 24^3, which leave most SMs idle)
+    // many small members: the resident schedule (measured 3.2x the persistent one on 304 members of 16^3,
+    // 2.5x on 152 of 24^3, 1.2x on 16 of 24^3, which leave most SMs idle)
     if (n_members >= kResidentMinMembers && b->resident_bytes <= hs::batch_resident_limit(precision)) b->schedule = 2;
     *out = b;
     return HS_OK;
@@ -1687,14 +1687,14 @@ int hs_batch_run(hs_batch *b, const double *betas, int64_t n_sweeps, int64_t n_e
         b->host_members[r].beta = betas[r];
         b->host_members[r].sweep0 = (uint32_t)h->sweep;
         h->last_n_sweeps = n_total;
-        HS_CUDA(cudaMemsetAsync(&h->acc->accepted, 0, sizeof(double), b->stream));
     }
-    if (n_total == 0) return HS_OK;
     HS_CUDA(cudaMemcpyAsync(b->d_members, b->host_members.data(), sizeof(hs::BatchMember) * n,
                             cudaMemcpyHostToDevice, b->stream));
+    hs::BatchArgs args = batch_args(b, n_total, n_eq);
+    HS_CUDA(hs::launch_batch_reset(args, b->stream));  // the accepted counts cover this run's sweeps
+    if (n_total == 0) return HS_OK;
     HS_CUDA(cudaMemsetAsync(b->d_bar, 0, 2 * sizeof(unsigned int), b->stream));
     HS_CUDA(cudaMemsetAsync(b->d_error, 0, sizeof(int), b->stream));
-    hs::BatchArgs args = batch_args(b, n_total, n_eq);
     if (b->schedule == 1 && !b->inject_timeout) {  // chained launches on the stream, no graph
         HS_CUDA(hs::launch_batch_passes(b->precision, args, b->grid, b->stream, b->prefetch));
         for (int r = 0; r < n; ++r) b->members[r]->sweep += (uint64_t)n_total;

@@ -309,6 +309,52 @@ __global__ void __launch_bounds__(kBlock) batch_finalize_kernel(const BatchArgs 
 // the streaming kernels, on generic pointers into shared memory, so the chain
 // is bit-identical; each sweep's FP64 totals (the two passes' CTA sums, in a
 // fixed order) go straight to the member's accumulator.
+constexpr int kResidentRing = 32;  // sweeps whose totals the resident kernel folds at once
+
+// Fold sweeps s0 .. s0 + n - 1 of a resident member (totals in s_tot) into its
+// accumulator, by one warp: lane k derives sweep k's observables (Eq. 2),
+// then lane 0 adds them to the moments in sweep order, holding the
+// accumulator in registers, as member_apply_sweep would sweep by sweep.
+__device__ void resident_fold(const BatchMember &m, const double (*s_tot)[kPartials], double (*s_obs)[8], int s0,
+                              int n, int n_equil) {
+    const int lane = threadIdx.x & 31;
+    if (lane < n) {
+        double tot[kPartials], o[8];
+#pragma unroll
+        for (int q = 0; q < kPartials; ++q) tot[q] = s_tot[lane][q];
+        sweep_observables(tot, m.n_present, m.e, o);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) s_obs[lane][q] = o[q];
+    }
+    __syncwarp();
+    if (lane == 0) {
+        AccRegs R;
+        R.load(m.acc);
+        for (int k = 0; k < n; ++k) {
+            const double *o = s_obs[k];
+            R.accepted += s_tot[k][4];
+            if (s0 + k >= n_equil) {
+                R.moments[HS_SUM_E] += o[0];
+                R.moments[HS_SUM_E2] += o[0] * o[0];
+                R.moments[HS_SUM_ABSM] += o[4];
+                R.moments[HS_SUM_M2] += o[5];
+                R.moments[HS_SUM_M4] += o[6];
+                R.moments[HS_SUM_MX] += o[1];
+                R.moments[HS_SUM_MY] += o[2];
+                R.moments[HS_SUM_MZ] += o[3];
+                R.moments[HS_SUM_ABSME] += o[7];
+                R.count += 1.0;
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < kPartials; ++q) R.sums[q] = s_tot[n - 1][q];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) R.last[q] = s_obs[n - 1][q];
+        R.store(m.acc);
+    }
+    __syncwarp();
+}
+
 template <int P>
 __global__ void __launch_bounds__(kBlock, 2) batch_resident_kernel(const BatchArgs b) {
     constexpr int V = kBatchVec<P>;
@@ -316,7 +362,9 @@ __global__ void __launch_bounds__(kBlock, 2) batch_resident_kernel(const BatchAr
     using VT = Vec<S, V>;
     using C = typename Tr<P>::C;
     extern __shared__ uint4 s_state[];
-    __shared__ double s_red[kBlock / 32][kPartials];
+    __shared__ C s_red[kBlock / 32][kPartials];          // the warps' sums of one pass
+    __shared__ double s_tot[kResidentRing][kPartials];   // per-sweep totals awaiting the fold
+    __shared__ double s_obs[kResidentRing][8];
     __shared__ PassArgs s_args;
     const BatchMember &m = b.members[blockIdx.x];
     const uint32_t plane = (uint32_t)m.Lz * m.Ly * m.Lh;  // elements of one component plane; Lh % V == 0
@@ -324,13 +372,17 @@ __global__ void __launch_bounds__(kBlock, 2) batch_resident_kernel(const BatchAr
     const uint32_t n16 = (uint32_t)(6u * (size_t)plane * sizeof(S) / 16u);
     const uint4 *g16 = static_cast<const uint4 *>(m.planes);
     for (uint32_t i = threadIdx.x; i < n16; i += kBlock) s_state[i] = __ldcg(g16 + i);
+    if (threadIdx.x == 0) s_args = member_args(m, 0, m.sweep0);  // per pass only the colour and sweep change
     S *const st = reinterpret_cast<S *>(s_state);
     const uint32_t n_items = plane / V;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double sweep_tot = 0.0;  // warp 0, lane q < kPartials: quantity q of the current sweep
     for (int s = 0; s < b.n_total; ++s) {
-        double tot[kPartials] = {0.0, 0.0, 0.0, 0.0, 0.0};
         for (int c = 0; c < 2; ++c) {
-            if (threadIdx.x == 0) s_args = member_args(m, c, m.sweep0 + (uint32_t)s);
+            if (threadIdx.x == 0) {
+                s_args.colour = c;
+                s_args.sweep = m.sweep0 + (uint32_t)s;
+            }
             __syncthreads();  // the parameters, and every store of the previous pass (or the initial copy)
             const PassArgs &a = s_args;
             S *own_w[3];
@@ -353,7 +405,8 @@ __global__ void __launch_bounds__(kBlock, 2) batch_resident_kernel(const BatchAr
                     for (int q = 0; q < 3; ++q) *reinterpret_cast<VT *>(own_w[q] + it.b0) = it.s[q];
                 }
             }
-            // the pass's sums: warp shuffle -> CTA (FP64), added to the sweep's totals in warp order
+            // the pass's sums: warp shuffle, then the warps' sums added in FP64 in warp order by warp 0, one
+            // lane per quantity, into the sweep's totals
             const C accE = warp_sum(acc.E());
             const C accX = warp_sum(acc.X());
             const C accY = warp_sum(acc.Y());
@@ -364,19 +417,31 @@ __global__ void __launch_bounds__(kBlock, 2) batch_resident_kernel(const BatchAr
                 s_red[warp][1] = accX;
                 s_red[warp][2] = accY;
                 s_red[warp][3] = accZ;
-                s_red[warp][4] = (double)nacc;
+                s_red[warp][4] = (C)nacc;  // an integer far below 2^24: exact
             }
             __syncthreads();
-            if (threadIdx.x == 0)
-                for (int w = 0; w < kBlock / 32; ++w)
-#pragma unroll
-                    for (int q = 0; q < kPartials; ++q) tot[q] += s_red[w][q];
+            if (warp == 0 && lane < kPartials)
+                for (int w = 0; w < kBlock / 32; ++w) sweep_tot += (double)s_red[w][lane];
         }
-        if (threadIdx.x == 0) member_apply_sweep(m, tot, s >= b.n_equil);
+        if (warp == 0) {
+            const int slot = s % kResidentRing;
+            if (lane < kPartials) s_tot[slot][lane] = sweep_tot;
+            sweep_tot = 0.0;
+            __syncwarp();
+            if (slot == kResidentRing - 1 || s == b.n_total - 1)
+                resident_fold(m, s_tot, s_obs, s - slot, slot + 1, b.n_equil);
+        }
     }
     __syncthreads();
     uint4 *w16 = static_cast<uint4 *>(m.planes);
     for (uint32_t i = threadIdx.x; i < n16; i += kBlock) w16[i] = s_state[i];
+}
+
+// Zero every member's accepted-move counter (hs_batch_run's count covers its
+// own sweeps): one launch for the whole batch.
+__global__ void batch_reset_kernel(const BatchMember *members, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) members[i].acc->accepted = 0.0;
 }
 
 template <typename... KArgs, typename... Args>
@@ -454,6 +519,12 @@ cudaError_t persistent_p(const BatchArgs &b, int grid, cudaStream_t s, int prefe
     return prefetch ? cudaLaunchKernelEx(&cfg, batch_kernel<P, 2>, b) : cudaLaunchKernelEx(&cfg, batch_kernel<P, 0>, b);
 }
 }  // namespace
+
+cudaError_t launch_batch_reset(const BatchArgs &b, cudaStream_t s) {
+    if (b.n_members < 1) return cudaSuccess;
+    batch_reset_kernel<<<(b.n_members + kBlock - 1) / kBlock, kBlock, 0, s>>>(b.members, b.n_members);
+    return cudaGetLastError();
+}
 
 int batch_occupancy(int precision, int prefetch) {
     switch (precision) {

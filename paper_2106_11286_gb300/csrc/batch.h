@@ -59,5 +59,7 @@ int batch_occupancy(int precision, int prefetch);
 // memory (smem bytes, at most batch_resident_limit(precision)) for the whole run
 cudaError_t launch_batch_resident(int precision, const BatchArgs &b, size_t smem, cudaStream_t s);
 size_t batch_resident_limit(int precision);
+// zero every member's accepted-move counter (reads b.members on the device)
+cudaError_t launch_batch_reset(const BatchArgs &b, cudaStream_t s);
 
 }  // namespace hs
