@@ -658,8 +658,8 @@ def noalloc_run(args, stream):
                                                               first_sweep=args.warmup, **kw))
     del St, z, y, x, col
     return {"value": round(L ** 3 * args.steps / (sec * 1e9), 3), "unit": UNIT, "sweeps": args.steps,
-            "what": "hs_sweep_sc_fp32_noalloc on the headline workload: register stencil, split prefetch, "
-                    "reductions finished by the last-arriving CTA of each sweep in static scratch"}
+            "what": "hs_sweep_sc_fp32_noalloc on the headline workload: register stencil, no prefetch, alternating "
+                    "order, reductions finished by the last-arriving CTA of each sweep in static scratch"}
 
 
 def slab_strong_run(args, rank, world, stream, barrier_sync, overlap=True):

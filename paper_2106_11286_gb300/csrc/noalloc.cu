@@ -92,8 +92,9 @@ extern "C" int hs_sweep_sc_fp32_noalloc(float *planes, const int32_t dims[3], co
         return fail(HS_E_INVALID, "planes must be aligned to " + std::to_string(4 * L.vec) +
                                       " bytes for this Lx (vector width " + std::to_string(L.vec) + ")");
     if ((uintptr_t)d_out % alignof(double) != 0) return fail(HS_E_INVALID, "d_out must be 8-byte aligned");
-    // split prefetch when a CTA's items span 8 rows or more, as for a handle
-    L.prefetch = (L.Lh / L.vec <= hs::kBlock / 8) ? 2 : 0;
+    // as a handle's automatic launch: no prefetch, the colour-1 pass descending (each pass starts on the
+    // planes the previous one touched last, still in L2)
+    L.prefetch = 0;
     L.n_sites = L.n_present = (int64_t)dims[0] * dims[1] * dims[2];
     L.planes = planes;
     const int occ = hs::pass_occupancy(HS_FP32, L, 1);
@@ -139,6 +140,7 @@ extern "C" int hs_sweep_sc_fp32_noalloc(float *planes, const int32_t dims[3], co
             a.colour = c;
             a.pass = c;
             a.finish = (c == 1);
+            a.rev = (c == 1) ? (uint32_t)((size_t)L.nz * L.Ly * (L.Lh / L.vec) - 1) : 0u;
             for (int q = 0; q < 3; ++q) {
                 a.own[q] = planes + (size_t)(3 * c + q) * plane;
                 a.oth[q] = planes + (size_t)(3 * (1 - c) + q) * plane;
