@@ -247,7 +247,7 @@ typedef struct {
                           0 = automatic (off);
                           table: 1 = ask L2 for the next site's table row
                           and spin ahead, 2 = off, 0 = automatic (on for FP32
-                          tables of at most 8 neighbours) */
+                          tables of fewer than 8 neighbours) */
     int order;         /* stencil: order of the work items over a sweep:
                           1 = every pass in ascending (z, y, x) order,
                           2 = alternating (the passes of colour 1 descending,

@@ -417,9 +417,10 @@ int configure_launch(hs_lattice *h) {
     if (!L.structured) {
         L.kernel = hs::kTable;
         // request 1 = L2 prefetch of the next site's table row, 2 = off, 0 = automatic (on for FP32 tables of
-        // at most 8 neighbours: measured faster there, slower for FP16 and for fcc's 12)
+        // fewer than 8 neighbours: measured faster there, slower for FP16 and for fcc's 12; off for 8, whose
+        // unrolled kernel measured 76.9 against 74.9 attempts/ns with it on the bcc nanoparticle)
         if (r.prefetch == 3) return fail(HS_E_INVALID, "split prefetch is a stencil option");
-        L.prefetch = r.prefetch == 0 ? ((h->precision == HS_FP32 && L.width <= 8) ? 1 : 0) : (r.prefetch == 1 ? 1 : 0);
+        L.prefetch = r.prefetch == 0 ? ((h->precision == HS_FP32 && L.width < 8) ? 1 : 0) : (r.prefetch == 1 ? 1 : 0);
         int bps = r.blocks_per_sm;
         const int occ = std::min(hs::pass_occupancy(h->precision, L, 0), hs::pass_occupancy(h->precision, L, 1));
         if (bps <= 0 || bps > occ) bps = occ;
