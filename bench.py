@@ -558,7 +558,7 @@ def run_variants(args, rank, stream, barrier_sync, world, dev):
         del rp, col
         lat.init()
         lat.accumulate(True)
-        launch = lat.launch if args.no_autotune else lat.autotune(1 / 0.9, 2)
+        launch = lat.launch if args.no_autotune else lat.autotune(1 / 0.9, 10)
         lat.sweep(1 / 0.9, 3)
         lat.reset_accumulator()
         sec = _timed(stream, lambda: lat.sweep(1 / 0.9, args.csr_sweeps))
