@@ -204,6 +204,28 @@ int hs_set_spins(hs_lattice *h, const double *xyz);
 int hs_get_spins_device(hs_lattice *h, double *d_xyz);
 int hs_set_spins_device(hs_lattice *h, const double *d_xyz);
 
+/* Asynchronous upload of a whole state from host memory, for callers that
+ * feed a new state every few sweeps and want the copy to run while earlier
+ * sweeps do (the state is what Eq. 1 and the Metropolis steps act on; the
+ * paper loads one initial state, so the pipelining is this library's own).
+ *   xyz    host, 3 * n_sites values in natural order (unit vectors; nothing is
+ *          normalised), FP64 when dtype = HS_FP64, FP32 when dtype = HS_FP32
+ *          (widened exactly, so an FP32 lattice stores the given values).
+ *          Page-locked memory lets the copy overlap the device's work;
+ *          pageable memory works but the copy may then block the caller.
+ * The copy runs on a stream of the handle's own into one of two device
+ * buffers (used alternately); the conversion into the lattice's layout is
+ * ordered on the handle's stream after the work already queued there, so
+ * the sweeps queued before this call see the old state and those queued
+ * after it the new one.  The call returns without waiting.  Keep xyz
+ * unchanged until a later synchronous call on the handle (hs_read_accumulator,
+ * hs_measure, hs_get_spins, ...) has returned or the handle's stream has been
+ * synchronised.  The first call allocates the two buffers (2 * 3 * n_sites
+ * doubles); later calls allocate nothing.  Errors: HS_E_INVALID for a null
+ * argument or another dtype, a CUDA error code for a failed allocation or
+ * launch. */
+int hs_set_spins_async(hs_lattice *h, const void *xyz, int dtype);
+
 /* Set the next sweep index (checkpoint / resume: spins + sweep counter +
  * seed + replica fix the rest of the chain bit for bit). */
 int hs_set_sweep_counter(hs_lattice *h, uint64_t sweep);

@@ -29,6 +29,7 @@
 #include "batch.h"
 #include "hs_impl.h"
 #include "slab.h"
+#include "upload.h"
 
 namespace {
 std::string &g_error_ref();
@@ -209,6 +210,13 @@ struct hs_lattice {
     double *partials = nullptr;
     DevAccum *acc = nullptr;
     double *stage = nullptr;  // 3 * n_sites doubles, lazily for host copies
+    // hs_set_spins_async: two upload buffers (3 * n_sites doubles each), filled
+    // on a copy stream of the handle's own and converted on the handle's stream
+    void *up_buf[2] = {nullptr, nullptr};
+    cudaStream_t up_stream = nullptr;
+    cudaEvent_t up_filled[2] = {nullptr, nullptr};  // buffer's copy done
+    cudaEvent_t up_free[2] = {nullptr, nullptr};    // buffer's conversion done
+    int up_next = 0;
     // z-slab: parts of colour passes and the halo copies
     uint64_t sets_written = 0;      // partial sets written in the current sweep
     int interior_due = -1;          // colour whose interior part must come next (-1: none)
@@ -229,6 +237,13 @@ struct hs_lattice {
         for (void *a : allocations) cudaFree(a);
         if (stage) cudaFree(stage);
         for (cudaEvent_t e : ev) cudaEventDestroy(e);
+        if (up_stream) cudaStreamSynchronize(up_stream);
+        for (int b = 0; b < 2; ++b) {
+            if (up_buf[b]) cudaFree(up_buf[b]);
+            if (up_filled[b]) cudaEventDestroy(up_filled[b]);
+            if (up_free[b]) cudaEventDestroy(up_free[b]);
+        }
+        if (up_stream) cudaStreamDestroy(up_stream);
     }
     template <typename T>
     int alloc(T **ptr, size_t bytes) {
@@ -1129,6 +1144,53 @@ int hs_set_spins(hs_lattice *h, const double *xyz) {
                             h->stream));
     if ((st = hs_set_spins_device(h, h->stage))) return st;
     HS_CUDA(cudaStreamSynchronize(h->stream));
+    return HS_OK;
+}
+
+// The upload buffers, copy stream and events of hs_set_spins_async, made on
+// the first call (the only one that allocates).
+static int ensure_upload(hs_lattice *h) {
+    if (h->up_stream) return HS_OK;
+    const size_t bytes = (size_t)std::max<int64_t>(h->L.n_sites, 1) * 3 * sizeof(double);
+    for (int b = 0; b < 2; ++b) {  // a failed set-up keeps what it made for the next try
+        cudaError_t e = cudaSuccess;
+        if (!h->up_buf[b]) {
+            void *p_ = nullptr;
+            e = cudaMalloc(&p_, bytes);
+            if (e == cudaSuccess) h->up_buf[b] = p_;
+        }
+        if (e == cudaSuccess && !h->up_filled[b]) e = cudaEventCreateWithFlags(&h->up_filled[b], cudaEventDisableTiming);
+        if (e == cudaSuccess && !h->up_free[b]) e = cudaEventCreateWithFlags(&h->up_free[b], cudaEventDisableTiming);
+        if (e != cudaSuccess) return cuda_fail(e, "hs_set_spins_async set-up");
+    }
+    cudaError_t e = cudaStreamCreateWithFlags(&h->up_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        h->up_stream = nullptr;
+        return cuda_fail(e, "cudaStreamCreate(upload)");
+    }
+    return HS_OK;
+}
+
+int hs_set_spins_async(hs_lattice *h, const void *xyz, int dtype) {
+    if (!h || !xyz) return fail(HS_E_INVALID, "null argument");
+    if (dtype != HS_FP64 && dtype != HS_FP32) return fail(HS_E_INVALID, "dtype must be HS_FP64 or HS_FP32");
+    int st = ensure_upload(h);
+    if (st) return st;
+    if (h->L.n_present == 0) return HS_OK;
+    const int b = h->up_next;
+    h->up_next ^= 1;
+    const size_t bytes = (size_t)h->L.n_sites * 3 * (dtype == HS_FP64 ? sizeof(double) : sizeof(float));
+    // the copy may start once the conversion that last read this buffer is done
+    HS_CUDA(cudaStreamWaitEvent(h->up_stream, h->up_free[b], 0));
+    HS_CUDA(cudaMemcpyAsync(h->up_buf[b], xyz, bytes, cudaMemcpyHostToDevice, h->up_stream));
+    HS_CUDA(cudaEventRecord(h->up_filled[b], h->up_stream));
+    // the conversion into the layout follows the work already on the handle's stream
+    HS_CUDA(cudaStreamWaitEvent(h->stream, h->up_filled[b], 0));
+    if (dtype == HS_FP64)
+        HS_CUDA(hs::launch_scatter(h->precision, h->L, (const double *)h->up_buf[b], h->stream));
+    else
+        HS_CUDA(hs::launch_scatter_f32(h->precision, h->L, (const float *)h->up_buf[b], h->stream));
+    HS_CUDA(cudaEventRecord(h->up_free[b], h->stream));
     return HS_OK;
 }
 

@@ -92,6 +92,7 @@ SIGNATURES = {
     "hs_set_spins": (ctypes.c_int, [_vp, _vp]),
     "hs_get_spins_device": (ctypes.c_int, [_vp, _vp]),
     "hs_set_spins_device": (ctypes.c_int, [_vp, _vp]),
+    "hs_set_spins_async": (ctypes.c_int, [_vp, _vp, ctypes.c_int]),
     "hs_set_sweep_counter": (ctypes.c_int, [_vp, ctypes.c_uint64]),
     "hs_get_info": (ctypes.c_int, [_vp, ctypes.POINTER(hs_info)]),
     "hs_enable_timing": (ctypes.c_int, [_vp, ctypes.c_int]),
@@ -338,6 +339,29 @@ def hs_set_spins_device(h, xyz):
     _check(load().hs_set_spins_device(h, xyz.data_ptr()))
 
 
+def hs_set_spins_async(h, xyz):
+    """xyz: contiguous host array (numpy, or a CPU torch tensor, ideally pinned)
+    of 3 * n_sites float64 or float32 values in natural order.  Returns at once;
+    the caller keeps xyz alive and unchanged until a later synchronous call on
+    the handle has returned."""
+    info = hs_get_info(h)
+    if isinstance(xyz, np.ndarray):
+        if not xyz.flags.c_contiguous:
+            raise ValueError("xyz must be contiguous")
+        dt, ptr, size = xyz.dtype, xyz.ctypes.data, xyz.size
+        dtype = {np.dtype(np.float64): HS_FP64, np.dtype(np.float32): HS_FP32}.get(np.dtype(dt))
+    else:
+        if xyz.device.type != "cpu" or not xyz.is_contiguous():
+            raise ValueError("xyz must be a contiguous host tensor")
+        ptr, size = xyz.data_ptr(), xyz.numel()
+        dtype = {"torch.float64": HS_FP64, "torch.float32": HS_FP32}.get(str(xyz.dtype))
+    if dtype is None:
+        raise ValueError("xyz must hold float64 or float32 values")
+    if size != 3 * info.n_sites:
+        raise ValueError(f"xyz holds {size} values, the lattice {3 * info.n_sites}")
+    _check(load().hs_set_spins_async(h, ptr, dtype))
+
+
 def hs_set_sweep_counter(h, sweep: int):
     _check(load().hs_set_sweep_counter(h, int(sweep)))
 
@@ -539,6 +563,9 @@ class Lattice:
 
     def set_spins(self, xyz):
         hs_set_spins(self.h, xyz)
+
+    def set_spins_async(self, xyz):
+        hs_set_spins_async(self.h, xyz)
 
     def set_sweep_counter(self, s):
         hs_set_sweep_counter(self.h, s)
