@@ -313,7 +313,7 @@ def run_ours(args):
                 "ms_per_step": round(ms64 / args.fp64_steps, 4), "kernel_ms": round(km64, 4),
                 "hbm_GBs": round(gbs64, 1), "hbm_frac": round(gbs64 / peaks["hbm_gbs"], 4),
                 "launch": lat64.launch}
-        fp64.update(fp64_roofline(v64, stream))
+        fp64.update(fp64_roofline(v64, stream, kernel_label(lat64.launch, precision_code=0)))
         lat64.close()
 
     # ---- end to end through the C ABI with host buffers
@@ -548,11 +548,13 @@ def run_variants(args, rank, stream, barrier_sync, world, dev):
 FP64_OPS_FILE = os.path.join(ROOT, "profiles", "sc_pass_fp64_sc256_ops.txt")
 
 
-def read_fp64_ops():
-    """FP64 pipe instructions per attempt of the FP64 colour-pass kernel (DADD,
-    DMUL and DFMA each take one issue slot of the FP64 pipe), from the
-    committed ncu instruction counts, if they were taken on the current
-    kernel sources; else None."""
+def read_fp64_ops(kernel=None):
+    """FP64 pipe instructions per attempt of the FP64 colour-pass kernel, from
+    the committed ncu instruction counts, if they were taken on the current
+    kernel sources and on this kernel (template label); else None.  inst:
+    DADD + DMUL + DFMA (each one issue slot of the FP64 pipe); pipe_inst:
+    every instruction the FP64 pipe executed (the arithmetic plus the
+    conversions and comparisons it also runs), when recorded."""
     try:
         kv = {}
         for line in open(FP64_OPS_FILE):
@@ -561,23 +563,29 @@ def read_fp64_ops():
                 kv[k.strip()] = v.strip()
         if kv.get("sources_sha") != kernels_sha():
             return None
-        return {"inst": float(kv["fp64_inst_per_attempt"]), "flop": float(kv["fp64_flop_per_attempt"]),
-                "kernel": kv.get("kernel", "")}
+        if kernel is not None and kv.get("kernel", "") != kernel:
+            return None
+        out = {"inst": float(kv["fp64_inst_per_attempt"]), "flop": float(kv["fp64_flop_per_attempt"]),
+               "kernel": kv.get("kernel", "")}
+        if "fp64_pipe_inst_per_attempt" in kv:
+            out["pipe_inst"] = float(kv["fp64_pipe_inst_per_attempt"])
+        return out
     except (OSError, KeyError, ValueError):
         return None
 
 
-def fp64_roofline(value, stream):
+def fp64_roofline(value, stream, kernel=None):
     """The FP64 path against the FP64 pipe.  hs_measure_alu_peak times DFMA
     chains on every SM in the same run; one DFMA is one FP64 pipe
     instruction, so peak instructions/s = measured FLOP/s / 2.  With the
     kernel's FP64 instructions per attempt (ncu counts of DADD + DMUL + DFMA)
     that bounds the attempts/ns; frac = achieved FP64 instructions/s over
-    that peak."""
+    that peak.  frac_pipe counts every instruction of the FP64 pipe instead
+    (the conversions and comparisons as well)."""
     from paper_2106_11286_gb300 import hs
     peak = max(hs.hs_measure_alu_peak(hs.ALU_FP64, stream) for _ in range(3))
     out = {"fp64_peak_tflops_measured": round(peak / 1e12, 4)}
-    ops = read_fp64_ops()
+    ops = read_fp64_ops(kernel)
     if ops:
         peak_inst = peak / 2.0
         achieved = value * 1e9 * ops["inst"]
@@ -587,6 +595,9 @@ def fp64_roofline(value, stream):
                     "alu_bound_attempts_per_ns": round(peak_inst / ops["inst"] / 1e9, 3),
                     "peak_source": "measured DFMA chains (hs_measure_alu_peak), 1 instruction = 2 FLOP",
                     "kernel": ops["kernel"]})
+        if "pipe_inst" in ops:
+            out.update({"fp64_pipe_inst_per_attempt": ops["pipe_inst"],
+                        "frac_pipe": round(value * 1e9 * ops["pipe_inst"] / peak_inst, 4)})
     return out
 
 

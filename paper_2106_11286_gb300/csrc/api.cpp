@@ -199,7 +199,7 @@ struct hs_lattice {
     uint64_t sweep = 0;
     int accumulate = 0;
     int64_t last_n_sweeps = 0;
-    double2 *sc_tab = nullptr;     // FP64: sin, cos(pi j / 128) table of the trial orientation
+    double2 *sc_tab = nullptr;     // FP64: sin, cos(pi j / 1024) table of the trial orientation
     int tensor = 0;                // on-site anisotropy tensor term on
     double tA[6] = {0, 0, 0, 0, 0, 0};
     Layout L{};
@@ -296,6 +296,7 @@ PassArgs base_args(const hs_lattice *h) {
     a.replica = h->replica;
     a.sc_tab = h->sc_tab;
     a.tensor = h->tensor;
+    a.zaxis = (h->p.e[0] == 0.0 && h->p.e[1] == 0.0 && h->p.e[2] == 1.0) ? 1 : 0;
     for (int q = 0; q < 6; ++q) {
         a.A[q] = h->tA[q];
         a.fA[q] = (float)h->tA[q];
@@ -684,16 +685,16 @@ int lattice_create(hs_lattice **out, int type, const int32_t dims[3], int period
     }
     if (st == HS_OK) st = h->alloc(&h->acc, sizeof(DevAccum));
     if (st == HS_OK && precision == HS_FP64) {
-        // sin, cos(pi j / 128) for the FP64 trial's table lookup, from long double on the host
+        // sin, cos(pi j / 1024) for the FP64 trial's table lookup, from long double on the host
         const long double pi = 3.141592653589793238462643383279502884L;
-        double2 tab[256];
-        for (int j = 0; j < 256; ++j) {
-            const long double a = pi * (long double)j / 128.0L;
+        std::vector<double2> tab(2048);
+        for (int j = 0; j < 2048; ++j) {
+            const long double a = pi * (long double)j / 1024.0L;
             tab[j] = make_double2((double)sinl(a), (double)cosl(a));
         }
-        st = h->alloc(&h->sc_tab, sizeof(tab));
+        st = h->alloc(&h->sc_tab, tab.size() * sizeof(double2));
         if (st == HS_OK) {
-            cudaError_t e = cudaMemcpy(h->sc_tab, tab, sizeof(tab), cudaMemcpyHostToDevice);
+            cudaError_t e = cudaMemcpy(h->sc_tab, tab.data(), tab.size() * sizeof(double2), cudaMemcpyHostToDevice);
             if (e != cudaSuccess) st = cuda_fail(e, "cudaMemcpy");
         }
     }
@@ -1707,6 +1708,7 @@ int hs_batch_create(hs_batch **out, hs_lattice *const *members, int n_members) {
             m.e[q] = h->p.e[q];
         }
         m.sc_tab = h->sc_tab;
+        m.zaxis = (h->p.e[0] == 0.0 && h->p.e[1] == 0.0 && h->p.e[2] == 1.0) ? 1 : 0;
         m.key0 = (uint32_t)h->seed;
         m.key1 = (uint32_t)(h->seed >> 32);
         m.replica = h->replica;

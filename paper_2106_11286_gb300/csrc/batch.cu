@@ -88,6 +88,7 @@ __device__ __forceinline__ PassArgs member_args(const BatchMember &m, int colour
     a.e[2] = m.e[2];
     a.beta = m.beta;
     a.sc_tab = m.sc_tab;
+    a.zaxis = m.zaxis;
     a.key0 = m.key0;
     a.key1 = m.key1;
     a.replica = m.replica;

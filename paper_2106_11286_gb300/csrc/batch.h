@@ -16,7 +16,8 @@ struct BatchMember {
     float fJ, fK, fe[3], fbeta;
     double J, K, beta;      // the same in FP64 (FP64 members)
     double e[3];
-    const double2 *sc_tab;  // FP64 members: sin, cos(pi j / 128) of the trial
+    const double2 *sc_tab;  // FP64 members: sin, cos(pi j / 1024) of the trial
+    int zaxis;              // 1: e = (0, 0, 1) exactly
     uint32_t key0, key1, replica;
     uint32_t sweep0;        // the member's sweep index at batch sweep 0
     double n_present;

@@ -86,47 +86,62 @@ __device__ __forceinline__ void sphere_fp64(uint4 w, double &x, double &y, doubl
 
 // sin(pi t), cos(pi t) for t = m 2^-52 in [0, 2) (m < 2^53), by table lookup
 // and angle addition (Tang, "Table-lookup algorithms for elementary functions
-// and their error analysis", 1991): t = j/128 + b with j = m >> 45 and
-// b = (m mod 2^45) 2^-52 in [0, 1/128) exact; sin, cos(pi j/128) come from a
-// 256-entry table (correctly rounded on the host), sin, cos(x) of x = pi b
-// (|x| < 0.0246) from their Taylor series up to x^7 and x^6, whose first
-// omitted terms are below 1e-20 and 4e-18.  Error a few units in the last
-// place, against the FP64 ALU cost of about 14 operations.
+// and their error analysis", 1991): j = m 2^-42 rounded to the nearest
+// integer (0 .. 2048; j = 2048 is j = 0, the period being 2) and b = m - j 2^42
+// in [-2^41, 2^41), so t = j/1024 + b 2^-52 exactly.  sin, cos(pi j/1024) come
+// from a 2048-entry table (correctly rounded on the host); x = pi b 2^-52
+// (|x| <= pi 2^-11 < 0.00154) takes sin x = x - x^3/6 (first omitted term
+// below 7.2e-17) and cos x = 1 - c, c = x^2/2 - x^4/24 (first omitted below
+// 1.8e-20); then sin(a + x) = sin a + (cos a sin x - sin a c) and
+// cos(a + x) = cos a - (sin a sin x + cos a c).  Error below two units in the
+// last place, for 10 FP64 operations.
+constexpr double kPiTwoM52 = 3.141592653589793 * 0x1p-52;  // pi (FP64) 2^-52, exact scaling
+
 __device__ __forceinline__ void sincospi_tab(uint64_t m, const double2 *tab, double &sn, double &cs) {
-    const uint32_t j = (uint32_t)(m >> 45);
-    const double b = (double)(int64_t)(m & ((1ull << 45) - 1)) * 0x1p-52;
-    const double x = b * 3.141592653589793;
+    const uint64_t j = (m + (1ull << 41)) >> 42;
+    const int64_t b = (int64_t)m - (int64_t)(j << 42);
+    const double x = (double)b * kPiTwoM52;
     const double x2 = x * x;
-    const double sx = x * fma(x2, fma(x2, fma(x2, -1.0 / 5040.0, 1.0 / 120.0), -1.0 / 6.0), 1.0);
-    const double cx = fma(x2, fma(x2, fma(x2, -1.0 / 720.0, 1.0 / 24.0), -0.5), 1.0);
-    const double2 t = __ldg(tab + j);
-    sn = fma(t.y, sx, t.x * cx);
-    cs = fma(-t.x, sx, t.y * cx);
+    const double sx = fma(x * x2, -1.0 / 6.0, x);
+    const double c = x2 * fma(x2, -1.0 / 24.0, 0.5);
+    const double2 t = __ldg(tab + (j & 2047u));
+    sn = fma(t.y, sx, fma(-t.x, c, t.x));
+    cs = fma(-t.x, sx, fma(-t.y, c, t.y));
+}
+
+// k 2^-s exactly, for an integer |k| < 2^53 and 0 < s <= 53: k converted
+// (exact), then s taken off its exponent field, which stays positive for
+// |k| >= 1; k = 0 gives +0.  Integer instructions in place of an FP64 multiply.
+__device__ __forceinline__ double scaled_int(int64_t k, int s) {
+    const double d = (double)k;
+    const double r = __hiloint2double(__double2hiint(d) - (s << 20), __double2loint(d));
+    return k == 0 ? 0.0 : r;
 }
 
 // Trial orientation and acceptance uniform of one site, FP64 schedule
-// (Metropolis step (ii)); the same sphere point as sphere_fp64, with
-// phi = pi v = pi t - pi (t = v + 1) from the table: sin(pi v) = -sin(pi t),
-// cos(pi v) = -cos(pi t).
+// (Metropolis step (ii)); the sphere point of sphere_fp64 up to rounding:
+// 1 - z^2 is formed with one rounding (fma), and phi = pi v = pi t - pi
+// (t = v + 1) from the table: sin(pi v) = -sin(pi t), cos(pi v) = -cos(pi t).
+// uf is the acceptance uniform's top 24 bits: uf <= u < uf + 2^-24.
 __device__ __forceinline__ void draw_trial64(uint32_t site, uint32_t sweep, uint32_t colour, uint32_t replica,
                                              uint32_t k0, uint32_t k1, const double2 *tab, double &tx, double &ty,
-                                             double &tz, double &u) {
+                                             double &tz, double &u, float &uf) {
     const uint32_t w2 = (kTagTrial << 24) | (colour << 8);
     const uint4 a = philox10(make_uint4(site, sweep, w2, replica), k0, k1);
     const uint4 b = philox10(make_uint4(site, sweep, w2 | 1u, replica), k0, k1);
     const int64_t two52 = int64_t(1) << 52;
     const int64_t iz = (int64_t)((((uint64_t)(a.x >> 5)) << 26) | (uint64_t)(a.y >> 6));
     const uint64_t iv = (((uint64_t)(a.z >> 5)) << 26) | (uint64_t)(a.w >> 6);
-    tz = (double)(iz - two52) * 0x1p-52;
-    const double r = sqrt((1.0 - tz) * (1.0 + tz));
+    tz = scaled_int(iz - two52, 52);
+    const double r = sqrt(fma(-tz, tz, 1.0));
     double sn, cs;
     sincospi_tab(iv, tab, sn, cs);
     tx = -(r * cs);
     ty = -(r * sn);
     const uint64_t ip = (((uint64_t)(b.x >> 5)) << 26) | (uint64_t)(b.y >> 6);
-    u = (double)ip * 0x1p-53;
+    u = scaled_int((int64_t)ip, 53);
+    uf = (float)(uint32_t)(ip >> 29) * 0x1p-24f;
 }
-
 
 // ---- FP32 arithmetic of one site (float) or of the two sites of a Philox
 // pair (float2, packed sm_100+ instructions).  Every operation is rounded
@@ -302,32 +317,42 @@ struct SiteDots {
     bool acc;
 };
 
-// The FP64 acceptance P <= exp(x), x = -beta dH < 0, decided first with the
-// hardware base-2 exponential in FP32: for |x| <= 80 its relative error is at
-// most 2^-22 (ex2) + 3 |x| 2^-24 (rounding x, x log2(e) and log2(e) to FP32)
-// < 1.5e-5, so outside a band of relative width 3e-5 around it the FP64
-// comparison has a known outcome.  Inside the band (or for |x| > 80) the FP64
+// The FP64 acceptance P <= exp(x), x = -beta dH < 0, decided first in FP32:
+// e = 2^(x log2(e)) from the hardware base-2 exponential has, for |x| <= 80,
+// a relative error of at most 2^-22 (ex2) + 3 |x| 2^-24 (rounding x, log2(e)
+// and their product to FP32) < 1.5e-5.  P lies in [uf, uf + 2^-24) (uf its
+// top 24 bits, exact in FP32); the bounds e (1 -+ 3e-5), rounded to FP32, keep
+// a margin over both errors, so outside that band the outcome of the FP64
+// comparison is known.  Inside the band (or for |x| > 80) the FP64
 // exponential decides, so the decision always equals the plain FP64 rule.
-__device__ __forceinline__ bool accept64(double x, double u) {
-    if (x >= -80.0) {
-        const float y = __fmul_rn((float)x, 1.44269504088896341f);
+__device__ __forceinline__ bool accept64(double x, double u, float uf) {
+    const float xf = (float)x;
+    if (xf >= -80.0f) {
+        const float y = __fmul_rn(xf, 1.44269504088896341f);
         float e;
         asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(y));
-        const double ed = (double)e;
-        if (u < ed * (1.0 - 3e-5)) return true;
-        if (u > ed * (1.0 + 3e-5)) return false;
+        if (__fadd_rn(uf, 0x1p-24f) < __fmul_rn(e, 1.0f - 3e-5f)) return true;
+        if (uf > __fmul_rn(e, 1.0f + 3e-5f)) return false;
     }
     return u <= exp(x);
 }
 
-template <typename C, bool TEN = false>
+// ZAX: the easy axis is e = (0, 0, 1) exactly, so S.e = S_z (what the three
+// products give for that e, without them).
+template <typename C, bool TEN = false, bool ZAX = false>
 __device__ __forceinline__ SiteDots<C> metropolis(C sx, C sy, C sz, C tx, C ty, C tz, C hx, C hy, C hz, C J, C K,
-                                                  C ex, C ey, C ez, C beta, C u, const double *A = nullptr) {
+                                                  C ex, C ey, C ez, C beta, C u, float uf,
+                                                  const double *A = nullptr) {
     SiteDots<C> d;
     d.sh = sx * hx + sy * hy + sz * hz;
     d.th = tx * hx + ty * hy + tz * hz;
-    d.se = sx * ex + sy * ey + sz * ez;
-    d.pe = tx * ex + ty * ey + tz * ez;
+    if constexpr (ZAX) {
+        d.se = sz;
+        d.pe = tz;
+    } else {
+        d.se = sx * ex + sy * ey + sz * ez;
+        d.pe = tx * ex + ty * ey + tz * ez;
+    }
     C dH = J * (d.sh - d.th) + K * ((d.se - d.pe) * (d.se + d.pe));
     if constexpr (TEN) {
         const double(&At)[6] = *reinterpret_cast<const double(*)[6]>(A);
@@ -335,7 +360,7 @@ __device__ __forceinline__ SiteDots<C> metropolis(C sx, C sy, C sz, C tx, C ty, 
         d.qt = quad64(tx, ty, tz, At);
         dH += d.qs - d.qt;
     }
-    d.acc = (dH <= C(0)) || accept64(-beta * dH, u);
+    d.acc = (dH <= C(0)) || accept64(-beta * dH, u, uf);
     return d;
 }
 
@@ -631,6 +656,49 @@ __device__ __forceinline__ void item_fields(const Vec<typename Tr<P>::S, V> (&o)
     }
 }
 
+// Metropolis steps (ii)-(iii) for the V sites of one FP64 work item (see
+// update_item_h); ZAX as in metropolis.
+template <int V, bool MEAS, bool TEN, bool ZAX>
+__device__ __forceinline__ bool update_fp64(Vec<double, V> (&s)[3], const double (&h)[3][V], uint32_t site0, int c,
+                                            const PassArgs &a, double J, double K, double ex, double ey, double ez,
+                                            double beta, SiteAcc<HS_FP64> &acc) {
+    using C = double;
+    bool any = false;
+#pragma unroll
+    for (int k = 0; k < V; ++k) {
+        C tx, ty, tz, u;
+        float uf;
+        draw_trial64(site0 + 2u * k, a.sweep, (uint32_t)c, a.replica, a.key0, a.key1, a.sc_tab, tx, ty, tz, u,
+                     uf);
+        C sx = s[0].v[k], sy = s[1].v[k], sz = s[2].v[k];
+        const SiteDots<C> d = metropolis<C, TEN, ZAX>(sx, sy, sz, tx, ty, tz, h[0][k], h[1][k], h[2][k], J, K,
+                                                      ex, ey, ez, beta, u, uf, a.A);
+        if (d.acc) {
+            sx = tx;
+            sy = ty;
+            sz = tz;
+            s[0].v[k] = tx;
+            s[1].v[k] = ty;
+            s[2].v[k] = tz;
+            any = true;
+            ++acc.n;
+        }
+        if (MEAS) {
+            // bond energy counted at the later colour's end: pass 1 owns
+            // every sc bond, pass 0 only the anisotropy term
+            const C e_new = d.acc ? d.pe : d.se;
+            C ei = -K * e_new * e_new;
+            if (TEN) ei -= d.acc ? d.qt : d.qs;
+            if (c == 1) ei -= J * (d.acc ? d.th : d.sh);
+            acc.e += ei;
+            acc.x += sx;
+            acc.y += sy;
+            acc.z += sz;
+        }
+    }
+    return any;
+}
+
 // Metropolis steps (ii)-(iii) for the V sites of one work item, given the
 // item's own spins s and the local fields h of step (i).  site0 is the
 // natural index of the item's first site (the FP64 schedule's counter), rank0
@@ -648,36 +716,12 @@ __device__ __forceinline__ bool update_item_h(Vec<typename Tr<P>::S, V> (&s)[3],
     using C = typename Tr<P>::C;
     bool any = false;
     if constexpr (P == HS_FP64) {
-#pragma unroll
-        for (int k = 0; k < V; ++k) {
-            C tx, ty, tz, u;
-            draw_trial64(site0 + 2u * k, a.sweep, (uint32_t)c, a.replica, a.key0, a.key1, a.sc_tab, tx, ty, tz, u);
-            C sx = to_c(s[0].v[k]), sy = to_c(s[1].v[k]), sz = to_c(s[2].v[k]);
-            const SiteDots<C> d = metropolis<C, TEN>(sx, sy, sz, tx, ty, tz, h[0][k], h[1][k], h[2][k], J, K, ex,
-                                                     ey, ez, beta, u, a.A);
-            if (d.acc) {
-                sx = tx;
-                sy = ty;
-                sz = tz;
-                s[0].v[k] = tx;
-                s[1].v[k] = ty;
-                s[2].v[k] = tz;
-                any = true;
-                ++acc.n;
-            }
-            if (MEAS) {
-                // bond energy counted at the later colour's end: pass 1 owns
-                // every sc bond, pass 0 only the anisotropy term
-                const C e_new = d.acc ? d.pe : d.se;
-                C ei = -K * e_new * e_new;
-                if (TEN) ei -= d.acc ? d.qt : d.qs;
-                if (c == 1) ei -= J * (d.acc ? d.th : d.sh);
-                acc.e += ei;
-                acc.x += sx;
-                acc.y += sy;
-                acc.z += sz;
-            }
-        }
+        // one uniform branch per work item: the item body with S.e = S_z
+        // (e = (0, 0, 1), the FP64 pipe spared six operations per site) or
+        // with the general dot products
+        if constexpr (!TEN)
+            if (a.zaxis) return update_fp64<V, MEAS, false, true>(s, h, site0, c, a, J, K, ex, ey, ez, beta, acc);
+        return update_fp64<V, MEAS, TEN, false>(s, h, site0, c, a, J, K, ex, ey, ez, beta, acc);
     } else {
         const float nb = neg_beta_log2e(beta);
         // one site in lane x of the accumulators

@@ -94,7 +94,8 @@ struct PassArgs {
     int tensor;             // 1: the on-site anisotropy tensor term is on
     double A[6];            // its symmetric tensor (xx, yy, zz, xy, xz, yz)
     float fA[6];
-    const double2 *sc_tab;  // FP64 trial: sin, cos(pi j / 128), j = 0..255
+    const double2 *sc_tab;  // FP64 trial: sin, cos(pi j / 1024), j = 0..2047
+    int zaxis;              // 1: e = (0, 0, 1) exactly (the FP64 stencil takes S.e = S_z)
     uint32_t key0, key1, replica, sweep;
     double *partials;       // [ring slots][n_colours][n_blocks][kPartials]; a slab has kSlabSets sets per colour
                             // (pass = kSlabSets colour + set, n_colours = 2 kSlabSets); a launch of fewer CTAs

@@ -412,9 +412,10 @@ __global__ void __launch_bounds__(kBlock, P == HS_FP64 ? 1 : (W > 0 ? 4 : 5)) ta
         C tx, ty, tz, u;
         bool accepted;
         if constexpr (P == HS_FP64) {
+            float uf;
             draw_trial64(__ldg(a.nat + i), a.sweep, (uint32_t)a.colour, a.replica, a.key0, a.key1, a.sc_tab, tx, ty,
-                         tz, u);
-            accepted = metropolis<C, TEN>(sx, sy, sz, tx, ty, tz, hx, hy, hz, J, K, ex, ey, ez, beta, u, a.A).acc;
+                         tz, u, uf);
+            accepted = metropolis<C, TEN>(sx, sy, sz, tx, ty, tz, hx, hy, hz, J, K, ex, ey, ez, beta, u, uf, a.A).acc;
         } else {
             draw_trial_rank<P>((uint32_t)(i - a.colour_begin), a.sweep, (uint32_t)a.colour, a.replica, a.key0,
                                a.key1, tx, ty, tz, u);

@@ -36,6 +36,25 @@ def test_committed_traffic_matches_the_sources():
     assert bench.read_traffic("sc_pass_kernel<1, 4, 1, 0, 0, 1>", 2) is not None
 
 
+def test_fp64_ops_only_for_the_captured_sources_and_kernel(tmp_path, monkeypatch):
+    f = tmp_path / "ops.txt"
+    f.write_text(f"kernel: sc_pass_kernel<0, 2, 1, 0, 0, 1>\nsources_sha: {bench.kernels_sha()}\n"
+                 "fp64_inst_per_attempt: 60.5\nfp64_flop_per_attempt: 80\nfp64_pipe_inst_per_attempt: 66\n")
+    monkeypatch.setattr(bench, "FP64_OPS_FILE", str(f))
+    ops = bench.read_fp64_ops("sc_pass_kernel<0, 2, 1, 0, 0, 1>")
+    assert ops["inst"] == 60.5 and ops["flop"] == 80.0 and ops["pipe_inst"] == 66.0
+    assert bench.read_fp64_ops("sc_pass_kernel<0, 1, 1, 0, 0, 1>") is None   # another kernel
+    f.write_text("kernel: sc_pass_kernel<0, 2, 1, 0, 0, 1>\nsources_sha: 0000\nfp64_inst_per_attempt: 60.5\n"
+                 "fp64_flop_per_attempt: 80\n")
+    assert bench.read_fp64_ops("sc_pass_kernel<0, 2, 1, 0, 0, 1>") is None   # other sources
+
+
+def test_committed_fp64_ops_match_the_sources():
+    """The stored FP64 instruction counts belong to the current kernel sources
+    and to the kernel the bench's FP64 form runs (the automatic launch)."""
+    assert bench.read_fp64_ops("sc_pass_kernel<0, 2, 1, 0, 0, 1>") is not None
+
+
 def test_spin_error_measure():
     rng = np.random.default_rng(3)
     S0 = rng.normal(size=(100, 3))
