@@ -235,7 +235,7 @@ __device__ __forceinline__ void batch_pass(const BatchArgs &b, int s, int c) {
             }
         }
         // segment partials: warp shuffle -> CTA (FP64) -> slot
-        const C accE = warp_sum(acc.E());
+        const C accE = warp_sum(acc.E(J, K));
         const C accX = warp_sum(acc.X());
         const C accY = warp_sum(acc.Y());
         const C accZ = warp_sum(acc.Z());
@@ -408,7 +408,7 @@ __global__ void __launch_bounds__(kBlock, 2) batch_resident_kernel(const BatchAr
             }
             // the pass's sums: warp shuffle, then the warps' sums added in FP64 in warp order by warp 0, one
             // lane per quantity, into the sweep's totals
-            const C accE = warp_sum(acc.E());
+            const C accE = warp_sum(acc.E(J, K));
             const C accX = warp_sum(acc.X());
             const C accY = warp_sum(acc.Y());
             const C accZ = warp_sum(acc.Z());

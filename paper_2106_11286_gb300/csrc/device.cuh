@@ -277,15 +277,21 @@ __device__ __forceinline__ double quad64(double x, double y, double z, const dou
     return x * ax + y * ay + z * az;
 }
 
-// TEN adds the tensor term: dH += S^T A S - S'^T A S'.
-template <typename T, bool TEN = false>
+// TEN adds the tensor term: dH += S^T A S - S'^T A S'.  ZAX: the easy axis is
+// e = (0, 0, 1) exactly, so S.e = S_z (what the three products give for it).
+template <typename T, bool TEN = false, bool ZAX = false>
 __device__ __forceinline__ Dots32<T> site_math32(T sx, T sy, T sz, T tx, T ty, T tz, T hx, T hy, T hz, float J,
                                                  float K, float ex, float ey, float ez, const float *A = nullptr) {
     Dots32<T> d;
     d.sh = f_fma(sz, hz, f_fma(sy, hy, f_mul(sx, hx)));
     d.th = f_fma(tz, hz, f_fma(ty, hy, f_mul(tx, hx)));
-    d.se = f_fma(sz, splat<T>(ez), f_fma(sy, splat<T>(ey), f_mul(sx, splat<T>(ex))));
-    d.pe = f_fma(tz, splat<T>(ez), f_fma(ty, splat<T>(ey), f_mul(tx, splat<T>(ex))));
+    if constexpr (ZAX) {
+        d.se = sz;
+        d.pe = tz;
+    } else {
+        d.se = f_fma(sz, splat<T>(ez), f_fma(sy, splat<T>(ey), f_mul(sx, splat<T>(ex))));
+        d.pe = f_fma(tz, splat<T>(ez), f_fma(ty, splat<T>(ey), f_mul(tx, splat<T>(ex))));
+    }
     d.dH = f_fma(splat<T>(K), f_mul(f_sub(d.se, d.pe), f_add(d.se, d.pe)), f_mul(splat<T>(J), f_sub(d.sh, d.th)));
     if constexpr (TEN) {
         const float(&At)[6] = *reinterpret_cast<const float(*)[6]>(A);
@@ -353,7 +359,13 @@ __device__ __forceinline__ SiteDots<C> metropolis(C sx, C sy, C sz, C tx, C ty, 
         d.se = sx * ex + sy * ey + sz * ez;
         d.pe = tx * ex + ty * ey + tz * ez;
     }
-    C dH = J * (d.sh - d.th) + K * ((d.se - d.pe) * (d.se + d.pe));
+    // the uniaxial term K ((S.e)^2 - (S'.e)^2): for e = z as S_z^2 - S'_z^2 with one
+    // rounding of S'_z^2 (an fma), else as the product of difference and sum
+    C dH;
+    if constexpr (ZAX)
+        dH = fma(K, fma(d.se, d.se, -(d.pe * d.pe)), J * (d.sh - d.th));
+    else
+        dH = J * (d.sh - d.th) + K * ((d.se - d.pe) * (d.se + d.pe));
     if constexpr (TEN) {
         const double(&At)[6] = *reinterpret_cast<const double(*)[6]>(A);
         d.qs = quad64(sx, sy, sz, At);
@@ -571,16 +583,19 @@ struct SiteAcc {
     float2 e = make_float2(0.f, 0.f), x = make_float2(0.f, 0.f), y = make_float2(0.f, 0.f),
            z = make_float2(0.f, 0.f);
     unsigned n = 0;
-    __device__ __forceinline__ float E() const { return e.x + e.y; }
+    __device__ __forceinline__ float E(float, float) const { return e.x + e.y; }
     __device__ __forceinline__ float X() const { return x.x + x.y; }
     __device__ __forceinline__ float Y() const { return y.x + y.y; }
     __device__ __forceinline__ float Z() const { return z.x + z.y; }
 };
+// FP64: the energy as its two sums, scaled once by -K and -J at the end:
+// k = sum (S.e)^2 over the sites, j = sum S.h over the later colour's sites,
+// e = the tensor term's share.
 template <>
 struct SiteAcc<HS_FP64> {
-    double e = 0.0, x = 0.0, y = 0.0, z = 0.0;
+    double e = 0.0, k = 0.0, j = 0.0, x = 0.0, y = 0.0, z = 0.0;
     unsigned n = 0;
-    __device__ __forceinline__ double E() const { return e; }
+    __device__ __forceinline__ double E(double J, double K) const { return e - J * j - K * k; }
     __device__ __forceinline__ double X() const { return x; }
     __device__ __forceinline__ double Y() const { return y; }
     __device__ __forceinline__ double Z() const { return z; }
@@ -687,10 +702,9 @@ __device__ __forceinline__ bool update_fp64(Vec<double, V> (&s)[3], const double
             // bond energy counted at the later colour's end: pass 1 owns
             // every sc bond, pass 0 only the anisotropy term
             const C e_new = d.acc ? d.pe : d.se;
-            C ei = -K * e_new * e_new;
-            if (TEN) ei -= d.acc ? d.qt : d.qs;
-            if (c == 1) ei -= J * (d.acc ? d.th : d.sh);
-            acc.e += ei;
+            acc.k = fma(e_new, e_new, acc.k);
+            if (TEN) acc.e -= d.acc ? d.qt : d.qs;
+            if (c == 1) acc.j += d.acc ? d.th : d.sh;
             acc.x += sx;
             acc.y += sy;
             acc.z += sz;
@@ -706,15 +720,103 @@ __device__ __forceinline__ bool update_fp64(Vec<double, V> (&s)[3], const double
 // sc lattice the natural index halved, kept separately so that it stays exact
 // beyond 2^32 sites).  Updates s in place; returns whether any site was
 // accepted.
+// Metropolis steps (ii)-(iii) for the V sites of one FP32 / FP16 work item
+// (see update_item_h); ZAX as in site_math32.
+template <int P, int V, bool MEAS, bool TEN, bool ZAX>
+__device__ __forceinline__ bool update_f32(Vec<typename Tr<P>::S, V> (&s)[3], const float (&h)[3][V], uint32_t rank0,
+                                           int c, const PassArgs &a, float J, float K, float ex, float ey, float ez,
+                                           float beta, SiteAcc<P> &acc) {
+    using S = typename Tr<P>::S;
+    using C = float;
+    bool any = false;
+    const float nb = neg_beta_log2e(beta);
+    // one site in lane x of the accumulators
+    auto single = [&](int k, float tx, float ty, float tz, float u) {
+        const float sx = to_c(s[0].v[k]), sy = to_c(s[1].v[k]), sz = to_c(s[2].v[k]);
+        const Dots32<float> d = site_math32<float, TEN, ZAX>(sx, sy, sz, tx, ty, tz, h[0][k], h[1][k], h[2][k], J, K,
+                                                        ex, ey, ez, a.fA);
+        const bool ac = accept32(d.dH, u, nb);
+        if (ac) {
+            s[0].v[k] = to_store<S, C>(tx);
+            s[1].v[k] = to_store<S, C>(ty);
+            s[2].v[k] = to_store<S, C>(tz);
+            any = true;
+            ++acc.n;
+        }
+        if (MEAS) {
+            const float en = ac ? d.pe : d.se;
+            float ei = f_mul(-K, f_mul(en, en));
+            if (TEN) ei = f_sub(ei, ac ? d.qt : d.qs);
+            if (c == 1) ei = f_fma(-J, ac ? d.th : d.sh, ei);
+            acc.e.x = f_add(acc.e.x, ei);
+            acc.x.x = f_add(acc.x.x, ac ? tx : sx);
+            acc.y.x = f_add(acc.y.x, ac ? ty : sy);
+            acc.z.x = f_add(acc.z.x, ac ? tz : sz);
+        }
+    };
+    // ranks of the item's sites in their colour class: rank0 + k
+    if (V >= 2 && (rank0 & 1u) == 0u) {
+#pragma unroll
+        for (int j = 0; j < V / 2; ++j) {  // one Philox block and packed arithmetic per pair
+            const int k0 = 2 * j, k1 = 2 * j + 1;
+            const uint4 w = trial_block((rank0 >> 1) + j, a.sweep, (uint32_t)c, a.replica, a.key0, a.key1);
+            float2 zi, vi, ui;
+            half_ints(w.x, w.y, zi.x, vi.x, ui.x);
+            half_ints(w.z, w.w, zi.y, vi.y, ui.y);
+            float2 tx, ty, tz, u;
+            trial32<P, float2>(zi, vi, ui, tx, ty, tz, u);
+            float2 hp[3];
+#pragma unroll
+            for (int q = 0; q < 3; ++q) hp[q] = make_float2(h[q][k0], h[q][k1]);
+            const float2 sx = make_float2(to_c(s[0].v[k0]), to_c(s[0].v[k1]));
+            const float2 sy = make_float2(to_c(s[1].v[k0]), to_c(s[1].v[k1]));
+            const float2 sz = make_float2(to_c(s[2].v[k0]), to_c(s[2].v[k1]));
+            const Dots32<float2> d =
+                site_math32<float2, TEN, ZAX>(sx, sy, sz, tx, ty, tz, hp[0], hp[1], hp[2], J, K, ex, ey, ez, a.fA);
+            const bool a0 = accept32(d.dH.x, u.x, nb);
+            const bool a1 = accept32(d.dH.y, u.y, nb);
+            if (a0) {
+                s[0].v[k0] = to_store<S, C>(tx.x);
+                s[1].v[k0] = to_store<S, C>(ty.x);
+                s[2].v[k0] = to_store<S, C>(tz.x);
+                ++acc.n;
+            }
+            if (a1) {
+                s[0].v[k1] = to_store<S, C>(tx.y);
+                s[1].v[k1] = to_store<S, C>(ty.y);
+                s[2].v[k1] = to_store<S, C>(tz.y);
+                ++acc.n;
+            }
+            any = any || a0 || a1;
+            if (MEAS) {
+                const float2 en = make_float2(a0 ? d.pe.x : d.se.x, a1 ? d.pe.y : d.se.y);
+                float2 ei = f_mul(splat<float2>(-K), f_mul(en, en));
+                if (TEN) ei = f_sub(ei, make_float2(a0 ? d.qt.x : d.qs.x, a1 ? d.qt.y : d.qs.y));
+                if (c == 1)
+                    ei = f_fma(splat<float2>(-J), make_float2(a0 ? d.th.x : d.sh.x, a1 ? d.th.y : d.sh.y), ei);
+                acc.e = f_add(acc.e, ei);
+                acc.x = f_add(acc.x, make_float2(a0 ? tx.x : sx.x, a1 ? tx.y : sx.y));
+                acc.y = f_add(acc.y, make_float2(a0 ? ty.x : sy.x, a1 ? ty.y : sy.y));
+                acc.z = f_add(acc.z, make_float2(a0 ? tz.x : sz.x, a1 ? tz.y : sz.y));
+            }
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < V; ++k) {
+            float tx, ty, tz, u;
+            draw_trial_rank<P>(rank0 + k, a.sweep, (uint32_t)c, a.replica, a.key0, a.key1, tx, ty, tz, u);
+            single(k, tx, ty, tz, u);
+        }
+    }
+    return any;
+}
+
 template <int P, int V, bool MEAS, bool TEN = false>
 __device__ __forceinline__ bool update_item_h(Vec<typename Tr<P>::S, V> (&s)[3], const typename Tr<P>::C (&h)[3][V],
                                               uint32_t site0, uint32_t rank0, int c, const PassArgs &a,
                                               typename Tr<P>::C J, typename Tr<P>::C K, typename Tr<P>::C ex,
                                               typename Tr<P>::C ey, typename Tr<P>::C ez, typename Tr<P>::C beta,
                                               SiteAcc<P> &acc) {
-    using S = typename Tr<P>::S;
-    using C = typename Tr<P>::C;
-    bool any = false;
     if constexpr (P == HS_FP64) {
         // one uniform branch per work item: the item body with S.e = S_z
         // (e = (0, 0, 1), the FP64 pipe spared six operations per site) or
@@ -723,87 +825,15 @@ __device__ __forceinline__ bool update_item_h(Vec<typename Tr<P>::S, V> (&s)[3],
             if (a.zaxis) return update_fp64<V, MEAS, false, true>(s, h, site0, c, a, J, K, ex, ey, ez, beta, acc);
         return update_fp64<V, MEAS, TEN, false>(s, h, site0, c, a, J, K, ex, ey, ez, beta, acc);
     } else {
-        const float nb = neg_beta_log2e(beta);
-        // one site in lane x of the accumulators
-        auto single = [&](int k, float tx, float ty, float tz, float u) {
-            const float sx = to_c(s[0].v[k]), sy = to_c(s[1].v[k]), sz = to_c(s[2].v[k]);
-            const Dots32<float> d = site_math32<float, TEN>(sx, sy, sz, tx, ty, tz, h[0][k], h[1][k], h[2][k], J, K,
-                                                            ex, ey, ez, a.fA);
-            const bool ac = accept32(d.dH, u, nb);
-            if (ac) {
-                s[0].v[k] = to_store<S, C>(tx);
-                s[1].v[k] = to_store<S, C>(ty);
-                s[2].v[k] = to_store<S, C>(tz);
-                any = true;
-                ++acc.n;
-            }
-            if (MEAS) {
-                const float en = ac ? d.pe : d.se;
-                float ei = f_mul(-K, f_mul(en, en));
-                if (TEN) ei = f_sub(ei, ac ? d.qt : d.qs);
-                if (c == 1) ei = f_fma(-J, ac ? d.th : d.sh, ei);
-                acc.e.x = f_add(acc.e.x, ei);
-                acc.x.x = f_add(acc.x.x, ac ? tx : sx);
-                acc.y.x = f_add(acc.y.x, ac ? ty : sy);
-                acc.z.x = f_add(acc.z.x, ac ? tz : sz);
-            }
-        };
-        // ranks of the item's sites in their colour class: rank0 + k
-        if (V >= 2 && (rank0 & 1u) == 0u) {
-#pragma unroll
-            for (int j = 0; j < V / 2; ++j) {  // one Philox block and packed arithmetic per pair
-                const int k0 = 2 * j, k1 = 2 * j + 1;
-                const uint4 w = trial_block((rank0 >> 1) + j, a.sweep, (uint32_t)c, a.replica, a.key0, a.key1);
-                float2 zi, vi, ui;
-                half_ints(w.x, w.y, zi.x, vi.x, ui.x);
-                half_ints(w.z, w.w, zi.y, vi.y, ui.y);
-                float2 tx, ty, tz, u;
-                trial32<P, float2>(zi, vi, ui, tx, ty, tz, u);
-                float2 hp[3];
-#pragma unroll
-                for (int q = 0; q < 3; ++q) hp[q] = make_float2(h[q][k0], h[q][k1]);
-                const float2 sx = make_float2(to_c(s[0].v[k0]), to_c(s[0].v[k1]));
-                const float2 sy = make_float2(to_c(s[1].v[k0]), to_c(s[1].v[k1]));
-                const float2 sz = make_float2(to_c(s[2].v[k0]), to_c(s[2].v[k1]));
-                const Dots32<float2> d =
-                    site_math32<float2, TEN>(sx, sy, sz, tx, ty, tz, hp[0], hp[1], hp[2], J, K, ex, ey, ez, a.fA);
-                const bool a0 = accept32(d.dH.x, u.x, nb);
-                const bool a1 = accept32(d.dH.y, u.y, nb);
-                if (a0) {
-                    s[0].v[k0] = to_store<S, C>(tx.x);
-                    s[1].v[k0] = to_store<S, C>(ty.x);
-                    s[2].v[k0] = to_store<S, C>(tz.x);
-                    ++acc.n;
-                }
-                if (a1) {
-                    s[0].v[k1] = to_store<S, C>(tx.y);
-                    s[1].v[k1] = to_store<S, C>(ty.y);
-                    s[2].v[k1] = to_store<S, C>(tz.y);
-                    ++acc.n;
-                }
-                any = any || a0 || a1;
-                if (MEAS) {
-                    const float2 en = make_float2(a0 ? d.pe.x : d.se.x, a1 ? d.pe.y : d.se.y);
-                    float2 ei = f_mul(splat<float2>(-K), f_mul(en, en));
-                    if (TEN) ei = f_sub(ei, make_float2(a0 ? d.qt.x : d.qs.x, a1 ? d.qt.y : d.qs.y));
-                    if (c == 1)
-                        ei = f_fma(splat<float2>(-J), make_float2(a0 ? d.th.x : d.sh.x, a1 ? d.th.y : d.sh.y), ei);
-                    acc.e = f_add(acc.e, ei);
-                    acc.x = f_add(acc.x, make_float2(a0 ? tx.x : sx.x, a1 ? tx.y : sx.y));
-                    acc.y = f_add(acc.y, make_float2(a0 ? ty.x : sy.x, a1 ? ty.y : sy.y));
-                    acc.z = f_add(acc.z, make_float2(a0 ? tz.x : sz.x, a1 ? tz.y : sz.y));
-                }
-            }
-        } else {
-#pragma unroll
-            for (int k = 0; k < V; ++k) {
-                float tx, ty, tz, u;
-                draw_trial_rank<P>(rank0 + k, a.sweep, (uint32_t)c, a.replica, a.key0, a.key1, tx, ty, tz, u);
-                single(k, tx, ty, tz, u);
-            }
-        }
+        // FP16 (bound by instruction issue, its loads decoupled by the
+        // pipelined landing slots) takes the same branch; the FP32 register
+        // stencil, bound by load latency, measured slower with it (the branch
+        // between an item's loads and its arithmetic costs more than the three
+        // instructions per site it saves) and keeps the general products
+        if constexpr (!TEN && P == HS_FP16)
+            if (a.zaxis) return update_f32<P, V, MEAS, false, true>(s, h, rank0, c, a, J, K, ex, ey, ez, beta, acc);
+        return update_f32<P, V, MEAS, TEN, false>(s, h, rank0, c, a, J, K, ex, ey, ez, beta, acc);
     }
-    return any;
 }
 
 // The same from the raw operands: step (i) then steps (ii)-(iii).

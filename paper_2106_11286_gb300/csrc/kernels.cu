@@ -117,7 +117,7 @@ __global__ void __launch_bounds__(kBlock, 2) sc_pass_kernel(const PassArgs a) {
             if (t >= n_items) break;
         }
     }
-    write_partials<C, MEAS>(a, acc.E(), acc.X(), acc.Y(), acc.Z(), acc.n);
+    write_partials<C, MEAS>(a, acc.E(J, K), acc.X(), acc.Y(), acc.Z(), acc.n);
 }
 
 // ----------------------------------------------------------------- pipelined stencil pass
@@ -264,7 +264,7 @@ __global__ void __launch_bounds__(kBlock, 2) sc_pipe_kernel(const PassArgs a) {
             t = tn;
         }
     }
-    write_partials<C, MEAS>(a, acc.E(), acc.X(), acc.Y(), acc.Z(), acc.n);
+    write_partials<C, MEAS>(a, acc.E(J, K), acc.X(), acc.Y(), acc.Z(), acc.n);
 }
 
 // ----------------------------------------------------------------- z-marching stencil pass
@@ -329,7 +329,7 @@ __global__ void __launch_bounds__(kBlock, 2) sc_march_kernel(const PassArgs a) {
             }
         }
     }
-    write_partials<C, MEAS>(a, acc.E(), acc.X(), acc.Y(), acc.Z(), acc.n);
+    write_partials<C, MEAS>(a, acc.E(J, K), acc.X(), acc.Y(), acc.Z(), acc.n);
 }
 
 // ----------------------------------------------------------------- table pass

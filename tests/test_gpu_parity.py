@@ -65,6 +65,26 @@ def _run_one_sweep(orc, case, precision, *, beta, seed, sweep_index, params=PARA
     return g, S0, S_gpu, S_orc, band, meas, acc
 
 
+# an easy axis that is not a coordinate axis: the general S.e products (the
+# e = (0, 0, 1) cases above take S.e = S_z)
+TILTED = dict(J=1.0, K=0.3, e=(0.3, -0.2, 1.0))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp16"])
+@pytest.mark.parametrize("name", ["sc16", "sc_12x8x6", "sc_10x6x4", "sc_masked"])
+def test_tilted_easy_axis_single_sweep(orc, name, precision):
+    g, S0, S_gpu, S_orc, band, meas, acc = _run_one_sweep(orc, CASES[name], precision, beta=1.0, seed=3,
+                                                         sweep_index=7, params=TILTED)
+    mism = check_sweep_parity(g, S0, S_gpu, S_orc, band, TOL[precision])
+    if precision == "fp64":
+        assert mism == int(band.sum() > 0) * mism
+    else:
+        assert mism <= max(2, g.n_present // 200)
+    assert 0 < acc < g.n_present
+    want = orc.measure(g, S_gpu, **TILTED)
+    assert meas["E"] == pytest.approx(want["E"], rel=1e-9, abs=1e-8)
+
+
 @pytest.mark.parametrize("name", list(CASES))
 def test_fp64_single_sweep(orc, name):
     g, S0, S_gpu, S_orc, band, meas, acc = _run_one_sweep(orc, CASES[name], "fp64", beta=1.0, seed=1,
@@ -142,13 +162,14 @@ def test_init_matches_oracle(orc, kind, dims, mask, precision):
         assert (diff <= ulp).all() and (diff > 0).mean() < 1e-3
 
 
-def test_accumulator_matches_oracle(orc):
+@pytest.mark.parametrize("params", [PARAMS, TILTED], ids=["z_axis", "tilted_axis"])
+def test_accumulator_matches_oracle(orc, params):
     """Fused per-sweep moments (E split at the later colour, FP64 totals)
     equal the oracle's full recompute after each sweep."""
     dims = (8, 8, 8)
     g = orc.lattice("sc", dims)
     beta = 0.8
-    with make_gpu("sc", dims, precision="fp64", seed=4, **PARAMS) as lat:
+    with make_gpu("sc", dims, precision="fp64", seed=4, **params) as lat:
         lat.init()
         S = lat.get_spins()
         lat.accumulate(True)
@@ -158,8 +179,8 @@ def test_accumulator_matches_oracle(orc):
     assert count == 5
     want = np.zeros(9)
     for s in range(5):
-        orc.sweep(g, S, beta=beta, seed=4, sweep_index=s, **PARAMS)
-        m = orc.measure(g, S, **PARAMS)
+        orc.sweep(g, S, beta=beta, seed=4, sweep_index=s, **params)
+        m = orc.measure(g, S, **params)
         want += [m["E"], m["E"] ** 2, m["absM"], m["M2"], m["M4"], *m["M"], m["absMe"]]
     np.testing.assert_allclose(mom, want, rtol=1e-10, atol=1e-10)
 
