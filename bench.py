@@ -204,7 +204,10 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     if world > 1:
         import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=dev)
+        import datetime
+        # between two collectives of this program the ranks work for seconds at most, so a rank whose peer
+        # failed on its own (out of memory, say) gives up after minutes instead of the default ten
+        dist.init_process_group("nccl", device_id=dev, timeout=datetime.timedelta(minutes=5))
     w = WORKLOAD
     L = w["L"]
     N = L ** 3
