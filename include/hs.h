@@ -47,14 +47,17 @@
  *   - Return HS_OK (0) or a negative hs_status; hs_last_error() gives a
  *     thread-local message for the last failure on the calling thread.
  *     Nothing aborts the process.
- *   - Host arrays passed in are copied; the caller keeps ownership.
- *   - The lattice handle owns all device memory it allocates.
+ *   - Host arrays passed in are copied before the call returns; the caller
+ *     keeps ownership (hs_set_spins_async reads its array later, see there).
+ *   - The lattice handle owns all device memory it allocates.  A handle is
+ *     used by one host thread at a time.
  *   - Device work is ordered on the CUDA stream given at creation (NULL =
  *     the legacy default stream).  Calls that return data to host memory
  *     synchronise that stream before returning.
- *   - Spins cross the boundary in FP64, natural site order, 3 doubles per
- *     site (x, y, z), for all n_sites natural indices; absent (masked) sites
- *     read back as 0 and are ignored on input.
+ *   - Spins cross the boundary in FP64 (hs_set_spins_async also takes FP32),
+ *     natural site order, 3 values per site (x, y, z), for all n_sites
+ *     natural indices; absent (masked) sites read back as 0 and are ignored
+ *     on input.
  *   - A device-side error (a bounded wait that timed out) is latched on the
  *     device and reported by the next call that synchronises.
  */
