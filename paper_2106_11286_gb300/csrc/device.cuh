@@ -811,7 +811,10 @@ __device__ __forceinline__ bool update_f32(Vec<typename Tr<P>::S, V> (&s)[3], co
     return any;
 }
 
-template <int P, int V, bool MEAS, bool TEN = false>
+// AX = 1: the kernel was chosen for e = (0, 0, 1) at launch, so S.e = S_z
+// with no branch (the FP32 register stencil's form); AX = 0: FP64 and FP16
+// decide per work item from PassArgs::zaxis, FP32 takes the general products.
+template <int P, int V, bool MEAS, bool TEN = false, int AX = 0>
 __device__ __forceinline__ bool update_item_h(Vec<typename Tr<P>::S, V> (&s)[3], const typename Tr<P>::C (&h)[3][V],
                                               uint32_t site0, uint32_t rank0, int c, const PassArgs &a,
                                               typename Tr<P>::C J, typename Tr<P>::C K, typename Tr<P>::C ex,
@@ -825,6 +828,8 @@ __device__ __forceinline__ bool update_item_h(Vec<typename Tr<P>::S, V> (&s)[3],
             if (a.zaxis) return update_fp64<V, MEAS, false, true>(s, h, site0, c, a, J, K, ex, ey, ez, beta, acc);
         return update_fp64<V, MEAS, TEN, false>(s, h, site0, c, a, J, K, ex, ey, ez, beta, acc);
     } else {
+        if constexpr (AX == 1 && !TEN)
+            return update_f32<P, V, MEAS, false, true>(s, h, rank0, c, a, J, K, ex, ey, ez, beta, acc);
         // FP16 (bound by instruction issue, its loads decoupled by the
         // pipelined landing slots) takes the same branch; the FP32 register
         // stencil, bound by load latency, measured slower with it (the branch
@@ -837,7 +842,7 @@ __device__ __forceinline__ bool update_item_h(Vec<typename Tr<P>::S, V> (&s)[3],
 }
 
 // The same from the raw operands: step (i) then steps (ii)-(iii).
-template <int P, int V, bool MEAS, bool TEN = false>
+template <int P, int V, bool MEAS, bool TEN = false, int AX = 0>
 __device__ __forceinline__ bool update_item(Vec<typename Tr<P>::S, V> (&s)[3], const Vec<typename Tr<P>::S, V> (&o)[3],
                                             const Vec<typename Tr<P>::S, V> (&nym)[3],
                                             const Vec<typename Tr<P>::S, V> (&nyp)[3],
@@ -849,7 +854,7 @@ __device__ __forceinline__ bool update_item(Vec<typename Tr<P>::S, V> (&s)[3], c
                                             SiteAcc<P> &acc) {
     typename Tr<P>::C h[3][V];
     item_fields<P, V>(o, nym, nyp, nzm, nzp, ed, p, h);
-    return update_item_h<P, V, MEAS, TEN>(s, h, site0, rank0, c, a, J, K, ex, ey, ez, beta, acc);
+    return update_item_h<P, V, MEAS, TEN, AX>(s, h, site0, rank0, c, a, J, K, ex, ey, ez, beta, acc);
 }
 
 // Vector load, optionally L2-only (ld.global.cg).  A kernel that reads data

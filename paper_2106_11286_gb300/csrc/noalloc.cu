@@ -120,6 +120,7 @@ extern "C" int hs_sweep_sc_fp32_noalloc(float *planes, const int32_t dims[3], co
     a.J = p->J;
     a.K = p->K;
     for (int q = 0; q < 3; ++q) a.e[q] = p->e[q] / en;
+    a.zaxis = (a.e[0] == 0.0 && a.e[1] == 0.0 && a.e[2] == 1.0) ? 1 : 0;
     a.beta = beta;
     a.fJ = (float)a.J;
     a.fK = (float)a.K;

@@ -9,9 +9,14 @@ import bench
 
 def test_kernel_labels():
     base = dict(kernel=1, vec_width=4, prefetch=3)
-    assert bench.kernel_label(base) == "sc_pass_kernel<1, 4, 1, 2, 0, 1>"
-    assert bench.kernel_label(dict(base, prefetch=1)) == "sc_pass_kernel<1, 4, 1, 1, 0, 1>"
-    assert bench.kernel_label(dict(base, prefetch=2)) == "sc_pass_kernel<1, 4, 1, 0, 0, 1>"
+    assert bench.kernel_label(base) == "sc_pass_kernel<1, 4, 1, 2, 0, 1, 0>"
+    assert bench.kernel_label(dict(base, prefetch=1)) == "sc_pass_kernel<1, 4, 1, 1, 0, 1, 0>"
+    assert bench.kernel_label(dict(base, prefetch=2)) == "sc_pass_kernel<1, 4, 1, 0, 0, 1, 0>"
+    # the S.e = S_z variant: FP32, V = 4, no prefetch, e = (0, 0, 1)
+    assert bench.kernel_label(dict(base, prefetch=2), zaxis=True) == "sc_pass_kernel<1, 4, 1, 0, 0, 1, 1>"
+    assert bench.kernel_label(dict(base, prefetch=3), zaxis=True) == "sc_pass_kernel<1, 4, 1, 2, 0, 1, 0>"
+    assert bench.kernel_label(dict(base, prefetch=2), precision_code=0, zaxis=True) == \
+        "sc_pass_kernel<0, 4, 1, 0, 0, 1, 0>"
     assert bench.kernel_label(dict(kernel=5, vec_width=8, prefetch=0)) == "sc_pipe_kernel"
     assert bench.kernel_label(dict(kernel=3, vec_width=1, prefetch=1)) == "table_pass_kernel"
 
@@ -33,7 +38,7 @@ def test_traffic_only_for_the_captured_sources_and_kernel(tmp_path, monkeypatch)
 def test_committed_traffic_matches_the_sources():
     """The stored capture belongs to the current kernel sources (else the bench
     reports no traffic)."""
-    assert bench.read_traffic("sc_pass_kernel<1, 4, 1, 0, 0, 1>", 2) is not None
+    assert bench.read_traffic("sc_pass_kernel<1, 4, 1, 0, 0, 1, 1>", 2) is not None
 
 
 def test_fp64_ops_only_for_the_captured_sources_and_kernel(tmp_path, monkeypatch):
@@ -52,7 +57,7 @@ def test_fp64_ops_only_for_the_captured_sources_and_kernel(tmp_path, monkeypatch
 def test_committed_fp64_ops_match_the_sources():
     """The stored FP64 instruction counts belong to the current kernel sources
     and to the kernel the bench's FP64 form runs (the automatic launch)."""
-    assert bench.read_fp64_ops("sc_pass_kernel<0, 2, 1, 0, 0, 1>") is not None
+    assert bench.read_fp64_ops("sc_pass_kernel<0, 2, 1, 0, 0, 1, 0>") is not None
 
 
 def test_spin_error_measure():
