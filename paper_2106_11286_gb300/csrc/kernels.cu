@@ -226,7 +226,7 @@ __device__ __forceinline__ void pipe_read(const typename PipeSlot<P, V>::VT *sv,
     it.rank0 = f.rank0;
 }
 
-template <int P, int V, bool MEAS>
+template <int P, int V, bool MEAS, int AX = 0>
 __global__ void __launch_bounds__(kBlock, 2) sc_pipe_kernel(const PassArgs a) {
     pdl_enter();
     using S = typename Tr<P>::S;
@@ -258,8 +258,8 @@ __global__ void __launch_bounds__(kBlock, 2) sc_pipe_kernel(const PassArgs a) {
             const uint32_t tn = t + stride;
             const bool more = tn < n_items;
             if (more) f = pipe_issue<P, V>(a, tn, own, oth, slot_v, slot_e);
-            if (update_item<P, V, MEAS>(it.s, it.o, it.nym, it.nyp, it.nzm, it.nzp, it.ed, it.p, it.site0, it.rank0, c, a, J, K,
-                                        ex, ey, ez, beta, acc)) {
+            if (update_item<P, V, MEAS, false, AX>(it.s, it.o, it.nym, it.nyp, it.nzm, it.nzp, it.ed, it.p, it.site0,
+                                                   it.rank0, c, a, J, K, ex, ey, ez, beta, acc)) {
 #pragma unroll
                 for (int q = 0; q < 3; ++q) *reinterpret_cast<VT *>(own_w[q] + it.b0) = it.s[q];
             }
@@ -736,9 +736,18 @@ cudaError_t launch_sc_v(const PassArgs &a, int n_blocks, cudaStream_t s, bool me
     return launch_sc_pf<P, V, 0>(a, n_blocks, s, meas);
 }
 
+// FP16 V = 8 (the pipelined kernel the FP16 workloads run) has the S.e = S_z
+// variant for e = (0, 0, 1), chosen here rather than per work item.
+template <int P, int V>
+constexpr bool has_pipe_ax_variant() { return P == HS_FP16 && V == 8; }
+
 template <int P, int V>
 cudaError_t launch_pipe_v(const PassArgs &a, int n_blocks, cudaStream_t s, bool meas) {
     const size_t smem = PipeSlot<P, V>::kBytes;
+    if constexpr (has_pipe_ax_variant<P, V>())
+        if (a.zaxis)
+            return meas ? launch_pdl(sc_pipe_kernel<P, V, true, 1>, n_blocks, kBlock, smem, s, a)
+                        : launch_pdl(sc_pipe_kernel<P, V, false, 1>, n_blocks, kBlock, smem, s, a);
     return meas ? launch_pdl(sc_pipe_kernel<P, V, true>, n_blocks, kBlock, smem, s, a)
                 : launch_pdl(sc_pipe_kernel<P, V, false>, n_blocks, kBlock, smem, s, a);
 }
@@ -849,6 +858,13 @@ static const void *march_ptr(bool meas) {
 template <int P, int V>
 static const void *pipe_ptr(bool meas) {
     return meas ? (const void *)sc_pipe_kernel<P, V, true> : (const void *)sc_pipe_kernel<P, V, false>;
+}
+
+// the S.e = S_z twin of the pipelined kernel for this precision and width, or nullptr
+static const void *pipe_ax_ptr(int precision, int vec, bool meas) {
+    if (precision == HS_FP16 && vec == 8)
+        return meas ? (const void *)sc_pipe_kernel<HS_FP16, 8, true, 1> : (const void *)sc_pipe_kernel<HS_FP16, 8, false, 1>;
+    return nullptr;
 }
 
 template <int P>
@@ -963,6 +979,11 @@ int pass_occupancy(int precision, const Layout &L, int accumulate) {
         if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
             cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, pct) != cudaSuccess)
             return 0;
+        // the launch may take the kernel's S.e = S_z twin (same slots and registers): the same opt-in
+        if (const void *kx = pipe_ax_ptr(precision, L.vec, accumulate != 0))
+            if (cudaFuncSetAttribute(kx, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+                cudaFuncSetAttribute(kx, cudaFuncAttributePreferredSharedMemoryCarveout, pct) != cudaSuccess)
+                return 0;
     }
     int blocks = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k, kBlock, smem) != cudaSuccess) return 1;
