@@ -1494,6 +1494,8 @@ hs::BatchArgs batch_args(const hs_batch *b, int n_total, int n_equil) {
     a.error = b->d_error;
     a.n_total = n_total;
     a.n_equil = n_equil;
+    a.zaxis_all = 1;
+    for (const hs::BatchMember &m : b->host_members) a.zaxis_all &= m.zaxis;
     return a;
 }
 }  // namespace

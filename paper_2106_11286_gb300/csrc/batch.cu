@@ -164,7 +164,9 @@ __device__ void finalize_sweep(const BatchArgs &b, int s) {
 template <int P>
 constexpr int kBatchVec = (P == HS_FP64) ? 2 : 4;  // batch_vec()
 
-template <int P, int PF, bool CG>
+// AX = 1: every member's easy axis is (0, 0, 1), so S.e = S_z (the FP32
+// kernels' variant chosen at launch, as for a single lattice).
+template <int P, int PF, bool CG, int AX = 0>
 __device__ __forceinline__ void batch_pass(const BatchArgs &b, int s, int c) {
     constexpr int V = kBatchVec<P>;
     using S = typename Tr<P>::S;
@@ -215,7 +217,7 @@ __device__ __forceinline__ void batch_pass(const BatchArgs &b, int s, int c) {
                     const uint32_t tn = t + sg.stride;
                     const bool more = tn < sg.end;
                     if (more) load_split_a<P, V, CG>(a, tn, own, oth, A);  // the neighbour vectors are dead
-                    if (update_item_h<P, V, true>(sv, h, site0, rank0, c, a, J, K, ex, ey, ez, beta, acc)) {
+                    if (update_item_h<P, V, true, false, AX>(sv, h, site0, rank0, c, a, J, K, ex, ey, ez, beta, acc)) {
 #pragma unroll
                         for (int q = 0; q < 3; ++q) *reinterpret_cast<VT *>(own_w[q] + b0) = sv[q];
                     }
@@ -227,8 +229,8 @@ __device__ __forceinline__ void batch_pass(const BatchArgs &b, int s, int c) {
             for (uint32_t t = sg.begin + threadIdx.x; t < sg.end; t += sg.stride) {
                 StencilItem<P, V> it;
                 load_item<P, V, CG>(a, t, own, oth, it);
-                if (update_item<P, V, true>(it.s, it.o, it.nym, it.nyp, it.nzm, it.nzp, it.ed, it.p, it.site0,
-                                            it.rank0, c, a, J, K, ex, ey, ez, beta, acc)) {
+                if (update_item<P, V, true, false, AX>(it.s, it.o, it.nym, it.nyp, it.nzm, it.nzp, it.ed, it.p, it.site0,
+                                                       it.rank0, c, a, J, K, ex, ey, ez, beta, acc)) {
 #pragma unroll
                     for (int q = 0; q < 3; ++q) *reinterpret_cast<VT *>(own_w[q] + it.b0) = it.s[q];
                 }
@@ -259,12 +261,12 @@ __device__ __forceinline__ void batch_pass(const BatchArgs &b, int s, int c) {
 
 // The persistent schedule: every sweep and colour pass in one cooperative
 // launch, passes separated by the bounded grid barrier.
-template <int P, int PF>
+template <int P, int PF, int AX = 0>
 __global__ void __launch_bounds__(kBlock, 2) batch_kernel(const BatchArgs b) {
     unsigned long long *cnt = reinterpret_cast<unsigned long long *>(b.bar);
     for (int s = 0; s < b.n_total; ++s) {
         for (int c = 0; c < 2; ++c) {
-            batch_pass<P, PF, true>(b, s, c);
+            batch_pass<P, PF, true, AX>(b, s, c);
             const bool skip = b.inject_skip && blockIdx.x == 0 && s == 0 && c == 0;
             barrier_arrive(cnt, skip);
             // the previous sweep's finalise runs while this CTA waits for the
@@ -288,11 +290,11 @@ __global__ void __launch_bounds__(kBlock, 2) batch_kernel(const BatchArgs b) {
 // touching memory).  Pass 0 of sweep s first finalises sweep s - 1, whose
 // passes have completed by then; the slots it reads (parity (s-1) & 1) are
 // rewritten only by pass 0 of sweep s + 1, two completed launches later.
-template <int P, int PF>
+template <int P, int PF, int AX = 0>
 __global__ void __launch_bounds__(kBlock, 2) batch_pass_kernel(const BatchArgs b, int s, int c) {
     pdl_enter();
     if (c == 0 && s > 0) finalize_sweep(b, s - 1);
-    batch_pass<P, PF, false>(b, s, c);
+    batch_pass<P, PF, false, AX>(b, s, c);
 }
 
 // The last sweep's finalise of the per-pass schedule.
@@ -356,7 +358,7 @@ __device__ void resident_fold(const BatchMember &m, const double (*s_tot)[kParti
     __syncwarp();
 }
 
-template <int P>
+template <int P, int AX = 0>
 __global__ void __launch_bounds__(kBlock, 2) batch_resident_kernel(const BatchArgs b) {
     constexpr int V = kBatchVec<P>;
     using S = typename Tr<P>::S;
@@ -400,8 +402,8 @@ __global__ void __launch_bounds__(kBlock, 2) batch_resident_kernel(const BatchAr
             for (uint32_t t = threadIdx.x; t < n_items; t += kBlock) {
                 StencilItem<P, V> it;
                 load_item<P, V>(a, t, own, oth, it);
-                if (update_item<P, V, true>(it.s, it.o, it.nym, it.nyp, it.nzm, it.nzp, it.ed, it.p, it.site0,
-                                            it.rank0, c, a, J, K, ex, ey, ez, beta, acc)) {
+                if (update_item<P, V, true, false, AX>(it.s, it.o, it.nym, it.nyp, it.nzm, it.nzp, it.ed, it.p, it.site0,
+                                                       it.rank0, c, a, J, K, ex, ey, ez, beta, acc)) {
 #pragma unroll
                     for (int q = 0; q < 3; ++q) *reinterpret_cast<VT *>(own_w[q] + it.b0) = it.s[q];
                 }
@@ -470,15 +472,38 @@ int occupancy_p(int prefetch) {
     const void *kp = prefetch ? (const void *)batch_pass_kernel<P, 2> : (const void *)batch_pass_kernel<P, 0>;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k, kBlock, 0) != cudaSuccess) return 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_pass, kp, kBlock, 0) != cudaSuccess) return 0;
-    return blocks < blocks_pass ? blocks : blocks_pass;
+    int occ = blocks < blocks_pass ? blocks : blocks_pass;
+    if constexpr (P == HS_FP32) {  // the launch may take the S.e = S_z variants: the grid must fit either
+        const void *kx = prefetch ? (const void *)batch_kernel<P, 2, 1> : (const void *)batch_kernel<P, 0, 1>;
+        const void *kpx = prefetch ? (const void *)batch_pass_kernel<P, 2, 1> : (const void *)batch_pass_kernel<P, 0, 1>;
+        int bx = 0, bpx = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bx, kx, kBlock, 0) != cudaSuccess) return 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bpx, kpx, kBlock, 0) != cudaSuccess) return 0;
+        occ = occ < bx ? occ : bx;
+        occ = occ < bpx ? occ : bpx;
+    }
+    return occ;
 }
+
+// the S.e = S_z kernels serve FP32 batches whose members all have e = (0, 0, 1)
+template <int P>
+constexpr bool batch_has_ax() { return P == HS_FP32; }
 
 template <int P>
 cudaError_t passes_p(const BatchArgs &b, int grid, cudaStream_t s, int prefetch) {
     for (int sw = 0; sw < b.n_total; ++sw)
         for (int c = 0; c < 2; ++c) {
-            const cudaError_t e = prefetch ? launch_chained(batch_pass_kernel<P, 2>, grid, s, b, sw, c)
-                                           : launch_chained(batch_pass_kernel<P, 0>, grid, s, b, sw, c);
+            cudaError_t e = cudaSuccess;
+            bool done = false;
+            if constexpr (batch_has_ax<P>())
+                if (b.zaxis_all) {
+                    e = prefetch ? launch_chained(batch_pass_kernel<P, 2, 1>, grid, s, b, sw, c)
+                                 : launch_chained(batch_pass_kernel<P, 0, 1>, grid, s, b, sw, c);
+                    done = true;
+                }
+            if (!done)
+                e = prefetch ? launch_chained(batch_pass_kernel<P, 2>, grid, s, b, sw, c)
+                             : launch_chained(batch_pass_kernel<P, 0>, grid, s, b, sw, c);
             if (e != cudaSuccess) return e;
         }
     if (b.n_total > 0) return launch_chained(batch_finalize_kernel, grid, s, b, b.n_total - 1);
@@ -496,13 +521,20 @@ size_t resident_limit_p() {
     return optin > (int)fa.sharedSizeBytes ? (size_t)optin - fa.sharedSizeBytes : 0;
 }
 
-template <int P>
-cudaError_t resident_p(const BatchArgs &b, size_t smem, cudaStream_t s) {
-    cudaError_t e = cudaFuncSetAttribute(batch_resident_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+template <int P, int AX>
+cudaError_t resident_ax(const BatchArgs &b, size_t smem, cudaStream_t s) {
+    cudaError_t e = cudaFuncSetAttribute(batch_resident_kernel<P, AX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    batch_resident_kernel<P><<<b.n_members, kBlock, smem, s>>>(b);
+    batch_resident_kernel<P, AX><<<b.n_members, kBlock, smem, s>>>(b);
     return cudaGetLastError();
+}
+
+template <int P>
+cudaError_t resident_p(const BatchArgs &b, size_t smem, cudaStream_t s) {
+    if constexpr (batch_has_ax<P>())
+        if (b.zaxis_all) return resident_ax<P, 1>(b, smem, s);
+    return resident_ax<P, 0>(b, smem, s);
 }
 
 template <int P>
@@ -517,6 +549,10 @@ cudaError_t persistent_p(const BatchArgs &b, int grid, cudaStream_t s, int prefe
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
+    if constexpr (batch_has_ax<P>())
+        if (b.zaxis_all)
+            return prefetch ? cudaLaunchKernelEx(&cfg, batch_kernel<P, 2, 1>, b)
+                            : cudaLaunchKernelEx(&cfg, batch_kernel<P, 0, 1>, b);
     return prefetch ? cudaLaunchKernelEx(&cfg, batch_kernel<P, 2>, b) : cudaLaunchKernelEx(&cfg, batch_kernel<P, 0>, b);
 }
 }  // namespace

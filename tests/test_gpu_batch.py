@@ -17,20 +17,25 @@ from paper_2106_11286_gb300 import hs
 pytestmark = pytest.mark.gpu
 
 
-def _members(dims_list, betas, K=0.1, seed=11, precision="fp32"):
-    return [hs.Lattice("sc", dims=d, J=1.0, K=K, e=(0, 0, 1), precision=precision, seed=seed, replica=r)
+def _members(dims_list, betas, K=0.1, seed=11, precision="fp32", axes=None):
+    axes = axes or [(0, 0, 1)] * len(dims_list)
+    return [hs.Lattice("sc", dims=d, J=1.0, K=K, e=axes[r], precision=precision, seed=seed, replica=r)
             for r, d in enumerate(dims_list)]
 
 
 RTOL = {"fp64": 1e-12, "fp32": 2e-6, "fp16": 2e-6}   # moments: FP64 sums taken in another order
 
 
+# every member along z (FP32 batches then run their S.e = S_z kernels), or one
+# member with another axis (the whole batch takes the general products)
+@pytest.mark.parametrize("axes", ["z", "mixed"])
 @pytest.mark.parametrize("precision", ["fp32", "fp64", "fp16"])
-def test_batch_matches_individual_sweeps(precision):
+def test_batch_matches_individual_sweeps(precision, axes):
     dims = [(16, 16, 16), (24, 24, 24), (8, 8, 8), (32, 16, 8), (40, 8, 12)]
     betas = [0.6, 0.8, 1.0, 1.2, 0.9]
-    a = _members(dims, betas, precision=precision)
-    b = _members(dims, betas, precision=precision)
+    ax = [(0, 0, 1)] * 5 if axes == "z" else [(0, 0, 1), (0.3, -0.2, 1.0), (0, 0, 1), (0, 0, 1), (1, 0, 0)]
+    a = _members(dims, betas, precision=precision, axes=ax)
+    b = _members(dims, betas, precision=precision, axes=ax)
     for x, y in zip(a, b):
         x.init()
         y.init()
