@@ -1495,7 +1495,11 @@ hs::BatchArgs batch_args(const hs_batch *b, int n_total, int n_equil) {
     a.n_total = n_total;
     a.n_equil = n_equil;
     a.zaxis_all = 1;
-    for (const hs::BatchMember &m : b->host_members) a.zaxis_all &= m.zaxis;
+    a.kzero_all = 1;
+    for (const hs::BatchMember &m : b->host_members) {
+        a.zaxis_all &= m.zaxis;
+        a.kzero_all &= (m.K == 0.0 && !std::signbit(m.K)) ? 1 : 0;
+    }
     return a;
 }
 }  // namespace

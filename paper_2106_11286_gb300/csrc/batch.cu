@@ -165,7 +165,8 @@ template <int P>
 constexpr int kBatchVec = (P == HS_FP64) ? 2 : 4;  // batch_vec()
 
 // AX = 1: every member's easy axis is (0, 0, 1), so S.e = S_z (the FP32
-// kernels' variant chosen at launch, as for a single lattice).
+// kernels' variant chosen at launch, as for a single lattice); AX = 2: every
+// member's K is +0 as well, so the uniaxial term is left out.
 template <int P, int PF, bool CG, int AX = 0>
 __device__ __forceinline__ void batch_pass(const BatchArgs &b, int s, int c) {
     constexpr int V = kBatchVec<P>;
@@ -473,17 +474,23 @@ int occupancy_p(int prefetch) {
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k, kBlock, 0) != cudaSuccess) return 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_pass, kp, kBlock, 0) != cudaSuccess) return 0;
     int occ = blocks < blocks_pass ? blocks : blocks_pass;
-    if constexpr (P == HS_FP32) {  // the launch may take the S.e = S_z variants: the grid must fit either
-        const void *kx = prefetch ? (const void *)batch_kernel<P, 2, 1> : (const void *)batch_kernel<P, 0, 1>;
-        const void *kpx = prefetch ? (const void *)batch_pass_kernel<P, 2, 1> : (const void *)batch_pass_kernel<P, 0, 1>;
-        int bx = 0, bpx = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bx, kx, kBlock, 0) != cudaSuccess) return 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bpx, kpx, kBlock, 0) != cudaSuccess) return 0;
-        occ = occ < bx ? occ : bx;
-        occ = occ < bpx ? occ : bpx;
+    if constexpr (P == HS_FP32) {  // the launch may take the axis variants: the grid must fit each
+        const void *ks[4] = {
+            prefetch ? (const void *)batch_kernel<P, 2, 1> : (const void *)batch_kernel<P, 0, 1>,
+            prefetch ? (const void *)batch_pass_kernel<P, 2, 1> : (const void *)batch_pass_kernel<P, 0, 1>,
+            prefetch ? (const void *)batch_kernel<P, 2, 2> : (const void *)batch_kernel<P, 0, 2>,
+            prefetch ? (const void *)batch_pass_kernel<P, 2, 2> : (const void *)batch_pass_kernel<P, 0, 2>};
+        for (const void *kx : ks) {
+            int bx = 0;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bx, kx, kBlock, 0) != cudaSuccess) return 0;
+            occ = occ < bx ? occ : bx;
+        }
     }
     return occ;
 }
+
+// the axis variant a batch takes: 0 general, 1 e = z for every member, 2 also K = +0 (FP32 only)
+inline int batch_ax(const BatchArgs &b) { return b.zaxis_all ? (b.kzero_all ? 2 : 1) : 0; }
 
 // the S.e = S_z kernels serve FP32 batches whose members all have e = (0, 0, 1)
 template <int P>
@@ -494,14 +501,16 @@ cudaError_t passes_p(const BatchArgs &b, int grid, cudaStream_t s, int prefetch)
     for (int sw = 0; sw < b.n_total; ++sw)
         for (int c = 0; c < 2; ++c) {
             cudaError_t e = cudaSuccess;
-            bool done = false;
+            const int ax = batch_has_ax<P>() ? batch_ax(b) : 0;
             if constexpr (batch_has_ax<P>())
-                if (b.zaxis_all) {
+                if (ax == 2)
+                    e = prefetch ? launch_chained(batch_pass_kernel<P, 2, 2>, grid, s, b, sw, c)
+                                 : launch_chained(batch_pass_kernel<P, 0, 2>, grid, s, b, sw, c);
+            if constexpr (batch_has_ax<P>())
+                if (ax == 1)
                     e = prefetch ? launch_chained(batch_pass_kernel<P, 2, 1>, grid, s, b, sw, c)
                                  : launch_chained(batch_pass_kernel<P, 0, 1>, grid, s, b, sw, c);
-                    done = true;
-                }
-            if (!done)
+            if (ax == 0)
                 e = prefetch ? launch_chained(batch_pass_kernel<P, 2>, grid, s, b, sw, c)
                              : launch_chained(batch_pass_kernel<P, 0>, grid, s, b, sw, c);
             if (e != cudaSuccess) return e;
@@ -532,8 +541,10 @@ cudaError_t resident_ax(const BatchArgs &b, size_t smem, cudaStream_t s) {
 
 template <int P>
 cudaError_t resident_p(const BatchArgs &b, size_t smem, cudaStream_t s) {
-    if constexpr (batch_has_ax<P>())
-        if (b.zaxis_all) return resident_ax<P, 1>(b, smem, s);
+    if constexpr (batch_has_ax<P>()) {
+        if (batch_ax(b) == 2) return resident_ax<P, 2>(b, smem, s);
+        if (batch_ax(b) == 1) return resident_ax<P, 1>(b, smem, s);
+    }
     return resident_ax<P, 0>(b, smem, s);
 }
 
@@ -549,10 +560,14 @@ cudaError_t persistent_p(const BatchArgs &b, int grid, cudaStream_t s, int prefe
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    if constexpr (batch_has_ax<P>())
-        if (b.zaxis_all)
+    if constexpr (batch_has_ax<P>()) {
+        if (batch_ax(b) == 2)
+            return prefetch ? cudaLaunchKernelEx(&cfg, batch_kernel<P, 2, 2>, b)
+                            : cudaLaunchKernelEx(&cfg, batch_kernel<P, 0, 2>, b);
+        if (batch_ax(b) == 1)
             return prefetch ? cudaLaunchKernelEx(&cfg, batch_kernel<P, 2, 1>, b)
                             : cudaLaunchKernelEx(&cfg, batch_kernel<P, 0, 1>, b);
+    }
     return prefetch ? cudaLaunchKernelEx(&cfg, batch_kernel<P, 2>, b) : cudaLaunchKernelEx(&cfg, batch_kernel<P, 0>, b);
 }
 }  // namespace

@@ -279,7 +279,9 @@ __device__ __forceinline__ double quad64(double x, double y, double z, const dou
 
 // TEN adds the tensor term: dH += S^T A S - S'^T A S'.  ZAX: the easy axis is
 // e = (0, 0, 1) exactly, so S.e = S_z (what the three products give for it).
-template <typename T, bool TEN = false, bool ZAX = false>
+// KZ: K = +0, so the uniaxial term, +0 times a finite number, adds nothing
+// (dH may differ only in the sign of a zero, which dH <= 0 does not see).
+template <typename T, bool TEN = false, bool ZAX = false, bool KZ = false>
 __device__ __forceinline__ Dots32<T> site_math32(T sx, T sy, T sz, T tx, T ty, T tz, T hx, T hy, T hz, float J,
                                                  float K, float ex, float ey, float ez, const float *A = nullptr) {
     Dots32<T> d;
@@ -292,7 +294,10 @@ __device__ __forceinline__ Dots32<T> site_math32(T sx, T sy, T sz, T tx, T ty, T
         d.se = f_fma(sz, splat<T>(ez), f_fma(sy, splat<T>(ey), f_mul(sx, splat<T>(ex))));
         d.pe = f_fma(tz, splat<T>(ez), f_fma(ty, splat<T>(ey), f_mul(tx, splat<T>(ex))));
     }
-    d.dH = f_fma(splat<T>(K), f_mul(f_sub(d.se, d.pe), f_add(d.se, d.pe)), f_mul(splat<T>(J), f_sub(d.sh, d.th)));
+    if constexpr (KZ)
+        d.dH = f_mul(splat<T>(J), f_sub(d.sh, d.th));
+    else
+        d.dH = f_fma(splat<T>(K), f_mul(f_sub(d.se, d.pe), f_add(d.se, d.pe)), f_mul(splat<T>(J), f_sub(d.sh, d.th)));
     if constexpr (TEN) {
         const float(&At)[6] = *reinterpret_cast<const float(*)[6]>(A);
         d.qs = quad32<T>(sx, sy, sz, At);
@@ -722,7 +727,9 @@ __device__ __forceinline__ bool update_fp64(Vec<double, V> (&s)[3], const double
 // accepted.
 // Metropolis steps (ii)-(iii) for the V sites of one FP32 / FP16 work item
 // (see update_item_h); ZAX as in site_math32.
-template <int P, int V, bool MEAS, bool TEN, bool ZAX>
+// KZ (with ZAX): K = +0, whose energy share -K (S.e)^2 is -0 (written as such,
+// so every sum takes the same values; adding -0 changes none).
+template <int P, int V, bool MEAS, bool TEN, bool ZAX, bool KZ = false>
 __device__ __forceinline__ bool update_f32(Vec<typename Tr<P>::S, V> (&s)[3], const float (&h)[3][V], uint32_t rank0,
                                            int c, const PassArgs &a, float J, float K, float ex, float ey, float ez,
                                            float beta, SiteAcc<P> &acc) {
@@ -733,7 +740,7 @@ __device__ __forceinline__ bool update_f32(Vec<typename Tr<P>::S, V> (&s)[3], co
     // one site in lane x of the accumulators
     auto single = [&](int k, float tx, float ty, float tz, float u) {
         const float sx = to_c(s[0].v[k]), sy = to_c(s[1].v[k]), sz = to_c(s[2].v[k]);
-        const Dots32<float> d = site_math32<float, TEN, ZAX>(sx, sy, sz, tx, ty, tz, h[0][k], h[1][k], h[2][k], J, K,
+        const Dots32<float> d = site_math32<float, TEN, ZAX, KZ>(sx, sy, sz, tx, ty, tz, h[0][k], h[1][k], h[2][k], J, K,
                                                         ex, ey, ez, a.fA);
         const bool ac = accept32(d.dH, u, nb);
         if (ac) {
@@ -745,7 +752,7 @@ __device__ __forceinline__ bool update_f32(Vec<typename Tr<P>::S, V> (&s)[3], co
         }
         if (MEAS) {
             const float en = ac ? d.pe : d.se;
-            float ei = f_mul(-K, f_mul(en, en));
+            float ei = KZ ? -0.0f : f_mul(-K, f_mul(en, en));
             if (TEN) ei = f_sub(ei, ac ? d.qt : d.qs);
             if (c == 1) ei = f_fma(-J, ac ? d.th : d.sh, ei);
             acc.e.x = f_add(acc.e.x, ei);
@@ -772,7 +779,7 @@ __device__ __forceinline__ bool update_f32(Vec<typename Tr<P>::S, V> (&s)[3], co
             const float2 sy = make_float2(to_c(s[1].v[k0]), to_c(s[1].v[k1]));
             const float2 sz = make_float2(to_c(s[2].v[k0]), to_c(s[2].v[k1]));
             const Dots32<float2> d =
-                site_math32<float2, TEN, ZAX>(sx, sy, sz, tx, ty, tz, hp[0], hp[1], hp[2], J, K, ex, ey, ez, a.fA);
+                site_math32<float2, TEN, ZAX, KZ>(sx, sy, sz, tx, ty, tz, hp[0], hp[1], hp[2], J, K, ex, ey, ez, a.fA);
             const bool a0 = accept32(d.dH.x, u.x, nb);
             const bool a1 = accept32(d.dH.y, u.y, nb);
             if (a0) {
@@ -790,7 +797,7 @@ __device__ __forceinline__ bool update_f32(Vec<typename Tr<P>::S, V> (&s)[3], co
             any = any || a0 || a1;
             if (MEAS) {
                 const float2 en = make_float2(a0 ? d.pe.x : d.se.x, a1 ? d.pe.y : d.se.y);
-                float2 ei = f_mul(splat<float2>(-K), f_mul(en, en));
+                float2 ei = KZ ? make_float2(-0.0f, -0.0f) : f_mul(splat<float2>(-K), f_mul(en, en));
                 if (TEN) ei = f_sub(ei, make_float2(a0 ? d.qt.x : d.qs.x, a1 ? d.qt.y : d.qs.y));
                 if (c == 1)
                     ei = f_fma(splat<float2>(-J), make_float2(a0 ? d.th.x : d.sh.x, a1 ? d.th.y : d.sh.y), ei);
@@ -812,8 +819,9 @@ __device__ __forceinline__ bool update_f32(Vec<typename Tr<P>::S, V> (&s)[3], co
 }
 
 // AX = 1: the kernel was chosen for e = (0, 0, 1) at launch, so S.e = S_z
-// with no branch (the FP32 register stencil's form); AX = 0: FP64 and FP16
-// decide per work item from PassArgs::zaxis, FP32 takes the general products.
+// with no branch (the FP32 register stencil's form); AX = 2: the same with
+// K = +0 (the FP32 batch kernels); AX = 0: FP64 and FP16 decide per work item
+// from PassArgs::zaxis, FP32 takes the general products.
 template <int P, int V, bool MEAS, bool TEN = false, int AX = 0>
 __device__ __forceinline__ bool update_item_h(Vec<typename Tr<P>::S, V> (&s)[3], const typename Tr<P>::C (&h)[3][V],
                                               uint32_t site0, uint32_t rank0, int c, const PassArgs &a,
@@ -828,8 +836,8 @@ __device__ __forceinline__ bool update_item_h(Vec<typename Tr<P>::S, V> (&s)[3],
             if (a.zaxis) return update_fp64<V, MEAS, false, true>(s, h, site0, c, a, J, K, ex, ey, ez, beta, acc);
         return update_fp64<V, MEAS, TEN, false>(s, h, site0, c, a, J, K, ex, ey, ez, beta, acc);
     } else {
-        if constexpr (AX == 1 && !TEN)
-            return update_f32<P, V, MEAS, false, true>(s, h, rank0, c, a, J, K, ex, ey, ez, beta, acc);
+        if constexpr (AX >= 1 && !TEN)
+            return update_f32<P, V, MEAS, false, true, AX == 2>(s, h, rank0, c, a, J, K, ex, ey, ez, beta, acc);
         // FP16 (bound by instruction issue, its loads decoupled by the
         // pipelined landing slots) takes the same branch; the FP32 register
         // stencil, bound by load latency, measured slower with it (the branch
