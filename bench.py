@@ -1170,7 +1170,7 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--fp64-steps", type=int, default=30)
-    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--e2e-sweeps", type=int, default=100)
     ap.add_argument("--cpu-sweeps", type=int, default=3)
     ap.add_argument("--no-fp64", action="store_true")
