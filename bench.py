@@ -988,8 +988,10 @@ CASES = {
 }
 
 
-# batch cases: name -> (replicas, L, precision, schedule)
-BATCH_CASES = {"batch304x16_resident": (304, 16, "fp32", 2), "batch304x16_persistent": (304, 16, "fp32", 0)}
+# batch cases: name -> (replicas, L, precision, schedule); L None: the bench's 64-replica mix
+# (L = BATCH_SIZES[r mod 6], K = 0)
+BATCH_CASES = {"batch304x16_resident": (304, 16, "fp32", 2), "batch304x16_persistent": (304, 16, "fp32", 0),
+               "batch64_mix": (64, None, "fp32", 0)}
 
 
 def run_batch_case(args):
@@ -1000,7 +1002,8 @@ def run_batch_case(args):
 
     from paper_2106_11286_gb300 import hs
     n, L, prec, sched = BATCH_CASES[args.case]
-    lats = [hs.Lattice("sc", dims=(L,) * 3, J=1.0, K=0.0, precision=prec, seed=8, replica=r) for r in range(n)]
+    sizes = [L if L else BATCH_SIZES[r % 6] for r in range(n)]
+    lats = [hs.Lattice("sc", dims=(sizes[r],) * 3, J=1.0, K=0.0, precision=prec, seed=8, replica=r) for r in range(n)]
     try:
         betas = [1.0 / (1.30 + 0.30 * r / (n - 1)) for r in range(n)]
         for m in lats:
@@ -1016,7 +1019,7 @@ def run_batch_case(args):
     finally:
         for m in lats:
             m.close()
-    return {"case": args.case, "layout": layout, "value": round(n * L ** 3 * args.steps / (sec * 1e9), 3),
+    return {"case": args.case, "layout": layout, "value": round(sum(x ** 3 for x in sizes) * args.steps / (sec * 1e9), 3),
             "unit": UNIT, "steps": args.steps}
 
 
