@@ -164,9 +164,9 @@ __device__ void finalize_sweep(const BatchArgs &b, int s) {
 template <int P>
 constexpr int kBatchVec = (P == HS_FP64) ? 2 : 4;  // batch_vec()
 
-// AX = 1: every member's easy axis is (0, 0, 1), so S.e = S_z (the FP32
-// kernels' variant chosen at launch, as for a single lattice); AX = 2: every
-// member's K is +0 as well, so the uniaxial term is left out.
+// AX = 1: every member's easy axis is (0, 0, 1), so S.e = S_z (the FP32 and
+// FP16 kernels' variant chosen at launch, as for a single lattice); AX = 2:
+// every member's K is +0 as well, so the uniaxial term is left out.
 template <int P, int PF, bool CG, int AX = 0>
 __device__ __forceinline__ void batch_pass(const BatchArgs &b, int s, int c) {
     constexpr int V = kBatchVec<P>;
@@ -474,7 +474,7 @@ int occupancy_p(int prefetch) {
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k, kBlock, 0) != cudaSuccess) return 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_pass, kp, kBlock, 0) != cudaSuccess) return 0;
     int occ = blocks < blocks_pass ? blocks : blocks_pass;
-    if constexpr (P == HS_FP32) {  // the launch may take the axis variants: the grid must fit each
+    if constexpr (P == HS_FP32 || P == HS_FP16) {  // the launch may take the axis variants: the grid must fit each
         const void *ks[4] = {
             prefetch ? (const void *)batch_kernel<P, 2, 1> : (const void *)batch_kernel<P, 0, 1>,
             prefetch ? (const void *)batch_pass_kernel<P, 2, 1> : (const void *)batch_pass_kernel<P, 0, 1>,
@@ -489,12 +489,12 @@ int occupancy_p(int prefetch) {
     return occ;
 }
 
-// the axis variant a batch takes: 0 general, 1 e = z for every member, 2 also K = +0 (FP32 only)
+// the axis variant a batch takes: 0 general, 1 e = z for every member, 2 also K = +0 (FP32 and FP16)
 inline int batch_ax(const BatchArgs &b) { return b.zaxis_all ? (b.kzero_all ? 2 : 1) : 0; }
 
-// the S.e = S_z kernels serve FP32 batches whose members all have e = (0, 0, 1)
+// the axis twins serve FP32 and FP16 batches whose members all have e = (0, 0, 1)
 template <int P>
-constexpr bool batch_has_ax() { return P == HS_FP32; }
+constexpr bool batch_has_ax() { return P == HS_FP32 || P == HS_FP16; }
 
 template <int P>
 cudaError_t passes_p(const BatchArgs &b, int grid, cudaStream_t s, int prefetch) {

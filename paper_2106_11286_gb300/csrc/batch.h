@@ -45,8 +45,8 @@ struct BatchArgs {
     int *error;              // latched device error (barrier timeout)
     int n_total, n_equil;    // sweeps, of which the first n_equil unmeasured
     int inject_skip;         // test hook: 1 = CTA 0 skips its first barrier arrival
-    int zaxis_all;           // 1: every member's easy axis is (0, 0, 1): FP32 runs the S.e = S_z kernels
-    int kzero_all;           // 1: besides, every member's K is +0: FP32 runs the kernels without the K term
+    int zaxis_all;           // 1: every member's easy axis is (0, 0, 1): FP32 / FP16 run the S.e = S_z kernels
+    int kzero_all;           // 1: besides, every member's K is +0: they run the kernels without the K term
 };
 
 // sites per work item of a batch member: 16-byte loads for FP64 and FP32,

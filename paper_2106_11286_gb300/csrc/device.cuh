@@ -820,8 +820,8 @@ __device__ __forceinline__ bool update_f32(Vec<typename Tr<P>::S, V> (&s)[3], co
 
 // AX = 1: the kernel was chosen for e = (0, 0, 1) at launch, so S.e = S_z
 // with no branch (the FP32 register stencil's form); AX = 2: the same with
-// K = +0 (the FP32 batch kernels); AX = 0: FP64 and FP16 decide per work item
-// from PassArgs::zaxis, FP32 takes the general products.
+// K = +0 (the FP32 and FP16 batch kernels); AX = 0: FP64 and FP16 decide per
+// work item from PassArgs::zaxis, FP32 takes the general products.
 template <int P, int V, bool MEAS, bool TEN = false, int AX = 0>
 __device__ __forceinline__ bool update_item_h(Vec<typename Tr<P>::S, V> (&s)[3], const typename Tr<P>::C (&h)[3][V],
                                               uint32_t site0, uint32_t rank0, int c, const PassArgs &a,
